@@ -1,0 +1,269 @@
+"""First-order generalized-harmonic (GH) system: RHS, constraints, boundaries (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The paper names the GH evolution equations ("GHEqns", Sec. 3.1 and Sec. 3.5)
+and the three boundary cases (Sec. 5: characteristic data exchanged at
+internal boundaries, conditions at the outer boundary, nothing at the
+excision boundary) without printing them.  The equations below are the
+standard first-order GH system (Lindblom, Scheel, Kidder, Owen & Rinne 2006),
+restated from the mathematics; the boundary treatment is the simplified
+characteristic one documented in ``rhs_with_boundaries``.
+
+Per point the 50 evolved fields are psi_ab (10), Pi_ab (10) and Phi_iab (30),
+symmetric pairs packed in the order (00,01,02,03,11,12,13,22,23,33):
+field index psi = p, Pi = 10 + p, Phi_i = 20 + 10 i + p.
+
+All pointwise functions take arrays with arbitrary leading (point) axes and
+trailing tensor axes, and are written with einsum index strings that mirror
+the equations term by term.
+"""
+import numpy as np
+
+PAIRS = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+NF = 50
+
+
+# ----------------------------------------------------------------- packing
+def unpack_fields(u):
+    """u[..., 50] -> psi[..., 4, 4], Pi[..., 4, 4], Phi[..., 3, 4, 4]."""
+    shp = u.shape[:-1]
+    psi = np.zeros(shp + (4, 4))
+    Pi = np.zeros(shp + (4, 4))
+    Phi = np.zeros(shp + (3, 4, 4))
+    for p, (a, b) in enumerate(PAIRS):
+        psi[..., a, b] = psi[..., b, a] = u[..., p]
+        Pi[..., a, b] = Pi[..., b, a] = u[..., 10 + p]
+        for i in range(3):
+            Phi[..., i, a, b] = Phi[..., i, b, a] = u[..., 20 + 10 * i + p]
+    return psi, Pi, Phi
+
+
+def pack_fields(psi, Pi, Phi):
+    """Inverse of unpack_fields (reads the a <= b entries)."""
+    shp = psi.shape[:-2]
+    u = np.zeros(shp + (50,))
+    for p, (a, b) in enumerate(PAIRS):
+        u[..., p] = psi[..., a, b]
+        u[..., 10 + p] = Pi[..., a, b]
+        for i in range(3):
+            u[..., 20 + 10 * i + p] = Phi[..., i, a, b]
+    return u
+
+
+# --------------------------------------------------------------- 3+1 split
+def spacetime_split(psi):
+    """Lapse, shift, spatial inverse metric, normal and inverse spacetime metric.
+
+    g_ij = psi_ij, g^ij its inverse, beta_i = psi_0i, beta^i = g^ij beta_j,
+    alpha = sqrt(beta^i beta_i - psi_00), t^a = (1, -beta^i)/alpha,
+    t_a = (-alpha, 0, 0, 0), psi^ab = g^ab-with-shift: psi^00 = -1/alpha^2,
+    psi^0i = beta^i/alpha^2, psi^ij = g^ij - beta^i beta^j/alpha^2, and the
+    spatial projector g^i_a = delta^i_a + t^i t_a.
+    """
+    g = psi[..., 1:, 1:]
+    ginv = np.linalg.inv(g)
+    beta_dn = psi[..., 0, 1:]
+    beta_up = np.einsum("...ij,...j->...i", ginv, beta_dn)
+    alpha = np.sqrt(np.einsum("...i,...i->...", beta_up, beta_dn) - psi[..., 0, 0])
+    shp = alpha.shape
+    t_up = np.zeros(shp + (4,))
+    t_up[..., 0] = 1.0 / alpha
+    t_up[..., 1:] = -beta_up / alpha[..., None]
+    t_dn = np.zeros(shp + (4,))
+    t_dn[..., 0] = -alpha
+    psi_inv = np.zeros(shp + (4, 4))
+    a2 = alpha * alpha
+    psi_inv[..., 0, 0] = -1.0 / a2
+    psi_inv[..., 0, 1:] = beta_up / a2[..., None]
+    psi_inv[..., 1:, 0] = beta_up / a2[..., None]
+    psi_inv[..., 1:, 1:] = ginv - np.einsum("...i,...j->...ij", beta_up, beta_up) / a2[..., None, None]
+    proj = np.zeros(shp + (3, 4))                     # g^i_a
+    for i in range(3):
+        proj[..., i, 1 + i] = 1.0
+    proj = proj + np.einsum("...i,...a->...ia", t_up[..., 1:], t_dn)
+    return dict(ginv=ginv, beta_dn=beta_dn, beta_up=beta_up, alpha=alpha,
+                t_up=t_up, t_dn=t_dn, psi_inv=psi_inv, proj=proj)
+
+
+def christoffel_first_kind(s, Pi, Phi):
+    """d_c psi_ab = t_c Pi_ab + g^i_c Phi_iab and Gamma_abc = (d_b psi_ac + d_c psi_ab - d_a psi_bc)/2."""
+    d = (np.einsum("...c,...ab->...cab", s["t_dn"], Pi)
+         + np.einsum("...ic,...iab->...cab", s["proj"], Phi))
+    Gam = 0.5 * (np.einsum("...bac->...abc", d) + np.einsum("...cab->...abc", d)
+                 - np.einsum("...abc->...abc", d))
+    return d, Gam
+
+
+def gauge_constraint(s, Gam, H):
+    """C_a = H_a + Gamma_a, Gamma_a = psi^bc Gamma_abc."""
+    return H + np.einsum("...bc,...abc->...a", s["psi_inv"], Gam)
+
+
+# ---------------------------------------------------------- GH right-hand side
+def gh_rhs_pointwise(u, du, H, dH, gamma0, gamma1, gamma2):
+    """Time derivative of the 50 GH fields at each point.
+
+    u[..., 50]; du[..., 3, 50] = d_k u (Cartesian); H[..., 4] = H_a;
+    dH[..., 3, 4] = d_i H_a (d_t H_a = 0).  Returns dudt[..., 50].
+
+    d_t psi_ab = (1+g1) b^k d_k psi_ab - N Pi_ab - g1 b^i Phi_iab
+    d_t Pi_ab  = b^k d_k Pi_ab - N g^ki d_k Phi_iab + g1 g2 b^k d_k psi_ab
+                 + 2N psi^cd (g^ij Phi_ica Phi_jdb - Pi_ca Pi_db - psi^ef Gam_ace Gam_bdf)
+                 - 2N nabla_(a H_b) - N/2 t^c t^d Pi_cd Pi_ab - N t^c Pi_ci g^ij Phi_jab
+                 + N g0 (2 delta^c_(a t_b) - psi_ab t^c) C_c - g1 g2 b^i Phi_iab
+    d_t Phi_iab = b^k d_k Phi_iab - N d_i Pi_ab + N g2 d_i psi_ab
+                 + N/2 t^c t^d Phi_icd Pi_ab + N g^jk t^c Phi_ijc Phi_kab - N g2 Phi_iab
+    with N = alpha, b = beta, nabla_a H_b = d_a H_b - psi^cd Gam_dab H_c.
+    """
+    psi, Pi, Phi = unpack_fields(u)
+    dpsi, dPi, dPhi = unpack_fields(du)              # dpsi[...,k,a,b], dPhi[...,k,i,a,b]
+    s = spacetime_split(psi)
+    N = s["alpha"]
+    b_up = s["beta_up"]
+    ginv = s["ginv"]
+    t_up, t_dn = s["t_up"], s["t_dn"]
+    psi_inv = s["psi_inv"]
+    _, Gam = christoffel_first_kind(s, Pi, Phi)
+    C = gauge_constraint(s, Gam, H)
+
+    shp = N.shape
+    dH4 = np.zeros(shp + (4, 4))                     # d_a H_b, d_0 H_b = 0
+    dH4[..., 1:, :] = dH
+    Gam_up = np.einsum("...cd,...dab->...cab", psi_inv, Gam)
+    nablaH = dH4 - np.einsum("...cab,...c->...ab", Gam_up, H)
+    nablaH_sym = 0.5 * (nablaH + np.einsum("...ab->...ba", nablaH))
+
+    Nb = N[..., None, None]
+    Ni = N[..., None, None, None]
+
+    dt_psi = ((1.0 + gamma1) * np.einsum("...k,...kab->...ab", b_up, dpsi)
+              - Nb * Pi
+              - gamma1 * np.einsum("...i,...iab->...ab", b_up, Phi))
+
+    quad = (np.einsum("...cd,...ij,...ica,...jdb->...ab", psi_inv, ginv, Phi, Phi)
+            - np.einsum("...cd,...ca,...db->...ab", psi_inv, Pi, Pi)
+            - np.einsum("...cd,...ef,...ace,...bdf->...ab", psi_inv, psi_inv, Gam, Gam))
+    tPt = np.einsum("...c,...d,...cd->...", t_up, t_up, Pi)
+    tPi_i = np.einsum("...c,...ci->...i", t_up, Pi[..., :, 1:])
+    tC = np.einsum("...c,...c->...", t_up, C)
+    damp = (np.einsum("...b,...a->...ab", t_dn, C) + np.einsum("...a,...b->...ab", t_dn, C)
+            - psi * tC[..., None, None])
+    dt_Pi = (np.einsum("...k,...kab->...ab", b_up, dPi)
+             - Nb * np.einsum("...ki,...kiab->...ab", ginv, dPhi)
+             + gamma1 * gamma2 * np.einsum("...k,...kab->...ab", b_up, dpsi)
+             + 2.0 * Nb * quad
+             - 2.0 * Nb * nablaH_sym
+             - 0.5 * Nb * tPt[..., None, None] * Pi
+             - Nb * np.einsum("...i,...ij,...jab->...ab", tPi_i, ginv, Phi)
+             + gamma0 * Nb * damp
+             - gamma1 * gamma2 * np.einsum("...i,...iab->...ab", b_up, Phi))
+
+    tPhit = np.einsum("...c,...d,...icd->...i", t_up, t_up, Phi)
+    dt_Phi = (np.einsum("...k,...kiab->...iab", b_up, dPhi)
+              - Ni * dPi
+              + gamma2 * Ni * dpsi
+              + 0.5 * Ni * np.einsum("...i,...ab->...iab", tPhit, Pi)
+              + Ni * np.einsum("...jk,...c,...ijc,...kab->...iab", ginv, t_up, Phi[..., :, 1:, :], Phi)
+              - gamma2 * Ni * Phi)
+    return pack_fields(dt_psi, dt_Pi, dt_Phi)
+
+
+# --------------------------------------------------------------- constraints
+def constraints_pointwise(u, du, H):
+    """The 64 stored constraint components per point.
+
+    [0:4]   C_a = H_a + Gamma_a
+    [4:34]  C_iab = d_i psi_ab - Phi_iab   (index 4 + 10 i + p)
+    [34:64] C_ijab = d_i Phi_jab - d_j Phi_iab for (i,j) = (x,y),(x,z),(y,z)
+            (index 34 + 10 q + p)
+    """
+    psi, Pi, Phi = unpack_fields(u)
+    dpsi, dPi, dPhi = unpack_fields(du)
+    s = spacetime_split(psi)
+    _, Gam = christoffel_first_kind(s, Pi, Phi)
+    C = gauge_constraint(s, Gam, H)
+    shp = C.shape[:-1]
+    out = np.zeros(shp + (64,))
+    out[..., 0:4] = C
+    C3 = dpsi - Phi
+    C4 = np.einsum("...ijab->...ijab", dPhi) - np.einsum("...jiab->...ijab", dPhi)
+    for p, (a, b) in enumerate(PAIRS):
+        for i in range(3):
+            out[..., 4 + 10 * i + p] = C3[..., i, a, b]
+        for q, (i, j) in enumerate([(0, 1), (0, 2), (1, 2)]):
+            out[..., 34 + 10 * q + p] = C4[..., i, j, a, b]
+    return out
+
+
+# ---------------------------------------------------- characteristic fields
+def boundary_background(psi_bg, X, Y, Z):
+    """Unit normal and speeds data from the background metric at boundary points.
+
+    n_i = d_i R / |d R|_g with R the Euclidean radius, n^i = g^ij n_j.
+    Returns dict with n_dn[...,3], n_up[...,3], alpha, beta_up[...,3].
+    """
+    s = spacetime_split(psi_bg)
+    R = np.sqrt(X * X + Y * Y + Z * Z)
+    dR = np.stack([X / R, Y / R, Z / R], axis=-1)
+    norm = np.sqrt(np.einsum("...ij,...i,...j->...", s["ginv"], dR, dR))
+    n_dn = dR / norm[..., None]
+    n_up = np.einsum("...ij,...j->...i", s["ginv"], n_dn)
+    return dict(n_dn=n_dn, n_up=n_up, alpha=s["alpha"], beta_up=s["beta_up"])
+
+
+def char_speeds(bg, gamma1):
+    """Speeds (v_psi, v_0, v_plus, v_minus) along n = +R direction."""
+    nb = np.einsum("...i,...i->...", bg["n_dn"], bg["beta_up"])
+    return (-(1.0 + gamma1) * nb, -nb, -nb + bg["alpha"], -nb - bg["alpha"])
+
+
+def to_char(v, bg, gamma2):
+    """Characteristic projection of a field vector v[..., 50].
+
+    w_psi = psi, w_0_iab = P_i^k Phi_kab (P_i^k = delta_i^k - n_i n^k),
+    w_pm = Pi +- n^k Phi_kab - gamma2 psi.
+    """
+    psi, Pi, Phi = unpack_fields(v)
+    nPhi = np.einsum("...k,...kab->...ab", bg["n_up"], Phi)
+    w0 = Phi - np.einsum("...i,...ab->...iab", bg["n_dn"], nPhi)
+    wp = Pi + nPhi - gamma2 * psi
+    wm = Pi - nPhi - gamma2 * psi
+    return psi, w0, wp, wm
+
+
+def from_char(wpsi, w0, wp, wm, bg, gamma2):
+    """Inverse of to_char: psi = w_psi, Pi = (w+ + w-)/2 + gamma2 w_psi,
+    Phi_iab = n_i (w+ - w-)/2 + w_0_iab."""
+    psi = wpsi
+    Pi = 0.5 * (wp + wm) + gamma2 * wpsi
+    Phi = np.einsum("...i,...ab->...iab", bg["n_dn"], 0.5 * (wp - wm)) + w0
+    return pack_fields(psi, Pi, Phi)
+
+
+def apply_outer_bc(dudt_b, bg, gamma1, gamma2):
+    """Freezing condition: incoming (v < 0) characteristic time derivatives set to 0."""
+    w = list(to_char(dudt_b, bg, gamma2))
+    for q, v in enumerate(char_speeds(bg, gamma1)):
+        mask = (v < 0.0)
+        w[q] = np.where(mask.reshape(mask.shape + (1,) * (w[q].ndim - mask.ndim)), 0.0, w[q])
+    return from_char(*w, bg, gamma2)
+
+
+def apply_interface_bc(dudt_in, dudt_out, bg, gamma1, gamma2):
+    """Upwind exchange at a shared radius between an inner and an outer shell.
+
+    With n along +R: a field with v < 0 travels inward, so both sides take the
+    outer shell's value; v > 0: both take the inner shell's; v == 0: each keeps
+    its own.  Returns the new (dudt_in, dudt_out) boundary slices.
+    """
+    wi = list(to_char(dudt_in, bg, gamma2))
+    wo = list(to_char(dudt_out, bg, gamma2))
+    for q, v in enumerate(char_speeds(bg, gamma1)):
+        shp = v.shape + (1,) * (wi[q].ndim - v.ndim)
+        neg = (v < 0.0).reshape(shp)
+        pos = (v > 0.0).reshape(shp)
+        new_i = np.where(neg, wo[q], wi[q])
+        new_o = np.where(pos, wi[q], wo[q])
+        wi[q], wo[q] = new_i, new_o
+    return from_char(*wi, bg, gamma2), from_char(*wo, bg, gamma2)

@@ -1,0 +1,378 @@
+"""Pins of the CPU oracle against what the mathematics and the paper fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, textbook formulas, a library routine (scipy), exact quadrature
+identities, the exact Kerr-Schild solution (the paper's stationary test
+problem, Sec. 3.1), or brute-force finite differences.  None of these tests
+needs a GPU.
+"""
+import numpy as np
+import pytest
+from scipy.special import sph_harm_y
+
+from oracle import grid, spectral, gh, kerr_schild, evolve
+
+
+# ------------------------------------------------------------------ grids
+@pytest.mark.parametrize("n", [5, 8, 11, 21])
+def test_clenshaw_curtis_exact_on_polynomials(n):
+    x = grid.cgl_nodes(n)
+    w = grid.clenshaw_curtis_weights(n)
+    for k in range(n):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, x ** k) - exact) < 1e-14
+
+
+@pytest.mark.parametrize("L", [3, 7, 15])
+def test_gauss_legendre_exact_to_degree_2L_plus_1(L):
+    g = grid.shell_grid(1.0, 2.0, 5, L)
+    for k in range(2 * L + 2):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(g["wth"], g["cth"] ** k) - exact) < 1e-14
+    assert np.all(np.diff(g["theta"]) > 0)
+
+
+def test_volume_weights_sum_to_shell_volume():
+    for (a, b, n, L) in [(1.8, 10.0, 11, 7), (1.3, 3.0, 21, 15)]:
+        g = grid.shell_grid(a, b, n, L)
+        vol = 4.0 * np.pi * (b ** 3 - a ** 3) / 3.0
+        assert abs(grid.volume_weights(g).sum() - vol) < 1e-13 * vol
+
+
+# ----------------------------------------------------------- radial part
+def test_radial_derivative_exact_below_degree_n_r():
+    g = grid.shell_grid(1.8, 10.0, 11, 3)
+    x = g["x"]
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal(11)
+    u = np.polynomial.polynomial.polyval(x, c)
+    du = np.polynomial.polynomial.polyval(x, np.polynomial.polynomial.polyder(c))
+    got = spectral.radial_derivative(u[:, None, None] * np.ones((1, 4, 8)), g)
+    assert np.abs(got[:, 0, 0] - du * 2.0 / 8.2).max() < 1e-12 * np.abs(du).max()
+
+
+def _textbook_cgl_matrix(x):
+    """Closed-form Chebyshev collocation derivative matrix (Gottlieb-Hussaini form)."""
+    n = len(x)
+    c = np.ones(n)
+    c[0] = c[-1] = 2.0
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                D[i, j] = (c[i] / c[j]) * (-1.0) ** (i + j) / (x[i] - x[j])
+    D -= np.diag(D.sum(axis=1))
+    return D
+
+
+@pytest.mark.parametrize("n", [5, 11, 21])
+def test_radial_derivative_delta_probe_is_textbook_matrix(n):
+    """Trace the oracle's operator with delta inputs (the paper's tracing idea,
+    Sec. 3.4) and compare with the closed-form collocation matrix."""
+    g = grid.shell_grid(-1.0, 1.0, n, 1)
+    probe = np.eye(n)[:, :, None, None] * np.ones((1, 1, 2, 4))
+    Dtraced = spectral.radial_derivative(probe, g)[:, :, 0, 0]
+    assert np.abs(Dtraced - _textbook_cgl_matrix(g["x"])).max() < 1e-11 * n * n
+
+
+def test_expcheb_filter_scales_each_chebyshev_mode():
+    g = grid.shell_grid(-1.0, 1.0, 11, 1)
+    s = spectral.expcheb_sigma(11, 36.0, 32)
+    assert s[0] == 1.0 and abs(s[-1] - np.exp(-36.0)) < 1e-30
+    for k in [0, 3, 7, 10]:
+        Tk = spectral.cheb_T(k, g["x"])[:, None, None] * np.ones((1, 2, 4))
+        out = spectral.radial_filter(Tk, g, 36.0, 32)
+        assert np.abs(out - s[k] * Tk).max() < 1e-13
+
+
+# ---------------------------------------------------------- angular part
+def _real_from_scipy(l, m, th, ph, diff):
+    """Real Y_lm (up to the per-mode sign convention) from scipy's complex one."""
+    mm = abs(m)
+    if diff:
+        y, dy = sph_harm_y(l, mm, th, ph, diff_n=1)
+        y = dy[..., 0]
+    else:
+        y = sph_harm_y(l, mm, th, ph)
+    if m == 0:
+        return np.real(y)
+    return np.sqrt(2.0) * (np.real(y) if m > 0 else np.imag(y))
+
+
+@pytest.mark.parametrize("L", [2, 7])
+def test_real_ylm_and_dtheta_match_scipy(L):
+    g = grid.shell_grid(1.0, 2.0, 3, L)
+    TH, PH = np.meshgrid(g["theta"], g["phi"], indexing="ij")
+    Y = spectral.real_ylm(L, g["theta"], g["phi"])
+    dY = spectral.real_ylm_dtheta(L, g["theta"], g["phi"])
+    for i, (l, m) in enumerate(spectral.sh_modes(L)):
+        ref = _real_from_scipy(l, m, TH, PH, False)
+        dref = _real_from_scipy(l, m, TH, PH, True)
+        k = np.argmax(np.abs(ref))
+        sgn = np.sign(Y[i].flat[k] / ref.flat[k])
+        assert np.abs(Y[i] - sgn * ref).max() < 1e-13
+        assert np.abs(dY[i] - sgn * dref).max() < 1e-12 * max(1.0, l)
+
+
+def test_dtheta_closed_forms_low_l():
+    th = np.linspace(0.1, 3.0, 7)
+    dY = spectral.real_ylm_dtheta(2, th, np.zeros(1))[:, :, 0]
+    modes = spectral.sh_modes(2)
+    i10 = modes.index((1, 0))
+    i20 = modes.index((2, 0))
+    assert np.abs(dY[i10] + np.sqrt(3 / (4 * np.pi)) * np.sin(th)).max() < 1e-14
+    ref20 = np.sqrt(5 / (16 * np.pi)) * (-6.0 * np.cos(th) * np.sin(th))
+    assert np.abs(dY[i20] - ref20).max() < 1e-14
+
+
+def test_real_ylm_orthonormal_on_grid():
+    g = grid.shell_grid(1.0, 2.0, 3, 7)
+    Y = spectral.real_ylm(7, g["theta"], g["phi"])
+    w = g["wth"][:, None] * g["wphi"]
+    G = np.einsum("ajk,bjk,jk->ab", Y, Y, w)
+    assert np.abs(G - np.eye(len(Y))).max() < 1e-13
+
+
+def test_sh_truncation_filter_keeps_low_l_and_drops_high_l():
+    L, keep = 7, 4
+    g = grid.shell_grid(1.0, 2.0, 3, L)
+    Y = spectral.real_ylm(L, g["theta"], g["phi"])
+    for i, (l, m) in enumerate(spectral.sh_modes(L)):
+        out = spectral.sh_truncation_filter(Y[i][None], g, keep)[0]
+        ref = Y[i] if l <= keep else 0.0 * Y[i]
+        assert np.abs(out - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("n_r,L,deg", [(11, 7, 5), (9, 5, 5)])
+def test_cartesian_gradient_exact_on_polynomials(n_r, L, deg):
+    """Radial + angular derivatives + DiffJac: exact on polynomials in (x,y,z)
+    of total degree <= min(n_r - 1, L)."""
+    g = grid.shell_grid(1.8, 10.0, n_r, L)
+    X, Y, Z = grid.cartesian_coords(g)
+    rng = np.random.default_rng(3)
+    terms = [(a, b, c) for a in range(deg + 1) for b in range(deg + 1 - a)
+             for c in range(deg + 1 - a - b)]
+    coef = rng.standard_normal(len(terms))
+    f = sum(k * X ** a * Y ** b * Z ** c for k, (a, b, c) in zip(coef, terms))
+    fx = sum(k * a * X ** max(a - 1, 0) * Y ** b * Z ** c for k, (a, b, c) in zip(coef, terms))
+    fy = sum(k * b * X ** a * Y ** max(b - 1, 0) * Z ** c for k, (a, b, c) in zip(coef, terms))
+    fz = sum(k * c * X ** a * Y ** b * Z ** max(c - 1, 0) for k, (a, b, c) in zip(coef, terms))
+    d = spectral.cartesian_gradient(f[:, None], g)[:, :, 0]
+    scale = np.abs(f).max()
+    for i, ref in enumerate([fx, fy, fz]):
+        assert np.abs(d[i] - ref).max() < 1e-11 * scale
+
+
+# ----------------------------------------------------------- Kerr-Schild
+def _sample_points():
+    rng = np.random.default_rng(5)
+    P = rng.uniform(-6, 6, size=(40, 3))
+    P = P[np.linalg.norm(P, axis=1) > 2.0]
+    return P[:, 0], P[:, 1], P[:, 2]
+
+
+@pytest.mark.parametrize("chi", [0.0, 0.9])
+def test_kerr_schild_null_vector_and_determinant(chi):
+    X, Y, Z = _sample_points()
+    g, dg, ddg = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, chi)
+    assert np.abs(np.linalg.det(g) + 1.0).max() < 1e-12
+    eta = np.diag([-1.0, 1, 1, 1])
+    # l_a l_b = (g - eta)/(2H) has rank one; l is null: eta^ab (g-eta)_ab = 0
+    assert np.abs(np.einsum("ab,...ab->...", eta, g - eta)).max() < 1e-13
+
+
+def test_kerr_schild_reduces_to_schwarzschild():
+    X, Y, Z = _sample_points()
+    g, _, _ = kerr_schild.metric_and_derivatives(X, Y, Z, 1.3, 0.0)
+    R = np.sqrt(X * X + Y * Y + Z * Z)
+    l = np.stack([np.ones_like(R), X / R, Y / R, Z / R], axis=-1)
+    ref = np.diag([-1.0, 1, 1, 1]) + 2 * (1.3 / R)[:, None, None] * l[:, :, None] * l[:, None, :]
+    assert np.abs(g - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("chi", [0.0, 0.9])
+def test_kerr_schild_derivatives_match_finite_differences(chi):
+    X, Y, Z = _sample_points()
+    g, dg, ddg = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, chi)
+    h = 1e-5
+    for i in range(3):
+        e = [0.0, 0.0, 0.0]
+        e[i] = h
+        gp, dgp, _ = kerr_schild.metric_and_derivatives(X + e[0], Y + e[1], Z + e[2], 1.0, chi)
+        gm, dgm, _ = kerr_schild.metric_and_derivatives(X - e[0], Y - e[1], Z - e[2], 1.0, chi)
+        assert np.abs((gp - gm) / (2 * h) - dg[:, i]).max() < 1e-8
+        assert np.abs((dgp - dgm) / (2 * h) - ddg[:, :, i]).max() < 1e-7
+
+
+@pytest.mark.parametrize("chi", [0.0, 0.9])
+def test_gauge_source_zeroes_gauge_constraint_and_dH_matches_fd(chi):
+    """H_a = -Gamma_a computed from d g (kerr_schild) makes C_a = H_a + Gamma_a,
+    computed through the t/Pi/Phi identity (gh), vanish; d_i H by FD."""
+    X, Y, Z = _sample_points()
+    g, dg, ddg = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, chi)
+    H, dH = kerr_schild.gauge_source(g, dg, ddg)
+    psi, Pi, Phi = kerr_schild.gh_fields(g, dg)
+    s = gh.spacetime_split(psi)
+    _, Gam = gh.christoffel_first_kind(s, Pi, Phi)
+    assert np.abs(gh.gauge_constraint(s, Gam, H)).max() < 1e-13
+    h = 1e-5
+    for i in range(3):
+        e = [0.0, 0.0, 0.0]
+        e[i] = h
+        Hp, _ = kerr_schild.gauge_source(*kerr_schild.metric_and_derivatives(
+            X + e[0], Y + e[1], Z + e[2], 1.0, chi))
+        Hm, _ = kerr_schild.gauge_source(*kerr_schild.metric_and_derivatives(
+            X - e[0], Y - e[1], Z - e[2], 1.0, chi))
+        assert np.abs((Hp - Hm) / (2 * h) - dH[:, i]).max() < 1e-7
+
+
+def test_inverse_spacetime_metric():
+    X, Y, Z = _sample_points()
+    g, _, _ = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, 0.7)
+    s = gh.spacetime_split(g)
+    assert np.abs(np.einsum("...ab,...bc->...ac", s["psi_inv"], g) - np.eye(4)).max() < 1e-13
+
+
+# ------------------------------------------------------- GH right-hand side
+@pytest.mark.slow
+@pytest.mark.parametrize("chi,shell", [(0.0, (1.8, 10.0)), (0.9, (3.0, 6.0))])
+def test_rhs_of_exact_kerr_schild_converges_exponentially(chi, shell):
+    """The stationary exact solution has d_t u = 0: the discrete RHS is pure
+    truncation error and must fall exponentially with resolution (this pins
+    every term of the RHS that does not multiply a constraint)."""
+    errs = []
+    for (n_r, L) in [(11, 7), (17, 13), (23, 19)]:
+        dom = evolve.Domain([(shell[0], shell[1], n_r, L)], 1.0, chi)
+        errs.append(np.abs(evolve.rhs_interior(dom, dom.u_exact)[0]).max())
+    assert errs[1] < 0.05 * errs[0] and errs[2] < 0.05 * errs[1], errs
+    assert errs[2] < 1e-6
+
+
+def _minkowski_point_state(rng, n=6):
+    psi = np.broadcast_to(np.diag([-1.0, 1, 1, 1]), (n, 4, 4)).copy()
+    Pi = np.zeros((n, 4, 4))
+    Phi = rng.standard_normal((n, 3, 4, 4))
+    Phi = 0.5 * (Phi + np.swapaxes(Phi, -1, -2))
+    Phi[:, :, 0, :] = 0.0
+    Phi[:, :, :, 0] = 0.0
+    return psi, Pi, Phi
+
+
+def test_three_index_constraint_decays_at_rate_gamma2_on_minkowski():
+    """alpha=1, beta=0, Pi=0, Phi_i0b=0 and d psi = 0: C_iab = -Phi_iab and the
+    RHS gives d_t C_iab = -gamma2 C_iab exactly (linear damping)."""
+    rng = np.random.default_rng(11)
+    psi, Pi, Phi = _minkowski_point_state(rng)
+    u = gh.pack_fields(psi, Pi, Phi)
+    du = np.zeros(u.shape[:-1] + (3, 50))
+    du[..., 20:] = rng.standard_normal(du[..., 20:].shape)   # d_k Phi arbitrary
+    for g2 in [0.5, 1.0, 2.0]:
+        r = gh.gh_rhs_pointwise(u, du, np.zeros((len(u), 4)), np.zeros((len(u), 3, 4)), 1.0, -1.0, g2)
+        _, dPi, dPhi = gh.unpack_fields(r)
+        dpsi_dt, _, _ = gh.unpack_fields(r)
+        # d_t C_iab = d_i (d_t psi_ab) - d_t Phi_iab; d_t psi is spatially constant (0) here
+        assert np.abs(dpsi_dt).max() < 1e-15
+        assert np.abs(-dPhi - (-g2) * (-Phi)).max() < 1e-14
+
+
+def test_gauge_constraint_damping_rates_on_minkowski():
+    """psi = eta, Pi = Phi = 0, d H = 0 and H = h: C_a = h_a.  The gamma0 term
+    gives d_t C_0 = -2 gamma0 C_0 and d_t C_i = -gamma0 C_i; checked by a
+    directional derivative of the oracle's own C_a along its own RHS."""
+    rng = np.random.default_rng(12)
+    n = 5
+    psi = np.broadcast_to(np.diag([-1.0, 1, 1, 1]), (n, 4, 4)).copy()
+    u = gh.pack_fields(psi, np.zeros((n, 4, 4)), np.zeros((n, 3, 4, 4)))
+    h = rng.standard_normal((n, 4))
+    du = np.zeros((n, 3, 50))
+    zero_dH = np.zeros((n, 3, 4))
+    for g0 in [0.5, 1.0]:
+        r = gh.gh_rhs_pointwise(u, du, h, zero_dH, g0, -1.0, 1.0)
+        eps = 1e-6
+
+        def C(v):
+            p, P, F = gh.unpack_fields(v)
+            s = gh.spacetime_split(p)
+            _, Gam = gh.christoffel_first_kind(s, P, F)
+            return gh.gauge_constraint(s, Gam, h)
+        dC = (C(u + eps * r) - C(u - eps * r)) / (2 * eps)
+        assert np.abs(dC[:, 0] - (-2 * g0) * h[:, 0]).max() < 1e-8
+        assert np.abs(dC[:, 1:] - (-g0) * h[:, 1:]).max() < 1e-8
+
+
+def test_gamma1_gamma2_terms_vanish_when_three_index_constraint_vanishes():
+    """Every gamma1 and gamma2 term multiplies C_iab = d_i psi_ab - Phi_iab; with
+    d psi = Phi the RHS does not depend on gamma1, gamma2."""
+    X, Y, Z = _sample_points()
+    g, dg, ddg = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, 0.6)
+    psi, Pi, Phi = kerr_schild.gh_fields(g, dg)
+    rng = np.random.default_rng(13)
+    Pi = Pi + 0.01 * rng.standard_normal(Pi.shape)
+    u = gh.pack_fields(psi, 0.5 * (Pi + np.swapaxes(Pi, -1, -2)), Phi)
+    du = rng.standard_normal(u.shape[:-1] + (3, 50))
+    du[..., 0:10] = u[..., None, 20:50].reshape(u.shape[:-1] + (3, 10))   # d_i psi = Phi_i
+    H = rng.standard_normal((len(X), 4))
+    dH = rng.standard_normal((len(X), 3, 4))
+    r1 = gh.gh_rhs_pointwise(u, du, H, dH, 1.0, -1.0, 1.0)
+    r2 = gh.gh_rhs_pointwise(u, du, H, dH, 1.0, 0.7, 3.0)
+    assert np.abs(r1 - r2).max() < 1e-12 * np.abs(r1).max()
+
+
+# ------------------------------------------------------ characteristic BCs
+def test_characteristic_round_trip():
+    X, Y, Z = _sample_points()
+    g, dg, _ = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, 0.8)
+    bg = gh.boundary_background(g, X, Y, Z)
+    v = np.random.default_rng(4).standard_normal((len(X), 50))
+    w = gh.to_char(v, bg, 1.0)
+    back = gh.from_char(*w, bg, 1.0)
+    psi, Pi, Phi = gh.unpack_fields(v)
+    assert np.abs(back - v).max() < 1e-13
+    assert abs(np.einsum("...i,...i->...", bg["n_dn"], bg["n_up"]) - 1.0).max() < 1e-14
+
+
+@pytest.mark.parametrize("r_in,chi", [(1.8, 0.0), (1.3, 0.9)])
+def test_all_speeds_point_into_the_hole_at_excision(r_in, chi):
+    """Inside the horizon every characteristic speed along +R is <= 0, so the
+    excision boundary needs no condition (the paper's no-op case, Sec. 5)."""
+    g = grid.shell_grid(r_in, 10.0, 5, 7)
+    X, Y, Z = grid.cartesian_coords(g)
+    gm, _, _ = kerr_schild.metric_and_derivatives(X[0], Y[0], Z[0], 1.0, chi)
+    bg = gh.boundary_background(gm, X[0], Y[0], Z[0])
+    for v in gh.char_speeds(bg, -1.0):
+        assert np.all(v <= 1e-15)
+
+
+def test_outer_bc_zeroes_only_incoming_fields():
+    g = grid.shell_grid(1.8, 10.0, 5, 3)
+    X, Y, Z = grid.cartesian_coords(g)
+    gm, _, _ = kerr_schild.metric_and_derivatives(X[-1], Y[-1], Z[-1], 1.0, 0.0)
+    bg = gh.boundary_background(gm, X[-1], Y[-1], Z[-1])
+    v = np.random.default_rng(8).standard_normal(X[-1].shape + (50,))
+    out = gh.apply_outer_bc(v, bg, -1.0, 1.0)
+    w_in = gh.to_char(v, bg, 1.0)
+    w_out = gh.to_char(out, bg, 1.0)
+    vpsi, v0, vp, vm = gh.char_speeds(bg, -1.0)
+    assert np.all(vp > 0) and np.all(vm < 0) and np.all(v0 < 0) and np.all(vpsi == 0)
+    assert np.abs(w_out[0] - w_in[0]).max() < 1e-13      # zero speed: untouched
+    assert np.abs(w_out[2] - w_in[2]).max() < 1e-13      # outgoing: untouched
+    assert np.abs(w_out[1]).max() < 1e-13 and np.abs(w_out[3]).max() < 1e-13
+
+
+# ------------------------------------------------------------------ RK4
+def test_rk4_matches_stability_polynomial(monkeypatch):
+    lam = -0.7 + 0.3j
+    dt = 0.1
+
+    def fake_rhs(dom, u):
+        return [lam * a for a in u]
+
+    class D:
+        radial_filter_on = False
+        sh_keep_l = -1
+        grids = [None]
+    monkeypatch.setattr(evolve, "rhs", fake_rhs)
+    u = [np.ones(3, dtype=complex)]
+    out = evolve.rk4_step(D(), u, dt)
+    z = lam * dt
+    assert abs(out[0][0] - (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24)) < 1e-15
