@@ -1,0 +1,176 @@
+/*
+ * gh.h -- C ABI of libgh: the generalized-harmonic (GH) right-hand side on
+ * spherical-shell spectral subdomains, with RK4, filters and boundary
+ * handling, on one NVIDIA GB300 (sm_103a), in FP64.
+ *
+ * Method: Lewis & Pfeiffer, "GPU-Accelerated Simulations of Isolated Black
+ * Holes" (arXiv:1804.09101).  The paper fixes the structure: collocation data
+ * on I1 x S2 shells expanded in T_k(r) Y_lm (Sec. 3.4), derivatives as cached
+ * linear maps (Sec. 3.4, Eqs. Differentiation and DifferentiatorI1S2), the
+ * DiffJac contraction (Sec. 3.3, Eq. DiffJac), the filters (Sec. 3.4), the GH
+ * equations and the three boundary cases (Sec. 3.5 and Sec. 5), and analytic
+ * Kerr-Schild data of mass m and spin chi (Sec. 3.1).  The GH equations are
+ * the standard first-order system of Lindblom et al. (2006).
+ *
+ * Conventions shared by every call
+ *  - All arrays passed to the library are DEVICE pointers to FP64 data on the
+ *    current CUDA device unless a parameter says "host".  The caller owns them;
+ *    the library never frees or retains them past the call.
+ *  - A state vector holds, for each shell in creation order, the array
+ *    u[r][field][theta][phi] (phi fastest): n_r * 50 * (L+1) * 2(L+1) doubles.
+ *    Field order: psi_ab = p, Pi_ab = 10+p, Phi_iab = 20+10i+p, where
+ *    p enumerates (ab) = 00,01,02,03,11,12,13,22,23,33 and i = x,y,z.
+ *  - Grid of a shell: r at the n_r Chebyshev-Gauss-Lobatto points of
+ *    [r_in, r_out] (ascending), theta at the L+1 Gauss-Legendre points
+ *    (ascending), phi_k = 2 pi k / (2(L+1)).  Cartesian coordinates are the
+ *    Kerr-Schild x, y, z of a hole at the origin with spin along +z.
+ *  - Every call is enqueued on the domain's CUDA stream (gh_set_stream) and
+ *    returns without synchronising, except where stated.  Errors raised on the
+ *    device (a non-finite constraint norm) are latched and reported by
+ *    gh_sync.  No call throws or aborts; each returns a gh_status, and
+ *    gh_last_error gives a one-line reason.
+ */
+#ifndef GH_H
+#define GH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GH_OK = 0,
+  GH_EINVAL = 1,      /* invalid argument (shape, pointer, parameter)          */
+  GH_ENOMEM = 2,      /* device allocation failed                              */
+  GH_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed           */
+  GH_ETIMEOUT = 4,    /* a bounded device-side wait ran out                    */
+  GH_ENONFINITE = 5,  /* a constraint norm came out NaN or Inf                 */
+  GH_ENOTSUP = 6      /* not supported in this build                           */
+} gh_status;
+
+/* One spherical shell: r in [r_in, r_out], n_r radial points, harmonics l <= L.
+ * Requires 0 < r_in < r_out, 3 <= n_r <= 64, 1 <= L <= 47. */
+typedef struct {
+  double r_in, r_out;
+  int n_r, L;
+} gh_shell;
+
+/* Evolution parameters.
+ * gamma0, gamma1, gamma2: GH constraint-damping parameters (Lindblom et al.).
+ * filt_alpha, filt_order: exponential Chebyshev filter sigma_k =
+ *   exp(-alpha (k/(n_r-1))^order) applied along r when radial_filter_on != 0
+ *   (the paper's ExpCheb filter, Sec. 3.4).
+ * sh_keep_l: Heaviside filter in l (keep l <= sh_keep_l) on every shell, or -1
+ *   for none (the paper's Heaviside filter, Sec. 3.4; applied per component). */
+typedef struct {
+  double gamma0, gamma1, gamma2;
+  double filt_alpha;
+  int filt_order;
+  int radial_filter_on;
+  int sh_keep_l;
+} gh_params;
+
+typedef struct gh_domain gh_domain;
+
+/* Create a domain of n_shells concentric shells ordered by radius; shell s+1
+ * must start where shell s ends (r_in[s+1] == r_out[s]).  Builds the cached
+ * operator matrices on the host in FP64 (the paper's matrix dictionary,
+ * Sec. 3.4) and uploads them together with grid tables; allocates the
+ * library's own scratch (three derivative buffers of one state each plus
+ * small tables).  stream: a cudaStream_t or NULL for the legacy stream.
+ * Errors: GH_EINVAL for invalid shells or params, GH_ENOMEM, GH_ECUDA.
+ * The domain starts with zero gauge source and a flat (Minkowski) boundary
+ * background; call gh_set_analytic_kerr_schild or gh_set_gauge and
+ * gh_set_background before evolving. */
+gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params* params,
+                           void* stream, gh_domain** out);
+
+/* Free everything the domain owns.  Synchronises its stream first. */
+gh_status gh_destroy_domain(gh_domain* dom);
+
+/* Change the stream later calls are enqueued on. */
+gh_status gh_set_stream(gh_domain* dom, void* stream);
+
+/* Sizes in doubles: one state vector; one RK4 work area (gh_rk4_step). */
+long long gh_state_size(const gh_domain* dom);
+long long gh_num_points(const gh_domain* dom);
+long long gh_rk4_work_size(const gh_domain* dom);
+int gh_num_shells(const gh_domain* dom);
+
+/* Write the exact Kerr-Schild state of a hole of mass M and dimensionless
+ * spin chi (along +z, a = chi M) into u (device, one state), and set the
+ * domain's gauge source H_a = -Gamma_a, d_i H_a of that solution and the
+ * boundary background used by the characteristic boundary conditions.
+ * Kerr-Schild data: Sec. 3.1 (Eq. dimensionlessspin).  Computed on the
+ * device with forward-mode second-order dual numbers. */
+gh_status gh_set_analytic_kerr_schild(gh_domain* dom, double M, double chi, double* u);
+
+/* Replace the gauge source: H (device) holds, for each shell, [r][4][theta][phi]
+ * with H_a; dH (device) holds [r][12][theta][phi] with entry 4*i + a = d_i H_a.
+ * d_t H_a = 0 always. */
+gh_status gh_set_gauge(gh_domain* dom, const double* H, const double* dH);
+
+/* Copy the domain's gauge source out, in the layout gh_set_gauge takes. */
+gh_status gh_get_gauge(const gh_domain* dom, double* H, double* dH);
+
+/* Take the boundary background (lapse, shift, unit normal used by the
+ * characteristic projection) from the metric part of state u_bg (device). */
+gh_status gh_set_background(gh_domain* dom, const double* u_bg);
+
+/* Add a perturbation to u (device).  kind 0: ingoing Gaussian shell on psi,
+ * dpsi_ab = A exp(-(R-Rc)^2/w^2) sum c_lm Y_lm on all 10 components, with
+ * dPhi_iab = d_i dpsi_ab and dPi_ab = -(d_R dpsi - beta^k d_k dpsi)/alpha from
+ * the boundary background's source metric (the current Kerr-Schild hole).
+ * kind 1: dPi_ab = exp(-((R-Rc)/w)^2) sum c_lm Y_lm on all 10 components
+ * (A ignored).  coeffs (host) holds (lmax+1)^2 real Y_lm coefficients in the
+ * order l = 0..lmax, m = -l..l; Y_lm real orthonormal, sqrt(2) cos(m phi) for
+ * m > 0 and sqrt(2) sin(|m| phi) for m < 0. */
+gh_status gh_add_perturbation(gh_domain* dom, int kind, double A, double Rc, double w,
+                              int lmax, const double* coeffs, double* u);
+
+/* Cartesian derivatives d_i u of all 50 fields: du (device) holds 3 states,
+ * du[i * state_size + ...].  Radial and angular derivative maps (Eq.
+ * DifferentiatorI1S2) followed by the DiffJac contraction (Eq. DiffJac). */
+gh_status gh_derivatives(gh_domain* dom, const double* u, double* du);
+
+/* One right-hand side evaluation dudt = F(u): derivatives, the pointwise GH
+ * equations (GHEqns) and the boundary conditions (ApplyBCs): outer boundary
+ * freezes the incoming characteristic fields, internal boundaries exchange
+ * incoming characteristic time derivatives upwind, the excision boundary is a
+ * no-op (Sec. 5).  u and dudt must not overlap. */
+gh_status gh_rhs(gh_domain* dom, const double* u, double* dudt);
+
+/* One classic RK4 step of size dt on u (device, in place), followed by the
+ * filters the domain's params switch on.  work (device) must hold
+ * gh_rk4_work_size doubles.  If norm2_pre (device, nullable) is given, the
+ * constraint norm of the incoming u is written to norm2_pre[s] for each shell
+ * s (computed inside the first stage, from the same derivatives). */
+gh_status gh_rk4_step(gh_domain* dom, double dt, double* u, double* work, double* norm2_pre);
+
+/* Apply the domain's filters to u (device) in place; work as for gh_rk4_step. */
+gh_status gh_apply_filters(gh_domain* dom, double* u, double* work);
+
+/* Constraints of u: c_out (device, nullable) receives, per shell,
+ * [r][64][theta][phi] with C_a (0..3), C_iab = d_i psi_ab - Phi_iab (4+10i+p) and
+ * C_ijab = d_i Phi_jab - d_j Phi_iab for (ij) = xy,xz,yz (34+10q+p);
+ * norm2 (device) receives per shell sum_points w dV sum_c C_c^2 with the
+ * Clenshaw-Curtis x Gauss-Legendre x uniform quadrature. */
+gh_status gh_constraints(gh_domain* dom, const double* u, double* c_out, double* norm2);
+
+/* Block until the domain's stream is idle; returns the first latched device
+ * error (GH_ENONFINITE) or GH_ECUDA, then clears the latch. */
+gh_status gh_sync(gh_domain* dom);
+
+/* Last error message of this domain (or of the last failed gh_create_domain
+ * when dom is NULL).  Valid until the next call on the same domain. */
+const char* gh_last_error(const gh_domain* dom);
+
+/* Number of kernel launches the library has enqueued on this domain so far. */
+long long gh_launch_count(const gh_domain* dom);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GH_H */

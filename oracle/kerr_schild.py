@@ -125,7 +125,7 @@ def kerr_schild_shell(g_shell, M, chi):
     """Exact KS data on one shell grid (spin chi along +z, a = chi M).
 
     Returns (u[n_r, 50, n_th, n_ph], H[n_r, 4, n_th, n_ph], dH[n_r, 12, n_th, n_ph]);
-    dH is ordered dH[3*i + a] = d_i H_a.
+    dH is ordered dH[4*i + a] = d_i H_a.
     """
     from . import grid
     X, Y, Z = grid.cartesian_coords(g_shell)

@@ -1,0 +1,704 @@
+// libgh host side: grids, the cached operator matrices (the paper's matrix
+// dictionary, Sec. 3.4), domain setup and the C ABI entry points of gh.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gh_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------ grids
+// Chebyshev-Gauss-Lobatto points x_j = -cos(pi j / N), ascending.
+std::vector<double> cgl_points(int n) {
+  std::vector<double> x(n);
+  const int N = n - 1;
+  for (int j = 0; j < n; ++j) x[j] = -std::cos(kPi * j / N);
+  x[0] = -1.0;
+  x[N] = 1.0;
+  return x;
+}
+
+// Clenshaw-Curtis weights on the CGL points (symmetric, so the ascending
+// order needs no change).
+std::vector<double> clenshaw_curtis(int n) {
+  const int N = n - 1;
+  std::vector<double> w(n);
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int k = 1; 2 * k <= N; ++k) {
+      const double b = (2 * k == N) ? 1.0 : 2.0;
+      s += b * std::cos(2.0 * kPi * j * k / N) / (4.0 * k * k - 1.0);
+    }
+    const double c = (j == 0 || j == N) ? 1.0 : 2.0;
+    w[j] = c / N * (1.0 - s);
+  }
+  return w;
+}
+
+// Gauss-Legendre nodes (descending in x, i.e. theta ascending) and weights,
+// by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Normalised associated Legendre functions Pbar_l^m(theta_j) and their theta
+// derivatives, tables [l][m][j] of (L+1)^2 x nth.
+void legendre_tables(int L, const std::vector<double>& ct, const std::vector<double>& st,
+                     std::vector<double>& P, std::vector<double>& dP) {
+  const int nth = (int)ct.size();
+  const int W = L + 1;
+  P.assign((size_t)W * W * nth, 0.0);
+  dP.assign((size_t)W * W * nth, 0.0);
+  auto at = [&](std::vector<double>& T, int l, int m, int j) -> double& {
+    return T[((size_t)l * W + m) * nth + j];
+  };
+  for (int j = 0; j < nth; ++j) {
+    at(P, 0, 0, j) = std::sqrt(0.25 / kPi);
+    for (int m = 1; m <= L; ++m)
+      at(P, m, m, j) = std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * st[j] * at(P, m - 1, m - 1, j);
+    for (int m = 0; m < L; ++m) at(P, m + 1, m, j) = std::sqrt(2.0 * m + 3.0) * ct[j] * at(P, m, m, j);
+    for (int m = 0; m <= L; ++m)
+      for (int l = m + 2; l <= L; ++l) {
+        const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+        const double b = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+        at(P, l, m, j) = a * (ct[j] * at(P, l - 1, m, j) - b * at(P, l - 2, m, j));
+      }
+    // sin(th) dP_l^m/dth = l cos(th) P_l^m - sqrt((2l+1)(l^2-m^2)/(2l-1)) P_{l-1}^m
+    for (int l = 0; l <= L; ++l)
+      for (int m = 0; m <= l; ++m) {
+        const double prev = (l > m) ? at(P, l - 1, m, j) : 0.0;
+        const double c = (l > m) ? std::sqrt((2.0 * l + 1.0) * ((double)l * l - (double)m * m) / (2.0 * l - 1.0)) : 0.0;
+        at(dP, l, m, j) = (l * ct[j] * at(P, l, m, j) - c * prev) / st[j];
+      }
+  }
+}
+
+// ------------------------------------------------------------ matrices
+// d/dx on the CGL points, closed form with the negative-sum diagonal.
+std::vector<double> cgl_derivative_matrix(int n) {
+  const int N = n - 1;
+  std::vector<double> D((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double rowsum = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      const double ci = (i == 0 || i == N) ? 2.0 : 1.0;
+      const double cj = (j == 0 || j == N) ? 2.0 : 1.0;
+      // x_i - x_j = 2 sin(pi (i+j) / 2N) sin(pi (i-j) / 2N)
+      const double dx = 2.0 * std::sin(kPi * (i + j) / (2.0 * N)) * std::sin(kPi * (i - j) / (2.0 * N));
+      const double v = (ci / cj) * (((i + j) % 2) ? -1.0 : 1.0) / dx;
+      D[(size_t)i * n + j] = v;
+      rowsum += v;
+    }
+    D[(size_t)i * n + i] = -rowsum;
+  }
+  return D;
+}
+
+// Exponential Chebyshev filter C^-1 diag(sigma) C on the CGL points.
+std::vector<double> cgl_filter_matrix(int n, double alpha, int order) {
+  const int N = n - 1;
+  std::vector<double> F((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double cj = (j == 0 || j == N) ? 2.0 : 1.0;
+      double acc = 0.0;
+      for (int k = 0; k <= N; ++k) {
+        const double ck = (k == 0 || k == N) ? 2.0 : 1.0;
+        const double sigma = std::exp(-alpha * std::pow((double)k / N, order));
+        const double Ti = std::cos(kPi * k * (N - i) / N);
+        const double Tj = std::cos(kPi * k * (N - j) / N);
+        acc += Ti * sigma * 2.0 / (N * ck * cj) * Tj;
+      }
+      F[(size_t)i * n + j] = acc;
+    }
+  return F;
+}
+
+struct AngularGrid {
+  int L, nth, nph, na;
+  std::vector<double> ct, st, wgl;
+};
+
+AngularGrid angular_grid(int L) {
+  AngularGrid g;
+  g.L = L;
+  g.nth = L + 1;
+  g.nph = 2 * (L + 1);
+  g.na = g.nth * g.nph;
+  gauss_legendre(g.nth, g.ct, g.wgl);
+  g.st.resize(g.nth);
+  for (int j = 0; j < g.nth; ++j) g.st[j] = std::sqrt((1.0 - g.ct[j]) * (1.0 + g.ct[j]));
+  return g;
+}
+
+// Transposed angular maps B[q][p] = M[p][q] for
+//   kind 0: d/dtheta of the projection onto Y_lm, l <= L
+//   kind 1: d/dphi   of the projection onto Y_lm, l <= L
+//   kind 2: projection onto Y_lm with l <= keep (Heaviside filter in l)
+// using M[(j,k)][(j',k')] = W_j' sum_m c_m phi_m(k-k') sum_l A_lm(j) P_lm(j'),
+// c_0 = 1, c_m = 2, phi_m = cos(m dphi) or -m sin(m dphi).
+std::vector<double> angular_matrix(const AngularGrid& g, int kind, int keep) {
+  std::vector<double> P, dP;
+  legendre_tables(g.L, g.ct, g.st, P, dP);
+  const int W = g.L + 1, nth = g.nth, nph = g.nph, na = g.na;
+  const int lmax = (kind == 2) ? keep : g.L;
+  // Q[m][j][j'] = sum_{l=m}^{lmax} A_lm(j) P_lm(j')
+  std::vector<double> Q((size_t)W * nth * nth, 0.0);
+  for (int m = 0; m <= lmax; ++m)
+    for (int j = 0; j < nth; ++j)
+      for (int jp = 0; jp < nth; ++jp) {
+        double acc = 0.0;
+        for (int l = m; l <= lmax; ++l) {
+          const double a = (kind == 0) ? dP[((size_t)l * W + m) * nth + j] : P[((size_t)l * W + m) * nth + j];
+          acc += a * P[((size_t)l * W + m) * nth + jp];
+        }
+        Q[((size_t)m * nth + j) * nth + jp] = acc;
+      }
+  // phi factor table F[m][dk]
+  std::vector<double> F((size_t)W * nph);
+  for (int m = 0; m <= lmax; ++m)
+    for (int dk = 0; dk < nph; ++dk) {
+      const double ang = 2.0 * kPi * m * dk / nph;
+      const double c = (m == 0) ? 1.0 : 2.0;
+      F[(size_t)m * nph + dk] = (kind == 1) ? -c * m * std::sin(ang) : c * std::cos(ang);
+    }
+  const double wphi = 2.0 * kPi / nph;
+  std::vector<double> B((size_t)na * na);
+  for (int j = 0; j < nth; ++j)
+    for (int k = 0; k < nph; ++k) {
+      const int p = j * nph + k;
+      for (int jp = 0; jp < nth; ++jp)
+        for (int kp = 0; kp < nph; ++kp) {
+          const int q = jp * nph + kp;
+          const int dk = ((k - kp) % nph + nph) % nph;
+          double acc = 0.0;
+          for (int m = 0; m <= lmax; ++m)
+            acc += F[(size_t)m * nph + dk] * Q[((size_t)m * nth + j) * nth + jp];
+          B[(size_t)q * na + p] = acc * g.wgl[jp] * wphi;
+        }
+    }
+  return B;
+}
+
+// ------------------------------------------------------------ helpers
+gh_status fail(gh_domain* d, gh_status s, const std::string& msg) {
+  if (d) d->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+#define GH_CUDA(d, call)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail((d), e_ == cudaErrorMemoryAllocation ? GH_ENOMEM : GH_ECUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(gh_domain* d, const std::vector<T>& h, T** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * (h.empty() ? 1 : h.size()));
+  if (e != cudaSuccess) return e;
+  d->owned.push_back(p);
+  if (!h.empty()) e = cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+  *out = (T*)p;
+  return e;
+}
+
+cudaError_t alloc_zero(gh_domain* d, size_t bytes, void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 8);
+  if (e != cudaSuccess) return e;
+  d->owned.push_back(p);
+  e = cudaMemset(p, 0, bytes ? bytes : 8);
+  *out = p;
+  return e;
+}
+
+bool fault_injected(const char* what) {
+  const char* f = std::getenv("GH_FAULT");
+  return f && std::strcmp(f, what) == 0;
+}
+
+gh_status check_latched(gh_domain* d) {
+  if (fault_injected("launch")) return fail(d, GH_ECUDA, "GH_FAULT=launch: injected launch failure");
+  return GH_OK;
+}
+
+gh_status derivatives(gh_domain* d, const double* u) {
+  GH_CUDA(d, gh::launch_radial(d, u, d->d_r, false));
+  GH_CUDA(d, gh::launch_angular_deriv(d, u));
+  return GH_OK;
+}
+
+gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
+  // src -> (radial) -> (angular) -> u ; tmp must not alias src or u
+  const bool rad = d->params.radial_filter_on != 0;
+  const bool ang = d->params.sh_keep_l >= 0;
+  double* cur = src;
+  if (rad) {
+    GH_CUDA(d, gh::launch_radial(d, cur, d->d_r, true));
+    cur = d->d_r;
+  }
+  if (ang) {
+    double* dst = (cur == u) ? tmp : u;
+    GH_CUDA(d, gh::launch_angular_filter(d, cur, dst));
+    cur = dst;
+  }
+  if (cur != u)
+    GH_CUDA(d, cudaMemcpyAsync(u, cur, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
+  return GH_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params* params,
+                           void* stream, gh_domain** out) {
+  if (!out) return fail(nullptr, GH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!shells || n_shells < 1 || n_shells > 1024) return fail(nullptr, GH_EINVAL, "need 1..1024 shells");
+  if (!params) return fail(nullptr, GH_EINVAL, "params is NULL");
+  for (int s = 0; s < n_shells; ++s) {
+    const gh_shell& sh = shells[s];
+    if (!(sh.r_in > 0.0) || !(sh.r_out > sh.r_in) || sh.n_r < 3 || sh.n_r > 64 || sh.L < 1 || sh.L > 47)
+      return fail(nullptr, GH_EINVAL, "shell " + std::to_string(s) + ": need 0 < r_in < r_out, 3 <= n_r <= 64, 1 <= L <= 47");
+    if (s > 0 && shells[s].r_in != shells[s - 1].r_out)
+      return fail(nullptr, GH_EINVAL, "shell " + std::to_string(s) + " does not start where shell " +
+                                          std::to_string(s - 1) + " ends");
+  }
+  if (params->sh_keep_l >= 0)
+    for (int s = 0; s < n_shells; ++s)
+      if (params->sh_keep_l > shells[s].L) return fail(nullptr, GH_EINVAL, "sh_keep_l exceeds a shell's L");
+  if (params->radial_filter_on && !(params->filt_order > 0)) return fail(nullptr, GH_EINVAL, "filt_order must be > 0");
+  if (fault_injected("alloc")) return fail(nullptr, GH_ENOMEM, "GH_FAULT=alloc: injected allocation failure");
+
+  gh_domain* d = new gh_domain();
+  d->n_shells = n_shells;
+  d->params = *params;
+  d->stream = (cudaStream_t)stream;
+  cudaGetDevice(&d->device);
+  auto bail = [&](gh_status st) {
+    g_create_error = d->err;
+    gh_destroy_domain(d);
+    return st;
+  };
+#define CREATE_CUDA(call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      d->err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+      return bail(e_ == cudaErrorMemoryAllocation ? GH_ENOMEM : GH_ECUDA);                 \
+    }                                                                                      \
+  } while (0)
+
+  // matrix dictionary keyed by the parameters that make a map new (Sec. 3.4)
+  std::map<int, std::pair<double*, double*>> radial_cache;              // n_r -> (D, F)
+  std::map<int, std::pair<double*, double*>> ang_cache;                 // L -> (Bth, Bph)
+  std::map<std::pair<int, int>, double*> filt_cache;                    // (L, keep) -> S
+  std::map<int, AngularGrid> grids;
+
+  long long off = 0, pts = 0;
+  d->shells_h.resize(n_shells);
+  for (int s = 0; s < n_shells; ++s) {
+    const gh_shell& in = shells[s];
+    gh::ShellDev& sh = d->shells_h[s];
+    std::memset(&sh, 0, sizeof(sh));
+    sh.n_r = in.n_r;
+    sh.L = in.L;
+    sh.nth = in.L + 1;
+    sh.nph = 2 * (in.L + 1);
+    sh.na = sh.nth * sh.nph;
+    sh.off = off;
+    sh.pt_off = pts;
+    sh.r_in = in.r_in;
+    sh.r_out = in.r_out;
+    sh.rscale = 2.0 / (in.r_out - in.r_in);
+    off += (long long)sh.n_r * gh::NF * sh.na;
+    pts += (long long)sh.n_r * sh.na;
+    if (!radial_cache.count(sh.n_r)) {
+      double *Dd = nullptr, *Fd = nullptr;
+      CREATE_CUDA(upload(d, cgl_derivative_matrix(sh.n_r), &Dd));
+      CREATE_CUDA(upload(d, cgl_filter_matrix(sh.n_r, params->filt_alpha, params->filt_order > 0 ? params->filt_order : 1), &Fd));
+      radial_cache[sh.n_r] = {Dd, Fd};
+    }
+    sh.Dr = radial_cache[sh.n_r].first;
+    sh.Fr = radial_cache[sh.n_r].second;
+    if (!grids.count(sh.L)) grids[sh.L] = angular_grid(sh.L);
+    const AngularGrid& ag = grids[sh.L];
+    if (!ang_cache.count(sh.L)) {
+      double *Bt = nullptr, *Bp = nullptr;
+      CREATE_CUDA(upload(d, angular_matrix(ag, 0, 0), &Bt));
+      CREATE_CUDA(upload(d, angular_matrix(ag, 1, 0), &Bp));
+      ang_cache[sh.L] = {Bt, Bp};
+    }
+    sh.Bth = ang_cache[sh.L].first;
+    sh.Bph = ang_cache[sh.L].second;
+    if (params->sh_keep_l >= 0) {
+      auto key = std::make_pair(sh.L, params->sh_keep_l);
+      if (!filt_cache.count(key)) {
+        double* Sd = nullptr;
+        CREATE_CUDA(upload(d, angular_matrix(ag, 2, params->sh_keep_l), &Sd));
+        filt_cache[key] = Sd;
+      }
+      sh.Sf = filt_cache[key];
+    }
+    // grid tables
+    std::vector<double> x = cgl_points(sh.n_r), wcc = clenshaw_curtis(sh.n_r);
+    std::vector<double> r(sh.n_r), wr(sh.n_r);
+    for (int i = 0; i < sh.n_r; ++i) {
+      r[i] = 0.5 * (in.r_in + in.r_out) + 0.5 * (in.r_out - in.r_in) * x[i];
+      if (i == 0) r[i] = in.r_in;
+      if (i == sh.n_r - 1) r[i] = in.r_out;
+      wr[i] = wcc[i] * 0.5 * (in.r_out - in.r_in) * r[i] * r[i];
+    }
+    std::vector<double> wth(sh.nth), cph(sh.nph), sph(sh.nph);
+    for (int j = 0; j < sh.nth; ++j) wth[j] = ag.wgl[j] * 2.0 * kPi / sh.nph;
+    for (int k = 0; k < sh.nph; ++k) {
+      cph[k] = std::cos(2.0 * kPi * k / sh.nph);
+      sph[k] = std::sin(2.0 * kPi * k / sh.nph);
+    }
+    double* p = nullptr;
+    CREATE_CUDA(upload(d, r, &p)); sh.r = p;
+    CREATE_CUDA(upload(d, wr, &p)); sh.wr = p;
+    CREATE_CUDA(upload(d, ag.ct, &p)); sh.cth = p;
+    CREATE_CUDA(upload(d, ag.st, &p)); sh.sth = p;
+    CREATE_CUDA(upload(d, wth, &p)); sh.wth = p;
+    CREATE_CUDA(upload(d, cph, &p)); sh.cph = p;
+    CREATE_CUDA(upload(d, sph, &p)); sh.sph = p;
+    void* gz = nullptr;
+    CREATE_CUDA(alloc_zero(d, sizeof(double) * (size_t)sh.n_r * gh::NGAUGE * sh.na, &gz));
+    sh.gauge = (double*)gz;
+    sh.bc_inner = -1;
+    sh.bc_outer = -1;
+  }
+  d->state = off;
+  d->points = pts;
+
+  // boundary slices: internal boundaries, then the outer boundary
+  std::vector<int> bc_begin;
+  int bpts = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    gh::BcSliceDev b;
+    std::memset(&b, 0, sizeof(b));
+    gh::ShellDev& sa = d->shells_h[s];
+    if (s + 1 < n_shells) {
+      gh::ShellDev& sb = d->shells_h[s + 1];
+      if (sa.L != sb.L) {
+        d->err = "adjacent shells must have the same L (shared boundary points)";
+        return bail(GH_EINVAL);
+      }
+      b.kind = 1;
+      b.shell_b = s + 1;
+      b.off_b = sb.off;
+      sb.bc_inner = (int)d->bc_h.size();
+    } else {
+      b.kind = 0;
+      b.shell_b = -1;
+      b.off_b = 0;
+    }
+    b.shell_a = s;
+    b.na = sa.na;
+    b.off_a = sa.off + (long long)(sa.n_r - 1) * gh::NF * sa.na;
+    sa.bc_outer = (int)d->bc_h.size();
+    // flat background: n = R-hat, alpha = 1, beta = 0
+    std::vector<double> bg((size_t)gh::NBG * sa.na, 0.0);
+    const AngularGrid& ag = grids[sa.L];
+    for (int j = 0; j < sa.nth; ++j)
+      for (int k = 0; k < sa.nph; ++k) {
+        const int q = j * sa.nph + k;
+        const double ph = 2.0 * kPi * k / sa.nph;
+        const double nh[3] = {ag.st[j] * std::cos(ph), ag.st[j] * std::sin(ph), ag.ct[j]};
+        for (int i = 0; i < 3; ++i) {
+          bg[(size_t)i * sa.na + q] = nh[i];
+          bg[(size_t)(3 + i) * sa.na + q] = nh[i];
+        }
+        bg[(size_t)6 * sa.na + q] = 1.0;
+      }
+    double* bgd = nullptr;
+    CREATE_CUDA(upload(d, bg, &bgd));
+    b.bg = bgd;
+    bc_begin.push_back(bpts);
+    bpts += sa.na;
+    d->bc_h.push_back(b);
+  }
+  bc_begin.push_back(bpts);
+  d->bc_points = bpts;
+  CREATE_CUDA(upload(d, d->bc_h, &d->bc_d));
+  CREATE_CUDA(upload(d, bc_begin, &d->bc_pt_begin_d));
+  CREATE_CUDA(upload(d, d->shells_h, &d->shells_d));
+
+  // launch maps
+  std::vector<int> rb(n_shells + 1), pb(n_shells + 1);
+  int nrb = 0, npb = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    const gh::ShellDev& sh = d->shells_h[s];
+    rb[s] = nrb;
+    pb[s] = npb;
+    nrb += (int)((gh::NF * (long long)sh.na + 255) / 256);
+    npb += sh.n_r * ((sh.na + 127) / 128);
+  }
+  rb[n_shells] = nrb;
+  pb[n_shells] = npb;
+  d->rad_blocks = nrb;
+  d->pt_blocks = npb;
+  CREATE_CUDA(upload(d, rb, &d->rad_block_begin_d));
+  CREATE_CUDA(upload(d, pb, &d->pt_block_begin_d));
+
+  // batched angular GEMM plans: two problems (theta, phi) per shell; one
+  // filter problem per shell.
+  std::vector<gh::GemmProb> pd, pf;
+  int tiles = 0, ftiles = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    const gh::ShellDev& sh = d->shells_h[s];
+    for (int c = 0; c < 2; ++c) {
+      gh::GemmProb P;
+      std::memset(&P, 0, sizeof(P));
+      P.a_off = sh.off;
+      P.c_off = sh.off;
+      P.B = c == 0 ? sh.Bth : sh.Bph;
+      P.M = sh.n_r * gh::NF;
+      P.N = sh.na;
+      P.K = sh.na;
+      P.lda = P.ldb = P.ldc = sh.na;
+      P.tiles_n = (P.N + 63) / 64;
+      P.tile_begin = tiles;
+      P.c_sel = c;
+      tiles += ((P.M + 63) / 64) * P.tiles_n;
+      pd.push_back(P);
+    }
+    if (sh.Sf) {
+      gh::GemmProb P;
+      std::memset(&P, 0, sizeof(P));
+      P.a_off = sh.off;
+      P.c_off = sh.off;
+      P.B = sh.Sf;
+      P.M = sh.n_r * gh::NF;
+      P.N = sh.na;
+      P.K = sh.na;
+      P.lda = P.ldb = P.ldc = sh.na;
+      P.tiles_n = (P.N + 63) / 64;
+      P.tile_begin = ftiles;
+      ftiles += ((P.M + 63) / 64) * P.tiles_n;
+      pf.push_back(P);
+    }
+  }
+  d->ang_deriv_np = (int)pd.size();
+  d->ang_deriv_tiles = tiles;
+  CREATE_CUDA(upload(d, pd, &d->ang_deriv_d));
+  d->ang_filt_np = (int)pf.size();
+  d->ang_filt_tiles = ftiles;
+  if (!pf.empty()) CREATE_CUDA(upload(d, pf, &d->ang_filt_d));
+
+  // scratch
+  void* p = nullptr;
+  CREATE_CUDA(alloc_zero(d, sizeof(double) * d->state, &p)); d->d_r = (double*)p;
+  CREATE_CUDA(alloc_zero(d, sizeof(double) * d->state, &p)); d->d_th = (double*)p;
+  CREATE_CUDA(alloc_zero(d, sizeof(double) * d->state, &p)); d->d_ph = (double*)p;
+  CREATE_CUDA(alloc_zero(d, sizeof(double) * (size_t)d->pt_blocks, &p)); d->partial = (double*)p;
+  CREATE_CUDA(alloc_zero(d, sizeof(int), &p)); d->err_flag = (int*)p;
+  CREATE_CUDA(cudaDeviceSynchronize());
+#undef CREATE_CUDA
+  *out = d;
+  return GH_OK;
+}
+
+gh_status gh_destroy_domain(gh_domain* d) {
+  if (!d) return GH_EINVAL;
+  cudaStreamSynchronize(d->stream);
+  for (void* p : d->owned) cudaFree(p);
+  delete d;
+  return GH_OK;
+}
+
+gh_status gh_set_stream(gh_domain* d, void* stream) {
+  if (!d) return GH_EINVAL;
+  d->stream = (cudaStream_t)stream;
+  return GH_OK;
+}
+
+long long gh_state_size(const gh_domain* d) { return d ? d->state : -1; }
+long long gh_num_points(const gh_domain* d) { return d ? d->points : -1; }
+long long gh_rk4_work_size(const gh_domain* d) { return d ? 3 * d->state : -1; }
+int gh_num_shells(const gh_domain* d) { return d ? d->n_shells : -1; }
+long long gh_launch_count(const gh_domain* d) { return d ? d->launches : -1; }
+
+const char* gh_last_error(const gh_domain* d) { return d ? d->err.c_str() : g_create_error.c_str(); }
+
+gh_status gh_set_analytic_kerr_schild(gh_domain* d, double M, double chi, double* u) {
+  if (!d || !u) return fail(d, GH_EINVAL, "null argument");
+  if (!(M > 0.0) || !(std::fabs(chi) < 1.0)) return fail(d, GH_EINVAL, "need M > 0 and |chi| < 1");
+  if (gh_status s = check_latched(d)) return s;
+  GH_CUDA(d, gh::launch_kerr_schild(d, M, chi, u));
+  GH_CUDA(d, gh::launch_bc_background(d, u));
+  return GH_OK;
+}
+
+gh_status gh_set_gauge(gh_domain* d, const double* H, const double* dH) {
+  if (!d || !H || !dH) return fail(d, GH_EINVAL, "null argument");
+  // user layout per shell: H [r][4][na], dH [r][12][na]; internal [r][16][na]
+  long long hoff = 0, dhoff = 0;
+  for (int s = 0; s < d->n_shells; ++s) {
+    const gh::ShellDev& sh = d->shells_h[s];
+    const size_t na = sh.na;
+    for (int ir = 0; ir < sh.n_r; ++ir) {
+      GH_CUDA(d, cudaMemcpyAsync(sh.gauge + (size_t)ir * gh::NGAUGE * na, H + hoff + (size_t)ir * 4 * na,
+                                 sizeof(double) * 4 * na, cudaMemcpyDeviceToDevice, d->stream));
+      GH_CUDA(d, cudaMemcpyAsync(sh.gauge + (size_t)ir * gh::NGAUGE * na + 4 * na,
+                                 dH + dhoff + (size_t)ir * 12 * na, sizeof(double) * 12 * na,
+                                 cudaMemcpyDeviceToDevice, d->stream));
+    }
+    hoff += (long long)sh.n_r * 4 * na;
+    dhoff += (long long)sh.n_r * 12 * na;
+  }
+  return GH_OK;
+}
+
+gh_status gh_get_gauge(const gh_domain* dc, double* H, double* dH) {
+  gh_domain* d = const_cast<gh_domain*>(dc);
+  if (!d || !H || !dH) return fail(d, GH_EINVAL, "null argument");
+  long long hoff = 0, dhoff = 0;
+  for (int s = 0; s < d->n_shells; ++s) {
+    const gh::ShellDev& sh = d->shells_h[s];
+    const size_t na = sh.na;
+    for (int ir = 0; ir < sh.n_r; ++ir) {
+      GH_CUDA(d, cudaMemcpyAsync(H + hoff + (size_t)ir * 4 * na, sh.gauge + (size_t)ir * gh::NGAUGE * na,
+                                 sizeof(double) * 4 * na, cudaMemcpyDeviceToDevice, d->stream));
+      GH_CUDA(d, cudaMemcpyAsync(dH + dhoff + (size_t)ir * 12 * na, sh.gauge + (size_t)ir * gh::NGAUGE * na + 4 * na,
+                                 sizeof(double) * 12 * na, cudaMemcpyDeviceToDevice, d->stream));
+    }
+    hoff += (long long)sh.n_r * 4 * na;
+    dhoff += (long long)sh.n_r * 12 * na;
+  }
+  return GH_OK;
+}
+
+gh_status gh_set_background(gh_domain* d, const double* u_bg) {
+  if (!d || !u_bg) return fail(d, GH_EINVAL, "null argument");
+  GH_CUDA(d, gh::launch_bc_background(d, u_bg));
+  return GH_OK;
+}
+
+gh_status gh_add_perturbation(gh_domain* d, int kind, double A, double Rc, double w, int lmax,
+                              const double* coeffs, double* u) {
+  if (!d || !u || !coeffs) return fail(d, GH_EINVAL, "null argument");
+  if (kind != 0 && kind != 1) return fail(d, GH_EINVAL, "kind must be 0 or 1");
+  if (lmax < 0 || lmax > 16 || !(w > 0.0)) return fail(d, GH_EINVAL, "need 0 <= lmax <= 16 and w > 0");
+  const size_t n = (size_t)(lmax + 1) * (lmax + 1);
+  double* cd = nullptr;
+  GH_CUDA(d, cudaMallocAsync(&cd, sizeof(double) * n, d->stream));
+  GH_CUDA(d, cudaMemcpyAsync(cd, coeffs, sizeof(double) * n, cudaMemcpyHostToDevice, d->stream));
+  GH_CUDA(d, gh::launch_perturbation(d, kind, A, Rc, w, lmax, cd, u));
+  GH_CUDA(d, cudaFreeAsync(cd, d->stream));
+  return GH_OK;
+}
+
+gh_status gh_derivatives(gh_domain* d, const double* u, double* du) {
+  if (!d || !u || !du) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = check_latched(d)) return s;
+  if (gh_status s = derivatives(d, u)) return s;
+  GH_CUDA(d, gh::launch_cartesian(d, u, du));
+  return GH_OK;
+}
+
+gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
+  if (!d || !u || !dudt) return fail(d, GH_EINVAL, "null argument");
+  if (u == dudt) return fail(d, GH_EINVAL, "u and dudt must not overlap");
+  if (gh_status s = check_latched(d)) return s;
+  if (gh_status s = derivatives(d, u)) return s;
+  GH_CUDA(d, gh::launch_pointwise(d, u, dudt, 0, 0.0, nullptr, nullptr, nullptr, false));
+  GH_CUDA(d, gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr));
+  return GH_OK;
+}
+
+gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
+  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = check_latched(d)) return s;
+  double* us = work;
+  double* k = work + d->state;
+  double* acc = work + 2 * d->state;
+  const bool filt = d->params.radial_filter_on || d->params.sh_keep_l >= 0;
+  for (int stage = 1; stage <= 4; ++stage) {
+    const double* in = (stage == 1) ? u : us;
+    if (gh_status s = derivatives(d, in)) return s;
+    double* target = (stage == 4 && !filt) ? u : us;
+    GH_CUDA(d, gh::launch_pointwise(d, in, k, stage, dt, u, acc, target, stage == 1 && norm2_pre));
+    if (stage == 1 && norm2_pre) GH_CUDA(d, gh::launch_norm_reduce(d, norm2_pre));
+    GH_CUDA(d, gh::launch_bc(d, k, stage, dt, u, acc, target));
+  }
+  if (filt) {
+    if (gh_status s = filters(d, us, u, k)) return s;
+  }
+  return GH_OK;
+}
+
+gh_status gh_apply_filters(gh_domain* d, double* u, double* work) {
+  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+  return filters(d, u, u, work);
+}
+
+gh_status gh_constraints(gh_domain* d, const double* u, double* c_out, double* norm2) {
+  if (!d || !u || !norm2) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = check_latched(d)) return s;
+  if (gh_status s = derivatives(d, u)) return s;
+  GH_CUDA(d, gh::launch_constraints(d, u, c_out));
+  GH_CUDA(d, gh::launch_norm_reduce(d, norm2));
+  return GH_OK;
+}
+
+gh_status gh_sync(gh_domain* d) {
+  if (!d) return GH_EINVAL;
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  int flag = 0;
+  GH_CUDA(d, cudaMemcpy(&flag, d->err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    GH_CUDA(d, cudaMemset(d->err_flag, 0, sizeof(int)));
+    return fail(d, (gh_status)flag, "device reported a non-finite constraint norm");
+  }
+  return GH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+// Initial data on the device: the analytic Kerr-Schild solution with its
+// gauge source (Sec. 3.1), and seeded-coefficient perturbations.
+//
+// Derivatives of the metric come from forward-mode second-order jets (value,
+// gradient and Hessian in x, y, z carried through every arithmetic
+// operation), so d_i g_ab and d_i d_j g_ab are exact to rounding.
+#include <cuda_runtime.h>
+
+#include "gh_internal.h"
+#include "gh_tensor.cuh"
+
+namespace gh {
+
+// ---------------------------------------------------------------- jets
+struct Jet {
+  double v;
+  double g[3];
+  double h[6];  // xx xy xz yy yz zz
+};
+
+__device__ __forceinline__ int h3(int i, int j) {
+  int a = i < j ? i : j, b = i < j ? j : i;
+  return a == 0 ? b : (a == 1 ? 2 + b : 5);
+}
+
+__device__ __forceinline__ Jet jconst(double c) {
+  Jet r;
+  r.v = c;
+  for (int i = 0; i < 3; ++i) r.g[i] = 0.0;
+  for (int i = 0; i < 6; ++i) r.h[i] = 0.0;
+  return r;
+}
+__device__ __forceinline__ Jet jvar(double x, int i) {
+  Jet r = jconst(x);
+  r.g[i] = 1.0;
+  return r;
+}
+__device__ __forceinline__ Jet operator+(const Jet& a, const Jet& b) {
+  Jet r;
+  r.v = a.v + b.v;
+  for (int i = 0; i < 3; ++i) r.g[i] = a.g[i] + b.g[i];
+  for (int i = 0; i < 6; ++i) r.h[i] = a.h[i] + b.h[i];
+  return r;
+}
+__device__ __forceinline__ Jet operator-(const Jet& a, const Jet& b) {
+  Jet r;
+  r.v = a.v - b.v;
+  for (int i = 0; i < 3; ++i) r.g[i] = a.g[i] - b.g[i];
+  for (int i = 0; i < 6; ++i) r.h[i] = a.h[i] - b.h[i];
+  return r;
+}
+__device__ __forceinline__ Jet operator*(double c, const Jet& a) {
+  Jet r;
+  r.v = c * a.v;
+  for (int i = 0; i < 3; ++i) r.g[i] = c * a.g[i];
+  for (int i = 0; i < 6; ++i) r.h[i] = c * a.h[i];
+  return r;
+}
+__device__ __forceinline__ Jet operator*(const Jet& a, const Jet& b) {
+  Jet r;
+  r.v = a.v * b.v;
+  for (int i = 0; i < 3; ++i) r.g[i] = a.v * b.g[i] + a.g[i] * b.v;
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j)
+      r.h[h3(i, j)] = a.v * b.h[h3(i, j)] + a.g[i] * b.g[j] + a.g[j] * b.g[i] + a.h[h3(i, j)] * b.v;
+  return r;
+}
+// unary chain rule: f(a) with f' = d1, f'' = d2 at a.v
+__device__ __forceinline__ Jet chain(const Jet& a, double f0, double d1, double d2) {
+  Jet r;
+  r.v = f0;
+  for (int i = 0; i < 3; ++i) r.g[i] = d1 * a.g[i];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) r.h[h3(i, j)] = d1 * a.h[h3(i, j)] + d2 * a.g[i] * a.g[j];
+  return r;
+}
+__device__ __forceinline__ Jet jinv(const Jet& a) {
+  const double iv = 1.0 / a.v;
+  return chain(a, iv, -iv * iv, 2.0 * iv * iv * iv);
+}
+__device__ __forceinline__ Jet jsqrt(const Jet& a) {
+  const double s = sqrt(a.v);
+  return chain(a, s, 0.5 / s, -0.25 / (s * a.v));
+}
+__device__ __forceinline__ Jet operator/(const Jet& a, const Jet& b) { return a * jinv(b); }
+
+// Kerr-Schild metric g_ab = eta_ab + 2 H l_a l_b, spin along +z, a = chi M.
+__device__ void kerr_schild_metric(double x, double y, double z, double M, double a, Jet g[10]) {
+  const Jet X = jvar(x, 0), Y = jvar(y, 1), Z = jvar(z, 2);
+  const Jet a2 = jconst(a * a);
+  const Jet R2 = X * X + Y * Y + Z * Z;
+  const Jet hm = 0.5 * (R2 - a2);
+  const Jet r2 = hm + jsqrt(hm * hm + (a * a) * (Z * Z));
+  const Jet r = jsqrt(r2);
+  const Jet H = M * (r * r2) / (r2 * r2 + (a * a) * (Z * Z));
+  const Jet den = jinv(r2 + a2);
+  Jet l[4];
+  l[0] = jconst(1.0);
+  l[1] = (r * X + a * Y) * den;
+  l[2] = (r * Y - a * X) * den;
+  l[3] = Z / r;
+  const Jet twoH = 2.0 * H;
+  for (int p = 0; p < 10; ++p) {
+    const int A = pair_a(p), B = pair_b(p);
+    const double eta = (A == B) ? (A == 0 ? -1.0 : 1.0) : 0.0;
+    g[p] = jconst(eta) + twoH * (l[A] * l[B]);
+  }
+}
+
+// One thread per point: u = (psi, Pi, Phi) of the stationary metric and the
+// gauge source H_a = -Gamma_a, d_i H_a = -d_i Gamma_a (d_t H_a = 0).
+__global__ void __launch_bounds__(64)
+kerr_schild_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                   double M, double a, double* __restrict__ u) {
+  const int s = [&] { int t = 0; while (t + 1 < n_shells && begin[t + 1] <= (int)blockIdx.x) ++t; return t; }();
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + 63) / 64;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * 64 + threadIdx.x;
+  if (q >= na) return;
+  const int j = q / sh.nph, k = q - j * sh.nph;
+  const double r = sh.r[ir];
+  const double x = r * sh.sth[j] * sh.cph[k], y = r * sh.sth[j] * sh.sph[k], z = r * sh.cth[j];
+  Jet g[10];
+  kerr_schild_metric(x, y, z, M, a, g);
+  double psi[10], Phi[30], Pi[10];
+  for (int p = 0; p < 10; ++p) {
+    psi[p] = g[p].v;
+    for (int i = 0; i < 3; ++i) Phi[i * 10 + p] = g[p].g[i];
+  }
+  Split S;
+  spacetime_split(psi, S);
+  for (int p = 0; p < 10; ++p)
+    Pi[p] = (S.beta_up[0] * Phi[p] + S.beta_up[1] * Phi[10 + p] + S.beta_up[2] * Phi[20 + p]) / S.alpha;
+  const long long base = sh.off + (long long)ir * NF * na + q;
+  for (int p = 0; p < 10; ++p) {
+    u[base + (long long)p * na] = psi[p];
+    u[base + (long long)(10 + p) * na] = Pi[p];
+    for (int i = 0; i < 3; ++i) u[base + (long long)(20 + 10 * i + p) * na] = Phi[i * 10 + p];
+  }
+  // Gamma_abc from D[c][ab] = d_c g_ab (d_0 = 0)
+  auto D = [&](int c, int A, int B) -> double { return c == 0 ? 0.0 : g[sym_index(A, B)].g[c - 1]; };
+  auto DD = [&](int i, int c, int A, int B) -> double {
+    return c == 0 ? 0.0 : g[sym_index(A, B)].h[h3(i, c - 1)];
+  };
+  double Ga[4], dGa[3][4];
+  for (int A = 0; A < 4; ++A) {
+    double acc = 0.0, dacc[3] = {0.0, 0.0, 0.0};
+    for (int B = 0; B < 4; ++B)
+      for (int C = 0; C < 4; ++C) {
+        const double gam = 0.5 * (D(B, A, C) + D(C, A, B) - D(A, B, C));
+        const double pinv = S.psi_inv[sym_index(B, C)];
+        acc += pinv * gam;
+        for (int i = 0; i < 3; ++i) {
+          // d_i psi^BC = -psi^BE d_i psi_EF psi^FC
+          double dpinv = 0.0;
+          for (int E = 0; E < 4; ++E)
+            for (int F = 0; F < 4; ++F)
+              dpinv -= S.psi_inv[sym_index(B, E)] * D(1 + i, E, F) * S.psi_inv[sym_index(F, C)];
+          const double dgam = 0.5 * (DD(i, B, A, C) + DD(i, C, A, B) - DD(i, A, B, C));
+          dacc[i] += dpinv * gam + pinv * dgam;
+        }
+      }
+    Ga[A] = acc;
+    for (int i = 0; i < 3; ++i) dGa[i][A] = dacc[i];
+  }
+  double* gd = sh.gauge + (long long)ir * NGAUGE * na + q;
+  for (int A = 0; A < 4; ++A) gd[(long long)A * na] = -Ga[A];
+  for (int i = 0; i < 3; ++i)
+    for (int A = 0; A < 4; ++A) gd[(long long)(4 + 4 * i + A) * na] = -dGa[i][A];
+}
+
+// ------------------------------------------------------- perturbations
+constexpr int PERT_LMAX = 16;
+
+// Normalised associated Legendre functions (orthonormal real harmonics, no
+// Condon-Shortley phase) and their theta derivatives from
+//   sin(th) dP_l^m/dth = l cos(th) P_l^m - sqrt((2l+1)(l^2-m^2)/(2l-1)) P_{l-1}^m.
+__device__ void legendre_table(int lmax, double ct, double st, double* P, double* dP) {
+  const int W = PERT_LMAX + 1;
+  for (int i = 0; i < W * W; ++i) { P[i] = 0.0; dP[i] = 0.0; }
+  P[0] = sqrt(0.25 / 3.14159265358979323846);
+  for (int m = 1; m <= lmax; ++m) P[m * W + m] = sqrt((2.0 * m + 1.0) / (2.0 * m)) * st * P[(m - 1) * W + m - 1];
+  for (int m = 0; m < lmax; ++m) P[(m + 1) * W + m] = sqrt(2.0 * m + 3.0) * ct * P[m * W + m];
+  for (int m = 0; m <= lmax; ++m)
+    for (int l = m + 2; l <= lmax; ++l) {
+      const double al = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+      const double bl = sqrt((((double)l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+      P[l * W + m] = al * (ct * P[(l - 1) * W + m] - bl * P[(l - 2) * W + m]);
+    }
+  for (int l = 0; l <= lmax; ++l)
+    for (int m = 0; m <= l; ++m) {
+      const double prev = (l > m) ? P[(l - 1) * W + m] : 0.0;
+      const double c = (l > m) ? sqrt((2.0 * l + 1.0) * ((double)l * l - (double)m * m) / (2.0 * l - 1.0)) : 0.0;
+      dP[l * W + m] = (l * ct * P[l * W + m] - c * prev) / st;
+    }
+}
+
+__global__ void __launch_bounds__(64)
+perturbation_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                    int kind, double A, double Rc, double w, int lmax,
+                    const double* __restrict__ coeffs, double* __restrict__ u) {
+  const int s = [&] { int t = 0; while (t + 1 < n_shells && begin[t + 1] <= (int)blockIdx.x) ++t; return t; }();
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + 63) / 64;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * 64 + threadIdx.x;
+  if (q >= na) return;
+  const int j = q / sh.nph, k = q - j * sh.nph;
+  const double r = sh.r[ir], ct = sh.cth[j], st = sh.sth[j];
+  const double phi = 2.0 * 3.14159265358979323846 * k / sh.nph;
+  const int W = PERT_LMAX + 1;
+  double P[W * W], dP[W * W];
+  legendre_table(lmax, ct, st, P, dP);
+  double S = 0.0, St = 0.0, Sp = 0.0;
+  int idx = 0;
+  for (int l = 0; l <= lmax; ++l)
+    for (int m = -l; m <= l; ++m, ++idx) {
+      const int am = m < 0 ? -m : m;
+      double f, fp;
+      if (m == 0) { f = 1.0; fp = 0.0; }
+      else {
+        double sn, cs;
+        sincos(am * phi, &sn, &cs);
+        const double r2 = 1.41421356237309504880;
+        if (m > 0) { f = r2 * cs; fp = -r2 * am * sn; }
+        else { f = r2 * sn; fp = r2 * am * cs; }
+      }
+      const double c = coeffs[idx];
+      S += c * P[l * W + am] * f;
+      St += c * dP[l * W + am] * f;
+      Sp += c * P[l * W + am] * fp;
+    }
+  const double G = exp(-((r - Rc) / w) * ((r - Rc) / w));
+  const long long base = sh.off + (long long)ir * NF * na + q;
+  if (kind == 1) {
+    for (int p = 0; p < 10; ++p) u[base + (long long)(10 + p) * na] += G * S;
+    return;
+  }
+  const double dG = -2.0 * (r - Rc) / (w * w) * G;
+  const double f = A * G * S, fr = A * dG * S, fth = A * G * St, fph = A * G * Sp;
+  const double cp = sh.cph[k], sp = sh.sph[k];
+  const double df[3] = {st * cp * fr + ct * cp / r * fth - sp / (r * st) * fph,
+                        st * sp * fr + ct * sp / r * fth + cp / (r * st) * fph,
+                        ct * fr - st / r * fth};
+  double psi[10];
+  for (int p = 0; p < 10; ++p) psi[p] = u[base + (long long)p * na];
+  Split Sp_;
+  spacetime_split(psi, Sp_);
+  const double bdf = Sp_.beta_up[0] * df[0] + Sp_.beta_up[1] * df[1] + Sp_.beta_up[2] * df[2];
+  const double dpi = -(fr - bdf) / Sp_.alpha;
+  for (int p = 0; p < 10; ++p) {
+    u[base + (long long)p * na] += f;
+    u[base + (long long)(10 + p) * na] += dpi;
+    for (int i = 0; i < 3; ++i) u[base + (long long)(20 + 10 * i + p) * na] += df[i];
+  }
+}
+
+cudaError_t launch_kerr_schild(gh_domain* d, double M, double chi, double* u) {
+  // 64-thread blocks: reuse the pointwise block map scaled by 2
+  int blocks = 0;
+  std::vector<int> begin(d->n_shells + 1);
+  for (int s = 0; s < d->n_shells; ++s) {
+    begin[s] = blocks;
+    blocks += d->shells_h[s].n_r * ((d->shells_h[s].na + 63) / 64);
+  }
+  begin[d->n_shells] = blocks;
+  int* bd = nullptr;
+  cudaError_t e = cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream);
+  if (e != cudaSuccess) return e;
+  kerr_schild_kernel<<<blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, bd, M, chi * M, u);
+  d->launches++;
+  e = cudaGetLastError();
+  cudaFreeAsync(bd, d->stream);
+  return e;
+}
+
+cudaError_t launch_perturbation(gh_domain* d, int kind, double A, double Rc, double w, int lmax,
+                                const double* coeffs_dev, double* u) {
+  int blocks = 0;
+  std::vector<int> begin(d->n_shells + 1);
+  for (int s = 0; s < d->n_shells; ++s) {
+    begin[s] = blocks;
+    blocks += d->shells_h[s].n_r * ((d->shells_h[s].na + 63) / 64);
+  }
+  begin[d->n_shells] = blocks;
+  int* bd = nullptr;
+  cudaError_t e = cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream);
+  if (e != cudaSuccess) return e;
+  perturbation_kernel<<<blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, bd, kind, A, Rc, w, lmax,
+                                                    coeffs_dev, u);
+  d->launches++;
+  e = cudaGetLastError();
+  cudaFreeAsync(bd, d->stream);
+  return e;
+}
+
+}  // namespace gh

@@ -1,0 +1,116 @@
+// Internal declarations shared by the libgh translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gh.h"
+
+namespace gh {
+
+constexpr int NF = 50;      // evolved fields per point
+constexpr int NC = 64;      // stored constraint components per point
+constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
+constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
+
+// One shell as the kernels see it (device-resident array of these).
+struct ShellDev {
+  int n_r, L, nth, nph, na;     // na = nth * nph angular points
+  int pad0;
+  long long off;                // offset of the shell in a state vector (doubles)
+  long long pt_off;             // offset of the shell's first point
+  double r_in, r_out, rscale;   // rscale = 2 / (r_out - r_in) = dx/dr
+  const double* Dr;             // [n_r][n_r] d/dx on the CGL points
+  const double* Fr;             // [n_r][n_r] exponential Chebyshev filter
+  const double* Bth;            // [na][na] transposed d/dtheta map (out = U * Bth)
+  const double* Bph;            // [na][na] transposed d/dphi map
+  const double* Sf;             // [na][na] transposed SH truncation filter (or null)
+  const double* r;              // [n_r]
+  const double* wr;             // [n_r] radial volume weight w_cc * (r_out-r_in)/2 * r^2
+  const double* cth;            // [nth] cos(theta)
+  const double* sth;            // [nth] sin(theta)
+  const double* wth;            // [nth] Gauss-Legendre weight * 2 pi / nph
+  const double* cph;            // [nph]
+  const double* sph;            // [nph]
+  double* gauge;                // [n_r][16][na]
+  int bc_inner;                 // boundary slice index at r_in, -1 if none (excision)
+  int bc_outer;                 // boundary slice index at r_out
+};
+
+// A boundary slice: the outer boundary of the last shell (kind 0) or an
+// internal boundary shared by shell a (its r_out) and shell b (its r_in).
+struct BcSliceDev {
+  int kind;                     // 0 outer, 1 interface
+  int shell_a, shell_b;         // shell_b = -1 for the outer boundary
+  int na;
+  long long off_a, off_b;       // state offset of the boundary r-slice in a / b
+  double* bg;                   // [10][na] n_dn(3) n_up(3) alpha beta_up(3)
+};
+
+// One FP64 GEMM problem of a batched launch: C = A * B, row-major.
+// A is addressed from one of the input bases, C from one of the output bases.
+struct GemmProb {
+  long long a_off, c_off;
+  const double* B;
+  int M, N, K;
+  int lda, ldb, ldc;
+  int tiles_n;                  // ceil(N / BN)
+  int tile_begin;               // first flattened tile index of this problem
+  int c_sel;                    // which output base
+  int pad;
+};
+
+struct MatrixCacheEntry;
+
+}  // namespace gh
+
+struct gh_domain {
+  int n_shells = 0;
+  gh_params params{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  long long state = 0, points = 0;
+  std::vector<gh::ShellDev> shells_h;
+  gh::ShellDev* shells_d = nullptr;
+  std::vector<gh::BcSliceDev> bc_h;
+  gh::BcSliceDev* bc_d = nullptr;
+  int bc_points = 0;            // total points over all boundary slices
+  int* bc_pt_begin_d = nullptr; // first point of each boundary slice, [n + 1]
+  // batched GEMM launch plans
+  gh::GemmProb* ang_deriv_d = nullptr; int ang_deriv_np = 0, ang_deriv_tiles = 0;
+  gh::GemmProb* ang_filt_d = nullptr;  int ang_filt_np = 0, ang_filt_tiles = 0;
+  // radial / pointwise launch maps: first block of each shell
+  int* rad_block_begin_d = nullptr; int rad_blocks = 0;
+  int* pt_block_begin_d = nullptr;  int pt_blocks = 0;
+  // scratch owned by the domain
+  double* d_r = nullptr;         // radial derivative  (one state)
+  double* d_th = nullptr;        // theta derivative   (one state)
+  double* d_ph = nullptr;        // phi derivative     (one state)
+  double* partial = nullptr;     // per-block constraint partial sums
+  int* err_flag = nullptr;       // latched device error
+  std::vector<void*> owned;      // every device allocation, freed on destroy
+  std::string err;
+  long long launches = 0;
+};
+
+namespace gh {
+
+// Kernel launchers (gh_kernels.cu).
+cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter);
+cudaError_t launch_angular_deriv(gh_domain* d, const double* in);
+cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
+cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage, double dt,
+                             const double* u0, double* acc, double* ustage, bool constraints);
+cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const double* u0,
+                      double* acc, double* ustage);
+cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out);
+cudaError_t launch_norm_reduce(gh_domain* d, double* norm2);
+cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du);
+cudaError_t launch_bc_background(gh_domain* d, const double* u);
+cudaError_t launch_kerr_schild(gh_domain* d, double M, double chi, double* u);
+cudaError_t launch_perturbation(gh_domain* d, int kind, double A, double Rc, double w,
+                                int lmax, const double* coeffs_dev, double* u);
+
+}  // namespace gh

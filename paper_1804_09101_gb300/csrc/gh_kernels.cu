@@ -1,0 +1,822 @@
+// libgh device kernels: spectral contractions, the fused pointwise GH
+// right-hand side with the RK4 stage combine, boundary conditions,
+// constraints and their quadrature norms.  FP64 throughout.
+//
+// On GB300 the FP64 FMA pipe (about 1.2 TFLOP/s measured) is faster than the
+// FP64 tensor-core path (mma.sync f64, about 1.05 TFLOP/s measured), and every
+// kernel here has an arithmetic intensity far above the FP64 ridge point
+// (about 0.18 flop per HBM byte), so all of them are FP64-ALU bound.  The
+// contractions are therefore register-tiled FFMA kernels, and the design goal
+// is to keep the FP64 pipe busy, not to save HBM traffic.
+#include <cuda_runtime.h>
+
+#include "gh_internal.h"
+#include "gh_tensor.cuh"
+
+namespace gh {
+
+// ---------------------------------------------------------------------------
+// Block -> shell lookup: begin[s] is the first block of shell s, begin[n] the
+// total.  n is small (tens), so a linear scan is enough.
+__device__ __forceinline__ int find_segment(const int* begin, int n, int b) {
+  int s = 0;
+  while (s + 1 < n && begin[s + 1] <= b) ++s;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Radial contraction (the R part of Eq. DifferentiatorI1S2, and the radial
+// ExpCheb filter): out[r][col] = sum_r' M[r][r'] in[r'][col] for every column
+// col = (field, theta, phi) of every shell.  One thread per column; the
+// column lives in registers, the n_r x n_r matrix in shared memory.
+constexpr int RAD_THREADS = 256;
+constexpr int MAXR = 64;
+
+template <bool FILTER>
+__global__ void __launch_bounds__(RAD_THREADS)
+radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+              const double* __restrict__ in, double* __restrict__ out) {
+  __shared__ double Ms[MAXR * MAXR];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int n = sh.n_r;
+  const double* M = FILTER ? sh.Fr : sh.Dr;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ms[i] = M[i];
+  __syncthreads();
+  const long long cols = (long long)NF * sh.na;
+  const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
+  if (col >= cols) return;
+  const double* src = in + sh.off + col;
+  double* dst = out + sh.off + col;
+  double v[MAXR];
+#pragma unroll
+  for (int r = 0; r < MAXR; ++r)
+    if (r < n) v[r] = src[(long long)r * cols];
+  for (int r = 0; r < n; ++r) {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q)
+      if (q < n) acc = fma(Ms[r * n + q], v[q], acc);
+    dst[(long long)r * cols] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched FP64 GEMM C = A * B (row-major), one flattened tile per block.
+// Used for the angular maps of Eq. DifferentiatorI1S2 (A = the state viewed as
+// (n_r * 50) x (N_theta N_phi), B = a cached transposed derivative matrix) and
+// for the SH truncation filter.  64x64 block tile, 16-deep k slices, 4x4
+// outputs per thread, register prefetch of the next slice.
+constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+constexpr int GEMM_THREADS = (BM / TM) * (BN / TN);  // 256
+
+__global__ void __launch_bounds__(GEMM_THREADS)
+gemm_batched_kernel(const GemmProb* __restrict__ probs, int nprob, const double* __restrict__ in,
+                    double* __restrict__ out0, double* __restrict__ out1) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN];
+  // locate the problem
+  int pi = 0;
+  while (pi + 1 < nprob && probs[pi + 1].tile_begin <= (int)blockIdx.x) ++pi;
+  const GemmProb P = probs[pi];
+  const int t = blockIdx.x - P.tile_begin;
+  const int m0 = (t / P.tiles_n) * BM;
+  const int n0 = (t % P.tiles_n) * BN;
+  const double* A = in + P.a_off;
+  const double* B = P.B;
+  double* C = (P.c_sel ? out1 : out0) + P.c_off;
+
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  constexpr int LA = BM * BK / GEMM_THREADS;  // 4
+  constexpr int LB = BK * BN / GEMM_THREADS;  // 4
+  double ra[LA], rb[LB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + q * GEMM_THREADS;
+      const int row = e / BK, kk = e % BK;
+      const int gm = m0 + row, gk = k0 + kk;
+      ra[q] = (gm < P.M && gk < P.K) ? A[(long long)gm * P.lda + gk] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + q * GEMM_THREADS;
+      const int kk = e / BN, col = e % BN;
+      const int gk = k0 + kk, gn = n0 + col;
+      rb[q] = (gk < P.K && gn < P.N) ? B[(long long)gk * P.ldb + gn] : 0.0;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + q * GEMM_THREADS;
+      As[e % BK][e / BK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + q * GEMM_THREADS;
+      Bs[e / BN][e % BN] = rb[q];
+    }
+  };
+
+  load(0);
+  for (int k0 = 0; k0 < P.K; k0 += BK) {
+    store();
+    __syncthreads();
+    if (k0 + BK < P.K) load(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * (BN / TN)];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gm = m0 + ty + i * (BM / TM);
+    if (gm >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tx + j * (BN / TN);
+      if (gn < P.N) C[(long long)gm * P.ldc + gn] = acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of one point: the DiffJac matrix J[i][d] = d(x_d)/d(x^i) for the
+// spherical coordinates (r, theta, phi), with the radial column multiplied by
+// dx/dr so that it acts on the CGL-coordinate derivative (Eq. DiffJac).
+struct PointGeom {
+  double J[3][3];
+  double xhat[3];  // x^i / R
+  double r;
+};
+
+__device__ __forceinline__ void point_geom(const ShellDev& sh, int ir, int q, PointGeom& g) {
+  const int j = q / sh.nph, k = q - j * sh.nph;
+  const double r = sh.r[ir];
+  const double ct = sh.cth[j], st = sh.sth[j], cp = sh.cph[k], sp = sh.sph[k];
+  const double ir_ = 1.0 / r;
+  const double irs = ir_ / st;
+  g.r = r;
+  g.xhat[0] = st * cp; g.xhat[1] = st * sp; g.xhat[2] = ct;
+  g.J[0][0] = st * cp * sh.rscale; g.J[0][1] = ct * cp * ir_; g.J[0][2] = -sp * irs;
+  g.J[1][0] = st * sp * sh.rscale; g.J[1][1] = ct * sp * ir_; g.J[1][2] = cp * irs;
+  g.J[2][0] = ct * sh.rscale;      g.J[2][1] = -st * ir_;     g.J[2][2] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Fused pointwise kernel: DiffJac (Eq. DiffJac) + the GH right-hand side
+// (GHEqns) for every point of every shell, one thread per point, with the
+// RK4 stage combine in the epilogue and, optionally, the constraint energy
+// density accumulated into per-block partial sums.
+//
+// stage 0: write k = dudt everywhere.
+// stage 1..4: at points that a boundary condition will still modify, write k
+//   and leave the combine to the boundary kernel; elsewhere skip k and write
+//   stage 1: acc = k,  us = u0 + dt/2 k;   stage 2: acc += 2k, us = u0 + dt/2 k
+//   stage 3: acc += 2k, us = u0 + dt k;    stage 4: us = u0 + dt/6 (acc + k)
+constexpr int PT_THREADS = 128;
+
+struct PointwiseArgs {
+  const ShellDev* shells;
+  int n_shells;
+  const int* begin;
+  const double* u;       // state the RHS is evaluated at
+  const double* dr;      // d/dx (CGL coordinate) of u
+  const double* dth;
+  const double* dph;
+  double* k;
+  const double* u0;
+  double* acc;
+  double* us;
+  double* partial;       // per-block constraint energy (nullable)
+  double* c_out;         // constraint components (nullable)
+  double gamma0, gamma1, gamma2, dt;
+  int stage;
+};
+
+__device__ __forceinline__ void stage_combine(int stage, double dt, double kv, long long idx,
+                                              const double* u0, double* acc, double* us) {
+  const double u0v = u0[idx];
+  if (stage == 1) {
+    acc[idx] = kv;
+    us[idx] = u0v + 0.5 * dt * kv;
+  } else if (stage == 2) {
+    acc[idx] += 2.0 * kv;
+    us[idx] = u0v + 0.5 * dt * kv;
+  } else if (stage == 3) {
+    acc[idx] += 2.0 * kv;
+    us[idx] = u0v + dt * kv;
+  } else {
+    us[idx] = u0v + (dt / 6.0) * (acc[idx] + kv);
+  }
+}
+
+template <bool RHS, bool CONSTRAINTS>
+__global__ void __launch_bounds__(PT_THREADS)
+pointwise_kernel(PointwiseArgs a) {
+  const int s = find_segment(a.begin, a.n_shells, blockIdx.x);
+  const ShellDev& sh = a.shells[s];
+  const int na = sh.na;
+  const int bps = (na + PT_THREADS - 1) / PT_THREADS;  // blocks per r-slice
+  const int lb = blockIdx.x - a.begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * PT_THREADS + threadIdx.x;
+  const bool valid = q < na;
+  double cdens = 0.0;
+  if (valid) {
+    const long long base = sh.off + (long long)ir * NF * na + q;
+    PointGeom G;
+    point_geom(sh, ir, q, G);
+    double psi[10], Pi[10], Phi[30];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      psi[p] = a.u[base + (long long)p * na];
+      Pi[p] = a.u[base + (long long)(10 + p) * na];
+    }
+#pragma unroll
+    for (int p = 0; p < 30; ++p) Phi[p] = a.u[base + (long long)(20 + p) * na];
+    const double* gsrc = sh.gauge + (long long)ir * NGAUGE * na + q;
+    double H[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
+
+    Split S;
+    spacetime_split(psi, S);
+    double Gam[40];
+    christoffel(S, Pi, Phi, Gam);
+    double C[4];
+    trace_gamma(S, Gam, C);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) C[c] += H[c];
+    const double al = S.alpha;
+    const double g0 = a.gamma0, g1 = a.gamma1, g2 = a.gamma2;
+
+    // ---- sources of the Pi equation that need no derivative (10 values)
+    double srcPi[10];
+    double srcPhi[30];
+    if (RHS) {
+      // nabla_(a H_b) = d_(a H_b) - psi^cd Gam_d(ab) H_c ;  d_0 H = 0
+      double dH[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
+      double PH[4];  // psi^cd H_c  (raised H)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(c, d)] * H[c];
+        PH[d] = acc;
+      }
+      // P_a[d][e] = psi^dc Gam_ace  (used for the Gam Gam term)
+      double Pm[4][16];
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(d, c)] * Gam[aa * 10 + sym_index(c, e)];
+            Pm[aa][d * 4 + e] = acc;
+          }
+      // U_i[d][a] = psi^dc Phi_ica ; W_j[d][a] = g^ij U_i[d][a]
+      double Wm[3][16];
+      {
+        double Um[3][16];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int aa = 0; aa < 4; ++aa) {
+              double acc = 0.0;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(d, c)] * Phi[i * 10 + sym_index(c, aa)];
+              Um[i][d * 4 + aa] = acc;
+            }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            Wm[j][e] = S.ginv[s3(0, j)] * Um[0][e] + S.ginv[s3(1, j)] * Um[1][e] + S.ginv[s3(2, j)] * Um[2][e];
+      }
+      // t^c t^d Pi_cd, t^c Pi_ci, t^c C_c
+      double tPt = 0.0, tC = 0.0;
+      double tPi[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tC += S.t_up[c] * C[c];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) tPt += S.t_up[c] * S.t_up[d] * Pi[sym_index(c, d)];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tPi[i] += S.t_up[c] * Pi[sym_index(c, 1 + i)];
+      }
+      // (t^c Pi_ci) g^ij  -> v^j
+      double tPig[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        tPig[j] = tPi[0] * S.ginv[s3(0, j)] + tPi[1] * S.ginv[s3(1, j)] + tPi[2] * S.ginv[s3(2, j)];
+      const double t_dn0 = -al;
+#pragma unroll
+      for (int p = 0; p < 10; ++p) {
+        const int A = pair_a(p), B = pair_b(p);
+        double T1 = 0.0, T2 = 0.0, T3 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int d = 0; d < 4; ++d) T1 += Wm[j][d * 4 + A] * Phi[j * 10 + sym_index(d, B)];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double pc = 0.0;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) pc += S.psi_inv[sym_index(c, d)] * Pi[sym_index(d, B)];
+          T2 += Pi[sym_index(c, A)] * pc;
+        }
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) T3 += Pm[A][d * 4 + e] * Pm[B][e * 4 + d];
+        // nabla_(A H_B)
+        const double dAHB = (A > 0 ? dH[4 * (A - 1) + B] : 0.0);
+        const double dBHA = (B > 0 ? dH[4 * (B - 1) + A] : 0.0);
+        double gh = 0.0;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) gh += PH[d] * Gam[d * 10 + p];
+        const double nablaH = 0.5 * (dAHB + dBHA) - gh;
+        // gamma0 damping: t_B C_A + t_A C_B - psi_AB t^c C_c, t_a = (-alpha,0,0,0)
+        const double damp = (B == 0 ? t_dn0 * C[A] : 0.0) + (A == 0 ? t_dn0 * C[B] : 0.0) - psi[p] * tC;
+        double tPiPhi = 0.0, bPhi = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          tPiPhi += tPig[j] * Phi[j * 10 + p];
+          bPhi += S.beta_up[j] * Phi[j * 10 + p];
+        }
+        srcPi[p] = 2.0 * al * (T1 - T2 - T3) - 2.0 * al * nablaH - 0.5 * al * tPt * Pi[p] -
+                   al * tPiPhi + g0 * al * damp - g1 * g2 * bPhi;
+      }
+      // Phi equation sources: 1/2 alpha t^c t^d Phi_icd Pi_ab
+      //   + alpha g^jk t^c Phi_ijc Phi_kab - alpha gamma2 Phi_iab
+      double tPhit[3], Mik[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int d = 0; d < 4; ++d) acc += S.t_up[c] * S.t_up[d] * Phi[i * 10 + sym_index(c, d)];
+        tPhit[i] = acc;
+        double tPhi_j[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          double t2 = 0.0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) t2 += S.t_up[c] * Phi[i * 10 + sym_index(1 + j, c)];
+          tPhi_j[j] = t2;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          Mik[i][k] = tPhi_j[0] * S.ginv[s3(0, k)] + tPhi_j[1] * S.ginv[s3(1, k)] + tPhi_j[2] * S.ginv[s3(2, k)];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int p = 0; p < 10; ++p)
+          srcPhi[i * 10 + p] = 0.5 * al * tPhit[i] * Pi[p] +
+                               al * (Mik[i][0] * Phi[p] + Mik[i][1] * Phi[10 + p] + Mik[i][2] * Phi[20 + p]) -
+                               al * g2 * Phi[i * 10 + p];
+    }
+
+    // beta^k J_k^d and g^ki J_k^d (spherical-basis contractions)
+    double bs[3], Gs[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bs[d] = S.beta_up[0] * G.J[0][d] + S.beta_up[1] * G.J[1][d] + S.beta_up[2] * G.J[2][d];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        Gs[i][d] = S.ginv[s3(0, i)] * G.J[0][d] + S.ginv[s3(1, i)] * G.J[1][d] + S.ginv[s3(2, i)] * G.J[2][d];
+    }
+
+    // constraint components of this point: c_out[64 pt_off + (ir*64 + comp)*na + q]
+    const long long cbase = 64LL * sh.pt_off + (long long)ir * NC * na + q;
+    if (CONSTRAINTS) {
+      double c2 = 0.0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        c2 += C[c] * C[c];
+        if (a.c_out) a.c_out[cbase + (long long)c * na] = C[c];
+      }
+      cdens = c2;
+    }
+
+    // ---- derivative terms, one symmetric pair at a time
+#pragma unroll 1
+    for (int p = 0; p < 10; ++p) {
+      double dpsi[3], dPi[3], dPhi[3][3];  // spherical-basis derivatives
+      {
+        const long long o = base + (long long)p * na;
+        dpsi[0] = a.dr[o]; dpsi[1] = a.dth[o]; dpsi[2] = a.dph[o];
+        const long long o2 = base + (long long)(10 + p) * na;
+        dPi[0] = a.dr[o2]; dPi[1] = a.dth[o2]; dPi[2] = a.dph[o2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const long long o3 = base + (long long)(20 + 10 * i + p) * na;
+          dPhi[i][0] = a.dr[o3]; dPhi[i][1] = a.dth[o3]; dPhi[i][2] = a.dph[o3];
+        }
+      }
+      // Cartesian derivatives d_i psi_p, d_i Pi_p
+      double cpsi[3], cPi[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        cpsi[i] = G.J[i][0] * dpsi[0] + G.J[i][1] * dpsi[1] + G.J[i][2] * dpsi[2];
+        cPi[i] = G.J[i][0] * dPi[0] + G.J[i][1] * dPi[1] + G.J[i][2] * dPi[2];
+      }
+      if (CONSTRAINTS) {
+        // C_iab = d_i psi_ab - Phi_iab ; C_ijab = d_i Phi_jab - d_j Phi_iab
+        double cPhi[3][3];  // cPhi[k][i] = d_k Phi_ip
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            cPhi[k][i] = G.J[k][0] * dPhi[i][0] + G.J[k][1] * dPhi[i][1] + G.J[k][2] * dPhi[i][2];
+        double c3[3], c4[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c3[i] = cpsi[i] - Phi[i * 10 + p];
+        c4[0] = cPhi[0][1] - cPhi[1][0];
+        c4[1] = cPhi[0][2] - cPhi[2][0];
+        c4[2] = cPhi[1][2] - cPhi[2][1];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) cdens += c3[i] * c3[i] + c4[i] * c4[i];
+        if (a.c_out) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            a.c_out[cbase + (long long)(4 + 10 * i + p) * na] = c3[i];
+            a.c_out[cbase + (long long)(34 + 10 * i + p) * na] = c4[i];
+          }
+        }
+      }
+      if (RHS) {
+        const double bdpsi = bs[0] * dpsi[0] + bs[1] * dpsi[1] + bs[2] * dpsi[2];
+        const double bdPi = bs[0] * dPi[0] + bs[1] * dPi[1] + bs[2] * dPi[2];
+        double gdPhi = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          gdPhi += Gs[i][0] * dPhi[i][0] + Gs[i][1] * dPhi[i][1] + Gs[i][2] * dPhi[i][2];
+        const double bPhi = S.beta_up[0] * Phi[p] + S.beta_up[1] * Phi[10 + p] + S.beta_up[2] * Phi[20 + p];
+        double out[5];
+        out[0] = (1.0 + g1) * bdpsi - al * Pi[p] - g1 * bPhi;
+        out[1] = bdPi - al * gdPhi + g1 * g2 * bdpsi + srcPi[p];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const double bdPhi = bs[0] * dPhi[i][0] + bs[1] * dPhi[i][1] + bs[2] * dPhi[i][2];
+          out[2 + i] = bdPhi - al * cPi[i] + al * g2 * cpsi[i] + srcPhi[i * 10 + p];
+        }
+        const int fidx[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
+        const bool on_bc = (ir == 0 && sh.bc_inner >= 0) || (ir == sh.n_r - 1 && sh.bc_outer >= 0);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+          const long long idx = base + (long long)fidx[e] * na;
+          if (a.stage == 0 || on_bc) a.k[idx] = out[e];
+          else stage_combine(a.stage, a.dt, out[e], idx, a.u0, a.acc, a.us);
+        }
+      }
+    }
+  }
+  if (CONSTRAINTS) {
+    // weighted block sum of the constraint energy density (deterministic order)
+    __shared__ double red[PT_THREADS];
+    double w = 0.0;
+    if (valid) {
+      const int j = q / sh.nph;
+      w = sh.wr[ir] * sh.wth[j];
+    }
+    red[threadIdx.x] = valid ? w * cdens : 0.0;
+    __syncthreads();
+    for (int st = PT_THREADS / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = red[0];
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Characteristic boundary conditions (ApplyBCs, Sec. 5), one thread per point
+// of every boundary slice.  The projection uses the fixed background (unit
+// normal n_i along +R, lapse, shift), so it is linear in dudt:
+//   w_psi = psi, w0_iab = Phi_iab - n_i n^k Phi_kab, w_pm = Pi +- n^k Phi_k - g2 psi
+//   speeds v_psi = -(1+g1) n.beta, v_0 = -n.beta, v_pm = -n.beta +- alpha.
+// Outer boundary: incoming families (v < 0) get zero time derivative.
+// Internal boundary: v < 0 families take the outer shell's value on both
+// sides, v > 0 families the inner shell's, v = 0 families keep their own.
+// After the condition the RK4 stage combine of those points is done here.
+struct CharVec {
+  double psi[10], wp[10], wm[10], w0[30];
+};
+
+__device__ __forceinline__ void char_project(const double* k, long long base, int na,
+                                             const double n_dn[3], const double n_up[3],
+                                             double g2, CharVec& c) {
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    const double ps = k[base + (long long)p * na];
+    const double pi = k[base + (long long)(10 + p) * na];
+    double ph[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ph[i] = k[base + (long long)(20 + 10 * i + p) * na];
+    const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
+    c.psi[p] = ps;
+    c.wp[p] = pi + nphi - g2 * ps;
+    c.wm[p] = pi - nphi - g2 * ps;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c.w0[i * 10 + p] = ph[i] - n_dn[i] * nphi;
+  }
+}
+
+__device__ __forceinline__ void char_recombine(const CharVec& c, const double n_dn[3], double g2,
+                                               double out[NF]) {
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    out[p] = c.psi[p];
+    out[10 + p] = 0.5 * (c.wp[p] + c.wm[p]) + g2 * c.psi[p];
+    const double h = 0.5 * (c.wp[p] - c.wm[p]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[20 + 10 * i + p] = n_dn[i] * h + c.w0[i * 10 + p];
+  }
+}
+
+struct BcArgs {
+  const BcSliceDev* slices;
+  int n_slices;
+  const int* pt_begin;   // first boundary point of each slice, [n_slices + 1]
+  double* k;
+  const double* u0;
+  double* acc;
+  double* us;
+  double gamma1, gamma2, dt;
+  int stage;
+};
+
+__device__ __forceinline__ void bc_write(const BcArgs& a, long long base, int na, const double v[NF]) {
+#pragma unroll 5
+  for (int f = 0; f < NF; ++f) {
+    const long long idx = base + (long long)f * na;
+    if (a.stage == 0) a.k[idx] = v[f];
+    else stage_combine(a.stage, a.dt, v[f], idx, a.u0, a.acc, a.us);
+  }
+}
+
+__device__ __forceinline__ void select_family(double* wi, double* wo, int n, double v) {
+  // v < 0: both take the outer side's value; v > 0: both take the inner side's.
+  if (v < 0.0) {
+    for (int e = 0; e < n; ++e) wi[e] = wo[e];
+  } else if (v > 0.0) {
+    for (int e = 0; e < n; ++e) wo[e] = wi[e];
+  }
+}
+
+__global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.pt_begin[a.n_slices]) return;
+  const int s = find_segment(a.pt_begin, a.n_slices, t);
+  const BcSliceDev& sl = a.slices[s];
+  const int q = t - a.pt_begin[s];
+  const int na = sl.na;
+  double n_dn[3], n_up[3], beta[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    n_dn[i] = sl.bg[(long long)i * na + q];
+    n_up[i] = sl.bg[(long long)(3 + i) * na + q];
+    beta[i] = sl.bg[(long long)(7 + i) * na + q];
+  }
+  const double alpha = sl.bg[(long long)6 * na + q];
+  const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
+  const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
+  const double g2 = a.gamma2;
+  double out[NF];
+  if (sl.kind == 0) {
+    const long long base = sl.off_a + q;
+    CharVec c;
+    char_project(a.k, base, na, n_dn, n_up, g2, c);
+    if (v_psi < 0.0) for (int e = 0; e < 10; ++e) c.psi[e] = 0.0;
+    if (v_0 < 0.0) for (int e = 0; e < 30; ++e) c.w0[e] = 0.0;
+    if (v_p < 0.0) for (int e = 0; e < 10; ++e) c.wp[e] = 0.0;
+    if (v_m < 0.0) for (int e = 0; e < 10; ++e) c.wm[e] = 0.0;
+    char_recombine(c, n_dn, g2, out);
+    bc_write(a, base, na, out);
+  } else {
+    const long long ba = sl.off_a + q, bb = sl.off_b + q;
+    CharVec ci, co;
+    char_project(a.k, ba, na, n_dn, n_up, g2, ci);
+    char_project(a.k, bb, na, n_dn, n_up, g2, co);
+    select_family(ci.psi, co.psi, 10, v_psi);
+    select_family(ci.w0, co.w0, 30, v_0);
+    select_family(ci.wp, co.wp, 10, v_p);
+    select_family(ci.wm, co.wm, 10, v_m);
+    char_recombine(ci, n_dn, g2, out);
+    bc_write(a, ba, na, out);
+    char_recombine(co, n_dn, g2, out);
+    bc_write(a, bb, na, out);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary background from the metric part of a state: lapse, shift and the
+// unit normal n_i = d_i R / |d R|_g, n^i = g^ij n_j.
+__global__ void __launch_bounds__(128)
+bc_background_kernel(const ShellDev* __restrict__ shells, BcSliceDev* slices, int n_slices,
+                     const int* __restrict__ pt_begin, const double* __restrict__ u) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pt_begin[n_slices]) return;
+  const int s = find_segment(pt_begin, n_slices, t);
+  BcSliceDev& sl = slices[s];
+  const int q = t - pt_begin[s];
+  const int na = sl.na;
+  const ShellDev& sh = shells[sl.shell_a];
+  double psi[10];
+#pragma unroll
+  for (int p = 0; p < 10; ++p) psi[p] = u[sl.off_a + (long long)p * na + q];
+  Split S;
+  spacetime_split(psi, S);
+  const int j = q / sh.nph, k = q - j * sh.nph;
+  const double dR[3] = {sh.sth[j] * sh.cph[k], sh.sth[j] * sh.sph[k], sh.cth[j]};
+  double nn = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) nn += S.ginv[s3(i, m)] * dR[i] * dR[m];
+  const double inv = 1.0 / sqrt(nn);
+  double n_dn[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) n_dn[i] = dR[i] * inv;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sl.bg[(long long)i * na + q] = n_dn[i];
+    sl.bg[(long long)(3 + i) * na + q] =
+        S.ginv[s3(i, 0)] * n_dn[0] + S.ginv[s3(i, 1)] * n_dn[1] + S.ginv[s3(i, 2)] * n_dn[2];
+    sl.bg[(long long)(7 + i) * na + q] = S.beta_up[i];
+  }
+  sl.bg[(long long)6 * na + q] = S.alpha;
+}
+
+// ---------------------------------------------------------------------------
+// Cartesian derivatives d_i u of all 50 fields (Eq. DiffJac applied to the
+// output of the radial and angular maps).  One thread per (point, field).
+__global__ void __launch_bounds__(PT_THREADS)
+cartesian_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                 const double* __restrict__ dr, const double* __restrict__ dth,
+                 const double* __restrict__ dph, double* __restrict__ du, long long state) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + PT_THREADS - 1) / PT_THREADS;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * PT_THREADS + threadIdx.x;
+  if (q >= na) return;
+  PointGeom G;
+  point_geom(sh, ir, q, G);
+  const long long base = sh.off + (long long)ir * NF * na + q;
+  for (int f = 0; f < NF; ++f) {
+    const long long o = base + (long long)f * na;
+    const double a0 = dr[o], a1 = dth[o], a2 = dph[o];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) du[i * state + o] = G.J[i][0] * a0 + G.J[i][1] * a1 + G.J[i][2] * a2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-shell sum of the per-block constraint partials, in a fixed order, and
+// a latched error if the result is not finite.
+__global__ void norm_reduce_kernel(const int* __restrict__ begin, int n_shells,
+                                   const double* __restrict__ partial, double* norm2, int* err) {
+  const int s = blockIdx.x;
+  if (s >= n_shells) return;
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int b = begin[s] + threadIdx.x; b < begin[s + 1]; b += blockDim.x) acc += partial[b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    norm2[s] = red[0];
+    if (!isfinite(red[0])) atomicExch(err, (int)GH_ENONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter) {
+  if (filter)
+    radial_kernel<true><<<d->rad_blocks, RAD_THREADS, 0, d->stream>>>(d->shells_d, d->n_shells,
+                                                                      d->rad_block_begin_d, in, out);
+  else
+    radial_kernel<false><<<d->rad_blocks, RAD_THREADS, 0, d->stream>>>(d->shells_d, d->n_shells,
+                                                                       d->rad_block_begin_d, in, out);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angular_deriv(gh_domain* d, const double* in) {
+  gemm_batched_kernel<<<d->ang_deriv_tiles, GEMM_THREADS, 0, d->stream>>>(
+      d->ang_deriv_d, d->ang_deriv_np, in, d->d_th, d->d_ph);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out) {
+  gemm_batched_kernel<<<d->ang_filt_tiles, GEMM_THREADS, 0, d->stream>>>(
+      d->ang_filt_d, d->ang_filt_np, in, out, out);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage, double dt,
+                             const double* u0, double* acc, double* ustage, bool constraints) {
+  PointwiseArgs a;
+  a.shells = d->shells_d; a.n_shells = d->n_shells; a.begin = d->pt_block_begin_d;
+  a.u = u; a.dr = d->d_r; a.dth = d->d_th; a.dph = d->d_ph;
+  a.k = k; a.u0 = u0; a.acc = acc; a.us = ustage;
+  a.partial = d->partial; a.c_out = nullptr;
+  a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
+  a.dt = dt; a.stage = stage;
+  if (constraints)
+    pointwise_kernel<true, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  else
+    pointwise_kernel<true, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out) {
+  PointwiseArgs a;
+  a.shells = d->shells_d; a.n_shells = d->n_shells; a.begin = d->pt_block_begin_d;
+  a.u = u; a.dr = d->d_r; a.dth = d->d_th; a.dph = d->d_ph;
+  a.k = nullptr; a.u0 = nullptr; a.acc = nullptr; a.us = nullptr;
+  a.partial = d->partial; a.c_out = c_out;
+  a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
+  a.dt = 0.0; a.stage = 0;
+  pointwise_kernel<false, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_reduce(gh_domain* d, double* norm2) {
+  norm_reduce_kernel<<<d->n_shells, 256, 0, d->stream>>>(d->pt_block_begin_d, d->n_shells,
+                                                          d->partial, norm2, d->err_flag);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const double* u0, double* acc,
+                      double* ustage) {
+  if (d->bc_points == 0) return cudaSuccess;
+  BcArgs a;
+  a.slices = d->bc_d; a.n_slices = (int)d->bc_h.size(); a.pt_begin = d->bc_pt_begin_d;
+  a.k = k; a.u0 = u0; a.acc = acc; a.us = ustage;
+  a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2; a.dt = dt; a.stage = stage;
+  bc_kernel<<<cdiv(d->bc_points, 128), 128, 0, d->stream>>>(a);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc_background(gh_domain* d, const double* u) {
+  if (d->bc_points == 0) return cudaSuccess;
+  bc_background_kernel<<<cdiv(d->bc_points, 128), 128, 0, d->stream>>>(
+      d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, u);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du) {
+  (void)u;
+  cartesian_kernel<<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(
+      d->shells_d, d->n_shells, d->pt_block_begin_d, d->d_r, d->d_th, d->d_ph, du, d->state);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace gh

@@ -1,0 +1,204 @@
+"""Thin Python binding of libgh (include/gh.h): argument marshalling only.
+
+Every function has the name of the C entry point it wraps and takes torch
+tensors that must be contiguous float64 CUDA tensors; all arithmetic runs in
+the library's CUDA kernels.  Calls are enqueued on torch's current CUDA
+stream.  There is no CPU fallback: if libgh.so cannot be loaded, importing
+this module raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libgh.so")
+
+GH_OK, GH_EINVAL, GH_ENOMEM, GH_ECUDA, GH_ETIMEOUT, GH_ENONFINITE, GH_ENOTSUP = range(7)
+_NAMES = ["GH_OK", "GH_EINVAL", "GH_ENOMEM", "GH_ECUDA", "GH_ETIMEOUT", "GH_ENONFINITE", "GH_ENOTSUP"]
+
+NF = 50
+
+
+class GHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_NAMES[status] if 0 <= status < len(_NAMES) else status, msg))
+        self.status = status
+
+
+class gh_shell(ctypes.Structure):
+    _fields_ = [("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+                ("n_r", ctypes.c_int), ("L", ctypes.c_int)]
+
+
+class gh_params(ctypes.Structure):
+    _fields_ = [("gamma0", ctypes.c_double), ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
+                ("filt_alpha", ctypes.c_double), ("filt_order", ctypes.c_int),
+                ("radial_filter_on", ctypes.c_int), ("sh_keep_l", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libgh.so not built at %s (run __graft_entry__.build())" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sigs = {
+        "gh_create_domain": ([ctypes.POINTER(gh_shell), I, ctypes.POINTER(gh_params), P, ctypes.POINTER(P)], I),
+        "gh_destroy_domain": ([P], I),
+        "gh_set_stream": ([P, P], I),
+        "gh_state_size": ([P], ctypes.c_longlong),
+        "gh_num_points": ([P], ctypes.c_longlong),
+        "gh_rk4_work_size": ([P], ctypes.c_longlong),
+        "gh_num_shells": ([P], I),
+        "gh_launch_count": ([P], ctypes.c_longlong),
+        "gh_last_error": ([P], ctypes.c_char_p),
+        "gh_set_analytic_kerr_schild": ([P, D, D, P], I),
+        "gh_set_gauge": ([P, P, P], I),
+        "gh_set_background": ([P, P], I),
+        "gh_get_gauge": ([P, P, P], I),
+        "gh_add_perturbation": ([P, I, D, D, D, I, P, P], I),
+        "gh_derivatives": ([P, P, P], I),
+        "gh_rhs": ([P, P, P], I),
+        "gh_rk4_step": ([P, D, P, P, P], I),
+        "gh_apply_filters": ([P, P, P], I),
+        "gh_constraints": ([P, P, P, P], I),
+        "gh_sync": ([P], I),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def _ptr(t, name, numel=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Domain:
+    """Owns a gh_domain handle (shells, cached matrices, scratch)."""
+
+    def __init__(self, shells, gamma0=1.0, gamma1=-1.0, gamma2=1.0, filt_alpha=36.0, filt_order=32,
+                 radial_filter_on=False, sh_keep_l=-1):
+        arr = (gh_shell * len(shells))(*[gh_shell(float(a), float(b), int(n), int(L)) for (a, b, n, L) in shells])
+        self.params = gh_params(gamma0, gamma1, gamma2, filt_alpha, int(filt_order),
+                                int(bool(radial_filter_on)), int(sh_keep_l))
+        h = ctypes.c_void_p()
+        st = _lib.gh_create_domain(arr, len(shells), ctypes.byref(self.params),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(h))
+        if st != GH_OK:
+            raise GHError(st, _lib.gh_last_error(None).decode())
+        self.handle = h
+        self.shells = [tuple(s) for s in shells]
+        self.state_size = _lib.gh_state_size(h)
+        self.num_points = _lib.gh_num_points(h)
+        self.work_size = _lib.gh_rk4_work_size(h)
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.shells, w.gamma0, w.gamma1, w.gamma2, w.filt_alpha, w.filt_order,
+                   w.radial_filter_on, w.sh_keep_l)
+
+    def _check(self, st):
+        if st != GH_OK:
+            raise GHError(st, _lib.gh_last_error(self.handle).decode())
+
+    def _stream(self):
+        _lib.gh_set_stream(self.handle, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.gh_destroy_domain(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self):
+        return _lib.gh_launch_count(self.handle)
+
+    # -- allocation helpers (torch owns the memory)
+    def new_state(self):
+        return torch.zeros(self.state_size, dtype=torch.float64, device="cuda")
+
+    def new_work(self):
+        return torch.zeros(self.work_size, dtype=torch.float64, device="cuda")
+
+
+def gh_set_analytic_kerr_schild(dom, M, chi, u):
+    dom._stream()
+    dom._check(_lib.gh_set_analytic_kerr_schild(dom.handle, float(M), float(chi), _ptr(u, "u", dom.state_size)))
+
+
+def gh_set_gauge(dom, H, dH):
+    dom._stream()
+    dom._check(_lib.gh_set_gauge(dom.handle, _ptr(H, "H", 4 * dom.num_points), _ptr(dH, "dH", 12 * dom.num_points)))
+
+
+def gh_get_gauge(dom, H, dH):
+    dom._stream()
+    dom._check(_lib.gh_get_gauge(dom.handle, _ptr(H, "H", 4 * dom.num_points), _ptr(dH, "dH", 12 * dom.num_points)))
+
+
+def gh_set_background(dom, u_bg):
+    dom._stream()
+    dom._check(_lib.gh_set_background(dom.handle, _ptr(u_bg, "u_bg", dom.state_size)))
+
+
+def gh_add_perturbation(dom, kind, A, Rc, w, lmax, coeffs, u):
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    if c.size != (lmax + 1) ** 2:
+        raise ValueError("need (lmax+1)^2 coefficients")
+    dom._stream()
+    dom._check(_lib.gh_add_perturbation(dom.handle, int(kind), float(A), float(Rc), float(w), int(lmax),
+                                        c.ctypes.data_as(ctypes.c_void_p), _ptr(u, "u", dom.state_size)))
+
+
+def gh_derivatives(dom, u, du):
+    dom._stream()
+    dom._check(_lib.gh_derivatives(dom.handle, _ptr(u, "u", dom.state_size), _ptr(du, "du", 3 * dom.state_size)))
+
+
+def gh_rhs(dom, u, dudt):
+    dom._stream()
+    dom._check(_lib.gh_rhs(dom.handle, _ptr(u, "u", dom.state_size), _ptr(dudt, "dudt", dom.state_size)))
+
+
+def gh_rk4_step(dom, dt, u, work, norm2_pre=None):
+    dom._stream()
+    dom._check(_lib.gh_rk4_step(dom.handle, float(dt), _ptr(u, "u", dom.state_size),
+                                _ptr(work, "work", dom.work_size), _ptr(norm2_pre, "norm2_pre")))
+
+
+def gh_apply_filters(dom, u, work):
+    dom._stream()
+    dom._check(_lib.gh_apply_filters(dom.handle, _ptr(u, "u", dom.state_size), _ptr(work, "work", dom.work_size)))
+
+
+def gh_constraints(dom, u, c_out, norm2):
+    dom._stream()
+    dom._check(_lib.gh_constraints(dom.handle, _ptr(u, "u", dom.state_size),
+                                   _ptr(c_out, "c_out", 64 * dom.num_points), _ptr(norm2, "norm2", len(dom.shells))))
+
+
+def gh_sync(dom):
+    dom._check(_lib.gh_sync(dom.handle))
