@@ -1,0 +1,301 @@
+"""Benchmark: GH right-hand-side grid-point evaluations per second on one GB300.
+
+One step = one full pass of the hot path on the 4-shell Kerr workload
+(a = 0.9, M = 1, shells [1.3, 3, 6, 12, 30], N_r = 21, L = 15; 43,008 points):
+an RK4 step (4 right-hand sides with derivatives, the fused GH kernel,
+characteristic boundary conditions and stage combines), the exponential
+Chebyshev and SH 2/3 filters, and the quadrature constraint norms (computed
+inside the first stage).  Throughput = points x 4 RHS evaluations per step / time.
+
+The state (17 MB) fits in L2, so L2 is flushed (a 256 MB write) before every
+timed step, outside the step's events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank evolves its own replica:
+the workload is one coupled black hole and does not shard (replicas only).
+"--impl reference" times the CPU oracle (the only reference this method has).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GH RHS grid-point evals/s (FP64, 1 GB300) + % roofline; batched vs plain; adjoint/fwd"
+UNIT = "grid-point RHS evals/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------- oracle timing
+def oracle_setup(w):
+    import numpy as np
+    from oracle import evolve, perturb
+    dom = evolve.Domain(w.shells, w.M, w.chi, w.gamma0, w.gamma1, w.gamma2, w.filt_alpha,
+                        w.filt_order, w.radial_filter_on, w.sh_keep_l)
+    u = []
+    for s, g in enumerate(dom.grids):
+        p = w.pulse
+        u.append(dom.u_exact[s] + perturb.psi_pulse(g, dom.u_exact[s], p.amplitude, p.center, p.width,
+                                                      p.lmax, p.coeffs))
+    return dom, u
+
+
+def cpu_baseline(w, min_seconds=10.0):
+    """Time the oracle's full right-hand side (all shells) until >= min_seconds."""
+    from oracle import evolve
+    dom, u = oracle_setup(w)
+    evals = 0
+    t0 = time.perf_counter()
+    while True:
+        evolve.rhs(dom, u)
+        evals += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return dict(value=w.points() * evals / el, unit=UNIT, cores=blas_threads(), kind="oracle",
+                sample="%d full right-hand-side evaluation(s) of the 4-shell workload (%d points), "
+                       "%.1f s, numpy FP64 on the host" % (evals, w.points(), el))
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import evolve
+    dom, u = oracle_setup(w)
+    for _ in range(args.warmup):
+        evolve.rhs(dom, u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        evolve.rhs(dom, u)
+    el = time.perf_counter() - t0
+    value = w.points() * args.steps / el
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000.0 * el / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=w.name, points=w.points(),
+                            step="one full oracle right-hand-side evaluation (all 4 shells)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=blas_threads(), kind="oracle",
+                                  sample="%d full RHS evaluations of the 4-shell workload" % args.steps),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for ln in open(self.f.name):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=reasons, samples=len(rows))
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, w):
+    import torch
+    from paper_1804_09101_gb300 import build
+    build.build()
+    from paper_1804_09101_gb300 import costmodel, gh
+
+    rank, world, local = dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    dom = gh.Domain.from_workload(w)
+    u = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, w.M, w.chi, u)
+    p = w.pulse
+    gh.gh_add_perturbation(dom, 0, p.amplitude, p.center, p.width, p.lmax, p.coeffs, u)
+    work = dom.new_work()
+    norm2 = torch.zeros(len(w.shells), dtype=torch.float64, device=dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        gh.gh_rk4_step(dom, w.dt, u, work, norm2)
+    gh.gh_sync(dom)
+
+    # ---- device-resident timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    gh.gh_profile_enable(dom, True)
+    for fam in range(len(gh.KERNEL_FAMILIES)):
+        gh.gh_profile_read(dom, fam)
+    barrier()
+    clocks.start()
+    n0 = dom.launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        gh.gh_rk4_step(dom, w.dt, u, work, norm2)
+        ev[i][1].record(stream)
+    barrier()
+    launches = dom.launch_count() - n0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    fam_ms = {}
+    for fam, name in enumerate(gh.KERNEL_FAMILIES):
+        fam_ms[name] = gh.gh_profile_read(dom, fam)
+    gh.gh_profile_enable(dom, False)
+    gh.gh_sync(dom)
+    if pg is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t[0])
+
+    pts = w.points()
+    value = world * pts * 4 * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through the C ABI with host buffers
+    u_host = u.detach().cpu().pin_memory()
+    out_host = torch.empty_like(u_host).pin_memory()
+    n_host = torch.empty(len(w.shells), dtype=torch.float64).pin_memory()
+    e2e_ms = 0.0
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        u.copy_(u_host, non_blocking=True)
+        gh.gh_rk4_step(dom, w.dt, u, work, norm2)
+        out_host.copy_(u, non_blocking=True)
+        n_host.copy_(norm2, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    barrier()
+    if pg is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t[0])
+    e2e_value = world * pts * 4 * args.steps / (e2e_ms / 1000.0)
+    state_bytes = dom.state_size * 8
+
+    # ---- roofline of the dominant kernel (angular derivative maps)
+    ang_ms, ang_n = fam_ms["angular"]
+    ang_flops = costmodel.angular_deriv_flops(w.shells)
+    achieved = ang_flops / (ang_ms / ang_n / 1000.0) / 1e12 if ang_n else None
+    peak = costmodel.GB300_FP64_PEAK_TFLOPS
+    roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                    frac=(achieved / peak) if achieved else None, traffic=None,
+                    kernel="gemm_batched_kernel (angular d/dtheta, d/dphi maps, FP64 FFMA)",
+                    flops_per_launch=ang_flops, launch_ms=ang_ms / ang_n if ang_n else None,
+                    peak_source="derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (recipe nominal 1.25 TFLOP/s)")
+    kernels = {name: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
+               for name, v in fam_ms.items() if v[1]}
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=w.name, points=pts, shells=[list(s) for s in w.shells], chi=w.chi,
+                            dt=w.dt, rhs_evals_per_step=4,
+                            step="RK4 step + ExpCheb(36,32) + SH keep l<=10 + constraint norms",
+                            l2="flushed before every timed step (256 MB write, outside the step events)",
+                            parallelism="replicas" if world > 1 else "single GPU"),
+                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=state_bytes,
+                         d2h_bytes_per_step=state_bytes + 8 * len(w.shells)),
+                gpu_launches=launches, roofline=roofline, kernels=kernels)
+    if clk is not None:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from paper_1804_09101_gb300 import workloads
+    w = workloads.kerr_four_shells()
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,25 @@ const char* gh_last_error(const gh_domain* dom);
 /* Number of kernel launches the library has enqueued on this domain so far. */
 long long gh_launch_count(const gh_domain* dom);
 
+/* Kernel families for the profiler below. */
+typedef enum {
+  GH_K_RADIAL = 0,        /* radial derivative map (Chebyshev, n_r x n_r)          */
+  GH_K_ANGULAR = 1,       /* angular derivative maps (d/dtheta, d/dphi)             */
+  GH_K_POINTWISE = 2,     /* fused DiffJac + GH right-hand side + RK4 combine       */
+  GH_K_BC = 3,            /* characteristic boundary conditions                     */
+  GH_K_RADIAL_FILTER = 4, /* exponential Chebyshev filter                          */
+  GH_K_ANGULAR_FILTER = 5,/* spherical-harmonic truncation filter                   */
+  GH_K_REDUCE = 6,        /* constraint-norm reduction                              */
+  GH_K_FAMILIES = 7
+} gh_kernel_family;
+
+/* Profiler: while enabled, every kernel the domain launches is bracketed by
+ * CUDA events recorded on the domain's stream.  gh_profile_read synchronises
+ * the stream, adds the elapsed times of all completed brackets of one family
+ * to *total_ms and their number to *launches, and clears that family. */
+gh_status gh_profile_enable(gh_domain* dom, int on);
+gh_status gh_profile_read(gh_domain* dom, int family, double* total_ms, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

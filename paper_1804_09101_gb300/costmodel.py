@@ -1,0 +1,79 @@
+"""Operation-count models: the paper's (Secs. 3.3 and 3.4) and this library's.
+
+The paper models each operation by its minimum memory transactions M
+(doubles moved) and floating-point operations F, with arithmetic intensity
+I = F / M (Sec. 2.3).  Its printed values pin these functions in the tests.
+The library's own counts (what its kernels compute per launch) are used for
+the roofline fractions the benchmark reports.
+"""
+
+# GB300 FP64 pipe: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA) x 2.07 GHz maximum SM clock.
+GB300_SMS = 152
+GB300_FP64_FLOP_PER_CLK_PER_SM = 4
+GB300_MAX_SM_GHZ = 2.07
+GB300_FP64_PEAK_TFLOPS = GB300_SMS * GB300_FP64_FLOP_PER_CLK_PER_SM * GB300_MAX_SM_GHZ / 1000.0
+
+
+# ------------------------------------------------------------ paper, Sec. 3.3
+def diffjac_intensity(n_e, d=3):
+    """DiffJac: M = N_x (2 N_e + d) d, F = N_x N_e (2d - 1) d, so I = 5 N_e / (2 N_e + 3) for d = 3."""
+    M = (2 * n_e + d) * d
+    F = n_e * (2 * d - 1) * d
+    return F / M
+
+
+SPATIAL_COORD_JAC = {
+    # structure: (M per point, F per point), Sec. 3.3
+    "a": (15, 15), "aa": (30, 75), "ab": (48, 120), "abb": (120, 495),
+}
+
+
+def spatial_coord_jac_intensity(structure):
+    M, F = SPATIAL_COORD_JAC[structure]
+    return F / M
+
+
+# ------------------------------------------------------------ paper, Sec. 3.4
+def i1s2_differentiator(n_e, n_r, n_th, n_ph):
+    """Dense-matrix differentiator on an I1 x S2 shell: (M, F)."""
+    na = n_th * n_ph
+    M = n_e * (n_r ** 2 + 2 * na ** 2 + 6 * n_r * na)
+    F = n_e * n_r * na * (2 * n_r + 4 * na - 3)
+    return M, F
+
+
+def singlebh_grid(k):
+    """SingleBH benchmark shells: N_r = 9 + 4k, N_theta = 6 + 2k, N_phi = 4k + 12."""
+    return 9 + 4 * k, 6 + 2 * k, 4 * k + 12
+
+
+def bbh_grid(k):
+    """BBH benchmark shells: N_r = 4 + k, N_theta = 7 + 2k, N_phi = 4k + 14."""
+    return 4 + k, 7 + 2 * k, 4 * k + 14
+
+
+# ------------------------------------------------------------ this library
+def angular_deriv_flops(shells):
+    """FP64 flops of one angular-derivative launch: two dense maps per shell,
+    each a (50 n_r) x N_a x N_a product (N_a = N_theta N_phi), 2 flops per FMA."""
+    f = 0
+    for (_, _, n_r, L) in shells:
+        na = (L + 1) * 2 * (L + 1)
+        f += 2 * (2 * 50 * n_r * na * na)
+    return f
+
+
+def angular_filter_flops(shells):
+    f = 0
+    for (_, _, n_r, L) in shells:
+        na = (L + 1) * 2 * (L + 1)
+        f += 2 * 50 * n_r * na * na
+    return f
+
+
+def radial_flops(shells):
+    f = 0
+    for (_, _, n_r, L) in shells:
+        na = (L + 1) * 2 * (L + 1)
+        f += 2 * 50 * na * n_r * n_r
+    return f

@@ -266,9 +266,46 @@ gh_status check_latched(gh_domain* d) {
   return GH_OK;
 }
 
+// Profiler brackets (no-ops unless gh_profile_enable(dom, 1)).
+cudaEvent_t take_event(gh_domain* d) {
+  if (!d->event_pool.empty()) {
+    cudaEvent_t e = d->event_pool.back();
+    d->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  gh_domain* d;
+  int fam;
+  cudaEvent_t a = nullptr;
+  ProfScope(gh_domain* dd, int f) : d(dd), fam(f) {
+    if (d->prof) {
+      a = take_event(d);
+      cudaEventRecord(a, d->stream);
+    }
+  }
+  ~ProfScope() {
+    if (d->prof && a) {
+      cudaEvent_t b = take_event(d);
+      cudaEventRecord(b, d->stream);
+      d->pending.push_back({fam, a, b});
+    }
+  }
+};
+
 gh_status derivatives(gh_domain* d, const double* u) {
-  GH_CUDA(d, gh::launch_radial(d, u, d->d_r, false));
-  GH_CUDA(d, gh::launch_angular_deriv(d, u));
+  {
+    ProfScope p(d, GH_K_RADIAL);
+    GH_CUDA(d, gh::launch_radial(d, u, d->d_r, false));
+  }
+  {
+    ProfScope p(d, GH_K_ANGULAR);
+    GH_CUDA(d, gh::launch_angular_deriv(d, u));
+  }
   return GH_OK;
 }
 
@@ -278,10 +315,12 @@ gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
   const bool ang = d->params.sh_keep_l >= 0;
   double* cur = src;
   if (rad) {
+    ProfScope p(d, GH_K_RADIAL_FILTER);
     GH_CUDA(d, gh::launch_radial(d, cur, d->d_r, true));
     cur = d->d_r;
   }
   if (ang) {
+    ProfScope p(d, GH_K_ANGULAR_FILTER);
     double* dst = (cur == u) ? tmp : u;
     GH_CUDA(d, gh::launch_angular_filter(d, cur, dst));
     cur = dst;
@@ -549,6 +588,11 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
 gh_status gh_destroy_domain(gh_domain* d) {
   if (!d) return GH_EINVAL;
   cudaStreamSynchronize(d->stream);
+  for (auto& b : d->pending) {
+    cudaEventDestroy(b.a);
+    cudaEventDestroy(b.b);
+  }
+  for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
   for (void* p : d->owned) cudaFree(p);
   delete d;
   return GH_OK;
@@ -649,8 +693,14 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
   if (u == dudt) return fail(d, GH_EINVAL, "u and dudt must not overlap");
   if (gh_status s = check_latched(d)) return s;
   if (gh_status s = derivatives(d, u)) return s;
-  GH_CUDA(d, gh::launch_pointwise(d, u, dudt, 0, 0.0, nullptr, nullptr, nullptr, false));
-  GH_CUDA(d, gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr));
+  {
+    ProfScope p(d, GH_K_POINTWISE);
+    GH_CUDA(d, gh::launch_pointwise(d, u, dudt, 0, 0.0, nullptr, nullptr, nullptr, false));
+  }
+  {
+    ProfScope p(d, GH_K_BC);
+    GH_CUDA(d, gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr));
+  }
   return GH_OK;
 }
 
@@ -665,9 +715,18 @@ gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* 
     const double* in = (stage == 1) ? u : us;
     if (gh_status s = derivatives(d, in)) return s;
     double* target = (stage == 4 && !filt) ? u : us;
-    GH_CUDA(d, gh::launch_pointwise(d, in, k, stage, dt, u, acc, target, stage == 1 && norm2_pre));
-    if (stage == 1 && norm2_pre) GH_CUDA(d, gh::launch_norm_reduce(d, norm2_pre));
-    GH_CUDA(d, gh::launch_bc(d, k, stage, dt, u, acc, target));
+    {
+      ProfScope p(d, GH_K_POINTWISE);
+      GH_CUDA(d, gh::launch_pointwise(d, in, k, stage, dt, u, acc, target, stage == 1 && norm2_pre));
+    }
+    if (stage == 1 && norm2_pre) {
+      ProfScope p(d, GH_K_REDUCE);
+      GH_CUDA(d, gh::launch_norm_reduce(d, norm2_pre));
+    }
+    {
+      ProfScope p(d, GH_K_BC);
+      GH_CUDA(d, gh::launch_bc(d, k, stage, dt, u, acc, target));
+    }
   }
   if (filt) {
     if (gh_status s = filters(d, us, u, k)) return s;
@@ -686,6 +745,33 @@ gh_status gh_constraints(gh_domain* d, const double* u, double* c_out, double* n
   if (gh_status s = derivatives(d, u)) return s;
   GH_CUDA(d, gh::launch_constraints(d, u, c_out));
   GH_CUDA(d, gh::launch_norm_reduce(d, norm2));
+  return GH_OK;
+}
+
+gh_status gh_profile_enable(gh_domain* d, int on) {
+  if (!d) return GH_EINVAL;
+  d->prof = on != 0;
+  return GH_OK;
+}
+
+gh_status gh_profile_read(gh_domain* d, int family, double* total_ms, long long* launches) {
+  if (!d || !total_ms || !launches || family < 0 || family >= GH_K_FAMILIES)
+    return fail(d, GH_EINVAL, "bad profiler arguments");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  std::vector<gh_domain::Bracket> keep;
+  for (auto& b : d->pending) {
+    float ms = 0.f;
+    GH_CUDA(d, cudaEventElapsedTime(&ms, b.a, b.b));
+    d->prof_ms[b.fam] += ms;
+    d->prof_n[b.fam] += 1;
+    d->event_pool.push_back(b.a);
+    d->event_pool.push_back(b.b);
+  }
+  d->pending.clear();
+  *total_ms = d->prof_ms[family];
+  *launches = d->prof_n[family];
+  d->prof_ms[family] = 0.0;
+  d->prof_n[family] = 0;
   return GH_OK;
 }
 

@@ -93,6 +93,13 @@ struct gh_domain {
   std::vector<void*> owned;      // every device allocation, freed on destroy
   std::string err;
   long long launches = 0;
+  // profiler (gh_profile_enable / gh_profile_read)
+  bool prof = false;
+  struct Bracket { int fam; cudaEvent_t a, b; };
+  std::vector<Bracket> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double prof_ms[8] = {0};
+  long long prof_n[8] = {0};
 };
 
 namespace gh {

@@ -65,6 +65,8 @@ def _load():
         "gh_apply_filters": ([P, P, P], I),
         "gh_constraints": ([P, P, P, P], I),
         "gh_sync": ([P], I),
+        "gh_profile_enable": ([P, I], I),
+        "gh_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -198,6 +200,22 @@ def gh_constraints(dom, u, c_out, norm2):
     dom._stream()
     dom._check(_lib.gh_constraints(dom.handle, _ptr(u, "u", dom.state_size),
                                    _ptr(c_out, "c_out", 64 * dom.num_points), _ptr(norm2, "norm2", len(dom.shells))))
+
+
+KERNEL_FAMILIES = ["radial", "angular", "pointwise", "bc", "radial_filter", "angular_filter", "reduce"]
+
+
+def gh_profile_enable(dom, on=True):
+    dom._stream()
+    dom._check(_lib.gh_profile_enable(dom.handle, int(bool(on))))
+
+
+def gh_profile_read(dom, family):
+    """(total_ms, launches) of one kernel family since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    dom._check(_lib.gh_profile_read(dom.handle, int(family), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def gh_sync(dom):
