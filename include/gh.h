@@ -158,6 +158,26 @@ gh_status gh_apply_filters(gh_domain* dom, double* u, double* work);
  * Clenshaw-Curtis x Gauss-Legendre x uniform quadrature. */
 gh_status gh_constraints(gh_domain* dom, const double* u, double* c_out, double* norm2);
 
+/* gh_rhs_noalloc: the same right-hand side as gh_rhs, computed without any
+ * device allocation.  The three derivative work buffers come from one fixed
+ * array inside the library (3 x 2^20 doubles = 24 MiB, present on every GPU
+ * that loads the library until the process exits) instead of the domain's
+ * own scratch.  It is meant for callers that must not allocate GPU memory at
+ * call time: a host whose own memory pool owns the device memory, or a
+ * time-critical loop that cannot afford an allocation or the synchronisation
+ * it can bring.  The domain itself is still created (and allocated) once, up
+ * front.  The paper has no counterpart of this entry point.
+ *   - Limit: gh_state_size(dom) <= 2^20 doubles (about 20,000 grid points);
+ *     larger domains get GH_EINVAL with a message.  Use gh_rhs for them.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make this first call before any stream capture.
+ *   - Every call uses the same array: calls that run at the same time on the
+ *     GPU (other streams, other host threads) race and corrupt each other's
+ *     results.  Serialise them.
+ *   - Nothing in the array needs to start at zero: each call writes every
+ *     element it later reads. */
+gh_status gh_rhs_noalloc(gh_domain* dom, const double* u, double* dudt);
+
 /* Block until the domain's stream is idle; returns the first latched device
  * error (GH_ENONFINITE) or GH_ECUDA, then clears the latch. */
 gh_status gh_sync(gh_domain* dom);

@@ -108,6 +108,9 @@ namespace gh {
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter);
 cudaError_t launch_angular_deriv(gh_domain* d, const double* in);
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
+cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph);
+cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const double* dr, const double* dth,
+                                      const double* dph, double* k);
 cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage, double dt,
                              const double* u0, double* acc, double* ustage, bool constraints);
 cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const double* u0,

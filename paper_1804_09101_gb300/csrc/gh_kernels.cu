@@ -747,6 +747,27 @@ cudaError_t launch_angular_deriv(gh_domain* d, const double* in) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph) {
+  gemm_batched_kernel<<<d->ang_deriv_tiles, GEMM_THREADS, 0, d->stream>>>(
+      d->ang_deriv_d, d->ang_deriv_np, in, dth, dph);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const double* dr, const double* dth,
+                                      const double* dph, double* k) {
+  PointwiseArgs a;
+  a.shells = d->shells_d; a.n_shells = d->n_shells; a.begin = d->pt_block_begin_d;
+  a.u = u; a.dr = dr; a.dth = dth; a.dph = dph;
+  a.k = k; a.u0 = nullptr; a.acc = nullptr; a.us = nullptr;
+  a.partial = nullptr; a.c_out = nullptr;
+  a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
+  a.dt = 0.0; a.stage = 0;
+  pointwise_kernel<true, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  d->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out) {
   gemm_batched_kernel<<<d->ang_filt_tiles, GEMM_THREADS, 0, d->stream>>>(
       d->ang_filt_d, d->ang_filt_np, in, out, out);

@@ -61,6 +61,7 @@ def _load():
         "gh_add_perturbation": ([P, I, D, D, D, I, P, P], I),
         "gh_derivatives": ([P, P, P], I),
         "gh_rhs": ([P, P, P], I),
+        "gh_rhs_noalloc": ([P, P, P], I),
         "gh_rk4_step": ([P, D, P, P, P], I),
         "gh_apply_filters": ([P, P, P], I),
         "gh_constraints": ([P, P, P, P], I),
@@ -183,6 +184,12 @@ def gh_derivatives(dom, u, du):
 def gh_rhs(dom, u, dudt):
     dom._stream()
     dom._check(_lib.gh_rhs(dom.handle, _ptr(u, "u", dom.state_size), _ptr(dudt, "dudt", dom.state_size)))
+
+
+def gh_rhs_noalloc(dom, u, dudt):
+    """gh_rhs with the library's fixed work area: no device allocation at call time."""
+    dom._stream()
+    dom._check(_lib.gh_rhs_noalloc(dom.handle, _ptr(u, "u", dom.state_size), _ptr(dudt, "dudt", dom.state_size)))
 
 
 def gh_rk4_step(dom, dt, u, work, norm2_pre=None):
