@@ -77,3 +77,45 @@ def radial_flops(shells):
         na = (L + 1) * 2 * (L + 1)
         f += 2 * 50 * na * n_r * n_r
     return f
+
+
+def _shell_dims(shell):
+    _, _, n_r, L = shell
+    nth, nph = L + 1, 2 * (L + 1)
+    return n_r, nth, nph, nth * nph
+
+
+def sep_angular_flops(shells, K=None, two=True):
+    """FP64 flops of one separable angular launch (sep_angular_kernel):
+    per (r, field) row, 2 nth nph M (phi DFT) + n_out 2 nth^2 M (Legendre maps)
+    + n_out 2 na M (inverse DFT), M = 2K + 1, n_out = 2 (derivatives) or 1 (filter)."""
+    f = 0
+    n_out = 2 if two else 1
+    for sh in shells:
+        n_r, nth, nph, na = _shell_dims(sh)
+        k = sh[3] if K is None else K
+        M = 2 * k + 1
+        f += 50 * n_r * (2 * nth * nph * M + n_out * 2 * nth * nth * M + n_out * 2 * na * M)
+    return f
+
+
+# FP64 flops per point executed by the fused pointwise kernel (DiffJac + GH
+# right-hand side + RK4 stage combine), from ncu's executed-instruction
+# counters (dadd + dmul + 2 dfma) on the 4-shell Kerr workload.
+POINTWISE_FLOPS_PER_POINT = 4934
+POINTWISE_CONSTRAINT_EXTRA_FLOPS_PER_POINT = 409
+
+
+def family_flops(family, shells, algorithm="separable", keep_l=-1):
+    """Algorithmic FP64 flops of one launch of a kernel family."""
+    pts = sum(n_r * 2 * (L + 1) ** 2 for (_, _, n_r, L) in shells)
+    if family == "angular":
+        return sep_angular_flops(shells) if algorithm == "separable" else angular_deriv_flops(shells)
+    if family == "angular_filter":
+        return (sep_angular_flops(shells, K=keep_l, two=False) if algorithm == "separable"
+                else angular_filter_flops(shells))
+    if family in ("radial", "radial_filter"):
+        return radial_flops(shells)
+    if family == "pointwise":
+        return POINTWISE_FLOPS_PER_POINT * pts
+    return None

@@ -2,6 +2,7 @@
 // dictionary, Sec. 3.4), domain setup and the C ABI entry points of gh.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -220,6 +221,71 @@ std::vector<double> angular_matrix(const AngularGrid& g, int kind, int keep) {
   return B;
 }
 
+// Separable plan (see sep_angular_kernel): modes cos m = 0..K then sin m = 1..K.
+//   F[k][mode]          forward DFT
+//   G0[mode][k]         c_m (2 pi / N_phi) x (cos m phi_k | sin m phi_k)
+//   G1[mode][k]         the phi derivative of G0 (derivative plan only)
+//   Q0[m][j_in][j_out]  sum_{l=m..K} A_lm(j_out) Pbar_lm(j_in) w_GL(j_in),
+//                       A = dPbar/dtheta (derivative plan) or Pbar (filter)
+//   Q1[m][j_in][j_out]  the same with A = Pbar (derivative plan only)
+struct SepHost {
+  int K, M;
+  std::vector<double> F, G0, G1, Q0, Q1;
+};
+
+SepHost sep_plan(const AngularGrid& g, int K, bool deriv) {
+  SepHost h;
+  h.K = K;
+  h.M = 2 * K + 1;
+  const int M = h.M, nph = g.nph, nth = g.nth, W = g.L + 1;
+  std::vector<double> P, dP;
+  legendre_tables(g.L, g.ct, g.st, P, dP);
+  h.F.assign((size_t)nph * M, 0.0);
+  h.G0.assign((size_t)M * nph, 0.0);
+  if (deriv) h.G1.assign((size_t)M * nph, 0.0);
+  const double wphi = 2.0 * kPi / nph;
+  for (int mode = 0; mode < M; ++mode) {
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    const double c = (m == 0) ? 1.0 : 2.0;
+    for (int k = 0; k < nph; ++k) {
+      const double ang = 2.0 * kPi * (double)m * k / nph;
+      const double cs = std::cos(ang), sn = std::sin(ang);
+      h.F[(size_t)k * M + mode] = cosm ? cs : sn;
+      h.G0[(size_t)mode * nph + k] = c * wphi * (cosm ? cs : sn);
+      if (deriv) h.G1[(size_t)mode * nph + k] = c * wphi * m * (cosm ? -sn : cs);
+    }
+  }
+  h.Q0.assign((size_t)(K + 1) * nth * nth, 0.0);
+  if (deriv) h.Q1.assign((size_t)(K + 1) * nth * nth, 0.0);
+  for (int m = 0; m <= K; ++m)
+    for (int ji = 0; ji < nth; ++ji)
+      for (int jo = 0; jo < nth; ++jo) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int l = m; l <= K; ++l) {
+          const double pin = P[((size_t)l * W + m) * nth + ji];
+          const double po = P[((size_t)l * W + m) * nth + jo];
+          const double dpo = dP[((size_t)l * W + m) * nth + jo];
+          a0 += (deriv ? dpo : po) * pin;
+          a1 += po * pin;
+        }
+        h.Q0[((size_t)m * nth + ji) * nth + jo] = a0 * g.wgl[ji];
+        if (deriv) h.Q1[((size_t)m * nth + ji) * nth + jo] = a1 * g.wgl[ji];
+      }
+  return h;
+}
+
+// Rows of one shell that a separable block holds in shared memory.
+int sep_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
+  const size_t per_row = (size_t)na + (two ? 3 : 2) * (size_t)nth * M;
+  const size_t budget = 64 * 1024 / sizeof(double);
+  int rb = (int)(budget / per_row);
+  if (rb < 1) rb = 1;
+  if (rb > 64) rb = 64;
+  if (rb > n_rows) rb = n_rows;
+  return rb;
+}
+
 // ------------------------------------------------------------ helpers
 gh_status fail(gh_domain* d, gh_status s, const std::string& msg) {
   if (d) d->err = msg;
@@ -332,6 +398,74 @@ gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
 
 }  // namespace
 
+// Dense traced matrices (the paper's Eq. DifferentiatorI1S2 maps) and their
+// batched GEMM plans, built on first use.
+gh_status build_dense(gh_domain* d) {
+  if (d->ang_deriv_d) return GH_OK;
+  std::map<int, std::pair<double*, double*>> ang_cache;   // L -> (Bth, Bph)
+  std::map<int, double*> filt_cache;                      // L -> S
+  std::vector<gh::GemmProb> pd, pf;
+  int tiles = 0, ftiles = 0;
+  for (int s = 0; s < d->n_shells; ++s) {
+    gh::ShellDev& sh = d->shells_h[s];
+    AngularGrid ag = angular_grid(sh.L);
+    if (!ang_cache.count(sh.L)) {
+      double *Bt = nullptr, *Bp = nullptr;
+      GH_CUDA(d, upload(d, angular_matrix(ag, 0, 0), &Bt));
+      GH_CUDA(d, upload(d, angular_matrix(ag, 1, 0), &Bp));
+      ang_cache[sh.L] = {Bt, Bp};
+    }
+    sh.Bth = ang_cache[sh.L].first;
+    sh.Bph = ang_cache[sh.L].second;
+    if (d->params.sh_keep_l >= 0) {
+      if (!filt_cache.count(sh.L)) {
+        double* Sd = nullptr;
+        GH_CUDA(d, upload(d, angular_matrix(ag, 2, d->params.sh_keep_l), &Sd));
+        filt_cache[sh.L] = Sd;
+      }
+      sh.Sf = filt_cache[sh.L];
+    }
+    for (int c = 0; c < 2; ++c) {
+      gh::GemmProb P;
+      std::memset(&P, 0, sizeof(P));
+      P.a_off = sh.off;
+      P.c_off = sh.off;
+      P.B = c == 0 ? sh.Bth : sh.Bph;
+      P.M = sh.n_r * gh::NF;
+      P.N = sh.na;
+      P.K = sh.na;
+      P.lda = P.ldb = P.ldc = sh.na;
+      P.tiles_n = (P.N + 63) / 64;
+      P.tile_begin = tiles;
+      P.c_sel = c;
+      tiles += ((P.M + 63) / 64) * P.tiles_n;
+      pd.push_back(P);
+    }
+    if (sh.Sf) {
+      gh::GemmProb P;
+      std::memset(&P, 0, sizeof(P));
+      P.a_off = sh.off;
+      P.c_off = sh.off;
+      P.B = sh.Sf;
+      P.M = sh.n_r * gh::NF;
+      P.N = sh.na;
+      P.K = sh.na;
+      P.lda = P.ldb = P.ldc = sh.na;
+      P.tiles_n = (P.N + 63) / 64;
+      P.tile_begin = ftiles;
+      ftiles += ((P.M + 63) / 64) * P.tiles_n;
+      pf.push_back(P);
+    }
+  }
+  d->ang_filt_np = (int)pf.size();
+  d->ang_filt_tiles = ftiles;
+  if (!pf.empty()) GH_CUDA(d, upload(d, pf, &d->ang_filt_d));
+  d->ang_deriv_np = (int)pd.size();
+  d->ang_deriv_tiles = tiles;
+  GH_CUDA(d, upload(d, pd, &d->ang_deriv_d));
+  return GH_OK;
+}
+
 // =================================================================== C ABI
 extern "C" {
 
@@ -376,8 +510,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
 
   // matrix dictionary keyed by the parameters that make a map new (Sec. 3.4)
   std::map<int, std::pair<double*, double*>> radial_cache;              // n_r -> (D, F)
-  std::map<int, std::pair<double*, double*>> ang_cache;                 // L -> (Bth, Bph)
-  std::map<std::pair<int, int>, double*> filt_cache;                    // (L, keep) -> S
+  std::map<std::tuple<int, int, int>, gh::SepPlan> sep_cache;           // (L, K, kind) -> plan
   std::map<int, AngularGrid> grids;
 
   long long off = 0, pts = 0;
@@ -408,22 +541,34 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     sh.Fr = radial_cache[sh.n_r].second;
     if (!grids.count(sh.L)) grids[sh.L] = angular_grid(sh.L);
     const AngularGrid& ag = grids[sh.L];
-    if (!ang_cache.count(sh.L)) {
-      double *Bt = nullptr, *Bp = nullptr;
-      CREATE_CUDA(upload(d, angular_matrix(ag, 0, 0), &Bt));
-      CREATE_CUDA(upload(d, angular_matrix(ag, 1, 0), &Bp));
-      ang_cache[sh.L] = {Bt, Bp};
-    }
-    sh.Bth = ang_cache[sh.L].first;
-    sh.Bph = ang_cache[sh.L].second;
-    if (params->sh_keep_l >= 0) {
-      auto key = std::make_pair(sh.L, params->sh_keep_l);
-      if (!filt_cache.count(key)) {
-        double* Sd = nullptr;
-        CREATE_CUDA(upload(d, angular_matrix(ag, 2, params->sh_keep_l), &Sd));
-        filt_cache[key] = Sd;
+    // separable angular plans, cached by (L, K, kind)
+    auto get_plan = [&](int K, bool deriv, gh::SepPlan& out) -> cudaError_t {
+      auto key = std::make_tuple(sh.L, K, deriv ? 1 : 0);
+      if (!sep_cache.count(key)) {
+        SepHost h = sep_plan(ag, K, deriv);
+        gh::SepPlan P;
+        std::memset(&P, 0, sizeof(P));
+        P.K = h.K;
+        P.M = h.M;
+        double* q = nullptr;
+        cudaError_t e;
+        if ((e = upload(d, h.F, &q)) != cudaSuccess) return e; P.F = q;
+        if ((e = upload(d, h.G0, &q)) != cudaSuccess) return e; P.G0 = q;
+        if ((e = upload(d, h.Q0, &q)) != cudaSuccess) return e; P.Q0 = q;
+        if (deriv) {
+          if ((e = upload(d, h.G1, &q)) != cudaSuccess) return e; P.G1 = q;
+          if ((e = upload(d, h.Q1, &q)) != cudaSuccess) return e; P.Q1 = q;
+        }
+        sep_cache[key] = P;
       }
-      sh.Sf = filt_cache[key];
+      out = sep_cache[key];
+      return cudaSuccess;
+    };
+    CREATE_CUDA(get_plan(sh.L, true, sh.sd));
+    sh.sd.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sd.M, true, gh::NF * sh.n_r);
+    if (params->sh_keep_l >= 0) {
+      CREATE_CUDA(get_plan(params->sh_keep_l, false, sh.sf));
+      sh.sf.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sf.M, false, gh::NF * sh.n_r);
     }
     // grid tables
     std::vector<double> x = cgl_points(sh.n_r), wcc = clenshaw_curtis(sh.n_r);
@@ -517,7 +662,8 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     const gh::ShellDev& sh = d->shells_h[s];
     rb[s] = nrb;
     pb[s] = npb;
-    nrb += (int)((gh::NF * (long long)sh.na + 255) / 256);
+    nrb += (int)((gh::NF * (long long)sh.na + 127) / 128);
+    d->max_n_r = std::max(d->max_n_r, sh.n_r);
     npb += sh.n_r * ((sh.na + 127) / 128);
   }
   rb[n_shells] = nrb;
@@ -527,50 +673,34 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   CREATE_CUDA(upload(d, rb, &d->rad_block_begin_d));
   CREATE_CUDA(upload(d, pb, &d->pt_block_begin_d));
 
-  // batched angular GEMM plans: two problems (theta, phi) per shell; one
-  // filter problem per shell.
-  std::vector<gh::GemmProb> pd, pf;
-  int tiles = 0, ftiles = 0;
-  for (int s = 0; s < n_shells; ++s) {
-    const gh::ShellDev& sh = d->shells_h[s];
-    for (int c = 0; c < 2; ++c) {
-      gh::GemmProb P;
-      std::memset(&P, 0, sizeof(P));
-      P.a_off = sh.off;
-      P.c_off = sh.off;
-      P.B = c == 0 ? sh.Bth : sh.Bph;
-      P.M = sh.n_r * gh::NF;
-      P.N = sh.na;
-      P.K = sh.na;
-      P.lda = P.ldb = P.ldc = sh.na;
-      P.tiles_n = (P.N + 63) / 64;
-      P.tile_begin = tiles;
-      P.c_sel = c;
-      tiles += ((P.M + 63) / 64) * P.tiles_n;
-      pd.push_back(P);
+  // separable angular launch maps (blocks of RB rows per shell)
+  {
+    std::vector<int> sb(n_shells + 1), fb(n_shells + 1);
+    int nsb = 0, nfb = 0;
+    size_t smd = 0, smf = 0;
+    for (int s = 0; s < n_shells; ++s) {
+      const gh::ShellDev& sh = d->shells_h[s];
+      const int rows = gh::NF * sh.n_r;
+      sb[s] = nsb;
+      nsb += (rows + sh.sd.rows_per_cta - 1) / sh.sd.rows_per_cta;
+      smd = std::max(smd, sizeof(double) * (size_t)sh.sd.rows_per_cta * (sh.na + 3 * (size_t)sh.nth * sh.sd.M));
+      fb[s] = nfb;
+      if (sh.sf.M > 0) {
+        nfb += (rows + sh.sf.rows_per_cta - 1) / sh.sf.rows_per_cta;
+        smf = std::max(smf, sizeof(double) * (size_t)sh.sf.rows_per_cta * (sh.na + 2 * (size_t)sh.nth * sh.sf.M));
+      }
     }
-    if (sh.Sf) {
-      gh::GemmProb P;
-      std::memset(&P, 0, sizeof(P));
-      P.a_off = sh.off;
-      P.c_off = sh.off;
-      P.B = sh.Sf;
-      P.M = sh.n_r * gh::NF;
-      P.N = sh.na;
-      P.K = sh.na;
-      P.lda = P.ldb = P.ldc = sh.na;
-      P.tiles_n = (P.N + 63) / 64;
-      P.tile_begin = ftiles;
-      ftiles += ((P.M + 63) / 64) * P.tiles_n;
-      pf.push_back(P);
-    }
+    sb[n_shells] = nsb;
+    fb[n_shells] = nfb;
+    d->sd_blocks = nsb;
+    d->sf_blocks = nfb;
+    d->sd_smem = smd;
+    d->sf_smem = smf;
+    CREATE_CUDA(upload(d, sb, &d->sd_block_begin_d));
+    CREATE_CUDA(upload(d, fb, &d->sf_block_begin_d));
+    CREATE_CUDA(gh::sep_set_smem_limits(std::max(smd, smf)));
+    CREATE_CUDA(gh::radial_set_smem_limits());
   }
-  d->ang_deriv_np = (int)pd.size();
-  d->ang_deriv_tiles = tiles;
-  CREATE_CUDA(upload(d, pd, &d->ang_deriv_d));
-  d->ang_filt_np = (int)pf.size();
-  d->ang_filt_tiles = ftiles;
-  if (!pf.empty()) CREATE_CUDA(upload(d, pf, &d->ang_filt_d));
 
   // scratch
   void* p = nullptr;
@@ -745,6 +875,17 @@ gh_status gh_constraints(gh_domain* d, const double* u, double* c_out, double* n
   if (gh_status s = derivatives(d, u)) return s;
   GH_CUDA(d, gh::launch_constraints(d, u, c_out));
   GH_CUDA(d, gh::launch_norm_reduce(d, norm2));
+  return GH_OK;
+}
+
+gh_status gh_set_algorithm(gh_domain* d, int algorithm) {
+  if (!d || (algorithm != GH_ALG_DENSE && algorithm != GH_ALG_SEPARABLE))
+    return fail(d, GH_EINVAL, "algorithm must be GH_ALG_DENSE or GH_ALG_SEPARABLE");
+  if (algorithm == GH_ALG_DENSE) {
+    GH_CUDA(d, cudaStreamSynchronize(d->stream));
+    if (gh_status st = build_dense(d)) return st;
+  }
+  d->algorithm = algorithm;
   return GH_OK;
 }
 

@@ -15,6 +15,19 @@ constexpr int NC = 64;      // stored constraint components per point
 constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
 constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
 
+// Separable spherical-harmonic map of one shell (Y_lm = Pbar_lm(theta) x
+// Fourier(phi)): phi-DFT, one N_theta x N_theta Legendre map per Fourier mode,
+// inverse DFT.  Modes: cos m = 0..K, then sin m = 1..K (M = 2K + 1).
+struct SepPlan {
+  int K, M;                     // highest m kept, number of Fourier modes
+  int rows_per_cta, pad;
+  const double* F;              // [nph][M]  forward DFT  cos(m phi_k) / sin(m phi_k)
+  const double* G0;             // [M][nph]  synthesis of output 0
+  const double* G1;             // [M][nph]  synthesis of output 1 (derivative plan: d/dphi)
+  const double* Q0;             // [K+1][nth_in][nth_out] Legendre map for output 0
+  const double* Q1;             // [K+1][nth_in][nth_out] Legendre map for output 1
+};
+
 // One shell as the kernels see it (device-resident array of these).
 struct ShellDev {
   int n_r, L, nth, nph, na;     // na = nth * nph angular points
@@ -37,6 +50,8 @@ struct ShellDev {
   double* gauge;                // [n_r][16][na]
   int bc_inner;                 // boundary slice index at r_in, -1 if none (excision)
   int bc_outer;                 // boundary slice index at r_out
+  SepPlan sd;                   // separable d/dtheta, d/dphi
+  SepPlan sf;                   // separable SH truncation filter (M = 0 if off)
 };
 
 // A boundary slice: the outer boundary of the last shell (kind 0) or an
@@ -82,8 +97,12 @@ struct gh_domain {
   gh::GemmProb* ang_deriv_d = nullptr; int ang_deriv_np = 0, ang_deriv_tiles = 0;
   gh::GemmProb* ang_filt_d = nullptr;  int ang_filt_np = 0, ang_filt_tiles = 0;
   // radial / pointwise launch maps: first block of each shell
-  int* rad_block_begin_d = nullptr; int rad_blocks = 0;
+  int* rad_block_begin_d = nullptr; int rad_blocks = 0; int max_n_r = 0;
   int* pt_block_begin_d = nullptr;  int pt_blocks = 0;
+  // separable angular maps: first block of each shell, dynamic shared memory
+  int algorithm = 1;            // 0 dense traced matrices, 1 separable
+  int* sd_block_begin_d = nullptr; int sd_blocks = 0; size_t sd_smem = 0;
+  int* sf_block_begin_d = nullptr; int sf_blocks = 0; size_t sf_smem = 0;
   // scratch owned by the domain
   double* d_r = nullptr;         // radial derivative  (one state)
   double* d_th = nullptr;        // theta derivative   (one state)
@@ -109,6 +128,8 @@ cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filt
 cudaError_t launch_angular_deriv(gh_domain* d, const double* in);
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph);
+cudaError_t sep_set_smem_limits(size_t bytes);
+cudaError_t radial_set_smem_limits();
 cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const double* dr, const double* dth,
                                       const double* dph, double* k);
 cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage, double dt,

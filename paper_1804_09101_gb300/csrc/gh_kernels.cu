@@ -27,9 +27,10 @@ __device__ __forceinline__ int find_segment(const int* begin, int n, int b) {
 // ---------------------------------------------------------------------------
 // Radial contraction (the R part of Eq. DifferentiatorI1S2, and the radial
 // ExpCheb filter): out[r][col] = sum_r' M[r][r'] in[r'][col] for every column
-// col = (field, theta, phi) of every shell.  One thread per column; the
-// column lives in registers, the n_r x n_r matrix in shared memory.
-constexpr int RAD_THREADS = 256;
+// col = (field, theta, phi) of every shell.  One thread per column; the block's
+// columns are staged in shared memory (coalesced loads along col), the
+// n_r x n_r matrix sits in shared memory too, and every FMA does useful work.
+constexpr int RAD_THREADS = 128;
 constexpr int MAXR = 64;
 
 template <bool FILTER>
@@ -37,28 +38,44 @@ __global__ void __launch_bounds__(RAD_THREADS)
 radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
               const double* __restrict__ in, double* __restrict__ out) {
   __shared__ double Ms[MAXR * MAXR];
+  extern __shared__ double Vs[];           // [n_r][RAD_THREADS]
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int n = sh.n_r;
   const double* M = FILTER ? sh.Fr : sh.Dr;
   for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ms[i] = M[i];
-  __syncthreads();
   const long long cols = (long long)NF * sh.na;
   const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
-  if (col >= cols) return;
+  const bool valid = col < cols;
   const double* src = in + sh.off + col;
+  for (int r = 0; r < n; ++r) Vs[r * RAD_THREADS + threadIdx.x] = valid ? src[(long long)r * cols] : 0.0;
+  __syncthreads();
+  if (!valid) return;
   double* dst = out + sh.off + col;
-  double v[MAXR];
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r)
-    if (r < n) v[r] = src[(long long)r * cols];
-  for (int r = 0; r < n; ++r) {
-    double acc = 0.0;
-#pragma unroll
-    for (int q = 0; q < MAXR; ++q)
-      if (q < n) acc = fma(Ms[r * n + q], v[q], acc);
-    dst[(long long)r * cols] = acc;
+  const double* v = Vs + threadIdx.x;
+  int r = 0;
+  for (; r + 1 < n; r += 2) {              // two outputs per pass: two independent FMA chains
+    double a0 = 0.0, a1 = 0.0;
+    for (int q = 0; q < n; ++q) {
+      const double x = v[q * RAD_THREADS];
+      a0 = fma(Ms[r * n + q], x, a0);
+      a1 = fma(Ms[(r + 1) * n + q], x, a1);
+    }
+    dst[(long long)r * cols] = a0;
+    dst[(long long)(r + 1) * cols] = a1;
   }
+  if (r < n) {
+    double a0 = 0.0;
+    for (int q = 0; q < n; ++q) a0 = fma(Ms[r * n + q], v[q * RAD_THREADS], a0);
+    dst[(long long)r * cols] = a0;
+  }
+}
+
+cudaError_t radial_set_smem_limits() {
+  const int bytes = (int)(sizeof(double) * MAXR * RAD_THREADS);
+  cudaError_t e = cudaFuncSetAttribute(radial_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(radial_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -155,6 +172,108 @@ gemm_batched_kernel(const GemmProb* __restrict__ probs, int nprob, const double*
       if (gn < P.N) C[(long long)gm * P.ldc + gn] = acc[i][j];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Separable angular maps.  A row is one (r, field) pair: N_theta x N_phi
+// values.  The projection onto Y_lm, l <= K, factorises into
+//   A[j][mode]  = sum_k u[j][k] F[k][mode]                      (phi DFT)
+//   B[j][mode]  = sum_j' Q_m[j'][j] A[j'][mode]                  (Legendre map of mode m)
+//   out[j][k]   = sum_mode B[j][mode] G[mode][k]                 (inverse DFT)
+// where Q_m folds the Gauss-Legendre analysis of the Pbar_lm (l = m..K) with
+// their synthesis (values, or theta derivatives), and G folds the Fourier
+// normalisation (and the phi derivative).  Per value this costs about
+// 2 M (N_phi + N_theta + N_phi) flops instead of the 2 N_theta N_phi of a
+// dense traced matrix (Eq. DifferentiatorI1S2).  A block loads RB rows into
+// shared memory and runs the three phases there.  TWO = true: two outputs
+// (d/dtheta and d/dphi) sharing phase A; false: one output (the SH filter).
+constexpr int SEP_THREADS = 256;
+
+template <bool TWO>
+__global__ void __launch_bounds__(SEP_THREADS)
+sep_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                   const double* __restrict__ in, double* __restrict__ out0, double* __restrict__ out1) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const SepPlan& P = TWO ? sh.sd : sh.sf;
+  const int nth = sh.nth, nph = sh.nph, na = sh.na, M = P.M, K = P.K;
+  const int rows = NF * sh.n_r;
+  const int RB = P.rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  double* U = sm;                          // [RB][na]
+  double* A = U + (size_t)RB * na;         // [RB][nth][M]
+  double* B0 = A + (size_t)RB * nth * M;   // [RB][nth][M]
+  double* B1 = B0 + (size_t)RB * nth * M;  // [RB][nth][M] (TWO only)
+  const double* src = in + sh.off + (long long)row0 * na;
+  for (int i = threadIdx.x; i < nr * na; i += SEP_THREADS) U[i] = src[i];
+  __syncthreads();
+  // phase A: phi DFT of every theta ring
+  const double* __restrict__ F = P.F;
+  for (int o = threadIdx.x; o < nr * nth * M; o += SEP_THREADS) {
+    const int mode = o % M;
+    const double* ring = U + (o / M) * nph;
+    double acc = 0.0;
+    for (int k = 0; k < nph; ++k) acc = fma(ring[k], __ldg(F + k * M + mode), acc);
+    A[o] = acc;
+  }
+  __syncthreads();
+  // phase B: Legendre map of each Fourier mode (threads along theta_out)
+  const double* __restrict__ Q0 = P.Q0;
+  const double* __restrict__ Q1 = P.Q1;
+  for (int o = threadIdx.x; o < nr * nth * M; o += SEP_THREADS) {
+    const int j = o % nth;
+    const int t = o / nth;
+    const int mode = t % M;
+    const int rr = t / M;
+    const int m = mode <= K ? mode : mode - K;
+    const double* a = A + (size_t)rr * nth * M + mode;
+    const double* q0 = Q0 + (size_t)m * nth * nth + j;
+    double acc0 = 0.0, acc1 = 0.0;
+    if (TWO) {
+      const double* q1 = Q1 + (size_t)m * nth * nth + j;
+      for (int jp = 0; jp < nth; ++jp) {
+        const double av = a[jp * M];
+        acc0 = fma(__ldg(q0 + jp * nth), av, acc0);
+        acc1 = fma(__ldg(q1 + jp * nth), av, acc1);
+      }
+      B1[((size_t)rr * nth + j) * M + mode] = acc1;
+    } else {
+      for (int jp = 0; jp < nth; ++jp) acc0 = fma(__ldg(q0 + jp * nth), a[jp * M], acc0);
+    }
+    B0[((size_t)rr * nth + j) * M + mode] = acc0;
+  }
+  __syncthreads();
+  // phase C: inverse DFT into the output rows
+  const double* __restrict__ G0 = P.G0;
+  const double* __restrict__ G1 = P.G1;
+  double* dst0 = out0 + sh.off + (long long)row0 * na;
+  double* dst1 = TWO ? out1 + sh.off + (long long)row0 * na : nullptr;
+  for (int o = threadIdx.x; o < nr * na; o += SEP_THREADS) {
+    const int k = o % nph;
+    const int rj = o / nph;
+    const double* b0 = B0 + (size_t)rj * M;
+    double acc0 = 0.0;
+    if (TWO) {
+      const double* b1 = B1 + (size_t)rj * M;
+      double acc1 = 0.0;
+      for (int mode = 0; mode < M; ++mode) {
+        acc0 = fma(b0[mode], __ldg(G0 + mode * nph + k), acc0);
+        acc1 = fma(b1[mode], __ldg(G1 + mode * nph + k), acc1);
+      }
+      dst1[o] = acc1;
+    } else {
+      for (int mode = 0; mode < M; ++mode) acc0 = fma(b0[mode], __ldg(G0 + mode * nph + k), acc0);
+    }
+    dst0[o] = acc0;
+  }
+}
+
+cudaError_t sep_set_smem_limits(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(sep_angular_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sep_angular_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,41 +647,6 @@ pointwise_kernel(PointwiseArgs a) {
 // Internal boundary: v < 0 families take the outer shell's value on both
 // sides, v > 0 families the inner shell's, v = 0 families keep their own.
 // After the condition the RK4 stage combine of those points is done here.
-struct CharVec {
-  double psi[10], wp[10], wm[10], w0[30];
-};
-
-__device__ __forceinline__ void char_project(const double* k, long long base, int na,
-                                             const double n_dn[3], const double n_up[3],
-                                             double g2, CharVec& c) {
-#pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    const double ps = k[base + (long long)p * na];
-    const double pi = k[base + (long long)(10 + p) * na];
-    double ph[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ph[i] = k[base + (long long)(20 + 10 * i + p) * na];
-    const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
-    c.psi[p] = ps;
-    c.wp[p] = pi + nphi - g2 * ps;
-    c.wm[p] = pi - nphi - g2 * ps;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) c.w0[i * 10 + p] = ph[i] - n_dn[i] * nphi;
-  }
-}
-
-__device__ __forceinline__ void char_recombine(const CharVec& c, const double n_dn[3], double g2,
-                                               double out[NF]) {
-#pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    out[p] = c.psi[p];
-    out[10 + p] = 0.5 * (c.wp[p] + c.wm[p]) + g2 * c.psi[p];
-    const double h = 0.5 * (c.wp[p] - c.wm[p]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) out[20 + 10 * i + p] = n_dn[i] * h + c.w0[i * 10 + p];
-  }
-}
-
 struct BcArgs {
   const BcSliceDev* slices;
   int n_slices;
@@ -575,30 +659,61 @@ struct BcArgs {
   int stage;
 };
 
-__device__ __forceinline__ void bc_write(const BcArgs& a, long long base, int na, const double v[NF]) {
-#pragma unroll 5
-  for (int f = 0; f < NF; ++f) {
-    const long long idx = base + (long long)f * na;
-    if (a.stage == 0) a.k[idx] = v[f];
-    else stage_combine(a.stage, a.dt, v[f], idx, a.u0, a.acc, a.us);
+// The characteristic projection couples only the 5 fields of one symmetric
+// pair p (psi_p, Pi_p, Phi_xp, Phi_yp, Phi_zp), so each thread handles one
+// (boundary point, pair): char fields w_psi, w_plus, w_minus, w0_i.
+struct CharPair {
+  double psi, wp, wm, w0[3];
+};
+
+__device__ __forceinline__ void char_project_pair(const double* k, long long base, int na, int p,
+                                                  const double n_dn[3], const double n_up[3], double g2,
+                                                  CharPair& c) {
+  const double ps = k[base + (long long)p * na];
+  const double pi = k[base + (long long)(10 + p) * na];
+  double ph[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ph[i] = k[base + (long long)(20 + 10 * i + p) * na];
+  const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
+  c.psi = ps;
+  c.wp = pi + nphi - g2 * ps;
+  c.wm = pi - nphi - g2 * ps;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) c.w0[i] = ph[i] - n_dn[i] * nphi;
+}
+
+__device__ __forceinline__ void char_write_pair(const BcArgs& a, long long base, int na, int p, const CharPair& c,
+                                                const double n_dn[3], double g2) {
+  double v[5];
+  v[0] = c.psi;
+  v[1] = 0.5 * (c.wp + c.wm) + g2 * c.psi;
+  const double h = 0.5 * (c.wp - c.wm);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[2 + i] = n_dn[i] * h + c.w0[i];
+  const int f[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
+#pragma unroll
+  for (int e = 0; e < 5; ++e) {
+    const long long idx = base + (long long)f[e] * na;
+    if (a.stage == 0) a.k[idx] = v[e];
+    else stage_combine(a.stage, a.dt, v[e], idx, a.u0, a.acc, a.us);
   }
 }
 
-__device__ __forceinline__ void select_family(double* wi, double* wo, int n, double v) {
+__device__ __forceinline__ void select_pair(double& wi, double& wo, double v) {
   // v < 0: both take the outer side's value; v > 0: both take the inner side's.
-  if (v < 0.0) {
-    for (int e = 0; e < n; ++e) wi[e] = wo[e];
-  } else if (v > 0.0) {
-    for (int e = 0; e < n; ++e) wo[e] = wi[e];
-  }
+  if (v < 0.0) wi = wo;
+  else if (v > 0.0) wo = wi;
 }
 
 __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
+  const int npts = a.pt_begin[a.n_slices];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.pt_begin[a.n_slices]) return;
-  const int s = find_segment(a.pt_begin, a.n_slices, t);
+  if (t >= 10 * npts) return;
+  const int p = t / npts;
+  const int pt = t - p * npts;
+  const int s = find_segment(a.pt_begin, a.n_slices, pt);
   const BcSliceDev& sl = a.slices[s];
-  const int q = t - a.pt_begin[s];
+  const int q = pt - a.pt_begin[s];
   const int na = sl.na;
   double n_dn[3], n_up[3], beta[3];
 #pragma unroll
@@ -611,30 +726,27 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
   const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
   const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
   const double g2 = a.gamma2;
-  double out[NF];
   if (sl.kind == 0) {
     const long long base = sl.off_a + q;
-    CharVec c;
-    char_project(a.k, base, na, n_dn, n_up, g2, c);
-    if (v_psi < 0.0) for (int e = 0; e < 10; ++e) c.psi[e] = 0.0;
-    if (v_0 < 0.0) for (int e = 0; e < 30; ++e) c.w0[e] = 0.0;
-    if (v_p < 0.0) for (int e = 0; e < 10; ++e) c.wp[e] = 0.0;
-    if (v_m < 0.0) for (int e = 0; e < 10; ++e) c.wm[e] = 0.0;
-    char_recombine(c, n_dn, g2, out);
-    bc_write(a, base, na, out);
+    CharPair c;
+    char_project_pair(a.k, base, na, p, n_dn, n_up, g2, c);
+    if (v_psi < 0.0) c.psi = 0.0;
+    if (v_0 < 0.0) c.w0[0] = c.w0[1] = c.w0[2] = 0.0;
+    if (v_p < 0.0) c.wp = 0.0;
+    if (v_m < 0.0) c.wm = 0.0;
+    char_write_pair(a, base, na, p, c, n_dn, g2);
   } else {
     const long long ba = sl.off_a + q, bb = sl.off_b + q;
-    CharVec ci, co;
-    char_project(a.k, ba, na, n_dn, n_up, g2, ci);
-    char_project(a.k, bb, na, n_dn, n_up, g2, co);
-    select_family(ci.psi, co.psi, 10, v_psi);
-    select_family(ci.w0, co.w0, 30, v_0);
-    select_family(ci.wp, co.wp, 10, v_p);
-    select_family(ci.wm, co.wm, 10, v_m);
-    char_recombine(ci, n_dn, g2, out);
-    bc_write(a, ba, na, out);
-    char_recombine(co, n_dn, g2, out);
-    bc_write(a, bb, na, out);
+    CharPair ci, co;
+    char_project_pair(a.k, ba, na, p, n_dn, n_up, g2, ci);
+    char_project_pair(a.k, bb, na, p, n_dn, n_up, g2, co);
+    select_pair(ci.psi, co.psi, v_psi);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) select_pair(ci.w0[i], co.w0[i], v_0);
+    select_pair(ci.wp, co.wp, v_p);
+    select_pair(ci.wm, co.wm, v_m);
+    char_write_pair(a, ba, na, p, ci, n_dn, g2);
+    char_write_pair(a, bb, na, p, co, n_dn, g2);
   }
 }
 
@@ -730,26 +842,28 @@ __global__ void norm_reduce_kernel(const int* __restrict__ begin, int n_shells,
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter) {
+  const size_t smem = sizeof(double) * (size_t)d->max_n_r * RAD_THREADS;
   if (filter)
-    radial_kernel<true><<<d->rad_blocks, RAD_THREADS, 0, d->stream>>>(d->shells_d, d->n_shells,
-                                                                      d->rad_block_begin_d, in, out);
+    radial_kernel<true><<<d->rad_blocks, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,
+                                                                         d->rad_block_begin_d, in, out);
   else
-    radial_kernel<false><<<d->rad_blocks, RAD_THREADS, 0, d->stream>>>(d->shells_d, d->n_shells,
-                                                                       d->rad_block_begin_d, in, out);
+    radial_kernel<false><<<d->rad_blocks, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,
+                                                                          d->rad_block_begin_d, in, out);
   d->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_angular_deriv(gh_domain* d, const double* in) {
-  gemm_batched_kernel<<<d->ang_deriv_tiles, GEMM_THREADS, 0, d->stream>>>(
-      d->ang_deriv_d, d->ang_deriv_np, in, d->d_th, d->d_ph);
-  d->launches++;
-  return cudaGetLastError();
+  return launch_angular_deriv_into(d, in, d->d_th, d->d_ph);
 }
 
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph) {
-  gemm_batched_kernel<<<d->ang_deriv_tiles, GEMM_THREADS, 0, d->stream>>>(
-      d->ang_deriv_d, d->ang_deriv_np, in, dth, dph);
+  if (d->algorithm == 1)
+    sep_angular_kernel<true><<<d->sd_blocks, SEP_THREADS, d->sd_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->sd_block_begin_d, in, dth, dph);
+  else
+    gemm_batched_kernel<<<d->ang_deriv_tiles, GEMM_THREADS, 0, d->stream>>>(
+        d->ang_deriv_d, d->ang_deriv_np, in, dth, dph);
   d->launches++;
   return cudaGetLastError();
 }
@@ -769,8 +883,12 @@ cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const doubl
 }
 
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out) {
-  gemm_batched_kernel<<<d->ang_filt_tiles, GEMM_THREADS, 0, d->stream>>>(
-      d->ang_filt_d, d->ang_filt_np, in, out, out);
+  if (d->algorithm == 1)
+    sep_angular_kernel<false><<<d->sf_blocks, SEP_THREADS, d->sf_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->sf_block_begin_d, in, out, nullptr);
+  else
+    gemm_batched_kernel<<<d->ang_filt_tiles, GEMM_THREADS, 0, d->stream>>>(
+        d->ang_filt_d, d->ang_filt_np, in, out, out);
   d->launches++;
   return cudaGetLastError();
 }
@@ -819,7 +937,7 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
   a.slices = d->bc_d; a.n_slices = (int)d->bc_h.size(); a.pt_begin = d->bc_pt_begin_d;
   a.k = k; a.u0 = u0; a.acc = acc; a.us = ustage;
   a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2; a.dt = dt; a.stage = stage;
-  bc_kernel<<<cdiv(d->bc_points, 128), 128, 0, d->stream>>>(a);
+  bc_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(a);
   d->launches++;
   return cudaGetLastError();
 }

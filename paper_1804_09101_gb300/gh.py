@@ -66,6 +66,7 @@ def _load():
         "gh_apply_filters": ([P, P, P], I),
         "gh_constraints": ([P, P, P, P], I),
         "gh_sync": ([P], I),
+        "gh_set_algorithm": ([P, I], I),
         "gh_profile_enable": ([P, I], I),
         "gh_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
     }
@@ -223,6 +224,14 @@ def gh_profile_read(dom, family):
     n = ctypes.c_longlong()
     dom._check(_lib.gh_profile_read(dom.handle, int(family), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+GH_ALG_DENSE, GH_ALG_SEPARABLE = 0, 1
+
+
+def gh_set_algorithm(dom, algorithm):
+    dom._stream()
+    dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
 
 
 def gh_sync(dom):

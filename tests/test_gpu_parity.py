@@ -92,10 +92,14 @@ def test_perturbations():
         assert max_rel(to_host(u), ref, np.abs(ref).max()) < REL_TOL
 
 
-def test_cartesian_derivatives(case):
+ALGS = ["separable", "dense"]
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_cartesian_derivatives(case, alg):
     gh = _gh()
     w, odom, u0 = case
-    dom = gpu_domain(w, odom)
+    dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     du = torch.zeros(3 * dom.state_size, dtype=torch.float64, device="cuda")
     gh.gh_derivatives(dom, u, du)
@@ -106,10 +110,11 @@ def test_cartesian_derivatives(case):
     assert max_rel(got, ref3, np.abs(flat(u0)).max()) < REL_TOL
 
 
-def test_rhs(case):
+@pytest.mark.parametrize("alg", ALGS)
+def test_rhs(case, alg):
     gh = _gh()
     w, odom, u0 = case
-    dom = gpu_domain(w, odom)
+    dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     k = dom.new_state()
     gh.gh_rhs(dom, u, k)
@@ -131,25 +136,28 @@ def test_constraints(case):
     assert np.abs(to_host(n2) - np.array(nref)).max() <= 1e-10 * max(max(nref), 1e-30) + 1e-28
 
 
-def test_filters(case):
+@pytest.mark.parametrize("alg", ALGS)
+def test_filters(case, alg):
     gh = _gh()
     w, odom, u0 = case
     if not (w.radial_filter_on or w.sh_keep_l >= 0):
         pytest.skip("workload has no filter")
-    dom = gpu_domain(w, odom)
+    dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     gh.gh_apply_filters(dom, u, dom.new_work())
     ref = flat(evolve.apply_filters(odom, u0))
     assert max_rel(to_host(u), ref, np.abs(flat(u0)).max()) < REL_TOL
 
 
-@pytest.mark.parametrize("name,steps", [("schwarzschild", 20), ("kerr2", 3), ("ragged", 2), ("minimal", 5)])
-def test_rk4_steps(name, steps):
+@pytest.mark.parametrize("name,steps,alg", [("schwarzschild", 20, "separable"), ("kerr2", 3, "separable"),
+                                            ("ragged", 2, "separable"), ("minimal", 5, "separable"),
+                                            ("kerr2", 2, "dense")])
+def test_rk4_steps(name, steps, alg):
     gh = _gh()
     w = CASES[name]()
     odom = oracle_domain(w)
     u0 = oracle_initial_state(w, odom)
-    dom = gpu_domain(w, odom)
+    dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     work = dom.new_work()
     n2 = torch.zeros(len(w.shells), dtype=torch.float64, device="cuda")
@@ -165,17 +173,24 @@ def test_rk4_steps(name, steps):
 
 
 def test_rhs_full_size_four_shell_kerr():
-    """The full 4-shell Kerr workload (N_r = 21, L = 15, 43,008 points), all points."""
+    """The full 4-shell Kerr workload (N_r = 21, L = 15, 43,008 points), all
+    points, both angular algorithms, plus one full RK4 step with filters."""
     gh = _gh()
     w = workloads.kerr_four_shells()
     odom = oracle_domain(w)
     u0 = oracle_initial_state(w, odom)
+    ref = flat(evolve.rhs(odom, u0))
+    for alg in ALGS:
+        dom = gpu_domain(w, odom, alg)
+        u = to_dev(flat(u0))
+        k = dom.new_state()
+        gh.gh_rhs(dom, u, k)
+        assert max_rel(to_host(k), ref, np.abs(flat(u0)).max()) < REL_TOL, alg
     dom = gpu_domain(w, odom)
     u = to_dev(flat(u0))
-    k = dom.new_state()
-    gh.gh_rhs(dom, u, k)
-    ref = flat(evolve.rhs(odom, u0))
-    assert max_rel(to_host(k), ref, np.abs(flat(u0)).max()) < REL_TOL
+    gh.gh_rk4_step(dom, w.dt, u, dom.new_work())
+    ref1 = flat(evolve.rk4_step(odom, u0, w.dt))
+    assert max_rel(to_host(u), ref1, np.abs(flat(u0)).max()) < REL_TOL
 
 
 def test_exact_solution_is_stationary_to_truncation_on_the_gpu():
