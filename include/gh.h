@@ -49,11 +49,16 @@ typedef enum {
   GH_ENOTSUP = 6      /* not supported in this build                           */
 } gh_status;
 
-/* One spherical shell: r in [r_in, r_out], n_r radial points, harmonics l <= L.
- * Requires 0 < r_in < r_out, 3 <= n_r <= 64, 1 <= L <= 47. */
+/* One spherical shell: r in [r_in, r_out], n_r radial points, harmonics l <= L,
+ * belonging to black hole bh (0, 1, ...).  Requires 0 < r_in < r_out,
+ * 3 <= n_r <= 64, 1 <= L <= 47.  The shells of one hole are consecutive in the
+ * array, ordered by radius, and adjacent (r_in of the next == r_out of the
+ * previous) with equal L; holes are independent of one another (the paper's
+ * one-domain-per-process picture, Sec. 4, batched into one set of launches). */
 typedef struct {
   double r_in, r_out;
   int n_r, L;
+  int bh;
 } gh_shell;
 
 /* Evolution parameters.
@@ -61,8 +66,9 @@ typedef struct {
  * filt_alpha, filt_order: exponential Chebyshev filter sigma_k =
  *   exp(-alpha (k/(n_r-1))^order) applied along r when radial_filter_on != 0
  *   (the paper's ExpCheb filter, Sec. 3.4).
- * sh_keep_l: Heaviside filter in l (keep l <= sh_keep_l) on every shell, or -1
- *   for none (the paper's Heaviside filter, Sec. 3.4; applied per component). */
+ * sh_keep_l: Heaviside filter in l (keep l <= sh_keep_l) on every shell, -1 for
+ *   none, or -2 for floor(2L/3) of each shell (the paper's Heaviside filter,
+ *   Sec. 3.4; applied per component). */
 typedef struct {
   double gamma0, gamma1, gamma2;
   double filt_alpha;
@@ -73,8 +79,8 @@ typedef struct {
 
 typedef struct gh_domain gh_domain;
 
-/* Create a domain of n_shells concentric shells ordered by radius; shell s+1
- * must start where shell s ends (r_in[s+1] == r_out[s]).  Builds the cached
+/* Create a domain of n_shells shells around one or more independent holes
+ * (see gh_shell for the ordering rules).  Builds the cached
  * operator matrices on the host in FP64 (the paper's matrix dictionary,
  * Sec. 3.4) and uploads them together with grid tables; allocates the
  * library's own scratch (three derivative buffers of one state each plus
@@ -98,13 +104,19 @@ long long gh_num_points(const gh_domain* dom);
 long long gh_rk4_work_size(const gh_domain* dom);
 int gh_num_shells(const gh_domain* dom);
 
-/* Write the exact Kerr-Schild state of a hole of mass M and dimensionless
- * spin chi (along +z, a = chi M) into u (device, one state), and set the
- * domain's gauge source H_a = -Gamma_a, d_i H_a of that solution and the
- * boundary background used by the characteristic boundary conditions.
- * Kerr-Schild data: Sec. 3.1 (Eq. dimensionlessspin).  Computed on the
- * device with forward-mode second-order dual numbers. */
-gh_status gh_set_analytic_kerr_schild(gh_domain* dom, double M, double chi, double* u);
+/* Write the exact Kerr-Schild state of hole bh (mass M, dimensionless spin chi
+ * along +z, a = chi M) into the shells of that hole in u (device, one state),
+ * and set, on those shells, the gauge source H_a = -Gamma_a, d_i H_a of that
+ * solution and the boundary background used by the characteristic boundary
+ * conditions.  bh = -1: every shell of the domain.  Kerr-Schild data: Sec. 3.1
+ * (Eq. dimensionlessspin).  Computed on the device with forward-mode
+ * second-order dual numbers. */
+gh_status gh_set_analytic_kerr_schild(gh_domain* dom, int bh, double M, double chi, double* u);
+
+/* Scale the time step of hole bh: its shells advance by dt * scale in every
+ * gh_rk4_step(dom, dt, ...).  Lets holes of different resolution take their
+ * own stable steps inside one batched step.  Default 1. */
+gh_status gh_set_dt_scale(gh_domain* dom, int bh, double scale);
 
 /* Replace the gauge source: H (device) holds, for each shell, [r][4][theta][phi]
  * with H_a; dH (device) holds [r][12][theta][phi] with entry 4*i + a = d_i H_a.
@@ -147,6 +159,14 @@ gh_status gh_rhs(gh_domain* dom, const double* u, double* dudt);
  * constraint norm of the incoming u is written to norm2_pre[s] for each shell
  * s (computed inside the first stage, from the same derivatives). */
 gh_status gh_rk4_step(gh_domain* dom, double dt, double* u, double* work, double* norm2_pre);
+
+/* CUDA graph of one RK4 step: gh_rk4_graph_capture records the launches of
+ * gh_rk4_step(dom, dt, u, work, norm2_pre) (same pointers, profiler off) into a
+ * graph owned by the domain, replacing any previous one; nothing runs.
+ * gh_rk4_graph_launch replays it n_steps times on the domain's stream, which
+ * removes the per-launch host overhead of the many small launches of a step. */
+gh_status gh_rk4_graph_capture(gh_domain* dom, double dt, double* u, double* work, double* norm2_pre);
+gh_status gh_rk4_graph_launch(gh_domain* dom, int n_steps);
 
 /* Apply the domain's filters to u (device) in place; work as for gh_rk4_step. */
 gh_status gh_apply_filters(gh_domain* dom, double* u, double* work);

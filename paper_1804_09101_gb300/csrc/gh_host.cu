@@ -378,7 +378,7 @@ gh_status derivatives(gh_domain* d, const double* u) {
 gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
   // src -> (radial) -> (angular) -> u ; tmp must not alias src or u
   const bool rad = d->params.radial_filter_on != 0;
-  const bool ang = d->params.sh_keep_l >= 0;
+  const bool ang = d->params.sh_keep_l != -1;
   double* cur = src;
   if (rad) {
     ProfScope p(d, GH_K_RADIAL_FILTER);
@@ -403,7 +403,7 @@ gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
 gh_status build_dense(gh_domain* d) {
   if (d->ang_deriv_d) return GH_OK;
   std::map<int, std::pair<double*, double*>> ang_cache;   // L -> (Bth, Bph)
-  std::map<int, double*> filt_cache;                      // L -> S
+  std::map<std::pair<int, int>, double*> filt_cache;      // (L, keep) -> S
   std::vector<gh::GemmProb> pd, pf;
   int tiles = 0, ftiles = 0;
   for (int s = 0; s < d->n_shells; ++s) {
@@ -417,13 +417,14 @@ gh_status build_dense(gh_domain* d) {
     }
     sh.Bth = ang_cache[sh.L].first;
     sh.Bph = ang_cache[sh.L].second;
-    if (d->params.sh_keep_l >= 0) {
-      if (!filt_cache.count(sh.L)) {
+    if (sh.keep >= 0) {
+      const auto key = std::make_pair(sh.L, sh.keep);
+      if (!filt_cache.count(key)) {
         double* Sd = nullptr;
-        GH_CUDA(d, upload(d, angular_matrix(ag, 2, d->params.sh_keep_l), &Sd));
-        filt_cache[sh.L] = Sd;
+        GH_CUDA(d, upload(d, angular_matrix(ag, 2, sh.keep), &Sd));
+        filt_cache[key] = Sd;
       }
-      sh.Sf = filt_cache[sh.L];
+      sh.Sf = filt_cache[key];
     }
     for (int c = 0; c < 2; ++c) {
       gh::GemmProb P;
@@ -479,10 +480,19 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     const gh_shell& sh = shells[s];
     if (!(sh.r_in > 0.0) || !(sh.r_out > sh.r_in) || sh.n_r < 3 || sh.n_r > 64 || sh.L < 1 || sh.L > 47)
       return fail(nullptr, GH_EINVAL, "shell " + std::to_string(s) + ": need 0 < r_in < r_out, 3 <= n_r <= 64, 1 <= L <= 47");
-    if (s > 0 && shells[s].r_in != shells[s - 1].r_out)
-      return fail(nullptr, GH_EINVAL, "shell " + std::to_string(s) + " does not start where shell " +
-                                          std::to_string(s - 1) + " ends");
+    if (sh.bh < 0) return fail(nullptr, GH_EINVAL, "shell " + std::to_string(s) + ": bh must be >= 0");
+    if (s > 0 && shells[s].bh == shells[s - 1].bh) {
+      if (shells[s].r_in != shells[s - 1].r_out)
+        return fail(nullptr, GH_EINVAL, "shell " + std::to_string(s) + " does not start where shell " +
+                                            std::to_string(s - 1) + " ends");
+      if (shells[s].L != shells[s - 1].L)
+        return fail(nullptr, GH_EINVAL, "adjacent shells of one hole must have the same L (shared boundary points)");
+    }
+    for (int t = 0; t + 1 < s; ++t)
+      if (shells[t].bh == sh.bh && shells[s - 1].bh != sh.bh)
+        return fail(nullptr, GH_EINVAL, "the shells of hole " + std::to_string(sh.bh) + " are not consecutive");
   }
+  if (params->sh_keep_l < -2) return fail(nullptr, GH_EINVAL, "sh_keep_l must be >= -2");
   if (params->sh_keep_l >= 0)
     for (int s = 0; s < n_shells; ++s)
       if (params->sh_keep_l > shells[s].L) return fail(nullptr, GH_EINVAL, "sh_keep_l exceeds a shell's L");
@@ -529,6 +539,9 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     sh.r_in = in.r_in;
     sh.r_out = in.r_out;
     sh.rscale = 2.0 / (in.r_out - in.r_in);
+    sh.bh = in.bh;
+    sh.dt_scale = 1.0;
+    sh.keep = params->sh_keep_l == -2 ? (2 * in.L) / 3 : params->sh_keep_l;
     off += (long long)sh.n_r * gh::NF * sh.na;
     pts += (long long)sh.n_r * sh.na;
     if (!radial_cache.count(sh.n_r)) {
@@ -566,8 +579,8 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     };
     CREATE_CUDA(get_plan(sh.L, true, sh.sd));
     sh.sd.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sd.M, true, gh::NF * sh.n_r);
-    if (params->sh_keep_l >= 0) {
-      CREATE_CUDA(get_plan(params->sh_keep_l, false, sh.sf));
+    if (sh.keep >= 0) {
+      CREATE_CUDA(get_plan(sh.keep, false, sh.sf));
       sh.sf.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sf.M, false, gh::NF * sh.n_r);
     }
     // grid tables
@@ -609,12 +622,10 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     gh::BcSliceDev b;
     std::memset(&b, 0, sizeof(b));
     gh::ShellDev& sa = d->shells_h[s];
-    if (s + 1 < n_shells) {
+    b.bh = sa.bh;
+    b.dt_scale = 1.0;
+    if (s + 1 < n_shells && d->shells_h[s + 1].bh == sa.bh) {
       gh::ShellDev& sb = d->shells_h[s + 1];
-      if (sa.L != sb.L) {
-        d->err = "adjacent shells must have the same L (shared boundary points)";
-        return bail(GH_EINVAL);
-      }
       b.kind = 1;
       b.shell_b = s + 1;
       b.off_b = sb.off;
@@ -723,6 +734,7 @@ gh_status gh_destroy_domain(gh_domain* d) {
     cudaEventDestroy(b.b);
   }
   for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
+  if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
   for (void* p : d->owned) cudaFree(p);
   delete d;
   return GH_OK;
@@ -742,12 +754,79 @@ long long gh_launch_count(const gh_domain* d) { return d ? d->launches : -1; }
 
 const char* gh_last_error(const gh_domain* d) { return d ? d->err.c_str() : g_create_error.c_str(); }
 
-gh_status gh_set_analytic_kerr_schild(gh_domain* d, double M, double chi, double* u) {
+gh_status gh_set_analytic_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u) {
   if (!d || !u) return fail(d, GH_EINVAL, "null argument");
   if (!(M > 0.0) || !(std::fabs(chi) < 1.0)) return fail(d, GH_EINVAL, "need M > 0 and |chi| < 1");
+  if (bh < -1) return fail(d, GH_EINVAL, "bh must be -1 (all) or a hole index");
   if (gh_status s = check_latched(d)) return s;
-  GH_CUDA(d, gh::launch_kerr_schild(d, M, chi, u));
-  GH_CUDA(d, gh::launch_bc_background(d, u));
+  GH_CUDA(d, gh::launch_kerr_schild(d, bh, M, chi, u));
+  GH_CUDA(d, gh::launch_bc_background(d, u, bh));
+  return GH_OK;
+}
+
+gh_status gh_set_dt_scale(gh_domain* d, int bh, double scale) {
+  if (!d) return GH_EINVAL;
+  if (!(scale > 0.0)) return fail(d, GH_EINVAL, "scale must be > 0");
+  int hit = 0;
+  for (auto& sh : d->shells_h)
+    if (sh.bh == bh) { sh.dt_scale = scale; ++hit; }
+  for (auto& b : d->bc_h)
+    if (b.bh == bh) b.dt_scale = scale;
+  if (!hit) return fail(d, GH_EINVAL, "no shell belongs to hole " + std::to_string(bh));
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  GH_CUDA(d, cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(gh::ShellDev) * d->shells_h.size(),
+                        cudaMemcpyHostToDevice));
+  GH_CUDA(d, cudaMemcpy(d->bc_d, d->bc_h.data(), sizeof(gh::BcSliceDev) * d->bc_h.size(), cudaMemcpyHostToDevice));
+  return GH_OK;
+}
+
+gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
+  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  cudaStream_t saved = d->stream;
+  cudaStream_t cap = nullptr;
+  GH_CUDA(d, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  const bool prof = d->prof;
+  d->prof = false;
+  d->stream = cap;
+  const long long n0 = d->launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  gh_status st = GH_OK;
+  if (e == cudaSuccess) {
+    st = gh_rk4_step(d, dt, u, work, norm2_pre);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e2 != cudaSuccess && st == GH_OK) e = e2;
+  }
+  d->stream = saved;
+  d->prof = prof;
+  cudaStreamDestroy(cap);
+  if (st != GH_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(d, GH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  if (d->graph_exec) {
+    cudaGraphExecDestroy(d->graph_exec);
+    d->graph_exec = nullptr;
+  }
+  e = cudaGraphInstantiate(&d->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(d, GH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  d->graph_step_launches = d->launches - n0;
+  d->launches = n0;
+  return GH_OK;
+}
+
+gh_status gh_rk4_graph_launch(gh_domain* d, int n_steps) {
+  if (!d || n_steps < 0) return fail(d, GH_EINVAL, "bad arguments");
+  if (!d->graph_exec) return fail(d, GH_EINVAL, "no graph captured (call gh_rk4_graph_capture first)");
+  if (gh_status s = check_latched(d)) return s;
+  for (int i = 0; i < n_steps; ++i) GH_CUDA(d, cudaGraphLaunch(d->graph_exec, d->stream));
+  d->launches += (long long)n_steps * d->graph_step_launches;
   return GH_OK;
 }
 
@@ -792,7 +871,7 @@ gh_status gh_get_gauge(const gh_domain* dc, double* H, double* dH) {
 
 gh_status gh_set_background(gh_domain* d, const double* u_bg) {
   if (!d || !u_bg) return fail(d, GH_EINVAL, "null argument");
-  GH_CUDA(d, gh::launch_bc_background(d, u_bg));
+  GH_CUDA(d, gh::launch_bc_background(d, u_bg, -1));
   return GH_OK;
 }
 
@@ -840,7 +919,7 @@ gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* 
   double* us = work;
   double* k = work + d->state;
   double* acc = work + 2 * d->state;
-  const bool filt = d->params.radial_filter_on || d->params.sh_keep_l >= 0;
+  const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
   for (int stage = 1; stage <= 4; ++stage) {
     const double* in = (stage == 1) ? u : us;
     if (gh_status s = derivatives(d, in)) return s;

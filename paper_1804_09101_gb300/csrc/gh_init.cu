@@ -111,9 +111,10 @@ __device__ void kerr_schild_metric(double x, double y, double z, double M, doubl
 // gauge source H_a = -Gamma_a, d_i H_a = -d_i Gamma_a (d_t H_a = 0).
 __global__ void __launch_bounds__(64)
 kerr_schild_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
-                   double M, double a, double* __restrict__ u) {
+                   int bh, double M, double a, double* __restrict__ u) {
   const int s = [&] { int t = 0; while (t + 1 < n_shells && begin[t + 1] <= (int)blockIdx.x) ++t; return t; }();
   const ShellDev& sh = shells[s];
+  if (bh >= 0 && sh.bh != bh) return;
   const int na = sh.na;
   const int bps = (na + 63) / 64;
   const int lb = blockIdx.x - begin[s];
@@ -260,7 +261,7 @@ perturbation_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   }
 }
 
-cudaError_t launch_kerr_schild(gh_domain* d, double M, double chi, double* u) {
+cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u) {
   // 64-thread blocks: reuse the pointwise block map scaled by 2
   int blocks = 0;
   std::vector<int> begin(d->n_shells + 1);
@@ -274,7 +275,7 @@ cudaError_t launch_kerr_schild(gh_domain* d, double M, double chi, double* u) {
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream);
   if (e != cudaSuccess) return e;
-  kerr_schild_kernel<<<blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, bd, M, chi * M, u);
+  kerr_schild_kernel<<<blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, bd, bh, M, chi * M, u);
   d->launches++;
   e = cudaGetLastError();
   cudaFreeAsync(bd, d->stream);

@@ -50,6 +50,9 @@ struct ShellDev {
   double* gauge;                // [n_r][16][na]
   int bc_inner;                 // boundary slice index at r_in, -1 if none (excision)
   int bc_outer;                 // boundary slice index at r_out
+  int bh;                       // black hole this shell belongs to
+  int keep;                     // SH filter: keep l <= keep (-1: no filter)
+  double dt_scale;              // this hole's step = dt * dt_scale
   SepPlan sd;                   // separable d/dtheta, d/dphi
   SepPlan sf;                   // separable SH truncation filter (M = 0 if off)
 };
@@ -62,6 +65,8 @@ struct BcSliceDev {
   int na;
   long long off_a, off_b;       // state offset of the boundary r-slice in a / b
   double* bg;                   // [10][na] n_dn(3) n_up(3) alpha beta_up(3)
+  double dt_scale;              // the hole's step scale (see ShellDev)
+  int bh, pad;
 };
 
 // One FP64 GEMM problem of a batched launch: C = A * B, row-major.
@@ -112,6 +117,9 @@ struct gh_domain {
   std::vector<void*> owned;      // every device allocation, freed on destroy
   std::string err;
   long long launches = 0;
+  // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
+  cudaGraphExec_t graph_exec = nullptr;
+  long long graph_step_launches = 0;
   // profiler (gh_profile_enable / gh_profile_read)
   bool prof = false;
   struct Bracket { int fam; cudaEvent_t a, b; };
@@ -139,8 +147,8 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
 cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out);
 cudaError_t launch_norm_reduce(gh_domain* d, double* norm2);
 cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du);
-cudaError_t launch_bc_background(gh_domain* d, const double* u);
-cudaError_t launch_kerr_schild(gh_domain* d, double M, double chi, double* u);
+cudaError_t launch_bc_background(gh_domain* d, const double* u, int bh);
+cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u);
 cudaError_t launch_perturbation(gh_domain* d, int kind, double A, double Rc, double w,
                                 int lmax, const double* coeffs_dev, double* u);
 

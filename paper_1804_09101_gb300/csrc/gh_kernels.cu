@@ -609,11 +609,12 @@ pointwise_kernel(PointwiseArgs a) {
         }
         const int fidx[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
         const bool on_bc = (ir == 0 && sh.bc_inner >= 0) || (ir == sh.n_r - 1 && sh.bc_outer >= 0);
+        const double dts = a.dt * sh.dt_scale;
 #pragma unroll
         for (int e = 0; e < 5; ++e) {
           const long long idx = base + (long long)fidx[e] * na;
           if (a.stage == 0 || on_bc) a.k[idx] = out[e];
-          else stage_combine(a.stage, a.dt, out[e], idx, a.u0, a.acc, a.us);
+          else stage_combine(a.stage, dts, out[e], idx, a.u0, a.acc, a.us);
         }
       }
     }
@@ -683,7 +684,7 @@ __device__ __forceinline__ void char_project_pair(const double* k, long long bas
 }
 
 __device__ __forceinline__ void char_write_pair(const BcArgs& a, long long base, int na, int p, const CharPair& c,
-                                                const double n_dn[3], double g2) {
+                                                const double n_dn[3], double g2, double dts) {
   double v[5];
   v[0] = c.psi;
   v[1] = 0.5 * (c.wp + c.wm) + g2 * c.psi;
@@ -695,7 +696,7 @@ __device__ __forceinline__ void char_write_pair(const BcArgs& a, long long base,
   for (int e = 0; e < 5; ++e) {
     const long long idx = base + (long long)f[e] * na;
     if (a.stage == 0) a.k[idx] = v[e];
-    else stage_combine(a.stage, a.dt, v[e], idx, a.u0, a.acc, a.us);
+    else stage_combine(a.stage, dts, v[e], idx, a.u0, a.acc, a.us);
   }
 }
 
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     if (v_0 < 0.0) c.w0[0] = c.w0[1] = c.w0[2] = 0.0;
     if (v_p < 0.0) c.wp = 0.0;
     if (v_m < 0.0) c.wm = 0.0;
-    char_write_pair(a, base, na, p, c, n_dn, g2);
+    char_write_pair(a, base, na, p, c, n_dn, g2, a.dt * sl.dt_scale);
   } else {
     const long long ba = sl.off_a + q, bb = sl.off_b + q;
     CharPair ci, co;
@@ -745,8 +746,8 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     for (int i = 0; i < 3; ++i) select_pair(ci.w0[i], co.w0[i], v_0);
     select_pair(ci.wp, co.wp, v_p);
     select_pair(ci.wm, co.wm, v_m);
-    char_write_pair(a, ba, na, p, ci, n_dn, g2);
-    char_write_pair(a, bb, na, p, co, n_dn, g2);
+    char_write_pair(a, ba, na, p, ci, n_dn, g2, a.dt * sl.dt_scale);
+    char_write_pair(a, bb, na, p, co, n_dn, g2, a.dt * sl.dt_scale);
   }
 }
 
@@ -755,11 +756,12 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
 // unit normal n_i = d_i R / |d R|_g, n^i = g^ij n_j.
 __global__ void __launch_bounds__(128)
 bc_background_kernel(const ShellDev* __restrict__ shells, BcSliceDev* slices, int n_slices,
-                     const int* __restrict__ pt_begin, const double* __restrict__ u) {
+                     const int* __restrict__ pt_begin, const double* __restrict__ u, int bh) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= pt_begin[n_slices]) return;
   const int s = find_segment(pt_begin, n_slices, t);
   BcSliceDev& sl = slices[s];
+  if (bh >= 0 && sl.bh != bh) return;
   const int q = t - pt_begin[s];
   const int na = sl.na;
   const ShellDev& sh = shells[sl.shell_a];
@@ -942,10 +944,10 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_bc_background(gh_domain* d, const double* u) {
+cudaError_t launch_bc_background(gh_domain* d, const double* u, int bh) {
   if (d->bc_points == 0) return cudaSuccess;
   bc_background_kernel<<<cdiv(d->bc_points, 128), 128, 0, d->stream>>>(
-      d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, u);
+      d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, u, bh);
   d->launches++;
   return cudaGetLastError();
 }

@@ -28,7 +28,7 @@ class GHError(RuntimeError):
 
 class gh_shell(ctypes.Structure):
     _fields_ = [("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
-                ("n_r", ctypes.c_int), ("L", ctypes.c_int)]
+                ("n_r", ctypes.c_int), ("L", ctypes.c_int), ("bh", ctypes.c_int)]
 
 
 class gh_params(ctypes.Structure):
@@ -54,7 +54,10 @@ def _load():
         "gh_num_shells": ([P], I),
         "gh_launch_count": ([P], ctypes.c_longlong),
         "gh_last_error": ([P], ctypes.c_char_p),
-        "gh_set_analytic_kerr_schild": ([P, D, D, P], I),
+        "gh_set_analytic_kerr_schild": ([P, I, D, D, P], I),
+        "gh_set_dt_scale": ([P, I, D], I),
+        "gh_rk4_graph_capture": ([P, D, P, P, P], I),
+        "gh_rk4_graph_launch": ([P, I], I),
         "gh_set_gauge": ([P, P, P], I),
         "gh_set_background": ([P, P], I),
         "gh_get_gauge": ([P, P, P], I),
@@ -99,7 +102,9 @@ class Domain:
 
     def __init__(self, shells, gamma0=1.0, gamma1=-1.0, gamma2=1.0, filt_alpha=36.0, filt_order=32,
                  radial_filter_on=False, sh_keep_l=-1):
-        arr = (gh_shell * len(shells))(*[gh_shell(float(a), float(b), int(n), int(L)) for (a, b, n, L) in shells])
+        shells = [tuple(s) + (0,) if len(s) == 4 else tuple(s) for s in shells]
+        arr = (gh_shell * len(shells))(*[gh_shell(float(a), float(b), int(n), int(L), int(h))
+                                         for (a, b, n, L, h) in shells])
         self.params = gh_params(gamma0, gamma1, gamma2, filt_alpha, int(filt_order),
                                 int(bool(radial_filter_on)), int(sh_keep_l))
         h = ctypes.c_void_p()
@@ -147,9 +152,26 @@ class Domain:
         return torch.zeros(self.work_size, dtype=torch.float64, device="cuda")
 
 
-def gh_set_analytic_kerr_schild(dom, M, chi, u):
+def gh_set_analytic_kerr_schild(dom, bh, M, chi, u):
     dom._stream()
-    dom._check(_lib.gh_set_analytic_kerr_schild(dom.handle, float(M), float(chi), _ptr(u, "u", dom.state_size)))
+    dom._check(_lib.gh_set_analytic_kerr_schild(dom.handle, int(bh), float(M), float(chi),
+                                                _ptr(u, "u", dom.state_size)))
+
+
+def gh_set_dt_scale(dom, bh, scale):
+    dom._stream()
+    dom._check(_lib.gh_set_dt_scale(dom.handle, int(bh), float(scale)))
+
+
+def gh_rk4_graph_capture(dom, dt, u, work, norm2_pre=None):
+    dom._stream()
+    dom._check(_lib.gh_rk4_graph_capture(dom.handle, float(dt), _ptr(u, "u", dom.state_size),
+                                         _ptr(work, "work", dom.work_size), _ptr(norm2_pre, "norm2_pre")))
+
+
+def gh_rk4_graph_launch(dom, n_steps):
+    dom._stream()
+    dom._check(_lib.gh_rk4_graph_launch(dom.handle, int(n_steps)))
 
 
 def gh_set_gauge(dom, H, dH):

@@ -113,6 +113,62 @@ def adjoint_single_shell(seed=104):
     return w
 
 
+@dataclass
+class BatchedWorkload:
+    """Independent single-shell holes evolved together (one shell per hole)."""
+    name: str
+    holes: list                      # dicts: M, chi, r_in, r_out, n_r, L, dt, seed
+    gamma0: float = 1.0
+    gamma1: float = -1.0
+    gamma2: float = 1.0
+    filt_alpha: float = 36.0
+    filt_order: int = 32
+    radial_filter_on: bool = True
+    sh_keep_l: int = -2              # floor(2L/3) on each shell
+    noise_amp: float = 1e-8
+
+    @property
+    def shells(self):
+        return [(h["r_in"], h["r_out"], h["n_r"], h["L"], b) for b, h in enumerate(self.holes)]
+
+    def points(self):
+        return sum(h["n_r"] * 2 * (h["L"] + 1) ** 2 for h in self.holes)
+
+    def state_len(self):
+        return 50 * self.points()
+
+    def noise(self):
+        """Seeded N(0,1) * noise_amp per hole, concatenated in shell order."""
+        parts = []
+        for h in self.holes:
+            n = 50 * h["n_r"] * 2 * (h["L"] + 1) ** 2
+            parts.append(np.random.default_rng(h["seed"]).standard_normal(n) * self.noise_amp)
+        return np.concatenate(parts)
+
+
+def _stable_dt(r_in, r_out, n_r, L):
+    """0.25 x the smallest grid spacing: the CGL gap or r_in sin(theta_1) 2 pi / N_phi."""
+    cgl_gap = 0.5 * (r_out - r_in) * (1.0 - np.cos(np.pi / (n_r - 1)))
+    mu = np.polynomial.legendre.leggauss(L + 1)[0]
+    s1 = np.sqrt(1.0 - mu.max() ** 2)
+    ang_gap = r_in * s1 * 2.0 * np.pi / (2 * (L + 1))
+    return 0.25 * min(cgl_gap, ang_gap)
+
+
+def batched_workload(n_bh=64, seed=103):
+    """The batched many-hole workload: seeded spins, masses and resolutions,
+    inner radius 0.9 x the polar horizon radius M + sqrt(M^2 - a^2), outer 20 M."""
+    holes = []
+    for d in batched_black_holes(n_bh, seed):
+        M, chi = d["M"], d["chi"]
+        a = chi * M
+        r_in = 0.9 * (M + np.sqrt(M * M - a * a))
+        r_out = 20.0 * M
+        holes.append(dict(M=M, chi=chi, r_in=r_in, r_out=r_out, n_r=d["n_r"], L=d["L"], seed=d["seed"],
+                          dt=_stable_dt(r_in, r_out, d["n_r"], d["L"])))
+    return BatchedWorkload(name="batched_%dbh" % n_bh, holes=holes)
+
+
 def batched_black_holes(n_bh=64, seed=103):
     """Independent single-shell holes of uneven resolution (seeded draws).
 

@@ -69,7 +69,7 @@ def test_kerr_schild_initial_data_and_gauge(case):
     w, odom, _ = case
     dom = gh.Domain.from_workload(w)
     u = dom.new_state()
-    gh.gh_set_analytic_kerr_schild(dom, w.M, w.chi, u)
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
     ref = flat(odom.u_exact)
     assert max_rel(to_host(u), ref, np.abs(ref).max()) < REL_TOL
     H = torch.zeros(4 * dom.num_points, dtype=torch.float64, device="cuda")
@@ -201,7 +201,7 @@ def test_exact_solution_is_stationary_to_truncation_on_the_gpu():
     for (n_r, L) in [(11, 7), (17, 13), (23, 19)]:
         dom = gh.Domain([(3.0, 6.0, n_r, L)])
         u = dom.new_state()
-        gh.gh_set_analytic_kerr_schild(dom, 1.0, 0.9, u)
+        gh.gh_set_analytic_kerr_schild(dom, -1, 1.0, 0.9, u)
         k = dom.new_state()
         gh.gh_rhs(dom, u, k)
         errs.append(float(to_host(k.abs().max().reshape(1))[0]))
