@@ -198,6 +198,35 @@ gh_status gh_constraints(gh_domain* dom, const double* u, double* c_out, double*
  *     element it later reads. */
 gh_status gh_rhs_noalloc(gh_domain* dom, const double* u, double* dudt);
 
+/* ---------------------------------------------------------------- adjoint
+ * Vector-Jacobian products of the evolution (reverse-mode derivatives), for
+ * gradients of functionals of the evolved state.  They need the separable
+ * angular algorithm (GH_ENOTSUP otherwise).  The boundary projection is linear
+ * in dudt (fixed background) and the filters and derivative maps are linear,
+ * so the adjoint is exact up to rounding: transposed boundary conditions, the
+ * reverse pass of the pointwise GH algebra, transposed DiffJac, radial and
+ * angular maps (Eqs. DiffJac and DifferentiatorI1S2, transposed). */
+
+/* ubar += (dF/du)^T kbar for F = gh_rhs; u, kbar, ubar: device states. */
+gh_status gh_rhs_vjp(gh_domain* dom, const double* u, const double* kbar, double* ubar);
+
+/* ubar_n = (d step / d u_n)^T ubar_np1 for step = gh_rk4_step(dom, dt, .) with
+ * its filters; u_n is the state the step started from.  Recomputes the stage
+ * states.  work: gh_rk4_vjp_work_size doubles (device).  ubar_n must not
+ * alias ubar_np1. */
+long long gh_rk4_vjp_work_size(const gh_domain* dom);
+gh_status gh_rk4_step_vjp(gh_domain* dom, double dt, const double* u_n, const double* ubar_np1,
+                          double* ubar_n, double* work);
+
+/* ubar += weight * d/du (sum over shells of the constraint norm that
+ * gh_constraints writes to norm2). */
+gh_status gh_constraint_energy_vjp(gh_domain* dom, const double* u, double weight, double* ubar);
+
+/* grad[lm] (host, (lmax+1)^2 doubles) = <ubar, d u / d c_lm> for the Pi-mode
+ * perturbation of gh_add_perturbation (kind 1 only; lmax <= 8).  Synchronises. */
+gh_status gh_perturbation_vjp(gh_domain* dom, int kind, double Rc, double w, int lmax, const double* ubar,
+                              double* grad);
+
 /* Block until the domain's stream is idle; returns the first latched device
  * error (GH_ENONFINITE) or GH_ECUDA, then clears the latch. */
 gh_status gh_sync(gh_domain* dom);

@@ -1,0 +1,603 @@
+// Adjoint (vector-Jacobian products) of the right-hand side, of one RK4 step
+// with its filters, and of the constraint energy; and the gradient of a
+// Pi-mode perturbation with respect to its coefficients.
+//
+// Every map of the forward path is linear except the pointwise GH algebra, so
+// the adjoint is: the transposed boundary projection (linear in dudt, fixed
+// background), the hand-derived reverse pass of the per-point algebra
+// (gh_point.cuh), the transposed DiffJac (folded into that pass), and the
+// transposed radial and angular maps (Eq. DifferentiatorI1S2 transposed).
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "gh_geom.cuh"
+#include "gh_internal.h"
+#include "gh_point.cuh"
+#include "gh_tensor.cuh"
+
+namespace gh {
+
+// ---------------------------------------------------------------------------
+// Transposed radial map: out[r][col] (+)= sum_q M^T[r][q] in[q][col].
+constexpr int ADJ_RAD_THREADS = 128;
+
+template <bool FILTER, bool ACCUM>
+__global__ void __launch_bounds__(ADJ_RAD_THREADS)
+radial_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                      const double* __restrict__ in, double* __restrict__ out) {
+  __shared__ double Ms[64 * 64];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int n = sh.n_r;
+  const double* M = FILTER ? sh.FrT : sh.DrT;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ms[i] = M[i];
+  __syncthreads();
+  const long long cols = (long long)NF * sh.na;
+  const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
+  if (col >= cols) return;
+  const double* src = in + sh.off + col;
+  double* dst = out + sh.off + col;
+  for (int r = 0; r < n; ++r) {
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q) acc = fma(Ms[r * n + q], src[(long long)q * cols], acc);
+    const long long o = (long long)r * cols;
+    dst[o] = ACCUM ? dst[o] + acc : acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed separable angular map.  TWO: out += Theta^T in0 + Phi^T in1 (the
+// cotangents of d/dtheta and d/dphi); one: out = S^T in0 (the filter).
+constexpr int SEPA_THREADS = 256;
+
+template <bool TWO>
+__global__ void __launch_bounds__(SEPA_THREADS)
+sep_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                   const double* __restrict__ in0, const double* __restrict__ in1, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const SepAdjPlan& P = TWO ? sh.sda : sh.sfa;
+  const int nth = sh.nth, nph = sh.nph, na = sh.na, M = P.M, K = P.K;
+  const int rows = NF * sh.n_r;
+  const int RB = P.rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  double* Y0 = sm;                                        // [RB][na]
+  double* Y1 = Y0 + (size_t)RB * na;                      // [RB][na] (TWO)
+  double* A0 = Y1 + (TWO ? (size_t)RB * na : 0);          // [RB][nth][M]
+  double* A1 = A0 + (size_t)RB * nth * M;                 // [RB][nth][M] (TWO)
+  double* Bm = A1 + (TWO ? (size_t)RB * nth * M : 0);     // [RB][nth][M]
+  const long long base = sh.off + (long long)row0 * na;
+  for (int i = threadIdx.x; i < nr * na; i += SEPA_THREADS) {
+    Y0[i] = in0[base + i];
+    if (TWO) Y1[i] = in1[base + i];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nr * nth * M; o += SEPA_THREADS) {
+    const int mode = o % M;
+    const double* r0 = Y0 + (o / M) * nph;
+    double a0 = 0.0, a1 = 0.0;
+    if (TWO) {
+      const double* r1 = Y1 + (o / M) * nph;
+      for (int k = 0; k < nph; ++k) {
+        a0 = fma(r0[k], __ldg(P.F0T + k * M + mode), a0);
+        a1 = fma(r1[k], __ldg(P.F1T + k * M + mode), a1);
+      }
+      A1[o] = a1;
+    } else {
+      for (int k = 0; k < nph; ++k) a0 = fma(r0[k], __ldg(P.F0T + k * M + mode), a0);
+    }
+    A0[o] = a0;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nr * nth * M; o += SEPA_THREADS) {
+    const int j = o % nth;
+    const int t = o / nth;
+    const int mode = t % M;
+    const int rr = t / M;
+    const int m = mode <= K ? mode : mode - K;
+    const double* a0 = A0 + (size_t)rr * nth * M + mode;
+    const double* q0 = P.Q0T + (size_t)m * nth * nth + j;
+    double acc = 0.0;
+    for (int jp = 0; jp < nth; ++jp) acc = fma(__ldg(q0 + jp * nth), a0[jp * M], acc);
+    if (TWO) {
+      const double* a1 = A1 + (size_t)rr * nth * M + mode;
+      const double* q1 = P.Q1T + (size_t)m * nth * nth + j;
+      for (int jp = 0; jp < nth; ++jp) acc = fma(__ldg(q1 + jp * nth), a1[jp * M], acc);
+    }
+    Bm[((size_t)rr * nth + j) * M + mode] = acc;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nr * na; o += SEPA_THREADS) {
+    const int k = o % nph;
+    const double* b = Bm + (size_t)(o / nph) * M;
+    double acc = 0.0;
+    for (int mode = 0; mode < M; ++mode) acc = fma(b[mode], __ldg(P.GT + mode * nph + k), acc);
+    out[base + o] = TWO ? out[base + o] + acc : acc;
+  }
+}
+
+cudaError_t sep_adj_set_smem_limits(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(sep_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sep_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// Transposed boundary conditions, in place on a cotangent of dudt, one thread
+// per (boundary point, symmetric pair).  Forward: v' = T^-1 S T v with T the
+// characteristic projection and S the zeroing / upwind selection; here
+// vbar <- T^T S^T T^-T vbar.
+struct CharBar {
+  double psi, wp, wm, w0[3];
+};
+
+__device__ __forceinline__ void load_pair(const double* k, long long base, int na, int p, double v[5]) {
+  v[0] = k[base + (long long)p * na];
+  v[1] = k[base + (long long)(10 + p) * na];
+  for (int i = 0; i < 3; ++i) v[2 + i] = k[base + (long long)(20 + 10 * i + p) * na];
+}
+
+__device__ __forceinline__ void store_pair(double* k, long long base, int na, int p, const double v[5]) {
+  k[base + (long long)p * na] = v[0];
+  k[base + (long long)(10 + p) * na] = v[1];
+  for (int i = 0; i < 3; ++i) k[base + (long long)(20 + 10 * i + p) * na] = v[2 + i];
+}
+
+// w_bar = (T^-1)^T v_bar, with T^-1: psi = w_psi, Pi = (w+ + w-)/2 + g2 w_psi,
+// Phi_i = n_i (w+ - w-)/2 + w0_i.
+__device__ __forceinline__ void inv_t_transpose(const double v[5], const double n_dn[3], double g2, CharBar& w) {
+  const double nphib = n_dn[0] * v[2] + n_dn[1] * v[3] + n_dn[2] * v[4];
+  w.psi = v[0] + g2 * v[1];
+  w.wp = 0.5 * v[1] + 0.5 * nphib;
+  w.wm = 0.5 * v[1] - 0.5 * nphib;
+  for (int i = 0; i < 3; ++i) w.w0[i] = v[2 + i];
+}
+
+// v_bar = T^T w_bar, with T: w_psi = psi, w_pm = Pi +- n^k Phi_k - g2 psi,
+// w0_i = Phi_i - n_i n^k Phi_k.
+__device__ __forceinline__ void t_transpose(const CharBar& w, const double n_dn[3], const double n_up[3], double g2,
+                                            double v[5]) {
+  const double nw0 = n_dn[0] * w.w0[0] + n_dn[1] * w.w0[1] + n_dn[2] * w.w0[2];
+  v[0] = w.psi - g2 * (w.wp + w.wm);
+  v[1] = w.wp + w.wm;
+  for (int k = 0; k < 3; ++k) v[2 + k] = n_up[k] * (w.wp - w.wm) + w.w0[k] - n_up[k] * nw0;
+}
+
+__device__ __forceinline__ void select_transpose(double& wi, double& wo, double v) {
+  if (v < 0.0) {            // forward: both took the outer value
+    wo += wi;
+    wi = 0.0;
+  } else if (v > 0.0) {     // forward: both took the inner value
+    wi += wo;
+    wo = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(128)
+bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int* __restrict__ pt_begin,
+                  double* __restrict__ kb, double gamma1, double gamma2) {
+  const int npts = pt_begin[n_slices];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 10 * npts) return;
+  const int p = t / npts;
+  const int pt = t - p * npts;
+  const int s = find_segment(pt_begin, n_slices, pt);
+  const BcSliceDev& sl = slices[s];
+  const int q = pt - pt_begin[s];
+  const int na = sl.na;
+  double n_dn[3], n_up[3], beta[3];
+  for (int i = 0; i < 3; ++i) {
+    n_dn[i] = sl.bg[(long long)i * na + q];
+    n_up[i] = sl.bg[(long long)(3 + i) * na + q];
+    beta[i] = sl.bg[(long long)(7 + i) * na + q];
+  }
+  const double alpha = sl.bg[(long long)6 * na + q];
+  const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
+  const double v_psi = -(1.0 + gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
+  if (sl.kind == 0) {
+    const long long base = sl.off_a + q;
+    double v[5];
+    load_pair(kb, base, na, p, v);
+    CharBar w;
+    inv_t_transpose(v, n_dn, gamma2, w);
+    if (v_psi < 0.0) w.psi = 0.0;
+    if (v_0 < 0.0) w.w0[0] = w.w0[1] = w.w0[2] = 0.0;
+    if (v_p < 0.0) w.wp = 0.0;
+    if (v_m < 0.0) w.wm = 0.0;
+    t_transpose(w, n_dn, n_up, gamma2, v);
+    store_pair(kb, base, na, p, v);
+  } else {
+    const long long ba = sl.off_a + q, bb = sl.off_b + q;
+    double vi[5], vo[5];
+    load_pair(kb, ba, na, p, vi);
+    load_pair(kb, bb, na, p, vo);
+    CharBar wi, wo;
+    inv_t_transpose(vi, n_dn, gamma2, wi);
+    inv_t_transpose(vo, n_dn, gamma2, wo);
+    select_transpose(wi.psi, wo.psi, v_psi);
+    for (int i = 0; i < 3; ++i) select_transpose(wi.w0[i], wo.w0[i], v_0);
+    select_transpose(wi.wp, wo.wp, v_p);
+    select_transpose(wi.wm, wo.wm, v_m);
+    t_transpose(wi, n_dn, n_up, gamma2, vi);
+    t_transpose(wo, n_dn, n_up, gamma2, vo);
+    store_pair(kb, ba, na, p, vi);
+    store_pair(kb, bb, na, p, vo);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise reverse pass, one thread per point.  Reads the point's fields and
+// the spherical derivatives d/dx, d/dtheta, d/dphi of u from dr/dth/dph,
+// adds the field cotangents to ubar, and overwrites dr/dth/dph at the point
+// with the derivative cotangents (each thread reads its own values first).
+// MODE 0: cotangent kb of dudt (before the boundary conditions).
+// MODE 1: gradient of weight * sum_points w_quadrature * (constraint energy).
+constexpr int ADJ_PT_THREADS = 64;
+
+template <int MODE>
+__global__ void __launch_bounds__(ADJ_PT_THREADS)
+pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                         const double* __restrict__ u, double* dr, double* dth, double* dph,
+                         const double* __restrict__ kb, double* ubar, double g0, double g1, double g2,
+                         double weight) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + ADJ_PT_THREADS - 1) / ADJ_PT_THREADS;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * ADJ_PT_THREADS + threadIdx.x;
+  if (q >= na) return;
+  const long long base = sh.off + (long long)ir * NF * na + q;
+  double uu[50], ds[150], ub[50], dsb[150];
+  for (int f = 0; f < NF; ++f) {
+    const long long o = base + (long long)f * na;
+    uu[f] = u[o];
+    ds[3 * f] = dr[o];
+    ds[3 * f + 1] = dth[o];
+    ds[3 * f + 2] = dph[o];
+    ub[f] = 0.0;
+    dsb[3 * f] = dsb[3 * f + 1] = dsb[3 * f + 2] = 0.0;
+  }
+  const double* gsrc = sh.gauge + (long long)ir * NGAUGE * na + q;
+  double H[4], dH[12];
+  for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
+  for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
+  PointGeom G;
+  point_geom(sh, ir, q, G);
+  PointIn in;
+  in.u = uu;
+  in.ds = ds;
+  for (int i = 0; i < 3; ++i)
+    for (int d = 0; d < 3; ++d) in.J[i][d] = G.J[i][d];
+  in.H = H;
+  in.dH = dH;
+  in.g0 = g0;
+  in.g1 = g1;
+  in.g2 = g2;
+  if (MODE == 0) {
+    double kk[50], out[50];
+    for (int f = 0; f < NF; ++f) kk[f] = kb[base + (long long)f * na];
+    PointFwd fw;
+    point_rhs(in, fw, out);
+    point_rhs_vjp(in, fw, kk, ub, dsb);
+  } else {
+    const int j = q / sh.nph;
+    point_constraint_energy(in, weight * sh.wr[ir] * sh.wth[j], ub, dsb);
+  }
+  for (int f = 0; f < NF; ++f) {
+    const long long o = base + (long long)f * na;
+    ubar[o] += ub[f];
+    dr[o] = dsb[3 * f];
+    dth[o] = dsb[3 * f + 1];
+    dph[o] = dsb[3 * f + 2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Element-wise combinations with the per-hole step dts = dt * dt_scale(shell),
+// one thread per (field, theta, phi) column of a shell.
+//   0: out = x + c * dts * y        1: out = dts * (a x + c y)        2: out += x
+__global__ void __launch_bounds__(128)
+ew_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin, int mode,
+          double* __restrict__ out, const double* __restrict__ x, const double* __restrict__ y, double a,
+          double c, double dt) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const long long cols = (long long)NF * sh.na;
+  const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
+  if (col >= cols) return;
+  const double dts = dt * sh.dt_scale;
+  for (int r = 0; r < sh.n_r; ++r) {
+    const long long o = sh.off + (long long)r * cols + col;
+    if (mode == 0) out[o] = x[o] + c * dts * y[o];
+    else if (mode == 1) out[o] = dts * (a * x[o] + c * y[o]);
+    else out[o] += x[o];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of a Pi-mode perturbation dPi_ab = exp(-((R-Rc)/w)^2) sum c_lm Y_lm
+// (all 10 components) with respect to c_lm: per-block partial sums of
+// sum_p ubar(Pi_p) G(R) Y_lm over the block's points.
+constexpr int PV_THREADS = 64;
+constexpr int PV_MAX_MODES = 81;   // lmax <= 8
+
+__global__ void __launch_bounds__(PV_THREADS)
+pi_modes_vjp_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                    double Rc, double w, int lmax, const double* __restrict__ ubar, double* __restrict__ partial) {
+  __shared__ double red[PV_THREADS];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + PV_THREADS - 1) / PV_THREADS;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * PV_THREADS + threadIdx.x;
+  const int nm = (lmax + 1) * (lmax + 1);
+  double sG = 0.0, ct = 0.0, st = 1.0, phi = 0.0;
+  if (q < na) {
+    const int j = q / sh.nph, k = q - j * sh.nph;
+    const long long base = sh.off + (long long)ir * NF * na + q;
+    double acc = 0.0;
+    for (int p = 0; p < 10; ++p) acc += ubar[base + (long long)(10 + p) * na];
+    const double r = sh.r[ir];
+    sG = acc * exp(-((r - Rc) / w) * ((r - Rc) / w));
+    ct = sh.cth[j];
+    st = sh.sth[j];
+    phi = 2.0 * 3.14159265358979323846 * k / sh.nph;
+  }
+  const int W = PERT_LMAX + 1;
+  double P[W * W], dP[W * W];
+  legendre_table(lmax, ct, st, P, dP);
+  int idx = 0;
+  for (int l = 0; l <= lmax; ++l)
+    for (int m = -l; m <= l; ++m, ++idx) {
+      const int am = m < 0 ? -m : m;
+      double fphi = 1.0;
+      if (m != 0) {
+        double sn, cs;
+        sincos(am * phi, &sn, &cs);
+        fphi = 1.41421356237309504880 * (m > 0 ? cs : sn);
+      }
+      red[threadIdx.x] = (q < na) ? sG * P[l * W + am] * fphi : 0.0;
+      __syncthreads();
+      for (int stp = PV_THREADS / 2; stp > 0; stp >>= 1) {
+        if (threadIdx.x < stp) red[threadIdx.x] += red[threadIdx.x + stp];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) partial[(long long)blockIdx.x * nm + idx] = red[0];
+      __syncthreads();
+    }
+}
+
+}  // namespace gh
+
+// =================================================================== C ABI
+namespace {
+
+gh_status afail(gh_domain* d, gh_status s, const std::string& m) {
+  d->err = m;
+  return s;
+}
+
+#define GH_ACUDA(d, call)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return afail((d), e_ == cudaErrorMemoryAllocation ? GH_ENOMEM : GH_ECUDA,                \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+gh_status adj_ready(gh_domain* d) {
+  if (d->algorithm != 1) return afail(d, GH_ENOTSUP, "the adjoint needs the separable angular algorithm");
+  if (!d->kbt) {
+    void* p = nullptr;
+    GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));
+    d->owned.push_back(p);
+    d->kbt = (double*)p;
+  }
+  return GH_OK;
+}
+
+cudaError_t ew(gh_domain* d, int mode, double* out, const double* x, const double* y, double a, double c,
+               double dt) {
+  gh::ew_kernel<<<d->rad_blocks, 128, 0, d->stream>>>(d->shells_d, d->n_shells, d->rad_block_begin_d, mode, out,
+                                                      x, y, a, c, dt);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+// Forward derivatives of u into d_r, d_th, d_ph.
+cudaError_t fwd_derivs(gh_domain* d, const double* u) {
+  cudaError_t e = gh::launch_radial(d, u, d->d_r, false);
+  if (e != cudaSuccess) return e;
+  return gh::launch_angular_deriv(d, u);
+}
+
+// ubar += (transposed derivative maps) applied to the cotangents in d_r, d_th, d_ph.
+cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {
+  gh::radial_adjoint_kernel<false, true><<<d->rad_blocks, gh::ADJ_RAD_THREADS, 0, d->stream>>>(
+      d->shells_d, d->n_shells, d->rad_block_begin_d, d->d_r, ubar);
+  d->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gh::sep_adjoint_kernel<true><<<d->sda_blocks, gh::SEPA_THREADS, d->sda_smem, d->stream>>>(
+      d->shells_d, d->n_shells, d->sda_block_begin_d, d->d_th, d->d_ph, ubar);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+int adj_pt_blocks(gh_domain* d, std::vector<int>& begin) {
+  int b = 0;
+  begin.resize(d->n_shells + 1);
+  for (int s = 0; s < d->n_shells; ++s) {
+    begin[s] = b;
+    b += d->shells_h[s].n_r * ((d->shells_h[s].na + gh::ADJ_PT_THREADS - 1) / gh::ADJ_PT_THREADS);
+  }
+  begin[d->n_shells] = b;
+  return b;
+}
+
+// ubar += J(u)^T kb; kb is not modified.
+gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar) {
+  GH_ACUDA(d, fwd_derivs(d, u));
+  GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
+  if (d->bc_points) {
+    gh::bc_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
+        d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->kbt, d->params.gamma1, d->params.gamma2);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+  }
+  static thread_local std::vector<int> begin;
+  const int blocks = adj_pt_blocks(d, begin);
+  int* bd = nullptr;
+  GH_ACUDA(d, cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream));
+  GH_ACUDA(d, cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream));
+  gh::pointwise_adjoint_kernel<0><<<blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+      d->shells_d, d->n_shells, bd, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar, d->params.gamma0,
+      d->params.gamma1, d->params.gamma2, 0.0);
+  d->launches++;
+  GH_ACUDA(d, cudaGetLastError());
+  GH_ACUDA(d, cudaFreeAsync(bd, d->stream));
+  GH_ACUDA(d, derivs_transpose_add(d, ubar));
+  return GH_OK;
+}
+
+// Forward RHS k = F(u) (derivatives, pointwise, boundary conditions).
+gh_status rhs_fwd(gh_domain* d, const double* u, double* k) {
+  GH_ACUDA(d, fwd_derivs(d, u));
+  GH_ACUDA(d, gh::launch_pointwise(d, u, k, 0, 0.0, nullptr, nullptr, nullptr, false));
+  GH_ACUDA(d, gh::launch_bc(d, k, 0, 0.0, nullptr, nullptr, nullptr));
+  return GH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long gh_rk4_vjp_work_size(const gh_domain* d) { return d ? 7 * d->state : -1; }
+
+gh_status gh_rhs_vjp(gh_domain* d, const double* u, const double* kbar, double* ubar) {
+  if (!d || !u || !kbar || !ubar) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+  if (gh_status s = adj_ready(d)) return s;
+  return rhs_vjp(d, u, kbar, ubar);
+}
+
+gh_status gh_constraint_energy_vjp(gh_domain* d, const double* u, double weight, double* ubar) {
+  if (!d || !u || !ubar) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+  if (gh_status s = adj_ready(d)) return s;
+  GH_ACUDA(d, fwd_derivs(d, u));
+  static thread_local std::vector<int> begin;
+  const int blocks = adj_pt_blocks(d, begin);
+  int* bd = nullptr;
+  GH_ACUDA(d, cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream));
+  GH_ACUDA(d, cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream));
+  gh::pointwise_adjoint_kernel<1><<<blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+      d->shells_d, d->n_shells, bd, u, d->d_r, d->d_th, d->d_ph, nullptr, ubar, d->params.gamma0,
+      d->params.gamma1, d->params.gamma2, weight);
+  d->launches++;
+  GH_ACUDA(d, cudaGetLastError());
+  GH_ACUDA(d, cudaFreeAsync(bd, d->stream));
+  GH_ACUDA(d, derivs_transpose_add(d, ubar));
+  return GH_OK;
+}
+
+gh_status gh_rk4_step_vjp(gh_domain* d, double dt, const double* u_n, const double* ubar_np1, double* ubar_n,
+                          double* work) {
+  if (!d || !u_n || !ubar_np1 || !ubar_n || !work) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+  if (gh_status s = adj_ready(d)) return s;
+  const long long N = d->state;
+  double* u2 = work;
+  double* u3 = work + N;
+  double* u4 = work + 2 * N;
+  double* k = work + 3 * N;
+  double* kb = work + 4 * N;
+  double* g = work + 5 * N;
+  double* sb = work + 6 * N;
+  // forward recomputation of the stage states
+  if (gh_status s = rhs_fwd(d, u_n, k)) return s;
+  GH_ACUDA(d, ew(d, 0, u2, u_n, k, 0.0, 0.5, dt));
+  if (gh_status s = rhs_fwd(d, u2, k)) return s;
+  GH_ACUDA(d, ew(d, 0, u3, u_n, k, 0.0, 0.5, dt));
+  if (gh_status s = rhs_fwd(d, u3, k)) return s;
+  GH_ACUDA(d, ew(d, 0, u4, u_n, k, 0.0, 1.0, dt));
+  // transposed filters: u_new = Fa(Fr(v))  =>  g = Fr^T Fa^T ubar_np1
+  const double* gin = ubar_np1;
+  if (d->params.sh_keep_l != -1) {
+    gh::sep_adjoint_kernel<false><<<d->sfa_blocks, gh::SEPA_THREADS, d->sfa_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->sfa_block_begin_d, gin, nullptr, g);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+    gin = g;
+  }
+  if (d->params.radial_filter_on) {
+    double* dst = (gin == g) ? kb : g;
+    gh::radial_adjoint_kernel<true, false><<<d->rad_blocks, gh::ADJ_RAD_THREADS, 0, d->stream>>>(
+        d->shells_d, d->n_shells, d->rad_block_begin_d, gin, dst);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+    if (dst != g) GH_ACUDA(d, cudaMemcpyAsync(g, dst, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
+    gin = g;
+  }
+  if (gin != g) GH_ACUDA(d, cudaMemcpyAsync(g, gin, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
+  // reverse through the stages
+  GH_ACUDA(d, cudaMemcpyAsync(ubar_n, g, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
+  GH_ACUDA(d, ew(d, 1, kb, g, g, 1.0 / 6.0, 0.0, dt));                 // kb4 = dt/6 g
+  GH_ACUDA(d, cudaMemsetAsync(sb, 0, sizeof(double) * N, d->stream));
+  if (gh_status s = rhs_vjp(d, u4, kb, sb)) return s;                  // sb = J(u4)^T kb4
+  GH_ACUDA(d, ew(d, 2, ubar_n, sb, nullptr, 0.0, 0.0, 0.0));
+  GH_ACUDA(d, ew(d, 1, kb, g, sb, 1.0 / 3.0, 1.0, dt));                // kb3 = dt (g/3 + sb)
+  GH_ACUDA(d, cudaMemsetAsync(sb, 0, sizeof(double) * N, d->stream));
+  if (gh_status s = rhs_vjp(d, u3, kb, sb)) return s;
+  GH_ACUDA(d, ew(d, 2, ubar_n, sb, nullptr, 0.0, 0.0, 0.0));
+  GH_ACUDA(d, ew(d, 1, kb, g, sb, 1.0 / 3.0, 0.5, dt));                // kb2 = dt (g/3 + sb/2)
+  GH_ACUDA(d, cudaMemsetAsync(sb, 0, sizeof(double) * N, d->stream));
+  if (gh_status s = rhs_vjp(d, u2, kb, sb)) return s;
+  GH_ACUDA(d, ew(d, 2, ubar_n, sb, nullptr, 0.0, 0.0, 0.0));
+  GH_ACUDA(d, ew(d, 1, kb, g, sb, 1.0 / 6.0, 0.5, dt));                // kb1 = dt (g/6 + sb/2)
+  return rhs_vjp(d, u_n, kb, ubar_n);
+}
+
+gh_status gh_perturbation_vjp(gh_domain* d, int kind, double Rc, double w, int lmax, const double* ubar,
+                              double* grad) {
+  if (!d || !ubar || !grad) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+  if (kind != 1) return afail(d, GH_ENOTSUP, "only the Pi-mode perturbation (kind 1) has a gradient entry");
+  if (lmax < 0 || lmax > 8 || !(w > 0.0)) return afail(d, GH_EINVAL, "need 0 <= lmax <= 8 and w > 0");
+  const int nm = (lmax + 1) * (lmax + 1);
+  std::vector<int> begin(d->n_shells + 1);
+  int blocks = 0;
+  for (int s = 0; s < d->n_shells; ++s) {
+    begin[s] = blocks;
+    blocks += d->shells_h[s].n_r * ((d->shells_h[s].na + gh::PV_THREADS - 1) / gh::PV_THREADS);
+  }
+  begin[d->n_shells] = blocks;
+  int* bd = nullptr;
+  double* part = nullptr;
+  GH_ACUDA(d, cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream));
+  GH_ACUDA(d, cudaMallocAsync(&part, sizeof(double) * (size_t)blocks * nm, d->stream));
+  GH_ACUDA(d, cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream));
+  gh::pi_modes_vjp_kernel<<<blocks, gh::PV_THREADS, 0, d->stream>>>(d->shells_d, d->n_shells, bd, Rc, w, lmax,
+                                                                     ubar, part);
+  d->launches++;
+  GH_ACUDA(d, cudaGetLastError());
+  std::vector<double> h((size_t)blocks * nm);
+  GH_ACUDA(d, cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, d->stream));
+  GH_ACUDA(d, cudaFreeAsync(bd, d->stream));
+  GH_ACUDA(d, cudaFreeAsync(part, d->stream));
+  GH_ACUDA(d, cudaStreamSynchronize(d->stream));
+  for (int m = 0; m < nm; ++m) {
+    double acc = 0.0;
+    for (int b = 0; b < blocks; ++b) acc += h[(size_t)b * nm + m];
+    grad[m] = acc;
+  }
+  return GH_OK;
+}
+
+}  // extern "C"

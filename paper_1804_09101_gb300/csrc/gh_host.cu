@@ -231,7 +231,29 @@ std::vector<double> angular_matrix(const AngularGrid& g, int kind, int keep) {
 struct SepHost {
   int K, M;
   std::vector<double> F, G0, G1, Q0, Q1;
+  std::vector<double> F0T, F1T, Q0T, Q1T, GT;   // transposed map (adjoint)
 };
+
+void sep_transpose(SepHost& h, int nth, int nph, bool deriv) {
+  const int M = h.M, K = h.K;
+  h.F0T.assign((size_t)nph * M, 0.0);
+  h.GT.assign((size_t)M * nph, 0.0);
+  if (deriv) h.F1T.assign((size_t)nph * M, 0.0);
+  for (int mode = 0; mode < M; ++mode)
+    for (int k = 0; k < nph; ++k) {
+      h.F0T[(size_t)k * M + mode] = h.G0[(size_t)mode * nph + k];
+      if (deriv) h.F1T[(size_t)k * M + mode] = h.G1[(size_t)mode * nph + k];
+      h.GT[(size_t)mode * nph + k] = h.F[(size_t)k * M + mode];
+    }
+  h.Q0T.assign((size_t)(K + 1) * nth * nth, 0.0);
+  if (deriv) h.Q1T.assign((size_t)(K + 1) * nth * nth, 0.0);
+  for (int m = 0; m <= K; ++m)
+    for (int a = 0; a < nth; ++a)
+      for (int b = 0; b < nth; ++b) {
+        h.Q0T[((size_t)m * nth + a) * nth + b] = h.Q0[((size_t)m * nth + b) * nth + a];
+        if (deriv) h.Q1T[((size_t)m * nth + a) * nth + b] = h.Q1[((size_t)m * nth + b) * nth + a];
+      }
+}
 
 SepHost sep_plan(const AngularGrid& g, int K, bool deriv) {
   SepHost h;
@@ -272,7 +294,20 @@ SepHost sep_plan(const AngularGrid& g, int K, bool deriv) {
         h.Q0[((size_t)m * nth + ji) * nth + jo] = a0 * g.wgl[ji];
         if (deriv) h.Q1[((size_t)m * nth + ji) * nth + jo] = a1 * g.wgl[ji];
       }
+  sep_transpose(h, nth, nph, deriv);
   return h;
+}
+
+// Rows per block of the transposed separable kernel: inputs (2 or 1 rows of
+// Na), their analyses (2 or 1 of nth x M) and one Legendre output.
+int sep_adj_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
+  const size_t per_row = (two ? 2 : 1) * (size_t)na + (two ? 3 : 2) * (size_t)nth * M;
+  const size_t budget = 64 * 1024 / sizeof(double);
+  int rb = (int)(budget / per_row);
+  if (rb < 1) rb = 1;
+  if (rb > 64) rb = 64;
+  if (rb > n_rows) rb = n_rows;
+  return rb;
 }
 
 // Rows of one shell that a separable block holds in shared memory.
@@ -520,7 +555,9 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
 
   // matrix dictionary keyed by the parameters that make a map new (Sec. 3.4)
   std::map<int, std::pair<double*, double*>> radial_cache;              // n_r -> (D, F)
+  std::map<int, std::pair<double*, double*>> radial_t_cache;            // n_r -> (D^T, F^T)
   std::map<std::tuple<int, int, int>, gh::SepPlan> sep_cache;           // (L, K, kind) -> plan
+  std::map<std::tuple<int, int, int>, gh::SepAdjPlan> sep_adj_cache;    // its transpose
   std::map<int, AngularGrid> grids;
 
   long long off = 0, pts = 0;
@@ -552,36 +589,61 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     }
     sh.Dr = radial_cache[sh.n_r].first;
     sh.Fr = radial_cache[sh.n_r].second;
+    if (!radial_t_cache.count(sh.n_r)) {
+      auto tr = [](std::vector<double> m, int n) {
+        std::vector<double> t(m.size());
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) t[(size_t)j * n + i] = m[(size_t)i * n + j];
+        return t;
+      };
+      double *DT = nullptr, *FT = nullptr;
+      CREATE_CUDA(upload(d, tr(cgl_derivative_matrix(sh.n_r), sh.n_r), &DT));
+      CREATE_CUDA(upload(d, tr(cgl_filter_matrix(sh.n_r, params->filt_alpha, params->filt_order > 0 ? params->filt_order : 1), sh.n_r), &FT));
+      radial_t_cache[sh.n_r] = {DT, FT};
+    }
+    sh.DrT = radial_t_cache[sh.n_r].first;
+    sh.FrT = radial_t_cache[sh.n_r].second;
     if (!grids.count(sh.L)) grids[sh.L] = angular_grid(sh.L);
     const AngularGrid& ag = grids[sh.L];
     // separable angular plans, cached by (L, K, kind)
-    auto get_plan = [&](int K, bool deriv, gh::SepPlan& out) -> cudaError_t {
+    auto get_plan = [&](int K, bool deriv, gh::SepPlan& out, gh::SepAdjPlan& adj) -> cudaError_t {
       auto key = std::make_tuple(sh.L, K, deriv ? 1 : 0);
       if (!sep_cache.count(key)) {
         SepHost h = sep_plan(ag, K, deriv);
         gh::SepPlan P;
+        gh::SepAdjPlan T;
         std::memset(&P, 0, sizeof(P));
-        P.K = h.K;
-        P.M = h.M;
+        std::memset(&T, 0, sizeof(T));
+        P.K = T.K = h.K;
+        P.M = T.M = h.M;
         double* q = nullptr;
         cudaError_t e;
         if ((e = upload(d, h.F, &q)) != cudaSuccess) return e; P.F = q;
         if ((e = upload(d, h.G0, &q)) != cudaSuccess) return e; P.G0 = q;
         if ((e = upload(d, h.Q0, &q)) != cudaSuccess) return e; P.Q0 = q;
+        if ((e = upload(d, h.F0T, &q)) != cudaSuccess) return e; T.F0T = q;
+        if ((e = upload(d, h.Q0T, &q)) != cudaSuccess) return e; T.Q0T = q;
+        if ((e = upload(d, h.GT, &q)) != cudaSuccess) return e; T.GT = q;
         if (deriv) {
           if ((e = upload(d, h.G1, &q)) != cudaSuccess) return e; P.G1 = q;
           if ((e = upload(d, h.Q1, &q)) != cudaSuccess) return e; P.Q1 = q;
+          if ((e = upload(d, h.F1T, &q)) != cudaSuccess) return e; T.F1T = q;
+          if ((e = upload(d, h.Q1T, &q)) != cudaSuccess) return e; T.Q1T = q;
         }
         sep_cache[key] = P;
+        sep_adj_cache[key] = T;
       }
       out = sep_cache[key];
+      adj = sep_adj_cache[key];
       return cudaSuccess;
     };
-    CREATE_CUDA(get_plan(sh.L, true, sh.sd));
+    CREATE_CUDA(get_plan(sh.L, true, sh.sd, sh.sda));
     sh.sd.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sd.M, true, gh::NF * sh.n_r);
+    sh.sda.rows_per_cta = sep_adj_rows_per_block(sh.na, sh.nth, sh.sda.M, true, gh::NF * sh.n_r);
     if (sh.keep >= 0) {
-      CREATE_CUDA(get_plan(sh.keep, false, sh.sf));
+      CREATE_CUDA(get_plan(sh.keep, false, sh.sf, sh.sfa));
       sh.sf.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sf.M, false, gh::NF * sh.n_r);
+      sh.sfa.rows_per_cta = sep_adj_rows_per_block(sh.na, sh.nth, sh.sfa.M, false, gh::NF * sh.n_r);
     }
     // grid tables
     std::vector<double> x = cgl_points(sh.n_r), wcc = clenshaw_curtis(sh.n_r);
@@ -711,6 +773,33 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     CREATE_CUDA(upload(d, fb, &d->sf_block_begin_d));
     CREATE_CUDA(gh::sep_set_smem_limits(std::max(smd, smf)));
     CREATE_CUDA(gh::radial_set_smem_limits());
+    // transposed maps
+    std::vector<int> ab(n_shells + 1), afb(n_shells + 1);
+    int nab = 0, nafb = 0;
+    size_t sma = 0, smfa = 0;
+    for (int s = 0; s < n_shells; ++s) {
+      const gh::ShellDev& sh = d->shells_h[s];
+      const int rows = gh::NF * sh.n_r;
+      ab[s] = nab;
+      nab += (rows + sh.sda.rows_per_cta - 1) / sh.sda.rows_per_cta;
+      sma = std::max(sma, sizeof(double) * (size_t)sh.sda.rows_per_cta *
+                              (2 * (size_t)sh.na + 3 * (size_t)sh.nth * sh.sda.M));
+      afb[s] = nafb;
+      if (sh.sfa.M > 0) {
+        nafb += (rows + sh.sfa.rows_per_cta - 1) / sh.sfa.rows_per_cta;
+        smfa = std::max(smfa, sizeof(double) * (size_t)sh.sfa.rows_per_cta *
+                                  ((size_t)sh.na + 2 * (size_t)sh.nth * sh.sfa.M));
+      }
+    }
+    ab[n_shells] = nab;
+    afb[n_shells] = nafb;
+    d->sda_blocks = nab;
+    d->sfa_blocks = nafb;
+    d->sda_smem = sma;
+    d->sfa_smem = smfa;
+    CREATE_CUDA(upload(d, ab, &d->sda_block_begin_d));
+    CREATE_CUDA(upload(d, afb, &d->sfa_block_begin_d));
+    CREATE_CUDA(gh::sep_adj_set_smem_limits(std::max(sma, smfa)));
   }
 
   // scratch

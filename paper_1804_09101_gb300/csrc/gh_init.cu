@@ -6,6 +6,7 @@
 // operation), so d_i g_ab and d_i d_j g_ab are exact to rounding.
 #include <cuda_runtime.h>
 
+#include "gh_geom.cuh"
 #include "gh_internal.h"
 #include "gh_tensor.cuh"
 
@@ -174,31 +175,6 @@ kerr_schild_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
 }
 
 // ------------------------------------------------------- perturbations
-constexpr int PERT_LMAX = 16;
-
-// Normalised associated Legendre functions (orthonormal real harmonics, no
-// Condon-Shortley phase) and their theta derivatives from
-//   sin(th) dP_l^m/dth = l cos(th) P_l^m - sqrt((2l+1)(l^2-m^2)/(2l-1)) P_{l-1}^m.
-__device__ void legendre_table(int lmax, double ct, double st, double* P, double* dP) {
-  const int W = PERT_LMAX + 1;
-  for (int i = 0; i < W * W; ++i) { P[i] = 0.0; dP[i] = 0.0; }
-  P[0] = sqrt(0.25 / 3.14159265358979323846);
-  for (int m = 1; m <= lmax; ++m) P[m * W + m] = sqrt((2.0 * m + 1.0) / (2.0 * m)) * st * P[(m - 1) * W + m - 1];
-  for (int m = 0; m < lmax; ++m) P[(m + 1) * W + m] = sqrt(2.0 * m + 3.0) * ct * P[m * W + m];
-  for (int m = 0; m <= lmax; ++m)
-    for (int l = m + 2; l <= lmax; ++l) {
-      const double al = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
-      const double bl = sqrt((((double)l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
-      P[l * W + m] = al * (ct * P[(l - 1) * W + m] - bl * P[(l - 2) * W + m]);
-    }
-  for (int l = 0; l <= lmax; ++l)
-    for (int m = 0; m <= l; ++m) {
-      const double prev = (l > m) ? P[(l - 1) * W + m] : 0.0;
-      const double c = (l > m) ? sqrt((2.0 * l + 1.0) * ((double)l * l - (double)m * m) / (2.0 * l - 1.0)) : 0.0;
-      dP[l * W + m] = (l * ct * P[l * W + m] - c * prev) / st;
-    }
-}
-
 __global__ void __launch_bounds__(64)
 perturbation_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                     int kind, double A, double Rc, double w, int lmax,

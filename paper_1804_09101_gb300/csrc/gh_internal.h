@@ -28,6 +28,20 @@ struct SepPlan {
   const double* Q1;             // [K+1][nth_in][nth_out] Legendre map for output 1
 };
 
+// Transposed separable map (for the adjoint): analysis with the transposed
+// synthesis matrices, Legendre maps with theta_in/theta_out swapped, synthesis
+// with the transposed DFT.  Two inputs (the d/dtheta and d/dphi cotangents)
+// for the derivative plan, one for the filter.
+struct SepAdjPlan {
+  int K, M;
+  int rows_per_cta, pad;
+  const double* F0T;            // [nph][M]
+  const double* F1T;            // [nph][M]  (derivative plan only)
+  const double* Q0T;            // [K+1][nth][nth]
+  const double* Q1T;            // [K+1][nth][nth]  (derivative plan only)
+  const double* GT;             // [M][nph]
+};
+
 // One shell as the kernels see it (device-resident array of these).
 struct ShellDev {
   int n_r, L, nth, nph, na;     // na = nth * nph angular points
@@ -55,6 +69,10 @@ struct ShellDev {
   double dt_scale;              // this hole's step = dt * dt_scale
   SepPlan sd;                   // separable d/dtheta, d/dphi
   SepPlan sf;                   // separable SH truncation filter (M = 0 if off)
+  SepAdjPlan sda;               // transpose of sd
+  SepAdjPlan sfa;               // transpose of sf (M = 0 if off)
+  const double* DrT;            // [n_r][n_r] transpose of Dr
+  const double* FrT;            // [n_r][n_r] transpose of Fr
 };
 
 // A boundary slice: the outer boundary of the last shell (kind 0) or an
@@ -117,6 +135,11 @@ struct gh_domain {
   std::vector<void*> owned;      // every device allocation, freed on destroy
   std::string err;
   long long launches = 0;
+  // adjoint: separable transposed-map launch maps and a cotangent scratch state
+  int* sda_block_begin_d = nullptr; int sda_blocks = 0; size_t sda_smem = 0;
+  int* sfa_block_begin_d = nullptr; int sfa_blocks = 0; size_t sfa_smem = 0;
+  double* kbt = nullptr;        // one state, allocated by the first adjoint call
+  double* pert_partial = nullptr; int pert_partial_len = 0;
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_step_launches = 0;
@@ -138,6 +161,7 @@ cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph);
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
+cudaError_t sep_adj_set_smem_limits(size_t bytes);
 cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const double* dr, const double* dth,
                                       const double* dph, double* k);
 cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage, double dt,

@@ -10,19 +10,11 @@
 // is to keep the FP64 pipe busy, not to save HBM traffic.
 #include <cuda_runtime.h>
 
+#include "gh_geom.cuh"
 #include "gh_internal.h"
 #include "gh_tensor.cuh"
 
 namespace gh {
-
-// ---------------------------------------------------------------------------
-// Block -> shell lookup: begin[s] is the first block of shell s, begin[n] the
-// total.  n is small (tens), so a linear scan is enough.
-__device__ __forceinline__ int find_segment(const int* begin, int n, int b) {
-  int s = 0;
-  while (s + 1 < n && begin[s + 1] <= b) ++s;
-  return s;
-}
 
 // ---------------------------------------------------------------------------
 // Radial contraction (the R part of Eq. DifferentiatorI1S2, and the radial
@@ -274,29 +266,6 @@ cudaError_t sep_set_smem_limits(size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(sep_angular_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sep_angular_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// ---------------------------------------------------------------------------
-// Geometry of one point: the DiffJac matrix J[i][d] = d(x_d)/d(x^i) for the
-// spherical coordinates (r, theta, phi), with the radial column multiplied by
-// dx/dr so that it acts on the CGL-coordinate derivative (Eq. DiffJac).
-struct PointGeom {
-  double J[3][3];
-  double xhat[3];  // x^i / R
-  double r;
-};
-
-__device__ __forceinline__ void point_geom(const ShellDev& sh, int ir, int q, PointGeom& g) {
-  const int j = q / sh.nph, k = q - j * sh.nph;
-  const double r = sh.r[ir];
-  const double ct = sh.cth[j], st = sh.sth[j], cp = sh.cph[k], sp = sh.sph[k];
-  const double ir_ = 1.0 / r;
-  const double irs = ir_ / st;
-  g.r = r;
-  g.xhat[0] = st * cp; g.xhat[1] = st * sp; g.xhat[2] = ct;
-  g.J[0][0] = st * cp * sh.rscale; g.J[0][1] = ct * cp * ir_; g.J[0][2] = -sp * irs;
-  g.J[1][0] = st * sp * sh.rscale; g.J[1][1] = ct * sp * ir_; g.J[1][2] = cp * irs;
-  g.J[2][0] = ct * sh.rscale;      g.J[2][1] = -st * ir_;     g.J[2][2] = 0.0;
 }
 
 // ---------------------------------------------------------------------------

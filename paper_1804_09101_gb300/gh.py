@@ -70,6 +70,11 @@ def _load():
         "gh_constraints": ([P, P, P, P], I),
         "gh_sync": ([P], I),
         "gh_set_algorithm": ([P, I], I),
+        "gh_rhs_vjp": ([P, P, P, P], I),
+        "gh_rk4_vjp_work_size": ([P], ctypes.c_longlong),
+        "gh_rk4_step_vjp": ([P, D, P, P, P, P], I),
+        "gh_constraint_energy_vjp": ([P, P, D, P], I),
+        "gh_perturbation_vjp": ([P, I, D, D, I, P, P], I),
         "gh_profile_enable": ([P, I], I),
         "gh_profile_read": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
     }
@@ -117,6 +122,7 @@ class Domain:
         self.state_size = _lib.gh_state_size(h)
         self.num_points = _lib.gh_num_points(h)
         self.work_size = _lib.gh_rk4_work_size(h)
+        self.vjp_work_size = _lib.gh_rk4_vjp_work_size(h)
 
     @classmethod
     def from_workload(cls, w):
@@ -254,6 +260,42 @@ GH_ALG_DENSE, GH_ALG_SEPARABLE = 0, 1
 def gh_set_algorithm(dom, algorithm):
     dom._stream()
     dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
+
+
+def gh_rhs_vjp(dom, u, kbar, ubar):
+    """ubar += (dF/du)^T kbar for F = gh_rhs."""
+    dom._stream()
+    dom._check(_lib.gh_rhs_vjp(dom.handle, _ptr(u, "u", dom.state_size), _ptr(kbar, "kbar", dom.state_size),
+                               _ptr(ubar, "ubar", dom.state_size)))
+
+
+def gh_rk4_step_vjp(dom, dt, u_n, ubar_np1, ubar_n, work):
+    """ubar_n = (d step/d u_n)^T ubar_np1."""
+    dom._stream()
+    dom._check(_lib.gh_rk4_step_vjp(dom.handle, float(dt), _ptr(u_n, "u_n", dom.state_size),
+                                    _ptr(ubar_np1, "ubar_np1", dom.state_size), _ptr(ubar_n, "ubar_n", dom.state_size),
+                                    _ptr(work, "work", dom.vjp_work_size)))
+
+
+def gh_constraint_energy_vjp(dom, u, weight, ubar):
+    """ubar += weight * d(sum of the shells' constraint norms)/du."""
+    dom._stream()
+    dom._check(_lib.gh_constraint_energy_vjp(dom.handle, _ptr(u, "u", dom.state_size), float(weight),
+                                             _ptr(ubar, "ubar", dom.state_size)))
+
+
+def gh_perturbation_vjp(dom, kind, Rc, w, lmax, ubar):
+    """Gradient of <ubar, u> with respect to the perturbation coefficients (numpy array)."""
+    import numpy as np
+    g = np.zeros((lmax + 1) ** 2)
+    dom._stream()
+    dom._check(_lib.gh_perturbation_vjp(dom.handle, int(kind), float(Rc), float(w), int(lmax),
+                                        _ptr(ubar, "ubar", dom.state_size), g.ctypes.data_as(ctypes.c_void_p)))
+    return g
+
+
+def new_vjp_work(dom):
+    return torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda")
 
 
 def gh_sync(dom):

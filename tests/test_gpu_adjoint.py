@@ -1,0 +1,182 @@
+"""The library's vector-Jacobian products against finite differences of its
+own forward path and of the oracle, and the gradient of the time-integrated
+constraint energy with respect to the Pi-mode coefficients against central
+finite differences (the adjoint workload)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import evolve
+from paper_1804_09101_gb300 import workloads
+from parity_helpers import flat, unflat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
+
+pytestmark = pytest.mark.gpu
+
+
+def _kerr2():
+    return workloads.Workload(name="kerr2", shells=[(1.3, 3.0, 9, 7), (3.0, 6.0, 9, 7)], M=1.0, chi=0.9,
+                              radial_filter_on=True, sh_keep_l=4, dt=0.005, seed=7, noise_amp=1e-6,
+                              pulse=workloads.Pulse("psi_pulse", 1e-3, 4.0, 1.0, 2, workloads.random_coeffs(7, 2)))
+
+
+def _setup(w):
+    odom = oracle_domain(w)
+    u0 = flat(oracle_initial_state(w, odom))
+    dom = gpu_domain(w, odom)
+    return odom, u0, dom
+
+
+@pytest.mark.parametrize("wname", ["schwarzschild", "kerr2"])
+def test_rhs_vjp_dot_product_against_finite_differences(wname):
+    """<v, J w> by central differences of gh_rhs equals <J^T v, w> from gh_rhs_vjp."""
+    from paper_1804_09101_gb300 import gh
+    w = workloads.schwarzschild_single_shell() if wname == "schwarzschild" else _kerr2()
+    odom, u0, dom = _setup(w)
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(u0.shape)
+    dw = rng.standard_normal(u0.shape)
+    h = 1e-6
+    kp, km = dom.new_state(), dom.new_state()
+    gh.gh_rhs(dom, to_dev(u0 + h * dw), kp)
+    gh.gh_rhs(dom, to_dev(u0 - h * dw), km)
+    jw = (to_host(kp) - to_host(km)) / (2 * h)
+    ub = dom.new_state()
+    gh.gh_rhs_vjp(dom, to_dev(u0), to_dev(v), ub)
+    lhs, rhs = float(v @ jw), float(to_host(ub) @ dw)
+    assert abs(lhs - rhs) <= 1e-6 * max(abs(lhs), 1e-30), (lhs, rhs)
+
+
+def test_rhs_vjp_against_the_oracle_directional_derivative():
+    """The same identity with J w from central differences of the oracle's RHS."""
+    from paper_1804_09101_gb300 import gh
+    w = _kerr2()
+    odom, u0, dom = _setup(w)
+    rng = np.random.default_rng(6)
+    v = rng.standard_normal(u0.shape)
+    dw = rng.standard_normal(u0.shape)
+    h = 1e-6
+    jw = (flat(evolve.rhs(odom, unflat(u0 + h * dw, odom))) - flat(evolve.rhs(odom, unflat(u0 - h * dw, odom)))) / (2 * h)
+    ub = dom.new_state()
+    gh.gh_rhs_vjp(dom, to_dev(u0), to_dev(v), ub)
+    lhs, rhs = float(v @ jw), float(to_host(ub) @ dw)
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs), (lhs, rhs)
+
+
+@pytest.mark.parametrize("wname", ["schwarzschild", "kerr2"])
+def test_rk4_step_vjp_dot_product(wname):
+    from paper_1804_09101_gb300 import gh
+    w = workloads.schwarzschild_single_shell() if wname == "schwarzschild" else _kerr2()
+    odom, u0, dom = _setup(w)
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(u0.shape)
+    dw = rng.standard_normal(u0.shape)
+    h = 1e-6
+    work = dom.new_work()
+    up, um = to_dev(u0 + h * dw), to_dev(u0 - h * dw)
+    gh.gh_rk4_step(dom, w.dt, up, work)
+    gh.gh_rk4_step(dom, w.dt, um, work)
+    jw = (to_host(up) - to_host(um)) / (2 * h)
+    ub = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, w.dt, to_dev(u0), to_dev(v), ub, gh.new_vjp_work(dom))
+    lhs, rhs = float(v @ jw), float(to_host(ub) @ dw)
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs), (lhs, rhs)
+
+
+def test_constraint_energy_vjp():
+    from paper_1804_09101_gb300 import gh
+    from paper_1804_09101_gb300.adjoint import constraint_energy
+    w = _kerr2()
+    odom, u0, dom = _setup(w)
+    rng = np.random.default_rng(8)
+    dw = rng.standard_normal(u0.shape) * 1e-3
+    h = 1e-4
+    fd = (constraint_energy(dom, to_dev(u0 + h * dw)) - constraint_energy(dom, to_dev(u0 - h * dw))) / (2 * h)
+    ub = dom.new_state()
+    gh.gh_constraint_energy_vjp(dom, to_dev(u0), 1.0, ub)
+    an = float(to_host(ub) @ dw)
+    assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
+def _adjoint_setup(n_r=11, L=7, steps=200):
+    from paper_1804_09101_gb300 import gh
+    w = workloads.adjoint_single_shell()
+    dom = gh.Domain([(1.8, 10.0, n_r, L)])
+    base = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, base)
+    p = w.pulse
+
+    def state(c):
+        u = base.clone()
+        gh.gh_add_perturbation(dom, 1, 1.0, p.center, p.width, p.lmax, c, u)
+        return u
+    return w, dom, state, p
+
+
+@pytest.mark.parametrize("steps", [20, 200])
+def test_energy_gradient_wrt_pi_mode_coefficients_matches_central_fd(steps):
+    """The adjoint workload: 16 l <= 3 coefficients on Pi, E = sum over the
+    steps of dt * constraint energy, checkpoints every 20 steps; every
+    gradient entry against central differences with h = 1e-6."""
+    from paper_1804_09101_gb300 import gh
+    from paper_1804_09101_gb300.adjoint import constraint_energy_gradient, evolve_energy
+    w, dom, state, p = _adjoint_setup()
+    c0 = np.asarray(p.coeffs, float)
+    E, lam = constraint_energy_gradient(dom, state(c0), w.dt, steps, ckpt=20)
+    g = gh.gh_perturbation_vjp(dom, 1, p.center, p.width, p.lmax, lam)
+    h = 1e-6
+    gfd = np.zeros(16)
+    for k in range(16):
+        e = np.zeros(16)
+        e[k] = h
+        gfd[k] = (evolve_energy(dom, state(c0 + e), w.dt, steps) - evolve_energy(dom, state(c0 - e), w.dt, steps)) / (2 * h)
+    scale = np.abs(gfd).max()
+    assert np.abs(g - gfd).max() <= 1e-6 * scale, (g, gfd)
+
+
+def test_energy_gradient_matches_oracle_fd_on_a_tiny_grid():
+    """Tiny grid (N_r = 5, L = 3), 3 steps: the library's adjoint gradient
+    against central differences of the oracle's own evolution."""
+    from paper_1804_09101_gb300 import gh
+    from paper_1804_09101_gb300.adjoint import constraint_energy_gradient
+    from oracle import perturb
+    w, dom, state, p = _adjoint_setup(n_r=5, L=3)
+    c0 = np.asarray(p.coeffs, float)
+    steps = 3
+    E, lam = constraint_energy_gradient(dom, state(c0), w.dt, steps, ckpt=2)
+    g = gh.gh_perturbation_vjp(dom, 1, p.center, p.width, p.lmax, lam)
+    odom = evolve.Domain([(1.8, 10.0, 5, 3)], w.M, w.chi)
+
+    def oracle_E(c):
+        u = [odom.u_exact[0] + perturb.pi_modes(odom.grids[0], p.center, p.width, p.lmax, c)]
+        return evolve.constraint_energy(odom, u, w.dt, steps)
+    h = 1e-6
+    gfd = np.zeros(16)
+    for k in range(16):
+        e = np.zeros(16)
+        e[k] = h
+        gfd[k] = (oracle_E(c0 + e) - oracle_E(c0 - e)) / (2 * h)
+    assert np.abs(g - gfd).max() <= 1e-6 * np.abs(gfd).max(), (g, gfd)
+
+
+def test_autograd_functions_chain():
+    """RK4Step and ConstraintEnergy compose under torch.autograd."""
+    from paper_1804_09101_gb300 import gh
+    from paper_1804_09101_gb300.adjoint import RK4Step, ConstraintEnergy, constraint_energy
+    w = _kerr2()
+    odom, u0, dom = _setup(w)
+    x = to_dev(u0).requires_grad_(True)
+    y = RK4Step.apply(RK4Step.apply(x, dom, w.dt), dom, w.dt)
+    loss = ConstraintEnergy.apply(y, dom)
+    loss.backward()
+    dw = np.random.default_rng(9).standard_normal(u0.shape) * 1e-3
+    h = 1e-4
+
+    def f(u):
+        t = to_dev(u)
+        work = dom.new_work()
+        gh.gh_rk4_step(dom, w.dt, t, work)
+        gh.gh_rk4_step(dom, w.dt, t, work)
+        return constraint_energy(dom, t)
+    fd = (f(u0 + h * dw) - f(u0 - h * dw)) / (2 * h)
+    an = float(to_host(x.grad) @ dw)
+    assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
