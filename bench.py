@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="kerr4", choices=["kerr4", "large", "schwarzschild", "batched"],
+    p.add_argument("--workload", default="kerr4",
+                   choices=["kerr4", "large", "schwarzschild", "batched", "adjoint"],
                    help="kerr4: 4-shell Kerr a=0.9 (default, the headline); large: 8-shell Kerr a=0.95, "
                         "N_r=41, L=31; schwarzschild: 1 shell N_r=11, L=7; batched: 64 independent "
                         "single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
@@ -424,12 +425,73 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Adjoint workload: gradient of the 200-step time-integrated constraint
+    energy with respect to 16 Pi-mode coefficients (checkpoints every 20 steps),
+    timed against the forward evolution that defines it."""
+    import numpy as np
+    import torch
+    from paper_1804_09101_gb300 import build
+    build.build()
+    from paper_1804_09101_gb300 import gh, workloads
+    from paper_1804_09101_gb300.adjoint import constraint_energy_gradient, evolve_energy
+    w = workloads.adjoint_single_shell()
+    dom = gh.Domain.from_workload(w)
+    u0 = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u0)
+    p = w.pulse
+    gh.gh_add_perturbation(dom, 1, 1.0, p.center, p.width, p.lmax, p.coeffs, u0)
+    steps = w.steps
+    for _ in range(max(1, args.warmup // 3)):
+        evolve_energy(dom, u0, w.dt, steps)
+        constraint_energy_gradient(dom, u0, w.dt, steps, ckpt=20)
+    reps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        E = evolve_energy(dom, u0, w.dt, steps)
+    torch.cuda.synchronize()
+    fwd = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        E2, lam = constraint_energy_gradient(dom, u0, w.dt, steps, ckpt=20)
+        g = gh.gh_perturbation_vjp(dom, 1, p.center, p.width, p.lmax, lam)
+    torch.cuda.synchronize()
+    bwd = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        E3, lam3 = constraint_energy_gradient(dom, u0, w.dt, steps, ckpt=steps)
+    torch.cuda.synchronize()
+    bwd_all = (time.perf_counter() - t0) / reps
+    pts = w.points()
+    line = dict(metric=METRIC, value=pts * 4 * steps / fwd, unit=UNIT, n_gpus=1, steps=reps, warmup=args.warmup,
+                ms_per_step=1000.0 * fwd / steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=w.name, points=pts, evolution_steps=steps, checkpoint_every=20,
+                            parameters=16, forward_s=fwd, gradient_s=bwd, adjoint_over_forward=bwd / fwd,
+                            backward_over_forward=(bwd - fwd) / fwd,
+                            keep_all_states_gradient_s=bwd_all,
+                            keep_all_states_backward_over_forward=(bwd_all - fwd) / fwd,
+                            energy=E, grad_norm=float(np.linalg.norm(g)),
+                            timing="wall clock around whole evolutions (host-driven launches), "
+                                   "mean of %d repetitions; gradient_s includes its own forward pass, "
+                                   "backward_over_forward excludes it (backward incl. checkpoint "
+                                   "recomputation)" % reps))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     from paper_1804_09101_gb300 import workloads
     w = {"kerr4": workloads.kerr_four_shells, "large": workloads.kerr_eight_shells_large,
          "schwarzschild": workloads.schwarzschild_single_shell,
-         "batched": workloads.kerr_four_shells}[args.workload]()
+         "batched": workloads.kerr_four_shells, "adjoint": workloads.kerr_four_shells}[args.workload]()
+    if args.workload == "adjoint":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no oracle arm"}))
+            return
+        run_adjoint(args)
+        return
     if args.workload == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle arm"}))

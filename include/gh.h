@@ -218,6 +218,16 @@ long long gh_rk4_vjp_work_size(const gh_domain* dom);
 gh_status gh_rk4_step_vjp(gh_domain* dom, double dt, const double* u_n, const double* ubar_np1,
                           double* ubar_n, double* work);
 
+/* The same step with its three intermediate stage states (u_n + dt/2 k1,
+ * u_n + dt/2 k2, u_n + dt k3) written to stages (3 states, device), and the
+ * step VJP that reuses them instead of recomputing them.  The latter also adds
+ * cweight * d/du (sum of the shells' constraint norms) at u_n to ubar_n, which
+ * shares the derivative passes with the last stage (0: no such term). */
+gh_status gh_rk4_step_save(gh_domain* dom, double dt, double* u, double* work, double* norm2_pre,
+                           double* stages);
+gh_status gh_rk4_step_vjp_saved(gh_domain* dom, double dt, const double* u_n, const double* stages,
+                                const double* ubar_np1, double* ubar_n, double* work, double cweight);
+
 /* ubar += weight * d/du (sum over shells of the constraint norm that
  * gh_constraints writes to norm2). */
 gh_status gh_constraint_energy_vjp(gh_domain* dom, const double* u, double weight, double* ubar);

@@ -62,16 +62,17 @@ def constraint_energy(dom, u):
 
 
 def evolve_energy(dom, u0, dt, n_steps):
-    """E = sum_{n=1..N} dt * sum_shells norm2(u_n) (forward only)."""
+    """E = sum_{n=1..N} dt * sum_shells norm2(u_n) (forward only).  The norm of
+    u_n (n < N) comes out of the first stage of step n+1 (gh_rk4_step's
+    norm2_pre); u_N takes one gh_constraints call."""
     u = u0.clone()
     work = dom.new_work()
-    n2 = torch.zeros(len(dom.shells), dtype=torch.float64, device=u.device)
-    acc = torch.zeros((), dtype=torch.float64, device=u.device)
-    for _ in range(n_steps):
-        gh.gh_rk4_step(dom, dt, u, work)
-        gh.gh_constraints(dom, u, None, n2)
-        acc += dt * n2.sum()
-    return float(acc)
+    ns = len(dom.shells)
+    norms = torch.zeros((n_steps + 1, ns), dtype=torch.float64, device=u.device)
+    for n in range(n_steps):
+        gh.gh_rk4_step(dom, dt, u, work, norms[n])          # norms[n] = C(u_n)
+    gh.gh_constraints(dom, u, None, norms[n_steps])
+    return float(dt * norms[1:].sum())
 
 
 def constraint_energy_gradient(dom, u0, dt, n_steps, ckpt=20):
@@ -79,32 +80,51 @@ def constraint_energy_gradient(dom, u0, dt, n_steps, ckpt=20):
     checkpoints every ckpt steps.
 
     Adjoint recursion: lam_N = dt grad C(u_N); lam_n = dt grad C(u_n) +
-    S'(u_n)^T lam_{n+1}; dE/du_0 = S'(u_0)^T lam_1.  The reverse pass walks the
-    segments (a, b] backwards, recomputing u_a..u_b from the checkpoint u_a.
+    S'(u_n)^T lam_{n+1}; dE/du_0 = S'(u_0)^T lam_1.  The forward pass keeps the
+    checkpoints u_0, u_ckpt, ... and, for the last segment, every state and its
+    RK4 stage states; the reverse pass walks the segments (a, b] backwards,
+    recomputing the other segments' states and stages from their checkpoints.
     """
     work = dom.new_work()
     vwork = gh.new_vjp_work(dom)
-    n2 = torch.zeros(len(dom.shells), dtype=torch.float64, device=u0.device)
+    N = dom.state_size
+    ns = len(dom.shells)
+    norms = torch.zeros((n_steps + 1, ns), dtype=torch.float64, device=u0.device)
+    last = ((n_steps - 1) // ckpt) * ckpt          # start of the last segment
     checkpoints = {0: u0.clone()}
     u = u0.clone()
-    E = torch.zeros((), dtype=torch.float64, device=u0.device)
+    saved_states, saved_stages = None, None
     for n in range(1, n_steps + 1):
-        gh.gh_rk4_step(dom, dt, u, work)
-        gh.gh_constraints(dom, u, None, n2)
-        E += dt * n2.sum()
+        if n - 1 == last:
+            saved_states = [u.clone()]
+            saved_stages = torch.empty((n_steps - last, 3 * N), dtype=torch.float64, device=u0.device)
+        if n - 1 >= last:
+            gh.gh_rk4_step_save(dom, dt, u, work, saved_stages[n - 1 - last], norms[n - 1])
+            saved_states.append(u.clone())
+        else:
+            gh.gh_rk4_step(dom, dt, u, work, norms[n - 1])
         if n % ckpt == 0 and n < n_steps:
             checkpoints[n] = u.clone()
+    gh.gh_constraints(dom, u, None, norms[n_steps])
+    E = float(dt * norms[1:].sum())
     lam = torch.zeros_like(u0)
     nxt = torch.zeros_like(u0)
     for a in sorted(checkpoints, reverse=True):
         b = min(a + ckpt, n_steps)
-        states = [checkpoints[a]]
-        s = checkpoints[a].clone()
-        for _ in range(a, b):
-            gh.gh_rk4_step(dom, dt, s, work)
-            states.append(s.clone())
+        if a == last:
+            states, stages = saved_states, saved_stages
+        else:
+            states = [checkpoints[a]]
+            stages = torch.empty((b - a, 3 * N), dtype=torch.float64, device=u0.device)
+            s = checkpoints[a].clone()
+            for i in range(a, b):
+                gh.gh_rk4_step_save(dom, dt, s, work, stages[i - a])
+                states.append(s.clone())
+        if b == n_steps:
+            gh.gh_constraint_energy_vjp(dom, states[b - a], dt, lam)      # lam_N = dt grad C(u_N)
         for n in range(b, a, -1):
-            gh.gh_constraint_energy_vjp(dom, states[n - a], dt, lam)
-            gh.gh_rk4_step_vjp(dom, dt, states[n - 1 - a], lam, nxt, vwork)
+            # lam_{n-1} = S'(u_{n-1})^T lam_n + dt grad C(u_{n-1}) (no C term for u_0)
+            cw = dt if n - 1 >= 1 else 0.0
+            gh.gh_rk4_step_vjp_saved(dom, dt, states[n - 1 - a], stages[n - 1 - a], lam, nxt, vwork, cw)
             lam, nxt = nxt, lam
-    return float(E), lam
+    return E, lam

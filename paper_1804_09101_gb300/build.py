@@ -47,8 +47,9 @@ def build(verbose=False, force=False):
 
     def compile_one(pair):
         src, obj = pair
-        cmd = [nvcc] + ARCH + FLAGS + ["-I", os.path.join(os.path.dirname(HERE), "include"),
-                                       "-c", src, "-o", obj]
+        extra = os.environ.get("GH_NVCC_EXTRA", "").split()
+        cmd = [nvcc] + ARCH + FLAGS + extra + ["-I", os.path.join(os.path.dirname(HERE), "include"),
+                                               "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))

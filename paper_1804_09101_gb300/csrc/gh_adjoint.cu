@@ -236,14 +236,24 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
 // with the derivative cotangents (each thread reads its own values first).
 // MODE 0: cotangent kb of dudt (before the boundary conditions).
 // MODE 1: gradient of weight * sum_points w_quadrature * (constraint energy).
+// MODE 2: both (the RHS cotangent and the constraint-energy gradient at u).
 constexpr int ADJ_PT_THREADS = 64;
 
+// The constraint-energy gradient as a separate (not inlined) call, so that the
+// fused kernel does not hold both reverse passes' locals at once.
+__device__ __noinline__ void constraint_part(const PointIn& in, double w, double* ub, double* dsb) {
+  point_constraint_energy(in, w, ub, dsb);
+}
+
+#ifndef GH_ADJ_MINB
+#define GH_ADJ_MINB 8
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(ADJ_PT_THREADS)
+__global__ void __launch_bounds__(ADJ_PT_THREADS, GH_ADJ_MINB)
 pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                          const double* __restrict__ u, double* dr, double* dth, double* dph,
                          const double* __restrict__ kb, double* ubar, double g0, double g1, double g2,
-                         double weight) {
+                         double weight, int assign) {
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int na = sh.na;
@@ -279,19 +289,24 @@ pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, cons
   in.g0 = g0;
   in.g1 = g1;
   in.g2 = g2;
-  if (MODE == 0) {
-    double kk[50], out[50];
+  if (MODE == 0 || MODE == 2) {
+    double kk[50];
     for (int f = 0; f < NF; ++f) kk[f] = kb[base + (long long)f * na];
     PointFwd fw;
-    point_rhs(in, fw, out);
+    point_intermediates(in, fw);
     point_rhs_vjp(in, fw, kk, ub, dsb);
-  } else {
+  }
+  if (MODE == 1) {
     const int j = q / sh.nph;
     point_constraint_energy(in, weight * sh.wr[ir] * sh.wth[j], ub, dsb);
   }
+  if (MODE == 2) {
+    const int j = q / sh.nph;
+    constraint_part(in, weight * sh.wr[ir] * sh.wth[j], ub, dsb);
+  }
   for (int f = 0; f < NF; ++f) {
     const long long o = base + (long long)f * na;
-    ubar[o] += ub[f];
+    ubar[o] = assign ? ub[f] : ubar[o] + ub[f];
     dr[o] = dsb[3 * f];
     dth[o] = dsb[3 * f + 1];
     dph[o] = dsb[3 * f + 2];
@@ -302,10 +317,11 @@ pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, cons
 // Element-wise combinations with the per-hole step dts = dt * dt_scale(shell),
 // one thread per (field, theta, phi) column of a shell.
 //   0: out = x + c * dts * y        1: out = dts * (a x + c y)        2: out += x
+//   3: out = dts * (a x + c y) and z += y
 __global__ void __launch_bounds__(128)
 ew_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin, int mode,
           double* __restrict__ out, const double* __restrict__ x, const double* __restrict__ y, double a,
-          double c, double dt) {
+          double c, double dt, double* __restrict__ z) {
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const long long cols = (long long)NF * sh.na;
@@ -316,7 +332,12 @@ ew_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restri
     const long long o = sh.off + (long long)r * cols + col;
     if (mode == 0) out[o] = x[o] + c * dts * y[o];
     else if (mode == 1) out[o] = dts * (a * x[o] + c * y[o]);
-    else out[o] += x[o];
+    else if (mode == 2) out[o] += x[o];
+    else {
+      const double yv = y[o];
+      out[o] = dts * (a * x[o] + c * yv);
+      z[o] += yv;
+    }
   }
 }
 
@@ -407,9 +428,9 @@ gh_status adj_ready(gh_domain* d) {
 }
 
 cudaError_t ew(gh_domain* d, int mode, double* out, const double* x, const double* y, double a, double c,
-               double dt) {
+               double dt, double* z = nullptr) {
   gh::ew_kernel<<<d->rad_blocks, 128, 0, d->stream>>>(d->shells_d, d->n_shells, d->rad_block_begin_d, mode, out,
-                                                      x, y, a, c, dt);
+                                                      x, y, a, c, dt, z);
   d->launches++;
   return cudaGetLastError();
 }
@@ -434,19 +455,10 @@ cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {
   return cudaGetLastError();
 }
 
-int adj_pt_blocks(gh_domain* d, std::vector<int>& begin) {
-  int b = 0;
-  begin.resize(d->n_shells + 1);
-  for (int s = 0; s < d->n_shells; ++s) {
-    begin[s] = b;
-    b += d->shells_h[s].n_r * ((d->shells_h[s].na + gh::ADJ_PT_THREADS - 1) / gh::ADJ_PT_THREADS);
-  }
-  begin[d->n_shells] = b;
-  return b;
-}
-
-// ubar += J(u)^T kb; kb is not modified.
-gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar) {
+// ubar (+)= J(u)^T kb (+ cweight * grad of the constraint energy at u when
+// cweight != 0); assign: overwrite ubar instead of adding; kb is not modified.
+gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar, double cweight = 0.0,
+                  bool assign = false) {
   GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
   if (d->bc_points) {
@@ -455,17 +467,16 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar)
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
-  static thread_local std::vector<int> begin;
-  const int blocks = adj_pt_blocks(d, begin);
-  int* bd = nullptr;
-  GH_ACUDA(d, cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream));
-  GH_ACUDA(d, cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream));
-  gh::pointwise_adjoint_kernel<0><<<blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
-      d->shells_d, d->n_shells, bd, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar, d->params.gamma0,
-      d->params.gamma1, d->params.gamma2, 0.0);
+  if (cweight != 0.0)
+    gh::pointwise_adjoint_kernel<2><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+        d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
+        d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight, assign ? 1 : 0);
+  else
+    gh::pointwise_adjoint_kernel<0><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+        d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
+        d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0);
   d->launches++;
   GH_ACUDA(d, cudaGetLastError());
-  GH_ACUDA(d, cudaFreeAsync(bd, d->stream));
   GH_ACUDA(d, derivs_transpose_add(d, ubar));
   return GH_OK;
 }
@@ -494,40 +505,47 @@ gh_status gh_constraint_energy_vjp(gh_domain* d, const double* u, double weight,
   if (!d || !u || !ubar) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
   if (gh_status s = adj_ready(d)) return s;
   GH_ACUDA(d, fwd_derivs(d, u));
-  static thread_local std::vector<int> begin;
-  const int blocks = adj_pt_blocks(d, begin);
-  int* bd = nullptr;
-  GH_ACUDA(d, cudaMallocAsync(&bd, sizeof(int) * begin.size(), d->stream));
-  GH_ACUDA(d, cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream));
-  gh::pointwise_adjoint_kernel<1><<<blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
-      d->shells_d, d->n_shells, bd, u, d->d_r, d->d_th, d->d_ph, nullptr, ubar, d->params.gamma0,
-      d->params.gamma1, d->params.gamma2, weight);
+  gh::pointwise_adjoint_kernel<1><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+      d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, nullptr, ubar,
+      d->params.gamma0, d->params.gamma1, d->params.gamma2, weight, 0);
   d->launches++;
   GH_ACUDA(d, cudaGetLastError());
-  GH_ACUDA(d, cudaFreeAsync(bd, d->stream));
   GH_ACUDA(d, derivs_transpose_add(d, ubar));
   return GH_OK;
 }
 
-gh_status gh_rk4_step_vjp(gh_domain* d, double dt, const double* u_n, const double* ubar_np1, double* ubar_n,
-                          double* work) {
-  if (!d || !u_n || !ubar_np1 || !ubar_n || !work) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+}  // extern "C"
+
+namespace {
+
+gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double* stages, const double* ubar_np1,
+                        double* ubar_n, double* work, double cweight) {
   if (gh_status s = adj_ready(d)) return s;
   const long long N = d->state;
-  double* u2 = work;
-  double* u3 = work + N;
-  double* u4 = work + 2 * N;
+  const double *u2, *u3, *u4;
   double* k = work + 3 * N;
   double* kb = work + 4 * N;
   double* g = work + 5 * N;
   double* sb = work + 6 * N;
-  // forward recomputation of the stage states
-  if (gh_status s = rhs_fwd(d, u_n, k)) return s;
-  GH_ACUDA(d, ew(d, 0, u2, u_n, k, 0.0, 0.5, dt));
-  if (gh_status s = rhs_fwd(d, u2, k)) return s;
-  GH_ACUDA(d, ew(d, 0, u3, u_n, k, 0.0, 0.5, dt));
-  if (gh_status s = rhs_fwd(d, u3, k)) return s;
-  GH_ACUDA(d, ew(d, 0, u4, u_n, k, 0.0, 1.0, dt));
+  if (stages) {
+    u2 = stages;
+    u3 = stages + N;
+    u4 = stages + 2 * N;
+  } else {
+    // forward recomputation of the stage states
+    double* w2 = work;
+    double* w3 = work + N;
+    double* w4 = work + 2 * N;
+    if (gh_status s = rhs_fwd(d, u_n, k)) return s;
+    GH_ACUDA(d, ew(d, 0, w2, u_n, k, 0.0, 0.5, dt));
+    if (gh_status s = rhs_fwd(d, w2, k)) return s;
+    GH_ACUDA(d, ew(d, 0, w3, u_n, k, 0.0, 0.5, dt));
+    if (gh_status s = rhs_fwd(d, w3, k)) return s;
+    GH_ACUDA(d, ew(d, 0, w4, u_n, k, 0.0, 1.0, dt));
+    u2 = w2;
+    u3 = w3;
+    u4 = w4;
+  }
   // transposed filters: u_new = Fa(Fr(v))  =>  g = Fr^T Fa^T ubar_np1
   const double* gin = ubar_np1;
   if (d->params.sh_keep_l != -1) {
@@ -543,26 +561,37 @@ gh_status gh_rk4_step_vjp(gh_domain* d, double dt, const double* u_n, const doub
         d->shells_d, d->n_shells, d->rad_block_begin_d, gin, dst);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
-    if (dst != g) GH_ACUDA(d, cudaMemcpyAsync(g, dst, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
-    gin = g;
+    gin = dst;
   }
+  // ubar_n starts as g (the direct u_n term of u_n + dt/6 (...)); g itself is
+  // kept for the stage cotangents
   if (gin != g) GH_ACUDA(d, cudaMemcpyAsync(g, gin, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
-  // reverse through the stages
   GH_ACUDA(d, cudaMemcpyAsync(ubar_n, g, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
   GH_ACUDA(d, ew(d, 1, kb, g, g, 1.0 / 6.0, 0.0, dt));                 // kb4 = dt/6 g
-  GH_ACUDA(d, cudaMemsetAsync(sb, 0, sizeof(double) * N, d->stream));
-  if (gh_status s = rhs_vjp(d, u4, kb, sb)) return s;                  // sb = J(u4)^T kb4
-  GH_ACUDA(d, ew(d, 2, ubar_n, sb, nullptr, 0.0, 0.0, 0.0));
-  GH_ACUDA(d, ew(d, 1, kb, g, sb, 1.0 / 3.0, 1.0, dt));                // kb3 = dt (g/3 + sb)
-  GH_ACUDA(d, cudaMemsetAsync(sb, 0, sizeof(double) * N, d->stream));
-  if (gh_status s = rhs_vjp(d, u3, kb, sb)) return s;
-  GH_ACUDA(d, ew(d, 2, ubar_n, sb, nullptr, 0.0, 0.0, 0.0));
-  GH_ACUDA(d, ew(d, 1, kb, g, sb, 1.0 / 3.0, 0.5, dt));                // kb2 = dt (g/3 + sb/2)
-  GH_ACUDA(d, cudaMemsetAsync(sb, 0, sizeof(double) * N, d->stream));
-  if (gh_status s = rhs_vjp(d, u2, kb, sb)) return s;
-  GH_ACUDA(d, ew(d, 2, ubar_n, sb, nullptr, 0.0, 0.0, 0.0));
-  GH_ACUDA(d, ew(d, 1, kb, g, sb, 1.0 / 6.0, 0.5, dt));                // kb1 = dt (g/6 + sb/2)
-  return rhs_vjp(d, u_n, kb, ubar_n);
+  if (gh_status s = rhs_vjp(d, u4, kb, sb, 0.0, true)) return s;       // sb = J(u4)^T kb4
+  GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 3.0, 1.0, dt, ubar_n));        // kb3 = dt (g/3 + sb); ubar_n += sb
+  if (gh_status s = rhs_vjp(d, u3, kb, sb, 0.0, true)) return s;
+  GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 3.0, 0.5, dt, ubar_n));        // kb2 = dt (g/3 + sb/2)
+  if (gh_status s = rhs_vjp(d, u2, kb, sb, 0.0, true)) return s;
+  GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 6.0, 0.5, dt, ubar_n));        // kb1 = dt (g/6 + sb/2)
+  return rhs_vjp(d, u_n, kb, ubar_n, cweight);
+}
+
+}  // namespace
+
+extern "C" {
+
+gh_status gh_rk4_step_vjp(gh_domain* d, double dt, const double* u_n, const double* ubar_np1, double* ubar_n,
+                          double* work) {
+  if (!d || !u_n || !ubar_np1 || !ubar_n || !work) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+  return step_vjp_impl(d, dt, u_n, nullptr, ubar_np1, ubar_n, work, 0.0);
+}
+
+gh_status gh_rk4_step_vjp_saved(gh_domain* d, double dt, const double* u_n, const double* stages,
+                                const double* ubar_np1, double* ubar_n, double* work, double cweight) {
+  if (!d || !u_n || !stages || !ubar_np1 || !ubar_n || !work)
+    return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
+  return step_vjp_impl(d, dt, u_n, stages, ubar_np1, ubar_n, work, cweight);
 }
 
 gh_status gh_perturbation_vjp(gh_domain* d, int kind, double Rc, double w, int lmax, const double* ubar,

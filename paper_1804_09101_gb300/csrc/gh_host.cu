@@ -743,6 +743,17 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   pb[n_shells] = npb;
   d->rad_blocks = nrb;
   d->pt_blocks = npb;
+  {
+    std::vector<int> ab(n_shells + 1);
+    int nab = 0;
+    for (int s = 0; s < n_shells; ++s) {
+      ab[s] = nab;
+      nab += d->shells_h[s].n_r * ((d->shells_h[s].na + 63) / 64);
+    }
+    ab[n_shells] = nab;
+    d->adj_pt_blocks = nab;
+    CREATE_CUDA(upload(d, ab, &d->adj_pt_block_begin_d));
+  }
   CREATE_CUDA(upload(d, rb, &d->rad_block_begin_d));
   CREATE_CUDA(upload(d, pb, &d->pt_block_begin_d));
 
@@ -1002,17 +1013,18 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
   return GH_OK;
 }
 
-gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
-  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
-  if (gh_status s = check_latched(d)) return s;
+// One RK4 step; with stages != NULL the three intermediate stage states
+// u_n + dt/2 k1, u_n + dt/2 k2, u_n + dt k3 are written there (and used as the
+// stage buffers) instead of the work area.
+gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages) {
   double* us = work;
   double* k = work + d->state;
   double* acc = work + 2 * d->state;
   const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
   for (int stage = 1; stage <= 4; ++stage) {
-    const double* in = (stage == 1) ? u : us;
+    const double* in = (stage == 1) ? u : (stages ? stages + (stage - 2) * d->state : us);
     if (gh_status s = derivatives(d, in)) return s;
-    double* target = (stage == 4 && !filt) ? u : us;
+    double* target = (stage == 4) ? (filt ? us : u) : (stages ? stages + (stage - 1) * d->state : us);
     {
       ProfScope p(d, GH_K_POINTWISE);
       GH_CUDA(d, gh::launch_pointwise(d, in, k, stage, dt, u, acc, target, stage == 1 && norm2_pre));
@@ -1030,6 +1042,18 @@ gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* 
     if (gh_status s = filters(d, us, u, k)) return s;
   }
   return GH_OK;
+}
+
+gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
+  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = check_latched(d)) return s;
+  return rk4_step_impl(d, dt, u, work, norm2_pre, nullptr);
+}
+
+gh_status gh_rk4_step_save(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages) {
+  if (!d || !u || !work || !stages) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = check_latched(d)) return s;
+  return rk4_step_impl(d, dt, u, work, norm2_pre, stages);
 }
 
 gh_status gh_apply_filters(gh_domain* d, double* u, double* work) {

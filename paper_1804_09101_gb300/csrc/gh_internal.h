@@ -139,6 +139,7 @@ struct gh_domain {
   int* sda_block_begin_d = nullptr; int sda_blocks = 0; size_t sda_smem = 0;
   int* sfa_block_begin_d = nullptr; int sfa_blocks = 0; size_t sfa_smem = 0;
   double* kbt = nullptr;        // one state, allocated by the first adjoint call
+  int* adj_pt_block_begin_d = nullptr; int adj_pt_blocks = 0;   // 64-thread point blocks
   double* pert_partial = nullptr; int pert_partial_len = 0;
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;

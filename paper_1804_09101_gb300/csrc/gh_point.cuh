@@ -76,8 +76,8 @@ GH_HD inline void point_split(const double psi[10], Split& s) {
       s.psi_inv[sym_index(1 + i, 1 + j)] = s.ginv[s3h(i, j)] - s.beta_up[i] * s.beta_up[j] * ia2;
 }
 
-// Forward: out[50] = dudt at the point; fills f.
-GH_HD inline void point_rhs(const PointIn& in, PointFwd& f, double out[50]) {
+// Forward intermediates only (what the reverse pass reads).
+GH_HD inline void point_intermediates(const PointIn& in, PointFwd& f) {
   const double* psi = in.u;
   const double* Pi = in.u + 10;
   const double* Phi = in.u + 20;
@@ -153,6 +153,16 @@ GH_HD inline void point_rhs(const PointIn& in, PointFwd& f, double out[50]) {
     for (int i = 0; i < 3; ++i)
       f.Gs[i][dd] = S.ginv[s3h(0, i)] * in.J[0][dd] + S.ginv[s3h(1, i)] * in.J[1][dd] + S.ginv[s3h(2, i)] * in.J[2][dd];
   }
+}
+
+// Forward: out[50] = dudt at the point; fills f.
+GH_HD inline void point_rhs(const PointIn& in, PointFwd& f, double out[50]) {
+  point_intermediates(in, f);
+  const double* psi = in.u;
+  const double* Pi = in.u + 10;
+  const double* Phi = in.u + 20;
+  const Split& S = f.S;
+  const double al = S.alpha;
   const double g0 = in.g0, g1 = in.g1, g2 = in.g2;
   for (int p = 0; p < 10; ++p) {
     const int A = pair_a(p), B = pair_b(p);

@@ -73,6 +73,8 @@ def _load():
         "gh_rhs_vjp": ([P, P, P, P], I),
         "gh_rk4_vjp_work_size": ([P], ctypes.c_longlong),
         "gh_rk4_step_vjp": ([P, D, P, P, P, P], I),
+        "gh_rk4_step_save": ([P, D, P, P, P, P], I),
+        "gh_rk4_step_vjp_saved": ([P, D, P, P, P, P, P, D], I),
         "gh_constraint_energy_vjp": ([P, P, D, P], I),
         "gh_perturbation_vjp": ([P, I, D, D, I, P, P], I),
         "gh_profile_enable": ([P, I], I),
@@ -275,6 +277,24 @@ def gh_rk4_step_vjp(dom, dt, u_n, ubar_np1, ubar_n, work):
     dom._check(_lib.gh_rk4_step_vjp(dom.handle, float(dt), _ptr(u_n, "u_n", dom.state_size),
                                     _ptr(ubar_np1, "ubar_np1", dom.state_size), _ptr(ubar_n, "ubar_n", dom.state_size),
                                     _ptr(work, "work", dom.vjp_work_size)))
+
+
+def gh_rk4_step_save(dom, dt, u, work, stages, norm2_pre=None):
+    """gh_rk4_step that also writes its three intermediate stage states to stages."""
+    dom._stream()
+    dom._check(_lib.gh_rk4_step_save(dom.handle, float(dt), _ptr(u, "u", dom.state_size),
+                                     _ptr(work, "work", dom.work_size), _ptr(norm2_pre, "norm2_pre"),
+                                     _ptr(stages, "stages", 3 * dom.state_size)))
+
+
+def gh_rk4_step_vjp_saved(dom, dt, u_n, stages, ubar_np1, ubar_n, work, cweight=0.0):
+    """Step VJP reusing saved stage states; adds cweight * grad(constraint energy)(u_n)."""
+    dom._stream()
+    dom._check(_lib.gh_rk4_step_vjp_saved(dom.handle, float(dt), _ptr(u_n, "u_n", dom.state_size),
+                                          _ptr(stages, "stages", 3 * dom.state_size),
+                                          _ptr(ubar_np1, "ubar_np1", dom.state_size),
+                                          _ptr(ubar_n, "ubar_n", dom.state_size),
+                                          _ptr(work, "work", dom.vjp_work_size), float(cweight)))
 
 
 def gh_constraint_energy_vjp(dom, u, weight, ubar):

@@ -46,3 +46,14 @@ double h_point_constraint_energy(const double* u, const double* ds, const double
   return gh::point_constraint_energy(in, w, ub, dsb);
 }
 }
+
+extern "C" void h_point_rhs_vjp_and_constraint(const double* u, const double* ds, const double* J, const double* H,
+                                               const double* dH, double g0, double g1, double g2, const double* kb,
+                                               double w, double* ub, double* dsb) {
+  gh::PointIn in = make_in(u, ds, J, H, dH, g0, g1, g2);
+  gh::PointFwd f;
+  double out[50];
+  gh::point_rhs(in, f, out);
+  gh::point_rhs_vjp(in, f, kb, ub, dsb);
+  gh::point_constraint_energy(in, w, ub, dsb);
+}

@@ -180,3 +180,24 @@ def test_autograd_functions_chain():
     fd = (f(u0 + h * dw) - f(u0 - h * dw)) / (2 * h)
     an = float(to_host(x.grad) @ dw)
     assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
+def test_saved_stage_step_and_vjp_agree_with_the_plain_ones():
+    from paper_1804_09101_gb300 import gh
+    w = _kerr2()
+    odom, u0, dom = _setup(w)
+    a, b = to_dev(u0), to_dev(u0)
+    stages = torch.zeros(3 * dom.state_size, dtype=torch.float64, device="cuda")
+    gh.gh_rk4_step(dom, w.dt, a, dom.new_work())
+    gh.gh_rk4_step_save(dom, w.dt, b, dom.new_work(), stages)
+    assert np.array_equal(to_host(a), to_host(b))
+    v = to_dev(np.random.default_rng(10).standard_normal(u0.shape))
+    r1, r2 = dom.new_state(), dom.new_state()
+    gh.gh_rk4_step_vjp(dom, w.dt, to_dev(u0), v, r1, gh.new_vjp_work(dom))
+    gh.gh_rk4_step_vjp_saved(dom, w.dt, to_dev(u0), stages, v, r2, gh.new_vjp_work(dom), 0.0)
+    assert np.abs(to_host(r1) - to_host(r2)).max() <= 1e-13 * np.abs(to_host(r1)).max()
+    # the fused constraint term equals a separate constraint-energy VJP
+    r3 = dom.new_state()
+    gh.gh_rk4_step_vjp_saved(dom, w.dt, to_dev(u0), stages, v, r3, gh.new_vjp_work(dom), 0.37)
+    gh.gh_constraint_energy_vjp(dom, to_dev(u0), 0.37, r2)
+    assert np.abs(to_host(r3) - to_host(r2)).max() <= 1e-12 * np.abs(to_host(r2)).max()

@@ -128,3 +128,17 @@ def test_constraint_energy_and_gradient(lib, seed):
         ee = ee.reshape(50, 3)
         fd = w * (E(u, ds + ee) - E(u, ds - ee)) / (2 * h)
         assert abs(fd - dsb[k]) < 1e-6 * max(1.0, abs(fd)), (k, fd, dsb[k])
+
+
+def test_fused_rhs_and_constraint_reverse_pass_is_the_sum(lib):
+    u, ds, J, H, dH = _point(4)
+    P = ctypes.c_void_p
+    lib.h_point_rhs_vjp_and_constraint.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_double, P, ctypes.c_double, P, P]
+    kb = np.random.default_rng(3).standard_normal(50)
+    ub1, dsb1 = np.zeros(50), np.zeros(150)
+    lib.h_point_rhs_vjp(_p(u), _p(ds), _p(J), _p(H), _p(dH), *G, _p(kb), _p(ub1), _p(dsb1))
+    lib.h_point_constraint_energy(_p(u), _p(ds), _p(J), _p(H), _p(dH), 0.37, _p(ub1), _p(dsb1))
+    ub2, dsb2 = np.zeros(50), np.zeros(150)
+    lib.h_point_rhs_vjp_and_constraint(_p(u), _p(ds), _p(J), _p(H), _p(dH), *G, _p(kb), 0.37, _p(ub2), _p(dsb2))
+    assert np.allclose(ub1, ub2, rtol=1e-14, atol=1e-14) and np.allclose(dsb1, dsb2, rtol=1e-14, atol=1e-14)
