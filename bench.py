@@ -51,7 +51,8 @@ def parse():
                         "N_r=41, L=31; schwarzschild: 1 shell N_r=11, L=7; batched: 64 independent "
                         "single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
                         "compared with the plain per-hole launch loop")
-    p.add_argument("--algorithm", default="separable", choices=["separable", "dense"])
+    p.add_argument("--algorithm", default="folded", choices=["folded", "separable", "dense"],
+                   help="angular maps: folded separable (default), plain separable, or dense traced matrices")
     return p.parse_args()
 
 
@@ -189,7 +190,8 @@ def run_ours(args, w):
     dev = torch.device("cuda", local)
 
     dom = gh.Domain.from_workload(w)
-    gh.gh_set_algorithm(dom, gh.GH_ALG_DENSE if args.algorithm == "dense" else gh.GH_ALG_SEPARABLE)
+    gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
+                              "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
     u = dom.new_state()
     gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
     p = w.pulse
@@ -276,8 +278,11 @@ def run_ours(args, w):
     d_flops = costmodel.family_flops(dom_name, w.shells, args.algorithm, w.sh_keep_l)
     achieved = d_flops / (d_ms / d_n / 1000.0) / 1e12 if (d_n and d_flops) else None
     peak = costmodel.GB300_FP64_PEAK_TFLOPS
-    kernel_names = {"angular": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, Legendre maps, inverse DFT)"
-                    if args.algorithm == "separable" else "gemm_batched_kernel (dense angular maps)",
+    kernel_names = {"angular": {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: folded phi DFT, "
+                                          "parity-split Legendre maps, folded inverse DFT)",
+                                "separable": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, "
+                                             "Legendre maps, inverse DFT)",
+                                "dense": "gemm_batched_kernel (dense angular maps)"}[args.algorithm],
                     "pointwise": "pointwise_kernel (DiffJac + GH RHS + RK4 combine)",
                     "radial": "radial_kernel<false> (Chebyshev d/dx)"}
     traffic = TRAFFIC_PER_LAUNCH.get((w.name, args.algorithm, dom_name))
@@ -398,9 +403,9 @@ def run_batched(args):
     plain_value = pts * 4 * psteps / (plain_ms / 1000.0)
     dom_name = max(fam_ms, key=lambda n: fam_ms[n][0])
     d_ms, d_n = fam_ms[dom_name]
-    d_flops = costmodel.family_flops(dom_name, [s[:4] for s in w.shells], "separable", None)
+    d_flops = costmodel.family_flops(dom_name, [s[:4] for s in w.shells], "folded", None)
     if dom_name == "angular_filter":
-        d_flops = sum(costmodel.sep_angular_flops([s[:4]], K=(2 * s[3]) // 3, two=False) for s in w.shells)
+        d_flops = sum(costmodel.fold_angular_flops([s[:4]], K=(2 * s[3]) // 3, two=False) for s in w.shells)
     achieved = d_flops / (d_ms / d_n / 1000.0) / 1e12 if (d_n and d_flops) else None
     peak = costmodel.GB300_FP64_PEAK_TFLOPS
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=args.steps, warmup=args.warmup,

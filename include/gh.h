@@ -251,10 +251,13 @@ long long gh_launch_count(const gh_domain* dom);
 /* How the angular maps (d/dtheta, d/dphi and the SH filter) are evaluated.
  * GH_ALG_DENSE: one dense (N_theta N_phi)^2 matrix per map, the paper's traced
  *   matrices of Eq. DifferentiatorI1S2 (built on first selection).
- * GH_ALG_SEPARABLE (default): the same linear maps factorised as a phi DFT,
- *   one N_theta x N_theta Legendre map per Fourier mode, and an inverse DFT;
- *   equal to the dense maps up to rounding, with far fewer flops. */
-enum { GH_ALG_DENSE = 0, GH_ALG_SEPARABLE = 1 };
+ * GH_ALG_SEPARABLE: the same linear maps factorised as a phi DFT, one
+ *   N_theta x N_theta Legendre map per Fourier mode, and an inverse DFT; equal
+ *   to the dense maps up to rounding, with far fewer flops.
+ * GH_ALG_SEPARABLE_FOLDED (default when every shell has odd L): the separable
+ *   maps with the cos/sin symmetries of the uniform phi grid and the
+ *   equatorial parity of Pbar_lm folded out (about 3x fewer flops again). */
+enum { GH_ALG_DENSE = 0, GH_ALG_SEPARABLE = 1, GH_ALG_SEPARABLE_FOLDED = 2 };
 gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
 
 /* Kernel families for the profiler below. */

@@ -106,14 +106,38 @@ POINTWISE_FLOPS_PER_POINT = 4934
 POINTWISE_CONSTRAINT_EXTRA_FLOPS_PER_POINT = 409
 
 
-def family_flops(family, shells, algorithm="separable", keep_l=-1):
+def fold_angular_flops(shells, K=None, two=True):
+    """FP64 flops of one folded separable launch (fold_angular_kernel), per
+    (r, field) row: fold 8 (N_phi/4) N_theta; phase A 2 N_theta M W + N_theta M;
+    phase B n_out M half (4 half + 5); phase C n_out N_theta W (2 M + 8), with
+    W = N_phi/4 + 1, half = N_theta/2, M = 2K+1."""
+    f = 0
+    n_out = 2 if two else 1
+    for sh in shells:
+        n_r, nth, nph, na = _shell_dims(sh)
+        k = sh[3] if K is None else K
+        M = 2 * k + 1
+        N4 = nph // 4
+        W = N4 + 1
+        half = nth // 2
+        per_row = (8 * N4 * nth + 2 * nth * M * W + nth * M + n_out * M * half * (4 * half + 5)
+                   + n_out * nth * W * (2 * M + 8))
+        f += 50 * n_r * per_row
+    return f
+
+
+def family_flops(family, shells, algorithm="folded", keep_l=-1):
     """Algorithmic FP64 flops of one launch of a kernel family."""
     pts = sum(n_r * 2 * (L + 1) ** 2 for (_, _, n_r, L) in shells)
     if family == "angular":
-        return sep_angular_flops(shells) if algorithm == "separable" else angular_deriv_flops(shells)
+        return {"separable": sep_angular_flops, "dense": angular_deriv_flops,
+                "folded": fold_angular_flops}[algorithm](shells)
     if family == "angular_filter":
-        return (sep_angular_flops(shells, K=keep_l, two=False) if algorithm == "separable"
-                else angular_filter_flops(shells))
+        if algorithm == "separable":
+            return sep_angular_flops(shells, K=keep_l, two=False)
+        if algorithm == "folded":
+            return fold_angular_flops(shells, K=keep_l, two=False)
+        return angular_filter_flops(shells)
     if family in ("radial", "radial_filter"):
         return radial_flops(shells)
     if family == "pointwise":

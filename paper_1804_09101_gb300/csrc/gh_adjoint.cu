@@ -417,7 +417,7 @@ gh_status afail(gh_domain* d, gh_status s, const std::string& m) {
 unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 gh_status adj_ready(gh_domain* d) {
-  if (d->algorithm != 1) return afail(d, GH_ENOTSUP, "the adjoint needs the separable angular algorithm");
+  if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
   if (!d->kbt) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));

@@ -1,0 +1,195 @@
+// Symmetry-folded separable angular maps (d/dtheta, d/dphi and the SH
+// truncation filter).  The same linear maps as sep_angular_kernel -- the
+// projection onto the real Y_lm, l <= K, followed by synthesis of values or
+// derivatives (the angular parts of Eq. DifferentiatorI1S2) -- evaluated with
+// fewer FP64 operations, since FP64 throughput bounds this kernel on GB300:
+//  * phi DFT: cos(m phi_k) and sin(m phi_k) are even/odd under k <-> N - k and
+//    (-1)^m even/odd under k <-> N/2 - k, so each ring is folded into four
+//    quarter-length vectors and every coefficient is a dot product of length
+//    N/4 + 1 (a quarter of the dense DFT);
+//  * Legendre maps: on symmetric Gauss-Legendre nodes Pbar_lm has parity
+//    (-1)^{l+m} about the equator (d/dtheta flips it), so each map acts on the
+//    symmetric and antisymmetric halves with half-size matrices;
+//  * inverse DFT: the same foldings produce four output points per quarter-ring
+//    sum.
+// Per (r, field) row: about 2 (N_theta M (N/4+1) + n_out M N_theta N_theta/2 +
+// n_out N_theta (N/4+1) M) flops, M = 2K+1, instead of 2 M (N_theta N_phi +
+// n_out N_theta^2 + n_out N_theta N_phi).
+#include <cuda_runtime.h>
+
+#include "gh_geom.cuh"
+#include "gh_internal.h"
+
+namespace gh {
+
+constexpr int FOLD_THREADS = 256;
+
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_THREADS)
+fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                    const double* __restrict__ in, double* __restrict__ out0, double* __restrict__ out1) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  const int nth = sh.nth, nph = sh.nph, na = sh.na;
+  const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = N4 + 1, N2 = nph / 2;
+  constexpr int NO = TWO ? 2 : 1;
+  const int rows = NF * sh.n_r;
+  const int RB = P.rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  double* U = sm;                                   // [RB][na]
+  double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
+  double* AB = F + (size_t)RB * nth * 4 * W;        // [RB][M][nth]: s (half) then t (half)
+  double* OUT = AB + (size_t)RB * M * nth;          // [NO][RB][nth][M]
+  const long long gbase = sh.off + (long long)row0 * na;
+  for (int i = threadIdx.x; i < nr * na; i += FOLD_THREADS) U[i] = in[gbase + i];
+  __syncthreads();
+  // fold every ring: Cp, Cm (cos, even / odd m), Sp, Sm (sin, odd / even m)
+  for (int o = threadIdx.x; o < nr * nth * W; o += FOLD_THREADS) {
+    const int k = o % W;
+    const int rj = o / W;
+    const double* ring = U + (size_t)rj * nph;
+    double* f = F + (size_t)rj * 4 * W;
+    auto ev = [&](int kk) { return (kk == 0 || kk == N2) ? ring[kk] : ring[kk] + ring[nph - kk]; };
+    auto od = [&](int kk) { return (kk == 0 || kk == N2) ? 0.0 : ring[kk] - ring[nph - kk]; };
+    if (k < N4) {
+      const double e1 = ev(k), e2 = ev(N2 - k), o1 = od(k), o2 = od(N2 - k);
+      f[k] = e1 + e2;
+      f[W + k] = e1 - e2;
+      f[2 * W + k] = o1 + o2;
+      f[3 * W + k] = o1 - o2;
+    } else {
+      f[k] = ev(N4);
+      f[W + k] = 0.0;
+      f[2 * W + k] = od(N4);
+      f[3 * W + k] = 0.0;
+    }
+  }
+  __syncthreads();
+  // phase A: Fourier coefficient of mode for rings j and N_theta-1-j, stored as
+  // their sum (symmetric part s) and difference (antisymmetric part t)
+  for (int o = threadIdx.x; o < nr * half * M; o += FOLD_THREADS) {
+    const int mode = o % M;
+    const int t = o / M;
+    const int jh = t % half;
+    const int rr = t / half;
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    const int q = cosm ? (m % 2 == 0 ? 0 : 1) : (m % 2 == 1 ? 2 : 3);
+    const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
+    const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
+    const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
+    double c1 = 0.0, c2 = 0.0;
+    for (int k = 0; k < W; ++k) {
+      const double tv = __ldg(tab + k);
+      c1 = fma(f1[k], tv, c1);
+      c2 = fma(f2[k], tv, c2);
+    }
+    double* ab = AB + ((size_t)rr * M + mode) * nth;
+    ab[jh] = c1 + c2;
+    ab[half + jh] = c1 - c2;
+  }
+  __syncthreads();
+  // phase B: half-size Legendre maps; normalised synthesis coefficients
+  for (int o = threadIdx.x; o < nr * M * half; o += FOLD_THREADS) {
+    const int j = o % half;
+    const int t = o / half;
+    const int mode = t % M;
+    const int rr = t / M;
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    const double* ab = AB + ((size_t)rr * M + mode) * nth;
+    const double cmv = __ldg(P.cm + m);
+#pragma unroll
+    for (int o2 = 0; o2 < NO; ++o2) {
+      const double* Qs = (o2 == 0 ? P.Q0s : P.Q1s) + (size_t)m * half * half + j;
+      const double* Qt = (o2 == 0 ? P.Q0t : P.Q1t) + (size_t)m * half * half + j;
+      double S = 0.0, T = 0.0;
+      for (int jp = 0; jp < half; ++jp) {
+        S = fma(__ldg(Qs + jp * half), ab[jp], S);
+        T = fma(__ldg(Qt + jp * half), ab[half + jp], T);
+      }
+      const double sig = (o2 == 0) ? P.sigma0 : P.sigma1;
+      const double y1 = S + T, y2 = sig * (S - T);
+      int slot = mode;
+      double fac = cmv;
+      if (TWO && o2 == 1) {
+        // d/dphi: the value projection of cos mode m feeds sin slot m with -m,
+        // that of sin mode m feeds cos slot m with +m
+        if (cosm) {
+          if (m == 0) {
+            double* c = OUT + (size_t)RB * nth * M + (size_t)rr * nth * M;
+            c[(size_t)j * M] = 0.0;
+            c[(size_t)(nth - 1 - j) * M] = 0.0;
+            continue;
+          }
+          slot = K + m;
+          fac = -m * cmv;
+        } else {
+          slot = m;
+          fac = m * cmv;
+        }
+      }
+      double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rr * nth * M;
+      c[(size_t)j * M + slot] = fac * y1;
+      c[(size_t)(nth - 1 - j) * M + slot] = fac * y2;
+    }
+  }
+  __syncthreads();
+  // phase C: quarter-ring sums give four output points each
+  for (int o = threadIdx.x; o < nr * nth * W; o += FOLD_THREADS) {
+    const int k = o % W;
+    const int rj = o / W;
+    const int rr = rj / nth;
+    const int j = rj - rr * nth;
+#pragma unroll
+    for (int o2 = 0; o2 < NO; ++o2) {
+      const double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M;
+      double Ee = 0.0, Eo = 0.0, Oe = 0.0, Oo = 0.0;
+      for (int m = 0; m <= K; m += 2) Ee = fma(c[m], __ldg(P.Tc + (size_t)m * W + k), Ee);
+      for (int m = 1; m <= K; m += 2) {
+        Eo = fma(c[m], __ldg(P.Tc + (size_t)m * W + k), Eo);
+        Oo = fma(c[K + m], __ldg(P.Ts + (size_t)m * W + k), Oo);
+      }
+      for (int m = 2; m <= K; m += 2) Oe = fma(c[K + m], __ldg(P.Ts + (size_t)m * W + k), Oe);
+      const double Ek = Ee + Eo, Eh = Ee - Eo, Ok = Oe + Oo, Oh = Oo - Oe;
+      double* dst = (o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * nph;
+      if (k == 0) {
+        dst[0] = Ek + Ok;
+        dst[N2] = Eh + Oh;
+      } else if (k == N4) {
+        dst[N4] = Ek + Ok;
+        dst[nph - N4] = Ek - Ok;
+      } else {
+        dst[k] = Ek + Ok;
+        dst[N2 - k] = Eh + Oh;
+        dst[N2 + k] = Eh - Oh;
+        dst[nph - k] = Ek - Ok;
+      }
+    }
+  }
+}
+
+cudaError_t fold_set_smem_limits(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(fold_angular_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fold_angular_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {
+  fold_angular_kernel<true><<<d->fd_blocks, FOLD_THREADS, d->fd_smem, d->stream>>>(
+      d->shells_d, d->n_shells, d->fd_block_begin_d, in, dth, dph);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out) {
+  fold_angular_kernel<false><<<d->ff_blocks, FOLD_THREADS, d->ff_smem, d->stream>>>(
+      d->shells_d, d->n_shells, d->ff_block_begin_d, in, out, nullptr);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace gh

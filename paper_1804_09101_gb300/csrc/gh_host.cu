@@ -79,6 +79,13 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
     x[i] = z;
     w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
   }
+  // make the node set exactly symmetric about the equator (the folded angular
+  // maps rely on x_{n-1-i} = -x_i and w_{n-1-i} = w_i)
+  for (int i = 0; i < n / 2; ++i) {
+    x[n - 1 - i] = -x[i];
+    w[n - 1 - i] = w[i];
+  }
+  if (n % 2) x[n / 2] = 0.0;
 }
 
 // Normalised associated Legendre functions Pbar_l^m(theta_j) and their theta
@@ -314,6 +321,73 @@ int sep_adj_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
 int sep_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
   const size_t per_row = (size_t)na + (two ? 3 : 2) * (size_t)nth * M;
   const size_t budget = 64 * 1024 / sizeof(double);
+  int rb = (int)(budget / per_row);
+  if (rb < 1) rb = 1;
+  if (rb > 64) rb = 64;
+  if (rb > n_rows) rb = n_rows;
+  return rb;
+}
+
+// Folded plan (see fold_angular_kernel).
+struct FoldHost {
+  int K, M, N4, half;
+  std::vector<double> Tc, Ts, Q0s, Q0t, Q1s, Q1t, cm;
+  double s0, s1;
+};
+
+bool fold_applicable(const AngularGrid& g) { return g.nph % 4 == 0 && g.nth % 2 == 0; }
+
+FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
+  FoldHost h;
+  h.K = K;
+  h.M = 2 * K + 1;
+  h.N4 = g.nph / 4;
+  h.half = g.nth / 2;
+  const int W = h.N4 + 1, nth = g.nth, half = h.half, Wl = g.L + 1;
+  h.Tc.assign((size_t)(K + 1) * W, 0.0);
+  h.Ts.assign((size_t)(K + 1) * W, 0.0);
+  for (int m = 0; m <= K; ++m)
+    for (int k = 0; k < W; ++k) {
+      const double ang = 2.0 * kPi * (double)m * k / g.nph;
+      h.Tc[(size_t)m * W + k] = std::cos(ang);
+      h.Ts[(size_t)m * W + k] = std::sin(ang);
+    }
+  std::vector<double> P, dP;
+  legendre_tables(g.L, g.ct, g.st, P, dP);
+  auto build = [&](bool dtheta, std::vector<double>& Qs, std::vector<double>& Qt) {
+    Qs.assign((size_t)(K + 1) * half * half, 0.0);
+    Qt.assign((size_t)(K + 1) * half * half, 0.0);
+    std::vector<double> Q((size_t)nth * nth);
+    for (int m = 0; m <= K; ++m) {
+      for (int jo = 0; jo < nth; ++jo)
+        for (int ji = 0; ji < nth; ++ji) {
+          double acc = 0.0;
+          for (int l = m; l <= K; ++l) {
+            const double a = dtheta ? dP[((size_t)l * Wl + m) * nth + jo] : P[((size_t)l * Wl + m) * nth + jo];
+            acc += a * P[((size_t)l * Wl + m) * nth + ji];
+          }
+          Q[(size_t)jo * nth + ji] = acc * g.wgl[ji];
+        }
+      for (int ji = 0; ji < half; ++ji)
+        for (int jo = 0; jo < half; ++jo) {
+          const double q1 = Q[(size_t)jo * nth + ji], q2 = Q[(size_t)jo * nth + (nth - 1 - ji)];
+          Qs[((size_t)m * half + ji) * half + jo] = 0.5 * (q1 + q2);
+          Qt[((size_t)m * half + ji) * half + jo] = 0.5 * (q1 - q2);
+        }
+    }
+  };
+  build(deriv, h.Q0s, h.Q0t);
+  if (deriv) build(false, h.Q1s, h.Q1t);
+  h.cm.resize(K + 1);
+  for (int m = 0; m <= K; ++m) h.cm[m] = (m == 0 ? 1.0 : 2.0) * 2.0 * kPi / g.nph;
+  h.s0 = deriv ? -1.0 : 1.0;
+  h.s1 = 1.0;
+  return h;
+}
+
+int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int n_rows) {
+  const size_t per_row = (size_t)na + 4 * (size_t)nth * W + (size_t)M * nth + (size_t)n_out * nth * M;
+  const size_t budget = 96 * 1024 / sizeof(double);
   int rb = (int)(budget / per_row);
   if (rb < 1) rb = 1;
   if (rb > 64) rb = 64;
@@ -558,6 +632,8 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   std::map<int, std::pair<double*, double*>> radial_t_cache;            // n_r -> (D^T, F^T)
   std::map<std::tuple<int, int, int>, gh::SepPlan> sep_cache;           // (L, K, kind) -> plan
   std::map<std::tuple<int, int, int>, gh::SepAdjPlan> sep_adj_cache;    // its transpose
+  std::map<std::tuple<int, int, int>, gh::FoldPlan> fold_cache;         // folded plans
+  bool all_fold = true;
   std::map<int, AngularGrid> grids;
 
   long long off = 0, pts = 0;
@@ -640,6 +716,45 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     CREATE_CUDA(get_plan(sh.L, true, sh.sd, sh.sda));
     sh.sd.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sd.M, true, gh::NF * sh.n_r);
     sh.sda.rows_per_cta = sep_adj_rows_per_block(sh.na, sh.nth, sh.sda.M, true, gh::NF * sh.n_r);
+    if (fold_applicable(ag)) {
+      auto get_fold = [&](int K, bool deriv, gh::FoldPlan& out) -> cudaError_t {
+        auto key = std::make_tuple(sh.L, K, deriv ? 1 : 0);
+        if (!fold_cache.count(key)) {
+          FoldHost f = fold_plan(ag, K, deriv);
+          gh::FoldPlan P;
+          std::memset(&P, 0, sizeof(P));
+          P.K = f.K;
+          P.M = f.M;
+          P.N4 = f.N4;
+          P.half = f.half;
+          P.two = deriv ? 1 : 0;
+          P.sigma0 = f.s0;
+          P.sigma1 = f.s1;
+          double* q = nullptr;
+          cudaError_t e;
+          if ((e = upload(d, f.Tc, &q)) != cudaSuccess) return e; P.Tc = q;
+          if ((e = upload(d, f.Ts, &q)) != cudaSuccess) return e; P.Ts = q;
+          if ((e = upload(d, f.Q0s, &q)) != cudaSuccess) return e; P.Q0s = q;
+          if ((e = upload(d, f.Q0t, &q)) != cudaSuccess) return e; P.Q0t = q;
+          if ((e = upload(d, f.cm, &q)) != cudaSuccess) return e; P.cm = q;
+          if (deriv) {
+            if ((e = upload(d, f.Q1s, &q)) != cudaSuccess) return e; P.Q1s = q;
+            if ((e = upload(d, f.Q1t, &q)) != cudaSuccess) return e; P.Q1t = q;
+          }
+          fold_cache[key] = P;
+        }
+        out = fold_cache[key];
+        return cudaSuccess;
+      };
+      CREATE_CUDA(get_fold(sh.L, true, sh.fd));
+      sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, sh.fd.N4 + 1, sh.fd.M, 2, gh::NF * sh.n_r);
+      if (sh.keep >= 0) {
+        CREATE_CUDA(get_fold(sh.keep, false, sh.ff));
+        sh.ff.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, sh.ff.N4 + 1, sh.ff.M, 1, gh::NF * sh.n_r);
+      }
+    } else {
+      all_fold = false;
+    }
     if (sh.keep >= 0) {
       CREATE_CUDA(get_plan(sh.keep, false, sh.sf, sh.sfa));
       sh.sf.rows_per_cta = sep_rows_per_block(sh.na, sh.nth, sh.sf.M, false, gh::NF * sh.n_r);
@@ -811,6 +926,38 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     CREATE_CUDA(upload(d, ab, &d->sda_block_begin_d));
     CREATE_CUDA(upload(d, afb, &d->sfa_block_begin_d));
     CREATE_CUDA(gh::sep_adj_set_smem_limits(std::max(sma, smfa)));
+    // folded maps
+    d->fold_ok = all_fold;
+    if (all_fold) {
+      std::vector<int> fb2(n_shells + 1), ffb(n_shells + 1);
+      int nfd = 0, nff = 0;
+      size_t smfd = 0, smff = 0;
+      for (int s = 0; s < n_shells; ++s) {
+        const gh::ShellDev& sh = d->shells_h[s];
+        const int rows = gh::NF * sh.n_r;
+        const size_t W = sh.fd.N4 + 1;
+        fb2[s] = nfd;
+        nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
+        smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta *
+                                  ((size_t)sh.na + 4 * (size_t)sh.nth * W + 3 * (size_t)sh.nth * sh.fd.M));
+        ffb[s] = nff;
+        if (sh.ff.M > 0) {
+          nff += (rows + sh.ff.rows_per_cta - 1) / sh.ff.rows_per_cta;
+          smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta *
+                                    ((size_t)sh.na + 4 * (size_t)sh.nth * W + 2 * (size_t)sh.nth * sh.ff.M));
+        }
+      }
+      fb2[n_shells] = nfd;
+      ffb[n_shells] = nff;
+      d->fd_blocks = nfd;
+      d->ff_blocks = nff;
+      d->fd_smem = smfd;
+      d->ff_smem = smff;
+      CREATE_CUDA(upload(d, fb2, &d->fd_block_begin_d));
+      CREATE_CUDA(upload(d, ffb, &d->ff_block_begin_d));
+      CREATE_CUDA(gh::fold_set_smem_limits(std::max(smfd, smff)));
+    }
+    d->algorithm = all_fold ? 2 : 1;
   }
 
   // scratch
@@ -1071,8 +1218,10 @@ gh_status gh_constraints(gh_domain* d, const double* u, double* c_out, double* n
 }
 
 gh_status gh_set_algorithm(gh_domain* d, int algorithm) {
-  if (!d || (algorithm != GH_ALG_DENSE && algorithm != GH_ALG_SEPARABLE))
-    return fail(d, GH_EINVAL, "algorithm must be GH_ALG_DENSE or GH_ALG_SEPARABLE");
+  if (!d || (algorithm != GH_ALG_DENSE && algorithm != GH_ALG_SEPARABLE && algorithm != GH_ALG_SEPARABLE_FOLDED))
+    return fail(d, GH_EINVAL, "algorithm must be GH_ALG_DENSE, GH_ALG_SEPARABLE or GH_ALG_SEPARABLE_FOLDED");
+  if (algorithm == GH_ALG_SEPARABLE_FOLDED && !d->fold_ok)
+    return fail(d, GH_EINVAL, "the folded maps need N_phi % 4 == 0 and even N_theta (odd L) on every shell");
   if (algorithm == GH_ALG_DENSE) {
     GH_CUDA(d, cudaStreamSynchronize(d->stream));
     if (gh_status st = build_dense(d)) return st;

@@ -42,6 +42,24 @@ struct SepAdjPlan {
   const double* GT;             // [M][nph]
 };
 
+// Symmetry-folded separable map (fold_angular_kernel): the phi DFT and its
+// inverse use the k <-> N-k and k <-> N/2-k symmetries of cos/sin (a quarter of
+// the dense DFT work), the Legendre maps the equatorial parity of Pbar_lm
+// (half-size matrices on the symmetric and antisymmetric parts).  Needs
+// N_phi % 4 == 0 and N_theta even (odd L).
+struct FoldPlan {
+  int K, M, N4, half;           // highest m, 2K+1 modes, N_phi/4, N_theta/2
+  int rows_per_cta, two;        // rows per block; 2 outputs (derivatives) or 1 (filter)
+  const double* Tc;             // [K+1][N4+1] cos(m phi_k)
+  const double* Ts;             // [K+1][N4+1] sin(m phi_k)
+  const double* Q0s;            // [K+1][half][half] (transposed: [m][j_in][j_out]) output 0, symmetric part
+  const double* Q0t;            //                   output 0, antisymmetric part
+  const double* Q1s;            // output 1 (value map; derivative plan only)
+  const double* Q1t;
+  const double* cm;             // [K+1] c_m 2 pi / N_phi
+  double sigma0, sigma1;        // parity of output 0 / 1 (-1 for d/dtheta, +1 for values)
+};
+
 // One shell as the kernels see it (device-resident array of these).
 struct ShellDev {
   int n_r, L, nth, nph, na;     // na = nth * nph angular points
@@ -71,6 +89,8 @@ struct ShellDev {
   SepPlan sf;                   // separable SH truncation filter (M = 0 if off)
   SepAdjPlan sda;               // transpose of sd
   SepAdjPlan sfa;               // transpose of sf (M = 0 if off)
+  FoldPlan fd;                  // folded d/dtheta, d/dphi (M = 0 if not applicable)
+  FoldPlan ff;                  // folded SH filter
   const double* DrT;            // [n_r][n_r] transpose of Dr
   const double* FrT;            // [n_r][n_r] transpose of Fr
 };
@@ -125,6 +145,9 @@ struct gh_domain {
   // separable angular maps: first block of each shell, dynamic shared memory
   int algorithm = 1;            // 0 dense traced matrices, 1 separable
   int* sd_block_begin_d = nullptr; int sd_blocks = 0; size_t sd_smem = 0;
+  int* fd_block_begin_d = nullptr; int fd_blocks = 0; size_t fd_smem = 0;
+  int* ff_block_begin_d = nullptr; int ff_blocks = 0; size_t ff_smem = 0;
+  bool fold_ok = false;         // every shell has a folded plan
   int* sf_block_begin_d = nullptr; int sf_blocks = 0; size_t sf_smem = 0;
   // scratch owned by the domain
   double* d_r = nullptr;         // radial derivative  (one state)
@@ -162,6 +185,9 @@ cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph);
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
+cudaError_t fold_set_smem_limits(size_t bytes);
+cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph);
+cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out);
 cudaError_t sep_adj_set_smem_limits(size_t bytes);
 cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const double* dr, const double* dth,
                                       const double* dph, double* k);

@@ -829,6 +829,7 @@ cudaError_t launch_angular_deriv(gh_domain* d, const double* in) {
 }
 
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph) {
+  if (d->algorithm == 2) return launch_fold_deriv(d, in, dth, dph);
   if (d->algorithm == 1)
     sep_angular_kernel<true><<<d->sd_blocks, SEP_THREADS, d->sd_smem, d->stream>>>(
         d->shells_d, d->n_shells, d->sd_block_begin_d, in, dth, dph);
@@ -854,6 +855,7 @@ cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const doubl
 }
 
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out) {
+  if (d->algorithm == 2) return launch_fold_filter(d, in, out);
   if (d->algorithm == 1)
     sep_angular_kernel<false><<<d->sf_blocks, SEP_THREADS, d->sf_smem, d->stream>>>(
         d->shells_d, d->n_shells, d->sf_block_begin_d, in, out, nullptr);

@@ -256,7 +256,7 @@ def gh_profile_read(dom, family):
     return ms.value, n.value
 
 
-GH_ALG_DENSE, GH_ALG_SEPARABLE = 0, 1
+GH_ALG_DENSE, GH_ALG_SEPARABLE, GH_ALG_SEPARABLE_FOLDED = 0, 1, 2
 
 
 def gh_set_algorithm(dom, algorithm):

@@ -57,10 +57,12 @@ def oracle_initial_state(w, odom):
     return unflat(flat(u) + w.noise(), odom)
 
 
-def gpu_domain(w, odom=None, algorithm="separable"):
+def gpu_domain(w, odom=None, algorithm="default"):
     """Library domain with the oracle's gauge source and background (when given)."""
     dom = gh.Domain.from_workload(w)
-    gh.gh_set_algorithm(dom, gh.GH_ALG_DENSE if algorithm == "dense" else gh.GH_ALG_SEPARABLE)
+    if algorithm != "default":
+        gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
+                                  "folded": gh.GH_ALG_SEPARABLE_FOLDED}[algorithm])
     if odom is not None:
         gh.gh_set_gauge(dom, to_dev(flat(odom.H)), to_dev(flat(odom.dH)))
         gh.gh_set_background(dom, to_dev(flat(odom.u_exact)))

@@ -52,8 +52,14 @@ def w_pi_modes():
     return w
 
 
+def w_even_L():
+    # even L: N_phi % 4 != 0, so the default falls back to the unfolded separable maps
+    return workloads.Workload(name="even_L", shells=[(1.6, 3.0, 7, 6), (3.0, 5.0, 7, 6)], M=1.0, chi=0.4,
+                              radial_filter_on=True, sh_keep_l=4, dt=0.005, seed=21, noise_amp=1e-7)
+
+
 CASES = {"schwarzschild": w_schwarzschild, "kerr2": w_kerr_two_shells, "ragged": w_ragged,
-         "minimal": w_minimal}
+         "minimal": w_minimal, "even_L": w_even_L}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
@@ -92,13 +98,15 @@ def test_perturbations():
         assert max_rel(to_host(u), ref, np.abs(ref).max()) < REL_TOL
 
 
-ALGS = ["separable", "dense"]
+ALGS = ["separable", "dense", "folded"]
 
 
 @pytest.mark.parametrize("alg", ALGS)
 def test_cartesian_derivatives(case, alg):
     gh = _gh()
     w, odom, u0 = case
+    if alg == "folded" and any(L % 2 == 0 for (_, _, _, L) in w.shells):
+        pytest.skip("folded maps need odd L")
     dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     du = torch.zeros(3 * dom.state_size, dtype=torch.float64, device="cuda")
@@ -114,6 +122,8 @@ def test_cartesian_derivatives(case, alg):
 def test_rhs(case, alg):
     gh = _gh()
     w, odom, u0 = case
+    if alg == "folded" and any(L % 2 == 0 for (_, _, _, L) in w.shells):
+        pytest.skip("folded maps need odd L")
     dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     k = dom.new_state()
@@ -142,6 +152,8 @@ def test_filters(case, alg):
     w, odom, u0 = case
     if not (w.radial_filter_on or w.sh_keep_l >= 0):
         pytest.skip("workload has no filter")
+    if alg == "folded" and any(L % 2 == 0 for (_, _, _, L) in w.shells):
+        pytest.skip("folded maps need odd L")
     dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     gh.gh_apply_filters(dom, u, dom.new_work())
@@ -151,7 +163,8 @@ def test_filters(case, alg):
 
 @pytest.mark.parametrize("name,steps,alg", [("schwarzschild", 20, "separable"), ("kerr2", 3, "separable"),
                                             ("ragged", 2, "separable"), ("minimal", 5, "separable"),
-                                            ("kerr2", 2, "dense")])
+                                            ("kerr2", 2, "dense"), ("kerr2", 3, "folded"),
+                                            ("schwarzschild", 5, "folded")])
 def test_rk4_steps(name, steps, alg):
     gh = _gh()
     w = CASES[name]()
