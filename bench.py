@@ -178,7 +178,7 @@ def run_ours(args, w):
     import torch
     from paper_1804_09101_gb300 import build
     build.build()
-    from paper_1804_09101_gb300 import costmodel, gh
+    from paper_1804_09101_gb300 import costmodel, gh, replicas
 
     rank, world, local = dist_env()
     pg = None
@@ -238,13 +238,10 @@ def run_ours(args, w):
         fam_ms[name] = gh.gh_profile_read(dom, fam)
     gh.gh_profile_enable(dom, False)
     gh.gh_sync(dom)
-    if pg is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t[0])
+    total_ms = replicas.max_over_ranks(total_ms, pg)
 
     pts = w.points()
-    value = world * pts * 4 * args.steps / (total_ms / 1000.0)
+    value = replicas.job_throughput(pts * 4 * args.steps, world, total_ms)
 
     # ---- end to end through the C ABI with host buffers
     u_host = u.detach().cpu().pin_memory()
@@ -265,11 +262,8 @@ def run_ours(args, w):
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
     barrier()
-    if pg is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t[0])
-    e2e_value = world * pts * 4 * args.steps / (e2e_ms / 1000.0)
+    e2e_ms = replicas.max_over_ranks(e2e_ms, pg)
+    e2e_value = replicas.job_throughput(pts * 4 * args.steps, world, e2e_ms)
     state_bytes = dom.state_size * 8
 
     # ---- roofline of the dominant kernel (the family with the largest time)
