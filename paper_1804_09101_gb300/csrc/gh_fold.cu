@@ -102,15 +102,27 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     const int m = cosm ? mode : mode - K;
     const double* ab = AB + ((size_t)rr * M + mode) * nth;
     const double cmv = __ldg(P.cm + m);
+    // all (output, parity) accumulators in one loop: independent FMA chains
+    double Sv[2] = {0.0, 0.0}, Tv[2] = {0.0, 0.0};
+    {
+      const size_t mo = (size_t)m * half * half + j;
+      const double* Q0s = P.Q0s + mo;
+      const double* Q0t = P.Q0t + mo;
+      const double* Q1s = TWO ? P.Q1s + mo : nullptr;
+      const double* Q1t = TWO ? P.Q1t + mo : nullptr;
+      for (int jp = 0; jp < half; ++jp) {
+        const double sv = ab[jp], tv = ab[half + jp];
+        Sv[0] = fma(__ldg(Q0s + jp * half), sv, Sv[0]);
+        Tv[0] = fma(__ldg(Q0t + jp * half), tv, Tv[0]);
+        if (TWO) {
+          Sv[1] = fma(__ldg(Q1s + jp * half), sv, Sv[1]);
+          Tv[1] = fma(__ldg(Q1t + jp * half), tv, Tv[1]);
+        }
+      }
+    }
 #pragma unroll
     for (int o2 = 0; o2 < NO; ++o2) {
-      const double* Qs = (o2 == 0 ? P.Q0s : P.Q1s) + (size_t)m * half * half + j;
-      const double* Qt = (o2 == 0 ? P.Q0t : P.Q1t) + (size_t)m * half * half + j;
-      double S = 0.0, T = 0.0;
-      for (int jp = 0; jp < half; ++jp) {
-        S = fma(__ldg(Qs + jp * half), ab[jp], S);
-        T = fma(__ldg(Qt + jp * half), ab[half + jp], T);
-      }
+      const double S = Sv[o2], T = Tv[o2];
       const double sig = (o2 == 0) ? P.sigma0 : P.sigma1;
       const double y1 = S + T, y2 = sig * (S - T);
       int slot = mode;
@@ -144,17 +156,34 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     const int rj = o / W;
     const int rr = rj / nth;
     const int j = rj - rr * nth;
+    // quarter-ring sums of every output in one pass over m (independent chains)
+    double Ee[2] = {0.0, 0.0}, Eo[2] = {0.0, 0.0}, Oe[2] = {0.0, 0.0}, Oo[2] = {0.0, 0.0};
+    {
+      const double* c0 = OUT + (size_t)rj * M;
+      const double* c1 = OUT + (size_t)RB * nth * M + (size_t)rj * M;
+      for (int m = 0; m <= K; ++m) {
+        const double tc = __ldg(P.Tc + (size_t)m * W + k);
+        const double ts = __ldg(P.Ts + (size_t)m * W + k);
+        if (m & 1) {
+          Eo[0] = fma(c0[m], tc, Eo[0]);
+          Oo[0] = fma(c0[K + m], ts, Oo[0]);
+          if (TWO) {
+            Eo[1] = fma(c1[m], tc, Eo[1]);
+            Oo[1] = fma(c1[K + m], ts, Oo[1]);
+          }
+        } else {
+          Ee[0] = fma(c0[m], tc, Ee[0]);
+          if (m > 0) Oe[0] = fma(c0[K + m], ts, Oe[0]);
+          if (TWO) {
+            Ee[1] = fma(c1[m], tc, Ee[1]);
+            if (m > 0) Oe[1] = fma(c1[K + m], ts, Oe[1]);
+          }
+        }
+      }
+    }
 #pragma unroll
     for (int o2 = 0; o2 < NO; ++o2) {
-      const double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M;
-      double Ee = 0.0, Eo = 0.0, Oe = 0.0, Oo = 0.0;
-      for (int m = 0; m <= K; m += 2) Ee = fma(c[m], __ldg(P.Tc + (size_t)m * W + k), Ee);
-      for (int m = 1; m <= K; m += 2) {
-        Eo = fma(c[m], __ldg(P.Tc + (size_t)m * W + k), Eo);
-        Oo = fma(c[K + m], __ldg(P.Ts + (size_t)m * W + k), Oo);
-      }
-      for (int m = 2; m <= K; m += 2) Oe = fma(c[K + m], __ldg(P.Ts + (size_t)m * W + k), Oe);
-      const double Ek = Ee + Eo, Eh = Ee - Eo, Ok = Oe + Oo, Oh = Oo - Oe;
+      const double Ek = Ee[o2] + Eo[o2], Eh = Ee[o2] - Eo[o2], Ok = Oe[o2] + Oo[o2], Oh = Oo[o2] - Oe[o2];
       double* dst = (o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * nph;
       if (k == 0) {
         dst[0] = Ek + Ok;

@@ -852,7 +852,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     pb[s] = npb;
     nrb += (int)((gh::NF * (long long)sh.na + 127) / 128);
     d->max_n_r = std::max(d->max_n_r, sh.n_r);
-    npb += sh.n_r * ((sh.na + 127) / 128);
+    npb += sh.n_r * ((sh.na + gh::PT_THREADS - 1) / gh::PT_THREADS);
   }
   rb[n_shells] = nrb;
   pb[n_shells] = npb;

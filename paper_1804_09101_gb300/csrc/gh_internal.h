@@ -14,6 +14,10 @@ constexpr int NF = 50;      // evolved fields per point
 constexpr int NC = 64;      // stored constraint components per point
 constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
 constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
+#ifndef GH_PT_THREADS
+#define GH_PT_THREADS 32
+#endif
+constexpr int PT_THREADS = GH_PT_THREADS;  // threads per block of the per-point kernels
 
 // Separable spherical-harmonic map of one shell (Y_lm = Pbar_lm(theta) x
 // Fourier(phi)): phi-DFT, one N_theta x N_theta Legendre map per Fourier mode,

@@ -29,13 +29,14 @@ template <bool FILTER>
 __global__ void __launch_bounds__(RAD_THREADS)
 radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
               const double* __restrict__ in, double* __restrict__ out) {
-  __shared__ double Ms[MAXR * MAXR];
+  __shared__ double Ms[(MAXR + 3) * MAXR];
   extern __shared__ double Vs[];           // [n_r][RAD_THREADS]
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int n = sh.n_r;
   const double* M = FILTER ? sh.Fr : sh.Dr;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ms[i] = M[i];
+  const int npad = ((n + 3) / 4) * 4;
+  for (int i = threadIdx.x; i < npad * n; i += blockDim.x) Ms[i] = (i < n * n) ? M[i] : 0.0;
   const long long cols = (long long)NF * sh.na;
   const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
   const bool valid = col < cols;
@@ -45,21 +46,22 @@ radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __re
   if (!valid) return;
   double* dst = out + sh.off + col;
   const double* v = Vs + threadIdx.x;
-  int r = 0;
-  for (; r + 1 < n; r += 2) {              // two outputs per pass: two independent FMA chains
-    double a0 = 0.0, a1 = 0.0;
+  // four outputs per pass: four independent FMA chains keep the slow FP64
+  // pipe supplied (the matrix rows past n are zero-padded in shared memory)
+  for (int r = 0; r < n; r += 4) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    const double* m0 = Ms + r * n;
     for (int q = 0; q < n; ++q) {
       const double x = v[q * RAD_THREADS];
-      a0 = fma(Ms[r * n + q], x, a0);
-      a1 = fma(Ms[(r + 1) * n + q], x, a1);
+      a0 = fma(m0[q], x, a0);
+      a1 = fma(m0[n + q], x, a1);
+      a2 = fma(m0[2 * n + q], x, a2);
+      a3 = fma(m0[3 * n + q], x, a3);
     }
     dst[(long long)r * cols] = a0;
-    dst[(long long)(r + 1) * cols] = a1;
-  }
-  if (r < n) {
-    double a0 = 0.0;
-    for (int q = 0; q < n; ++q) a0 = fma(Ms[r * n + q], v[q * RAD_THREADS], a0);
-    dst[(long long)r * cols] = a0;
+    if (r + 1 < n) dst[(long long)(r + 1) * cols] = a1;
+    if (r + 2 < n) dst[(long long)(r + 2) * cols] = a2;
+    if (r + 3 < n) dst[(long long)(r + 3) * cols] = a3;
   }
 }
 
@@ -279,7 +281,6 @@ cudaError_t sep_set_smem_limits(size_t bytes) {
 //   and leave the combine to the boundary kernel; elsewhere skip k and write
 //   stage 1: acc = k,  us = u0 + dt/2 k;   stage 2: acc += 2k, us = u0 + dt/2 k
 //   stage 3: acc += 2k, us = u0 + dt k;    stage 4: us = u0 + dt/6 (acc + k)
-constexpr int PT_THREADS = 128;
 
 struct PointwiseArgs {
   const ShellDev* shells;
@@ -299,25 +300,41 @@ struct PointwiseArgs {
   int stage;
 };
 
-__device__ __forceinline__ void stage_combine(int stage, double dt, double kv, long long idx,
+__device__ __forceinline__ double stage_factor(int stage) {
+  // u_s = u0 + stage_factor * dt * (k or acc + k)
+  return stage == 3 ? 1.0 : (stage == 4 ? 1.0 / 6.0 : 0.5);
+}
+
+__device__ __forceinline__ void stage_combine(int stage, double cdt, double kv, long long idx,
                                               const double* u0, double* acc, double* us) {
+  // cdt = stage_factor(stage) * dt
   const double u0v = u0[idx];
   if (stage == 1) {
     acc[idx] = kv;
-    us[idx] = u0v + 0.5 * dt * kv;
-  } else if (stage == 2) {
-    acc[idx] += 2.0 * kv;
-    us[idx] = u0v + 0.5 * dt * kv;
-  } else if (stage == 3) {
-    acc[idx] += 2.0 * kv;
-    us[idx] = u0v + dt * kv;
+    us[idx] = fma(cdt, kv, u0v);
+  } else if (stage == 2 || stage == 3) {
+    acc[idx] = fma(2.0, kv, acc[idx]);
+    us[idx] = fma(cdt, kv, u0v);
   } else {
-    us[idx] = u0v + (dt / 6.0) * (acc[idx] + kv);
+    us[idx] = fma(cdt, acc[idx] + kv, u0v);
   }
 }
 
+#ifndef GH_PT_MINB
+#define GH_PT_MINB 9
+#endif
+#ifdef GH_PT_MAXNREG
+#define GH_PT_BOUNDS __maxnreg__(GH_PT_MAXNREG)
+#else
+#define GH_PT_BOUNDS __launch_bounds__(PT_THREADS, GH_PT_MINB)
+#endif
+// The algebra below is arranged so that almost every FP64 operation is an
+// FMA (GB300's FP64 pipe issues DADD and DMUL no faster than DFMA): the
+// constant factors (alpha, gamma's, 1/2) are folded into per-point
+// coefficient arrays, each output is built as one FMA chain, and the
+// Christoffel symbols are carried as E = 2 Gamma.
 template <bool RHS, bool CONSTRAINTS>
-__global__ void __launch_bounds__(PT_THREADS)
+__global__ void GH_PT_BOUNDS
 pointwise_kernel(PointwiseArgs a) {
   const int s = find_segment(a.begin, a.n_shells, blockIdx.x);
   const ShellDev& sh = a.shells[s];
@@ -347,173 +364,271 @@ pointwise_kernel(PointwiseArgs a) {
 
     Split S;
     spacetime_split(psi, S);
-    double Gam[40];
-    christoffel(S, Pi, Phi, Gam);
-    double C[4];
-    trace_gamma(S, Gam, C);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) C[c] += H[c];
     const double al = S.alpha;
     const double g0 = a.gamma0, g1 = a.gamma1, g2 = a.gamma2;
 
-    // ---- sources of the Pi equation that need no derivative (10 values)
-    double srcPi[10];
-    double srcPhi[30];
-    if (RHS) {
-      // nabla_(a H_b) = d_(a H_b) - psi^cd Gam_d(ab) H_c ;  d_0 H = 0
-      double dH[12];
+    // E[a][p(b,c)] = 2 Gamma_abc = d_b psi_ac + d_c psi_ab - d_a psi_bc with
+    // d_0 psi = -alpha Pi + beta^k Phi_k, d_i psi = Phi_i.  Entries with a
+    // repeated index reduce to one term (a=b: d_c psi_aa) or one FMA.
+    double E[40];
+    {
+      double d0[10];
 #pragma unroll
-      for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
-      double PH[4];  // psi^cd H_c  (raised H)
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        double acc = 0.0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(c, d)] * H[c];
-        PH[d] = acc;
-      }
-      // P_a[d][e] = psi^dc Gam_ace  (used for the Gam Gam term)
-      double Pm[4][16];
+      for (int p = 0; p < 10; ++p)
+        d0[p] = fma(S.beta_up[2], Phi[20 + p], fma(S.beta_up[1], Phi[10 + p], fma(S.beta_up[0], Phi[p], -al * Pi[p])));
+#define GH_DPSI(c, p) ((c) == 0 ? d0[(p)] : Phi[((c) - 1) * 10 + (p)])
 #pragma unroll
       for (int aa = 0; aa < 4; ++aa)
 #pragma unroll
-        for (int d = 0; d < 4; ++d)
+        for (int b = 0; b < 4; ++b)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(d, c)] * Gam[aa * 10 + sym_index(c, e)];
-            Pm[aa][d * 4 + e] = acc;
+          for (int c = b; c < 4; ++c) {
+            double e;
+            if (b == c)
+              e = (aa == b) ? GH_DPSI(aa, sym_index(aa, aa))
+                            : fma(2.0, GH_DPSI(b, sym_index(aa, b)), -GH_DPSI(aa, sym_index(b, b)));
+            else if (aa == b)
+              e = GH_DPSI(c, sym_index(aa, aa));
+            else if (aa == c)
+              e = GH_DPSI(b, sym_index(aa, aa));
+            else
+              e = (GH_DPSI(b, sym_index(aa, c)) + GH_DPSI(c, sym_index(aa, b))) - GH_DPSI(aa, sym_index(b, c));
+            E[aa * 10 + sym_index(b, c)] = e;
           }
-      // U_i[d][a] = psi^dc Phi_ica ; W_j[d][a] = g^ij U_i[d][a]
-      double Wm[3][16];
-      {
-        double Um[3][16];
+#undef GH_DPSI
+    }
+    // C_a = H_a + psi^bc Gamma_abc: packed sum, diagonal pairs weighted 1/2
+    double C[4];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+    for (int aa = 0; aa < 4; ++aa) {
+      double acc = H[aa];
+#pragma unroll
+      for (int p = 0; p < 10; ++p)
+        acc = fma(pair_a(p) == pair_b(p) ? 0.5 * S.psi_inv[p] : S.psi_inv[p], E[aa * 10 + p], acc);
+      C[aa] = acc;
+    }
+
+    // ---- sources of the Pi equation that need no derivative (10 values)
+    double srcPi[10];
+    double c1[3], Mp[3][3];   // Phi-equation sources: c1[i] Pi_p + Mp[i][k] Phi_kp
+    if (RHS) {
+      const double a2 = 2.0 * al;
+      // T1: 2 alpha psi^cd g^ij Phi_ica Phi_jdb.  Raise the derivative index
+      // first (R^j = 2 alpha g^ij Phi_i), then U_j[d][a] = psi^dc R^j_ca.
+      {
+        double ga2[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) ga2[m] = a2 * S.ginv[m];
+        double R[30];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int p = 0; p < 10; ++p)
+            R[j * 10 + p] = fma(ga2[s3(2, j)], Phi[20 + p], fma(ga2[s3(1, j)], Phi[10 + p], ga2[s3(0, j)] * Phi[p]));
+        double U[3][16];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
 #pragma unroll
           for (int d = 0; d < 4; ++d)
 #pragma unroll
             for (int aa = 0; aa < 4; ++aa) {
-              double acc = 0.0;
+              double acc = S.psi_inv[sym_index(d, 0)] * R[j * 10 + sym_index(0, aa)];
 #pragma unroll
-              for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(d, c)] * Phi[i * 10 + sym_index(c, aa)];
-              Um[i][d * 4 + aa] = acc;
+              for (int c = 1; c < 4; ++c) acc = fma(S.psi_inv[sym_index(d, c)], R[j * 10 + sym_index(c, aa)], acc);
+              U[j][d * 4 + aa] = acc;
             }
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+        for (int p = 0; p < 10; ++p) {
+          const int A = pair_a(p), B = pair_b(p);
+          double acc = U[0][A] * Phi[sym_index(0, B)];
 #pragma unroll
-          for (int e = 0; e < 16; ++e)
-            Wm[j][e] = S.ginv[s3(0, j)] * Um[0][e] + S.ginv[s3(1, j)] * Um[1][e] + S.ginv[s3(2, j)] * Um[2][e];
-      }
-      // t^c t^d Pi_cd, t^c Pi_ci, t^c C_c
-      double tPt = 0.0, tC = 0.0;
-      double tPi[3] = {0.0, 0.0, 0.0};
+          for (int j = 0; j < 3; ++j)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tC += S.t_up[c] * C[c];
-#pragma unroll
-        for (int d = 0; d < 4; ++d) tPt += S.t_up[c] * S.t_up[d] * Pi[sym_index(c, d)];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) tPi[i] += S.t_up[c] * Pi[sym_index(c, 1 + i)];
-      }
-      // (t^c Pi_ci) g^ij  -> v^j
-      double tPig[3];
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        tPig[j] = tPi[0] * S.ginv[s3(0, j)] + tPi[1] * S.ginv[s3(1, j)] + tPi[2] * S.ginv[s3(2, j)];
-      const double t_dn0 = -al;
-#pragma unroll
-      for (int p = 0; p < 10; ++p) {
-        const int A = pair_a(p), B = pair_b(p);
-        double T1 = 0.0, T2 = 0.0, T3 = 0.0;
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int d = 0; d < 4; ++d) T1 += Wm[j][d * 4 + A] * Phi[j * 10 + sym_index(d, B)];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double pc = 0.0;
-#pragma unroll
-          for (int d = 0; d < 4; ++d) pc += S.psi_inv[sym_index(c, d)] * Pi[sym_index(d, B)];
-          T2 += Pi[sym_index(c, A)] * pc;
+            for (int d = 0; d < 4; ++d)
+              if (j > 0 || d > 0) acc = fma(U[j][d * 4 + A], Phi[j * 10 + sym_index(d, B)], acc);
+          srcPi[p] = acc;
         }
-#pragma unroll
-        for (int d = 0; d < 4; ++d)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) T3 += Pm[A][d * 4 + e] * Pm[B][e * 4 + d];
-        // nabla_(A H_B)
-        const double dAHB = (A > 0 ? dH[4 * (A - 1) + B] : 0.0);
-        const double dBHA = (B > 0 ? dH[4 * (B - 1) + A] : 0.0);
-        double gh = 0.0;
-#pragma unroll
-        for (int d = 0; d < 4; ++d) gh += PH[d] * Gam[d * 10 + p];
-        const double nablaH = 0.5 * (dAHB + dBHA) - gh;
-        // gamma0 damping: t_B C_A + t_A C_B - psi_AB t^c C_c, t_a = (-alpha,0,0,0)
-        const double damp = (B == 0 ? t_dn0 * C[A] : 0.0) + (A == 0 ? t_dn0 * C[B] : 0.0) - psi[p] * tC;
-        double tPiPhi = 0.0, bPhi = 0.0;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          tPiPhi += tPig[j] * Phi[j * 10 + p];
-          bPhi += S.beta_up[j] * Phi[j * 10 + p];
-        }
-        srcPi[p] = 2.0 * al * (T1 - T2 - T3) - 2.0 * al * nablaH - 0.5 * al * tPt * Pi[p] -
-                   al * tPiPhi + g0 * al * damp - g1 * g2 * bPhi;
       }
-      // Phi equation sources: 1/2 alpha t^c t^d Phi_icd Pi_ab
-      //   + alpha g^jk t^c Phi_ijc Phi_kab - alpha gamma2 Phi_iab
-      double tPhit[3], Mik[3][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        double acc = 0.0;
+      // T2: -2 alpha psi^cd Pi_ca Pi_db  (P[c][b] = -2 alpha psi^cd Pi_db)
+      {
+        double P[16];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int d = 0; d < 4; ++d) acc += S.t_up[c] * S.t_up[d] * Phi[i * 10 + sym_index(c, d)];
-        tPhit[i] = acc;
-        double tPhi_j[3];
+          for (int b = 0; b < 4; ++b) {
+            double acc = S.psi_inv[sym_index(c, 0)] * Pi[sym_index(0, b)];
+#pragma unroll
+            for (int d = 1; d < 4; ++d) acc = fma(S.psi_inv[sym_index(c, d)], Pi[sym_index(d, b)], acc);
+            P[c * 4 + b] = -a2 * acc;
+          }
+#pragma unroll
+        for (int p = 0; p < 10; ++p) {
+          const int A = pair_a(p), B = pair_b(p);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) srcPi[p] = fma(Pi[sym_index(c, A)], P[c * 4 + B], srcPi[p]);
+        }
+      }
+      // T3: -2 alpha psi^cd psi^ef Gamma_ace Gamma_bdf = -(alpha/2) sum_de Q_a[d][e] Q_b[e][d]
+      // with Q_a[d][e] = psi^dc E_a[ce]
+      {
+        double Q[4][16];
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              double acc = S.psi_inv[sym_index(d, 0)] * E[aa * 10 + sym_index(0, e)];
+#pragma unroll
+              for (int c = 1; c < 4; ++c) acc = fma(S.psi_inv[sym_index(d, c)], E[aa * 10 + sym_index(c, e)], acc);
+              Q[aa][d * 4 + e] = acc;
+            }
+        const double mh = -0.5 * al;
+#pragma unroll
+        for (int p = 0; p < 10; ++p) {
+          const int A = pair_a(p), B = pair_b(p);
+          double t3 = Q[A][0] * Q[B][0];
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (d > 0 || e > 0) t3 = fma(Q[A][d * 4 + e], Q[B][e * 4 + d], t3);
+          srcPi[p] = fma(mh, t3, srcPi[p]);
+        }
+      }
+      // remaining Pi sources, one FMA chain per pair:
+      //   -2 alpha nabla_(a H_b) = -alpha (d_a H_b + d_b H_a) + alpha psi^cd H_c E_d[ab]
+      //   -1/2 alpha t^c t^d Pi_cd Pi_ab
+      //   (-alpha t^c Pi_ci g^ij - gamma1 gamma2 beta^j) Phi_jab
+      //   + alpha gamma0 (t_b C_a + t_a C_b - psi_ab t^c C_c),  t_a = (-alpha, 0, 0, 0)
+      {
+        double dH[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
+        double aH[4], PHa[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) aH[c] = al * H[c];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          double acc = S.psi_inv[sym_index(0, d)] * aH[0];
+#pragma unroll
+          for (int c = 1; c < 4; ++c) acc = fma(S.psi_inv[sym_index(c, d)], aH[c], acc);
+          PHa[d] = acc;
+        }
+        // tt[p] = t^a t^b, off-diagonal pairs doubled (for t^c t^d X_cd sums)
+        double tt[10];
+#pragma unroll
+        for (int p = 0; p < 10; ++p) {
+          const int A = pair_a(p), B = pair_b(p);
+          tt[p] = (A == B ? S.t_up[A] : 2.0 * S.t_up[A]) * S.t_up[B];
+        }
+        double tPt = tt[0] * Pi[0];
+#pragma unroll
+        for (int p = 1; p < 10; ++p) tPt = fma(tt[p], Pi[p], tPt);
+        const double k1 = -0.5 * al * tPt;
+        double tPi[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          double acc = S.t_up[0] * Pi[sym_index(0, 1 + i)];
+#pragma unroll
+          for (int c = 1; c < 4; ++c) acc = fma(S.t_up[c], Pi[sym_index(c, 1 + i)], acc);
+          tPi[i] = acc;
+        }
+        const double g12 = g1 * g2;
+        double qv[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-          double t2 = 0.0;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) t2 += S.t_up[c] * Phi[i * 10 + sym_index(1 + j, c)];
-          tPhi_j[j] = t2;
+          const double tg = fma(tPi[2], S.ginv[s3(2, j)], fma(tPi[1], S.ginv[s3(1, j)], tPi[0] * S.ginv[s3(0, j)]));
+          qv[j] = fma(-al, tg, -g12 * S.beta_up[j]);
         }
+        double tC = S.t_up[0] * C[0];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-          Mik[i][k] = tPhi_j[0] * S.ginv[s3(0, k)] + tPhi_j[1] * S.ginv[s3(1, k)] + tPhi_j[2] * S.ginv[s3(2, k)];
+        for (int c = 1; c < 4; ++c) tC = fma(S.t_up[c], C[c], tC);
+        const double kd1 = -al * al * g0, kd2 = -al * g0 * tC;
+#pragma unroll
+        for (int p = 0; p < 10; ++p) {
+          const int A = pair_a(p), B = pair_b(p);
+          double acc = srcPi[p];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) acc = fma(PHa[d], E[d * 10 + p], acc);
+          if (A > 0 || B > 0) {
+            const double dAHB = (A > 0 ? dH[4 * (A - 1) + B] : 0.0);
+            const double dBHA = (B > 0 ? dH[4 * (B - 1) + A] : 0.0);
+            acc = fma(-al, (A > 0 && B > 0) ? dAHB + dBHA : (A > 0 ? dAHB : dBHA), acc);
+          }
+          acc = fma(k1, Pi[p], acc);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc = fma(qv[j], Phi[j * 10 + p], acc);
+          acc = fma(kd2, psi[p], acc);
+          if (p == 0) acc = fma(2.0 * kd1, C[0], acc);
+          else if (A == 0) acc = fma(kd1, C[B], acc);
+          srcPi[p] = acc;
+        }
+        // Phi sources: 1/2 alpha t^c t^d Phi_icd Pi_ab + alpha g^jk t^c Phi_ijc Phi_kab
+        //              - alpha gamma2 Phi_iab
+        const double hal = 0.5 * al, ag2 = al * g2;
+        double gal[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) gal[m] = al * S.ginv[m];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          double acc = tt[0] * Phi[i * 10];
+#pragma unroll
+          for (int p = 1; p < 10; ++p) acc = fma(tt[p], Phi[i * 10 + p], acc);
+          c1[i] = hal * acc;
+          double tj[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            double t2 = S.t_up[0] * Phi[i * 10 + sym_index(1 + j, 0)];
+#pragma unroll
+            for (int c = 1; c < 4; ++c) t2 = fma(S.t_up[c], Phi[i * 10 + sym_index(1 + j, c)], t2);
+            tj[j] = t2;
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double m = fma(tj[2], gal[s3(2, k)], fma(tj[1], gal[s3(1, k)], tj[0] * gal[s3(0, k)]));
+            Mp[i][k] = (i == k) ? m - ag2 : m;
+          }
+        }
       }
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int p = 0; p < 10; ++p)
-          srcPhi[i * 10 + p] = 0.5 * al * tPhit[i] * Pi[p] +
-                               al * (Mik[i][0] * Phi[p] + Mik[i][1] * Phi[10 + p] + Mik[i][2] * Phi[20 + p]) -
-                               al * g2 * Phi[i * 10 + p];
     }
 
-    // beta^k J_k^d and g^ki J_k^d (spherical-basis contractions)
-    double bs[3], Gs[3][3];
+    // loop-invariant coefficients of the derivative terms (spherical basis):
+    //   bs[d] = beta^k J_k^d,  Gsa[i][d] = -alpha g^ki J_k^d,
+    //   Ja = -alpha J,  Jg = alpha gamma2 J
+    double bs[3], Gsa[3][3], Ja[3][3], Jg[3][3];
+    {
+      const double ag2 = al * g2;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      bs[d] = S.beta_up[0] * G.J[0][d] + S.beta_up[1] * G.J[1][d] + S.beta_up[2] * G.J[2][d];
+      for (int d = 0; d < 3; ++d) {
+        bs[d] = fma(S.beta_up[2], G.J[2][d], fma(S.beta_up[1], G.J[1][d], S.beta_up[0] * G.J[0][d]));
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-        Gs[i][d] = S.ginv[s3(0, i)] * G.J[0][d] + S.ginv[s3(1, i)] * G.J[1][d] + S.ginv[s3(2, i)] * G.J[2][d];
+        for (int i = 0; i < 3; ++i) {
+          const double gj = fma(S.ginv[s3(2, i)], G.J[2][d], fma(S.ginv[s3(1, i)], G.J[1][d], S.ginv[s3(0, i)] * G.J[0][d]));
+          Gsa[i][d] = -al * gj;
+          Ja[i][d] = -al * G.J[i][d];
+          Jg[i][d] = ag2 * G.J[i][d];
+        }
+      }
     }
+    const double g1p = 1.0 + g1, g12 = g1 * g2;
+    const double nbg[3] = {-g1 * S.beta_up[0], -g1 * S.beta_up[1], -g1 * S.beta_up[2]};
 
     // constraint components of this point: c_out[64 pt_off + (ir*64 + comp)*na + q]
     const long long cbase = 64LL * sh.pt_off + (long long)ir * NC * na + q;
     if (CONSTRAINTS) {
-      double c2 = 0.0;
+      double c2 = C[0] * C[0];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        c2 += C[c] * C[c];
-        if (a.c_out) a.c_out[cbase + (long long)c * na] = C[c];
+      for (int c = 1; c < 4; ++c) c2 = fma(C[c], C[c], c2);
+      if (a.c_out) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a.c_out[cbase + (long long)c * na] = C[c];
       }
       cdens = c2;
     }
 
+    const bool on_bc = (ir == 0 && sh.bc_inner >= 0) || (ir == sh.n_r - 1 && sh.bc_outer >= 0);
+    const double cdt = stage_factor(a.stage) * a.dt * sh.dt_scale;
     // ---- derivative terms, one symmetric pair at a time
 #pragma unroll 1
     for (int p = 0; p < 10; ++p) {
@@ -529,29 +644,21 @@ pointwise_kernel(PointwiseArgs a) {
           dPhi[i][0] = a.dr[o3]; dPhi[i][1] = a.dth[o3]; dPhi[i][2] = a.dph[o3];
         }
       }
-      // Cartesian derivatives d_i psi_p, d_i Pi_p
-      double cpsi[3], cPi[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        cpsi[i] = G.J[i][0] * dpsi[0] + G.J[i][1] * dpsi[1] + G.J[i][2] * dpsi[2];
-        cPi[i] = G.J[i][0] * dPi[0] + G.J[i][1] * dPi[1] + G.J[i][2] * dPi[2];
-      }
       if (CONSTRAINTS) {
         // C_iab = d_i psi_ab - Phi_iab ; C_ijab = d_i Phi_jab - d_j Phi_iab
-        double cPhi[3][3];  // cPhi[k][i] = d_k Phi_ip
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-            cPhi[k][i] = G.J[k][0] * dPhi[i][0] + G.J[k][1] * dPhi[i][1] + G.J[k][2] * dPhi[i][2];
         double c3[3], c4[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) c3[i] = cpsi[i] - Phi[i * 10 + p];
-        c4[0] = cPhi[0][1] - cPhi[1][0];
-        c4[1] = cPhi[0][2] - cPhi[2][0];
-        c4[2] = cPhi[1][2] - cPhi[2][1];
+        for (int i = 0; i < 3; ++i)
+          c3[i] = fma(G.J[i][2], dpsi[2], fma(G.J[i][1], dpsi[1], fma(G.J[i][0], dpsi[0], -Phi[i * 10 + p])));
+        // d_k Phi_i = J[k] . dPhi[i]
+        auto dk = [&](int k, int i) {
+          return fma(G.J[k][2], dPhi[i][2], fma(G.J[k][1], dPhi[i][1], G.J[k][0] * dPhi[i][0]));
+        };
+        c4[0] = dk(0, 1) - dk(1, 0);
+        c4[1] = dk(0, 2) - dk(2, 0);
+        c4[2] = dk(1, 2) - dk(2, 1);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) cdens += c3[i] * c3[i] + c4[i] * c4[i];
+        for (int i = 0; i < 3; ++i) cdens = fma(c4[i], c4[i], fma(c3[i], c3[i], cdens));
         if (a.c_out) {
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
@@ -561,29 +668,46 @@ pointwise_kernel(PointwiseArgs a) {
         }
       }
       if (RHS) {
-        const double bdpsi = bs[0] * dpsi[0] + bs[1] * dpsi[1] + bs[2] * dpsi[2];
-        const double bdPi = bs[0] * dPi[0] + bs[1] * dPi[1] + bs[2] * dPi[2];
-        double gdPhi = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          gdPhi += Gs[i][0] * dPhi[i][0] + Gs[i][1] * dPhi[i][1] + Gs[i][2] * dPhi[i][2];
-        const double bPhi = S.beta_up[0] * Phi[p] + S.beta_up[1] * Phi[10 + p] + S.beta_up[2] * Phi[20 + p];
+        const double bdpsi = fma(bs[2], dpsi[2], fma(bs[1], dpsi[1], bs[0] * dpsi[0]));
         double out[5];
-        out[0] = (1.0 + g1) * bdpsi - al * Pi[p] - g1 * bPhi;
-        out[1] = bdPi - al * gdPhi + g1 * g2 * bdpsi + srcPi[p];
+        // psi: (1 + gamma1) beta.d psi - alpha Pi - gamma1 beta^k Phi_k
+        {
+          double acc = fma(-al, Pi[p], g1p * bdpsi);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc = fma(nbg[k], Phi[k * 10 + p], acc);
+          out[0] = acc;
+        }
+        // Pi: src + beta.d Pi - alpha g^ki d_k Phi_i + gamma1 gamma2 beta.d psi
+        {
+          double acc = fma(g12, bdpsi, srcPi[p]);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) acc = fma(bs[d], dPi[d], acc);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) acc = fma(Gsa[i][d], dPhi[i][d], acc);
+          out[1] = acc;
+        }
+        // Phi_i: src + beta.d Phi_i - alpha d_i Pi + alpha gamma2 d_i psi
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const double bdPhi = bs[0] * dPhi[i][0] + bs[1] * dPhi[i][1] + bs[2] * dPhi[i][2];
-          out[2 + i] = bdPhi - al * cPi[i] + al * g2 * cpsi[i] + srcPhi[i * 10 + p];
+          double acc = c1[i] * Pi[p];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc = fma(Mp[i][k], Phi[k * 10 + p], acc);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            acc = fma(bs[d], dPhi[i][d], acc);
+            acc = fma(Ja[i][d], dPi[d], acc);
+            acc = fma(Jg[i][d], dpsi[d], acc);
+          }
+          out[2 + i] = acc;
         }
         const int fidx[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
-        const bool on_bc = (ir == 0 && sh.bc_inner >= 0) || (ir == sh.n_r - 1 && sh.bc_outer >= 0);
-        const double dts = a.dt * sh.dt_scale;
 #pragma unroll
         for (int e = 0; e < 5; ++e) {
           const long long idx = base + (long long)fidx[e] * na;
           if (a.stage == 0 || on_bc) a.k[idx] = out[e];
-          else stage_combine(a.stage, dts, out[e], idx, a.u0, a.acc, a.us);
+          else stage_combine(a.stage, cdt, out[e], idx, a.u0, a.acc, a.us);
         }
       }
     }
@@ -653,7 +777,7 @@ __device__ __forceinline__ void char_project_pair(const double* k, long long bas
 }
 
 __device__ __forceinline__ void char_write_pair(const BcArgs& a, long long base, int na, int p, const CharPair& c,
-                                                const double n_dn[3], double g2, double dts) {
+                                                const double n_dn[3], double g2, double cdt) {
   double v[5];
   v[0] = c.psi;
   v[1] = 0.5 * (c.wp + c.wm) + g2 * c.psi;
@@ -665,7 +789,7 @@ __device__ __forceinline__ void char_write_pair(const BcArgs& a, long long base,
   for (int e = 0; e < 5; ++e) {
     const long long idx = base + (long long)f[e] * na;
     if (a.stage == 0) a.k[idx] = v[e];
-    else stage_combine(a.stage, dts, v[e], idx, a.u0, a.acc, a.us);
+    else stage_combine(a.stage, cdt, v[e], idx, a.u0, a.acc, a.us);
   }
 }
 
@@ -704,7 +828,7 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     if (v_0 < 0.0) c.w0[0] = c.w0[1] = c.w0[2] = 0.0;
     if (v_p < 0.0) c.wp = 0.0;
     if (v_m < 0.0) c.wm = 0.0;
-    char_write_pair(a, base, na, p, c, n_dn, g2, a.dt * sl.dt_scale);
+    char_write_pair(a, base, na, p, c, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
   } else {
     const long long ba = sl.off_a + q, bb = sl.off_b + q;
     CharPair ci, co;
@@ -715,8 +839,8 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     for (int i = 0; i < 3; ++i) select_pair(ci.w0[i], co.w0[i], v_0);
     select_pair(ci.wp, co.wp, v_p);
     select_pair(ci.wm, co.wm, v_m);
-    char_write_pair(a, ba, na, p, ci, n_dn, g2, a.dt * sl.dt_scale);
-    char_write_pair(a, bb, na, p, co, n_dn, g2, a.dt * sl.dt_scale);
+    char_write_pair(a, ba, na, p, ci, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
+    char_write_pair(a, bb, na, p, co, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
   }
 }
 
