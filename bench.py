@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default work schedule instead of running gh_autotune before timing")
     p.add_argument("--workload", default="kerr4",
                    choices=["kerr4", "large", "schwarzschild", "batched", "adjoint"],
                    help="kerr4: 4-shell Kerr a=0.9 (default, the headline); large: 8-shell Kerr a=0.95, "
@@ -192,6 +194,8 @@ def run_ours(args, w):
     dom = gh.Domain.from_workload(w)
     gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
                               "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
+    if not args.no_autotune:
+        gh.gh_autotune(dom, 5)
     u = dom.new_state()
     gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
     p = w.pulse
@@ -294,9 +298,10 @@ def run_ours(args, w):
                 dtype="f64", data="synthetic",
                 config=dict(workload=w.name, points=pts, shells=[list(s) for s in w.shells], chi=w.chi,
                             dt=w.dt, rhs_evals_per_step=4,
-                            step="RK4 step + ExpCheb(36,32) + SH keep l<=10 + constraint norms",
+                            step="RK4 step + ExpCheb(36,32) + SH keep l<=%d + constraint norms" % w.sh_keep_l,
                             l2="flushed before every timed step (256 MB write, outside the step events)",
-                            parallelism="replicas" if world > 1 else "single GPU"),
+                            parallelism="replicas" if world > 1 else "single GPU",
+                            schedule=gh.gh_get_schedule(dom), autotuned=not args.no_autotune),
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=state_bytes,
                          d2h_bytes_per_step=state_bytes + 8 * len(w.shells)),
                 gpu_launches=launches, roofline=roofline, kernels=kernels)
@@ -331,6 +336,8 @@ def run_batched(args):
         gh.gh_set_analytic_kerr_schild(dom, b_, h["M"], h["chi"], u)
         gh.gh_set_dt_scale(dom, b_, h["dt"])
     u += noise
+    if not args.no_autotune:
+        gh.gh_autotune(dom, 5)
     work = dom.new_work()
     norm2 = torch.zeros(len(w.holes), dtype=torch.float64, device=dev)
     # per-family profile from direct (non-graph) steps
@@ -378,6 +385,8 @@ def run_batched(args):
         gh.gh_set_dt_scale(d1, 0, h["dt"])
         u1 += noise[off:off + d1.state_size]
         off += d1.state_size
+        if not args.no_autotune:
+            gh.gh_autotune(d1, 3)
         doms.append((d1, u1, d1.new_work(), torch.zeros(1, dtype=torch.float64, device=dev)))
     for _ in range(args.warmup):
         for d1, u1, w1, n1 in doms:
@@ -436,6 +445,8 @@ def run_adjoint(args):
     from paper_1804_09101_gb300.adjoint import constraint_energy_gradient, evolve_energy
     w = workloads.adjoint_single_shell()
     dom = gh.Domain.from_workload(w)
+    if not args.no_autotune:
+        gh.gh_autotune(dom, 5)
     u0 = dom.new_state()
     gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u0)
     p = w.pulse

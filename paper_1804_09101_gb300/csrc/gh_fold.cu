@@ -22,10 +22,19 @@
 
 namespace gh {
 
-constexpr int FOLD_THREADS = 256;
+constexpr int FOLD_MAX_THREADS = 512;
 
+__device__ __forceinline__ double flip_sign(double v, unsigned long long mask) {
+  // v or -v without an FP64 instruction (mask is 0 or the sign bit)
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)mask);
+}
+
+// One block takes RB consecutive (r, field) rows of one shell.  Shared memory
+// per row: the input ring values and their quarter folds, later reused for the
+// synthesis coefficients, plus the Fourier coefficients of both half-rings.
+// The thread count is a launch parameter (a multiple of 32, at most 512).
 template <bool TWO>
-__global__ void __launch_bounds__(FOLD_THREADS)
+__global__ void __launch_bounds__(FOLD_MAX_THREADS)
 fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                     const double* __restrict__ in, double* __restrict__ out0, double* __restrict__ out1) {
   extern __shared__ double sm[];
@@ -35,19 +44,21 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   const int nth = sh.nth, nph = sh.nph, na = sh.na;
   const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = N4 + 1, N2 = nph / 2;
   constexpr int NO = TWO ? 2 : 1;
+  const int T = blockDim.x;
   const int rows = NF * sh.n_r;
   const int RB = P.rows_per_cta;
   const int row0 = (blockIdx.x - begin[s]) * RB;
   const int nr = min(RB, rows - row0);
+  const int r1 = max(na + 4 * nth * W, NO * nth * M);
   double* U = sm;                                   // [RB][na]
   double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
-  double* AB = F + (size_t)RB * nth * 4 * W;        // [RB][M][nth]: s (half) then t (half)
-  double* OUT = AB + (size_t)RB * M * nth;          // [NO][RB][nth][M]
+  double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
+  double* AB = sm + (size_t)RB * r1;                // [RB][M][nth]: s (half) then t (half)
   const long long gbase = sh.off + (long long)row0 * na;
-  for (int i = threadIdx.x; i < nr * na; i += FOLD_THREADS) U[i] = in[gbase + i];
+  for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
   __syncthreads();
   // fold every ring: Cp, Cm (cos, even / odd m), Sp, Sm (sin, odd / even m)
-  for (int o = threadIdx.x; o < nr * nth * W; o += FOLD_THREADS) {
+  for (int o = threadIdx.x; o < nr * nth * W; o += T) {
     const int k = o % W;
     const int rj = o / W;
     const double* ring = U + (size_t)rj * nph;
@@ -70,7 +81,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   __syncthreads();
   // phase A: Fourier coefficient of mode for rings j and N_theta-1-j, stored as
   // their sum (symmetric part s) and difference (antisymmetric part t)
-  for (int o = threadIdx.x; o < nr * half * M; o += FOLD_THREADS) {
+  for (int o = threadIdx.x; o < nr * half * M; o += T) {
     const int mode = o % M;
     const int t = o / M;
     const int jh = t % half;
@@ -81,8 +92,8 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
     const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
     const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
-    double c1 = 0.0, c2 = 0.0;
-    for (int k = 0; k < W; ++k) {
+    double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
+    for (int k = 1; k < W; ++k) {
       const double tv = __ldg(tab + k);
       c1 = fma(f1[k], tv, c1);
       c2 = fma(f2[k], tv, c2);
@@ -92,8 +103,9 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     ab[half + jh] = c1 - c2;
   }
   __syncthreads();
-  // phase B: half-size Legendre maps; normalised synthesis coefficients
-  for (int o = threadIdx.x; o < nr * M * half; o += FOLD_THREADS) {
+  // phase B: half-size Legendre maps (tables carry the synthesis factors)
+  const unsigned long long sbit = 0x8000000000000000ULL;
+  for (int o = threadIdx.x; o < nr * M * half; o += T) {
     const int j = o % half;
     const int t = o / half;
     const int mode = t % M;
@@ -101,16 +113,21 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     const bool cosm = mode <= K;
     const int m = cosm ? mode : mode - K;
     const double* ab = AB + ((size_t)rr * M + mode) * nth;
-    const double cmv = __ldg(P.cm + m);
-    // all (output, parity) accumulators in one loop: independent FMA chains
-    double Sv[2] = {0.0, 0.0}, Tv[2] = {0.0, 0.0};
+    double Sv[2], Tv[2];
     {
       const size_t mo = (size_t)m * half * half + j;
       const double* Q0s = P.Q0s + mo;
       const double* Q0t = P.Q0t + mo;
       const double* Q1s = TWO ? P.Q1s + mo : nullptr;
       const double* Q1t = TWO ? P.Q1t + mo : nullptr;
-      for (int jp = 0; jp < half; ++jp) {
+      const double sv0 = ab[0], tv0 = ab[half];
+      Sv[0] = __ldg(Q0s) * sv0;
+      Tv[0] = __ldg(Q0t) * tv0;
+      if (TWO) {
+        Sv[1] = __ldg(Q1s) * sv0;
+        Tv[1] = __ldg(Q1t) * tv0;
+      }
+      for (int jp = 1; jp < half; ++jp) {
         const double sv = ab[jp], tv = ab[half + jp];
         Sv[0] = fma(__ldg(Q0s + jp * half), sv, Sv[0]);
         Tv[0] = fma(__ldg(Q0t + jp * half), tv, Tv[0]);
@@ -122,14 +139,13 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     }
 #pragma unroll
     for (int o2 = 0; o2 < NO; ++o2) {
-      const double S = Sv[o2], T = Tv[o2];
-      const double sig = (o2 == 0) ? P.sigma0 : P.sigma1;
-      const double y1 = S + T, y2 = sig * (S - T);
+      // parity of the output about the equator
+      const unsigned long long par = ((o2 == 0 ? P.sigma0 : P.sigma1) < 0.0) ? sbit : 0ULL;
+      unsigned long long flip = 0ULL;
       int slot = mode;
-      double fac = cmv;
       if (TWO && o2 == 1) {
-        // d/dphi: the value projection of cos mode m feeds sin slot m with -m,
-        // that of sin mode m feeds cos slot m with +m
+        // d/dphi: the value projection of cos mode m feeds sin slot m with
+        // factor -m, that of sin mode m feeds cos slot m with +m
         if (cosm) {
           if (m == 0) {
             double* c = OUT + (size_t)RB * nth * M + (size_t)rr * nth * M;
@@ -138,65 +154,54 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
             continue;
           }
           slot = K + m;
-          fac = -m * cmv;
+          flip = sbit;
         } else {
           slot = m;
-          fac = m * cmv;
         }
       }
+      const double y1 = Sv[o2] + Tv[o2], y2 = Sv[o2] - Tv[o2];
       double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rr * nth * M;
-      c[(size_t)j * M + slot] = fac * y1;
-      c[(size_t)(nth - 1 - j) * M + slot] = fac * y2;
+      c[(size_t)j * M + slot] = flip_sign(y1, flip);
+      c[(size_t)(nth - 1 - j) * M + slot] = flip_sign(y2, flip ^ par);
     }
   }
   __syncthreads();
-  // phase C: quarter-ring sums give four output points each
-  for (int o = threadIdx.x; o < nr * nth * W; o += FOLD_THREADS) {
+  // phase C: quarter-ring sums give four output points each; one item per
+  // (output, ring, k)
+  for (int o = threadIdx.x; o < NO * nr * nth * W; o += T) {
     const int k = o % W;
-    const int rj = o / W;
+    const int t = o / W;
+    const int o2 = TWO ? t % NO : 0;
+    const int rj = TWO ? t / NO : t;
     const int rr = rj / nth;
     const int j = rj - rr * nth;
-    // quarter-ring sums of every output in one pass over m (independent chains)
-    double Ee[2] = {0.0, 0.0}, Eo[2] = {0.0, 0.0}, Oe[2] = {0.0, 0.0}, Oo[2] = {0.0, 0.0};
-    {
-      const double* c0 = OUT + (size_t)rj * M;
-      const double* c1 = OUT + (size_t)RB * nth * M + (size_t)rj * M;
-      for (int m = 0; m <= K; ++m) {
-        const double tc = __ldg(P.Tc + (size_t)m * W + k);
-        const double ts = __ldg(P.Ts + (size_t)m * W + k);
-        if (m & 1) {
-          Eo[0] = fma(c0[m], tc, Eo[0]);
-          Oo[0] = fma(c0[K + m], ts, Oo[0]);
-          if (TWO) {
-            Eo[1] = fma(c1[m], tc, Eo[1]);
-            Oo[1] = fma(c1[K + m], ts, Oo[1]);
-          }
-        } else {
-          Ee[0] = fma(c0[m], tc, Ee[0]);
-          if (m > 0) Oe[0] = fma(c0[K + m], ts, Oe[0]);
-          if (TWO) {
-            Ee[1] = fma(c1[m], tc, Ee[1]);
-            if (m > 0) Oe[1] = fma(c1[K + m], ts, Oe[1]);
-          }
-        }
+    const double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M;
+    double Ee = c[0] * __ldg(P.Tc + k), Eo = 0.0, Oe = 0.0, Oo = 0.0;
+    for (int m = 1; m <= K; m += 2) {
+      const double tc1 = __ldg(P.Tc + (size_t)m * W + k);
+      const double ts1 = __ldg(P.Ts + (size_t)m * W + k);
+      Eo = fma(c[m], tc1, Eo);
+      Oo = fma(c[K + m], ts1, Oo);
+      if (m + 1 <= K) {
+        const double tc2 = __ldg(P.Tc + (size_t)(m + 1) * W + k);
+        const double ts2 = __ldg(P.Ts + (size_t)(m + 1) * W + k);
+        Ee = fma(c[m + 1], tc2, Ee);
+        Oe = fma(c[K + m + 1], ts2, Oe);
       }
     }
-#pragma unroll
-    for (int o2 = 0; o2 < NO; ++o2) {
-      const double Ek = Ee[o2] + Eo[o2], Eh = Ee[o2] - Eo[o2], Ok = Oe[o2] + Oo[o2], Oh = Oo[o2] - Oe[o2];
-      double* dst = (o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * nph;
-      if (k == 0) {
-        dst[0] = Ek + Ok;
-        dst[N2] = Eh + Oh;
-      } else if (k == N4) {
-        dst[N4] = Ek + Ok;
-        dst[nph - N4] = Ek - Ok;
-      } else {
-        dst[k] = Ek + Ok;
-        dst[N2 - k] = Eh + Oh;
-        dst[N2 + k] = Eh - Oh;
-        dst[nph - k] = Ek - Ok;
-      }
+    const double Ek = Ee + Eo, Eh = Ee - Eo, Ok = Oe + Oo, Oh = Oo - Oe;
+    double* dst = (o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * nph;
+    if (k == 0) {
+      dst[0] = Ek + Ok;
+      dst[N2] = Eh + Oh;
+    } else if (k == N4) {
+      dst[N4] = Ek + Ok;
+      dst[nph - N4] = Ek - Ok;
+    } else {
+      dst[k] = Ek + Ok;
+      dst[N2 - k] = Eh + Oh;
+      dst[N2 + k] = Eh - Oh;
+      dst[nph - k] = Ek - Ok;
     }
   }
 }
@@ -208,14 +213,14 @@ cudaError_t fold_set_smem_limits(size_t bytes) {
 }
 
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {
-  fold_angular_kernel<true><<<d->fd_blocks, FOLD_THREADS, d->fd_smem, d->stream>>>(
+  fold_angular_kernel<true><<<d->fd_blocks, d->fd_threads, d->fd_smem, d->stream>>>(
       d->shells_d, d->n_shells, d->fd_block_begin_d, in, dth, dph);
   d->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out) {
-  fold_angular_kernel<false><<<d->ff_blocks, FOLD_THREADS, d->ff_smem, d->stream>>>(
+  fold_angular_kernel<false><<<d->ff_blocks, d->ff_threads, d->ff_smem, d->stream>>>(
       d->shells_d, d->n_shells, d->ff_block_begin_d, in, out, nullptr);
   d->launches++;
   return cudaGetLastError();

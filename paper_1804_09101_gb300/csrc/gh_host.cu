@@ -331,7 +331,7 @@ int sep_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
 // Folded plan (see fold_angular_kernel).
 struct FoldHost {
   int K, M, N4, half;
-  std::vector<double> Tc, Ts, Q0s, Q0t, Q1s, Q1t, cm;
+  std::vector<double> Tc, Ts, Q0s, Q0t, Q1s, Q1t;
   double s0, s1;
 };
 
@@ -354,7 +354,10 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
     }
   std::vector<double> P, dP;
   legendre_tables(g.L, g.ct, g.st, P, dP);
-  auto build = [&](bool dtheta, std::vector<double>& Qs, std::vector<double>& Qt) {
+  // synthesis factor of mode m: c_m for the first output, m c_m for the value
+  // map that feeds d/dphi
+  auto cfac = [&](int m) { return (m == 0 ? 1.0 : 2.0) * 2.0 * kPi / g.nph; };
+  auto build = [&](bool dtheta, bool mscale, std::vector<double>& Qs, std::vector<double>& Qt) {
     Qs.assign((size_t)(K + 1) * half * half, 0.0);
     Qt.assign((size_t)(K + 1) * half * half, 0.0);
     std::vector<double> Q((size_t)nth * nth);
@@ -368,27 +371,31 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
           }
           Q[(size_t)jo * nth + ji] = acc * g.wgl[ji];
         }
+      const double f = (mscale ? (double)m : 1.0) * cfac(m);
       for (int ji = 0; ji < half; ++ji)
         for (int jo = 0; jo < half; ++jo) {
           const double q1 = Q[(size_t)jo * nth + ji], q2 = Q[(size_t)jo * nth + (nth - 1 - ji)];
-          Qs[((size_t)m * half + ji) * half + jo] = 0.5 * (q1 + q2);
-          Qt[((size_t)m * half + ji) * half + jo] = 0.5 * (q1 - q2);
+          Qs[((size_t)m * half + ji) * half + jo] = f * (0.5 * (q1 + q2));
+          Qt[((size_t)m * half + ji) * half + jo] = f * (0.5 * (q1 - q2));
         }
     }
   };
-  build(deriv, h.Q0s, h.Q0t);
-  if (deriv) build(false, h.Q1s, h.Q1t);
-  h.cm.resize(K + 1);
-  for (int m = 0; m <= K; ++m) h.cm[m] = (m == 0 ? 1.0 : 2.0) * 2.0 * kPi / g.nph;
+  build(deriv, false, h.Q0s, h.Q0t);
+  if (deriv) build(false, true, h.Q1s, h.Q1t);
   h.s0 = deriv ? -1.0 : 1.0;
   h.s1 = 1.0;
   return h;
 }
 
-int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int n_rows) {
-  const size_t per_row = (size_t)na + 4 * (size_t)nth * W + (size_t)M * nth + (size_t)n_out * nth * M;
-  const size_t budget = 96 * 1024 / sizeof(double);
-  int rb = (int)(budget / per_row);
+// Shared memory (doubles) per row of the folded kernel: ring values and their
+// quarter folds (reused for the synthesis coefficients) plus the Fourier
+// coefficients of the half-rings.
+size_t fold_row_doubles(int na, int nth, int W, int M, int n_out) {
+  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + (size_t)M * nth;
+}
+
+int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int n_rows, int budget_bytes) {
+  int rb = (int)((size_t)budget_bytes / (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out)));
   if (rb < 1) rb = 1;
   if (rb > 64) rb = 64;
   if (rb > n_rows) rb = n_rows;
@@ -429,6 +436,48 @@ cudaError_t alloc_zero(gh_domain* d, size_t bytes, void** out) {
   e = cudaMemset(p, 0, bytes ? bytes : 8);
   *out = p;
   return e;
+}
+
+// Rows per block, block maps and shared memory of the folded kernels from the
+// domain's current schedule (fd/ff threads and budgets); re-run by gh_autotune.
+cudaError_t fold_build_maps(gh_domain* d) {
+  const int n_shells = d->n_shells;
+  std::vector<int> fb2(n_shells + 1), ffb(n_shells + 1);
+  int nfd = 0, nff = 0;
+  size_t smfd = 0, smff = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    gh::ShellDev& sh = d->shells_h[s];
+    const int rows = gh::NF * sh.n_r;
+    const int W = sh.fd.N4 + 1;
+    sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, rows, d->fd_budget);
+    fb2[s] = nfd;
+    nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
+    smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta * fold_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2));
+    ffb[s] = nff;
+    if (sh.ff.M > 0) {
+      sh.ff.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.ff.M, 1, rows, d->ff_budget);
+      nff += (rows + sh.ff.rows_per_cta - 1) / sh.ff.rows_per_cta;
+      smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta * fold_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1));
+    }
+  }
+  fb2[n_shells] = nfd;
+  ffb[n_shells] = nff;
+  d->fd_blocks = nfd;
+  d->ff_blocks = nff;
+  d->fd_smem = smfd;
+  d->ff_smem = smff;
+  cudaError_t e;
+  if (!d->fd_block_begin_d) {
+    if ((e = upload(d, fb2, &d->fd_block_begin_d)) != cudaSuccess) return e;
+    if ((e = upload(d, ffb, &d->ff_block_begin_d)) != cudaSuccess) return e;
+  } else {
+    if ((e = cudaMemcpy(d->fd_block_begin_d, fb2.data(), sizeof(int) * fb2.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(d->ff_block_begin_d, ffb.data(), sizeof(int) * ffb.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  }
+  if (d->shells_d &&
+      (e = cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(gh::ShellDev) * d->shells_h.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  return gh::fold_set_smem_limits(std::max(smfd, smff));
 }
 
 bool fault_injected(const char* what) {
@@ -577,6 +626,44 @@ gh_status build_dense(gh_domain* d) {
 }
 
 // =================================================================== C ABI
+// ------------------------------------------------------------ autotuner
+namespace {
+// Average time of one call of f over reps calls (after one warm-up call),
+// measured with CUDA events on the domain's stream.
+template <typename F>
+cudaError_t time_calls(gh_domain* d, int reps, F f, float* ms) {
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return e; }
+  e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(a, d->stream);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(b, d->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  *ms = t / reps;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return e;
+}
+
+bool schedule_ok(const int* v) {
+  auto in = [](int x, int lo, int hi) { return x >= lo && x <= hi; };
+  return in(v[0], 2, 4) && in(v[1], 1, 4) && in(v[2], 2, 4) && in(v[3], 1, 4) &&
+         in(v[4], 32, 512) && v[4] % 32 == 0 && in(v[5], 8 * 1024, 200 * 1024) &&
+         in(v[6], 32, 512) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024);
+}
+
+void invalidate_graph(gh_domain* d) {
+  if (d->graph_exec) {
+    cudaGraphExecDestroy(d->graph_exec);
+    d->graph_exec = nullptr;
+  }
+}
+}  // namespace
+
 extern "C" {
 
 gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params* params,
@@ -736,7 +823,6 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
           if ((e = upload(d, f.Ts, &q)) != cudaSuccess) return e; P.Ts = q;
           if ((e = upload(d, f.Q0s, &q)) != cudaSuccess) return e; P.Q0s = q;
           if ((e = upload(d, f.Q0t, &q)) != cudaSuccess) return e; P.Q0t = q;
-          if ((e = upload(d, f.cm, &q)) != cudaSuccess) return e; P.cm = q;
           if (deriv) {
             if ((e = upload(d, f.Q1s, &q)) != cudaSuccess) return e; P.Q1s = q;
             if ((e = upload(d, f.Q1t, &q)) != cudaSuccess) return e; P.Q1t = q;
@@ -747,11 +833,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
         return cudaSuccess;
       };
       CREATE_CUDA(get_fold(sh.L, true, sh.fd));
-      sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, sh.fd.N4 + 1, sh.fd.M, 2, gh::NF * sh.n_r);
-      if (sh.keep >= 0) {
-        CREATE_CUDA(get_fold(sh.keep, false, sh.ff));
-        sh.ff.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, sh.ff.N4 + 1, sh.ff.M, 1, gh::NF * sh.n_r);
-      }
+      if (sh.keep >= 0) CREATE_CUDA(get_fold(sh.keep, false, sh.ff));
     } else {
       all_fold = false;
     }
@@ -859,6 +941,14 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   d->rad_blocks = nrb;
   d->pt_blocks = npb;
   {
+    // default radial row groups: about 12 warps per FP64 unit (4 per SM)
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const double warps = nrb * (double)gh::RAD_THREADS_HOST / 32.0;
+    const int g = (int)std::ceil(12.0 * 4.0 * sms / std::max(1.0, warps));
+    d->rad_groups = d->radf_groups = std::min(4, std::max(1, g));
+  }
+  {
     std::vector<int> ab(n_shells + 1);
     int nab = 0;
     for (int s = 0; s < n_shells; ++s) {
@@ -928,35 +1018,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     CREATE_CUDA(gh::sep_adj_set_smem_limits(std::max(sma, smfa)));
     // folded maps
     d->fold_ok = all_fold;
-    if (all_fold) {
-      std::vector<int> fb2(n_shells + 1), ffb(n_shells + 1);
-      int nfd = 0, nff = 0;
-      size_t smfd = 0, smff = 0;
-      for (int s = 0; s < n_shells; ++s) {
-        const gh::ShellDev& sh = d->shells_h[s];
-        const int rows = gh::NF * sh.n_r;
-        const size_t W = sh.fd.N4 + 1;
-        fb2[s] = nfd;
-        nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
-        smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta *
-                                  ((size_t)sh.na + 4 * (size_t)sh.nth * W + 3 * (size_t)sh.nth * sh.fd.M));
-        ffb[s] = nff;
-        if (sh.ff.M > 0) {
-          nff += (rows + sh.ff.rows_per_cta - 1) / sh.ff.rows_per_cta;
-          smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta *
-                                    ((size_t)sh.na + 4 * (size_t)sh.nth * W + 2 * (size_t)sh.nth * sh.ff.M));
-        }
-      }
-      fb2[n_shells] = nfd;
-      ffb[n_shells] = nff;
-      d->fd_blocks = nfd;
-      d->ff_blocks = nff;
-      d->fd_smem = smfd;
-      d->ff_smem = smff;
-      CREATE_CUDA(upload(d, fb2, &d->fd_block_begin_d));
-      CREATE_CUDA(upload(d, ffb, &d->ff_block_begin_d));
-      CREATE_CUDA(gh::fold_set_smem_limits(std::max(smfd, smff)));
-    }
+    if (all_fold) CREATE_CUDA(fold_build_maps(d));
     d->algorithm = all_fold ? 2 : 1;
   }
 
@@ -1227,6 +1289,81 @@ gh_status gh_set_algorithm(gh_domain* d, int algorithm) {
     if (gh_status st = build_dense(d)) return st;
   }
   d->algorithm = algorithm;
+  return GH_OK;
+}
+
+
+gh_status gh_get_schedule(const gh_domain* d, int* v, int n) {
+  if (!d || !v || n < GH_SCHEDULE_LEN) return GH_EINVAL;
+  v[0] = d->rad_chains; v[1] = d->rad_groups; v[2] = d->radf_chains; v[3] = d->radf_groups;
+  v[4] = d->fd_threads; v[5] = d->fd_budget; v[6] = d->ff_threads; v[7] = d->ff_budget;
+  return GH_OK;
+}
+
+gh_status gh_set_schedule(gh_domain* d, const int* v, int n) {
+  if (!d) return GH_EINVAL;
+  if (!v || n < GH_SCHEDULE_LEN || !schedule_ok(v)) return fail(d, GH_EINVAL, "invalid schedule");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  d->rad_chains = v[0]; d->rad_groups = v[1]; d->radf_chains = v[2]; d->radf_groups = v[3];
+  d->fd_threads = v[4]; d->fd_budget = v[5]; d->ff_threads = v[6]; d->ff_budget = v[7];
+  if (d->fold_ok) GH_CUDA(d, fold_build_maps(d));
+  invalidate_graph(d);
+  return GH_OK;
+}
+
+gh_status gh_autotune(gh_domain* d, int reps) {
+  if (!d) return GH_EINVAL;
+  if (reps < 1) return fail(d, GH_EINVAL, "reps must be >= 1");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  const double* in = d->d_r;
+  double* o1 = d->d_th;
+  double* o2 = d->d_ph;
+  float ms = 0.f;
+  // radial derivative and radial filter: FMA chains per pass x row groups
+  for (int filter = 0; filter < 2; ++filter) {
+    int& ch = filter ? d->radf_chains : d->rad_chains;
+    int& gr = filter ? d->radf_groups : d->rad_groups;
+    float best = 1e30f;
+    int bc = ch, bg = gr;
+    for (int c = 2; c <= 4; ++c)
+      for (int g = 1; g <= 4; ++g) {
+        ch = c;
+        gr = g;
+        GH_CUDA(d, time_calls(d, reps, [&] { return gh::launch_radial(d, in, o1, filter != 0); }, &ms));
+        if (ms < best) { best = ms; bc = c; bg = g; }
+      }
+    ch = bc;
+    gr = bg;
+  }
+  // folded angular maps: threads per block x shared-memory budget per block
+  if (d->fold_ok) {
+    const int threads[] = {128, 256, 384, 512};
+    const int budgets[] = {16 * 1024, 24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 112 * 1024};
+    bool any_filter = false;
+    for (const auto& sh : d->shells_h) any_filter = any_filter || sh.ff.M > 0;
+    for (int filter = 0; filter < (any_filter ? 2 : 1); ++filter) {
+      int& th = filter ? d->ff_threads : d->fd_threads;
+      int& bu = filter ? d->ff_budget : d->fd_budget;
+      float best = 1e30f;
+      int bt = th, bb = bu;
+      for (int t : threads)
+        for (int b : budgets) {
+          th = t;
+          bu = b;
+          GH_CUDA(d, fold_build_maps(d));
+          if (filter)
+            GH_CUDA(d, time_calls(d, reps, [&] { return gh::launch_fold_filter(d, in, o1); }, &ms));
+          else
+            GH_CUDA(d, time_calls(d, reps, [&] { return gh::launch_fold_deriv(d, in, o1, o2); }, &ms));
+          if (ms < best) { best = ms; bt = t; bb = b; }
+        }
+      th = bt;
+      bu = bb;
+    }
+    GH_CUDA(d, fold_build_maps(d));
+  }
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  invalidate_graph(d);
   return GH_OK;
 }
 

@@ -18,6 +18,7 @@ constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, b
 #define GH_PT_THREADS 32
 #endif
 constexpr int PT_THREADS = GH_PT_THREADS;  // threads per block of the per-point kernels
+constexpr int RAD_THREADS_HOST = 128;      // threads per block of the radial kernel
 
 // Separable spherical-harmonic map of one shell (Y_lm = Pbar_lm(theta) x
 // Fourier(phi)): phi-DFT, one N_theta x N_theta Legendre map per Fourier mode,
@@ -56,11 +57,13 @@ struct FoldPlan {
   int rows_per_cta, two;        // rows per block; 2 outputs (derivatives) or 1 (filter)
   const double* Tc;             // [K+1][N4+1] cos(m phi_k)
   const double* Ts;             // [K+1][N4+1] sin(m phi_k)
-  const double* Q0s;            // [K+1][half][half] (transposed: [m][j_in][j_out]) output 0, symmetric part
-  const double* Q0t;            //                   output 0, antisymmetric part
-  const double* Q1s;            // output 1 (value map; derivative plan only)
+  // [K+1][half][half] (transposed: [m][j_in][j_out]) half-size Legendre maps,
+  // symmetric (s) and antisymmetric (t) parts, scaled by the synthesis factor
+  // of mode m: c_m = (m ? 2 : 1) 2 pi / N_phi for output 0, m c_m for output 1
+  const double* Q0s;
+  const double* Q0t;
+  const double* Q1s;            // output 1 (value map feeding d/dphi; derivative plan only)
   const double* Q1t;
-  const double* cm;             // [K+1] c_m 2 pi / N_phi
   double sigma0, sigma1;        // parity of output 0 / 1 (-1 for d/dtheta, +1 for values)
 };
 
@@ -151,6 +154,12 @@ struct gh_domain {
   int* sd_block_begin_d = nullptr; int sd_blocks = 0; size_t sd_smem = 0;
   int* fd_block_begin_d = nullptr; int fd_blocks = 0; size_t fd_smem = 0;
   int* ff_block_begin_d = nullptr; int ff_blocks = 0; size_t ff_smem = 0;
+  // folded-map work schedule: threads per block and shared-memory budget per
+  // block that sets the rows per block (chosen by gh_autotune, else defaults)
+  int fd_threads = 256, ff_threads = 256;
+  int fd_budget = 32 * 1024, ff_budget = 32 * 1024;
+  // radial-map work schedule: FMA chains per pass (2..4) and row groups (1..4)
+  int rad_chains = 2, rad_groups = 1, radf_chains = 2, radf_groups = 1;
   bool fold_ok = false;         // every shell has a folded plan
   int* sf_block_begin_d = nullptr; int sf_blocks = 0; size_t sf_smem = 0;
   // scratch owned by the domain

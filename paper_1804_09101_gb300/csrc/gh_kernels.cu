@@ -20,23 +20,28 @@ namespace gh {
 // Radial contraction (the R part of Eq. DifferentiatorI1S2, and the radial
 // ExpCheb filter): out[r][col] = sum_r' M[r][r'] in[r'][col] for every column
 // col = (field, theta, phi) of every shell.  One thread per column; the block's
-// columns are staged in shared memory (coalesced loads along col), the
-// n_r x n_r matrix sits in shared memory too, and every FMA does useful work.
-constexpr int RAD_THREADS = 128;
+// columns are staged in shared memory (coalesced loads along col), the rows
+// of M it needs sit in shared memory too.  blockIdx.y splits the output rows
+// into gridDim.y groups (more, shorter warps per FP64 unit); within a group CH
+// rows are computed per pass as independent FMA chains and the remainder
+// rows one at a time, so no FMA works on padding.
+constexpr int RAD_THREADS = RAD_THREADS_HOST;
 constexpr int MAXR = 64;
 
-template <bool FILTER>
+template <bool FILTER, int CH>
 __global__ void __launch_bounds__(RAD_THREADS)
 radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
               const double* __restrict__ in, double* __restrict__ out) {
-  __shared__ double Ms[(MAXR + 3) * MAXR];
+  __shared__ double Ms[MAXR * MAXR];
   extern __shared__ double Vs[];           // [n_r][RAD_THREADS]
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int n = sh.n_r;
   const double* M = FILTER ? sh.Fr : sh.Dr;
-  const int npad = ((n + 3) / 4) * 4;
-  for (int i = threadIdx.x; i < npad * n; i += blockDim.x) Ms[i] = (i < n * n) ? M[i] : 0.0;
+  const int chunk = (n + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * chunk;
+  const int r1 = min(n, r0 + chunk);
+  for (int i = threadIdx.x; i < (r1 - r0) * n; i += blockDim.x) Ms[i] = M[r0 * n + i];
   const long long cols = (long long)NF * sh.na;
   const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
   const bool valid = col < cols;
@@ -46,30 +51,42 @@ radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __re
   if (!valid) return;
   double* dst = out + sh.off + col;
   const double* v = Vs + threadIdx.x;
-  // four outputs per pass: four independent FMA chains keep the slow FP64
-  // pipe supplied (the matrix rows past n are zero-padded in shared memory)
-  for (int r = 0; r < n; r += 4) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    const double* m0 = Ms + r * n;
-    for (int q = 0; q < n; ++q) {
+  int r = r0;
+  for (; r + CH <= r1; r += CH) {
+    const double* m0 = Ms + (r - r0) * n;
+    double acc[CH];
+    const double x0 = v[0];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = m0[c * n] * x0;
+    for (int q = 1; q < n; ++q) {
       const double x = v[q * RAD_THREADS];
-      a0 = fma(m0[q], x, a0);
-      a1 = fma(m0[n + q], x, a1);
-      a2 = fma(m0[2 * n + q], x, a2);
-      a3 = fma(m0[3 * n + q], x, a3);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) acc[c] = fma(m0[c * n + q], x, acc[c]);
     }
-    dst[(long long)r * cols] = a0;
-    if (r + 1 < n) dst[(long long)(r + 1) * cols] = a1;
-    if (r + 2 < n) dst[(long long)(r + 2) * cols] = a2;
-    if (r + 3 < n) dst[(long long)(r + 3) * cols] = a3;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) dst[(long long)(r + c) * cols] = acc[c];
+  }
+  for (; r < r1; ++r) {
+    const double* m0 = Ms + (r - r0) * n;
+    double acc = m0[0] * v[0];
+    for (int q = 1; q < n; ++q) acc = fma(m0[q], v[q * RAD_THREADS], acc);
+    dst[(long long)r * cols] = acc;
   }
 }
 
 cudaError_t radial_set_smem_limits() {
   const int bytes = (int)(sizeof(double) * MAXR * RAD_THREADS);
-  cudaError_t e = cudaFuncSetAttribute(radial_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(radial_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)radial_kernel<true, 2>);
+  set((const void*)radial_kernel<true, 3>);
+  set((const void*)radial_kernel<true, 4>);
+  set((const void*)radial_kernel<false, 2>);
+  set((const void*)radial_kernel<false, 3>);
+  set((const void*)radial_kernel<false, 4>);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -938,12 +955,17 @@ static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b
 
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter) {
   const size_t smem = sizeof(double) * (size_t)d->max_n_r * RAD_THREADS;
-  if (filter)
-    radial_kernel<true><<<d->rad_blocks, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,
-                                                                         d->rad_block_begin_d, in, out);
-  else
-    radial_kernel<false><<<d->rad_blocks, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,
-                                                                          d->rad_block_begin_d, in, out);
+  const int ch = filter ? d->radf_chains : d->rad_chains;
+  const dim3 grid(d->rad_blocks, filter ? d->radf_groups : d->rad_groups);
+#define GH_RAD(F, C)                                                                       \
+  radial_kernel<F, C><<<grid, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,    \
+                                                               d->rad_block_begin_d, in, out)
+  if (filter) {
+    if (ch == 4) GH_RAD(true, 4); else if (ch == 3) GH_RAD(true, 3); else GH_RAD(true, 2);
+  } else {
+    if (ch == 4) GH_RAD(false, 4); else if (ch == 3) GH_RAD(false, 3); else GH_RAD(false, 2);
+  }
+#undef GH_RAD
   d->launches++;
   return cudaGetLastError();
 }

@@ -70,6 +70,9 @@ def _load():
         "gh_constraints": ([P, P, P, P], I),
         "gh_sync": ([P], I),
         "gh_set_algorithm": ([P, I], I),
+        "gh_autotune": ([P, I], I),
+        "gh_get_schedule": ([P, ctypes.POINTER(I), I], I),
+        "gh_set_schedule": ([P, ctypes.POINTER(I), I], I),
         "gh_rhs_vjp": ([P, P, P, P], I),
         "gh_rk4_vjp_work_size": ([P], ctypes.c_longlong),
         "gh_rk4_step_vjp": ([P, D, P, P, P, P], I),
@@ -262,6 +265,30 @@ GH_ALG_DENSE, GH_ALG_SEPARABLE, GH_ALG_SEPARABLE_FOLDED = 0, 1, 2
 def gh_set_algorithm(dom, algorithm):
     dom._stream()
     dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
+
+
+SCHEDULE_LEN = 8
+SCHEDULE_KEYS = ("radial_chains", "radial_groups", "radial_filter_chains", "radial_filter_groups",
+                 "fold_deriv_threads", "fold_deriv_budget", "fold_filter_threads", "fold_filter_budget")
+
+
+def gh_autotune(dom, reps=5):
+    """Time the work-schedule candidates of the radial and folded angular maps
+    on this domain and keep the fastest (results are bitwise unchanged)."""
+    dom._stream()
+    dom._check(_lib.gh_autotune(dom.handle, int(reps)))
+
+
+def gh_get_schedule(dom):
+    v = (ctypes.c_int * SCHEDULE_LEN)()
+    dom._check(_lib.gh_get_schedule(dom.handle, v, SCHEDULE_LEN))
+    return dict(zip(SCHEDULE_KEYS, list(v)))
+
+
+def gh_set_schedule(dom, sched):
+    v = (ctypes.c_int * SCHEDULE_LEN)(*[int(sched[k]) for k in SCHEDULE_KEYS])
+    dom._stream()
+    dom._check(_lib.gh_set_schedule(dom.handle, v, SCHEDULE_LEN))
 
 
 def gh_rhs_vjp(dom, u, kbar, ubar):

@@ -72,3 +72,13 @@ def test_invalid_shells_are_rejected_before_any_device_call(lib):
 def test_injected_allocation_fault_returns_enomem_without_touching_the_gpu(lib):
     st, msg = _run_create({"GH_FAULT": "alloc"}, "[(1.0, 2.0, 11, 7)]")
     assert st == 2 and "GH_FAULT" in msg                  # GH_ENOMEM
+
+
+def test_schedule_entry_points_reject_bad_arguments_on_the_host(lib):
+    v = (ctypes.c_int * 8)(2, 1, 2, 1, 128, 49152, 128, 49152)
+    lib.gh_get_schedule.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.gh_set_schedule.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.gh_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.gh_get_schedule(None, v, 8) == 1          # GH_EINVAL: no domain
+    assert lib.gh_set_schedule(None, v, 8) == 1
+    assert lib.gh_autotune(None, 3) == 1

@@ -1,0 +1,73 @@
+"""The work-schedule autotuner and explicit schedules: every schedule of the
+radial and folded angular maps gives bitwise identical derivatives, filters
+and RK4 steps; invalid schedules are rejected."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1804_09101_gb300 import gh, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _domain():
+    w = workloads.kerr_four_shells(n_r=9, L=7)
+    dom = gh.Domain.from_workload(w)
+    u = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
+    g = torch.Generator().manual_seed(7)
+    u += 1e-6 * torch.randn(dom.state_size, generator=g, dtype=torch.float64).to(u.device)
+    return w, dom, u
+
+
+def _outputs(w, dom, u):
+    d = torch.empty((3, dom.state_size), dtype=torch.float64, device=u.device)
+    gh.gh_derivatives(dom, u, d)
+    f = u.clone()
+    gh.gh_apply_filters(dom, f, dom.new_work())
+    s = u.clone()
+    gh.gh_rk4_step(dom, w.dt, s, dom.new_work())
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), f.cpu().numpy(), s.cpu().numpy()
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_keeps_results_bitwise():
+    w, dom, u = _domain()
+    ref = _outputs(w, dom, u)
+    gh.gh_autotune(dom, reps=2)
+    sched = gh.gh_get_schedule(dom)
+    assert 2 <= sched["radial_chains"] <= 4 and 1 <= sched["radial_groups"] <= 4
+    assert sched["fold_deriv_threads"] % 32 == 0
+    _same(ref, _outputs(w, dom, u))
+
+
+@pytest.mark.parametrize("sched", [
+    (2, 1, 2, 1, 128, 49152, 128, 49152),
+    (3, 2, 4, 3, 32, 8192, 64, 8192),
+    (4, 4, 3, 2, 512, 200 * 1024, 256, 112 * 1024),
+    (2, 3, 2, 4, 96, 24576, 480, 65536),
+])
+def test_every_schedule_gives_identical_results(sched):
+    w, dom, u = _domain()
+    ref = _outputs(w, dom, u)
+    gh.gh_set_schedule(dom, dict(zip(gh.SCHEDULE_KEYS, sched)))
+    assert tuple(gh.gh_get_schedule(dom).values()) == sched
+    _same(ref, _outputs(w, dom, u))
+
+
+@pytest.mark.parametrize("bad", [
+    (1, 1, 2, 1, 128, 49152, 128, 49152),     # chains < 2
+    (2, 5, 2, 1, 128, 49152, 128, 49152),     # groups > 4
+    (2, 1, 2, 1, 100, 49152, 128, 49152),     # threads not a multiple of 32
+    (2, 1, 2, 1, 128, 1024, 128, 49152),      # budget below 8 KiB
+    (2, 1, 2, 1, 128, 49152, 1024, 49152),    # threads above 512
+])
+def test_invalid_schedules_are_rejected(bad):
+    w, dom, u = _domain()
+    with pytest.raises(RuntimeError):
+        gh.gh_set_schedule(dom, dict(zip(gh.SCHEDULE_KEYS, bad)))
