@@ -29,9 +29,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
-# from the ncu capture summarised in profiles/ (None once the kernel changes).
+# from the ncu captures of the current kernels (None once a kernel changes).
 TRAFFIC_PER_LAUNCH = {
-    ("kerr_a0.9_4shells_nr21_L15", "separable", "angular"): 17.32e6,
+    # pointwise_kernel<1,0>, 4-shell L=15: 121.8 MB read + 109.9 MB written
+    ("kerr_a0.9_4shells_nr21_L15", "folded", "pointwise"): 231.7e6,
+    # fold_angular_kernel<1>, 8-shell L=31: 269.1 MB read + 477.2 MB written
+    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): 746.3e6,
+    # fold_angular_kernel<1>, 4-shell L=15: 17.3 MB read + 1.3 MB written
+    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): 18.5e6,
 }
 
 METRIC = "GH RHS grid-point evals/s (FP64, 1 GB300) + % roofline; batched vs plain; adjoint/fwd"
@@ -47,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default work schedule instead of running gh_autotune before timing")
+    p.add_argument("--schedule", default=None,
+                   help="explicit work schedule as JSON (keys of gh.SCHEDULE_KEYS) instead of gh_autotune")
     p.add_argument("--workload", default="kerr4",
                    choices=["kerr4", "large", "schwarzschild", "batched", "adjoint"],
                    help="kerr4: 4-shell Kerr a=0.9 (default, the headline); large: 8-shell Kerr a=0.95, "
@@ -194,7 +201,9 @@ def run_ours(args, w):
     dom = gh.Domain.from_workload(w)
     gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
                               "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
-    if not args.no_autotune:
+    if args.schedule:
+        gh.gh_set_schedule(dom, json.loads(args.schedule))
+    elif not args.no_autotune:
         gh.gh_autotune(dom, 5)
     u = dom.new_state()
     gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
@@ -301,7 +310,8 @@ def run_ours(args, w):
                             step="RK4 step + ExpCheb(36,32) + SH keep l<=%d + constraint norms" % w.sh_keep_l,
                             l2="flushed before every timed step (256 MB write, outside the step events)",
                             parallelism="replicas" if world > 1 else "single GPU",
-                            schedule=gh.gh_get_schedule(dom), autotuned=not args.no_autotune),
+                            schedule=gh.gh_get_schedule(dom),
+                            autotuned=not (args.no_autotune or args.schedule)),
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=state_bytes,
                          d2h_bytes_per_step=state_bytes + 8 * len(w.shells)),
                 gpu_launches=launches, roofline=roofline, kernels=kernels)

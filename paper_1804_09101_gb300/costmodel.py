@@ -99,11 +99,12 @@ def sep_angular_flops(shells, K=None, two=True):
     return f
 
 
-# FP64 flops per point executed by the fused pointwise kernel (DiffJac + GH
-# right-hand side + RK4 stage combine), from ncu's executed-instruction
-# counters (dadd + dmul + 2 dfma) on the 4-shell Kerr workload.
-POINTWISE_FLOPS_PER_POINT = 4934
-POINTWISE_CONSTRAINT_EXTRA_FLOPS_PER_POINT = 409
+# FP64 flops per point of the fused pointwise kernel (DiffJac + GH right-hand
+# side + RK4 stage combine) in its FMA-chain formulation: ncu's executed
+# DFMA/DADD/DMUL counts of one launch on the 4-shell Kerr workload
+# (2 x 2,398,144 + 53,760 + 587,328 warp instructions x 32 lanes / 43,008
+# points).
+POINTWISE_FLOPS_PER_POINT = 4046
 
 
 def fold_angular_flops(shells, K=None, two=True):

@@ -121,9 +121,10 @@ sep_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
 }
 
 cudaError_t sep_adj_set_smem_limits(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(sep_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static size_t cur[2] = {0, 0};
+  cudaError_t e = raise_smem_limit((const void*)sep_adjoint_kernel<true>, bytes, &cur[0]);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sep_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_smem_limit((const void*)sep_adjoint_kernel<false>, bytes, &cur[1]);
 }
 
 // ---------------------------------------------------------------------------

@@ -207,9 +207,10 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
 }
 
 cudaError_t fold_set_smem_limits(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(fold_angular_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static size_t cur[2] = {0, 0};
+  cudaError_t e = raise_smem_limit((const void*)fold_angular_kernel<true>, bytes, &cur[0]);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fold_angular_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_smem_limit((const void*)fold_angular_kernel<false>, bytes, &cur[1]);
 }
 
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {

@@ -199,6 +199,10 @@ cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dt
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
 cudaError_t fold_set_smem_limits(size_t bytes);
+// Raise the dynamic shared-memory limit of kernel f to at least `bytes`.  The
+// limit is a process-wide attribute of the kernel that every domain shares, so
+// it only ever grows (*current tracks it; guarded by a mutex).
+cudaError_t raise_smem_limit(const void* f, size_t bytes, size_t* current);
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph);
 cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out);
 cudaError_t sep_adj_set_smem_limits(size_t bytes);

@@ -10,6 +10,8 @@
 // is to keep the FP64 pipe busy, not to save HBM traffic.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "gh_geom.cuh"
 #include "gh_internal.h"
 #include "gh_tensor.cuh"
@@ -74,19 +76,26 @@ radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __re
   }
 }
 
-cudaError_t radial_set_smem_limits() {
-  const int bytes = (int)(sizeof(double) * MAXR * RAD_THREADS);
-  cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  };
-  set((const void*)radial_kernel<true, 2>);
-  set((const void*)radial_kernel<true, 3>);
-  set((const void*)radial_kernel<true, 4>);
-  set((const void*)radial_kernel<false, 2>);
-  set((const void*)radial_kernel<false, 3>);
-  set((const void*)radial_kernel<false, 4>);
+cudaError_t raise_smem_limit(const void* f, size_t bytes, size_t* current) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (bytes <= *current) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *current = bytes;
   return e;
+}
+
+cudaError_t radial_set_smem_limits() {
+  const size_t bytes = sizeof(double) * MAXR * RAD_THREADS;
+  static size_t cur[6] = {0, 0, 0, 0, 0, 0};
+  const void* f[6] = {(const void*)radial_kernel<true, 2>, (const void*)radial_kernel<true, 3>,
+                      (const void*)radial_kernel<true, 4>, (const void*)radial_kernel<false, 2>,
+                      (const void*)radial_kernel<false, 3>, (const void*)radial_kernel<false, 4>};
+  for (int i = 0; i < 6; ++i) {
+    cudaError_t e = raise_smem_limit(f[i], bytes, &cur[i]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -282,9 +291,10 @@ sep_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
 }
 
 cudaError_t sep_set_smem_limits(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(sep_angular_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static size_t cur[2] = {0, 0};
+  cudaError_t e = raise_smem_limit((const void*)sep_angular_kernel<true>, bytes, &cur[0]);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sep_angular_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_smem_limit((const void*)sep_angular_kernel<false>, bytes, &cur[1]);
 }
 
 // ---------------------------------------------------------------------------

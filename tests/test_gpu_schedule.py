@@ -71,3 +71,23 @@ def test_invalid_schedules_are_rejected(bad):
     w, dom, u = _domain()
     with pytest.raises(RuntimeError):
         gh.gh_set_schedule(dom, dict(zip(gh.SCHEDULE_KEYS, bad)))
+
+
+def test_schedules_of_two_domains_do_not_interfere():
+    # the shared-memory limit of a kernel is process-wide: a second domain with
+    # a small schedule must not break the launches of a first one with a large
+    # schedule
+    w1 = workloads.kerr_four_shells(n_r=9, L=15)
+    d1 = gh.Domain.from_workload(w1)
+    u1 = d1.new_state()
+    gh.gh_set_analytic_kerr_schild(d1, -1, w1.M, w1.chi, u1)
+    s = gh.gh_get_schedule(d1)
+    s.update(fold_deriv_budget=200 * 1024, fold_filter_budget=200 * 1024)
+    gh.gh_set_schedule(d1, s)
+    ref = _outputs(w1, d1, u1)
+    w2, d2, u2 = _domain()
+    s2 = gh.gh_get_schedule(d2)
+    s2.update(fold_deriv_budget=8192, fold_filter_budget=8192)
+    gh.gh_set_schedule(d2, s2)
+    _outputs(w2, d2, u2)
+    _same(ref, _outputs(w1, d1, u1))
