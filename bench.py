@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--schedule", default=None,
                    help="explicit work schedule as JSON (keys of gh.SCHEDULE_KEYS) instead of gh_autotune")
     p.add_argument("--workload", default="kerr4",
-                   choices=["kerr4", "large", "schwarzschild", "batched", "adjoint"],
+                   choices=["kerr4", "large", "schwarzschild", "batched", "adjoint", "families"],
                    help="kerr4: 4-shell Kerr a=0.9 (default, the headline); large: 8-shell Kerr a=0.95, "
                         "N_r=41, L=31; schwarzschild: 1 shell N_r=11, L=7; batched: 64 independent "
                         "single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
@@ -500,17 +500,101 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_families(args):
+    """The paper's benchmark grid families (Sec. 3.4) on four Kerr shells:
+    SingleBH k = 0..8 (odd L: folded maps) and BBH k = 0..8 (even L:
+    separable maps).  Per member: the derivative step (radial + angular maps,
+    the paper's Differentiator), the full RHS and the RK4 step, timed with CUDA
+    events after warm-up; the paper's dense-matrix Differentiator flop count
+    beside the library's own count."""
+    import torch
+    from paper_1804_09101_gb300 import build
+    build.build()
+    from paper_1804_09101_gb300 import costmodel, gh, workloads
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    reps = max(3, args.steps // 10)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    members = []
+    tot_units, tot_ms, launches = 0.0, 0.0, 0
+    for family in ("singlebh", "bbh"):
+        for k in range(9):
+            w = workloads.grid_family_workload(family, k)
+            dom = gh.Domain.from_workload(w)
+            if not args.no_autotune:
+                gh.gh_autotune(dom, 3)
+            u = dom.new_state()
+            gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
+            u += torch.from_numpy(w.noise()).to(u.device)
+            du = torch.empty(3 * dom.state_size, dtype=torch.float64, device="cuda")
+            kk = dom.new_state()
+            work = dom.new_work()
+            d_ms = timed(lambda: gh.gh_derivatives(dom, u, du))
+            r_ms = timed(lambda: gh.gh_rhs(dom, u, kk))
+            us = u.clone()
+            n0 = dom.launch_count()
+            s_ms = timed(lambda: gh.gh_rk4_step(dom, w.dt, us, work))
+            launches += (dom.launch_count() - n0) // (reps + 3)
+            pts = w.points()
+            n_r, L = workloads.grid_family_resolution(family, k)
+            nth, nph = L + 1, 2 * (L + 1)
+            _, F_dense = costmodel.i1s2_differentiator(50, n_r, nth, nph)
+            alg = "folded" if L % 2 == 1 else "separable"
+            F_lib = (costmodel.radial_flops(w.shells) + costmodel.family_flops("angular", w.shells, alg)) / 4
+            members.append(dict(family=family, k=k, n_r=n_r, n_theta=nth, n_phi=nph, points=pts,
+                                algorithm=alg, deriv_ms=d_ms, rhs_ms=r_ms, rk4_step_ms=s_ms,
+                                rhs_evals_per_s=pts / (r_ms / 1e3),
+                                step_evals_per_s=4 * pts / (s_ms / 1e3),
+                                paper_dense_deriv_flops_per_shell=F_dense,
+                                library_deriv_flops_per_shell=F_lib,
+                                deriv_tflops=4 * F_lib / (d_ms / 1e3) / 1e12))
+            tot_units += 4 * pts
+            tot_ms += s_ms
+            del dom
+    line = dict(metric=METRIC, value=tot_units / (tot_ms / 1e3), unit=UNIT, n_gpus=1, steps=reps,
+                warmup=3, ms_per_step=tot_ms / len(members), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload="paper grid families (SingleBH, BBH k=0..8) on 4 Kerr a=0.9 shells",
+                            value="all members' RK4 grid-point RHS evaluations / sum of their step times",
+                            l2="flushed before every timed call", members=members),
+                gpu_launches=launches)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     from paper_1804_09101_gb300 import workloads
     w = {"kerr4": workloads.kerr_four_shells, "large": workloads.kerr_eight_shells_large,
          "schwarzschild": workloads.schwarzschild_single_shell,
-         "batched": workloads.kerr_four_shells, "adjoint": workloads.kerr_four_shells}[args.workload]()
+         "batched": workloads.kerr_four_shells, "adjoint": workloads.kerr_four_shells,
+         "families": workloads.kerr_four_shells}[args.workload]()
     if args.workload == "adjoint":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no oracle arm"}))
             return
         run_adjoint(args)
+        return
+    if args.workload == "families":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the grid-family sweep has no oracle arm"}))
+            return
+        run_families(args)
         return
     if args.workload == "batched":
         if args.impl == "reference":

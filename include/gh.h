@@ -260,6 +260,24 @@ long long gh_launch_count(const gh_domain* dom);
 enum { GH_ALG_DENSE = 0, GH_ALG_SEPARABLE = 1, GH_ALG_SEPARABLE_FOLDED = 2 };
 gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
 
+/* Dormand-Prince 5(4) adaptive step: the paper's time stepper (Sec. 2.1; the
+ * embedded pair of Dormand & Prince 1980, seven right-hand sides per attempt,
+ * no stage reused across steps).  One attempt from u with step dt:
+ *   k_s = F(u + dt sum_j a_sj k_j) (F = gh_rhs, boundary conditions included),
+ *   unew = u + dt sum_j b_j k_j (fifth order),
+ *   err = sqrt(mean over every value of (e / (atol + rtol max(|u|, |unew|)))^2)
+ *   with e = dt sum_j (b_j - bhat_j) k_j (fourth-order companion).
+ * accepted = (err <= 1); then u <- unew followed by the filters (as for RK4),
+ * else u is left unchanged.  dt_next = dt min(5, max(0.2, 0.9 err^(-1/5)))
+ * (5 dt when err = 0).  err_out, accepted and dt_next are host pointers; the
+ * call synchronises the stream to read err.  work: device scratch of
+ * gh_dp5_work_size doubles (the seven stage derivatives and two states).
+ * GH_EINVAL for dt <= 0, negative tolerances or both zero; GH_ENOTSUP when a
+ * shell has a dt scale other than 1 (gh_set_dt_scale). */
+long long gh_dp5_work_size(const gh_domain* dom);
+gh_status gh_dp5_step(gh_domain* dom, double dt, double rtol, double atol, double* u, double* work,
+                      double* err_out, int* accepted, double* dt_next);
+
 /* Work-schedule autotuner.  The schedule is how the radial and folded angular
  * maps split their work (the paper has no counterpart: its traced-matrix
  * products run as library GEMMs, Sec. 3.4); it never changes the arithmetic of
@@ -291,7 +309,8 @@ typedef enum {
   GH_K_RADIAL_FILTER = 4, /* exponential Chebyshev filter                          */
   GH_K_ANGULAR_FILTER = 5,/* spherical-harmonic truncation filter                   */
   GH_K_REDUCE = 6,        /* constraint-norm reduction                              */
-  GH_K_FAMILIES = 7
+  GH_K_COMBINE = 7,       /* Dormand-Prince stage combinations and error norm       */
+  GH_K_FAMILIES = 8
 } gh_kernel_family;
 
 /* Profiler: while enabled, every kernel the domain launches is bracketed by

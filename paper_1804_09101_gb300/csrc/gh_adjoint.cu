@@ -238,7 +238,6 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
 // MODE 0: cotangent kb of dudt (before the boundary conditions).
 // MODE 1: gradient of weight * sum_points w_quadrature * (constraint energy).
 // MODE 2: both (the RHS cotangent and the constraint-energy gradient at u).
-constexpr int ADJ_PT_THREADS = 64;
 
 // The constraint-energy gradient as a separate (not inlined) call, so that the
 // fused kernel does not hold both reverse passes' locals at once.
@@ -247,7 +246,7 @@ __device__ __noinline__ void constraint_part(const PointIn& in, double w, double
 }
 
 #ifndef GH_ADJ_MINB
-#define GH_ADJ_MINB 8
+#define GH_ADJ_MINB 16
 #endif
 template <int MODE>
 __global__ void __launch_bounds__(ADJ_PT_THREADS, GH_ADJ_MINB)

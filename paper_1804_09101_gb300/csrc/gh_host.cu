@@ -953,7 +953,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     int nab = 0;
     for (int s = 0; s < n_shells; ++s) {
       ab[s] = nab;
-      nab += d->shells_h[s].n_r * ((d->shells_h[s].na + 63) / 64);
+      nab += d->shells_h[s].n_r * ((d->shells_h[s].na + gh::ADJ_PT_THREADS - 1) / gh::ADJ_PT_THREADS);
     }
     ab[n_shells] = nab;
     d->adj_pt_blocks = nab;
@@ -1029,6 +1029,8 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   CREATE_CUDA(alloc_zero(d, sizeof(double) * d->state, &p)); d->d_ph = (double*)p;
   CREATE_CUDA(alloc_zero(d, sizeof(double) * (size_t)d->pt_blocks, &p)); d->partial = (double*)p;
   CREATE_CUDA(alloc_zero(d, sizeof(int), &p)); d->err_flag = (int*)p;
+  CREATE_CUDA(alloc_zero(d, sizeof(double) * gh::DP_MAX_BLOCKS, &p)); d->dp_partial = (double*)p;
+  CREATE_CUDA(alloc_zero(d, sizeof(double), &p)); d->dp_err = (double*)p;
   CREATE_CUDA(cudaDeviceSynchronize());
 #undef CREATE_CUDA
   *out = d;
@@ -1263,6 +1265,85 @@ gh_status gh_rk4_step_save(gh_domain* d, double dt, double* u, double* work, dou
   if (!d || !u || !work || !stages) return fail(d, GH_EINVAL, "null argument");
   if (gh_status s = check_latched(d)) return s;
   return rk4_step_impl(d, dt, u, work, norm2_pre, stages);
+}
+
+long long gh_dp5_work_size(const gh_domain* d) { return d ? 9LL * (long long)d->state : 0; }
+
+gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double* u, double* work,
+                      double* err_out, int* accepted, double* dt_next) {
+  if (!d || !u || !work || !err_out || !accepted || !dt_next) return fail(d, GH_EINVAL, "null argument");
+  if (!(dt > 0.0) || !(rtol >= 0.0) || !(atol >= 0.0) || (rtol == 0.0 && atol == 0.0))
+    return fail(d, GH_EINVAL, "need dt > 0, rtol >= 0, atol >= 0, not both tolerances zero");
+  for (const auto& sh : d->shells_h)
+    if (sh.dt_scale != 1.0) return fail(d, GH_ENOTSUP, "the Dormand-Prince step needs dt_scale = 1 on every shell");
+  if (gh_status s = check_latched(d)) return s;
+  // Dormand & Prince (1980) pair: stage matrix rows 2..7 (row 7 = b) and b - b_hat
+  static const double A[7][6] = {
+      {0, 0, 0, 0, 0, 0},
+      {1.0 / 5, 0, 0, 0, 0, 0},
+      {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+      {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+      {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+      {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+      {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+  static const double bh[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
+                               1.0 / 40};
+  const long long N = d->state;
+  double* k[7];
+  for (int j = 0; j < 7; ++j) k[j] = work + j * N;
+  double* ustage = work + 7 * N;
+  double* unew = work + 8 * N;
+  for (int s = 0; s < 7; ++s) {
+    const double* in = (s == 0) ? u : (s == 6 ? unew : ustage);
+    if (gh_status st = derivatives(d, in)) return st;
+    {
+      ProfScope p(d, GH_K_POINTWISE);
+      GH_CUDA(d, gh::launch_pointwise(d, in, k[s], 0, 0.0, nullptr, nullptr, nullptr, false));
+    }
+    {
+      ProfScope p(d, GH_K_BC);
+      GH_CUDA(d, gh::launch_bc(d, k[s], 0, 0.0, nullptr, nullptr, nullptr));
+    }
+    if (s < 6) {
+      // next stage state (s = 5 gives the fifth-order solution, row 7 = b)
+      gh::LinComb lc;
+      lc.nk = s + 1;
+      for (int j = 0; j <= s; ++j) {
+        lc.k[j] = k[j];
+        lc.c[j] = dt * A[s + 1][j];
+      }
+      ProfScope p(d, GH_K_COMBINE);
+      GH_CUDA(d, gh::launch_dp5_lincomb(d, u, lc, s == 5 ? unew : ustage));
+    }
+  }
+  {
+    gh::LinComb lc;
+    lc.nk = 7;
+    for (int j = 0; j < 7; ++j) {
+      lc.k[j] = k[j];
+      lc.c[j] = dt * ((j < 6 ? A[6][j] : 0.0) - bh[j]);
+    }
+    ProfScope p(d, GH_K_COMBINE);
+    GH_CUDA(d, gh::launch_dp5_error(d, u, unew, lc, rtol, atol, d->dp_err));
+  }
+  double err = 0.0;
+  GH_CUDA(d, cudaMemcpyAsync(&err, d->dp_err, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  const bool ok = err <= 1.0;
+  // controller: dt min(5, max(0.2, 0.9 err^(-1/5))), 5 when err = 0
+  const double fac = (err == 0.0) ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+  *err_out = err;
+  *accepted = ok ? 1 : 0;
+  *dt_next = dt * fac;
+  if (ok) {
+    const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
+    if (filt) {
+      if (gh_status st = filters(d, unew, u, ustage)) return st;
+    } else {
+      GH_CUDA(d, cudaMemcpyAsync(u, unew, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
+    }
+  }
+  return GH_OK;
 }
 
 gh_status gh_apply_filters(gh_domain* d, double* u, double* work) {

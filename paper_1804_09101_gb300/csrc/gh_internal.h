@@ -14,11 +14,22 @@ constexpr int NF = 50;      // evolved fields per point
 constexpr int NC = 64;      // stored constraint components per point
 constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
 constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
+constexpr int DP_MAX_BLOCKS = 1024;  // blocks of the Dormand-Prince elementwise kernels
+// Linear combination of up to seven stage derivatives (passed by value).
+struct LinComb {
+  const double* k[7];
+  double c[7];
+  int nk;
+};
 #ifndef GH_PT_THREADS
 #define GH_PT_THREADS 32
 #endif
 constexpr int PT_THREADS = GH_PT_THREADS;  // threads per block of the per-point kernels
 constexpr int RAD_THREADS_HOST = 128;      // threads per block of the radial kernel
+#ifndef GH_ADJ_PT_THREADS
+#define GH_ADJ_PT_THREADS 32
+#endif
+constexpr int ADJ_PT_THREADS = GH_ADJ_PT_THREADS;  // threads per block of the pointwise reverse kernel
 
 // Separable spherical-harmonic map of one shell (Y_lm = Pbar_lm(theta) x
 // Fourier(phi)): phi-DFT, one N_theta x N_theta Legendre map per Fourier mode,
@@ -175,8 +186,11 @@ struct gh_domain {
   int* sda_block_begin_d = nullptr; int sda_blocks = 0; size_t sda_smem = 0;
   int* sfa_block_begin_d = nullptr; int sfa_blocks = 0; size_t sfa_smem = 0;
   double* kbt = nullptr;        // one state, allocated by the first adjoint call
-  int* adj_pt_block_begin_d = nullptr; int adj_pt_blocks = 0;   // 64-thread point blocks
+  int* adj_pt_block_begin_d = nullptr; int adj_pt_blocks = 0;   // ADJ_PT_THREADS-point blocks
   double* pert_partial = nullptr; int pert_partial_len = 0;
+  // Dormand-Prince step: per-block partial sums of the error norm and the norm
+  double* dp_partial = nullptr;
+  double* dp_err = nullptr;
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_step_launches = 0;
@@ -185,8 +199,8 @@ struct gh_domain {
   struct Bracket { int fam; cudaEvent_t a, b; };
   std::vector<Bracket> pending;
   std::vector<cudaEvent_t> event_pool;
-  double prof_ms[8] = {0};
-  long long prof_n[8] = {0};
+  double prof_ms[GH_K_FAMILIES] = {0};
+  long long prof_n[GH_K_FAMILIES] = {0};
 };
 
 namespace gh {
@@ -199,6 +213,11 @@ cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dt
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
 cudaError_t fold_set_smem_limits(size_t bytes);
+// Dormand-Prince step: out = base + sum_j c[j] k[j] (j < nk), and the scaled
+// RMS norm of sum_j c[j] k[j] (the embedded error estimate) into err_dev.
+cudaError_t launch_dp5_lincomb(gh_domain* d, const double* base, const LinComb& lc, double* out);
+cudaError_t launch_dp5_error(gh_domain* d, const double* u, const double* unew, const LinComb& lc, double rtol,
+                             double atol, double* err_dev);
 // Raise the dynamic shared-memory limit of kernel f to at least `bytes`.  The
 // limit is a process-wide attribute of the kernel that every domain shares, so
 // it only ever grows (*current tracks it; guarded by a mutex).

@@ -71,6 +71,8 @@ def _load():
         "gh_sync": ([P], I),
         "gh_set_algorithm": ([P, I], I),
         "gh_autotune": ([P, I], I),
+        "gh_dp5_work_size": ([P], ctypes.c_longlong),
+        "gh_dp5_step": ([P, D, D, D, P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "gh_get_schedule": ([P, ctypes.POINTER(I), I], I),
         "gh_set_schedule": ([P, ctypes.POINTER(I), I], I),
         "gh_rhs_vjp": ([P, P, P, P], I),
@@ -128,6 +130,7 @@ class Domain:
         self.num_points = _lib.gh_num_points(h)
         self.work_size = _lib.gh_rk4_work_size(h)
         self.vjp_work_size = _lib.gh_rk4_vjp_work_size(h)
+        self.dp5_work_size = _lib.gh_dp5_work_size(h)
 
     @classmethod
     def from_workload(cls, w):
@@ -243,7 +246,7 @@ def gh_constraints(dom, u, c_out, norm2):
                                    _ptr(c_out, "c_out", 64 * dom.num_points), _ptr(norm2, "norm2", len(dom.shells))))
 
 
-KERNEL_FAMILIES = ["radial", "angular", "pointwise", "bc", "radial_filter", "angular_filter", "reduce"]
+KERNEL_FAMILIES = ["radial", "angular", "pointwise", "bc", "radial_filter", "angular_filter", "reduce", "combine"]
 
 
 def gh_profile_enable(dom, on=True):
@@ -265,6 +268,21 @@ GH_ALG_DENSE, GH_ALG_SEPARABLE, GH_ALG_SEPARABLE_FOLDED = 0, 1, 2
 def gh_set_algorithm(dom, algorithm):
     dom._stream()
     dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
+
+
+def gh_dp5_step(dom, dt, rtol, atol, u, work):
+    """One Dormand-Prince 5(4) attempt; returns (err, accepted, dt_next).  On
+    acceptance u holds the new (filtered) state, else it is unchanged."""
+    err, acc, dtn = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    dom._stream()
+    dom._check(_lib.gh_dp5_step(dom.handle, float(dt), float(rtol), float(atol), _ptr(u, "u", dom.state_size),
+                                _ptr(work, "work", dom.dp5_work_size), ctypes.byref(err), ctypes.byref(acc),
+                                ctypes.byref(dtn)))
+    return err.value, bool(acc.value), dtn.value
+
+
+def new_dp5_work(dom):
+    return torch.zeros(dom.dp5_work_size, dtype=torch.float64, device="cuda")
 
 
 SCHEDULE_LEN = 8

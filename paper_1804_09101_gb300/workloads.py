@@ -101,6 +101,28 @@ def kerr_eight_shells_large(n_r=41, L=31, seed=105):
                     pulse=Pulse("psi_pulse", 1e-5, 50.0, 4.0, 8, random_coeffs(seed, 8)))
 
 
+def grid_family_resolution(family, k):
+    """(N_r, L) of member k of the paper's benchmark grid families (Sec. 3.4):
+    SingleBH N_r = 9 + 4k, N_theta = 6 + 2k; BBH N_r = 4 + k, N_theta = 7 + 2k;
+    both with N_phi = 2 N_theta, i.e. L = N_theta - 1 on this grid."""
+    if family == "singlebh":
+        return 9 + 4 * k, 5 + 2 * k
+    if family == "bbh":
+        return 4 + k, 6 + 2 * k
+    raise ValueError(family)
+
+
+def grid_family_workload(family, k, seed=106):
+    """Four Kerr a=0.9 shells [1.3, 3, 6, 12, 30] at the resolution of family
+    member k, both filters on, seeded N(0,1) 1e-8 noise."""
+    n_r, L = grid_family_resolution(family, k)
+    b = [1.3, 3.0, 6.0, 12.0, 30.0]
+    return Workload(name="%s_k%d_4shells_nr%d_L%d" % (family, k, n_r, L),
+                    shells=[(b[i], b[i + 1], n_r, L) for i in range(4)], M=1.0, chi=0.9,
+                    radial_filter_on=True, sh_keep_l=(2 * L) // 3, dt=0.001, steps=20,
+                    seed=seed + 17 * k + (0 if family == "singlebh" else 1000), noise_amp=1e-8)
+
+
 def adjoint_single_shell(seed=104):
     """The single Schwarzschild shell with 16 l<=3 mode coefficients on Pi."""
     w = schwarzschild_single_shell(seed=seed)

@@ -58,8 +58,24 @@ def w_even_L():
                               radial_filter_on=True, sh_keep_l=4, dt=0.005, seed=21, noise_amp=1e-7)
 
 
+def w_singlebh_k1():
+    # the paper's SingleBH grid family, member k = 1 (N_r = 13, N_theta = 8), two shells
+    w = workloads.grid_family_workload("singlebh", 1)
+    w.shells = w.shells[:2]
+    w.name = "singlebh_k1_2shells"
+    return w
+
+
+def w_bbh_k1():
+    # the paper's BBH grid family, member k = 1 (N_r = 5, N_theta = 9: even L), two shells
+    w = workloads.grid_family_workload("bbh", 1)
+    w.shells = w.shells[:2]
+    w.name = "bbh_k1_2shells"
+    return w
+
+
 CASES = {"schwarzschild": w_schwarzschild, "kerr2": w_kerr_two_shells, "ragged": w_ragged,
-         "minimal": w_minimal, "even_L": w_even_L}
+         "minimal": w_minimal, "even_L": w_even_L, "singlebh_k1": w_singlebh_k1, "bbh_k1": w_bbh_k1}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
