@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default work schedule instead of running gh_autotune before timing")
+    p.add_argument("--stepper", default="rk4", choices=["rk4", "dp5"],
+                   help="rk4 (fixed step, the headline) or dp5 (Dormand-Prince 5(4), adaptive)")
     p.add_argument("--schedule", default=None,
                    help="explicit work schedule as JSON (keys of gh.SCHEDULE_KEYS) instead of gh_autotune")
     p.add_argument("--workload", default="kerr4",
@@ -500,6 +502,65 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dp5(args, w):
+    """Dormand-Prince 5(4) adaptive evolution of the workload: each timed
+    attempt is 7 right-hand sides, 6 stage combinations and the error norm
+    (device time between CUDA events around the call, which ends with the
+    error norm read back to the host controller); rejected attempts count as
+    work done.  rtol = atol = 1e-8, starting from the workload's dt."""
+    import torch
+    from paper_1804_09101_gb300 import build
+    build.build()
+    from paper_1804_09101_gb300 import gh
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    dom = gh.Domain.from_workload(w)
+    if not args.no_autotune:
+        gh.gh_autotune(dom, 5)
+    u = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
+    p = w.pulse
+    if p is not None:
+        gh.gh_add_perturbation(dom, 0, p.amplitude, p.center, p.width, p.lmax, p.coeffs, u)
+    if w.noise_amp:
+        u += torch.from_numpy(w.noise()).to(u.device)
+    work = gh.new_dp5_work(dom)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    dt = w.dt
+    for _ in range(args.warmup):
+        _, _, dt = gh.gh_dp5_step(dom, dt, 1e-8, 1e-8, u, work)
+    clocks = ClockSampler(0)
+    clocks.start()
+    n0 = dom.launch_count()
+    tot_ms, acc, t_sim = 0.0, 0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dt0 = dt
+        _, ok, dt = gh.gh_dp5_step(dom, dt, 1e-8, 1e-8, u, work)
+        b.record(stream)
+        b.synchronize()
+        tot_ms += a.elapsed_time(b)
+        acc += int(ok)
+        t_sim += dt0 if ok else 0.0
+    clk = clocks.stop()
+    launches = dom.launch_count() - n0
+    pts = w.points()
+    line = dict(metric=METRIC, value=pts * 7 * args.steps / (tot_ms / 1e3), unit=UNIT, n_gpus=1,
+                steps=args.steps, warmup=args.warmup, ms_per_step=tot_ms / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=w.name, points=pts, stepper="Dormand-Prince 5(4), rtol = atol = 1e-8",
+                            rhs_evals_per_step=7, accepted=acc, attempts=args.steps, simulated_time=t_sim,
+                            final_dt=dt, l2="flushed before every timed attempt",
+                            schedule=gh.gh_get_schedule(dom)),
+                gpu_launches=launches)
+    if clk is not None:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def run_families(args):
     """The paper's benchmark grid families (Sec. 3.4) on four Kerr shells:
     SingleBH k = 0..8 (odd L: folded maps) and BBH k = 0..8 (even L:
@@ -604,6 +665,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.stepper == "dp5":
+        run_dp5(args, w)
     else:
         run_ours(args, w)
 
