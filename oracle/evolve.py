@@ -22,12 +22,13 @@ class Domain:
     """Shells, exact background and gauge source for one Kerr-Schild hole."""
 
     def __init__(self, shells, M, chi, gamma0=1.0, gamma1=-1.0, gamma2=1.0,
-                 filt_alpha=36.0, filt_order=32, radial_filter_on=False, sh_keep_l=-1):
+                 filt_alpha=36.0, filt_order=32, radial_filter_on=False, sh_keep_l=-1, outer_bc="freeze"):
         self.specs = list(shells)                 # (r_in, r_out, n_r, L)
         self.M, self.chi = M, chi
         self.gamma0, self.gamma1, self.gamma2 = gamma0, gamma1, gamma2
         self.filt_alpha, self.filt_order = filt_alpha, filt_order
         self.radial_filter_on, self.sh_keep_l = radial_filter_on, sh_keep_l
+        self.outer_bc = outer_bc                  # "freeze" or "cp" (constraint preserving, Bjorhus form)
         self.grids = [grid.shell_grid(*s) for s in self.specs]
         self.u_exact, self.H, self.dH = [], [], []
         for g in self.grids:
@@ -79,8 +80,10 @@ def rhs_interior(dom, u):
     return out
 
 
-def apply_boundaries(dom, dudt):
-    """ApplyBCs: outer freezing condition, upwind interface exchange, no-op at excision.
+def apply_boundaries(dom, dudt, u=None):
+    """ApplyBCs: outer freezing (or constraint-preserving) condition, upwind
+    interface exchange, no-op at excision.  u is needed for the
+    constraint-preserving outer condition.
 
     Shells are ordered by radius; shell s's outer slice and shell s+1's inner
     slice are the same physical points.
@@ -99,13 +102,19 @@ def apply_boundaries(dom, dudt):
     nr = out[s].shape[0]
     bg = dom.boundary_bg(s, nr - 1)
     a = np.moveaxis(out[s][nr - 1], 0, -1)
-    out[s][nr - 1] = np.moveaxis(gh.apply_outer_bc(a, bg, dom.gamma1, dom.gamma2), -1, 0)
+    if dom.outer_bc == "cp":
+        ub = np.moveaxis(u[s][nr - 1], 0, -1)                                    # [th, ph, 50]
+        dub = np.moveaxis(spectral.cartesian_gradient(u[s], dom.grids[s])[:, nr - 1], (0, 1), (-2, -1))
+        new = gh.apply_outer_bc_cp(a, ub, dub, bg, dom.gamma1, dom.gamma2)
+    else:
+        new = gh.apply_outer_bc(a, bg, dom.gamma1, dom.gamma2)
+    out[s][nr - 1] = np.moveaxis(new, -1, 0)
     return out
 
 
 def rhs(dom, u):
     """One full right-hand side evaluation: interior GH RHS, then ApplyBCs."""
-    return apply_boundaries(dom, rhs_interior(dom, u))
+    return apply_boundaries(dom, rhs_interior(dom, u), u)
 
 
 def apply_filters(dom, u):

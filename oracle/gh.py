@@ -250,6 +250,40 @@ def apply_outer_bc(dudt_b, bg, gamma1, gamma2):
     return from_char(*w, bg, gamma2)
 
 
+def apply_outer_bc_cp(dudt_b, u_b, du_b, bg, gamma1, gamma2):
+    """Constraint-preserving outer condition of Bjorhus form for the u^psi and
+    u^0 families, freezing for u^- (and u^+ if it were incoming).
+
+    The outer boundary condition of the paper is constraint preserving (Sec. 5);
+    its equations are those of the standard first-order GH system (Lindblom
+    et al. 2006, Sec. VI).  For the two families whose incoming parts carry the
+    derivative constraints, the characteristic time derivative computed from
+    the equations, D_t w, is replaced at incoming points by
+        d_t w_psi_ab  = D_t w_psi_ab + v_psi n^i C_iab,        C_iab  = d_i psi_ab - Phi_iab,
+        d_t w_0_iab   = D_t w_0_iab  + v_0 P_i^k n^j C_jkab,   C_jkab = d_j Phi_kab - d_k Phi_jab,
+    which removes the incoming normal derivative of the field from its
+    evolution equation.  u_b[..., 50] is the state and du_b[..., 3, 50] its
+    Cartesian derivatives at the boundary points.
+    """
+    wpsi, w0, wp, wm = to_char(dudt_b, bg, gamma2)
+    v_psi, v_0, v_p, v_m = char_speeds(bg, gamma1)
+    psi, Pi, Phi = unpack_fields(u_b)
+    dpsi = np.stack([unpack_fields(du_b[..., i, :])[0] for i in range(3)], axis=-3)   # [..., i, a, b]
+    dPhi = np.stack([unpack_fields(du_b[..., j, :])[2] for j in range(3)], axis=-4)   # [..., j, k, a, b]
+    C3 = dpsi - Phi
+    C4 = dPhi - np.swapaxes(dPhi, -4, -3)
+    nC3 = np.einsum("...i,...iab->...ab", bg["n_up"], C3)
+    m = np.einsum("...j,...jkab->...kab", bg["n_up"], C4)
+    Pm = m - np.einsum("...i,...k,...kab->...iab", bg["n_dn"], bg["n_up"], m)
+    inc_psi = (v_psi < 0.0)[..., None, None]
+    inc_0 = (v_0 < 0.0)[..., None, None, None]
+    wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)
+    w0 = np.where(inc_0, w0 + v_0[..., None, None, None] * Pm, w0)
+    wm = np.where((v_m < 0.0)[..., None, None], 0.0, wm)
+    wp = np.where((v_p < 0.0)[..., None, None], 0.0, wp)
+    return from_char(wpsi, w0, wp, wm, bg, gamma2)
+
+
 def apply_interface_bc(dudt_in, dudt_out, bg, gamma1, gamma2):
     """Upwind exchange at a shared radius between an inner and an outer shell.
 
