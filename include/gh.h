@@ -260,6 +260,18 @@ long long gh_launch_count(const gh_domain* dom);
 enum { GH_ALG_DENSE = 0, GH_ALG_SEPARABLE = 1, GH_ALG_SEPARABLE_FOLDED = 2 };
 gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
 
+/* Outer boundary condition (ApplyBCs at the external boundary, Sec. 5).
+ * GH_BC_FREEZE (default): incoming characteristic time derivatives set to 0.
+ * GH_BC_CONSTRAINT_PRESERVING: Bjorhus form for the u^psi and u^0 families --
+ *   at incoming points d_t u^psi_ab = D_t u^psi_ab + v_psi n^i C_iab and
+ *   d_t u^0_iab = D_t u^0_iab + v_0 P_i^k n^j C_jkab (D_t: the characteristic
+ *   projection of the equations, C_iab = d_i psi_ab - Phi_iab, C_jkab = d_j Phi_kab
+ *   - d_k Phi_jab), which removes the incoming normal derivative of those fields;
+ *   u^- is frozen.  The adjoint entry points return GH_ENOTSUP in this mode.
+ * Synchronises the stream and discards a captured RK4 graph. */
+enum { GH_BC_FREEZE = 0, GH_BC_CONSTRAINT_PRESERVING = 1 };
+gh_status gh_set_outer_bc(gh_domain* dom, int mode);
+
 /* Dormand-Prince 5(4) adaptive step: the paper's time stepper (Sec. 2.1; the
  * embedded pair of Dormand & Prince 1980, seven right-hand sides per attempt,
  * no stage reused across steps).  One attempt from u with step dt:

@@ -418,6 +418,8 @@ unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 gh_status adj_ready(gh_domain* d) {
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
+  if (d->outer_bc != 0)
+    return afail(d, GH_ENOTSUP, "the adjoint is built for the freezing outer boundary condition only");
   if (!d->kbt) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));
@@ -485,7 +487,7 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
 gh_status rhs_fwd(gh_domain* d, const double* u, double* k) {
   GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, gh::launch_pointwise(d, u, k, 0, 0.0, nullptr, nullptr, nullptr, false));
-  GH_ACUDA(d, gh::launch_bc(d, k, 0, 0.0, nullptr, nullptr, nullptr));
+  GH_ACUDA(d, gh::launch_bc(d, k, 0, 0.0, nullptr, nullptr, nullptr, u));
   return GH_OK;
 }
 

@@ -1219,7 +1219,7 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
   }
   {
     ProfScope p(d, GH_K_BC);
-    GH_CUDA(d, gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr));
+    GH_CUDA(d, gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr, u));
   }
   return GH_OK;
 }
@@ -1246,7 +1246,7 @@ gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double
     }
     {
       ProfScope p(d, GH_K_BC);
-      GH_CUDA(d, gh::launch_bc(d, k, stage, dt, u, acc, target));
+      GH_CUDA(d, gh::launch_bc(d, k, stage, dt, u, acc, target, in));
     }
   }
   if (filt) {
@@ -1302,7 +1302,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
     }
     {
       ProfScope p(d, GH_K_BC);
-      GH_CUDA(d, gh::launch_bc(d, k[s], 0, 0.0, nullptr, nullptr, nullptr));
+      GH_CUDA(d, gh::launch_bc(d, k[s], 0, 0.0, nullptr, nullptr, nullptr, in));
     }
     if (s < 6) {
       // next stage state (s = 5 gives the fifth-order solution, row 7 = b)
@@ -1445,6 +1445,19 @@ gh_status gh_autotune(gh_domain* d, int reps) {
   }
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   invalidate_graph(d);
+  return GH_OK;
+}
+
+gh_status gh_set_outer_bc(gh_domain* d, int mode) {
+  if (!d) return GH_EINVAL;
+  if (mode != GH_BC_FREEZE && mode != GH_BC_CONSTRAINT_PRESERVING)
+    return fail(d, GH_EINVAL, "mode must be GH_BC_FREEZE or GH_BC_CONSTRAINT_PRESERVING");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  d->outer_bc = mode;
+  if (d->graph_exec) {
+    cudaGraphExecDestroy(d->graph_exec);
+    d->graph_exec = nullptr;
+  }
   return GH_OK;
 }
 

@@ -190,6 +190,8 @@ struct gh_domain {
   double* pert_partial = nullptr; int pert_partial_len = 0;
   // Dormand-Prince step: per-block partial sums of the error norm and the norm
   double* dp_partial = nullptr;
+  // outer boundary condition: 0 freezing, 1 constraint preserving (gh_set_outer_bc)
+  int outer_bc = 0;
   double* dp_err = nullptr;
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;
@@ -229,8 +231,12 @@ cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const doubl
                                       const double* dph, double* k);
 cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage, double dt,
                              const double* u0, double* acc, double* ustage, bool constraints);
-cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const double* u0,
-                      double* acc, double* ustage);
+// Boundary conditions on k = dudt (RK4 combine of boundary points for stage
+// >= 1).  u_in: the state the RHS was evaluated at, and deriv[3] its
+// spherical-basis derivatives (null: the domain's scratch); both used by the
+// constraint-preserving outer condition only.
+cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const double* u0, double* acc,
+                      double* ustage, const double* u_in = nullptr, const double* const* deriv = nullptr);
 cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out);
 cudaError_t launch_norm_reduce(gh_domain* d, double* norm2);
 cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du);

@@ -778,7 +778,51 @@ struct BcArgs {
   double* us;
   double gamma1, gamma2, dt;
   int stage;
+  // constraint-preserving outer condition: the state the RHS was evaluated at,
+  // its spherical-basis derivatives and the shells (for the DiffJac matrix)
+  int cp_outer;
+  const ShellDev* shells;
+  const double* u_in;
+  const double* dr;
+  const double* dth;
+  const double* dph;
 };
+
+// Bjorhus-form constraint-preserving corrections at an outer-boundary point for
+// pair p: nC3 = n^i C_ip (C_iab = d_i psi_ab - Phi_iab) and
+// Pm[i] = P_i^k n^j C_jkp (C_jkab = d_j Phi_kab - d_k Phi_jab).
+__device__ __forceinline__ void cp_corrections(const BcArgs& a, const BcSliceDev& sl, int q, int p,
+                                               const double n_dn[3], const double n_up[3], double& nC3,
+                                               double Pm[3]) {
+  const ShellDev& sh = a.shells[sl.shell_a];
+  PointGeom G;
+  point_geom(sh, sh.n_r - 1, q, G);
+  const int na = sl.na;
+  const long long base = sl.off_a + q;
+  auto cart = [&](int f, int i) {
+    const long long o = base + (long long)f * na;
+    return fma(G.J[i][2], a.dph[o], fma(G.J[i][1], a.dth[o], G.J[i][0] * a.dr[o]));
+  };
+  nC3 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) nC3 = fma(n_up[i], cart(p, i) - a.u_in[base + (long long)(20 + 10 * i + p) * na], nC3);
+  double dPhi[3][3];   // dPhi[j][k] = d_j Phi_kp
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dPhi[j][k] = cart(20 + 10 * k + p, j);
+  double m[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc = fma(n_up[j], dPhi[j][k] - dPhi[k][j], acc);
+    m[k] = acc;
+  }
+  const double nm = n_up[0] * m[0] + n_up[1] * m[1] + n_up[2] * m[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Pm[i] = m[i] - n_dn[i] * nm;
+}
 
 // The characteristic projection couples only the 5 fields of one symmetric
 // pair p (psi_p, Pi_p, Phi_xp, Phi_yp, Phi_zp), so each thread handles one
@@ -851,8 +895,21 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     const long long base = sl.off_a + q;
     CharPair c;
     char_project_pair(a.k, base, na, p, n_dn, n_up, g2, c);
-    if (v_psi < 0.0) c.psi = 0.0;
-    if (v_0 < 0.0) c.w0[0] = c.w0[1] = c.w0[2] = 0.0;
+    if (a.cp_outer) {
+      // constraint preserving for u^psi and u^0, freezing for u^- (and u^+)
+      if (v_psi < 0.0 || v_0 < 0.0) {
+        double nC3, Pm[3];
+        cp_corrections(a, sl, q, p, n_dn, n_up, nC3, Pm);
+        if (v_psi < 0.0) c.psi = fma(v_psi, nC3, c.psi);
+        if (v_0 < 0.0) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) c.w0[i] = fma(v_0, Pm[i], c.w0[i]);
+        }
+      }
+    } else {
+      if (v_psi < 0.0) c.psi = 0.0;
+      if (v_0 < 0.0) c.w0[0] = c.w0[1] = c.w0[2] = 0.0;
+    }
     if (v_p < 0.0) c.wp = 0.0;
     if (v_m < 0.0) c.wm = 0.0;
     char_write_pair(a, base, na, p, c, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
@@ -1060,12 +1117,19 @@ cudaError_t launch_norm_reduce(gh_domain* d, double* norm2) {
 }
 
 cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const double* u0, double* acc,
-                      double* ustage) {
+                      double* ustage, const double* u_in, const double* const* deriv) {
   if (d->bc_points == 0) return cudaSuccess;
   BcArgs a;
   a.slices = d->bc_d; a.n_slices = (int)d->bc_h.size(); a.pt_begin = d->bc_pt_begin_d;
   a.k = k; a.u0 = u0; a.acc = acc; a.us = ustage;
   a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2; a.dt = dt; a.stage = stage;
+  a.cp_outer = d->outer_bc;
+  a.shells = d->shells_d;
+  a.u_in = u_in;
+  a.dr = deriv ? deriv[0] : d->d_r;
+  a.dth = deriv ? deriv[1] : d->d_th;
+  a.dph = deriv ? deriv[2] : d->d_ph;
+  if (a.cp_outer && !u_in) return cudaErrorInvalidValue;
   bc_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(a);
   d->launches++;
   return cudaGetLastError();

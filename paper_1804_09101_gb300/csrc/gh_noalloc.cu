@@ -70,7 +70,8 @@ extern "C" gh_status gh_rhs_noalloc(gh_domain* d, const double* u, double* dudt)
   if (e == cudaSuccess) e = gh::launch_radial(d, u, w, false);
   if (e == cudaSuccess) e = gh::launch_angular_deriv_into(d, u, w + kMaxState, w + 2 * kMaxState);
   if (e == cudaSuccess) e = gh::launch_pointwise_rhs_from(d, u, w, w + kMaxState, w + 2 * kMaxState, dudt);
-  if (e == cudaSuccess) e = gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr);
+  const double* deriv[3] = {w, w + kMaxState, w + 2 * kMaxState};
+  if (e == cudaSuccess) e = gh::launch_bc(d, dudt, 0, 0.0, nullptr, nullptr, nullptr, u, deriv);
   if (e != cudaSuccess) {
     d->err = std::string("gh_rhs_noalloc: ") + cudaGetErrorString(e);
     return GH_ECUDA;

@@ -71,6 +71,7 @@ def _load():
         "gh_sync": ([P], I),
         "gh_set_algorithm": ([P, I], I),
         "gh_autotune": ([P, I], I),
+        "gh_set_outer_bc": ([P, I], I),
         "gh_dp5_work_size": ([P], ctypes.c_longlong),
         "gh_dp5_step": ([P, D, D, D, P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "gh_get_schedule": ([P, ctypes.POINTER(I), I], I),
@@ -268,6 +269,14 @@ GH_ALG_DENSE, GH_ALG_SEPARABLE, GH_ALG_SEPARABLE_FOLDED = 0, 1, 2
 def gh_set_algorithm(dom, algorithm):
     dom._stream()
     dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
+
+
+GH_BC_FREEZE, GH_BC_CONSTRAINT_PRESERVING = 0, 1
+
+
+def gh_set_outer_bc(dom, mode):
+    dom._stream()
+    dom._check(_lib.gh_set_outer_bc(dom.handle, int(mode)))
 
 
 def gh_dp5_step(dom, dt, rtol, atol, u, work):
