@@ -16,6 +16,16 @@ First and second spatial derivatives come from sympy's symbolic
 differentiation of exactly these expressions, evaluated with numpy
 (lambdify): the definition written out, no hand-derived derivative.
 
+For a spin vector a = chi M (any direction; the paper's own test uses
+chi = (0.2, 0.3, 0.4), Sec. 3.1) the same form reads, with a.x the Euclidean
+dot product and a x x the cross product,
+
+    H    = M r^3 / (r^4 + (a.x)^2),
+    l_i  = (r x_i - (a x x)_i + (a.x) a_i / r) / (r^2 + a^2),
+    r^2  = (R^2 - a^2)/2 + sqrt((R^2 - a^2)^2 / 4 + (a.x)^2),
+
+which reduces to the expressions above for a along +z.
+
 From the metric the GH evolved fields and the gauge source follow:
     psi_ab   = g_ab,
     Phi_iab  = d_i g_ab,
@@ -61,17 +71,53 @@ def _lambdified():
     return f_g, f_dg, f_ddg
 
 
+@functools.lru_cache(maxsize=1)
+def _lambdified_vector():
+    x, y, z, M, ax, ay, az = sp.symbols("x y z M ax ay az", real=True)
+    R2 = x * x + y * y + z * z
+    a2 = ax * ax + ay * ay + az * az
+    ad = ax * x + ay * y + az * z
+    r2 = (R2 - a2) / 2 + sp.sqrt((R2 - a2) ** 2 / 4 + ad * ad)
+    r = sp.sqrt(r2)
+    H = M * r ** 3 / (r ** 4 + ad * ad)
+    X = [x, y, z]
+    A = [ax, ay, az]
+    cross = [ay * z - az * y, az * x - ax * z, ax * y - ay * x]
+    l = [sp.Integer(1)] + [(r * X[i] - cross[i] + ad * A[i] / r) / (r2 + a2) for i in range(3)]
+    eta = sp.diag(-1, 1, 1, 1)
+    g, dg, ddg = [], [], []
+    for P in range(4):
+        for Q in range(P, 4):
+            gab = eta[P, Q] + 2 * H * l[P] * l[Q]
+            g.append(gab)
+            for i in range(3):
+                d = sp.diff(gab, X[i])
+                dg.append(d)
+                for j in range(i, 3):
+                    ddg.append(sp.diff(d, X[j]))
+    args = (x, y, z, M, ax, ay, az)
+    return (sp.lambdify(args, g, modules="numpy", cse=True), sp.lambdify(args, dg, modules="numpy", cse=True),
+            sp.lambdify(args, ddg, modules="numpy", cse=True))
+
+
 _PAIRS = [(A, B) for A in range(4) for B in range(A, 4)]
 
 
 def metric_and_derivatives(X, Y, Z, M, a):
-    """g[..., 4, 4], dg[..., 3, 4, 4] (d_i g_ab), ddg[..., 3, 3, 4, 4] (d_i d_j g_ab)."""
-    f_g, f_dg, f_ddg = _lambdified()
+    """g[..., 4, 4], dg[..., 3, 4, 4] (d_i g_ab), ddg[..., 3, 3, 4, 4] (d_i d_j g_ab).
+
+    a: the spin parameter along +z (a scalar), or a spin vector (3 numbers)."""
+    if np.ndim(a) == 0:
+        f_g, f_dg, f_ddg = _lambdified()
+        args = (X, Y, Z, M, a)
+    else:
+        f_g, f_dg, f_ddg = _lambdified_vector()
+        args = (X, Y, Z, M) + tuple(float(c) for c in a)
     shp = np.shape(X)
     one = np.ones(shp)
-    gv = [np.asarray(v) * one for v in f_g(X, Y, Z, M, a)]
-    dgv = [np.asarray(v) * one for v in f_dg(X, Y, Z, M, a)]
-    ddgv = [np.asarray(v) * one for v in f_ddg(X, Y, Z, M, a)]
+    gv = [np.asarray(v) * one for v in f_g(*args)]
+    dgv = [np.asarray(v) * one for v in f_dg(*args)]
+    ddgv = [np.asarray(v) * one for v in f_ddg(*args)]
     g = np.zeros(shp + (4, 4))
     dg = np.zeros(shp + (3, 4, 4))
     ddg = np.zeros(shp + (3, 3, 4, 4))
@@ -122,14 +168,15 @@ def gh_fields(g, dg):
 
 
 def kerr_schild_shell(g_shell, M, chi):
-    """Exact KS data on one shell grid (spin chi along +z, a = chi M).
+    """Exact KS data on one shell grid (a = chi M; chi a number: spin along +z,
+    or a dimensionless spin vector of 3 numbers).
 
     Returns (u[n_r, 50, n_th, n_ph], H[n_r, 4, n_th, n_ph], dH[n_r, 12, n_th, n_ph]);
     dH is ordered dH[4*i + a] = d_i H_a.
     """
     from . import grid
     X, Y, Z = grid.cartesian_coords(g_shell)
-    a = chi * M
+    a = chi * M if np.ndim(chi) == 0 else tuple(float(c) * M for c in chi)
     g, dg, ddg = metric_and_derivatives(X, Y, Z, M, a)
     psi, Pi, Phi = gh_fields(g, dg)
     H, dH = gauge_source(g, dg, ddg)

@@ -171,7 +171,10 @@ def _sample_points():
     return P[:, 0], P[:, 1], P[:, 2]
 
 
-@pytest.mark.parametrize("chi", [0.0, 0.9])
+TILTED = (0.2, 0.3, 0.4)     # the paper's test-problem spin vector (Sec. 3.1)
+
+
+@pytest.mark.parametrize("chi", [0.0, 0.9, TILTED])
 def test_kerr_schild_null_vector_and_determinant(chi):
     X, Y, Z = _sample_points()
     g, dg, ddg = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, chi)
@@ -190,7 +193,47 @@ def test_kerr_schild_reduces_to_schwarzschild():
     assert np.abs(g - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("chi", [0.0, 0.9])
+def _rotation_taking_z_to(n):
+    """Rodrigues rotation matrix R with R e_z = n (unit vector)."""
+    z = np.array([0.0, 0.0, 1.0])
+    v = np.cross(z, n)
+    c = float(np.dot(z, n))
+    K = np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+    return np.eye(3) + K + K @ K / (1.0 + c)
+
+
+def test_spin_vector_form_is_the_rotated_z_axis_metric():
+    """Kerr-Schild with spin vector a equals the z-axis metric of the same |a|
+    evaluated at R^T x and transformed as a tensor (R e_z = a/|a|): the vector
+    formula is pinned by rotation covariance, not by itself."""
+    X, Y, Z = _sample_points()
+    a = np.array(TILTED) * 1.3
+    amag = float(np.linalg.norm(a))
+    R = _rotation_taking_z_to(a / amag)
+    assert np.abs(R @ R.T - np.eye(3)).max() < 1e-15
+    x = np.stack([X, Y, Z], axis=-1)
+    xr = x @ R                                      # R^T x for row vectors
+    gz, dgz, _ = kerr_schild.metric_and_derivatives(xr[:, 0], xr[:, 1], xr[:, 2], 1.3, amag)
+    L = np.eye(4)
+    L[1:, 1:] = R
+    ref = np.einsum("ac,...cd,bd->...ab", L, gz, L)
+    # d_i g(x) = R_ij (d_j g^z)(R^T x), transformed on ab as above
+    dref = np.einsum("ij,ac,...jcd,bd->...iab", R, L, dgz, L)
+    g, dg, _ = kerr_schild.metric_and_derivatives(X, Y, Z, 1.3, tuple(a))
+    assert np.abs(g - ref).max() < 1e-13
+    assert np.abs(dg - dref).max() < 1e-12
+
+
+def test_spin_vector_along_z_matches_the_scalar_form():
+    X, Y, Z = _sample_points()
+    g1, dg1, ddg1 = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, 0.9)
+    g2, dg2, ddg2 = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, (0.0, 0.0, 0.9))
+    assert np.abs(g1 - g2).max() < 1e-14
+    assert np.abs(dg1 - dg2).max() < 1e-13
+    assert np.abs(ddg1 - ddg2).max() < 1e-12
+
+
+@pytest.mark.parametrize("chi", [0.0, 0.9, TILTED])
 def test_kerr_schild_derivatives_match_finite_differences(chi):
     X, Y, Z = _sample_points()
     g, dg, ddg = kerr_schild.metric_and_derivatives(X, Y, Z, 1.0, chi)
@@ -204,7 +247,7 @@ def test_kerr_schild_derivatives_match_finite_differences(chi):
         assert np.abs((dgp - dgm) / (2 * h) - ddg[:, :, i]).max() < 1e-7
 
 
-@pytest.mark.parametrize("chi", [0.0, 0.9])
+@pytest.mark.parametrize("chi", [0.0, 0.9, TILTED])
 def test_gauge_source_zeroes_gauge_constraint_and_dH_matches_fd(chi):
     """H_a = -Gamma_a computed from d g (kerr_schild) makes C_a = H_a + Gamma_a,
     computed through the t/Pi/Phi identity (gh), vanish; d_i H by FD."""
