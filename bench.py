@@ -57,12 +57,12 @@ def parse():
     p.add_argument("--schedule", default=None,
                    help="explicit work schedule as JSON (keys of gh.SCHEDULE_KEYS) instead of gh_autotune")
     p.add_argument("--workload", default="kerr4",
-                   choices=["kerr4", "large", "schwarzschild", "batched", "adjoint", "families"],
+                   choices=["kerr4", "large", "schwarzschild", "batched", "adjoint", "families", "paper"],
                    help="kerr4: 4-shell Kerr a=0.9 (default, the headline); large: 8-shell Kerr a=0.95, "
                         "N_r=41, L=31; schwarzschild: 1 shell N_r=11, L=7; batched: 64 independent "
                         "single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
                         "compared with the plain per-hole launch loop")
-    p.add_argument("--algorithm", default="folded", choices=["folded", "separable", "dense"],
+    p.add_argument("--algorithm", default="auto", choices=["auto", "folded", "separable", "dense"],
                    help="angular maps: folded separable (default), plain separable, or dense traced matrices")
     return p.parse_args()
 
@@ -201,8 +201,12 @@ def run_ours(args, w):
     dev = torch.device("cuda", local)
 
     dom = gh.Domain.from_workload(w)
-    gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
-                              "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
+    if args.algorithm == "auto":
+        # the library's default: folded maps when every shell has odd L, else separable
+        args.algorithm = "folded" if all(s[3] % 2 == 1 for s in w.shells) else "separable"
+    else:
+        gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
+                                  "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
     if args.schedule:
         gh.gh_set_schedule(dom, json.loads(args.schedule))
     elif not args.no_autotune:
@@ -311,7 +315,7 @@ def run_ours(args, w):
                             dt=w.dt, rhs_evals_per_step=4,
                             step="RK4 step + ExpCheb(36,32) + SH keep l<=%d + constraint norms" % w.sh_keep_l,
                             l2="flushed before every timed step (256 MB write, outside the step events)",
-                            parallelism="replicas" if world > 1 else "single GPU",
+                            parallelism="replicas" if world > 1 else "single GPU", algorithm=args.algorithm,
                             schedule=gh.gh_get_schedule(dom),
                             autotuned=not (args.no_autotune or args.schedule)),
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=state_bytes,
@@ -644,7 +648,7 @@ def main():
     w = {"kerr4": workloads.kerr_four_shells, "large": workloads.kerr_eight_shells_large,
          "schwarzschild": workloads.schwarzschild_single_shell,
          "batched": workloads.kerr_four_shells, "adjoint": workloads.kerr_four_shells,
-         "families": workloads.kerr_four_shells}[args.workload]()
+         "families": workloads.kerr_four_shells, "paper": workloads.paper_single_bh}[args.workload]()
     if args.workload == "adjoint":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no oracle arm"}))

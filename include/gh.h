@@ -112,6 +112,14 @@ int gh_num_shells(const gh_domain* dom);
  * (Eq. dimensionlessspin).  Computed on the device with forward-mode
  * second-order dual numbers. */
 gh_status gh_set_analytic_kerr_schild(gh_domain* dom, int bh, double M, double chi, double* u);
+/* The same for a dimensionless spin vector chi[3] of any direction (host
+ * pointer), a = chi M: the paper's own test hole has chi = (0.2, 0.3, 0.4)
+ * (Sec. 3.1, Eq. dimensionlessspin).  With a.x the Euclidean dot product and
+ * a x x the cross product: H = M r^3 / (r^4 + (a.x)^2), l_0 = 1,
+ * l_i = (r x_i - (a x x)_i + (a.x) a_i / r) / (r^2 + a^2),
+ * r^2 = (R^2 - a^2)/2 + sqrt((R^2 - a^2)^2/4 + (a.x)^2).  GH_EINVAL unless
+ * M > 0 and |chi| < 1. */
+gh_status gh_set_analytic_kerr_schild_spin(gh_domain* dom, int bh, double M, const double chi[3], double* u);
 
 /* Scale the time step of hole bh: its shells advance by dt * scale in every
  * gh_rk4_step(dom, dt, ...).  Lets holes of different resolution take their

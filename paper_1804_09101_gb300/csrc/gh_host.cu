@@ -1065,14 +1065,20 @@ long long gh_launch_count(const gh_domain* d) { return d ? d->launches : -1; }
 
 const char* gh_last_error(const gh_domain* d) { return d ? d->err.c_str() : g_create_error.c_str(); }
 
-gh_status gh_set_analytic_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u) {
-  if (!d || !u) return fail(d, GH_EINVAL, "null argument");
-  if (!(M > 0.0) || !(std::fabs(chi) < 1.0)) return fail(d, GH_EINVAL, "need M > 0 and |chi| < 1");
+gh_status gh_set_analytic_kerr_schild_spin(gh_domain* d, int bh, double M, const double chi[3], double* u) {
+  if (!d || !u || !chi) return fail(d, GH_EINVAL, "null argument");
+  const double c2 = chi[0] * chi[0] + chi[1] * chi[1] + chi[2] * chi[2];
+  if (!(M > 0.0) || !(c2 < 1.0)) return fail(d, GH_EINVAL, "need M > 0 and |chi| < 1");
   if (bh < -1) return fail(d, GH_EINVAL, "bh must be -1 (all) or a hole index");
   if (gh_status s = check_latched(d)) return s;
   GH_CUDA(d, gh::launch_kerr_schild(d, bh, M, chi, u));
   GH_CUDA(d, gh::launch_bc_background(d, u, bh));
   return GH_OK;
+}
+
+gh_status gh_set_analytic_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u) {
+  const double v[3] = {0.0, 0.0, chi};
+  return gh_set_analytic_kerr_schild_spin(d, bh, M, v, u);
 }
 
 gh_status gh_set_dt_scale(gh_domain* d, int bh, double scale) {

@@ -85,21 +85,30 @@ __device__ __forceinline__ Jet jsqrt(const Jet& a) {
 }
 __device__ __forceinline__ Jet operator/(const Jet& a, const Jet& b) { return a * jinv(b); }
 
-// Kerr-Schild metric g_ab = eta_ab + 2 H l_a l_b, spin along +z, a = chi M.
-__device__ void kerr_schild_metric(double x, double y, double z, double M, double a, Jet g[10]) {
+// Kerr-Schild metric g_ab = eta_ab + 2 H l_a l_b for the spin vector a = chi M
+// (any direction): with a.x the Euclidean dot product and a x x the cross product,
+//   r^2 = (R^2 - a^2)/2 + sqrt((R^2 - a^2)^2/4 + (a.x)^2),  H = M r^3 / (r^4 + (a.x)^2),
+//   l = (1, (r x_i - (a x x)_i + (a.x) a_i / r) / (r^2 + a^2)).
+__device__ void kerr_schild_metric(double x, double y, double z, double M, const double av[3], Jet g[10]) {
   const Jet X = jvar(x, 0), Y = jvar(y, 1), Z = jvar(z, 2);
-  const Jet a2 = jconst(a * a);
+  const double ax = av[0], ay = av[1], az = av[2];
+  const double a2v = ax * ax + ay * ay + az * az;
+  const Jet a2 = jconst(a2v);
+  const Jet ad = ax * X + ay * Y + az * Z;
   const Jet R2 = X * X + Y * Y + Z * Z;
   const Jet hm = 0.5 * (R2 - a2);
-  const Jet r2 = hm + jsqrt(hm * hm + (a * a) * (Z * Z));
+  const Jet ad2 = ad * ad;
+  const Jet r2 = hm + jsqrt(hm * hm + ad2);
   const Jet r = jsqrt(r2);
-  const Jet H = M * (r * r2) / (r2 * r2 + (a * a) * (Z * Z));
+  const Jet H = M * (r * r2) / (r2 * r2 + ad2);
   const Jet den = jinv(r2 + a2);
+  const Jet adr = ad / r;
+  const Jet cx = ay * Z - az * Y, cy = az * X - ax * Z, cz = ax * Y - ay * X;
   Jet l[4];
   l[0] = jconst(1.0);
-  l[1] = (r * X + a * Y) * den;
-  l[2] = (r * Y - a * X) * den;
-  l[3] = Z / r;
+  l[1] = (r * X - cx + ax * adr) * den;
+  l[2] = (r * Y - cy + ay * adr) * den;
+  l[3] = (r * Z - cz + az * adr) * den;
   const Jet twoH = 2.0 * H;
   for (int p = 0; p < 10; ++p) {
     const int A = pair_a(p), B = pair_b(p);
@@ -112,7 +121,7 @@ __device__ void kerr_schild_metric(double x, double y, double z, double M, doubl
 // gauge source H_a = -Gamma_a, d_i H_a = -d_i Gamma_a (d_t H_a = 0).
 __global__ void __launch_bounds__(64)
 kerr_schild_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
-                   int bh, double M, double a, double* __restrict__ u) {
+                   int bh, double M, double ax, double ay, double az, double* __restrict__ u) {
   const int s = [&] { int t = 0; while (t + 1 < n_shells && begin[t + 1] <= (int)blockIdx.x) ++t; return t; }();
   const ShellDev& sh = shells[s];
   if (bh >= 0 && sh.bh != bh) return;
@@ -126,7 +135,8 @@ kerr_schild_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
   const double r = sh.r[ir];
   const double x = r * sh.sth[j] * sh.cph[k], y = r * sh.sth[j] * sh.sph[k], z = r * sh.cth[j];
   Jet g[10];
-  kerr_schild_metric(x, y, z, M, a, g);
+  const double av[3] = {ax, ay, az};
+  kerr_schild_metric(x, y, z, M, av, g);
   double psi[10], Phi[30], Pi[10];
   for (int p = 0; p < 10; ++p) {
     psi[p] = g[p].v;
@@ -237,7 +247,7 @@ perturbation_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   }
 }
 
-cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u) {
+cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, const double chi[3], double* u) {
   // 64-thread blocks: reuse the pointwise block map scaled by 2
   int blocks = 0;
   std::vector<int> begin(d->n_shells + 1);
@@ -251,7 +261,8 @@ cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, double chi, doubl
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(bd, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice, d->stream);
   if (e != cudaSuccess) return e;
-  kerr_schild_kernel<<<blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, bd, bh, M, chi * M, u);
+  kerr_schild_kernel<<<blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, bd, bh, M, chi[0] * M, chi[1] * M,
+                                                    chi[2] * M, u);
   d->launches++;
   e = cudaGetLastError();
   cudaFreeAsync(bd, d->stream);

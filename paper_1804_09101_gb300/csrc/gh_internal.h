@@ -241,7 +241,7 @@ cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out);
 cudaError_t launch_norm_reduce(gh_domain* d, double* norm2);
 cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du);
 cudaError_t launch_bc_background(gh_domain* d, const double* u, int bh);
-cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, double chi, double* u);
+cudaError_t launch_kerr_schild(gh_domain* d, int bh, double M, const double chi[3], double* u);
 cudaError_t launch_perturbation(gh_domain* d, int kind, double A, double Rc, double w,
                                 int lmax, const double* coeffs_dev, double* u);
 

@@ -55,6 +55,7 @@ def _load():
         "gh_launch_count": ([P], ctypes.c_longlong),
         "gh_last_error": ([P], ctypes.c_char_p),
         "gh_set_analytic_kerr_schild": ([P, I, D, D, P], I),
+        "gh_set_analytic_kerr_schild_spin": ([P, I, D, ctypes.POINTER(D), P], I),
         "gh_set_dt_scale": ([P, I, D], I),
         "gh_rk4_graph_capture": ([P, D, P, P, P], I),
         "gh_rk4_graph_launch": ([P, I], I),
@@ -168,9 +169,15 @@ class Domain:
 
 
 def gh_set_analytic_kerr_schild(dom, bh, M, chi, u):
+    """Exact Kerr-Schild data; chi a number (spin along +z) or a 3-vector."""
     dom._stream()
-    dom._check(_lib.gh_set_analytic_kerr_schild(dom.handle, int(bh), float(M), float(chi),
-                                                _ptr(u, "u", dom.state_size)))
+    if hasattr(chi, "__len__"):
+        v = (ctypes.c_double * 3)(*[float(c) for c in chi])
+        dom._check(_lib.gh_set_analytic_kerr_schild_spin(dom.handle, int(bh), float(M), v,
+                                                         _ptr(u, "u", dom.state_size)))
+    else:
+        dom._check(_lib.gh_set_analytic_kerr_schild(dom.handle, int(bh), float(M), float(chi),
+                                                    _ptr(u, "u", dom.state_size)))
 
 
 def gh_set_dt_scale(dom, bh, scale):

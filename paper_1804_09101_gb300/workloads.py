@@ -101,6 +101,18 @@ def kerr_eight_shells_large(n_r=41, L=31, seed=105):
                     pulse=Pulse("psi_pulse", 1e-5, 50.0, 4.0, 8, random_coeffs(seed, 8)))
 
 
+def paper_single_bh(seed=107):
+    """The paper's own test problem (Sec. 3.1): M = 1, spin vector
+    chi = (0.2, 0.3, 0.4), two shells [1.62, 6] and [6, 12] with 10 x 19 x 38
+    points each (N_r = 10, L = 18: 7,220 points per shell).  No radial filter
+    (as in the paper's production runs, Sec. 3.4); SH filter keep l <= 12;
+    dt = 0.25 x the smallest grid spacing; seeded 1e-8 noise."""
+    shells = [(1.62, 6.0, 10, 18), (6.0, 12.0, 10, 18)]
+    return Workload(name="paper_singlebh_chi0.2_0.3_0.4_2shells_nr10_L18", shells=shells, M=1.0,
+                    chi=(0.2, 0.3, 0.4), radial_filter_on=False, sh_keep_l=12,
+                    dt=_stable_dt(1.62, 6.0, 10, 18), steps=100, seed=seed, noise_amp=1e-8)
+
+
 def grid_family_resolution(family, k):
     """(N_r, L) of member k of the paper's benchmark grid families (Sec. 3.4):
     SingleBH N_r = 9 + 4k, N_theta = 6 + 2k; BBH N_r = 4 + k, N_theta = 7 + 2k;

@@ -74,8 +74,14 @@ def w_bbh_k1():
     return w
 
 
+def w_paper_singlebh():
+    # the paper's own test problem: tilted spin (0.2, 0.3, 0.4), two 10 x 19 x 38 shells
+    return workloads.paper_single_bh()
+
+
 CASES = {"schwarzschild": w_schwarzschild, "kerr2": w_kerr_two_shells, "ragged": w_ragged,
-         "minimal": w_minimal, "even_L": w_even_L, "singlebh_k1": w_singlebh_k1, "bbh_k1": w_bbh_k1}
+         "minimal": w_minimal, "even_L": w_even_L, "singlebh_k1": w_singlebh_k1, "bbh_k1": w_bbh_k1,
+         "paper_singlebh": w_paper_singlebh}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
@@ -180,7 +186,7 @@ def test_filters(case, alg):
 @pytest.mark.parametrize("name,steps,alg", [("schwarzschild", 20, "separable"), ("kerr2", 3, "separable"),
                                             ("ragged", 2, "separable"), ("minimal", 5, "separable"),
                                             ("kerr2", 2, "dense"), ("kerr2", 3, "folded"),
-                                            ("schwarzschild", 5, "folded")])
+                                            ("schwarzschild", 5, "folded"), ("paper_singlebh", 2, "separable")])
 def test_rk4_steps(name, steps, alg):
     gh = _gh()
     w = CASES[name]()
