@@ -202,8 +202,7 @@ def run_ours(args, w):
 
     dom = gh.Domain.from_workload(w)
     if args.algorithm == "auto":
-        # the library's default: folded maps when every shell has odd L, else separable
-        args.algorithm = "folded" if all(s[3] % 2 == 1 for s in w.shells) else "separable"
+        args.algorithm = "folded"          # the library's default
     else:
         gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
                                   "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
@@ -567,8 +566,8 @@ def run_dp5(args, w):
 
 def run_families(args):
     """The paper's benchmark grid families (Sec. 3.4) on four Kerr shells:
-    SingleBH k = 0..8 (odd L: folded maps) and BBH k = 0..8 (even L:
-    separable maps).  Per member: the derivative step (radial + angular maps,
+    SingleBH k = 0..8 (odd L) and BBH k = 0..8 (even L), all with the folded
+    angular maps.  Per member: the derivative step (radial + angular maps,
     the paper's Differentiator), the full RHS and the RK4 step, timed with CUDA
     events after warm-up; the paper's dense-matrix Differentiator flop count
     beside the library's own count."""
@@ -620,7 +619,7 @@ def run_families(args):
             n_r, L = workloads.grid_family_resolution(family, k)
             nth, nph = L + 1, 2 * (L + 1)
             _, F_dense = costmodel.i1s2_differentiator(50, n_r, nth, nph)
-            alg = "folded" if L % 2 == 1 else "separable"
+            alg = "folded"
             F_lib = (costmodel.radial_flops(w.shells) + costmodel.family_flops("angular", w.shells, alg)) / 4
             members.append(dict(family=family, k=k, n_r=n_r, n_theta=nth, n_phi=nph, points=pts,
                                 algorithm=alg, deriv_ms=d_ms, rhs_ms=r_ms, rk4_step_ms=s_ms,

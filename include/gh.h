@@ -262,9 +262,10 @@ long long gh_launch_count(const gh_domain* dom);
  * GH_ALG_SEPARABLE: the same linear maps factorised as a phi DFT, one
  *   N_theta x N_theta Legendre map per Fourier mode, and an inverse DFT; equal
  *   to the dense maps up to rounding, with far fewer flops.
- * GH_ALG_SEPARABLE_FOLDED (default when every shell has odd L): the separable
- *   maps with the cos/sin symmetries of the uniform phi grid and the
- *   equatorial parity of Pbar_lm folded out (about 3x fewer flops again). */
+ * GH_ALG_SEPARABLE_FOLDED (default): the separable maps with the cos/sin
+ *   symmetries of the uniform phi grid and the equatorial parity of Pbar_lm
+ *   folded out (about 3x fewer flops again); any L (odd N_theta: the equator
+ *   ring is its own mirror; N_phi % 4 == 2: no quarter point is). */
 enum { GH_ALG_DENSE = 0, GH_ALG_SEPARABLE = 1, GH_ALG_SEPARABLE_FOLDED = 2 };
 gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
 

@@ -109,20 +109,21 @@ POINTWISE_FLOPS_PER_POINT = 4046
 
 def fold_angular_flops(shells, K=None, two=True):
     """FP64 flops of one folded separable launch (fold_angular_kernel), per
-    (r, field) row: fold 8 (N_phi/4) N_theta; phase A 2 N_theta M W + N_theta M;
-    phase B n_out M half (4 half + 5); phase C n_out N_theta W (2 M + 8), with
-    W = N_phi/4 + 1, half = N_theta/2, M = 2K+1."""
+    (r, field) row: fold 8 (W - 1) N_theta; phase A half M (4 W + 2) plus
+    (hs - half) M 2 W for an odd N_theta's equator ring; phase B
+    n_out M hs (4 hs + 5); phase C n_out N_theta W (2 M + 8), with
+    W = N_phi/4 + 1 (N_phi % 4 == 0) or (N_phi + 2)/4, half = floor(N_theta/2),
+    hs = ceil(N_theta/2), M = 2K+1."""
     f = 0
     n_out = 2 if two else 1
     for sh in shells:
         n_r, nth, nph, na = _shell_dims(sh)
         k = sh[3] if K is None else K
         M = 2 * k + 1
-        N4 = nph // 4
-        W = N4 + 1
-        half = nth // 2
-        per_row = (8 * N4 * nth + 2 * nth * M * W + nth * M + n_out * M * half * (4 * half + 5)
-                   + n_out * nth * W * (2 * M + 8))
+        W = nph // 4 + 1 if nph % 4 == 0 else (nph + 2) // 4
+        half, hs = nth // 2, (nth + 1) // 2
+        per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W
+                   + n_out * M * hs * (4 * hs + 5) + n_out * nth * W * (2 * M + 8))
         f += 50 * n_r * per_row
     return f
 

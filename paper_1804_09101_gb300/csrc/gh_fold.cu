@@ -6,10 +6,12 @@
 //  * phi DFT: cos(m phi_k) and sin(m phi_k) are even/odd under k <-> N - k and
 //    (-1)^m even/odd under k <-> N/2 - k, so each ring is folded into four
 //    quarter-length vectors and every coefficient is a dot product of length
-//    N/4 + 1 (a quarter of the dense DFT);
+//    W = floor(N/4) + 1 (a quarter of the dense DFT; for N % 4 == 2 no point is
+//    its own quarter mirror and W = (N + 2)/4);
 //  * Legendre maps: on symmetric Gauss-Legendre nodes Pbar_lm has parity
 //    (-1)^{l+m} about the equator (d/dtheta flips it), so each map acts on the
-//    symmetric and antisymmetric halves with half-size matrices;
+//    symmetric and antisymmetric halves with half-size matrices (odd N_theta:
+//    the equator ring belongs to the symmetric half and is its own mirror);
 //  * inverse DFT: the same foldings produce four output points per quarter-ring
 //    sum.
 // Per (r, field) row: about 2 (N_theta M (N/4+1) + n_out M N_theta N_theta/2 +
@@ -42,7 +44,8 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   const ShellDev& sh = shells[s];
   const FoldPlan& P = TWO ? sh.fd : sh.ff;
   const int nth = sh.nth, nph = sh.nph, na = sh.na;
-  const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = N4 + 1, N2 = nph / 2;
+  const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = P.W, hs = P.hs, N2 = nph / 2;
+  const bool qself = P.qself != 0;
   constexpr int NO = TWO ? 2 : 1;
   const int T = blockDim.x;
   const int rows = NF * sh.n_r;
@@ -53,7 +56,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   double* U = sm;                                   // [RB][na]
   double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
   double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
-  double* AB = sm + (size_t)RB * r1;                // [RB][M][nth]: s (half) then t (half)
+  double* AB = sm + (size_t)RB * r1;                // [RB][M][2 hs]: s (hs) then t (hs)
   const long long gbase = sh.off + (long long)row0 * na;
   for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
   __syncthreads();
@@ -65,7 +68,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     double* f = F + (size_t)rj * 4 * W;
     auto ev = [&](int kk) { return (kk == 0 || kk == N2) ? ring[kk] : ring[kk] + ring[nph - kk]; };
     auto od = [&](int kk) { return (kk == 0 || kk == N2) ? 0.0 : ring[kk] - ring[nph - kk]; };
-    if (k < N4) {
+    if (!(qself && k == N4)) {
       const double e1 = ev(k), e2 = ev(N2 - k), o1 = od(k), o2 = od(N2 - k);
       f[k] = e1 + e2;
       f[W + k] = e1 - e2;
@@ -80,63 +83,72 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   }
   __syncthreads();
   // phase A: Fourier coefficient of mode for rings j and N_theta-1-j, stored as
-  // their sum (symmetric part s) and difference (antisymmetric part t)
-  for (int o = threadIdx.x; o < nr * half * M; o += T) {
+  // their sum (symmetric part s) and difference (antisymmetric part t); the
+  // equator ring of an odd N_theta is symmetric (s = its coefficient, t = 0)
+  for (int o = threadIdx.x; o < nr * hs * M; o += T) {
     const int mode = o % M;
     const int t = o / M;
-    const int jh = t % half;
-    const int rr = t / half;
+    const int jh = t % hs;
+    const int rr = t / hs;
     const bool cosm = mode <= K;
     const int m = cosm ? mode : mode - K;
     const int q = cosm ? (m % 2 == 0 ? 0 : 1) : (m % 2 == 1 ? 2 : 3);
     const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
     const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
-    const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
-    double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
-    for (int k = 1; k < W; ++k) {
-      const double tv = __ldg(tab + k);
-      c1 = fma(f1[k], tv, c1);
-      c2 = fma(f2[k], tv, c2);
+    double* ab = AB + ((size_t)rr * M + mode) * 2 * hs;
+    if (jh < half) {
+      const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
+      double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
+      for (int k = 1; k < W; ++k) {
+        const double tv = __ldg(tab + k);
+        c1 = fma(f1[k], tv, c1);
+        c2 = fma(f2[k], tv, c2);
+      }
+      ab[jh] = c1 + c2;
+      ab[hs + jh] = c1 - c2;
+    } else {
+      double c1 = f1[0] * __ldg(tab);
+      for (int k = 1; k < W; ++k) c1 = fma(f1[k], __ldg(tab + k), c1);
+      ab[jh] = c1;
+      ab[hs + jh] = 0.0;
     }
-    double* ab = AB + ((size_t)rr * M + mode) * nth;
-    ab[jh] = c1 + c2;
-    ab[half + jh] = c1 - c2;
   }
   __syncthreads();
   // phase B: half-size Legendre maps (tables carry the synthesis factors)
   const unsigned long long sbit = 0x8000000000000000ULL;
-  for (int o = threadIdx.x; o < nr * M * half; o += T) {
-    const int j = o % half;
-    const int t = o / half;
+  for (int o = threadIdx.x; o < nr * M * hs; o += T) {
+    const int j = o % hs;
+    const int t = o / hs;
     const int mode = t % M;
     const int rr = t / M;
     const bool cosm = mode <= K;
     const int m = cosm ? mode : mode - K;
-    const double* ab = AB + ((size_t)rr * M + mode) * nth;
+    const double* ab = AB + ((size_t)rr * M + mode) * 2 * hs;
     double Sv[2], Tv[2];
     {
-      const size_t mo = (size_t)m * half * half + j;
+      const size_t mo = (size_t)m * hs * hs + j;
       const double* Q0s = P.Q0s + mo;
       const double* Q0t = P.Q0t + mo;
       const double* Q1s = TWO ? P.Q1s + mo : nullptr;
       const double* Q1t = TWO ? P.Q1t + mo : nullptr;
-      const double sv0 = ab[0], tv0 = ab[half];
+      const double sv0 = ab[0], tv0 = ab[hs];
       Sv[0] = __ldg(Q0s) * sv0;
       Tv[0] = __ldg(Q0t) * tv0;
       if (TWO) {
         Sv[1] = __ldg(Q1s) * sv0;
         Tv[1] = __ldg(Q1t) * tv0;
       }
-      for (int jp = 1; jp < half; ++jp) {
-        const double sv = ab[jp], tv = ab[half + jp];
-        Sv[0] = fma(__ldg(Q0s + jp * half), sv, Sv[0]);
-        Tv[0] = fma(__ldg(Q0t + jp * half), tv, Tv[0]);
+      for (int jp = 1; jp < hs; ++jp) {
+        const double sv = ab[jp], tv = ab[hs + jp];
+        Sv[0] = fma(__ldg(Q0s + jp * hs), sv, Sv[0]);
+        Tv[0] = fma(__ldg(Q0t + jp * hs), tv, Tv[0]);
         if (TWO) {
-          Sv[1] = fma(__ldg(Q1s + jp * half), sv, Sv[1]);
-          Tv[1] = fma(__ldg(Q1t + jp * half), tv, Tv[1]);
+          Sv[1] = fma(__ldg(Q1s + jp * hs), sv, Sv[1]);
+          Tv[1] = fma(__ldg(Q1t + jp * hs), tv, Tv[1]);
         }
       }
     }
+    const bool eq = (j >= half);            // the equator ring of an odd N_theta
 #pragma unroll
     for (int o2 = 0; o2 < NO; ++o2) {
       // parity of the output about the equator
@@ -150,7 +162,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
           if (m == 0) {
             double* c = OUT + (size_t)RB * nth * M + (size_t)rr * nth * M;
             c[(size_t)j * M] = 0.0;
-            c[(size_t)(nth - 1 - j) * M] = 0.0;
+            if (!eq) c[(size_t)(nth - 1 - j) * M] = 0.0;
             continue;
           }
           slot = K + m;
@@ -159,10 +171,10 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
           slot = m;
         }
       }
-      const double y1 = Sv[o2] + Tv[o2], y2 = Sv[o2] - Tv[o2];
+      const double y1 = Sv[o2] + Tv[o2];
       double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rr * nth * M;
       c[(size_t)j * M + slot] = flip_sign(y1, flip);
-      c[(size_t)(nth - 1 - j) * M + slot] = flip_sign(y2, flip ^ par);
+      if (!eq) c[(size_t)(nth - 1 - j) * M + slot] = flip_sign(Sv[o2] - Tv[o2], flip ^ par);
     }
   }
   __syncthreads();
@@ -194,7 +206,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     if (k == 0) {
       dst[0] = Ek + Ok;
       dst[N2] = Eh + Oh;
-    } else if (k == N4) {
+    } else if (qself && k == N4) {
       dst[N4] = Ek + Ok;
       dst[nph - N4] = Ek - Ok;
     } else {

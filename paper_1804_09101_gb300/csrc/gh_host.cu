@@ -330,20 +330,25 @@ int sep_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
 
 // Folded plan (see fold_angular_kernel).
 struct FoldHost {
-  int K, M, N4, half;
+  int K, M, N4, half, W, hs, qself;
   std::vector<double> Tc, Ts, Q0s, Q0t, Q1s, Q1t;
   double s0, s1;
 };
 
-bool fold_applicable(const AngularGrid& g) { return g.nph % 4 == 0 && g.nth % 2 == 0; }
+// The phi grid has N_phi = 2(L+1) points (always even) and the Gauss-Legendre
+// theta nodes are symmetric, so every shell can be folded.
+bool fold_applicable(const AngularGrid& g) { return g.nph % 2 == 0; }
 
 FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
   FoldHost h;
   h.K = K;
   h.M = 2 * K + 1;
   h.N4 = g.nph / 4;
+  h.qself = (g.nph % 4 == 0) ? 1 : 0;
+  h.W = h.qself ? h.N4 + 1 : (g.nph + 2) / 4;
   h.half = g.nth / 2;
-  const int W = h.N4 + 1, nth = g.nth, half = h.half, Wl = g.L + 1;
+  h.hs = (g.nth + 1) / 2;
+  const int W = h.W, nth = g.nth, half = h.half, hs = h.hs, Wl = g.L + 1;
   h.Tc.assign((size_t)(K + 1) * W, 0.0);
   h.Ts.assign((size_t)(K + 1) * W, 0.0);
   for (int m = 0; m <= K; ++m)
@@ -358,8 +363,8 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
   // map that feeds d/dphi
   auto cfac = [&](int m) { return (m == 0 ? 1.0 : 2.0) * 2.0 * kPi / g.nph; };
   auto build = [&](bool dtheta, bool mscale, std::vector<double>& Qs, std::vector<double>& Qt) {
-    Qs.assign((size_t)(K + 1) * half * half, 0.0);
-    Qt.assign((size_t)(K + 1) * half * half, 0.0);
+    Qs.assign((size_t)(K + 1) * hs * hs, 0.0);
+    Qt.assign((size_t)(K + 1) * hs * hs, 0.0);
     std::vector<double> Q((size_t)nth * nth);
     for (int m = 0; m <= K; ++m) {
       for (int jo = 0; jo < nth; ++jo)
@@ -372,11 +377,22 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
           Q[(size_t)jo * nth + ji] = acc * g.wgl[ji];
         }
       const double f = (mscale ? (double)m : 1.0) * cfac(m);
-      for (int ji = 0; ji < half; ++ji)
-        for (int jo = 0; jo < half; ++jo) {
-          const double q1 = Q[(size_t)jo * nth + ji], q2 = Q[(size_t)jo * nth + (nth - 1 - ji)];
-          Qs[((size_t)m * half + ji) * half + jo] = f * (0.5 * (q1 + q2));
-          Qt[((size_t)m * half + ji) * half + jo] = f * (0.5 * (q1 - q2));
+      // inputs: s_ji = in_ji + in_{nth-1-ji}, t_ji = in_ji - in_{nth-1-ji} (ji < half);
+      // an odd N_theta's equator ring is s_eq = in_eq, t_eq = 0.  Outputs jo < hs
+      // (jo = half: the equator).
+      for (int ji = 0; ji < hs; ++ji)
+        for (int jo = 0; jo < hs; ++jo) {
+          double qs, qt;
+          if (ji < half) {
+            const double q1 = Q[(size_t)jo * nth + ji], q2 = Q[(size_t)jo * nth + (nth - 1 - ji)];
+            qs = 0.5 * (q1 + q2);
+            qt = 0.5 * (q1 - q2);
+          } else {
+            qs = Q[(size_t)jo * nth + ji];
+            qt = 0.0;
+          }
+          Qs[((size_t)m * hs + ji) * hs + jo] = f * qs;
+          Qt[((size_t)m * hs + ji) * hs + jo] = f * qt;
         }
     }
   };
@@ -391,7 +407,8 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
 // quarter folds (reused for the synthesis coefficients) plus the Fourier
 // coefficients of the half-rings.
 size_t fold_row_doubles(int na, int nth, int W, int M, int n_out) {
-  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + (size_t)M * nth;
+  const size_t ab = (size_t)M * 2 * (size_t)((nth + 1) / 2);
+  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + ab;
 }
 
 int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int n_rows, int budget_bytes) {
@@ -448,7 +465,7 @@ cudaError_t fold_build_maps(gh_domain* d) {
   for (int s = 0; s < n_shells; ++s) {
     gh::ShellDev& sh = d->shells_h[s];
     const int rows = gh::NF * sh.n_r;
-    const int W = sh.fd.N4 + 1;
+    const int W = sh.fd.W;
     sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, rows, d->fd_budget);
     fb2[s] = nfd;
     nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
@@ -814,6 +831,9 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
           P.M = f.M;
           P.N4 = f.N4;
           P.half = f.half;
+          P.W = f.W;
+          P.hs = f.hs;
+          P.qself = f.qself;
           P.two = deriv ? 1 : 0;
           P.sigma0 = f.s0;
           P.sigma1 = f.s1;
@@ -1370,7 +1390,7 @@ gh_status gh_set_algorithm(gh_domain* d, int algorithm) {
   if (!d || (algorithm != GH_ALG_DENSE && algorithm != GH_ALG_SEPARABLE && algorithm != GH_ALG_SEPARABLE_FOLDED))
     return fail(d, GH_EINVAL, "algorithm must be GH_ALG_DENSE, GH_ALG_SEPARABLE or GH_ALG_SEPARABLE_FOLDED");
   if (algorithm == GH_ALG_SEPARABLE_FOLDED && !d->fold_ok)
-    return fail(d, GH_EINVAL, "the folded maps need N_phi % 4 == 0 and even N_theta (odd L) on every shell");
+    return fail(d, GH_EINVAL, "the folded maps are not available on this domain");
   if (algorithm == GH_ALG_DENSE) {
     GH_CUDA(d, cudaStreamSynchronize(d->stream));
     if (gh_status st = build_dense(d)) return st;

@@ -64,11 +64,13 @@ struct SepAdjPlan {
 // (half-size matrices on the symmetric and antisymmetric parts).  Needs
 // N_phi % 4 == 0 and N_theta even (odd L).
 struct FoldPlan {
-  int K, M, N4, half;           // highest m, 2K+1 modes, N_phi/4, N_theta/2
+  int K, M, N4, half;           // highest m, 2K+1 modes, floor(N_phi/4), floor(N_theta/2)
+  int W, hs;                    // quarter-ring points, symmetric half-ring size ceil(N_theta/2)
+  int qself;                    // 1 if N_phi % 4 == 0 (the point N_phi/4 is its own mirror)
   int rows_per_cta, two;        // rows per block; 2 outputs (derivatives) or 1 (filter)
-  const double* Tc;             // [K+1][N4+1] cos(m phi_k)
-  const double* Ts;             // [K+1][N4+1] sin(m phi_k)
-  // [K+1][half][half] (transposed: [m][j_in][j_out]) half-size Legendre maps,
+  const double* Tc;             // [K+1][W] cos(m phi_k)
+  const double* Ts;             // [K+1][W] sin(m phi_k)
+  // [K+1][hs][hs] (transposed: [m][j_in][j_out]) half-size Legendre maps,
   // symmetric (s) and antisymmetric (t) parts, scaled by the synthesis factor
   // of mode m: c_m = (m ? 2 : 1) 2 pi / N_phi for output 0, m c_m for output 1
   const double* Q0s;

@@ -53,7 +53,7 @@ def w_pi_modes():
 
 
 def w_even_L():
-    # even L: N_phi % 4 != 0, so the default falls back to the unfolded separable maps
+    # even L: odd N_theta (an equator ring) and N_phi % 4 == 2 (no quarter point)
     return workloads.Workload(name="even_L", shells=[(1.6, 3.0, 7, 6), (3.0, 5.0, 7, 6)], M=1.0, chi=0.4,
                               radial_filter_on=True, sh_keep_l=4, dt=0.005, seed=21, noise_amp=1e-7)
 
@@ -127,8 +127,6 @@ ALGS = ["separable", "dense", "folded"]
 def test_cartesian_derivatives(case, alg):
     gh = _gh()
     w, odom, u0 = case
-    if alg == "folded" and any(L % 2 == 0 for (_, _, _, L) in w.shells):
-        pytest.skip("folded maps need odd L")
     dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     du = torch.zeros(3 * dom.state_size, dtype=torch.float64, device="cuda")
@@ -144,8 +142,6 @@ def test_cartesian_derivatives(case, alg):
 def test_rhs(case, alg):
     gh = _gh()
     w, odom, u0 = case
-    if alg == "folded" and any(L % 2 == 0 for (_, _, _, L) in w.shells):
-        pytest.skip("folded maps need odd L")
     dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     k = dom.new_state()
@@ -174,8 +170,6 @@ def test_filters(case, alg):
     w, odom, u0 = case
     if not (w.radial_filter_on or w.sh_keep_l >= 0):
         pytest.skip("workload has no filter")
-    if alg == "folded" and any(L % 2 == 0 for (_, _, _, L) in w.shells):
-        pytest.skip("folded maps need odd L")
     dom = gpu_domain(w, odom, alg)
     u = to_dev(flat(u0))
     gh.gh_apply_filters(dom, u, dom.new_work())
@@ -186,7 +180,9 @@ def test_filters(case, alg):
 @pytest.mark.parametrize("name,steps,alg", [("schwarzschild", 20, "separable"), ("kerr2", 3, "separable"),
                                             ("ragged", 2, "separable"), ("minimal", 5, "separable"),
                                             ("kerr2", 2, "dense"), ("kerr2", 3, "folded"),
-                                            ("schwarzschild", 5, "folded"), ("paper_singlebh", 2, "separable")])
+                                            ("schwarzschild", 5, "folded"), ("paper_singlebh", 2, "separable"),
+                                            ("paper_singlebh", 2, "folded"), ("even_L", 3, "folded"),
+                                            ("bbh_k1", 2, "folded")])
 def test_rk4_steps(name, steps, alg):
     gh = _gh()
     w = CASES[name]()
