@@ -302,21 +302,27 @@ gh_status gh_dp5_step(gh_domain* dom, double dt, double rtol, double atol, doubl
 /* Work-schedule autotuner.  The schedule is how the radial and folded angular
  * maps split their work (the paper has no counterpart: its traced-matrix
  * products run as library GEMMs, Sec. 3.4); it never changes the arithmetic of
- * any output, so every schedule gives bitwise identical results.
+ * any output of the forward maps, so every schedule of sched[0..7] gives
+ * bitwise identical results.
  *   sched[0], sched[1]: radial derivative -- FMA chains per pass (2..4) and
  *     row groups per column (1..4, one grid row each);
  *   sched[2], sched[3]: the same for the radial ExpCheb filter;
  *   sched[4], sched[5]: folded d/dtheta, d/dphi kernel -- threads per block
  *     (32..512, a multiple of 32) and the shared-memory budget per block in
  *     bytes (8 KiB..200 KiB), which sets the rows per block of every shell;
- *   sched[6], sched[7]: the same for the folded SH filter.
+ *   sched[6], sched[7]: the same for the folded SH filter;
+ *   sched[8]: reverse pass of the pointwise algebra (gh_rhs_vjp and the step
+ *     VJPs) with one thread per point (0) or ten, one per symmetric pair (1):
+ *     the pair-split form does ~3x the work with a ~3x shorter serial path per
+ *     thread and wins on small grids (default: 1 up to 8,192 points); not
+ *     timed by gh_autotune.  Results agree to rounding, not bitwise.
  * gh_autotune times every candidate of each map on this domain (CUDA events
  * on the domain's stream, one warm-up and `reps` timed launches each, the
  * domain's own scratch as input and output), keeps the fastest, and
  * synchronises the stream.  gh_set_schedule validates and installs a
  * schedule (GH_EINVAL otherwise).  Both discard a captured RK4 graph
  * (capture again).  n must be at least GH_SCHEDULE_LEN. */
-#define GH_SCHEDULE_LEN 8
+#define GH_SCHEDULE_LEN 9
 gh_status gh_autotune(gh_domain* dom, int reps);
 gh_status gh_get_schedule(const gh_domain* dom, int* sched, int n);
 gh_status gh_set_schedule(gh_domain* dom, const int* sched, int n);

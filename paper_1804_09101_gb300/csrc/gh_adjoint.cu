@@ -9,6 +9,8 @@
 // transposed radial and angular maps (Eq. DifferentiatorI1S2 transposed).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <string>
 #include <vector>
 
@@ -457,6 +459,80 @@ cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {
   return cudaGetLastError();
 }
 
+}  // namespace
+namespace gh {
+
+// Pair-split pointwise reverse pass for small grids: one thread per (point,
+// symmetric pair): one-warp blocks on a grid of (32-point chunk of the forward
+// pointwise kernel) x (pair), so the warps of a chunk spread over the SMs.  Each thread runs the pair-restricted reverse
+// pass (and, MODE 2, its share of the constraint-energy gradient), writes the
+// cotangents of its pair's derivatives in place and its partial field
+// cotangents to ubp[p][state]; adj_pair_reduce_kernel sums the ten partials
+// in a fixed order.
+constexpr int PAIR_PTS = 32;
+template <int MODE>
+__global__ void __launch_bounds__(PAIR_PTS)
+pointwise_adjoint_pair_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                              const double* __restrict__ u, double* dr, double* dth, double* dph,
+                              const double* __restrict__ kb, double* __restrict__ ubp, long long state, double g0,
+                              double g1, double g2, double weight) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + PAIR_PTS - 1) / PAIR_PTS;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * PAIR_PTS + threadIdx.x;
+  const int p = blockIdx.y;
+  if (q >= na) return;
+  const long long base = sh.off + (long long)ir * NF * na + q;
+  double uu[50], ub[50];
+  for (int f = 0; f < NF; ++f) {
+    uu[f] = u[base + (long long)f * na];
+    ub[f] = 0.0;
+  }
+  const int fid[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
+  double dsp[15], kb5[5], dsb15[15];
+  for (int e = 0; e < 5; ++e) {
+    const long long o = base + (long long)fid[e] * na;
+    dsp[3 * e] = dr[o];
+    dsp[3 * e + 1] = dth[o];
+    dsp[3 * e + 2] = dph[o];
+    kb5[e] = kb[o];
+  }
+  const double* gsrc = sh.gauge + (long long)ir * NGAUGE * na + q;
+  double H[4], dH[12];
+  for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
+  for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
+  PointGeom G;
+  point_geom(sh, ir, q, G);
+  point_rhs_vjp_pair(uu, G.J, H, dH, g0, g1, g2, p, dsp, kb5, ub, dsb15);
+  if (MODE == 2) {
+    const int j = q / sh.nph;
+    point_constraint_energy_pair(uu, G.J, H, p, dsp, weight * sh.wr[ir] * sh.wth[j], ub, dsb15);
+  }
+  for (int e = 0; e < 5; ++e) {
+    const long long o = base + (long long)fid[e] * na;
+    dr[o] = dsb15[3 * e];
+    dth[o] = dsb15[3 * e + 1];
+    dph[o] = dsb15[3 * e + 2];
+  }
+  double* out = ubp + (long long)p * state;
+  for (int f = 0; f < NF; ++f) out[base + (long long)f * na] = ub[f];
+}
+
+__global__ void __launch_bounds__(256)
+adj_pair_reduce_kernel(long long state, const double* __restrict__ ubp, double* __restrict__ ubar, int assign) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < state; i += (long long)gridDim.x * blockDim.x) {
+    double acc = ubp[i];
+    for (int p = 1; p < 10; ++p) acc += ubp[(long long)p * state + i];
+    ubar[i] = assign ? acc : ubar[i] + acc;
+  }
+}
+
+}  // namespace gh
+namespace {
+
 // ubar (+)= J(u)^T kb (+ cweight * grad of the constraint energy at u when
 // cweight != 0); assign: overwrite ubar instead of adding; kb is not modified.
 gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar, double cweight = 0.0,
@@ -469,16 +545,41 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
-  if (cweight != 0.0)
-    gh::pointwise_adjoint_kernel<2><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
-        d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
-        d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight, assign ? 1 : 0);
-  else
-    gh::pointwise_adjoint_kernel<0><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
-        d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
-        d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0);
-  d->launches++;
-  GH_ACUDA(d, cudaGetLastError());
+  if (d->adj_pair_split) {
+    // small grid: ten threads per point (one per symmetric pair)
+    if (!d->adj_ubp) {
+      void* p = nullptr;
+      GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * 10 * (size_t)d->state));
+      d->owned.push_back(p);
+      d->adj_ubp = (double*)p;
+    }
+    const dim3 grid(d->pt_blocks, 10);
+    if (cweight != 0.0)
+      gh::pointwise_adjoint_pair_kernel<2><<<grid, gh::PAIR_PTS, 0, d->stream>>>(
+          d->shells_d, d->n_shells, d->pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, d->adj_ubp, d->state,
+          d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight);
+    else
+      gh::pointwise_adjoint_pair_kernel<0><<<grid, gh::PAIR_PTS, 0, d->stream>>>(
+          d->shells_d, d->n_shells, d->pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, d->adj_ubp, d->state,
+          d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+    const long long nb = std::min<long long>((d->state + 255) / 256, 4096);
+    gh::adj_pair_reduce_kernel<<<(unsigned)nb, 256, 0, d->stream>>>(d->state, d->adj_ubp, ubar, assign ? 1 : 0);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+  } else {
+    if (cweight != 0.0)
+      gh::pointwise_adjoint_kernel<2><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+          d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
+          d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight, assign ? 1 : 0);
+    else
+      gh::pointwise_adjoint_kernel<0><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
+          d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
+          d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+  }
   GH_ACUDA(d, derivs_transpose_add(d, ubar));
   return GH_OK;
 }

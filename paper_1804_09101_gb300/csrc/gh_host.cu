@@ -670,7 +670,7 @@ bool schedule_ok(const int* v) {
   auto in = [](int x, int lo, int hi) { return x >= lo && x <= hi; };
   return in(v[0], 2, 4) && in(v[1], 1, 4) && in(v[2], 2, 4) && in(v[3], 1, 4) &&
          in(v[4], 32, 512) && v[4] % 32 == 0 && in(v[5], 8 * 1024, 200 * 1024) &&
-         in(v[6], 32, 512) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024);
+         in(v[6], 32, 512) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024) && in(v[8], 0, 1);
 }
 
 void invalidate_graph(gh_domain* d) {
@@ -960,6 +960,9 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   pb[n_shells] = npb;
   d->rad_blocks = nrb;
   d->pt_blocks = npb;
+  // the pair-split reverse kernel wins while ten threads per point still leave
+  // FP64 units idle or lightly loaded (measured crossover near 10^4 points)
+  d->adj_pair_split = (long long)npb * gh::PT_THREADS <= 8192;
   {
     // default radial row groups: about 12 warps per FP64 unit (4 per SM)
     int dev = 0, sms = 152;
@@ -1404,6 +1407,7 @@ gh_status gh_get_schedule(const gh_domain* d, int* v, int n) {
   if (!d || !v || n < GH_SCHEDULE_LEN) return GH_EINVAL;
   v[0] = d->rad_chains; v[1] = d->rad_groups; v[2] = d->radf_chains; v[3] = d->radf_groups;
   v[4] = d->fd_threads; v[5] = d->fd_budget; v[6] = d->ff_threads; v[7] = d->ff_budget;
+  v[8] = d->adj_pair_split ? 1 : 0;
   return GH_OK;
 }
 
@@ -1413,6 +1417,7 @@ gh_status gh_set_schedule(gh_domain* d, const int* v, int n) {
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   d->rad_chains = v[0]; d->rad_groups = v[1]; d->radf_chains = v[2]; d->radf_groups = v[3];
   d->fd_threads = v[4]; d->fd_budget = v[5]; d->ff_threads = v[6]; d->ff_budget = v[7];
+  d->adj_pair_split = v[8] != 0;
   if (d->fold_ok) GH_CUDA(d, fold_build_maps(d));
   invalidate_graph(d);
   return GH_OK;

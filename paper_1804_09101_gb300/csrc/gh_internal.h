@@ -192,6 +192,10 @@ struct gh_domain {
   double* pert_partial = nullptr; int pert_partial_len = 0;
   // Dormand-Prince step: per-block partial sums of the error norm and the norm
   double* dp_partial = nullptr;
+  // pointwise reverse pass: ten threads per point (one per symmetric pair) on
+  // small grids, partial field cotangents in adj_ubp (10 states, lazily)
+  bool adj_pair_split = false;
+  double* adj_ubp = nullptr;
   // outer boundary condition: 0 freezing, 1 constraint preserving (gh_set_outer_bc)
   int outer_bc = 0;
   double* dp_err = nullptr;

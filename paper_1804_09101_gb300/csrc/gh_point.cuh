@@ -634,4 +634,382 @@ GH_HD inline double point_constraint_energy(const PointIn& in, double w, double 
   return e;
 }
 
+// ---------------------------------------------------------------------------
+// Pair-restricted reverse pass.  The vector-Jacobian product is linear in the
+// output cotangent, so it is the sum over the symmetric pairs p of the
+// products with kb restricted to pair p's five outputs (psi_p, Pi_p, Phi_ip).
+// Each restricted product needs only the forward pieces that pair reads
+// (Wm[.][.][A], Pm[A], Pm[B] of the full pass) and touches only the matching
+// adjoint slices, so ten threads can share one point with short serial paths.
+// Inputs: u[50], dsp[15] (spherical derivatives of psi_p, Pi_p, Phi_0p,
+// Phi_1p, Phi_2p; d = x, theta, phi), kb5[5] (cotangents of pair p's
+// outputs).  Adds to ub[50]; writes the cotangents of dsp to dsb15.
+GH_HD inline void point_rhs_vjp_pair(const double* u, const double J[3][3], const double H[4], const double dH[12],
+                                     double g0, double g1, double g2, int p, const double dsp[15],
+                                     const double kb5[5], double ub[50], double dsb15[15]) {
+  const double* psi = u;
+  const double* Pi = u + 10;
+  const double* Phi = u + 20;
+  const int A = pair_a(p), B = pair_b(p);
+  Split S;
+  point_split(psi, S);
+  const double al = S.alpha;
+  // ---- forward pieces
+  double Gam[40];
+  {
+    double d[40];
+    for (int q = 0; q < 10; ++q) {
+      d[q] = -al * Pi[q] + S.beta_up[0] * Phi[q] + S.beta_up[1] * Phi[10 + q] + S.beta_up[2] * Phi[20 + q];
+      for (int i = 0; i < 3; ++i) d[10 * (1 + i) + q] = Phi[10 * i + q];
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        for (int c = b; c < 4; ++c)
+          Gam[a * 10 + sym_index(b, c)] =
+              0.5 * (d[b * 10 + sym_index(a, c)] + d[c * 10 + sym_index(a, b)] - d[a * 10 + sym_index(b, c)]);
+  }
+  double C[4], PH[4];
+  for (int a = 0; a < 4; ++a) {
+    double acc = 0.0;
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(b, c)] * Gam[a * 10 + sym_index(b, c)];
+    C[a] = H[a] + acc;
+  }
+  for (int dd = 0; dd < 4; ++dd) {
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(c, dd)] * H[c];
+    PH[dd] = acc;
+  }
+  double PmA[16], PmB[16];
+  for (int dd = 0; dd < 4; ++dd)
+    for (int e = 0; e < 4; ++e) {
+      double a1 = 0.0, a2 = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        a1 += S.psi_inv[sym_index(dd, c)] * Gam[A * 10 + sym_index(c, e)];
+        a2 += S.psi_inv[sym_index(dd, c)] * Gam[B * 10 + sym_index(c, e)];
+      }
+      PmA[dd * 4 + e] = a1;
+      PmB[dd * 4 + e] = a2;
+    }
+  double UmA[3][4], WmA[3][4];   // Um[i][d][A], Wm[j][d][A]
+  for (int i = 0; i < 3; ++i)
+    for (int dd = 0; dd < 4; ++dd) {
+      double acc = 0.0;
+      for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(dd, c)] * Phi[i * 10 + sym_index(c, A)];
+      UmA[i][dd] = acc;
+    }
+  for (int j = 0; j < 3; ++j)
+    for (int dd = 0; dd < 4; ++dd)
+      WmA[j][dd] = S.ginv[s3h(0, j)] * UmA[0][dd] + S.ginv[s3h(1, j)] * UmA[1][dd] + S.ginv[s3h(2, j)] * UmA[2][dd];
+  double tPt = 0.0, tC = 0.0, tPi[3] = {0.0, 0.0, 0.0}, tPig[3];
+  for (int c = 0; c < 4; ++c) {
+    tC += S.t_up[c] * C[c];
+    for (int dd = 0; dd < 4; ++dd) tPt += S.t_up[c] * S.t_up[dd] * Pi[sym_index(c, dd)];
+    for (int i = 0; i < 3; ++i) tPi[i] += S.t_up[c] * Pi[sym_index(c, 1 + i)];
+  }
+  for (int j = 0; j < 3; ++j)
+    tPig[j] = tPi[0] * S.ginv[s3h(0, j)] + tPi[1] * S.ginv[s3h(1, j)] + tPi[2] * S.ginv[s3h(2, j)];
+  double tPhit[3], tPhij[3][3], Mik[3][3];
+  for (int i = 0; i < 3; ++i) {
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c)
+      for (int dd = 0; dd < 4; ++dd) acc += S.t_up[c] * S.t_up[dd] * Phi[i * 10 + sym_index(c, dd)];
+    tPhit[i] = acc;
+    for (int j = 0; j < 3; ++j) {
+      double t2 = 0.0;
+      for (int c = 0; c < 4; ++c) t2 += S.t_up[c] * Phi[i * 10 + sym_index(1 + j, c)];
+      tPhij[i][j] = t2;
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k)
+      Mik[i][k] = tPhij[i][0] * S.ginv[s3h(0, k)] + tPhij[i][1] * S.ginv[s3h(1, k)] + tPhij[i][2] * S.ginv[s3h(2, k)];
+  double bs[3], Gs[3][3];
+  for (int dd = 0; dd < 3; ++dd) {
+    bs[dd] = S.beta_up[0] * J[0][dd] + S.beta_up[1] * J[1][dd] + S.beta_up[2] * J[2][dd];
+    for (int i = 0; i < 3; ++i)
+      Gs[i][dd] = S.ginv[s3h(0, i)] * J[0][dd] + S.ginv[s3h(1, i)] * J[1][dd] + S.ginv[s3h(2, i)] * J[2][dd];
+  }
+  // ---- adjoint accumulators
+  double* psib = ub;
+  double* Pib = ub + 10;
+  double* Phib = ub + 20;
+  double alb = 0.0, betab[3] = {0.0, 0.0, 0.0}, ginvb[6] = {0, 0, 0, 0, 0, 0}, tb[4] = {0.0, 0.0, 0.0, 0.0};
+  double pinvb[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double Gamb[40];
+  for (int e = 0; e < 40; ++e) Gamb[e] = 0.0;
+  double Cb[4] = {0.0, 0.0, 0.0, 0.0}, PHb[4] = {0.0, 0.0, 0.0, 0.0};
+  double PmbA[16], PmbB[16], WmbA[3][4];
+  for (int e = 0; e < 16; ++e) PmbA[e] = PmbB[e] = 0.0;
+  for (int j = 0; j < 3; ++j)
+    for (int dd = 0; dd < 4; ++dd) WmbA[j][dd] = 0.0;
+  double tPtb = 0.0, tCb = 0.0, tPigb[3] = {0.0, 0.0, 0.0}, tPhitb[3] = {0.0, 0.0, 0.0};
+  double Mikb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double bsb[3] = {0.0, 0.0, 0.0}, Gsb[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  const double* dpsi = dsp;
+  const double* dPi = dsp + 3;
+  double* dpsib = dsb15;
+  double* dPib = dsb15 + 3;
+  for (int e = 0; e < 15; ++e) dsb15[e] = 0.0;
+  const double kpsi = kb5[0], kPi = kb5[1];
+  // ---- the pair's forward scalars
+  double T1 = 0.0, T2 = 0.0, T3 = 0.0;
+  for (int j = 0; j < 3; ++j)
+    for (int dd = 0; dd < 4; ++dd) T1 += WmA[j][dd] * Phi[j * 10 + sym_index(dd, B)];
+  double pcv[4];
+  for (int c = 0; c < 4; ++c) {
+    double pc = 0.0;
+    for (int dd = 0; dd < 4; ++dd) pc += S.psi_inv[sym_index(c, dd)] * Pi[sym_index(dd, B)];
+    pcv[c] = pc;
+    T2 += Pi[sym_index(c, A)] * pc;
+  }
+  for (int dd = 0; dd < 4; ++dd)
+    for (int e = 0; e < 4; ++e) T3 += PmA[dd * 4 + e] * PmB[e * 4 + dd];
+  const double dAHB = (A > 0 ? dH[4 * (A - 1) + B] : 0.0);
+  const double dBHA = (B > 0 ? dH[4 * (B - 1) + A] : 0.0);
+  double gh_ = 0.0;
+  for (int dd = 0; dd < 4; ++dd) gh_ += PH[dd] * Gam[dd * 10 + p];
+  const double nablaH = 0.5 * (dAHB + dBHA) - gh_;
+  const double damp = (B == 0 ? -al * C[A] : 0.0) + (A == 0 ? -al * C[B] : 0.0) - psi[p] * tC;
+  double tPiPhi = 0.0;
+  for (int j = 0; j < 3; ++j) tPiPhi += tPig[j] * Phi[j * 10 + p];
+  double gdPhi = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double* dPhi = dsp + 6 + 3 * i;
+    gdPhi += Gs[i][0] * dPhi[0] + Gs[i][1] * dPhi[1] + Gs[i][2] * dPhi[2];
+  }
+  // ---- out[p] = (1+g1) bdpsi - al Pi_p - g1 bPhi
+  double bdpsib = (1.0 + g1) * kpsi;
+  alb -= Pi[p] * kpsi;
+  Pib[p] -= al * kpsi;
+  double bPhib = -g1 * kpsi;
+  // ---- out[10+p] = bdPi - al gdPhi + g1 g2 bdpsi + srcPi
+  const double bdPib = kPi;
+  alb -= gdPhi * kPi;
+  const double gdPhib = -al * kPi;
+  bdpsib += g1 * g2 * kPi;
+  const double sPb = kPi;
+  // ---- out[20+10i+p]
+  double cpsib[3], cPib[3];
+  for (int i = 0; i < 3; ++i) {
+    const double kPhi = kb5[2 + i];
+    const double* dPhi = dsp + 6 + 3 * i;
+    double* dPhib = dsb15 + 6 + 3 * i;
+    const double cpsi = J[i][0] * dpsi[0] + J[i][1] * dpsi[1] + J[i][2] * dpsi[2];
+    const double cPi = J[i][0] * dPi[0] + J[i][1] * dPi[1] + J[i][2] * dPi[2];
+    for (int dd = 0; dd < 3; ++dd) {
+      dPhib[dd] += bs[dd] * kPhi;
+      bsb[dd] += dPhi[dd] * kPhi;
+    }
+    alb += (-cPi + g2 * cpsi) * kPhi;
+    cPib[i] = -al * kPhi;
+    cpsib[i] = al * g2 * kPhi;
+    const double mphi = Mik[i][0] * Phi[p] + Mik[i][1] * Phi[10 + p] + Mik[i][2] * Phi[20 + p];
+    alb += (0.5 * tPhit[i] * Pi[p] + mphi - g2 * Phi[i * 10 + p]) * kPhi;
+    tPhitb[i] += 0.5 * al * Pi[p] * kPhi;
+    Pib[p] += 0.5 * al * tPhit[i] * kPhi;
+    for (int k = 0; k < 3; ++k) {
+      Mikb[i][k] += al * Phi[k * 10 + p] * kPhi;
+      Phib[k * 10 + p] += al * Mik[i][k] * kPhi;
+    }
+    Phib[i * 10 + p] -= al * g2 * kPhi;
+  }
+  for (int dd = 0; dd < 3; ++dd) {
+    dpsib[dd] += J[0][dd] * cpsib[0] + J[1][dd] * cpsib[1] + J[2][dd] * cpsib[2];
+    dPib[dd] += J[0][dd] * cPib[0] + J[1][dd] * cPib[1] + J[2][dd] * cPib[2];
+  }
+  for (int dd = 0; dd < 3; ++dd) {
+    dpsib[dd] += bs[dd] * bdpsib;
+    bsb[dd] += dpsi[dd] * bdpsib;
+    dPib[dd] += bs[dd] * bdPib;
+    bsb[dd] += dPi[dd] * bdPib;
+  }
+  for (int i = 0; i < 3; ++i) {
+    const double* dPhi = dsp + 6 + 3 * i;
+    double* dPhib = dsb15 + 6 + 3 * i;
+    for (int dd = 0; dd < 3; ++dd) {
+      dPhib[dd] += Gs[i][dd] * gdPhib;
+      Gsb[i][dd] += dPhi[dd] * gdPhib;
+    }
+  }
+  // ---- srcPi = 2al(T1-T2-T3) - 2al nablaH - 0.5 al tPt Pi_p - al tPiPhi + g0 al damp - g1 g2 bPhi
+  alb += sPb * (2.0 * (T1 - T2 - T3) - 2.0 * nablaH - 0.5 * tPt * Pi[p] - tPiPhi + g0 * damp);
+  const double T1b = 2.0 * al * sPb, T2b = -2.0 * al * sPb, T3b = -2.0 * al * sPb;
+  const double nHb = -2.0 * al * sPb;
+  tPtb += -0.5 * al * Pi[p] * sPb;
+  Pib[p] += -0.5 * al * tPt * sPb;
+  const double tPiPhib = -al * sPb;
+  const double dampb = g0 * al * sPb;
+  bPhib += -g1 * g2 * sPb;
+  for (int j = 0; j < 3; ++j)
+    for (int dd = 0; dd < 4; ++dd) {
+      WmbA[j][dd] += Phi[j * 10 + sym_index(dd, B)] * T1b;
+      Phib[j * 10 + sym_index(dd, B)] += WmA[j][dd] * T1b;
+    }
+  for (int c = 0; c < 4; ++c) {
+    Pib[sym_index(c, A)] += pcv[c] * T2b;
+    const double pcb = Pi[sym_index(c, A)] * T2b;
+    for (int dd = 0; dd < 4; ++dd) {
+      pinvb[sym_index(c, dd)] += Pi[sym_index(dd, B)] * pcb;
+      Pib[sym_index(dd, B)] += S.psi_inv[sym_index(c, dd)] * pcb;
+    }
+  }
+  for (int dd = 0; dd < 4; ++dd)
+    for (int e = 0; e < 4; ++e) {
+      PmbA[dd * 4 + e] += PmB[e * 4 + dd] * T3b;
+      PmbB[e * 4 + dd] += PmA[dd * 4 + e] * T3b;
+    }
+  for (int dd = 0; dd < 4; ++dd) {
+    PHb[dd] -= Gam[dd * 10 + p] * nHb;
+    Gamb[dd * 10 + p] -= PH[dd] * nHb;
+  }
+  if (B == 0) {
+    alb -= C[A] * dampb;
+    Cb[A] -= al * dampb;
+  }
+  if (A == 0) {
+    alb -= C[B] * dampb;
+    Cb[B] -= al * dampb;
+  }
+  psib[p] -= tC * dampb;
+  tCb -= psi[p] * dampb;
+  for (int j = 0; j < 3; ++j) {
+    tPigb[j] += Phi[j * 10 + p] * tPiPhib;
+    Phib[j * 10 + p] += tPig[j] * tPiPhib + S.beta_up[j] * bPhib;
+    betab[j] += Phi[j * 10 + p] * bPhib;
+  }
+  // ---- reverse of the pair-independent pieces (restricted where possible)
+  for (int dd = 0; dd < 3; ++dd) {
+    for (int k = 0; k < 3; ++k) betab[k] += J[k][dd] * bsb[dd];
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) ginvb[s3h(k, i)] += J[k][dd] * Gsb[i][dd];
+  }
+  for (int i = 0; i < 3; ++i) {
+    double tPhijb[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 3; ++j) {
+        tPhijb[j] += S.ginv[s3h(j, k)] * Mikb[i][k];
+        ginvb[s3h(j, k)] += tPhij[i][j] * Mikb[i][k];
+      }
+    for (int j = 0; j < 3; ++j)
+      for (int c = 0; c < 4; ++c) {
+        tb[c] += Phi[i * 10 + sym_index(1 + j, c)] * tPhijb[j];
+        Phib[i * 10 + sym_index(1 + j, c)] += S.t_up[c] * tPhijb[j];
+      }
+    for (int c = 0; c < 4; ++c)
+      for (int dd = 0; dd < 4; ++dd) {
+        const double ph = Phi[i * 10 + sym_index(c, dd)];
+        tb[c] += S.t_up[dd] * ph * tPhitb[i];
+        tb[dd] += S.t_up[c] * ph * tPhitb[i];
+        Phib[i * 10 + sym_index(c, dd)] += S.t_up[c] * S.t_up[dd] * tPhitb[i];
+      }
+  }
+  // Wm[j][d][A] = sum_i ginv(i,j) Um[i][d][A] ; Um[i][d][A] = sum_c psi_inv(d,c) Phi_i(c,A)
+  for (int i = 0; i < 3; ++i) {
+    double UmbA[4];
+    for (int dd = 0; dd < 4; ++dd) {
+      UmbA[dd] = S.ginv[s3h(i, 0)] * WmbA[0][dd] + S.ginv[s3h(i, 1)] * WmbA[1][dd] + S.ginv[s3h(i, 2)] * WmbA[2][dd];
+      for (int j = 0; j < 3; ++j) ginvb[s3h(i, j)] += UmA[i][dd] * WmbA[j][dd];
+    }
+    for (int dd = 0; dd < 4; ++dd)
+      for (int c = 0; c < 4; ++c) {
+        pinvb[sym_index(dd, c)] += Phi[i * 10 + sym_index(c, A)] * UmbA[dd];
+        Phib[i * 10 + sym_index(c, A)] += S.psi_inv[sym_index(dd, c)] * UmbA[dd];
+      }
+  }
+  // Pm[a][d][e] = sum_c psi_inv(d,c) Gam[a](c,e) for a = A and a = B
+  for (int w = 0; w < 2; ++w) {
+    const int a = (w == 0) ? A : B;
+    const double* Pb = (w == 0) ? PmbA : PmbB;
+    for (int dd = 0; dd < 4; ++dd)
+      for (int e = 0; e < 4; ++e)
+        for (int c = 0; c < 4; ++c) {
+          pinvb[sym_index(dd, c)] += Gam[a * 10 + sym_index(c, e)] * Pb[dd * 4 + e];
+          Gamb[a * 10 + sym_index(c, e)] += S.psi_inv[sym_index(dd, c)] * Pb[dd * 4 + e];
+        }
+  }
+  for (int dd = 0; dd < 4; ++dd)
+    for (int c = 0; c < 4; ++c) pinvb[sym_index(c, dd)] += H[c] * PHb[dd];
+  double tPib[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i < 3; ++i) {
+      tPib[i] += S.ginv[s3h(i, j)] * tPigb[j];
+      ginvb[s3h(i, j)] += tPi[i] * tPigb[j];
+    }
+  for (int c = 0; c < 4; ++c) {
+    for (int i = 0; i < 3; ++i) {
+      tb[c] += Pi[sym_index(c, 1 + i)] * tPib[i];
+      Pib[sym_index(c, 1 + i)] += S.t_up[c] * tPib[i];
+    }
+    for (int dd = 0; dd < 4; ++dd) {
+      const double pv = Pi[sym_index(c, dd)];
+      tb[c] += S.t_up[dd] * pv * tPtb;
+      tb[dd] += S.t_up[c] * pv * tPtb;
+      Pib[sym_index(c, dd)] += S.t_up[c] * S.t_up[dd] * tPtb;
+    }
+    tb[c] += C[c] * tCb;
+    Cb[c] += S.t_up[c] * tCb;
+  }
+  gamma_split_reverse(psi, Pi, Phi, S, Gam, Cb, Gamb, alb, betab, ginvb, tb, pinvb, psib, Pib, Phib);
+}
+
+// Constraint-energy gradient restricted to pair p: the C_iab and C_ijab terms
+// of pair p (which read only pair p's derivatives) and, for p == 0, the C_a
+// term.  Adds w * de/d(inputs) to ub[50] and dsb15 (pair p's derivatives).
+GH_HD inline void point_constraint_energy_pair(const double* u, const double J[3][3], const double H[4], int p,
+                                               const double dsp[15], double w, double ub[50], double dsb15[15]) {
+  const double* Phi = u + 20;
+  double cpsi[3], cPhi[3][3];   // cPhi[j][i] = d_i Phi_jp
+  for (int i = 0; i < 3; ++i) {
+    cpsi[i] = J[i][0] * dsp[0] + J[i][1] * dsp[1] + J[i][2] * dsp[2];
+    for (int j = 0; j < 3; ++j)
+      cPhi[j][i] = J[i][0] * dsp[6 + 3 * j] + J[i][1] * dsp[7 + 3 * j] + J[i][2] * dsp[8 + 3 * j];
+  }
+  double cpsib[3] = {0.0, 0.0, 0.0}, cPhib[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int i = 0; i < 3; ++i) {
+    const double c3 = cpsi[i] - Phi[i * 10 + p];
+    cpsib[i] += 2.0 * w * c3;
+    ub[20 + i * 10 + p] -= 2.0 * w * c3;
+  }
+  const int qi[3] = {0, 0, 1}, qj[3] = {1, 2, 2};
+  for (int q = 0; q < 3; ++q) {
+    const int i = qi[q], j = qj[q];
+    const double c4 = cPhi[j][i] - cPhi[i][j];
+    cPhib[j][i] += 2.0 * w * c4;
+    cPhib[i][j] -= 2.0 * w * c4;
+  }
+  for (int dd = 0; dd < 3; ++dd) {
+    dsb15[dd] += J[0][dd] * cpsib[0] + J[1][dd] * cpsib[1] + J[2][dd] * cpsib[2];
+    for (int j = 0; j < 3; ++j)
+      dsb15[6 + 3 * j + dd] += J[0][dd] * cPhib[j][0] + J[1][dd] * cPhib[j][1] + J[2][dd] * cPhib[j][2];
+  }
+  if (p != 0) return;
+  const double* psi = u;
+  const double* Pi = u + 10;
+  Split S;
+  point_split(psi, S);
+  double d[40], Gam[40];
+  for (int q = 0; q < 10; ++q) {
+    d[q] = -S.alpha * Pi[q] + S.beta_up[0] * Phi[q] + S.beta_up[1] * Phi[10 + q] + S.beta_up[2] * Phi[20 + q];
+    for (int i = 0; i < 3; ++i) d[10 * (1 + i) + q] = Phi[10 * i + q];
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = b; c < 4; ++c)
+        Gam[a * 10 + sym_index(b, c)] =
+            0.5 * (d[b * 10 + sym_index(a, c)] + d[c * 10 + sym_index(a, b)] - d[a * 10 + sym_index(b, c)]);
+  double Cb[4];
+  for (int a = 0; a < 4; ++a) {
+    double acc = 0.0;
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c) acc += S.psi_inv[sym_index(b, c)] * Gam[a * 10 + sym_index(b, c)];
+    Cb[a] = 2.0 * w * (H[a] + acc);
+  }
+  double Gamb[40];
+  for (int q = 0; q < 40; ++q) Gamb[q] = 0.0;
+  double alb = 0.0, betab[3] = {0, 0, 0}, ginvb[6] = {0, 0, 0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
+  double pinvb[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  gamma_split_reverse(psi, Pi, Phi, S, Gam, Cb, Gamb, alb, betab, ginvb, tb, pinvb, ub, ub + 10, ub + 20);
+}
+
 }  // namespace gh

@@ -301,9 +301,10 @@ def new_dp5_work(dom):
     return torch.zeros(dom.dp5_work_size, dtype=torch.float64, device="cuda")
 
 
-SCHEDULE_LEN = 8
+SCHEDULE_LEN = 9
 SCHEDULE_KEYS = ("radial_chains", "radial_groups", "radial_filter_chains", "radial_filter_groups",
-                 "fold_deriv_threads", "fold_deriv_budget", "fold_filter_threads", "fold_filter_budget")
+                 "fold_deriv_threads", "fold_deriv_budget", "fold_filter_threads", "fold_filter_budget",
+                 "adjoint_pair_split")
 
 
 def gh_autotune(dom, reps=5):
@@ -320,7 +321,10 @@ def gh_get_schedule(dom):
 
 
 def gh_set_schedule(dom, sched):
-    v = (ctypes.c_int * SCHEDULE_LEN)(*[int(sched[k]) for k in SCHEDULE_KEYS])
+    """Install a schedule; keys left out keep their current values."""
+    cur = gh_get_schedule(dom)
+    cur.update(sched)
+    v = (ctypes.c_int * SCHEDULE_LEN)(*[int(cur[k]) for k in SCHEDULE_KEYS])
     dom._stream()
     dom._check(_lib.gh_set_schedule(dom.handle, v, SCHEDULE_LEN))
 

@@ -75,10 +75,10 @@ def test_injected_allocation_fault_returns_enomem_without_touching_the_gpu(lib):
 
 
 def test_schedule_entry_points_reject_bad_arguments_on_the_host(lib):
-    v = (ctypes.c_int * 8)(2, 1, 2, 1, 128, 49152, 128, 49152)
+    v = (ctypes.c_int * 9)(2, 1, 2, 1, 128, 49152, 128, 49152, 0)
     lib.gh_get_schedule.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     lib.gh_set_schedule.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     lib.gh_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int]
-    assert lib.gh_get_schedule(None, v, 8) == 1          # GH_EINVAL: no domain
-    assert lib.gh_set_schedule(None, v, 8) == 1
+    assert lib.gh_get_schedule(None, v, 9) == 1          # GH_EINVAL: no domain
+    assert lib.gh_set_schedule(None, v, 9) == 1
     assert lib.gh_autotune(None, 3) == 1

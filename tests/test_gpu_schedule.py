@@ -47,10 +47,10 @@ def test_autotune_keeps_results_bitwise():
 
 
 @pytest.mark.parametrize("sched", [
-    (2, 1, 2, 1, 128, 49152, 128, 49152),
-    (3, 2, 4, 3, 32, 8192, 64, 8192),
-    (4, 4, 3, 2, 512, 200 * 1024, 256, 112 * 1024),
-    (2, 3, 2, 4, 96, 24576, 480, 65536),
+    (2, 1, 2, 1, 128, 49152, 128, 49152, 1),
+    (3, 2, 4, 3, 32, 8192, 64, 8192, 0),
+    (4, 4, 3, 2, 512, 200 * 1024, 256, 112 * 1024, 1),
+    (2, 3, 2, 4, 96, 24576, 480, 65536, 0),
 ])
 def test_every_schedule_gives_identical_results(sched):
     w, dom, u = _domain()
@@ -61,11 +61,12 @@ def test_every_schedule_gives_identical_results(sched):
 
 
 @pytest.mark.parametrize("bad", [
-    (1, 1, 2, 1, 128, 49152, 128, 49152),     # chains < 2
-    (2, 5, 2, 1, 128, 49152, 128, 49152),     # groups > 4
-    (2, 1, 2, 1, 100, 49152, 128, 49152),     # threads not a multiple of 32
-    (2, 1, 2, 1, 128, 1024, 128, 49152),      # budget below 8 KiB
-    (2, 1, 2, 1, 128, 49152, 1024, 49152),    # threads above 512
+    (1, 1, 2, 1, 128, 49152, 128, 49152, 0),     # chains < 2
+    (2, 5, 2, 1, 128, 49152, 128, 49152, 0),     # groups > 4
+    (2, 1, 2, 1, 100, 49152, 128, 49152, 0),     # threads not a multiple of 32
+    (2, 1, 2, 1, 128, 1024, 128, 49152, 0),      # budget below 8 KiB
+    (2, 1, 2, 1, 128, 49152, 1024, 49152, 0),    # threads above 512
+    (2, 1, 2, 1, 128, 49152, 128, 49152, 2),     # pair split not 0 or 1
 ])
 def test_invalid_schedules_are_rejected(bad):
     w, dom, u = _domain()
@@ -91,3 +92,28 @@ def test_schedules_of_two_domains_do_not_interfere():
     gh.gh_set_schedule(d2, s2)
     _outputs(w2, d2, u2)
     _same(ref, _outputs(w1, d1, u1))
+
+
+@pytest.mark.parametrize("cweight", [0.0, 0.01])
+def test_pair_split_and_per_point_reverse_passes_agree(cweight):
+    w, dom, u = _domain()
+    N = dom.state_size
+    g = torch.Generator().manual_seed(11)
+    kb = torch.randn(N, generator=g, dtype=torch.float64).to(u.device)
+    work = gh.new_vjp_work(dom)
+    stages = torch.empty(3 * N, dtype=torch.float64, device=u.device)
+    s0 = u.clone()
+    gh.gh_rk4_step_save(dom, w.dt, s0.clone(), dom.new_work(), stages)
+    out = {}
+    for split in (0, 1):
+        sch = gh.gh_get_schedule(dom)
+        sch["adjoint_pair_split"] = split
+        gh.gh_set_schedule(dom, sch)
+        ub = torch.zeros_like(u)
+        gh.gh_rhs_vjp(dom, u, kb, ub)
+        nx = torch.zeros_like(u)
+        gh.gh_rk4_step_vjp_saved(dom, w.dt, s0, stages, kb, nx, work, cweight)
+        torch.cuda.synchronize()
+        out[split] = (ub.cpu().numpy(), nx.cpu().numpy())
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())

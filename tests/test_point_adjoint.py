@@ -142,3 +142,24 @@ def test_fused_rhs_and_constraint_reverse_pass_is_the_sum(lib):
     ub2, dsb2 = np.zeros(50), np.zeros(150)
     lib.h_point_rhs_vjp_and_constraint(_p(u), _p(ds), _p(J), _p(H), _p(dH), *G, _p(kb), 0.37, _p(ub2), _p(dsb2))
     assert np.allclose(ub1, ub2, rtol=1e-14, atol=1e-14) and np.allclose(dsb1, dsb2, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+@pytest.mark.parametrize("w", [0.0, 0.37])
+def test_pair_restricted_reverse_passes_sum_to_the_full_one(lib, seed, w):
+    u, ds, J, H, dH = _point(seed)
+    G = (1.0, -1.0, 1.0)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    lib.h_point_vjp_pairsum.argtypes = [P, P, P, P, P, D, D, D, P, D, P, P]
+    lib.h_point_rhs_vjp_and_constraint.argtypes = [P, P, P, P, P, D, D, D, P, D, P, P]
+    kb = np.random.default_rng(seed + 100).standard_normal(50)
+    ub1, dsb1 = np.zeros(50), np.zeros(150)
+    lib.h_point_rhs_vjp_and_constraint(_p(u), _p(ds), _p(J), _p(H), _p(dH), *G, _p(kb), w, _p(ub1), _p(dsb1))
+    if w == 0.0:
+        ub1, dsb1 = np.zeros(50), np.zeros(150)
+        lib.h_point_rhs_vjp(_p(u), _p(ds), _p(J), _p(H), _p(dH), *G, _p(kb), _p(ub1), _p(dsb1))
+    ub2, dsb2 = np.zeros(50), np.zeros(150)
+    lib.h_point_vjp_pairsum(_p(u), _p(ds), _p(J), _p(H), _p(dH), *G, _p(kb), w, _p(ub2), _p(dsb2))
+    assert np.abs(ub2 - ub1).max() <= 1e-12 * max(1.0, np.abs(ub1).max())
+    assert np.abs(dsb2 - dsb1).max() <= 1e-12 * max(1.0, np.abs(dsb1).max())
