@@ -26,6 +26,7 @@ Modules
               fields and boundary conditions
   evolve      RK4, constraint energy, finite-difference gradients
   dp5         Dormand-Prince 5(4) adaptive step (the paper's stepper, Sec. 2.1)
+  frame       rotating dual frame: SpatialCoordJac and the grid velocity (Sec. 3.1)
   perturb     seeded-coefficient perturbations added to the exact data
 
 Nothing here is blocked, fused or reordered beyond what the definitions

@@ -80,19 +80,21 @@ def rhs_interior(dom, u):
     return out
 
 
-def apply_boundaries(dom, dudt, u=None):
+def apply_boundaries(dom, dudt, u=None, bg_map=None):
     """ApplyBCs: outer freezing (or constraint-preserving) condition, upwind
     interface exchange, no-op at excision.  u is needed for the
-    constraint-preserving outer condition.
+    constraint-preserving outer condition; bg_map transforms the boundary
+    background (the rotating frame rotates its vectors).
 
     Shells are ordered by radius; shell s's outer slice and shell s+1's inner
     slice are the same physical points.
     """
     out = [d.copy() for d in dudt]
     ns = len(out)
+    bgf = (lambda b: b) if bg_map is None else bg_map
     for s in range(ns - 1):
         nr = out[s].shape[0]
-        bg = dom.boundary_bg(s, nr - 1)
+        bg = bgf(dom.boundary_bg(s, nr - 1))
         a = np.moveaxis(out[s][nr - 1], 0, -1)
         b = np.moveaxis(out[s + 1][0], 0, -1)
         na, nb = gh.apply_interface_bc(a, b, bg, dom.gamma1, dom.gamma2)
@@ -100,7 +102,7 @@ def apply_boundaries(dom, dudt, u=None):
         out[s + 1][0] = np.moveaxis(nb, -1, 0)
     s = ns - 1
     nr = out[s].shape[0]
-    bg = dom.boundary_bg(s, nr - 1)
+    bg = bgf(dom.boundary_bg(s, nr - 1))
     a = np.moveaxis(out[s][nr - 1], 0, -1)
     if dom.outer_bc == "cp":
         ub = np.moveaxis(u[s][nr - 1], 0, -1)                                    # [th, ph, 50]
