@@ -269,6 +269,31 @@ long long gh_launch_count(const gh_domain* dom);
 enum { GH_ALG_DENSE = 0, GH_ALG_SEPARABLE = 1, GH_ALG_SEPARABLE_FOLDED = 2 };
 gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
 
+/* Rotating dual frame (Sec. 3.1: collocation points fixed in grid
+ * coordinates, equations in inertial coordinates, related by a time-dependent
+ * map; Sec. 3.3: SpatialCoordJac).  The map is the rigid rotation
+ * x = R(t) x_grid about `axis` (host pointer, any nonzero length) at rate
+ * omega (0: static grid, the default).  The evolved values are inertial-frame
+ * components at the grid points, so every right-hand side becomes
+ *   d/dt u = ApplyBCs(F(u, R d_grid u)) + xdot^k (R d_grid u)_k,
+ *   xdot = omega e x (R x_grid):
+ * the map's Jacobian on the derivative index (after DiffJac), the boundary
+ * conditions on the inertial rate F, and the grid-velocity term.  The
+ * background must be invariant under rotations about the axis (Schwarzschild:
+ * any axis; Kerr: its spin axis): its gauge source and boundary background at
+ * a moving point are then the stored t = 0 values with rotated components, and
+ * the characteristic speeds do not change (xdot is tangential).
+ * gh_rhs, gh_constraints and gh_derivatives evaluate at the domain's time
+ * (gh_set_time / gh_get_time); gh_rk4_step and accepted gh_dp5_step attempts
+ * advance it and use their stage times.  With omega != 0: the adjoint entry
+ * points and gh_rk4_graph_capture return GH_ENOTSUP, as do steps on domains
+ * with a dt scale other than 1.  gh_set_rotating_frame synchronises the
+ * stream and discards a captured graph; GH_EINVAL for a zero axis or a
+ * non-finite rate. */
+gh_status gh_set_rotating_frame(gh_domain* dom, const double axis[3], double omega);
+gh_status gh_set_time(gh_domain* dom, double t);
+gh_status gh_get_time(const gh_domain* dom, double* t);
+
 /* Outer boundary condition (ApplyBCs at the external boundary, Sec. 5).
  * GH_BC_FREEZE (default): incoming characteristic time derivatives set to 0.
  * GH_BC_CONSTRAINT_PRESERVING: Bjorhus form for the u^psi and u^0 families --

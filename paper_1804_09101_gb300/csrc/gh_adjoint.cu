@@ -422,6 +422,7 @@ gh_status adj_ready(gh_domain* d) {
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
   if (d->outer_bc != 0)
     return afail(d, GH_ENOTSUP, "the adjoint is built for the freezing outer boundary condition only");
+  if (d->rot_omega != 0.0) return afail(d, GH_ENOTSUP, "the adjoint is built for a static grid only");
   if (!d->kbt) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));

@@ -681,6 +681,29 @@ void invalidate_graph(gh_domain* d) {
 }
 }  // namespace
 
+namespace gh {
+Frame frame_at(const gh_domain* d, double t) {
+  Frame f;
+  f.on = d->rot_omega != 0.0 ? 1 : 0;
+  const double n = std::sqrt(d->rot_axis[0] * d->rot_axis[0] + d->rot_axis[1] * d->rot_axis[1] +
+                             d->rot_axis[2] * d->rot_axis[2]);
+  const double e[3] = {d->rot_axis[0] / n, d->rot_axis[1] / n, d->rot_axis[2] / n};
+  const double th = d->rot_omega * t, c = std::cos(th), sn = std::sin(th);
+  // Rodrigues: R = I + sin K + (1 - cos) K^2, K the cross-product matrix of e
+  const double K[9] = {0.0, -e[2], e[1], e[2], 0.0, -e[0], -e[1], e[0], 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double k2 = 0.0;
+      for (int m = 0; m < 3; ++m) k2 += K[3 * i + m] * K[3 * m + j];
+      f.R[3 * i + j] = (i == j ? 1.0 : 0.0) + sn * K[3 * i + j] + (1.0 - c) * k2;
+    }
+  for (int i = 0; i < 3; ++i) f.w[i] = d->rot_omega * e[i];
+  if (!f.on)
+    for (int i = 0; i < 9; ++i) f.R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  return f;
+}
+}  // namespace gh
+
 extern "C" {
 
 gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params* params,
@@ -1121,6 +1144,8 @@ gh_status gh_set_dt_scale(gh_domain* d, int bh, double scale) {
 }
 
 gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
+  if (d && d->rot_omega != 0.0)
+    return fail(d, GH_ENOTSUP, "a captured step would freeze the rotating frame's time; step directly");
   if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   cudaStream_t saved = d->stream;
@@ -1233,6 +1258,7 @@ gh_status gh_derivatives(gh_domain* d, const double* u, double* du) {
   if (!d || !u || !du) return fail(d, GH_EINVAL, "null argument");
   if (gh_status s = check_latched(d)) return s;
   if (gh_status s = derivatives(d, u)) return s;
+  d->fr = gh::frame_at(d, d->time);
   GH_CUDA(d, gh::launch_cartesian(d, u, du));
   return GH_OK;
 }
@@ -1241,6 +1267,7 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
   if (!d || !u || !dudt) return fail(d, GH_EINVAL, "null argument");
   if (u == dudt) return fail(d, GH_EINVAL, "u and dudt must not overlap");
   if (gh_status s = check_latched(d)) return s;
+  d->fr = gh::frame_at(d, d->time);
   if (gh_status s = derivatives(d, u)) return s;
   {
     ProfScope p(d, GH_K_POINTWISE);
@@ -1256,13 +1283,23 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
 // One RK4 step; with stages != NULL the three intermediate stage states
 // u_n + dt/2 k1, u_n + dt/2 k2, u_n + dt k3 are written there (and used as the
 // stage buffers) instead of the work area.
+gh_status rotation_guard(gh_domain* d) {
+  if (d->rot_omega == 0.0) return GH_OK;
+  for (const auto& sh : d->shells_h)
+    if (sh.dt_scale != 1.0) return fail(d, GH_ENOTSUP, "the rotating frame needs dt_scale = 1 on every shell");
+  return GH_OK;
+}
+
 gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages) {
+  if (gh_status s = rotation_guard(d)) return s;
+  static const double cst[4] = {0.0, 0.5, 0.5, 1.0};
   double* us = work;
   double* k = work + d->state;
   double* acc = work + 2 * d->state;
   const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
   for (int stage = 1; stage <= 4; ++stage) {
     const double* in = (stage == 1) ? u : (stages ? stages + (stage - 2) * d->state : us);
+    d->fr = gh::frame_at(d, d->time + cst[stage - 1] * dt);
     if (gh_status s = derivatives(d, in)) return s;
     double* target = (stage == 4) ? (filt ? us : u) : (stages ? stages + (stage - 1) * d->state : us);
     {
@@ -1281,6 +1318,7 @@ gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double
   if (filt) {
     if (gh_status s = filters(d, us, u, k)) return s;
   }
+  if (!stages) d->time += dt;   // gh_rk4_step advances the clock; the adjoint's recomputation does not
   return GH_OK;
 }
 
@@ -1306,6 +1344,8 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   for (const auto& sh : d->shells_h)
     if (sh.dt_scale != 1.0) return fail(d, GH_ENOTSUP, "the Dormand-Prince step needs dt_scale = 1 on every shell");
   if (gh_status s = check_latched(d)) return s;
+  if (gh_status s = rotation_guard(d)) return s;
+  static const double cdp[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
   // Dormand & Prince (1980) pair: stage matrix rows 2..7 (row 7 = b) and b - b_hat
   static const double A[7][6] = {
       {0, 0, 0, 0, 0, 0},
@@ -1324,6 +1364,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   double* unew = work + 8 * N;
   for (int s = 0; s < 7; ++s) {
     const double* in = (s == 0) ? u : (s == 6 ? unew : ustage);
+    d->fr = gh::frame_at(d, d->time + cdp[s] * dt);
     if (gh_status st = derivatives(d, in)) return st;
     {
       ProfScope p(d, GH_K_POINTWISE);
@@ -1365,6 +1406,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   *accepted = ok ? 1 : 0;
   *dt_next = dt * fac;
   if (ok) {
+    d->time += dt;
     const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
     if (filt) {
       if (gh_status st = filters(d, unew, u, ustage)) return st;
@@ -1383,6 +1425,7 @@ gh_status gh_apply_filters(gh_domain* d, double* u, double* work) {
 gh_status gh_constraints(gh_domain* d, const double* u, double* c_out, double* norm2) {
   if (!d || !u || !norm2) return fail(d, GH_EINVAL, "null argument");
   if (gh_status s = check_latched(d)) return s;
+  d->fr = gh::frame_at(d, d->time);
   if (gh_status s = derivatives(d, u)) return s;
   GH_CUDA(d, gh::launch_constraints(d, u, c_out));
   GH_CUDA(d, gh::launch_norm_reduce(d, norm2));
@@ -1476,6 +1519,33 @@ gh_status gh_autotune(gh_domain* d, int reps) {
   }
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   invalidate_graph(d);
+  return GH_OK;
+}
+
+gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega) {
+  if (!d || !axis) return GH_EINVAL;
+  const double n = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+  if (!(n > 0.0) || !std::isfinite(omega)) return fail(d, GH_EINVAL, "need a nonzero axis and a finite rate");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  for (int i = 0; i < 3; ++i) d->rot_axis[i] = axis[i];
+  d->rot_omega = omega;
+  d->fr = gh::frame_at(d, d->time);
+  if (d->graph_exec) {
+    cudaGraphExecDestroy(d->graph_exec);
+    d->graph_exec = nullptr;
+  }
+  return GH_OK;
+}
+
+gh_status gh_set_time(gh_domain* d, double t) {
+  if (!d || !std::isfinite(t)) return GH_EINVAL;
+  d->time = t;
+  return GH_OK;
+}
+
+gh_status gh_get_time(const gh_domain* d, double* t) {
+  if (!d || !t) return GH_EINVAL;
+  *t = d->time;
   return GH_OK;
 }
 

@@ -15,6 +15,13 @@ constexpr int NC = 64;      // stored constraint components per point
 constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
 constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
 constexpr int DP_MAX_BLOCKS = 1024;  // blocks of the Dormand-Prince elementwise kernels
+// Rotating dual frame at one instant (Sec. 3.1 dual frame): inertial position
+// x = R x_grid, grid velocity xdot = w x x.  on = 0: static grid.
+struct Frame {
+  int on;
+  double R[9];
+  double w[3];
+};
 // Linear combination of up to seven stage derivatives (passed by value).
 struct LinComb {
   const double* k[7];
@@ -196,6 +203,12 @@ struct gh_domain {
   // small grids, partial field cotangents in adj_ubp (10 states, lazily)
   bool adj_pair_split = false;
   double* adj_ubp = nullptr;
+  // rotating dual frame (gh_set_rotating_frame): axis, rate, the domain's
+  // time, and the frame of the launches being issued
+  double rot_axis[3] = {0.0, 0.0, 1.0};
+  double rot_omega = 0.0;
+  double time = 0.0;
+  gh::Frame fr = {0, {1, 0, 0, 0, 1, 0, 0, 0, 1}, {0, 0, 0}};
   // outer boundary condition: 0 freezing, 1 constraint preserving (gh_set_outer_bc)
   int outer_bc = 0;
   double* dp_err = nullptr;
@@ -221,6 +234,8 @@ cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dt
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
 cudaError_t fold_set_smem_limits(size_t bytes);
+// The rotating frame of the domain at time t (identity when not rotating).
+Frame frame_at(const gh_domain* d, double t);
 // Dormand-Prince step: out = base + sum_j c[j] k[j] (j < nk), and the scaled
 // RMS norm of sum_j c[j] k[j] (the embedded error estimate) into err_dev.
 cudaError_t launch_dp5_lincomb(gh_domain* d, const double* base, const LinComb& lc, double* out);

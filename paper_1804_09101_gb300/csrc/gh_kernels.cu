@@ -325,6 +325,7 @@ struct PointwiseArgs {
   double* c_out;         // constraint components (nullable)
   double gamma0, gamma1, gamma2, dt;
   int stage;
+  Frame fr;              // rotating frame of this evaluation (fr.on = 0: static)
 };
 
 __device__ __forceinline__ double stage_factor(int stage) {
@@ -347,6 +348,52 @@ __device__ __forceinline__ void stage_combine(int stage, double cdt, double kv, 
   }
 }
 
+// Rotating frame: DiffJac followed by the map's Jacobian, J <- R J (the
+// SpatialCoordJac of Sec. 3.3 for a rotation), and the grid velocity
+// w x (R x_grid) at the point.
+__device__ __forceinline__ void frame_geom(const Frame& fr, PointGeom& G, double vel[3]) {
+  double J2[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      J2[k][d] = fma(fr.R[3 * k + 2], G.J[2][d], fma(fr.R[3 * k + 1], G.J[1][d], fr.R[3 * k] * G.J[0][d]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) G.J[k][d] = J2[k][d];
+  double xi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    xi[k] = G.r * fma(fr.R[3 * k + 2], G.xhat[2], fma(fr.R[3 * k + 1], G.xhat[1], fr.R[3 * k] * G.xhat[0]));
+  vel[0] = fr.w[1] * xi[2] - fr.w[2] * xi[1];
+  vel[1] = fr.w[2] * xi[0] - fr.w[0] * xi[2];
+  vel[2] = fr.w[0] * xi[1] - fr.w[1] * xi[0];
+}
+
+// Gauge source of a background invariant under the rotation, at the moving
+// point: H_a -> Lambda_a^b H_b, d_i H_a -> R_ij Lambda_a^b d_j H_b.
+__device__ __forceinline__ void frame_rotate_h(const Frame& fr, double H[4]) {
+  const double h1 = H[1], h2 = H[2], h3 = H[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) H[1 + i] = fma(fr.R[3 * i + 2], h3, fma(fr.R[3 * i + 1], h2, fr.R[3 * i] * h1));
+}
+__device__ __forceinline__ void frame_rotate_dh(const Frame& fr, double dH[12]) {
+  double t[12];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      t[4 * i + a] = fma(fr.R[3 * i + 2], dH[8 + a], fma(fr.R[3 * i + 1], dH[4 + a], fr.R[3 * i] * dH[a]));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dH[4 * i] = t[4 * i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      dH[4 * i + 1 + a] = fma(fr.R[3 * a + 2], t[4 * i + 3], fma(fr.R[3 * a + 1], t[4 * i + 2], fr.R[3 * a] * t[4 * i + 1]));
+  }
+}
+
 #ifndef GH_PT_MINB
 #define GH_PT_MINB 9
 #endif
@@ -360,7 +407,7 @@ __device__ __forceinline__ void stage_combine(int stage, double cdt, double kv, 
 // constant factors (alpha, gamma's, 1/2) are folded into per-point
 // coefficient arrays, each output is built as one FMA chain, and the
 // Christoffel symbols are carried as E = 2 Gamma.
-template <bool RHS, bool CONSTRAINTS>
+template <bool RHS, bool CONSTRAINTS, bool ROT>
 __global__ void GH_PT_BOUNDS
 pointwise_kernel(PointwiseArgs a) {
   const int s = find_segment(a.begin, a.n_shells, blockIdx.x);
@@ -376,6 +423,8 @@ pointwise_kernel(PointwiseArgs a) {
     const long long base = sh.off + (long long)ir * NF * na + q;
     PointGeom G;
     point_geom(sh, ir, q, G);
+    double vel[3] = {0.0, 0.0, 0.0};
+    if (ROT) frame_geom(a.fr, G, vel);
     double psi[10], Pi[10], Phi[30];
 #pragma unroll
     for (int p = 0; p < 10; ++p) {
@@ -388,6 +437,7 @@ pointwise_kernel(PointwiseArgs a) {
     double H[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
+    if (ROT) frame_rotate_h(a.fr, H);
 
     Split S;
     spacetime_split(psi, S);
@@ -532,6 +582,7 @@ pointwise_kernel(PointwiseArgs a) {
         double dH[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
+        if (ROT) frame_rotate_dh(a.fr, dH);
         double aH[4], PHa[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) aH[c] = al * H[c];
@@ -656,6 +707,14 @@ pointwise_kernel(PointwiseArgs a) {
 
     const bool on_bc = (ir == 0 && sh.bc_inner >= 0) || (ir == sh.n_r - 1 && sh.bc_outer >= 0);
     const double cdt = stage_factor(a.stage) * a.dt * sh.dt_scale;
+    // grid-velocity term xdot^k d_k (spherical basis); at boundary points the
+    // boundary kernel adds it after the boundary conditions
+    const bool adv = ROT && !on_bc;
+    double vs[3] = {0.0, 0.0, 0.0};
+    if (adv) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) vs[d] = fma(vel[2], G.J[2][d], fma(vel[1], G.J[1][d], vel[0] * G.J[0][d]));
+    }
     // ---- derivative terms, one symmetric pair at a time
 #pragma unroll 1
     for (int p = 0; p < 10; ++p) {
@@ -729,6 +788,13 @@ pointwise_kernel(PointwiseArgs a) {
           }
           out[2 + i] = acc;
         }
+        if (adv) {
+          out[0] = fma(vs[2], dpsi[2], fma(vs[1], dpsi[1], fma(vs[0], dpsi[0], out[0])));
+          out[1] = fma(vs[2], dPi[2], fma(vs[1], dPi[1], fma(vs[0], dPi[0], out[1])));
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            out[2 + i] = fma(vs[2], dPhi[i][2], fma(vs[1], dPhi[i][1], fma(vs[0], dPhi[i][0], out[2 + i])));
+        }
         const int fidx[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
 #pragma unroll
         for (int e = 0; e < 5; ++e) {
@@ -786,6 +852,7 @@ struct BcArgs {
   const double* dr;
   const double* dth;
   const double* dph;
+  Frame fr;              // rotating frame (fr.on = 0: static)
 };
 
 // Bjorhus-form constraint-preserving corrections at an outer-boundary point for
@@ -797,6 +864,10 @@ __device__ __forceinline__ void cp_corrections(const BcArgs& a, const BcSliceDev
   const ShellDev& sh = a.shells[sl.shell_a];
   PointGeom G;
   point_geom(sh, sh.n_r - 1, q, G);
+  if (a.fr.on) {
+    double vel[3];
+    frame_geom(a.fr, G, vel);
+  }
   const int na = sl.na;
   const long long base = sl.off_a + q;
   auto cart = [&](int f, int i) {
@@ -847,14 +918,39 @@ __device__ __forceinline__ void char_project_pair(const double* k, long long bas
   for (int i = 0; i < 3; ++i) c.w0[i] = ph[i] - n_dn[i] * nphi;
 }
 
+// Grid-velocity term xdot^k d_k u of pair p's five fields at a boundary point
+// (shell `shell`, radial index ir, slice offset base), from the derivative
+// scratch of the state the RHS was evaluated at.
+__device__ __forceinline__ void frame_adv(const BcArgs& a, int shell, int ir, long long base, int na, int p, int q,
+                                          double adv[5]) {
+  const ShellDev& sh = a.shells[shell];
+  PointGeom G;
+  point_geom(sh, ir, q, G);
+  double vel[3], vs[3];
+  frame_geom(a.fr, G, vel);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) vs[d] = fma(vel[2], G.J[2][d], fma(vel[1], G.J[1][d], vel[0] * G.J[0][d]));
+  const int f[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
+#pragma unroll
+  for (int e = 0; e < 5; ++e) {
+    const long long o = base + (long long)f[e] * na;
+    adv[e] = fma(vs[2], a.dph[o], fma(vs[1], a.dth[o], vs[0] * a.dr[o]));
+  }
+}
+
 __device__ __forceinline__ void char_write_pair(const BcArgs& a, long long base, int na, int p, const CharPair& c,
-                                                const double n_dn[3], double g2, double cdt) {
+                                                const double n_dn[3], double g2, double cdt,
+                                                const double* adv = nullptr) {
   double v[5];
   v[0] = c.psi;
   v[1] = 0.5 * (c.wp + c.wm) + g2 * c.psi;
   const double h = 0.5 * (c.wp - c.wm);
 #pragma unroll
   for (int i = 0; i < 3; ++i) v[2 + i] = n_dn[i] * h + c.w0[i];
+  if (adv) {
+#pragma unroll
+    for (int e = 0; e < 5; ++e) v[e] += adv[e];
+  }
   const int f[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
 #pragma unroll
   for (int e = 0; e < 5; ++e) {
@@ -888,6 +984,22 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     beta[i] = sl.bg[(long long)(7 + i) * na + q];
   }
   const double alpha = sl.bg[(long long)6 * na + q];
+  if (a.fr.on) {
+    // the background's vectors at the moving point: rotated components
+    double t1[3], t2[3], t3[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t1[i] = fma(a.fr.R[3 * i + 2], n_dn[2], fma(a.fr.R[3 * i + 1], n_dn[1], a.fr.R[3 * i] * n_dn[0]));
+      t2[i] = fma(a.fr.R[3 * i + 2], n_up[2], fma(a.fr.R[3 * i + 1], n_up[1], a.fr.R[3 * i] * n_up[0]));
+      t3[i] = fma(a.fr.R[3 * i + 2], beta[2], fma(a.fr.R[3 * i + 1], beta[1], a.fr.R[3 * i] * beta[0]));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      n_dn[i] = t1[i];
+      n_up[i] = t2[i];
+      beta[i] = t3[i];
+    }
+  }
   const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
   const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
   const double g2 = a.gamma2;
@@ -912,7 +1024,10 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     }
     if (v_p < 0.0) c.wp = 0.0;
     if (v_m < 0.0) c.wm = 0.0;
-    char_write_pair(a, base, na, p, c, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
+    double adv[5];
+    if (a.fr.on) frame_adv(a, sl.shell_a, a.shells[sl.shell_a].n_r - 1, base, na, p, q, adv);
+    char_write_pair(a, base, na, p, c, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
+                    a.fr.on ? adv : nullptr);
   } else {
     const long long ba = sl.off_a + q, bb = sl.off_b + q;
     CharPair ci, co;
@@ -923,8 +1038,15 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     for (int i = 0; i < 3; ++i) select_pair(ci.w0[i], co.w0[i], v_0);
     select_pair(ci.wp, co.wp, v_p);
     select_pair(ci.wm, co.wm, v_m);
-    char_write_pair(a, ba, na, p, ci, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
-    char_write_pair(a, bb, na, p, co, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale);
+    double adv_a[5], adv_b[5];
+    if (a.fr.on) {
+      frame_adv(a, sl.shell_a, a.shells[sl.shell_a].n_r - 1, ba, na, p, q, adv_a);
+      frame_adv(a, sl.shell_b, 0, bb, na, p, q, adv_b);
+    }
+    char_write_pair(a, ba, na, p, ci, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
+                    a.fr.on ? adv_a : nullptr);
+    char_write_pair(a, bb, na, p, co, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
+                    a.fr.on ? adv_b : nullptr);
   }
 }
 
@@ -974,7 +1096,7 @@ bc_background_kernel(const ShellDev* __restrict__ shells, BcSliceDev* slices, in
 __global__ void __launch_bounds__(PT_THREADS)
 cartesian_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                  const double* __restrict__ dr, const double* __restrict__ dth,
-                 const double* __restrict__ dph, double* __restrict__ du, long long state) {
+                 const double* __restrict__ dph, double* __restrict__ du, long long state, Frame fr) {
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int na = sh.na;
@@ -985,6 +1107,10 @@ cartesian_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* _
   if (q >= na) return;
   PointGeom G;
   point_geom(sh, ir, q, G);
+  if (fr.on) {
+    double vel[3];
+    frame_geom(fr, G, vel);
+  }
   const long long base = sh.off + (long long)ir * NF * na + q;
   for (int f = 0; f < NF; ++f) {
     const long long o = base + (long long)f * na;
@@ -1062,7 +1188,11 @@ cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const doubl
   a.partial = nullptr; a.c_out = nullptr;
   a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
   a.dt = 0.0; a.stage = 0;
-  pointwise_kernel<true, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  a.fr = d->fr;
+  if (a.fr.on)
+    pointwise_kernel<true, false, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  else
+    pointwise_kernel<true, false, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
   d->launches++;
   return cudaGetLastError();
 }
@@ -1088,10 +1218,18 @@ cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage
   a.partial = d->partial; a.c_out = nullptr;
   a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
   a.dt = dt; a.stage = stage;
-  if (constraints)
-    pointwise_kernel<true, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
-  else
-    pointwise_kernel<true, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  a.fr = d->fr;
+  if (a.fr.on) {
+    if (constraints)
+      pointwise_kernel<true, true, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+    else
+      pointwise_kernel<true, false, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  } else {
+    if (constraints)
+      pointwise_kernel<true, true, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+    else
+      pointwise_kernel<true, false, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  }
   d->launches++;
   return cudaGetLastError();
 }
@@ -1104,7 +1242,11 @@ cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out) {
   a.partial = d->partial; a.c_out = c_out;
   a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
   a.dt = 0.0; a.stage = 0;
-  pointwise_kernel<false, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  a.fr = d->fr;
+  if (a.fr.on)
+    pointwise_kernel<false, true, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
+  else
+    pointwise_kernel<false, true, false><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
   d->launches++;
   return cudaGetLastError();
 }
@@ -1129,6 +1271,7 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
   a.dr = deriv ? deriv[0] : d->d_r;
   a.dth = deriv ? deriv[1] : d->d_th;
   a.dph = deriv ? deriv[2] : d->d_ph;
+  a.fr = d->fr;
   if (a.cp_outer && !u_in) return cudaErrorInvalidValue;
   bc_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(a);
   d->launches++;
@@ -1146,7 +1289,7 @@ cudaError_t launch_bc_background(gh_domain* d, const double* u, int bh) {
 cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du) {
   (void)u;
   cartesian_kernel<<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(
-      d->shells_d, d->n_shells, d->pt_block_begin_d, d->d_r, d->d_th, d->d_ph, du, d->state);
+      d->shells_d, d->n_shells, d->pt_block_begin_d, d->d_r, d->d_th, d->d_ph, du, d->state, d->fr);
   d->launches++;
   return cudaGetLastError();
 }

@@ -73,6 +73,9 @@ def _load():
         "gh_set_algorithm": ([P, I], I),
         "gh_autotune": ([P, I], I),
         "gh_set_outer_bc": ([P, I], I),
+        "gh_set_rotating_frame": ([P, ctypes.POINTER(D), D], I),
+        "gh_set_time": ([P, D], I),
+        "gh_get_time": ([P, ctypes.POINTER(D)], I),
         "gh_dp5_work_size": ([P], ctypes.c_longlong),
         "gh_dp5_step": ([P, D, D, D, P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         "gh_get_schedule": ([P, ctypes.POINTER(I), I], I),
@@ -279,6 +282,23 @@ def gh_set_algorithm(dom, algorithm):
 
 
 GH_BC_FREEZE, GH_BC_CONSTRAINT_PRESERVING = 0, 1
+
+
+def gh_set_rotating_frame(dom, axis, omega):
+    """Rigid rotation of the grid about axis at rate omega (0: static)."""
+    v = (ctypes.c_double * 3)(*[float(c) for c in axis])
+    dom._stream()
+    dom._check(_lib.gh_set_rotating_frame(dom.handle, v, float(omega)))
+
+
+def gh_set_time(dom, t):
+    dom._check(_lib.gh_set_time(dom.handle, float(t)))
+
+
+def gh_get_time(dom):
+    t = ctypes.c_double()
+    dom._check(_lib.gh_get_time(dom.handle, ctypes.byref(t)))
+    return t.value
 
 
 def gh_set_outer_bc(dom, mode):
