@@ -27,6 +27,7 @@ Modules
   evolve      RK4, constraint energy, finite-difference gradients
   dp5         Dormand-Prince 5(4) adaptive step (the paper's stepper, Sec. 2.1)
   frame       rotating dual frame: SpatialCoordJac and the grid velocity (Sec. 3.1)
+  tensor_filter  tensor (spin-weighted) spherical-harmonic truncation on S2 (Secs. 3.1, 3.4)
   perturb     seeded-coefficient perturbations added to the exact data
 
 Nothing here is blocked, fused or reordered beyond what the definitions
