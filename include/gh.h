@@ -306,6 +306,23 @@ gh_status gh_get_time(const gh_domain* dom, double* t);
 enum { GH_BC_FREEZE = 0, GH_BC_CONSTRAINT_PRESERVING = 1 };
 gh_status gh_set_outer_bc(gh_domain* dom, int mode);
 
+/* Angular (S2) filter mode (Sec. 3.1: the filter acts on tensors through
+ * tensor spherical harmonics; Sec. 3.4: its matrix couples the components).
+ * GH_SH_FILTER_COMPONENT (default): every one of the 50 fields is truncated to
+ *   Y_lm, l <= keep, on its own (Cartesian components treated as scalars).
+ * GH_SH_FILTER_TENSOR: each spatial tensor (psi_00, psi_0i, psi_ij, the same
+ *   for Pi, Phi_i00, Phi_i0j, Phi_ijk) is written in the local complex frame
+ *   r_hat, m = (theta_hat + i phi_hat)/sqrt(2), conj(m); a frame component of
+ *   spin weight s (#m - #conj(m)) is projected onto the spin-weighted
+ *   harmonics sY_lm, |s| <= l <= keep, and the tensor is rebuilt with the dual
+ *   frame.  keep is the domain's sh_keep_l (per shell for -2).  Uses a device
+ *   buffer of 130 doubles per grid point, allocated by the first switch to
+ *   this mode (GH_ECUDA if it does not fit).  The adjoint entry points return
+ *   GH_ENOTSUP in this mode.  Synchronises the stream and discards a captured
+ *   RK4 graph; GH_EINVAL for an unknown mode. */
+enum { GH_SH_FILTER_COMPONENT = 0, GH_SH_FILTER_TENSOR = 1 };
+gh_status gh_set_sh_filter(gh_domain* dom, int mode);
+
 /* Dormand-Prince 5(4) adaptive step: the paper's time stepper (Sec. 2.1; the
  * embedded pair of Dormand & Prince 1980, seven right-hand sides per attempt,
  * no stage reused across steps).  One attempt from u with step dt:

@@ -22,13 +22,15 @@ class Domain:
     """Shells, exact background and gauge source for one Kerr-Schild hole."""
 
     def __init__(self, shells, M, chi, gamma0=1.0, gamma1=-1.0, gamma2=1.0,
-                 filt_alpha=36.0, filt_order=32, radial_filter_on=False, sh_keep_l=-1, outer_bc="freeze"):
+                 filt_alpha=36.0, filt_order=32, radial_filter_on=False, sh_keep_l=-1, outer_bc="freeze",
+                 sh_filter="component"):
         self.specs = list(shells)                 # (r_in, r_out, n_r, L)
         self.M, self.chi = M, chi
         self.gamma0, self.gamma1, self.gamma2 = gamma0, gamma1, gamma2
         self.filt_alpha, self.filt_order = filt_alpha, filt_order
         self.radial_filter_on, self.sh_keep_l = radial_filter_on, sh_keep_l
         self.outer_bc = outer_bc                  # "freeze" or "cp" (constraint preserving, Bjorhus form)
+        self.sh_filter = sh_filter                # "component" (each Cartesian component) or "tensor"
         self.grids = [grid.shell_grid(*s) for s in self.specs]
         self.u_exact, self.H, self.dH = [], [], []
         for g in self.grids:
@@ -120,14 +122,21 @@ def rhs(dom, u):
 
 
 def apply_filters(dom, u):
-    """Radial ExpCheb filter (if on), then the SH truncation filter (if on)."""
+    """Radial ExpCheb filter (if on), then the SH truncation filter (if on):
+    per Cartesian component, or through tensor harmonics (sh_filter =
+    "tensor", oracle/tensor_filter.py).  sh_keep_l = -2 keeps l <= floor(2L/3)."""
+    from . import tensor_filter
     out = []
     for us, g in zip(u, dom.grids):
         v = us
         if dom.radial_filter_on:
             v = spectral.radial_filter(v, g, dom.filt_alpha, dom.filt_order)
-        if dom.sh_keep_l >= 0:
-            v = spectral.sh_truncation_filter(v, g, dom.sh_keep_l)
+        keep = (2 * g["L"]) // 3 if dom.sh_keep_l == -2 else dom.sh_keep_l
+        if keep >= 0:
+            if dom.sh_filter == "tensor":
+                v = np.stack([tensor_filter.filter_fields(v[r], g, keep) for r in range(v.shape[0])])
+            else:
+                v = spectral.sh_truncation_filter(v, g, keep)
         out.append(v)
     return out
 

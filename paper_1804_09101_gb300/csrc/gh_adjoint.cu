@@ -423,6 +423,8 @@ gh_status adj_ready(gh_domain* d) {
   if (d->outer_bc != 0)
     return afail(d, GH_ENOTSUP, "the adjoint is built for the freezing outer boundary condition only");
   if (d->rot_omega != 0.0) return afail(d, GH_ENOTSUP, "the adjoint is built for a static grid only");
+  if (d->sh_filter_mode != GH_SH_FILTER_COMPONENT)
+    return afail(d, GH_ENOTSUP, "the adjoint is built for the per-component angular filter only");
   if (!d->kbt) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));

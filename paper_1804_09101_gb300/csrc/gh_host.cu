@@ -563,7 +563,10 @@ gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
   if (ang) {
     ProfScope p(d, GH_K_ANGULAR_FILTER);
     double* dst = (cur == u) ? tmp : u;
-    GH_CUDA(d, gh::launch_angular_filter(d, cur, dst));
+    if (d->sh_filter_mode == GH_SH_FILTER_TENSOR)
+      GH_CUDA(d, gh::launch_tensor_filter(d, cur, dst));
+    else
+      GH_CUDA(d, gh::launch_angular_filter(d, cur, dst));
     cur = dst;
   }
   if (cur != u)
@@ -1555,6 +1558,28 @@ gh_status gh_set_outer_bc(gh_domain* d, int mode) {
     return fail(d, GH_EINVAL, "mode must be GH_BC_FREEZE or GH_BC_CONSTRAINT_PRESERVING");
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   d->outer_bc = mode;
+  if (d->graph_exec) {
+    cudaGraphExecDestroy(d->graph_exec);
+    d->graph_exec = nullptr;
+  }
+  return GH_OK;
+}
+
+gh_status gh_set_sh_filter(gh_domain* d, int mode) {
+  if (!d) return GH_EINVAL;
+  if (mode != GH_SH_FILTER_COMPONENT && mode != GH_SH_FILTER_TENSOR)
+    return fail(d, GH_EINVAL, "mode must be GH_SH_FILTER_COMPONENT or GH_SH_FILTER_TENSOR");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  if (mode == GH_SH_FILTER_TENSOR && !d->tf_buf) {
+    std::vector<std::vector<double>> xs, ws;
+    for (const auto& sh : d->shells_h) {
+      const AngularGrid ag = angular_grid(sh.L);
+      xs.push_back(ag.ct);
+      ws.push_back(ag.wgl);
+    }
+    GH_CUDA(d, gh::tensor_filter_prepare(d, xs, ws));
+  }
+  d->sh_filter_mode = mode;
   if (d->graph_exec) {
     cudaGraphExecDestroy(d->graph_exec);
     d->graph_exec = nullptr;

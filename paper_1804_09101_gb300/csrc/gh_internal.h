@@ -87,6 +87,17 @@ struct FoldPlan {
   double sigma0, sigma1;        // parity of output 0 / 1 (-1 for d/dtheta, +1 for values)
 };
 
+// Tensor spherical-harmonic filter of one shell (tensor_filter kernels): the
+// spin-s projection onto sY_lm, |s| <= l <= K, after a complex phi DFT is one
+// real N_theta x N_theta map per (s, m).
+struct TensorFilterPlan {
+  int K;                        // keep l <= K (-1: off)
+  const double* Q;              // [7 spins s = -3..3][2K+1 modes m = -K..K][j_out][j_in]
+  const double* tc;             // [K+1][nph] cos(m phi_k)
+  const double* ts;             // [K+1][nph] sin(m phi_k)
+};
+constexpr int TF_SLOTS = 65;    // complex frame components per point (9 tensor groups)
+
 // One shell as the kernels see it (device-resident array of these).
 struct ShellDev {
   int n_r, L, nth, nph, na;     // na = nth * nph angular points
@@ -118,6 +129,7 @@ struct ShellDev {
   SepAdjPlan sfa;               // transpose of sf (M = 0 if off)
   FoldPlan fd;                  // folded d/dtheta, d/dphi (M = 0 if not applicable)
   FoldPlan ff;                  // folded SH filter
+  TensorFilterPlan tf;          // tensor-harmonic SH filter (used when selected)
   const double* DrT;            // [n_r][n_r] transpose of Dr
   const double* FrT;            // [n_r][n_r] transpose of Fr
 };
@@ -203,6 +215,13 @@ struct gh_domain {
   // small grids, partial field cotangents in adj_ubp (10 states, lazily)
   bool adj_pair_split = false;
   double* adj_ubp = nullptr;
+  // SH filter mode (gh_set_sh_filter): 0 per Cartesian component, 1 tensor
+  // harmonics; complex frame components [shell][r][TF_SLOTS][na][2] (lazily)
+  int sh_filter_mode = 0;
+  double* tf_buf = nullptr;
+  int* tf_pb_d = nullptr;       // tensor-filter launch maps: point blocks, then rows
+  int tf_point_blocks = 0, tf_rows = 0;
+  size_t tf_smem = 0;
   // rotating dual frame (gh_set_rotating_frame): axis, rate, the domain's
   // time, and the frame of the launches being issued
   double rot_axis[3] = {0.0, 0.0, 1.0};
@@ -234,6 +253,12 @@ cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dt
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
 cudaError_t fold_set_smem_limits(size_t bytes);
+// Tensor-harmonic SH filter: tables, launch maps and the component buffer
+// (once; gl_x / gl_w are each shell's Gauss-Legendre nodes cos(theta) and
+// weights), then in -> out (may alias) using d->tf_buf.
+cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<double>>& gl_x,
+                                  const std::vector<std::vector<double>>& gl_w);
+cudaError_t launch_tensor_filter(gh_domain* d, const double* in, double* out);
 // The rotating frame of the domain at time t (identity when not rotating).
 Frame frame_at(const gh_domain* d, double t);
 // Dormand-Prince step: out = base + sum_j c[j] k[j] (j < nk), and the scaled

@@ -73,6 +73,7 @@ def _load():
         "gh_set_algorithm": ([P, I], I),
         "gh_autotune": ([P, I], I),
         "gh_set_outer_bc": ([P, I], I),
+        "gh_set_sh_filter": ([P, I], I),
         "gh_set_rotating_frame": ([P, ctypes.POINTER(D), D], I),
         "gh_set_time": ([P, D], I),
         "gh_get_time": ([P, ctypes.POINTER(D)], I),
@@ -282,6 +283,7 @@ def gh_set_algorithm(dom, algorithm):
 
 
 GH_BC_FREEZE, GH_BC_CONSTRAINT_PRESERVING = 0, 1
+GH_SH_FILTER_COMPONENT, GH_SH_FILTER_TENSOR = 0, 1
 
 
 def gh_set_rotating_frame(dom, axis, omega):
@@ -304,6 +306,15 @@ def gh_get_time(dom):
 def gh_set_outer_bc(dom, mode):
     dom._stream()
     dom._check(_lib.gh_set_outer_bc(dom.handle, int(mode)))
+
+
+def gh_set_sh_filter(dom, mode):
+    """0 / "component": each field truncated as a scalar; 1 / "tensor": the
+    tensor spherical-harmonic filter (spin-weighted harmonics in the complex
+    frame)."""
+    mode = {"component": 0, "tensor": 1}.get(mode, mode)
+    dom._stream()
+    dom._check(_lib.gh_set_sh_filter(dom.handle, int(mode)))
 
 
 def gh_dp5_step(dom, dt, rtol, atol, u, work):

@@ -1,0 +1,177 @@
+"""Parity of the tensor spherical-harmonic S2 filter (spin-weighted harmonics in
+the complex frame r_hat, m, conj(m); Secs. 3.1 and 3.4) with the oracle
+through the C ABI: the filter alone on seeded, non-band-limited states (one
+and two shells, a given keep and floor(2L/3), keep = 0 and keep = L), RK4 steps with the filter; at full size the properties that hold at
+any resolution (constant Cartesian tensors are kept when keep >= 3, the
+filter is a projection); the captured RK4 graph agrees with the plain calls,
+switching back restores the per-component filter, the adjoint refuses the
+mode."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import evolve
+from paper_1804_09101_gb300 import workloads
+from parity_helpers import REL_TOL, flat, unflat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
+
+pytestmark = pytest.mark.gpu
+
+
+def _gh():
+    from paper_1804_09101_gb300 import gh
+    return gh
+
+
+def _wl(name, shells, keep, radial=True):
+    return workloads.Workload(name=name, shells=shells, M=1.0, chi=0.7, gamma1=-1.0, radial_filter_on=radial,
+                              sh_keep_l=keep, dt=0.005, seed=11, noise_amp=1e-6,
+                              pulse=workloads.Pulse("psi_pulse", 1e-3, 4.0, 0.7, 2, workloads.random_coeffs(11, 2)))
+
+
+CASES = {
+    "one_shell_keep4": lambda: _wl("tf1", [(1.5, 5.0, 7, 7)], 4, radial=False),
+    "two_shells_keep4": lambda: _wl("tf2", [(1.3, 3.0, 7, 7), (3.0, 6.0, 7, 7)], 4),
+    "two_thirds_L9": lambda: _wl("tf3", [(1.5, 5.0, 5, 9)], -2, radial=False),
+    "keep0": lambda: _wl("tf4", [(1.5, 5.0, 5, 5)], 0, radial=False),
+    "keepL": lambda: _wl("tf5", [(1.5, 5.0, 5, 6)], 6, radial=False),
+}
+
+
+def _tensor_domain(w, odom=None):
+    gh = _gh()
+    dom = gpu_domain(w, odom)
+    gh.gh_set_sh_filter(dom, "tensor")
+    return dom
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    w = CASES[request.param]()
+    odom = oracle_domain(w)
+    odom.sh_filter = "tensor"
+    return w, odom
+
+
+def test_filter_matches_oracle(case):
+    gh = _gh()
+    w, odom = case
+    dom = _tensor_domain(w, odom)
+    # O(1) seeded noise on every field: every frame component and spin is exercised
+    rng = np.random.default_rng(2024)
+    x = rng.standard_normal(dom.state_size)
+    u = to_dev(x)
+    gh.gh_apply_filters(dom, u, dom.new_work())
+    ref = flat(evolve.apply_filters(odom, unflat(x, odom)))
+    assert np.abs(to_host(u) - ref).max() <= REL_TOL * np.abs(x).max()
+    # and it is not the per-component filter
+    odom.sh_filter = "component"
+    comp = flat(evolve.apply_filters(odom, unflat(x, odom)))
+    odom.sh_filter = "tensor"
+    assert np.abs(comp - ref).max() > 1e-3
+
+
+def test_rk4_steps_match_oracle():
+    gh = _gh()
+    w = CASES["two_shells_keep4"]()
+    odom = oracle_domain(w)
+    odom.sh_filter = "tensor"
+    u0 = oracle_initial_state(w, odom)
+    dom = _tensor_domain(w, odom)
+    u = to_dev(flat(u0))
+    work = dom.new_work()
+    ou = u0
+    for _ in range(2):
+        gh.gh_rk4_step(dom, w.dt, u, work)
+        ou = evolve.rk4_step(odom, ou, w.dt)
+    assert np.abs(to_host(u) - flat(ou)).max() <= REL_TOL * np.abs(flat(u0)).max()
+
+
+def _constant_tensors(w, seed):
+    """Every field constant in space (random values): Cartesian tensors of rank
+    <= 3 whose frame components have l <= rank."""
+    rng = np.random.default_rng(seed)
+    vals = rng.standard_normal(50)
+    out = []
+    for (_, _, n_r, L) in w.shells:                # [n_r, 50, n_theta, n_phi]
+        a = np.empty((n_r, 50, L + 1, 2 * (L + 1)))
+        a[...] = vals[None, :, None, None]
+        out.append(a)
+    return flat(out)
+
+
+@pytest.mark.parametrize("make", [workloads.kerr_four_shells, workloads.kerr_eight_shells_large])
+def test_full_size_properties(make):
+    gh = _gh()
+    w = make()
+    w.radial_filter_on = False
+    dom = gh.Domain.from_workload(w)
+    gh.gh_set_sh_filter(dom, "tensor")
+    work = dom.new_work()
+    # constant Cartesian tensors survive any keep >= 3
+    c = to_dev(_constant_tensors(w, 5))
+    c0 = c.clone()
+    gh.gh_apply_filters(dom, c, work)
+    torch.cuda.synchronize()
+    assert float((c - c0).abs().max()) <= REL_TOL * float(c0.abs().max())
+    # a projection: filtering twice is filtering once
+    g = torch.Generator(device="cuda").manual_seed(9)
+    x = torch.randn(dom.state_size, dtype=torch.float64, device="cuda", generator=g)
+    gh.gh_apply_filters(dom, x, work)
+    y = x.clone()
+    gh.gh_apply_filters(dom, y, work)
+    torch.cuda.synchronize()
+    assert float((y - x).abs().max()) <= REL_TOL * float(x.abs().max())
+    # and it removes something from non-band-limited data
+    z = torch.randn(dom.state_size, dtype=torch.float64, device="cuda", generator=g)
+    z0 = z.clone()
+    gh.gh_apply_filters(dom, z, work)
+    torch.cuda.synchronize()
+    assert float((z - z0).abs().max()) > 1e-2
+
+
+def test_keep_below_rank_changes_constant_tensors():
+    """keep = 1 removes the l = 2, 3 parts of constant rank-2 and rank-3
+    tensors while the per-component filter keeps every constant."""
+    gh = _gh()
+    w = _wl("tf6", [(1.5, 5.0, 5, 5)], 1, radial=False)
+    dom = gh.Domain.from_workload(w)
+    work = dom.new_work()
+    c0 = to_dev(_constant_tensors(w, 6))
+    a = c0.clone()
+    gh.gh_apply_filters(dom, a, work)
+    gh.gh_set_sh_filter(dom, "tensor")
+    b = c0.clone()
+    gh.gh_apply_filters(dom, b, work)
+    torch.cuda.synchronize()
+    assert float((a - c0).abs().max()) <= REL_TOL * float(c0.abs().max())
+    assert float((b - c0).abs().max()) > 1e-2
+
+
+def test_graph_mode_switch_and_adjoint():
+    gh = _gh()
+    w = CASES["two_shells_keep4"]()
+    dom = gh.Domain.from_workload(w)
+    with pytest.raises(RuntimeError):
+        gh.gh_set_sh_filter(dom, 5)
+    u = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    u += 1e-6 * torch.randn(dom.state_size, dtype=torch.float64, device="cuda", generator=g)
+    comp = u.clone()
+    gh.gh_apply_filters(dom, comp, dom.new_work())
+    gh.gh_set_sh_filter(dom, "tensor")
+    a, b = u.clone(), u.clone()
+    wa, wb = dom.new_work(), dom.new_work()
+    for _ in range(3):
+        gh.gh_rk4_step(dom, w.dt, a, wa)
+    gh.gh_rk4_graph_capture(dom, w.dt, b, wb)
+    gh.gh_rk4_graph_launch(dom, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    with pytest.raises(RuntimeError):
+        gh.gh_rhs_vjp(dom, u, u.clone(), torch.zeros_like(u))
+    gh.gh_set_sh_filter(dom, "component")
+    back = u.clone()
+    gh.gh_apply_filters(dom, back, dom.new_work())
+    torch.cuda.synchronize()
+    assert torch.equal(back, comp)
