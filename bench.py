@@ -64,6 +64,9 @@ def parse():
                         "N_r=41, L=31; schwarzschild: 1 shell N_r=11, L=7; batched: 64 independent "
                         "single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
                         "compared with the plain per-hole launch loop")
+    p.add_argument("--sh-filter", default="component", choices=["component", "tensor"],
+                   help="angular filter: per Cartesian component (default) or tensor spherical harmonics "
+                        "(spin-weighted harmonics in the complex frame)")
     p.add_argument("--algorithm", default="auto", choices=["auto", "folded", "separable", "dense"],
                    help="angular maps: folded separable (default), plain separable, or dense traced matrices")
     return p.parse_args()
@@ -212,6 +215,8 @@ def run_ours(args, w):
         gh.gh_set_schedule(dom, json.loads(args.schedule))
     elif not args.no_autotune:
         gh.gh_autotune(dom, 5)
+    if args.sh_filter == "tensor":
+        gh.gh_set_sh_filter(dom, "tensor")
     u = dom.new_state()
     gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
     p = w.pulse
@@ -315,6 +320,9 @@ def run_ours(args, w):
                 config=dict(workload=w.name, points=pts, shells=[list(s) for s in w.shells], chi=w.chi,
                             dt=w.dt, rhs_evals_per_step=4,
                             step="RK4 step + ExpCheb(36,32) + SH keep l<=%d + constraint norms" % w.sh_keep_l,
+                            sh_filter={"component": "per Cartesian component (scalar Y_lm truncation)",
+                                       "tensor": "tensor spherical harmonics (spin-weighted sY_lm of the "
+                                                 "31 independent complex frame components)"}[args.sh_filter],
                             l2="flushed before every timed step (256 MB write, outside the step events)",
                             parallelism="replicas" if world > 1 else "single GPU", algorithm=args.algorithm,
                             schedule=gh.gh_get_schedule(dom),

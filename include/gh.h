@@ -316,8 +316,9 @@ gh_status gh_set_outer_bc(gh_domain* dom, int mode);
  *   spin weight s (#m - #conj(m)) is projected onto the spin-weighted
  *   harmonics sY_lm, |s| <= l <= keep, and the tensor is rebuilt with the dual
  *   frame.  keep is the domain's sh_keep_l (per shell for -2).  Uses a device
- *   buffer of 130 doubles per grid point, allocated by the first switch to
- *   this mode (GH_ECUDA if it does not fit).  The adjoint entry points return
+ *   buffer of 62 doubles per grid point (the 31 independent complex frame
+ *   components), allocated by the first switch to this mode (GH_ECUDA if it
+ *   does not fit).  The adjoint entry points return
  *   GH_ENOTSUP in this mode.  Synchronises the stream and discards a captured
  *   RK4 graph; GH_EINVAL for an unknown mode. */
 enum { GH_SH_FILTER_COMPONENT = 0, GH_SH_FILTER_TENSOR = 1 };

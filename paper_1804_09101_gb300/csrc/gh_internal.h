@@ -96,7 +96,7 @@ struct TensorFilterPlan {
   const double* tc;             // [K+1][nph] cos(m phi_k)
   const double* ts;             // [K+1][nph] sin(m phi_k)
 };
-constexpr int TF_SLOTS = 65;    // complex frame components per point (9 tensor groups)
+constexpr int TF_ROWS = 31;     // independent complex frame components per point (9 tensor groups)
 
 // One shell as the kernels see it (device-resident array of these).
 struct ShellDev {
@@ -216,7 +216,7 @@ struct gh_domain {
   bool adj_pair_split = false;
   double* adj_ubp = nullptr;
   // SH filter mode (gh_set_sh_filter): 0 per Cartesian component, 1 tensor
-  // harmonics; complex frame components [shell][r][TF_SLOTS][na][2] (lazily)
+  // harmonics; complex frame components [shell][r][TF_ROWS][na][2]
   int sh_filter_mode = 0;
   double* tf_buf = nullptr;
   int* tf_pb_d = nullptr;       // tensor-filter launch maps: point blocks, then rows

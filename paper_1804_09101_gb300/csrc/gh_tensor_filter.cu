@@ -5,18 +5,22 @@
 // has spin weight s = #m - #conj(m) and is projected onto the spin-weighted
 // harmonics sY_lm, |s| <= l <= K; the filtered tensor is
 // Re sum_A c'_A conj(E_A1) x .. (conj(E) is the dual basis).  Three kernels:
-//   tf_frame_kernel   per point: the 65 complex components of the 9 tensor
-//                     groups (psi_00, psi_0i, psi_ij, the same for Pi, Phi_i00,
-//                     Phi_i0j, Phi_ijk), one index contracted at a time;
-//   tf_spin_kernel    per (r, component) row: complex phi DFT (m = -K..K), the
-//                     real N_theta x N_theta map of (s, m), inverse DFT;
-//   tf_unframe_kernel per point: back to the Cartesian components.
+//   tf_frame_kernel   per point: the complex components of the 9 tensor groups
+//                     (psi_00, psi_0i, psi_ij, the same for Pi, Phi_i00,
+//                     Phi_i0j, Phi_ijk), one index contracted at a time; the
+//                     31 independent ones of the 65 are stored;
+//   tf_spin_kernel    per (r, independent component) row: complex phi DFT
+//                     (m = -K..K), the real N_theta x N_theta map of (s, m),
+//                     inverse DFT;
+//   tf_unframe_kernel per point: all 65 from the 31, back to the Cartesian
+//                     components.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <utility>
 #include <vector>
 
 #include "gh_geom.cuh"
@@ -25,18 +29,91 @@
 
 namespace gh {
 
-// 9 tensor groups: rank, first component slot, field of each Cartesian index tuple
-__constant__ int c_tf_rank[9] = {0, 1, 2, 0, 1, 2, 1, 2, 3};
-__constant__ int c_tf_slot[9] = {0, 1, 4, 13, 14, 17, 26, 29, 38};
-__constant__ int c_tf_field[9][27];
-__constant__ unsigned char c_tf_write[9][27];  // 1 for the stored (canonical) index tuple
+// The 9 tensor groups (psi_00, psi_0i, psi_ij, Pi_00, Pi_0i, Pi_ij, Phi_i00,
+// Phi_i0j, Phi_ijk): rank, and the field of each Cartesian index tuple o
+// (row-major, first index slowest).  Everything here is constexpr so that the
+// unrolled contractions keep only what is stored.
+__host__ __device__ constexpr int tf_rank(int g) {
+  return (g == 0 || g == 3) ? 0 : (g == 1 || g == 4 || g == 6) ? 1 : (g == 8 ? 3 : 2);
+}
+__host__ __device__ constexpr int tf_size(int g) {
+  return tf_rank(g) == 0 ? 1 : tf_rank(g) == 1 ? 3 : tf_rank(g) == 2 ? 9 : 27;
+}
+__host__ __device__ constexpr bool tf_sym(int g) { return g == 2 || g == 5 || g == 8; }  // last two indices
+__host__ __device__ constexpr int tf_digit(int g, int o, int k) {
+  int div = 1;
+  for (int q = k + 1; q < tf_rank(g); ++q) div *= 3;
+  return (o / div) % 3;
+}
+__host__ __device__ constexpr int tf_field(int g, int o) {
+  return g < 6 ? (g % 3 == 0 ? 10 * (g / 3) + sym_index(0, 0)
+                  : g % 3 == 1 ? 10 * (g / 3) + sym_index(0, 1 + o)
+                               : 10 * (g / 3) + sym_index(1 + o / 3, 1 + o % 3))
+       : g == 6 ? 20 + 10 * o + sym_index(0, 0)
+       : g == 7 ? 20 + 10 * (o / 3) + sym_index(0, 1 + o % 3)
+                : 20 + 10 * (o / 9) + sym_index(1 + (o / 3) % 3, 1 + o % 3);
+}
+__host__ __device__ constexpr bool tf_written(int g, int o) {  // the stored tuple of a symmetric pair
+  return !tf_sym(g) || tf_digit(g, o, tf_rank(g) - 2) <= tf_digit(g, o, tf_rank(g) - 1);
+}
+// The frame components of a real tensor obey c_conj(A) = conj(c_A) (conj
+// swaps m and conj(m)), and a symmetric pair gives equal components: each
+// class {A, swap(A), conj(A), conj(swap(A))} is represented by its first tuple.
+__host__ __device__ constexpr int tf_variant(int g, int o, int c, int sw) {
+  const int r = tf_rank(g);
+  int e[3] = {0, 0, 0};
+  for (int k = 0; k < r; ++k) e[k] = tf_digit(g, o, k);
+  if (sw) {
+    const int x = e[r - 2];
+    e[r - 2] = e[r - 1];
+    e[r - 1] = x;
+  }
+  if (c)
+    for (int k = 0; k < r; ++k) e[k] = e[k] == 0 ? 0 : 3 - e[k];
+  int v = 0;
+  for (int k = 0; k < r; ++k) v = 3 * v + e[k];
+  return v;
+}
+__host__ __device__ constexpr int tf_best(int g, int o) {
+  int best = o;
+  for (int c = 0; c < 2; ++c)
+    for (int sw = 0; sw < (tf_sym(g) ? 2 : 1); ++sw)
+      if (tf_variant(g, o, c, sw) < best) best = tf_variant(g, o, c, sw);
+  return best;
+}
+__host__ __device__ constexpr bool tf_best_conj(int g, int o) {  // c_o = conj(c_best)
+  int best = o;
+  bool cj = false;
+  for (int c = 0; c < 2; ++c)
+    for (int sw = 0; sw < (tf_sym(g) ? 2 : 1); ++sw)
+      if (tf_variant(g, o, c, sw) < best) {
+        best = tf_variant(g, o, c, sw);
+        cj = c != 0;
+      }
+  return cj;
+}
+__host__ __device__ constexpr int tf_row(int g, int o) {  // independent row of tuple o, -1 if not canonical
+  if (tf_best(g, o) != o) return -1;
+  int row = 0;
+  for (int gg = 0; gg < g; ++gg)
+    for (int oo = 0; oo < tf_size(gg); ++oo) row += tf_best(gg, oo) == oo;
+  for (int oo = 0; oo < o; ++oo) row += tf_best(g, oo) == oo;
+  return row;
+}
+__host__ __device__ constexpr int tf_spin(int g, int o) {  // #m - #conj(m)
+  int s = 0;
+  for (int k = 0; k < tf_rank(g); ++k) s += tf_digit(g, o, k) == 1 ? 1 : (tf_digit(g, o, k) == 2 ? -1 : 0);
+  return s;
+}
+static_assert(tf_row(8, 26) < 0 && tf_row(8, 9 * 1 + 3 * 2 + 2) == TF_ROWS - 1, "31 independent components");
+
+__constant__ signed char c_tf_spin[TF_ROWS];   // spin of each independent row
 
 constexpr int TF_THREADS = 128;
 
 struct Cx {
   double re, im;
 };
-__device__ __forceinline__ Cx cmul(Cx a, Cx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 
 __device__ __forceinline__ void frame_vectors(const ShellDev& sh, int q, Cx E[3][3]) {
   const int j = q / sh.nph, k = q - j * sh.nph;
@@ -45,6 +122,7 @@ __device__ __forceinline__ void frame_vectors(const ShellDev& sh, int q, Cx E[3]
   const double th[3] = {ct * cp, ct * sp, -st};
   const double ph[3] = {-sp, cp, 0.0};
   const double h = 0.70710678118654752440;
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     E[0][i] = {rh[i], 0.0};
     E[1][i] = {h * th[i], h * ph[i]};
@@ -53,31 +131,110 @@ __device__ __forceinline__ void frame_vectors(const ShellDev& sh, int q, Cx E[3]
 }
 
 // Contract every index of a rank-n tensor (3^n values, row-major, first index
-// slowest) with the frame.  Forward (inverse = false): Cartesian -> frame,
-// c_..A.. = sum_i E_A^i T_..i..; inverse: frame -> Cartesian with the dual
-// basis, T_..i.. = sum_A conj(E_A^i) c_..A...
-__device__ __forceinline__ void contract(int rank, Cx* t, Cx* w, const Cx E[3][3], bool inverse) {
-  int n = 1;
-  for (int k = 0; k < rank; ++k) n *= 3;
-  for (int k = 0; k < rank; ++k) {
-    // contract index k: output index Ak of w from summed index i of t
-    int stride = 1;
-    for (int q = k + 1; q < rank; ++q) stride *= 3;
+// slowest) with the frame.  Forward (INV = false): Cartesian -> frame,
+// c_..A.. = sum_i E_A^i T_..i.. (T real); inverse: frame -> Cartesian with the
+// dual basis, T_..i.. = sum_A conj(E_A^i) c_..A...  Fully unrolled (t stays
+// in registers); products with a real factor (the input tensor, r_hat, the z
+// component of m) skip the zero imaginary part.
+template <int RANK, bool INV>
+__device__ __forceinline__ void contract(Cx* t, const Cx E[3][3]) {
+  constexpr int n = RANK == 0 ? 1 : RANK == 1 ? 3 : RANK == 2 ? 9 : 27;
+#pragma unroll
+  for (int k = 0; k < RANK; ++k) {
+    const int stride = k == RANK - 1 ? 1 : (k == RANK - 2 ? 3 : 9);
+    Cx w[n];
+#pragma unroll
     for (int o = 0; o < n; ++o) {
-      const int Ak = (o / stride) % 3;
+      const int Ak = (o / stride) % 3;          // output index
       const int base = o - Ak * stride;
       Cx acc = {0.0, 0.0};
-      for (int i = 0; i < 3; ++i) {
-        Cx e = inverse ? E[i][Ak] : E[Ak][i];
-        if (inverse) e.im = -e.im;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {             // summed index
+        const int a = INV ? i : Ak, x = INV ? Ak : i;
+        const Cx e = INV ? Cx{E[a][x].re, -E[a][x].im} : E[a][x];
+        const bool e_real = a == 0 || x == 2;
+        const bool v_real = !INV && k == 0;
         const Cx v = t[base + i * stride];
-        acc.re += e.re * v.re - e.im * v.im;
-        acc.im += e.re * v.im + e.im * v.re;
+        if (e_real && v_real) {
+          acc.re = fma(e.re, v.re, acc.re);
+        } else if (e_real) {
+          acc.re = fma(e.re, v.re, acc.re);
+          acc.im = fma(e.re, v.im, acc.im);
+        } else if (v_real) {
+          acc.re = fma(e.re, v.re, acc.re);
+          acc.im = fma(e.im, v.re, acc.im);
+        } else {
+          acc.re = fma(e.re, v.re, fma(-e.im, v.im, acc.re));
+          acc.im = fma(e.re, v.im, fma(e.im, v.re, acc.im));
+        }
       }
       w[o] = acc;
     }
+#pragma unroll
     for (int o = 0; o < n; ++o) t[o] = w[o];
   }
+}
+
+// component buffer: per radial slice, TF_ROWS rows of na complex values
+__device__ __forceinline__ long long tf_index(const ShellDev& sh, int ir, int row, int q) {
+  return 2LL * ((sh.pt_off + (long long)ir * sh.na) * TF_ROWS + (long long)row * sh.na + q);
+}
+
+template <int G, int O>
+__device__ __forceinline__ void tf_load_u(Cx* t, const double* __restrict__ u, long long ubase, int na) {
+  t[O] = {u[ubase + (long long)tf_field(G, O) * na], 0.0};
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_store_c(const Cx* t, const ShellDev& sh, int ir, int q, double* __restrict__ cb) {
+  constexpr int row = tf_row(G, O);
+  if constexpr (row >= 0) {
+    const long long c = tf_index(sh, ir, row, q);
+    cb[c] = t[O].re;
+    cb[c + 1] = t[O].im;
+  }
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_load_c(Cx* t, const ShellDev& sh, int ir, int q, const double* __restrict__ cb) {
+  constexpr int row = tf_row(G, tf_best(G, O));
+  const long long c = tf_index(sh, ir, row, q);
+  t[O] = {cb[c], tf_best_conj(G, O) ? -cb[c + 1] : cb[c + 1]};
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_store_u(const Cx* t, double* __restrict__ out, long long ubase, int na) {
+  if constexpr (tf_written(G, O)) out[ubase + (long long)tf_field(G, O) * na] = t[O].re;
+}
+
+template <int G, int... O>
+__device__ __forceinline__ void frame_group(std::integer_sequence<int, O...>, const ShellDev& sh, int ir, int q,
+                                            const Cx E[3][3], const double* __restrict__ u, long long ubase,
+                                            double* __restrict__ cb) {
+  Cx t[sizeof...(O)];
+  (tf_load_u<G, O>(t, u, ubase, sh.na), ...);
+  contract<tf_rank(G), false>(t, E);
+  (tf_store_c<G, O>(t, sh, ir, q, cb), ...);
+}
+
+template <int G, int... O>
+__device__ __forceinline__ void unframe_group(std::integer_sequence<int, O...>, const ShellDev& sh, int ir, int q,
+                                              const Cx E[3][3], const double* __restrict__ cb, long long ubase,
+                                              double* __restrict__ out) {
+  Cx t[sizeof...(O)];
+  (tf_load_c<G, O>(t, sh, ir, q, cb), ...);
+  contract<tf_rank(G), true>(t, E);
+  (tf_store_u<G, O>(t, out, ubase, sh.na), ...);
+}
+
+template <int... G>
+__device__ __forceinline__ void frame_all(std::integer_sequence<int, G...>, const ShellDev& sh, int ir, int q,
+                                          const Cx E[3][3], const double* __restrict__ u, long long ub,
+                                          double* __restrict__ cb) {
+  (frame_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, E, u, ub, cb), ...);
+}
+template <int... G>
+__device__ __forceinline__ void unframe_all(std::integer_sequence<int, G...>, const ShellDev& sh, int ir, int q,
+                                            const Cx E[3][3], const double* __restrict__ cb, long long ub,
+                                            double* __restrict__ out) {
+  (unframe_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, E, cb, ub, out), ...);
 }
 
 __global__ void __launch_bounds__(TF_THREADS)
@@ -93,20 +250,8 @@ tf_frame_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __
   if (q >= na) return;
   Cx E[3][3];
   frame_vectors(sh, q, E);
-  const long long ubase = sh.off + (long long)ir * NF * na + q;
-  const long long cbase = 2LL * TF_SLOTS * (sh.pt_off + (long long)ir * na);
-  for (int g = 0; g < 9; ++g) {
-    const int rank = c_tf_rank[g];
-    const int n = rank == 0 ? 1 : (rank == 1 ? 3 : (rank == 2 ? 9 : 27));
-    Cx t[27], w[27];
-    for (int o = 0; o < n; ++o) t[o] = {u[ubase + (long long)c_tf_field[g][o] * na], 0.0};
-    contract(rank, t, w, E, false);
-    for (int o = 0; o < n; ++o) {
-      const long long c = cbase + 2LL * ((long long)(c_tf_slot[g] + o) * na + q);
-      cb[c] = t[o].re;
-      cb[c + 1] = t[o].im;
-    }
-  }
+  const long long ub = sh.off + (long long)ir * NF * na + q;
+  frame_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, E, u, ub, cb);
 }
 
 __global__ void __launch_bounds__(TF_THREADS)
@@ -122,33 +267,17 @@ tf_unframe_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* 
   if (q >= na) return;
   Cx E[3][3];
   frame_vectors(sh, q, E);
-  const long long ubase = sh.off + (long long)ir * NF * na + q;
-  const long long cbase = 2LL * TF_SLOTS * (sh.pt_off + (long long)ir * na);
-  for (int g = 0; g < 9; ++g) {
-    const int rank = c_tf_rank[g];
-    const int n = rank == 0 ? 1 : (rank == 1 ? 3 : (rank == 2 ? 9 : 27));
-    Cx t[27], w[27];
-    for (int o = 0; o < n; ++o) {
-      const long long c = cbase + 2LL * ((long long)(c_tf_slot[g] + o) * na + q);
-      t[o] = {cb[c], cb[c + 1]};
-    }
-    contract(rank, t, w, E, true);
-    for (int o = 0; o < n; ++o)
-      if (c_tf_write[g][o]) out[ubase + (long long)c_tf_field[g][o] * na] = t[o].re;
-  }
+  const long long ub = sh.off + (long long)ir * NF * na + q;
+  unframe_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, E, cb, ub, out);
 }
 
-// spin of component o of group g: #m - #conj(m) over its frame indices
-__device__ __forceinline__ int slot_spin(int rank, int o) {
-  int sp = 0;
-  for (int k = 0; k < rank; ++k) {
-    const int a = o % 3;
-    o /= 3;
-    sp += (a == 1) ? 1 : (a == 2 ? -1 : 0);
-  }
-  return sp;
-}
-
+// One independent component row of one radial slice: the projection onto
+// sY_lm, |s| <= l <= K, of a complex function on the (theta, phi) grid:
+//   F_m(theta_i) = (1/N_phi) sum_k f(theta_i, phi_k) e^{-i m phi_k},  |m| <= K
+//   G_m(theta_j) = sum_i Q^{s,m}[j][i] F_m(theta_i)
+//   f'(theta_j, phi_k) = sum_m G_m(theta_j) e^{i m phi_k}.
+// phi_{k+N/2} = phi_k + pi multiplies e^{i m phi} by (-1)^m (half-period fold
+// of both transforms), and +m, -m share their cos / sin products.
 __global__ void __launch_bounds__(TF_THREADS)
 tf_spin_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                double* __restrict__ cb) {
@@ -156,63 +285,89 @@ tf_spin_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __r
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const TensorFilterPlan& P = sh.tf;
-  const int na = sh.na, nth = sh.nth, nph = sh.nph, K = P.K, M2 = 2 * K + 1;
-  const int row = blockIdx.x - begin[s];          // (ir, slot)
-  const int slot = row % TF_SLOTS;
-  const int ir = row / TF_SLOTS;
-  int g = 0;
-  while (g + 1 < 9 && c_tf_slot[g + 1] <= slot) ++g;
-  const int sp = slot_spin(c_tf_rank[g], slot - c_tf_slot[g]);
+  const int na = sh.na, nth = sh.nth, nph = sh.nph, h = nph / 2, K = P.K, M2 = 2 * K + 1, K1 = K + 1;
+  const int rr = blockIdx.x - begin[s];           // (ir, row)
+  const int row = rr % TF_ROWS;
+  const int ir = rr / TF_ROWS;
+  const int sp = c_tf_spin[row];
   double* f = sm;                                 // [na][2]
-  double* F = f + 2 * na;                         // [nth][M2][2]
-  double* G = F + 2 * nth * M2;                   // [nth][M2][2]
-  double* row_ptr = cb + 2LL * TF_SLOTS * (sh.pt_off + (long long)ir * na) + 2LL * slot * na;
-  for (int i = threadIdx.x; i < 2 * na; i += blockDim.x) f[i] = row_ptr[i];
+  double* F = f + 2 * na;                         // [nth][M2][2], m = -K..K
+  double* PM = F + 2 * nth * M2;                  // [nth][K1][4]: G_m + G_-m, G_m - G_-m
+  double* gp = cb + tf_index(sh, ir, row, 0);
+  for (int i = threadIdx.x; i < 2 * na; i += blockDim.x) f[i] = gp[i];
   __syncthreads();
   const double inv = 1.0 / nph;
-  for (int o = threadIdx.x; o < nth * M2; o += blockDim.x) {
-    const int mi = o % M2, j = o / M2, m = mi - K, am = m < 0 ? -m : m;
-    const double sg = m < 0 ? -1.0 : 1.0;
-    const double* c = P.tc + (size_t)am * nph;
-    const double* sn = P.ts + (size_t)am * nph;
-    double re = 0.0, im = 0.0;
-    for (int k = 0; k < nph; ++k) {
-      // f e^{-i m phi}: (a + i b)(cos - i sg sin)
-      const double a = f[2 * (j * nph + k)], b = f[2 * (j * nph + k) + 1];
-      const double cs = __ldg(c + k), ss = sg * __ldg(sn + k);
-      re = fma(a, cs, fma(b, ss, re));
-      im = fma(b, cs, fma(-a, ss, im));
+  for (int o = threadIdx.x; o < nth * K1; o += blockDim.x) {
+    const int m = o % K1, j = o / K1;
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    const double* c = P.tc + (size_t)m * nph;
+    const double* sn = P.ts + (size_t)m * nph;
+    const double* fr = f + 2 * j * nph;
+    double ac = 0.0, bs = 0.0, bc = 0.0, as = 0.0;
+    for (int k = 0; k < h; ++k) {
+      const double a = fma(sg, fr[2 * (k + h)], fr[2 * k]);
+      const double b = fma(sg, fr[2 * (k + h) + 1], fr[2 * k + 1]);
+      const double cs = __ldg(c + k), ss = __ldg(sn + k);
+      ac = fma(a, cs, ac);
+      bs = fma(b, ss, bs);
+      bc = fma(b, cs, bc);
+      as = fma(a, ss, as);
     }
-    F[2 * o] = re * inv;
-    F[2 * o + 1] = im * inv;
+    double* Fj = F + 2 * (j * M2 + K);
+    Fj[2 * m] = (ac + bs) * inv;                  // (a + ib) e^{-i m phi}
+    Fj[2 * m + 1] = (bc - as) * inv;
+    Fj[-2 * m] = (ac - bs) * inv;                 // (a + ib) e^{+i m phi}
+    Fj[-2 * m + 1] = (bc + as) * inv;
   }
   __syncthreads();
   const double* Qs = P.Q + (size_t)(sp + 3) * M2 * nth * nth;
-  for (int o = threadIdx.x; o < nth * M2; o += blockDim.x) {
-    const int mi = o % M2, j = o / M2;
-    const double* Qm = Qs + ((size_t)mi * nth + j) * nth;
-    double re = 0.0, im = 0.0;
+  for (int o = threadIdx.x; o < nth * K1; o += blockDim.x) {
+    const int m = o % K1, j = o / K1;
+    const double* Qp = Qs + ((size_t)(K + m) * nth + j) * nth;
+    const double* Qn = Qs + ((size_t)(K - m) * nth + j) * nth;
+    double pr = 0.0, pi = 0.0, nr = 0.0, ni = 0.0;
     for (int i = 0; i < nth; ++i) {
-      const double qv = __ldg(Qm + i);
-      re = fma(qv, F[2 * (i * M2 + mi)], re);
-      im = fma(qv, F[2 * (i * M2 + mi) + 1], im);
+      const double qp = __ldg(Qp + i), qn = __ldg(Qn + i);
+      const double* Fi = F + 2 * (i * M2 + K);
+      pr = fma(qp, Fi[2 * m], pr);
+      pi = fma(qp, Fi[2 * m + 1], pi);
+      nr = fma(qn, Fi[-2 * m], nr);
+      ni = fma(qn, Fi[-2 * m + 1], ni);
     }
-    G[2 * o] = re;
-    G[2 * o + 1] = im;
+    double* q4 = PM + 4 * (j * K1 + m);
+    if (m == 0) {
+      q4[0] = pr;
+      q4[1] = pi;
+      q4[2] = 0.0;
+      q4[3] = 0.0;
+    } else {
+      q4[0] = pr + nr;
+      q4[1] = pi + ni;
+      q4[2] = pr - nr;
+      q4[3] = pi - ni;
+    }
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < na; o += blockDim.x) {
-    const int k = o % nph, j = o / nph;
-    double re = 0.0, im = 0.0;
-    for (int mi = 0; mi < M2; ++mi) {
-      const int m = mi - K, am = m < 0 ? -m : m;
-      const double cs = __ldg(P.tc + (size_t)am * nph + k), ss = (m < 0 ? -1.0 : 1.0) * __ldg(P.ts + (size_t)am * nph + k);
-      const double a = G[2 * (j * M2 + mi)], b = G[2 * (j * M2 + mi) + 1];
-      re = fma(a, cs, fma(-b, ss, re));
-      im = fma(b, cs, fma(a, ss, im));
+  for (int o = threadIdx.x; o < nth * h; o += blockDim.x) {
+    const int k = o % h, j = o / h;
+    // sum_m G_m e^{i m phi} = sum_{m>=0} (G_m + G_-m) cos m phi + i (G_m - G_-m) sin m phi
+    double er = 0.0, ei = 0.0, orr = 0.0, oi = 0.0;
+    const double* q4 = PM + 4 * j * K1;
+    for (int m = 0; m < K1; m += 2) {
+      const double cs = __ldg(P.tc + (size_t)m * nph + k), ss = __ldg(P.ts + (size_t)m * nph + k);
+      er = fma(q4[4 * m], cs, fma(-q4[4 * m + 3], ss, er));
+      ei = fma(q4[4 * m + 1], cs, fma(q4[4 * m + 2], ss, ei));
     }
-    row_ptr[2 * o] = re;
-    row_ptr[2 * o + 1] = im;
+    for (int m = 1; m < K1; m += 2) {
+      const double cs = __ldg(P.tc + (size_t)m * nph + k), ss = __ldg(P.ts + (size_t)m * nph + k);
+      orr = fma(q4[4 * m], cs, fma(-q4[4 * m + 3], ss, orr));
+      oi = fma(q4[4 * m + 1], cs, fma(q4[4 * m + 2], ss, oi));
+    }
+    double* g0 = gp + 2 * (j * nph + k);
+    g0[0] = er + orr;
+    g0[1] = ei + oi;
+    g0[2 * h] = er - orr;
+    g0[2 * h + 1] = ei - oi;
   }
 }
 
@@ -292,37 +447,11 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
                                   const std::vector<std::vector<double>>& gl_w) {
   if (d->tf_buf) return cudaSuccess;
   cudaError_t e;
-  // index tuple -> field, and which tuples are the stored ones
-  int map[9][27];
-  unsigned char wr[9][27];
-  std::memset(map, 0, sizeof(map));
-  std::memset(wr, 0, sizeof(wr));
-  for (int base = 0, g0 = 0; base <= 10; base += 10, g0 += 3) {
-    map[g0][0] = base + sym_index(0, 0);
-    wr[g0][0] = 1;
-    for (int i = 0; i < 3; ++i) {
-      map[g0 + 1][i] = base + sym_index(0, 1 + i);
-      wr[g0 + 1][i] = 1;
-      for (int j = 0; j < 3; ++j) {
-        map[g0 + 2][3 * i + j] = base + sym_index(1 + i, 1 + j);
-        wr[g0 + 2][3 * i + j] = i <= j;
-      }
-    }
-  }
-  for (int i = 0; i < 3; ++i) {
-    map[6][i] = 20 + 10 * i + sym_index(0, 0);
-    wr[6][i] = 1;
-    for (int j = 0; j < 3; ++j) {
-      map[7][3 * i + j] = 20 + 10 * i + sym_index(0, 1 + j);
-      wr[7][3 * i + j] = 1;
-      for (int k = 0; k < 3; ++k) {
-        map[8][9 * i + 3 * j + k] = 20 + 10 * i + sym_index(1 + j, 1 + k);
-        wr[8][9 * i + 3 * j + k] = j <= k;
-      }
-    }
-  }
-  if ((e = cudaMemcpyToSymbol(c_tf_field, map, sizeof(map))) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_tf_write, wr, sizeof(wr))) != cudaSuccess) return e;
+  signed char spin[TF_ROWS];
+  for (int g = 0; g < 9; ++g)
+    for (int o = 0; o < tf_size(g); ++o)
+      if (tf_row(g, o) >= 0) spin[tf_row(g, o)] = (signed char)tf_spin(g, o);
+  if ((e = cudaMemcpyToSymbol(c_tf_spin, spin, sizeof(spin))) != cudaSuccess) return e;
   // per-shell tables, shared between shells of the same (L, keep)
   std::map<std::pair<int, int>, TensorFilterPlan> cache;
   std::vector<int> pb(d->n_shells + 1), rb(d->n_shells + 1);
@@ -335,9 +464,9 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
     np += sh.n_r * ((sh.na + TF_THREADS - 1) / TF_THREADS);
     sh.tf.K = sh.keep;
     if (sh.keep < 0) continue;
-    nr += sh.n_r * TF_SLOTS;
+    nr += sh.n_r * TF_ROWS;
     const int K = sh.keep, M2 = 2 * K + 1, nth = sh.nth, nph = sh.nph;
-    smem = std::max(smem, sizeof(double) * (size_t)(2 * sh.na + 4 * nth * M2));
+    smem = std::max(smem, sizeof(double) * (size_t)(2 * sh.na + 2 * nth * M2 + 4 * nth * (K + 1)));
     const auto key = std::make_pair(sh.L, K);
     if (!cache.count(key)) {
       TensorFilterPlan P{};
@@ -378,7 +507,7 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
   void* p = nullptr;
-  if ((e = cudaMalloc(&p, sizeof(double) * 2 * TF_SLOTS * (size_t)d->points)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&p, sizeof(double) * 2 * TF_ROWS * (size_t)d->points)) != cudaSuccess) return e;
   d->owned.push_back(p);
   d->tf_buf = (double*)p;
   return cudaSuccess;
