@@ -330,6 +330,14 @@ def run_ours(args, w):
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=state_bytes,
                          d2h_bytes_per_step=state_bytes + 8 * len(w.shells)),
                 gpu_launches=launches, roofline=roofline, kernels=kernels)
+    if args.sh_filter == "tensor":
+        tf = costmodel.tensor_filter_flops(w.shells, w.sh_keep_l)
+        f_ms, f_n = fam_ms["angular_filter"]
+        tf_ach = tf["total"] / (f_ms / f_n / 1000.0) / 1e12 if f_n else None
+        line["tensor_filter"] = dict(
+            kernels="tf_frame_kernel + tf_spin_kernel + tf_unframe_kernel", ms_per_step=f_ms / args.steps,
+            flops_per_launch=tf["total"], flops_split={k: tf[k] for k in ("frame", "spin", "unframe")},
+            achieved=tf_ach, peak=peak, unit="TFLOP/s", frac=(tf_ach / peak) if tf_ach else None, bound="alu")
     if clk is not None:
         line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "kerr4":

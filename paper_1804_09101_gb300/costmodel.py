@@ -145,3 +145,72 @@ def family_flops(family, shells, algorithm="folded", keep_l=-1):
     if family == "pointwise":
         return POINTWISE_FLOPS_PER_POINT * pts
     return None
+
+
+# The nine tensor groups of the GH fields (psi_00, psi_0i, psi_ij, Pi_00, Pi_0i,
+# Pi_ij, Phi_i00, Phi_i0j, Phi_ijk): rank, and whether the last two indices are
+# symmetric.
+TENSOR_GROUPS = [(0, False), (1, False), (2, True), (0, False), (1, False), (2, True), (1, False), (2, False),
+                 (3, True)]
+
+
+def tensor_filter_row_spins():
+    """Spin weights of the independent complex frame components (one per class
+    under conjugation m <-> conj(m) and the symmetric index pair)."""
+    import itertools
+    spins = []
+    for rank, sym in TENSOR_GROUPS:
+        tuples = list(itertools.product(range(3), repeat=rank))
+        for t in tuples:
+            variants = []
+            for c in (0, 1):
+                for sw in ((0, 1) if sym else (0,)):
+                    e = list(t)
+                    if sw:
+                        e[-2], e[-1] = e[-1], e[-2]
+                    if c:
+                        e = [0 if a == 0 else 3 - a for a in e]
+                    variants.append(tuple(e))
+            if min(variants) == t:
+                spins.append(sum({0: 0, 1: 1, 2: -1}[a] for a in t))
+    return spins
+
+
+def tensor_filter_flops(shells, keep_l):
+    """FP64 flops (FMA = 2) of one tensor-harmonic filter application
+    (tf_frame_kernel, tf_spin_kernel, tf_unframe_kernel).  Per point, the frame
+    kernels contract each rank-n group index by index in the real frame
+    (8 * 3^(n-1) FMAs per index, the zero phi_hat_z term skipped) and form the
+    complex combinations with additions; per (r, independent component) row of
+    spin s the spin kernel does the quarter fold (16 adds per slot pair), the
+    folded forward DFT (4 W FMAs per ring and m >= 0), the analysis and
+    synthesis (2 N_theta FMAs per coefficient each, sum_m n_b(s, m)
+    coefficients, n_b = K - max(|m|, |s|) + 1) and the folded inverse DFT
+    (4 (K+1) FMAs per ring and slot), W = N_phi/4 + 1."""
+    spins = tensor_filter_row_spins()
+    frame = unframe = spin = 0
+    per_pt_f = per_pt_u = 0
+    for rank, _ in TENSOR_GROUPS:
+        n = 3 ** rank
+        fma = rank * 8 * 3 ** (rank - 1) if rank else 0
+        nz = 2 * 3 ** (rank - 1) if rank else 0          # outputs with a nonzero frame index, per pass
+        per_pt_f += 2 * fma + (rank - 1 if rank else 0) * nz * 2
+        per_pt_u += 2 * fma + rank * nz * 2 + (n - 1)
+    per_pt_f += 2 * len(spins)                            # the 1/sqrt(2) scaling of the stored components
+    for sh in shells:
+        n_r, nth, nph, na = _shell_dims(sh)
+        L = sh[3]
+        K = (2 * L) // 3 if keep_l == -2 else keep_l
+        if K < 0:
+            continue
+        h, W, K1 = nph // 2, nph // 4 + 1, K + 1
+        frame += per_pt_f * n_r * na
+        unframe += per_pt_u * n_r * na
+        fold = nth * (4 + (4 if h % 2 == 0 else 0) + 16 * (W - 1 - (1 if h % 2 == 0 else 0)))
+        fwd = nth * K1 * (8 * W + 8)
+        inv = nth * W * (8 * K1 + 16)
+        for s in spins:
+            ncoef = sum(max(0, K - max(abs(m), abs(s)) + 1) for m in range(-K, K + 1))
+            theta = ncoef * nth * 4 * 2 + nth * K1 * 4
+            spin += n_r * (fold + fwd + theta + inv)
+    return dict(frame=frame, spin=spin, unframe=unframe, total=frame + spin + unframe)

@@ -87,14 +87,21 @@ struct FoldPlan {
   double sigma0, sigma1;        // parity of output 0 / 1 (-1 for d/dtheta, +1 for values)
 };
 
-// Tensor spherical-harmonic filter of one shell (tensor_filter kernels): the
-// spin-s projection onto sY_lm, |s| <= l <= K, after a complex phi DFT is one
-// real N_theta x N_theta map per (s, m).
+// Tensor spherical-harmonic filter of one shell (tensor_filter kernels).  The
+// spin-s projection onto sY_lm, |s| <= l <= K, of a complex function: a phi
+// DFT per ring, then per (s, m) the analysis onto the n_b = K - max(|m|,|s|) + 1
+// orthonormal theta functions and the synthesis back.
 struct TensorFilterPlan {
   int K;                        // keep l <= K (-1: off)
-  const double* Q;              // [7 spins s = -3..3][2K+1 modes m = -K..K][j_out][j_in]
-  const double* tc;             // [K+1][nph] cos(m phi_k)
-  const double* ts;             // [K+1][nph] sin(m phi_k)
+  int W;                        // phi slots of the quarter fold: N_phi / 4 + 1 (k = 0 .. W-1)
+  const double* twc;            // [K+1][W] cos(m phi_k)
+  const double* tws;            // [K+1][W] sin(m phi_k)
+  const double* An;             // per (s, m): [N_theta][n_b] analysis, 2 pi w_i b_n(theta_i)
+  const double* Sy;             // per (s, m): [n_b][N_theta] synthesis, b_n(theta_j)
+  const int* coff;              // [7 spins][2K+1 modes] offset of the (s, m) block in An and Sy
+  const int* cidx;              // [7][2K+1] first coefficient of (s, m) in its spin's packed list
+  const int* ist;               // [8] start of each spin's packed (m + K) << 8 | n items
+  const int* items;
 };
 constexpr int TF_ROWS = 31;     // independent complex frame components per point (9 tensor groups)
 
@@ -220,7 +227,7 @@ struct gh_domain {
   int sh_filter_mode = 0;
   double* tf_buf = nullptr;
   int* tf_pb_d = nullptr;       // tensor-filter launch maps: point blocks, then rows
-  int tf_point_blocks = 0, tf_rows = 0;
+  int tf_point_blocks = 0, tf_rows = 0, tf_spin_threads = 128;
   size_t tf_smem = 0;
   // rotating dual frame (gh_set_rotating_frame): axis, rate, the domain's
   // time, and the frame of the launches being issued

@@ -4,16 +4,18 @@
 // i phi_hat)/sqrt(2), E_2 = conj(m); a frame component c_A = T_I E_A1^I1 ..
 // has spin weight s = #m - #conj(m) and is projected onto the spin-weighted
 // harmonics sY_lm, |s| <= l <= K; the filtered tensor is
-// Re sum_A c'_A conj(E_A1) x .. (conj(E) is the dual basis).  Three kernels:
-//   tf_frame_kernel   per point: the complex components of the 9 tensor groups
+// sum_A c'_A conj(E_A1) x .. (conj(E) is the dual basis).  Three kernels:
+//   tf_frame_kernel   per point: the components of the 9 tensor groups
 //                     (psi_00, psi_0i, psi_ij, the same for Pi, Phi_i00,
-//                     Phi_i0j, Phi_ijk), one index contracted at a time; the
-//                     31 independent ones of the 65 are stored;
-//   tf_spin_kernel    per (r, independent component) row: complex phi DFT
-//                     (m = -K..K), the real N_theta x N_theta map of (s, m),
+//                     Phi_i0j, Phi_ijk) in the real frame (r_hat, theta_hat,
+//                     phi_hat), then the complex combinations; the 31
+//                     independent ones of the 65 are stored;
+//   tf_spin_kernel    per (r, independent component) row: quarter-folded phi
+//                     DFT (m = -K..K), analysis onto and synthesis from the
+//                     spin-weighted theta functions of each (s, m), folded
 //                     inverse DFT;
-//   tf_unframe_kernel per point: all 65 from the 31, back to the Cartesian
-//                     components.
+//   tf_unframe_kernel per point: all 65 from the 31, back to the real frame
+//                     and to the Cartesian components.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -109,64 +111,43 @@ static_assert(tf_row(8, 26) < 0 && tf_row(8, 9 * 1 + 3 * 2 + 2) == TF_ROWS - 1, 
 
 __constant__ signed char c_tf_spin[TF_ROWS];   // spin of each independent row
 
-constexpr int TF_THREADS = 128;
+constexpr int TF_THREADS = 128;        // per-point kernels
+constexpr int TF_SPIN_MAX_THREADS = 128;
 
 struct Cx {
   double re, im;
 };
 
-__device__ __forceinline__ void frame_vectors(const ShellDev& sh, int q, Cx E[3][3]) {
+// Real orthonormal frame e[a][i]: a = 0 r_hat, 1 theta_hat, 2 phi_hat (phi_hat_z = 0).
+__device__ __forceinline__ void real_frame(const ShellDev& sh, int q, double e[3][3]) {
   const int j = q / sh.nph, k = q - j * sh.nph;
   const double st = sh.sth[j], ct = sh.cth[j], sp = sh.sph[k], cp = sh.cph[k];
-  const double rh[3] = {st * cp, st * sp, ct};
-  const double th[3] = {ct * cp, ct * sp, -st};
-  const double ph[3] = {-sp, cp, 0.0};
-  const double h = 0.70710678118654752440;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    E[0][i] = {rh[i], 0.0};
-    E[1][i] = {h * th[i], h * ph[i]};
-    E[2][i] = {h * th[i], -h * ph[i]};
-  }
+  e[0][0] = st * cp; e[0][1] = st * sp; e[0][2] = ct;
+  e[1][0] = ct * cp; e[1][1] = ct * sp; e[1][2] = -st;
+  e[2][0] = -sp;     e[2][1] = cp;      e[2][2] = 0.0;
 }
 
-// Contract every index of a rank-n tensor (3^n values, row-major, first index
-// slowest) with the frame.  Forward (INV = false): Cartesian -> frame,
-// c_..A.. = sum_i E_A^i T_..i.. (T real); inverse: frame -> Cartesian with the
-// dual basis, T_..i.. = sum_A conj(E_A^i) c_..A...  Fully unrolled (t stays
-// in registers); products with a real factor (the input tensor, r_hat, the z
-// component of m) skip the zero imaginary part.
+// Contract every index of a rank-n real tensor (3^n values, row-major, first
+// index slowest) with the real frame: forward R_..a.. = sum_i e_a^i T_..i..,
+// inverse T_..i.. = sum_a e_a^i R_..a...  Fully unrolled (t stays in
+// registers); the zero phi_hat_z term is skipped.
 template <int RANK, bool INV>
-__device__ __forceinline__ void contract(Cx* t, const Cx E[3][3]) {
+__device__ __forceinline__ void contract_real(double* t, const double e[3][3]) {
   constexpr int n = RANK == 0 ? 1 : RANK == 1 ? 3 : RANK == 2 ? 9 : 27;
 #pragma unroll
   for (int k = 0; k < RANK; ++k) {
     const int stride = k == RANK - 1 ? 1 : (k == RANK - 2 ? 3 : 9);
-    Cx w[n];
+    double w[n];
 #pragma unroll
     for (int o = 0; o < n; ++o) {
-      const int Ak = (o / stride) % 3;          // output index
-      const int base = o - Ak * stride;
-      Cx acc = {0.0, 0.0};
+      const int out = (o / stride) % 3;
+      const int base = o - out * stride;
+      double acc = 0.0;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {             // summed index
-        const int a = INV ? i : Ak, x = INV ? Ak : i;
-        const Cx e = INV ? Cx{E[a][x].re, -E[a][x].im} : E[a][x];
-        const bool e_real = a == 0 || x == 2;
-        const bool v_real = !INV && k == 0;
-        const Cx v = t[base + i * stride];
-        if (e_real && v_real) {
-          acc.re = fma(e.re, v.re, acc.re);
-        } else if (e_real) {
-          acc.re = fma(e.re, v.re, acc.re);
-          acc.im = fma(e.re, v.im, acc.im);
-        } else if (v_real) {
-          acc.re = fma(e.re, v.re, acc.re);
-          acc.im = fma(e.im, v.re, acc.im);
-        } else {
-          acc.re = fma(e.re, v.re, fma(-e.im, v.im, acc.re));
-          acc.im = fma(e.re, v.im, fma(e.im, v.re, acc.im));
-        }
+      for (int x = 0; x < 3; ++x) {
+        const int a = INV ? x : out, i = INV ? out : x;
+        if (a == 2 && i == 2) continue;
+        acc = fma(e[a][i], t[base + x * stride], acc);
       }
       w[o] = acc;
     }
@@ -175,66 +156,144 @@ __device__ __forceinline__ void contract(Cx* t, const Cx E[3][3]) {
   }
 }
 
+// Real frame -> complex frame, index by index: A = 0 keeps R_0, A = 1 takes
+// R_1 + i R_2, A = 2 takes R_1 - i R_2 (the 1/sqrt(2) of each m is applied at
+// the store).  Additions only.
+template <int RANK>
+__device__ __forceinline__ void complexify(const double* R, Cx* c) {
+  constexpr int n = RANK == 0 ? 1 : RANK == 1 ? 3 : RANK == 2 ? 9 : 27;
+#pragma unroll
+  for (int o = 0; o < n; ++o) c[o] = {R[o], 0.0};
+#pragma unroll
+  for (int k = 0; k < RANK; ++k) {
+    const int stride = k == RANK - 1 ? 1 : (k == RANK - 2 ? 3 : 9);
+    Cx w[n];
+#pragma unroll
+    for (int o = 0; o < n; ++o) {
+      const int A = (o / stride) % 3;
+      const int base = o - A * stride;
+      const Cx v1 = c[base + stride], v2 = c[base + 2 * stride];
+      if (A == 0) {
+        w[o] = c[base];
+      } else if (k == 0) {                       // inputs still real
+        w[o] = {v1.re, A == 1 ? v2.re : -v2.re};
+      } else if (A == 1) {
+        w[o] = {v1.re - v2.im, v1.im + v2.re};
+      } else {
+        w[o] = {v1.re + v2.im, v1.im - v2.re};
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < n; ++o) c[o] = w[o];
+  }
+}
+
+// Complex frame -> real frame (the dual basis conj(E)), index by index:
+// R_0 = c_0, R_1 = c_1 + c_2, R_2 = i (c_2 - c_1) (1/sqrt(2) at the end); the
+// result is real, only its real part is kept.
+template <int RANK>
+__device__ __forceinline__ void decomplexify(Cx* c, double* R) {
+  constexpr int n = RANK == 0 ? 1 : RANK == 1 ? 3 : RANK == 2 ? 9 : 27;
+#pragma unroll
+  for (int k = 0; k < RANK; ++k) {
+    const int stride = k == RANK - 1 ? 1 : (k == RANK - 2 ? 3 : 9);
+    Cx w[n];
+#pragma unroll
+    for (int o = 0; o < n; ++o) {
+      const int a = (o / stride) % 3;
+      const int base = o - a * stride;
+      const Cx v1 = c[base + stride], v2 = c[base + 2 * stride];
+      if (a == 0)
+        w[o] = c[base];
+      else if (a == 1)
+        w[o] = {v1.re + v2.re, v1.im + v2.im};
+      else
+        w[o] = {v1.im - v2.im, v2.re - v1.re};
+    }
+#pragma unroll
+    for (int o = 0; o < n; ++o) c[o] = w[o];
+  }
+#pragma unroll
+  for (int o = 0; o < n; ++o) R[o] = c[o].re;
+}
+
+// (1/sqrt(2))^(number of m and conj(m) indices of tuple o)
+__host__ __device__ constexpr double tf_scale(int g, int o) {
+  int n = 0;
+  for (int k = 0; k < tf_rank(g); ++k) n += tf_digit(g, o, k) != 0;
+  return n == 0 ? 1.0 : n == 1 ? 0.70710678118654752440 : n == 2 ? 0.5 : 0.35355339059327376220;
+}
+
 // component buffer: per radial slice, TF_ROWS rows of na complex values
 __device__ __forceinline__ long long tf_index(const ShellDev& sh, int ir, int row, int q) {
   return 2LL * ((sh.pt_off + (long long)ir * sh.na) * TF_ROWS + (long long)row * sh.na + q);
 }
 
 template <int G, int O>
-__device__ __forceinline__ void tf_load_u(Cx* t, const double* __restrict__ u, long long ubase, int na) {
-  t[O] = {u[ubase + (long long)tf_field(G, O) * na], 0.0};
+__device__ __forceinline__ void tf_load_u(double* t, const double* __restrict__ u, long long ubase, int na) {
+  t[O] = u[ubase + (long long)tf_field(G, O) * na];
 }
 template <int G, int O>
-__device__ __forceinline__ void tf_store_c(const Cx* t, const ShellDev& sh, int ir, int q, double* __restrict__ cb) {
+__device__ __forceinline__ void tf_store_c(const Cx* c, const ShellDev& sh, int ir, int q, double* __restrict__ cb) {
   constexpr int row = tf_row(G, O);
   if constexpr (row >= 0) {
-    const long long c = tf_index(sh, ir, row, q);
-    cb[c] = t[O].re;
-    cb[c + 1] = t[O].im;
+    constexpr double f = tf_scale(G, O);
+    const long long i = tf_index(sh, ir, row, q);
+    cb[i] = f * c[O].re;
+    cb[i + 1] = f * c[O].im;
   }
 }
 template <int G, int O>
-__device__ __forceinline__ void tf_load_c(Cx* t, const ShellDev& sh, int ir, int q, const double* __restrict__ cb) {
+__device__ __forceinline__ void tf_load_c(Cx* c, const ShellDev& sh, int ir, int q, const double* __restrict__ cb) {
   constexpr int row = tf_row(G, tf_best(G, O));
-  const long long c = tf_index(sh, ir, row, q);
-  t[O] = {cb[c], tf_best_conj(G, O) ? -cb[c + 1] : cb[c + 1]};
+  const long long i = tf_index(sh, ir, row, q);
+  c[O] = {cb[i], tf_best_conj(G, O) ? -cb[i + 1] : cb[i + 1]};
 }
 template <int G, int O>
-__device__ __forceinline__ void tf_store_u(const Cx* t, double* __restrict__ out, long long ubase, int na) {
-  if constexpr (tf_written(G, O)) out[ubase + (long long)tf_field(G, O) * na] = t[O].re;
+__device__ __forceinline__ void tf_scale_r(double* R) {
+  if constexpr (tf_scale(G, O) != 1.0) R[O] *= tf_scale(G, O);
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_store_u(const double* t, double* __restrict__ out, long long ubase, int na) {
+  if constexpr (tf_written(G, O)) out[ubase + (long long)tf_field(G, O) * na] = t[O];
 }
 
 template <int G, int... O>
 __device__ __forceinline__ void frame_group(std::integer_sequence<int, O...>, const ShellDev& sh, int ir, int q,
-                                            const Cx E[3][3], const double* __restrict__ u, long long ubase,
+                                            const double e[3][3], const double* __restrict__ u, long long ubase,
                                             double* __restrict__ cb) {
-  Cx t[sizeof...(O)];
+  double t[sizeof...(O)];
+  Cx c[sizeof...(O)];
   (tf_load_u<G, O>(t, u, ubase, sh.na), ...);
-  contract<tf_rank(G), false>(t, E);
-  (tf_store_c<G, O>(t, sh, ir, q, cb), ...);
+  contract_real<tf_rank(G), false>(t, e);
+  complexify<tf_rank(G)>(t, c);
+  (tf_store_c<G, O>(c, sh, ir, q, cb), ...);
 }
 
 template <int G, int... O>
 __device__ __forceinline__ void unframe_group(std::integer_sequence<int, O...>, const ShellDev& sh, int ir, int q,
-                                              const Cx E[3][3], const double* __restrict__ cb, long long ubase,
+                                              const double e[3][3], const double* __restrict__ cb, long long ubase,
                                               double* __restrict__ out) {
-  Cx t[sizeof...(O)];
-  (tf_load_c<G, O>(t, sh, ir, q, cb), ...);
-  contract<tf_rank(G), true>(t, E);
+  Cx c[sizeof...(O)];
+  double t[sizeof...(O)];
+  (tf_load_c<G, O>(c, sh, ir, q, cb), ...);
+  decomplexify<tf_rank(G)>(c, t);
+  (tf_scale_r<G, O>(t), ...);
+  contract_real<tf_rank(G), true>(t, e);
   (tf_store_u<G, O>(t, out, ubase, sh.na), ...);
 }
 
 template <int... G>
 __device__ __forceinline__ void frame_all(std::integer_sequence<int, G...>, const ShellDev& sh, int ir, int q,
-                                          const Cx E[3][3], const double* __restrict__ u, long long ub,
+                                          const double e[3][3], const double* __restrict__ u, long long ub,
                                           double* __restrict__ cb) {
-  (frame_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, E, u, ub, cb), ...);
+  (frame_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, e, u, ub, cb), ...);
 }
 template <int... G>
 __device__ __forceinline__ void unframe_all(std::integer_sequence<int, G...>, const ShellDev& sh, int ir, int q,
-                                            const Cx E[3][3], const double* __restrict__ cb, long long ub,
+                                            const double e[3][3], const double* __restrict__ cb, long long ub,
                                             double* __restrict__ out) {
-  (unframe_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, E, cb, ub, out), ...);
+  (unframe_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, e, cb, ub, out), ...);
 }
 
 __global__ void __launch_bounds__(TF_THREADS)
@@ -248,10 +307,10 @@ tf_frame_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __
   const int ir = lb / bps;
   const int q = (lb - ir * bps) * TF_THREADS + threadIdx.x;
   if (q >= na) return;
-  Cx E[3][3];
-  frame_vectors(sh, q, E);
+  double e[3][3];
+  real_frame(sh, q, e);
   const long long ub = sh.off + (long long)ir * NF * na + q;
-  frame_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, E, u, ub, cb);
+  frame_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, e, u, ub, cb);
 }
 
 __global__ void __launch_bounds__(TF_THREADS)
@@ -265,133 +324,219 @@ tf_unframe_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* 
   const int ir = lb / bps;
   const int q = (lb - ir * bps) * TF_THREADS + threadIdx.x;
   if (q >= na) return;
-  Cx E[3][3];
-  frame_vectors(sh, q, E);
+  double e[3][3];
+  real_frame(sh, q, e);
   const long long ub = sh.off + (long long)ir * NF * na + q;
-  unframe_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, E, cb, ub, out);
+  unframe_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, e, cb, ub, out);
+}
+
+__device__ __forceinline__ int tf_nb(int K, int s, int m) {
+  const int am = m < 0 ? -m : m, as = s < 0 ? -s : s;
+  const int n = K - (am > as ? am : as) + 1;
+  return n > 0 ? n : 0;
+}
+
+// Shared-memory doubles of the spin kernel for one shell.
+__host__ __device__ inline int tf_spin_smem_doubles(int nth, int K, int W) {
+  const int K1 = K + 1, M2 = 2 * K + 1, nthp = nth | 1;
+  const int ab = 8 * W * nthp, pm = 4 * nth * K1;
+  return 2 * K1 * W + (ab > pm ? ab : pm) + 2 * nth * M2 + 2 * K1 * K1;
 }
 
 // One independent component row of one radial slice: the projection onto
-// sY_lm, |s| <= l <= K, of a complex function on the (theta, phi) grid:
-//   F_m(theta_i) = (1/N_phi) sum_k f(theta_i, phi_k) e^{-i m phi_k},  |m| <= K
-//   G_m(theta_j) = sum_i Q^{s,m}[j][i] F_m(theta_i)
+// sY_lm, |s| <= l <= K, of a complex function f on the (theta, phi) grid.
+//   F_m(theta_i) = (1/N_phi) sum_k f(theta_i, phi_k) e^{-i m phi_k},  |m| <= K,
+//   a_n = sum_i 2 pi w_i b_n(theta_i) F_m(theta_i),  G_m(theta_j) = sum_n b_n(theta_j) a_n
+//   (b_n the orthonormal theta functions of (s, m)),
 //   f'(theta_j, phi_k) = sum_m G_m(theta_j) e^{i m phi_k}.
-// phi_{k+N/2} = phi_k + pi multiplies e^{i m phi} by (-1)^m (half-period fold
-// of both transforms), and +m, -m share their cos / sin products.
-__global__ void __launch_bounds__(TF_THREADS)
+// Both phi transforms are quarter-folded: phi + pi multiplies e^{i m phi} by
+// (-1)^m and pi - phi maps it to (-1)^m e^{-i m phi}, so slots k and h - k
+// (h = N_phi/2) share one cos/sin pair, and +m, -m share their products.
+// Items are laid out so that the lanes of a warp have equal trip counts.
+__global__ void __launch_bounds__(TF_SPIN_MAX_THREADS)
 tf_spin_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                double* __restrict__ cb) {
   extern __shared__ double sm[];
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const TensorFilterPlan& P = sh.tf;
-  const int na = sh.na, nth = sh.nth, nph = sh.nph, h = nph / 2, K = P.K, M2 = 2 * K + 1, K1 = K + 1;
+  const int nth = sh.nth, nph = sh.nph, h = nph / 2, K = P.K, M2 = 2 * K + 1, K1 = K + 1, W = P.W;
+  const int nthp = nth | 1;
   const int rr = blockIdx.x - begin[s];           // (ir, row)
   const int row = rr % TF_ROWS;
   const int ir = rr / TF_ROWS;
   const int sp = c_tf_spin[row];
-  double* f = sm;                                 // [na][2]
-  double* F = f + 2 * na;                         // [nth][M2][2], m = -K..K
-  double* PM = F + 2 * nth * M2;                  // [nth][K1][4]: G_m + G_-m, G_m - G_-m
+  const int sb = (sp + 3) * M2;
+  double* TC = sm;                                // [K1][W]
+  double* TS = TC + K1 * W;                       // [K1][W]
+  double* AB = TS + K1 * W;                       // [p][A.re A.im B.re B.im][W][nthp]
+  double* PM = AB;                                // later [m][P.re P.im M.re M.im][nth]
+  const int r1 = 8 * W * nthp > 4 * nth * K1 ? 8 * W * nthp : 4 * nth * K1;
+  double* F = AB + r1;                            // [M2][re, im][nth], m = -K..K
+  double* AC = F + 2 * nth * M2;                  // [packed item][2]
   double* gp = cb + tf_index(sh, ir, row, 0);
-  for (int i = threadIdx.x; i < 2 * na; i += blockDim.x) f[i] = gp[i];
+  for (int i = threadIdx.x; i < K1 * W; i += blockDim.x) {
+    TC[i] = __ldg(P.twc + i);
+    TS[i] = __ldg(P.tws + i);
+  }
+  // fold: g^p_k = f_k + (-1)^p f_{k+h};  A^p_k = g^p_k + (-1)^p g^p_{h-k},
+  // B^p_k = g^p_k - (-1)^p g^p_{h-k} (k = 0: A = g, B = 0; 2k = h: A = B = g)
+  for (int o = threadIdx.x; o < nth * W; o += blockDim.x) {
+    const int k = o % W, j = o / W;
+    const double* fj = gp + 2 * j * nph;
+    const double ar = fj[2 * k], ai = fj[2 * k + 1], br = fj[2 * (k + h)], bi = fj[2 * (k + h) + 1];
+    double A0r = ar + br, A0i = ai + bi, A1r = ar - br, A1i = ai - bi;
+    double B0r = 0.0, B0i = 0.0, B1r = 0.0, B1i = 0.0;
+    if (2 * k == h) {
+      B0r = A0r; B0i = A0i; B1r = A1r; B1i = A1i;
+    } else if (k > 0) {
+      const int k2 = h - k;
+      const double cr = fj[2 * k2], ci = fj[2 * k2 + 1], dr = fj[2 * (k2 + h)], di = fj[2 * (k2 + h) + 1];
+      const double g0r = cr + dr, g0i = ci + di, g1r = cr - dr, g1i = ci - di;
+      B0r = A0r - g0r; B0i = A0i - g0i; A0r += g0r; A0i += g0i;
+      B1r = A1r + g1r; B1i = A1i + g1i; A1r -= g1r; A1i -= g1i;
+    }
+    double* a0 = AB + (size_t)k * nthp + j;
+    const int cs = W * nthp;                      // stride between the 8 arrays
+    a0[0 * cs] = A0r; a0[1 * cs] = A0i; a0[2 * cs] = B0r; a0[3 * cs] = B0i;
+    a0[4 * cs] = A1r; a0[5 * cs] = A1i; a0[6 * cs] = B1r; a0[7 * cs] = B1i;
+  }
   __syncthreads();
+  // forward: F_{+-m} = (1/N) (sum_k A^p_k c_mk -+ i sum_k B^p_k s_mk), p = m mod 2
   const double inv = 1.0 / nph;
   for (int o = threadIdx.x; o < nth * K1; o += blockDim.x) {
-    const int m = o % K1, j = o / K1;
-    const double sg = (m & 1) ? -1.0 : 1.0;
-    const double* c = P.tc + (size_t)m * nph;
-    const double* sn = P.ts + (size_t)m * nph;
-    const double* fr = f + 2 * j * nph;
-    double ac = 0.0, bs = 0.0, bc = 0.0, as = 0.0;
-    for (int k = 0; k < h; ++k) {
-      const double a = fma(sg, fr[2 * (k + h)], fr[2 * k]);
-      const double b = fma(sg, fr[2 * (k + h) + 1], fr[2 * k + 1]);
-      const double cs = __ldg(c + k), ss = __ldg(sn + k);
-      ac = fma(a, cs, ac);
-      bs = fma(b, ss, bs);
-      bc = fma(b, cs, bc);
-      as = fma(a, ss, as);
+    const int j = o % nth, m = o / nth;
+    const int cs = W * nthp;
+    const double* ab = AB + (size_t)(m & 1) * 4 * cs + j;
+    const double* tc = TC + m * W;
+    const double* ts = TS + m * W;
+    double acr = 0.0, aci = 0.0, bsr = 0.0, bsi = 0.0;
+    for (int k = 0; k < W; ++k) {
+      const double c = tc[k], sn = ts[k];
+      const double* a = ab + (size_t)k * nthp;
+      acr = fma(a[0], c, acr);
+      aci = fma(a[cs], c, aci);
+      bsr = fma(a[2 * cs], sn, bsr);
+      bsi = fma(a[3 * cs], sn, bsi);
     }
-    double* Fj = F + 2 * (j * M2 + K);
-    Fj[2 * m] = (ac + bs) * inv;                  // (a + ib) e^{-i m phi}
-    Fj[2 * m + 1] = (bc - as) * inv;
-    Fj[-2 * m] = (ac - bs) * inv;                 // (a + ib) e^{+i m phi}
-    Fj[-2 * m + 1] = (bc + as) * inv;
+    double* Fp = F + (size_t)(K + m) * 2 * nth + j;
+    double* Fn = F + (size_t)(K - m) * 2 * nth + j;
+    Fp[0] = (acr + bsi) * inv;
+    Fp[nth] = (aci - bsr) * inv;
+    if (m > 0) {
+      Fn[0] = (acr - bsi) * inv;
+      Fn[nth] = (aci + bsr) * inv;
+    }
   }
   __syncthreads();
-  const double* Qs = P.Q + (size_t)(sp + 3) * M2 * nth * nth;
+  // analysis: one packed item (m, n) per thread, N_theta terms each
+  {
+    const int i0 = __ldg(P.ist + sp + 3), n_it = __ldg(P.ist + sp + 4) - i0;
+    for (int o = threadIdx.x; o < n_it; o += blockDim.x) {
+      const int v = __ldg(P.items + i0 + o), mi = v >> 8, n = v & 255;
+      const int nb = tf_nb(K, sp, mi - K);
+      const double* an = P.An + __ldg(P.coff + sb + mi) + n;
+      const double* Fm = F + (size_t)mi * 2 * nth;
+      double re = 0.0, im = 0.0;
+      for (int i = 0; i < nth; ++i) {
+        const double a = __ldg(an + (size_t)i * nb);
+        re = fma(a, Fm[i], re);
+        im = fma(a, Fm[nth + i], im);
+      }
+      AC[2 * o] = re;
+      AC[2 * o + 1] = im;
+    }
+  }
+  __syncthreads();
+  // synthesis of G_{+m}, G_{-m} on every ring, stored as P = G_m + G_-m, M = G_m - G_-m
   for (int o = threadIdx.x; o < nth * K1; o += blockDim.x) {
-    const int m = o % K1, j = o / K1;
-    const double* Qp = Qs + ((size_t)(K + m) * nth + j) * nth;
-    const double* Qn = Qs + ((size_t)(K - m) * nth + j) * nth;
+    const int j = o % nth, m = o / nth;
+    const int nb = tf_nb(K, sp, m);
     double pr = 0.0, pi = 0.0, nr = 0.0, ni = 0.0;
-    for (int i = 0; i < nth; ++i) {
-      const double qp = __ldg(Qp + i), qn = __ldg(Qn + i);
-      const double* Fi = F + 2 * (i * M2 + K);
-      pr = fma(qp, Fi[2 * m], pr);
-      pi = fma(qp, Fi[2 * m + 1], pi);
-      nr = fma(qn, Fi[-2 * m], nr);
-      ni = fma(qn, Fi[-2 * m + 1], ni);
+    {
+      const double* sy = P.Sy + __ldg(P.coff + sb + K + m) + j;
+      const double* ac = AC + 2 * __ldg(P.cidx + sb + K + m);
+      for (int n = 0; n < nb; ++n) {
+        const double b = __ldg(sy + (size_t)n * nth);
+        pr = fma(b, ac[2 * n], pr);
+        pi = fma(b, ac[2 * n + 1], pi);
+      }
     }
-    double* q4 = PM + 4 * (j * K1 + m);
-    if (m == 0) {
-      q4[0] = pr;
-      q4[1] = pi;
-      q4[2] = 0.0;
-      q4[3] = 0.0;
-    } else {
-      q4[0] = pr + nr;
-      q4[1] = pi + ni;
-      q4[2] = pr - nr;
-      q4[3] = pi - ni;
+    if (m > 0) {
+      const double* sy = P.Sy + __ldg(P.coff + sb + K - m) + j;
+      const double* ac = AC + 2 * __ldg(P.cidx + sb + K - m);
+      for (int n = 0; n < nb; ++n) {
+        const double b = __ldg(sy + (size_t)n * nth);
+        nr = fma(b, ac[2 * n], nr);
+        ni = fma(b, ac[2 * n + 1], ni);
+      }
     }
+    double* pm = PM + (size_t)m * 4 * nth + j;
+    pm[0] = pr + nr;
+    pm[nth] = pi + ni;
+    pm[2 * nth] = pr - nr;
+    pm[3 * nth] = pi - ni;
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < nth * h; o += blockDim.x) {
-    const int k = o % h, j = o / h;
-    // sum_m G_m e^{i m phi} = sum_{m>=0} (G_m + G_-m) cos m phi + i (G_m - G_-m) sin m phi
-    double er = 0.0, ei = 0.0, orr = 0.0, oi = 0.0;
-    const double* q4 = PM + 4 * j * K1;
+  // inverse: sum_m G_m e^{i m phi} = sum_{m>=0} P_m cos m phi + i M_m sin m phi,
+  // split into even / odd m and cos / sin parts for the four slots k, k + h,
+  // h - k, 2h - k
+  for (int o = threadIdx.x; o < nth * W; o += blockDim.x) {
+    const int k = o % W, j = o / W;
+    double cer = 0.0, cei = 0.0, ser = 0.0, sei = 0.0, cor = 0.0, coi = 0.0, sor = 0.0, soi = 0.0;
     for (int m = 0; m < K1; m += 2) {
-      const double cs = __ldg(P.tc + (size_t)m * nph + k), ss = __ldg(P.ts + (size_t)m * nph + k);
-      er = fma(q4[4 * m], cs, fma(-q4[4 * m + 3], ss, er));
-      ei = fma(q4[4 * m + 1], cs, fma(q4[4 * m + 2], ss, ei));
+      const double c = TC[m * W + k], sn = TS[m * W + k];
+      const double* pm = PM + (size_t)m * 4 * nth + j;
+      cer = fma(pm[0], c, cer);
+      cei = fma(pm[nth], c, cei);
+      ser = fma(-pm[3 * nth], sn, ser);
+      sei = fma(pm[2 * nth], sn, sei);
     }
     for (int m = 1; m < K1; m += 2) {
-      const double cs = __ldg(P.tc + (size_t)m * nph + k), ss = __ldg(P.ts + (size_t)m * nph + k);
-      orr = fma(q4[4 * m], cs, fma(-q4[4 * m + 3], ss, orr));
-      oi = fma(q4[4 * m + 1], cs, fma(q4[4 * m + 2], ss, oi));
+      const double c = TC[m * W + k], sn = TS[m * W + k];
+      const double* pm = PM + (size_t)m * 4 * nth + j;
+      cor = fma(pm[0], c, cor);
+      coi = fma(pm[nth], c, coi);
+      sor = fma(-pm[3 * nth], sn, sor);
+      soi = fma(pm[2 * nth], sn, soi);
     }
-    double* g0 = gp + 2 * (j * nph + k);
-    g0[0] = er + orr;
-    g0[1] = ei + oi;
-    g0[2 * h] = er - orr;
-    g0[2 * h + 1] = ei - oi;
+    double* g = gp + 2 * j * nph;
+    const double er = cer + ser, ei = cei + sei, fr = cer - ser, fi = cei - sei;   // even: C + S, C - S
+    const double orr = cor + sor, oi = coi + soi, qr = cor - sor, qi = coi - soi;  // odd
+    g[2 * k] = er + orr;
+    g[2 * k + 1] = ei + oi;
+    g[2 * (k + h)] = er - orr;
+    g[2 * (k + h) + 1] = ei - oi;
+    if (k > 0 && 2 * k != h) {
+      g[2 * (h - k)] = fr - qr;
+      g[2 * (h - k) + 1] = fi - qi;
+      g[2 * (nph - k)] = fr + qr;
+      g[2 * (nph - k) + 1] = fi + qi;
+    }
   }
 }
 
 namespace {
 
-// Orthonormal basis of the spin-s, azimuthal-m harmonics sY_lm, l0 <= l <= K
-// (l0 = max(|m|, |s|)), in theta: with x = cos(theta) they span
-// sin(theta/2)^|s+m| cos(theta/2)^|m-s| p(x), deg p <= K - l0, and the p are
-// the Jacobi polynomials P_n^(|s+m|, |m-s|) (their weight is the square of the
-// prefactor).  Built by the Jacobi three-term recurrence and normalised under
-// the Gauss-Legendre quadrature, which integrates these products exactly.  The
-// projection kernel sum_l y_l(j) y_l(i) does not depend on the phase convention
-// of the harmonics.
-void spin_theta_map(int s, int m, int K, const std::vector<double>& x, const std::vector<double>& w,
-                    double* Q) {
+// Orthonormal basis b_n(theta), n < n_b = K - l0 + 1 (l0 = max(|m|, |s|)), of
+// the theta parts of the spin-s, azimuthal-m harmonics sY_lm, l0 <= l <= K:
+// with x = cos(theta) they span sin(theta/2)^|s+m| cos(theta/2)^|m-s| p(x),
+// deg p <= K - l0, and the p are the Jacobi polynomials P_n^(|s+m|, |m-s|)
+// (their weight is the square of the prefactor).  Built by the Jacobi
+// three-term recurrence and normalised under <f, g> = 2 pi sum_i w_i f_i g_i
+// (Gauss-Legendre, exact for these products).  The projection sum_n b_n b_n
+// does not depend on the phase convention of the harmonics.  B: [n_b][N_theta].
+int spin_theta_basis(int s, int m, int K, const std::vector<double>& x, const std::vector<double>& w,
+                     std::vector<long double>& B) {
   const int nth = (int)x.size();
   const int am = m < 0 ? -m : m, as = s < 0 ? -s : s;
   const int l0 = am > as ? am : as;
-  for (int q = 0; q < nth * nth; ++q) Q[q] = 0.0;
-  if (l0 > K) return;
+  B.clear();
+  if (l0 > K) return 0;
   const int nb = K - l0 + 1;
   const long double a = std::abs(s + m), b = std::abs(m - s);
   const long double two_pi = 6.283185307179586476925286766559L;
-  std::vector<long double> B((size_t)nb * nth);
+  B.assign((size_t)nb * nth, 0.0L);
   for (int j = 0; j < nth; ++j) {
     const long double xj = x[j];
     const long double pre = std::pow((1.0L - xj) / 2.0L, a / 2.0L) * std::pow((1.0L + xj) / 2.0L, b / 2.0L);
@@ -408,8 +553,8 @@ void spin_theta_map(int s, int m, int K, const std::vector<double>& x, const std
       B[(size_t)n * nth + j] = pre * p2;
     }
   }
-  // modified Gram-Schmidt under <f, g> = 2 pi sum_i w_i f_i g_i (the basis is
-  // orthogonal already; this normalises it and removes rounding)
+  // modified Gram-Schmidt (the basis is orthogonal already; this normalises
+  // it and removes rounding)
   for (int n = 0; n < nb; ++n) {
     long double* bn = &B[(size_t)n * nth];
     for (int k = 0; k < n; ++k) {
@@ -423,12 +568,7 @@ void spin_theta_map(int s, int m, int K, const std::vector<double>& x, const std
     const long double inv = 1.0L / std::sqrt(nn);
     for (int i = 0; i < nth; ++i) bn[i] *= inv;
   }
-  for (int j = 0; j < nth; ++j)
-    for (int i = 0; i < nth; ++i) {
-      long double acc = 0.0L;
-      for (int n = 0; n < nb; ++n) acc += B[(size_t)n * nth + j] * B[(size_t)n * nth + i];
-      Q[(size_t)j * nth + i] = (double)(two_pi * w[i] * acc);
-    }
+  return nb;
 }
 
 template <typename T>
@@ -455,7 +595,7 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
   // per-shell tables, shared between shells of the same (L, keep)
   std::map<std::pair<int, int>, TensorFilterPlan> cache;
   std::vector<int> pb(d->n_shells + 1), rb(d->n_shells + 1);
-  int np = 0, nr = 0;
+  int np = 0, nr = 0, max_items = 0;
   size_t smem = 0;
   for (int s = 0; s < d->n_shells; ++s) {
     ShellDev& sh = d->shells_h[s];
@@ -465,30 +605,60 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
     sh.tf.K = sh.keep;
     if (sh.keep < 0) continue;
     nr += sh.n_r * TF_ROWS;
-    const int K = sh.keep, M2 = 2 * K + 1, nth = sh.nth, nph = sh.nph;
-    smem = std::max(smem, sizeof(double) * (size_t)(2 * sh.na + 2 * nth * M2 + 4 * nth * (K + 1)));
+    const int K = sh.keep, M2 = 2 * K + 1, K1 = K + 1, nth = sh.nth, nph = sh.nph, W = nph / 4 + 1;
+    smem = std::max(smem, sizeof(double) * (size_t)tf_spin_smem_doubles(nth, K, W));
+    max_items = std::max(max_items, nth * K1);
     const auto key = std::make_pair(sh.L, K);
     if (!cache.count(key)) {
       TensorFilterPlan P{};
       P.K = K;
-      std::vector<double> Q((size_t)7 * M2 * nth * nth);
-      for (int sp = -3; sp <= 3; ++sp)
-        for (int m = -K; m <= K; ++m)
-          spin_theta_map(sp, m, K, gl_x[s], gl_w[s], &Q[((size_t)(sp + 3) * M2 + (m + K)) * nth * nth]);
-      std::vector<double> tc((size_t)(K + 1) * nph), ts((size_t)(K + 1) * nph);
+      P.W = W;
+      std::vector<double> twc((size_t)K1 * W), tws((size_t)K1 * W);
       for (int m = 0; m <= K; ++m)
-        for (int k = 0; k < nph; ++k) {
+        for (int k = 0; k < W; ++k) {
           const double ang = 2.0 * 3.14159265358979323846 * (double)((m * k) % nph) / nph;
-          tc[(size_t)m * nph + k] = std::cos(ang);
-          ts[(size_t)m * nph + k] = std::sin(ang);
+          twc[(size_t)m * W + k] = std::cos(ang);
+          tws[(size_t)m * W + k] = std::sin(ang);
         }
+      std::vector<double> An, Sy;
+      std::vector<int> coff(7 * M2), cidx(7 * M2), ist(8), items;
+      std::vector<long double> B;
+      const long double two_pi = 6.283185307179586476925286766559L;
+      for (int sp = -3; sp <= 3; ++sp) {
+        ist[sp + 3] = (int)items.size();
+        int c = 0;
+        for (int m = -K; m <= K; ++m) {
+          const int nb = spin_theta_basis(sp, m, K, gl_x[s], gl_w[s], B);
+          coff[(sp + 3) * M2 + m + K] = (int)An.size();
+          cidx[(sp + 3) * M2 + m + K] = c;
+          for (int i = 0; i < nth; ++i)
+            for (int n = 0; n < nb; ++n) An.push_back((double)(two_pi * gl_w[s][i] * B[(size_t)n * nth + i]));
+          for (int n = 0; n < nb; ++n)
+            for (int j = 0; j < nth; ++j) Sy.push_back((double)B[(size_t)n * nth + j]);
+          for (int n = 0; n < nb; ++n) items.push_back(((m + K) << 8) | n);
+          c += nb;
+        }
+      }
+      ist[7] = (int)items.size();
+      std::vector<int> ints(coff);
+      ints.insert(ints.end(), cidx.begin(), cidx.end());
+      ints.insert(ints.end(), ist.begin(), ist.end());
+      ints.insert(ints.end(), items.begin(), items.end());
       double* p = nullptr;
-      if ((e = tf_upload(d, Q, &p)) != cudaSuccess) return e;
-      P.Q = p;
-      if ((e = tf_upload(d, tc, &p)) != cudaSuccess) return e;
-      P.tc = p;
-      if ((e = tf_upload(d, ts, &p)) != cudaSuccess) return e;
-      P.ts = p;
+      int* q = nullptr;
+      if ((e = tf_upload(d, twc, &p)) != cudaSuccess) return e;
+      P.twc = p;
+      if ((e = tf_upload(d, tws, &p)) != cudaSuccess) return e;
+      P.tws = p;
+      if ((e = tf_upload(d, An, &p)) != cudaSuccess) return e;
+      P.An = p;
+      if ((e = tf_upload(d, Sy, &p)) != cudaSuccess) return e;
+      P.Sy = p;
+      if ((e = tf_upload(d, ints, &q)) != cudaSuccess) return e;
+      P.coff = q;
+      P.cidx = q + 7 * M2;
+      P.ist = q + 14 * M2;
+      P.items = q + 14 * M2 + 8;
       cache[key] = P;
     }
     sh.tf = cache[key];
@@ -501,6 +671,7 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
   d->tf_point_blocks = np;
   d->tf_rows = nr;
   d->tf_smem = smem;
+  d->tf_spin_threads = max_items >= 4 * TF_SPIN_MAX_THREADS ? TF_SPIN_MAX_THREADS : TF_SPIN_MAX_THREADS / 2;
   static size_t spin_smem = 0;
   if ((e = raise_smem_limit((const void*)tf_spin_kernel, smem, &spin_smem)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(ShellDev) * d->shells_h.size(),
@@ -521,7 +692,8 @@ cudaError_t launch_tensor_filter(gh_domain* d, const double* in, double* out) {
   d->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (d->tf_rows > 0) {
-    tf_spin_kernel<<<d->tf_rows, TF_THREADS, d->tf_smem, d->stream>>>(d->shells_d, n, d->tf_pb_d + n + 1, d->tf_buf);
+    tf_spin_kernel<<<d->tf_rows, d->tf_spin_threads, d->tf_smem, d->stream>>>(d->shells_d, n, d->tf_pb_d + n + 1,
+                                                                             d->tf_buf);
     d->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -38,3 +38,17 @@ def test_singlebh_polynomials_match_paper():
 
 def test_bbh_polynomials_match_paper():
     _check_family(costmodel.bbh_grid, "bbh_polynomials")
+
+
+def test_tensor_filter_components_and_flops():
+    """31 independent complex components (9 groups: 1 + 2 + 4 for psi and Pi,
+    2 + 5 + 10 for Phi), spins within [-3, 3], 14 of spin 0 (1 + 1 + 2 for psi
+    and Pi; 1, 2 and 3 for Phi_i00, Phi_i0j, Phi_ijk); the flop count grows
+    with the radial points and vanishes without a filter."""
+    spins = costmodel.tensor_filter_row_spins()
+    assert len(spins) == 31
+    assert max(abs(s) for s in spins) == 3 and spins.count(0) == 14
+    a = costmodel.tensor_filter_flops([(1.0, 2.0, 5, 7)], 4)
+    b = costmodel.tensor_filter_flops([(1.0, 2.0, 10, 7)], 4)
+    assert b["total"] == 2 * a["total"] and a["spin"] > 0 and a["frame"] > 0
+    assert costmodel.tensor_filter_flops([(1.0, 2.0, 5, 7)], -1)["total"] == 0
