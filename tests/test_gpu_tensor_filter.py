@@ -175,3 +175,46 @@ def test_graph_mode_switch_and_adjoint():
     gh.gh_apply_filters(dom, back, dom.new_work())
     torch.cuda.synchronize()
     assert torch.equal(back, comp)
+
+
+def test_dp5_attempt_matches_oracle():
+    """One Dormand-Prince 5(4) attempt with the tensor filter after it."""
+    from oracle import dp5 as odp5
+    gh = _gh()
+    w = CASES["two_shells_keep4"]()
+    odom = oracle_domain(w)
+    odom.sh_filter = "tensor"
+    u0 = oracle_initial_state(w, odom)
+    dom = _tensor_domain(w, odom)
+    u = to_dev(flat(u0))
+    work = torch.zeros(dom.dp5_work_size, dtype=torch.float64, device="cuda")
+    err, ok, dtn = gh.gh_dp5_step(dom, w.dt, 1e-8, 1e-8, u, work)
+    ou, oerr, ook, odtn = odp5.dp5_step(odom, u0, w.dt, 1e-8, 1e-8)
+    assert ok == ook and ok
+    assert abs(err - oerr) <= 1e-9 * max(1.0, abs(oerr))
+    assert np.abs(to_host(u) - flat(ou)).max() <= REL_TOL * np.abs(flat(u0)).max()
+
+
+def test_holes_of_different_resolution_in_one_domain():
+    """Three holes of L = 7, 11 and 5 (plans with different K, shared memory
+    and items in one launch): each hole's part equals the oracle's tensor
+    filter (floor(2L/3) per hole, radial filter on) of that hole alone."""
+    gh = _gh()
+    holes = [dict(M=1.0, chi=0.3, shells=[(1.6, 8.0, 9, 7)]),
+             dict(M=0.7, chi=0.8, shells=[(0.9, 3.0, 7, 11), (3.0, 9.0, 7, 11)]),
+             dict(M=1.5, chi=0.0, shells=[(2.5, 20.0, 11, 5)])]
+    shells = [s + (b,) for b, h in enumerate(holes) for s in h["shells"]]
+    dom = gh.Domain(shells, radial_filter_on=True, sh_keep_l=-2)
+    gh.gh_set_sh_filter(dom, "tensor")
+    x = np.random.default_rng(77).standard_normal(dom.state_size)
+    u = to_dev(x)
+    gh.gh_apply_filters(dom, u, dom.new_work())
+    got = to_host(u)
+    off = 0
+    for h in holes:
+        odom = evolve.Domain(h["shells"], h["M"], h["chi"], radial_filter_on=True, sh_keep_l=-2,
+                             sh_filter="tensor")
+        n = 50 * sum(nr * 2 * (L + 1) ** 2 for (_, _, nr, L) in h["shells"])
+        ref = flat(evolve.apply_filters(odom, unflat(x[off:off + n], odom)))
+        assert np.abs(got[off:off + n] - ref).max() <= REL_TOL * np.abs(x[off:off + n]).max(), h
+        off += n
