@@ -318,9 +318,10 @@ gh_status gh_set_outer_bc(gh_domain* dom, int mode);
  *   frame.  keep is the domain's sh_keep_l (per shell for -2).  Uses a device
  *   buffer of 62 doubles per grid point (the 31 independent complex frame
  *   components), allocated by the first switch to this mode (GH_ECUDA if it
- *   does not fit).  The adjoint entry points return
- *   GH_ENOTSUP in this mode.  Synchronises the stream and discards a captured
- *   RK4 graph; GH_EINVAL for an unknown mode. */
+ *   does not fit).  The adjoint entry points use the filter's transpose (the
+ *   spin projection is self-adjoint under the quadrature weights).
+ *   Synchronises the stream and discards a captured RK4 graph; GH_EINVAL for
+ *   an unknown mode. */
 enum { GH_SH_FILTER_COMPONENT = 0, GH_SH_FILTER_TENSOR = 1 };
 gh_status gh_set_sh_filter(gh_domain* dom, int mode);
 

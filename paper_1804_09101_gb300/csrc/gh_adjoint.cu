@@ -423,8 +423,6 @@ gh_status adj_ready(gh_domain* d) {
   if (d->outer_bc != 0)
     return afail(d, GH_ENOTSUP, "the adjoint is built for the freezing outer boundary condition only");
   if (d->rot_omega != 0.0) return afail(d, GH_ENOTSUP, "the adjoint is built for a static grid only");
-  if (d->sh_filter_mode != GH_SH_FILTER_COMPONENT)
-    return afail(d, GH_ENOTSUP, "the adjoint is built for the per-component angular filter only");
   if (!d->kbt) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));
@@ -655,10 +653,14 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
   // transposed filters: u_new = Fa(Fr(v))  =>  g = Fr^T Fa^T ubar_np1
   const double* gin = ubar_np1;
   if (d->params.sh_keep_l != -1) {
-    gh::sep_adjoint_kernel<false><<<d->sfa_blocks, gh::SEPA_THREADS, d->sfa_smem, d->stream>>>(
-        d->shells_d, d->n_shells, d->sfa_block_begin_d, gin, nullptr, g);
-    d->launches++;
-    GH_ACUDA(d, cudaGetLastError());
+    if (d->sh_filter_mode == GH_SH_FILTER_TENSOR) {
+      GH_ACUDA(d, gh::launch_tensor_filter_transpose(d, gin, g));
+    } else {
+      gh::sep_adjoint_kernel<false><<<d->sfa_blocks, gh::SEPA_THREADS, d->sfa_smem, d->stream>>>(
+          d->shells_d, d->n_shells, d->sfa_block_begin_d, gin, nullptr, g);
+      d->launches++;
+      GH_ACUDA(d, cudaGetLastError());
+    }
     gin = g;
   }
   if (d->params.radial_filter_on) {

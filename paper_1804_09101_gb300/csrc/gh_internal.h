@@ -266,6 +266,8 @@ cudaError_t fold_set_smem_limits(size_t bytes);
 cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<double>>& gl_x,
                                   const std::vector<std::vector<double>>& gl_w);
 cudaError_t launch_tensor_filter(gh_domain* d, const double* in, double* out);
+// Its transpose (reverse mode): out = S^T in (in and out distinct).
+cudaError_t launch_tensor_filter_transpose(gh_domain* d, const double* in, double* out);
 // The rotating frame of the domain at time t (identity when not rotating).
 Frame frame_at(const gh_domain* d, double t);
 // Dormand-Prince step: out = base + sum_j c[j] k[j] (j < nk), and the scaled

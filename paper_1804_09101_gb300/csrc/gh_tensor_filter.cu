@@ -330,6 +330,143 @@ tf_unframe_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* 
   unframe_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, e, cb, ub, out);
 }
 
+// ---- transpose of the filter (reverse mode).  The spin projection P is
+// self-adjoint under the quadrature inner product sum_j w_j conj(f) g, so its
+// transpose is D P D^-1 with D = diag(w_j) per theta ring: the transposed
+// frame kernels divide by and multiply with w_j around the unchanged spin
+// kernel.  The transposes of the per-point steps: complexify <-> decomplexify,
+// forward <-> inverse real contraction, the conjugate/symmetric expansion of
+// the stored rows -> accumulation into them.
+__host__ __device__ constexpr int tf_first_row(int g) { return tf_row(g, 0); }   // tuple 0 is canonical
+__host__ __device__ constexpr int tf_group_rows(int g) {
+  int n = 0;
+  for (int o = 0; o < tf_size(g); ++o) n += tf_best(g, o) == o;
+  return n;
+}
+
+template <int G, int O>
+__device__ __forceinline__ void tf_load_ubar(double* t, const double* __restrict__ ub, long long ubase, int na) {
+  if constexpr (tf_written(G, O)) t[O] = ub[ubase + (long long)tf_field(G, O) * na];
+  else t[O] = 0.0;
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_accum_row(const Cx* c, Cx* acc) {
+  constexpr int r = tf_row(G, tf_best(G, O)) - tf_first_row(G);
+  if constexpr (tf_best_conj(G, O)) {
+    acc[r].re += c[O].re;
+    acc[r].im -= c[O].im;
+  } else {
+    acc[r].re += c[O].re;
+    acc[r].im += c[O].im;
+  }
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_load_cbar(Cx* c, const ShellDev& sh, int ir, int q, const double* __restrict__ cb,
+                                             double w) {
+  constexpr int row = tf_row(G, O);
+  if constexpr (row >= 0) {
+    constexpr double f = tf_scale(G, O);
+    const long long i = tf_index(sh, ir, row, q);
+    c[O] = {f * w * cb[i], f * w * cb[i + 1]};
+  } else {
+    c[O] = {0.0, 0.0};
+  }
+}
+template <int G, int O>
+__device__ __forceinline__ void tf_add_u(const double* t, double* uacc) {
+  uacc[tf_field(G, O)] += t[O];
+}
+
+// U^T, then D^-1: Cartesian cotangent -> row cotangents / w_j
+template <int G, int... O>
+__device__ __forceinline__ void unframe_t_group(std::integer_sequence<int, O...>, const ShellDev& sh, int ir, int q,
+                                                const double e[3][3], double iw, const double* __restrict__ ub,
+                                                long long ubase, double* __restrict__ cb) {
+  double t[sizeof...(O)];
+  Cx c[sizeof...(O)];
+  (tf_load_ubar<G, O>(t, ub, ubase, sh.na), ...);
+  contract_real<tf_rank(G), false>(t, e);
+  (tf_scale_r<G, O>(t), ...);
+  complexify<tf_rank(G)>(t, c);
+  Cx acc[tf_group_rows(G)];
+#pragma unroll
+  for (int r = 0; r < tf_group_rows(G); ++r) acc[r] = {0.0, 0.0};
+  (tf_accum_row<G, O>(c, acc), ...);
+#pragma unroll
+  for (int r = 0; r < tf_group_rows(G); ++r) {
+    const long long i = tf_index(sh, ir, tf_first_row(G) + r, q);
+    cb[i] = iw * acc[r].re;
+    cb[i + 1] = iw * acc[r].im;
+  }
+}
+
+// D, then F^T: row cotangents -> Cartesian cotangent (accumulated per field)
+template <int G, int... O>
+__device__ __forceinline__ void frame_t_group(std::integer_sequence<int, O...>, const ShellDev& sh, int ir, int q,
+                                              const double e[3][3], double w, const double* __restrict__ cb,
+                                              double* uacc) {
+  Cx c[sizeof...(O)];
+  double t[sizeof...(O)];
+  (tf_load_cbar<G, O>(c, sh, ir, q, cb, w), ...);
+  decomplexify<tf_rank(G)>(c, t);
+  contract_real<tf_rank(G), true>(t, e);
+  (tf_add_u<G, O>(t, uacc), ...);
+}
+
+template <int... G>
+__device__ __forceinline__ void unframe_t_all(std::integer_sequence<int, G...>, const ShellDev& sh, int ir, int q,
+                                              const double e[3][3], double iw, const double* __restrict__ ub,
+                                              long long ubase, double* __restrict__ cb) {
+  (unframe_t_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, e, iw, ub, ubase, cb), ...);
+}
+template <int... G>
+__device__ __forceinline__ void frame_t_all(std::integer_sequence<int, G...>, const ShellDev& sh, int ir, int q,
+                                            const double e[3][3], double w, const double* __restrict__ cb,
+                                            double* uacc) {
+  (frame_t_group<G>(std::make_integer_sequence<int, tf_size(G)>{}, sh, ir, q, e, w, cb, uacc), ...);
+}
+
+__global__ void __launch_bounds__(TF_THREADS)
+tf_unframe_t_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                    const double* __restrict__ ub, double* __restrict__ cb) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + TF_THREADS - 1) / TF_THREADS;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * TF_THREADS + threadIdx.x;
+  if (q >= na) return;
+  double e[3][3];
+  real_frame(sh, q, e);
+  const double iw = 1.0 / sh.wth[q / sh.nph];
+  const long long base = sh.off + (long long)ir * NF * na + q;
+  unframe_t_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, e, iw, ub, base, cb);
+}
+
+__global__ void __launch_bounds__(TF_THREADS)
+tf_frame_t_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                  const double* __restrict__ cb, double* __restrict__ out) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + TF_THREADS - 1) / TF_THREADS;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * TF_THREADS + threadIdx.x;
+  if (q >= na) return;
+  double e[3][3];
+  real_frame(sh, q, e);
+  const double w = sh.wth[q / sh.nph];
+  double uacc[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) uacc[f] = 0.0;
+  frame_t_all(std::make_integer_sequence<int, 9>{}, sh, ir, q, e, w, cb, uacc);
+  const long long base = sh.off + (long long)ir * NF * na + q;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) out[base + (long long)f * na] = uacc[f];
+}
+
 __device__ __forceinline__ int tf_nb(int K, int s, int m) {
   const int am = m < 0 ? -m : m, as = s < 0 ? -s : s;
   const int n = K - (am > as ? am : as) + 1;
@@ -698,6 +835,24 @@ cudaError_t launch_tensor_filter(gh_domain* d, const double* in, double* out) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   tf_unframe_kernel<<<d->tf_point_blocks, TF_THREADS, 0, d->stream>>>(d->shells_d, n, d->tf_pb_d, d->tf_buf, out);
+  d->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_filter_transpose(gh_domain* d, const double* in, double* out) {
+  cudaError_t e;
+  if (!d->tf_buf) return cudaErrorNotReady;
+  const int n = d->n_shells;
+  tf_unframe_t_kernel<<<d->tf_point_blocks, TF_THREADS, 0, d->stream>>>(d->shells_d, n, d->tf_pb_d, in, d->tf_buf);
+  d->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (d->tf_rows > 0) {
+    tf_spin_kernel<<<d->tf_rows, d->tf_spin_threads, d->tf_smem, d->stream>>>(d->shells_d, n, d->tf_pb_d + n + 1,
+                                                                             d->tf_buf);
+    d->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  tf_frame_t_kernel<<<d->tf_point_blocks, TF_THREADS, 0, d->stream>>>(d->shells_d, n, d->tf_pb_d, d->tf_buf, out);
   d->launches++;
   return cudaGetLastError();
 }

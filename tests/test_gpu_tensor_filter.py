@@ -4,8 +4,9 @@ through the C ABI: the filter alone on seeded, non-band-limited states (one
 and two shells, a given keep and floor(2L/3), keep = 0 and keep = L), RK4 steps with the filter; at full size the properties that hold at
 any resolution (constant Cartesian tensors are kept when keep >= 3, the
 filter is a projection); the captured RK4 graph agrees with the plain calls,
-switching back restores the per-component filter, the adjoint refuses the
-mode."""
+switching back restores the per-component filter; the reverse mode (the
+filter's transpose exactly, and the RK4 step's VJP against finite
+differences)."""
 import numpy as np
 import pytest
 import torch
@@ -147,7 +148,7 @@ def test_keep_below_rank_changes_constant_tensors():
     assert float((b - c0).abs().max()) > 1e-2
 
 
-def test_graph_mode_switch_and_adjoint():
+def test_graph_and_mode_switch():
     gh = _gh()
     w = CASES["two_shells_keep4"]()
     dom = gh.Domain.from_workload(w)
@@ -168,8 +169,6 @@ def test_graph_mode_switch_and_adjoint():
     gh.gh_rk4_graph_launch(dom, 3)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
-    with pytest.raises(RuntimeError):
-        gh.gh_rhs_vjp(dom, u, u.clone(), torch.zeros_like(u))
     gh.gh_set_sh_filter(dom, "component")
     back = u.clone()
     gh.gh_apply_filters(dom, back, dom.new_work())
@@ -200,9 +199,7 @@ def test_holes_of_different_resolution_in_one_domain():
     and items in one launch): each hole's part equals the oracle's tensor
     filter (floor(2L/3) per hole, radial filter on) of that hole alone."""
     gh = _gh()
-    holes = [dict(M=1.0, chi=0.3, shells=[(1.6, 8.0, 9, 7)]),
-             dict(M=0.7, chi=0.8, shells=[(0.9, 3.0, 7, 11), (3.0, 9.0, 7, 11)]),
-             dict(M=1.5, chi=0.0, shells=[(2.5, 20.0, 11, 5)])]
+    holes = _three_holes()
     shells = [s + (b,) for b, h in enumerate(holes) for s in h["shells"]]
     dom = gh.Domain(shells, radial_filter_on=True, sh_keep_l=-2)
     gh.gh_set_sh_filter(dom, "tensor")
@@ -218,3 +215,69 @@ def test_holes_of_different_resolution_in_one_domain():
         ref = flat(evolve.apply_filters(odom, unflat(x[off:off + n], odom)))
         assert np.abs(got[off:off + n] - ref).max() <= REL_TOL * np.abs(x[off:off + n]).max(), h
         off += n
+
+
+def _three_holes():
+    return [dict(M=1.0, chi=0.3, shells=[(1.6, 8.0, 9, 7)]),
+            dict(M=0.7, chi=0.8, shells=[(0.9, 3.0, 7, 11), (3.0, 9.0, 7, 11)]),
+            dict(M=1.5, chi=0.0, shells=[(2.5, 20.0, 11, 5)])]
+
+
+@pytest.mark.parametrize("which", ["one_shell_keep4", "two_shells_keep4", "three_holes"])
+def test_filter_transpose_exact(which):
+    """A step with dt = 0 is the filters alone, u -> S u, and its VJP is S^T ybar:
+    <ybar, S x> = <S^T ybar, x> to rounding (the transpose of the spin
+    projection is D P D^-1 with the quadrature weights D)."""
+    gh = _gh()
+    u = None
+    if which == "three_holes":
+        holes = _three_holes()
+        shells = [s + (b,) for b, h in enumerate(holes) for s in h["shells"]]
+        dom = gh.Domain(shells, radial_filter_on=True, sh_keep_l=-2)
+        u = dom.new_state()
+        for b, h in enumerate(holes):
+            gh.gh_set_analytic_kerr_schild(dom, b, h["M"], h["chi"], u)
+    else:
+        w = CASES[which]()
+        dom = gh.Domain.from_workload(w)
+        u = dom.new_state()
+        gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
+    gh.gh_set_sh_filter(dom, "tensor")
+    # a valid metric plus noise: the right-hand side is finite, so the dt = 0
+    # step is exactly the filters
+    rng = np.random.default_rng(31)
+    x = to_host(u) + 1e-2 * rng.standard_normal(dom.state_size)
+    yb = rng.standard_normal(dom.state_size)
+    u = to_dev(x)
+    gh.gh_rk4_step(dom, 0.0, u, dom.new_work())
+    sx = to_host(u)
+    g = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, 0.0, to_dev(x), to_dev(yb), g, gh.new_vjp_work(dom))
+    lhs, rhs = float(yb @ sx), float(to_host(g) @ x)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(yb), (lhs, rhs)
+    # and it is not the per-component transpose
+    gh.gh_set_sh_filter(dom, "component")
+    g2 = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, 0.0, to_dev(x), to_dev(yb), g2, gh.new_vjp_work(dom))
+    assert float((g2 - g).abs().max()) > 1e-3
+
+
+def test_step_vjp_dot_product_against_finite_differences():
+    gh = _gh()
+    w = CASES["two_shells_keep4"]()
+    odom = oracle_domain(w)
+    u0 = flat(oracle_initial_state(w, odom))
+    dom = _tensor_domain(w, odom)
+    rng = np.random.default_rng(32)
+    v = rng.standard_normal(u0.shape)
+    dw = rng.standard_normal(u0.shape)
+    h = 1e-6
+    work = dom.new_work()
+    up, um = to_dev(u0 + h * dw), to_dev(u0 - h * dw)
+    gh.gh_rk4_step(dom, w.dt, up, work)
+    gh.gh_rk4_step(dom, w.dt, um, work)
+    jw = (to_host(up) - to_host(um)) / (2 * h)
+    ub = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, w.dt, to_dev(u0), to_dev(v), ub, gh.new_vjp_work(dom))
+    lhs, rhs = float(v @ jw), float(to_host(ub) @ dw)
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs), (lhs, rhs)
