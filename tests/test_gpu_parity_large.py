@@ -1,0 +1,135 @@
+"""Parity at the full size of the large workload (Kerr a = 0.95, 8 shells
+r in [1.2, 100], N_r = 41, L = 31; 671,744 points), in the launch configuration
+the benchmark times (folded angular maps, autotuned schedule).
+
+The input is the workload's initial data plus seeded noise (1e-4 on every
+value).  The oracle's whole-shell right-hand side is minutes of work at this size, so
+it is evaluated one point at a time at sampled points: the radial derivative
+along the point's radial line, the angular derivatives by the harmonic
+analysis of the point's (r, field) slices and the synthesis of the
+derivative harmonics at the point, the DiffJac contraction, the pointwise GH
+algebra, and at boundary points the oracle's characteristic conditions
+(interface upwinding from both shells' interior values, outer freezing).
+The RK4 step at this size is checked by a property that holds at any size:
+it equals u + dt/6 (k1 + 2 k2 + 2 k3 + k4) built from gh_rhs calls, followed
+by the filters."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gh as ogh
+from oracle import spectral
+from paper_1804_09101_gb300 import workloads
+from parity_helpers import REL_TOL, flat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def large():
+    w = workloads.kerr_eight_shells_large()
+    # seeded N(0,1) * 1e-4 on every value, so that the right-hand side is far
+    # from the stationary background's truncation error at every point
+    w.noise_amp = 1e-4
+    odom = oracle_domain(w)
+    u0 = oracle_initial_state(w, odom)
+    return w, odom, u0
+
+
+def _interior_rhs_at(odom, u, s, ir, j, k, jac):
+    """The oracle's GH right-hand side (before boundary conditions) at point
+    (ir, j, k) of shell s, from that point's radial line and angular slice."""
+    g = odom.grids[s]
+    us = u[s]
+    dr = spectral.radial_derivative(us[:, :, j, k], g)[ir]                     # [50]
+    c = spectral.sh_analysis(us[ir], g)                                         # [50, modes]
+    th, ph = g["theta"][j:j + 1], g["phi"][k:k + 1]
+    dth = spectral.sh_synthesis(c, spectral.real_ylm_dtheta(g["L"], th, ph))[:, 0, 0]
+    dph = spectral.sh_synthesis(c, spectral.real_ylm_dphi(g["L"], th, ph))[:, 0, 0]
+    J = jac[s][:, :, ir, j, k]                                                  # [3 (x^i), 3 (r, th, ph)]
+    du = J[:, 0:1] * dr[None] + J[:, 1:2] * dth[None] + J[:, 2:3] * dph[None]   # [3, 50]
+    U = us[ir, :, j, k]
+    H = odom.H[s][ir, :, j, k]
+    dH = odom.dH[s][ir, :, j, k].reshape(3, 4)
+    return ogh.gh_rhs_pointwise(U[None], du[None], H[None], dH[None], odom.gamma0, odom.gamma1, odom.gamma2)[0]
+
+
+def _bg_at(odom, s, ir, j, k):
+    bg = odom.boundary_bg(s, ir)
+    return {key: np.asarray(v)[j:j + 1, k:k + 1] for key, v in bg.items()}
+
+
+def test_rhs_at_sampled_points_full_size(large):
+    from paper_1804_09101_gb300 import gh
+    w, odom, u0 = large
+    dom = gpu_domain(w, odom)
+    gh.gh_autotune(dom, 3)
+    k = dom.new_state()
+    gh.gh_rhs(dom, to_dev(flat(u0)), k)
+    got = to_host(k)
+    del k
+    scale = np.abs(flat(u0)).max()
+    offs = np.cumsum([0] + [int(np.prod(sh)) for sh in odom.shapes()])
+    jac = [spectral.spherical_jacobian(g) for g in odom.grids]
+    rng = np.random.default_rng(2025)
+
+    def gpu_at(s, ir, j, kk):
+        n_r, _, nth, nph = odom.shapes()[s]
+        idx = offs[s] + ((ir * 50 + np.arange(50)) * nth + j) * nph + kk
+        return got[idx]
+
+    n_cmp, worst = 0, 0.0
+    ns = len(odom.grids)
+    for s in range(ns):
+        n_r, _, nth, nph = odom.shapes()[s]
+        # interior points
+        for _ in range(6):
+            ir, j, kk = int(rng.integers(1, n_r - 1)), int(rng.integers(0, nth)), int(rng.integers(0, nph))
+            ref = _interior_rhs_at(odom, u0, s, ir, j, kk, jac)
+            err = np.abs(gpu_at(s, ir, j, kk) - ref).max() / scale
+            worst = max(worst, err)
+            n_cmp += 1
+        # the boundary slice at r_out: an interface with shell s + 1, or the outer boundary
+        for _ in range(2):
+            j, kk = int(rng.integers(0, nth)), int(rng.integers(0, nph))
+            a = _interior_rhs_at(odom, u0, s, n_r - 1, j, kk, jac)
+            bg = _bg_at(odom, s, n_r - 1, j, kk)
+            if s + 1 < ns:
+                b = _interior_rhs_at(odom, u0, s + 1, 0, j, kk, jac)
+                na, nb = ogh.apply_interface_bc(a[None, None], b[None, None], bg, odom.gamma1, odom.gamma2)
+                err = max(np.abs(gpu_at(s, n_r - 1, j, kk) - na[0, 0]).max(),
+                          np.abs(gpu_at(s + 1, 0, j, kk) - nb[0, 0]).max()) / scale
+            else:
+                new = ogh.apply_outer_bc(a[None, None], bg, odom.gamma1, odom.gamma2)
+                err = np.abs(gpu_at(s, n_r - 1, j, kk) - new[0, 0]).max() / scale
+            worst = max(worst, err)
+            n_cmp += 1
+    assert n_cmp == 8 * ns and worst < REL_TOL, worst
+
+
+def test_rk4_step_is_the_composition_of_its_parts_full_size(large):
+    """u1 = F(u0 + dt/6 (k1 + 2 k2 + 2 k3 + k4)) with k from gh_rhs at the
+    stage states and F = gh_apply_filters, against gh_rk4_step."""
+    from paper_1804_09101_gb300 import gh
+    w, odom, u0 = large
+    dom = gpu_domain(w, odom)
+    gh.gh_autotune(dom, 3)
+    dt = w.dt
+    u = to_dev(flat(u0))
+    ks = []
+    x = u
+    for c in (0.5, 0.5, 1.0, None):
+        kk = dom.new_state()
+        gh.gh_rhs(dom, x, kk)
+        ks.append(kk)
+        if c is not None:
+            x = u + c * dt * kk
+    ref = u + (dt / 6.0) * (ks[0] + 2.0 * ks[1] + 2.0 * ks[2] + ks[3])
+    del ks, x
+    work = dom.new_work()
+    gh.gh_apply_filters(dom, ref, work)
+    step = u.clone()
+    gh.gh_rk4_step(dom, dt, step, work)
+    torch.cuda.synchronize()
+    err = float((step - ref).abs().max()) / float(u.abs().max())
+    assert err < REL_TOL, err
