@@ -112,3 +112,44 @@ def test_batched_workload_builds_and_steps():
     # bound is meaningful here
     assert torch.isfinite(u).all()
     assert float((u - u0).abs().max()) < float(u0.abs().max())
+
+
+def test_full_size_batched_workload_sampled_holes_match_oracle():
+    """The full 64-hole workload (613,888 points, one domain, autotuned, one
+    captured CUDA graph per RK4 step, as the benchmark runs it) on the
+    oracle's exact data plus seeded noise: the right-hand side of every point
+    of the largest hole and of three seeded sample holes, and their state
+    after one graph-launched RK4 step (each hole with its own dt), against the
+    oracle run on each of those holes alone."""
+    from paper_1804_09101_gb300 import gh
+    w = workloads.batched_workload(64)
+    w.noise_amp = 1e-6
+    odoms = [evolve.Domain([(h["r_in"], h["r_out"], h["n_r"], h["L"])], h["M"], h["chi"], w.gamma0, w.gamma1,
+                           w.gamma2, w.filt_alpha, w.filt_order, True, (2 * h["L"]) // 3) for h in w.holes]
+    u_host = np.concatenate([flat(od.u_exact) for od in odoms]) + w.noise()
+    dom = gh.Domain(w.shells, w.gamma0, w.gamma1, w.gamma2, w.filt_alpha, w.filt_order, True, -2)
+    gh.gh_set_gauge(dom, to_dev(np.concatenate([flat(od.H) for od in odoms])),
+                    to_dev(np.concatenate([flat(od.dH) for od in odoms])))
+    gh.gh_set_background(dom, to_dev(np.concatenate([flat(od.u_exact) for od in odoms])))
+    for b, h in enumerate(w.holes):
+        gh.gh_set_dt_scale(dom, b, h["dt"])
+    gh.gh_autotune(dom, 3)
+    u = to_dev(u_host)
+    k = dom.new_state()
+    gh.gh_rhs(dom, u, k)
+    k_host = to_host(k)
+    del k
+    work = dom.new_work()
+    gh.gh_rk4_graph_capture(dom, 1.0, u, work)     # the capture does not step u
+    gh.gh_rk4_graph_launch(dom, 1)
+    u1 = to_host(u)
+    offs = np.cumsum([0] + [50 * h["n_r"] * 2 * (h["L"] + 1) ** 2 for h in w.holes])
+    largest = int(np.argmax(np.diff(offs)))
+    picks = sorted({largest} | set(int(b) for b in np.random.default_rng(9).choice(len(w.holes), 3, replace=False)))
+    for b in picks:
+        od, h = odoms[b], w.holes[b]
+        sl = slice(offs[b], offs[b + 1])
+        ub = [u_host[sl].reshape(od.shapes()[0])]
+        scale = np.abs(u_host[sl]).max()
+        assert np.abs(k_host[sl] - flat(evolve.rhs(od, ub))).max() <= REL_TOL * scale, (b, h)
+        assert np.abs(u1[sl] - flat(evolve.rk4_step(od, ub, h["dt"]))).max() <= REL_TOL * scale, (b, h)
