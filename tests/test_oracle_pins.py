@@ -419,3 +419,50 @@ def test_rk4_matches_stability_polynomial(monkeypatch):
     out = evolve.rk4_step(D(), u, dt)
     z = lam * dt
     assert abs(out[0][0] - (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24)) < 1e-15
+
+
+# ------------------------------------------------------------- perturbations
+def _pulse_setup(M):
+    from oracle import perturb
+    g = grid.shell_grid(3.0, 8.0, 31, 11)
+    u_bg, _, _ = kerr_schild.kerr_schild_shell(g, M, 0.0)
+    coeffs = np.random.default_rng(41).standard_normal(len(spectral.sh_modes(2)))
+    du = perturb.psi_pulse(g, u_bg, 1e-3, 5.5, 1.2, 2, coeffs)
+    return g, u_bg, du, coeffs
+
+
+def test_psi_pulse_phi_is_the_gradient_of_psi():
+    """dPhi_iab = d_i dpsi_ab: against the oracle's spectral Cartesian gradient
+    of dpsi on a grid that resolves the pulse (an independent route: radial
+    Chebyshev and Y_lm derivatives instead of the chain rule on G(r) S)."""
+    g, _, du, _ = _pulse_setup(1.0)
+    grad = spectral.cartesian_gradient(du[:, 0:10], g)            # [3, n_r, 10, th, ph]
+    for i in range(3):
+        phi = du[:, 20 + 10 * i:30 + 10 * i]
+        assert np.abs(grad[i] - phi).max() <= 1e-7 * np.abs(phi).max()
+    # the same pulse on all ten components
+    assert np.array_equal(du[:, 0], du[:, 7]) and np.array_equal(du[:, 20], du[:, 29])
+
+
+def test_psi_pulse_is_ingoing_on_flat_space():
+    """With M = 0 (alpha = 1, beta = 0) Pi_ab = -d_t psi_ab and an ingoing
+    wave f(t + R) has d_t f = d_R f, so dPi must equal -d_R dpsi."""
+    g, _, du, _ = _pulse_setup(0.0)
+    dR = spectral.radial_derivative(du[:, 0:10], g)
+    assert np.abs(du[:, 10:20] + dR).max() <= 1e-7 * np.abs(dR).max()
+
+
+def test_pi_modes_recover_their_coefficients():
+    """Y_lm analysis of each radial slice of the Pi mode perturbation returns
+    exp(-((R - Rc)/w)^2) c_lm (l <= 3 < L, exact quadrature); psi and Phi
+    are untouched."""
+    from oracle import perturb
+    g = grid.shell_grid(2.0, 9.0, 9, 7)
+    coeffs = np.random.default_rng(42).standard_normal(len(spectral.sh_modes(3)))
+    du = perturb.pi_modes(g, 4.0, 2.0, 3, coeffs)
+    c = spectral.sh_analysis(du[:, 12], g)                            # [n_r, modes of L = 7]
+    G = np.exp(-((g["r"] - 4.0) / 2.0) ** 2)
+    ref = np.zeros_like(c)
+    ref[:, :len(coeffs)] = G[:, None] * coeffs[None, :]
+    assert np.abs(c - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert not du[:, 0:10].any() and not du[:, 20:].any()
