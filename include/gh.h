@@ -301,7 +301,8 @@ gh_status gh_get_time(const gh_domain* dom, double* t);
  *   d_t u^0_iab = D_t u^0_iab + v_0 P_i^k n^j C_jkab (D_t: the characteristic
  *   projection of the equations, C_iab = d_i psi_ab - Phi_iab, C_jkab = d_j Phi_kab
  *   - d_k Phi_jab), which removes the incoming normal derivative of those fields;
- *   u^- is frozen.  The adjoint entry points return GH_ENOTSUP in this mode.
+ *   u^- is frozen.  The adjoint entry points transpose these terms (they are
+ *   linear in u and its derivatives for the fixed background).
  * Synchronises the stream and discards a captured RK4 graph. */
 enum { GH_BC_FREEZE = 0, GH_BC_CONSTRAINT_PRESERVING = 1 };
 gh_status gh_set_outer_bc(gh_domain* dom, int mode);

@@ -180,9 +180,13 @@ __device__ __forceinline__ void select_transpose(double& wi, double& wo, double 
   }
 }
 
+// cp != 0 (constraint-preserving outer condition): at incoming outer points the
+// u^psi and u^0 cotangents pass through (the forward adds v_psi n^i C_ip and
+// v_0 P_i^k n^j C_jkp instead of freezing), and v_psi w_psi_bar, v_0 w0_bar
+// are stashed in cpbar[(p * npts + point) * 4 + {0, 1..3}] for cp_adjoint_kernel.
 __global__ void __launch_bounds__(128)
 bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int* __restrict__ pt_begin,
-                  double* __restrict__ kb, double gamma1, double gamma2) {
+                  double* __restrict__ kb, double gamma1, double gamma2, int cp, double* __restrict__ cpbar) {
   const int npts = pt_begin[n_slices];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 10 * npts) return;
@@ -207,8 +211,14 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
     load_pair(kb, base, na, p, v);
     CharBar w;
     inv_t_transpose(v, n_dn, gamma2, w);
-    if (v_psi < 0.0) w.psi = 0.0;
-    if (v_0 < 0.0) w.w0[0] = w.w0[1] = w.w0[2] = 0.0;
+    if (cp) {
+      double* cb = cpbar + ((long long)p * npts + pt) * 4;
+      cb[0] = v_psi < 0.0 ? v_psi * w.psi : 0.0;
+      for (int i = 0; i < 3; ++i) cb[1 + i] = v_0 < 0.0 ? v_0 * w.w0[i] : 0.0;
+    } else {
+      if (v_psi < 0.0) w.psi = 0.0;
+      if (v_0 < 0.0) w.w0[0] = w.w0[1] = w.w0[2] = 0.0;
+    }
     if (v_p < 0.0) w.wp = 0.0;
     if (v_m < 0.0) w.wm = 0.0;
     t_transpose(w, n_dn, n_up, gamma2, v);
@@ -229,6 +239,66 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
     t_transpose(wo, n_dn, n_up, gamma2, vo);
     store_pair(kb, ba, na, p, vi);
     store_pair(kb, bb, na, p, vo);
+  }
+}
+
+// Transpose of the constraint-preserving corrections at the outer boundary,
+// after the pointwise reverse pass has left the derivative cotangents in
+// dr/dth/dph.  Forward, for pair p at an outer point:
+//   nC3  = n^i (d_i psi_p - Phi_ip),
+//   Pm_i = m_i - n_i (n^k m_k),  m_k = n^j (d_j Phi_kp - d_k Phi_jp),
+//   d_i = J_i^d D_d (DiffJac, D = d/dx, d/dtheta, d/dphi).
+// Reverse, with c = nC3_bar and Pbar = Pm_bar from bc_adjoint_kernel:
+//   D_d psi_p bar += (n^i J_i^d) c,  Phi_ip bar -= n^i c,
+//   m_bar_k = Pbar_k - n^k (n_i Pbar_i),
+//   (d_j Phi_kp) bar = n^j m_bar_k - n^k m_bar_j,  D_d Phi_kp bar += J_j^d (d_j Phi_kp) bar.
+__global__ void __launch_bounds__(128)
+cp_adjoint_kernel(const ShellDev* __restrict__ shells, const BcSliceDev* __restrict__ slices, int n_slices,
+                  const int* __restrict__ pt_begin, const double* __restrict__ cpbar, double* dr, double* dth,
+                  double* dph, double* ubar) {
+  const int npts = pt_begin[n_slices];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 10 * npts) return;
+  const int p = t / npts;
+  const int pt = t - p * npts;
+  const int s = find_segment(pt_begin, n_slices, pt);
+  const BcSliceDev& sl = slices[s];
+  if (sl.kind != 0) return;
+  const int q = pt - pt_begin[s];
+  const int na = sl.na;
+  const double* cb = cpbar + ((long long)p * npts + pt) * 4;
+  const double c = cb[0], P0 = cb[1], P1 = cb[2], P2 = cb[3];
+  if (c == 0.0 && P0 == 0.0 && P1 == 0.0 && P2 == 0.0) return;
+  double n_dn[3], n_up[3];
+  for (int i = 0; i < 3; ++i) {
+    n_dn[i] = sl.bg[(long long)i * na + q];
+    n_up[i] = sl.bg[(long long)(3 + i) * na + q];
+  }
+  const ShellDev& sh = shells[sl.shell_a];
+  PointGeom G;
+  point_geom(sh, sh.n_r - 1, q, G);
+  const long long base = sl.off_a + q;
+  auto add_d = [&](int f, const double v[3]) {   // D_d bar of field f += sum_i J_i^d v_i
+    const long long o = base + (long long)f * na;
+    double g[3];
+    for (int d = 0; d < 3; ++d) g[d] = G.J[0][d] * v[0] + G.J[1][d] * v[1] + G.J[2][d] * v[2];
+    dr[o] += g[0];
+    dth[o] += g[1];
+    dph[o] += g[2];
+  };
+  {
+    const double v[3] = {n_up[0] * c, n_up[1] * c, n_up[2] * c};
+    add_d(p, v);
+    for (int i = 0; i < 3; ++i) ubar[base + (long long)(20 + 10 * i + p) * na] -= v[i];
+  }
+  const double Pb[3] = {P0, P1, P2};
+  const double nP = n_dn[0] * P0 + n_dn[1] * P1 + n_dn[2] * P2;
+  double mb[3];
+  for (int k = 0; k < 3; ++k) mb[k] = Pb[k] - n_up[k] * nP;
+  for (int k = 0; k < 3; ++k) {          // field Phi_kp: (d_j Phi_kp) bar for j = 0..2
+    double v[3];
+    for (int j = 0; j < 3; ++j) v[j] = n_up[j] * mb[k] - n_up[k] * mb[j];
+    add_d(20 + 10 * k + p, v);
   }
 }
 
@@ -420,8 +490,12 @@ unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 gh_status adj_ready(gh_domain* d) {
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
-  if (d->outer_bc != 0)
-    return afail(d, GH_ENOTSUP, "the adjoint is built for the freezing outer boundary condition only");
+  if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
+    void* p = nullptr;
+    GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * 40 * (size_t)d->bc_points));
+    d->owned.push_back(p);
+    d->adj_cpbar = (double*)p;
+  }
   if (d->rot_omega != 0.0) return afail(d, GH_ENOTSUP, "the adjoint is built for a static grid only");
   if (!d->kbt) {
     void* p = nullptr;
@@ -540,9 +614,11 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
                   bool assign = false) {
   GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
+  const int cp = d->outer_bc == GH_BC_CONSTRAINT_PRESERVING;
   if (d->bc_points) {
     gh::bc_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
-        d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->kbt, d->params.gamma1, d->params.gamma2);
+        d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->kbt, d->params.gamma1, d->params.gamma2, cp,
+        d->adj_cpbar);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
@@ -578,6 +654,12 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
       gh::pointwise_adjoint_kernel<0><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
           d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
           d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+  }
+  if (cp && d->bc_points) {
+    gh::cp_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
+        d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpbar, d->d_r, d->d_th, d->d_ph, ubar);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }

@@ -224,6 +224,7 @@ struct gh_domain {
   double* adj_ubp = nullptr;
   // SH filter mode (gh_set_sh_filter): 0 per Cartesian component, 1 tensor
   // harmonics; complex frame components [shell][r][TF_ROWS][na][2]
+  double* adj_cpbar = nullptr;  // reverse mode, constraint-preserving outer condition: [10][bc points][4]
   int sh_filter_mode = 0;
   double* tf_buf = nullptr;
   int* tf_pb_d = nullptr;       // tensor-filter launch maps: point blocks, then rows
