@@ -80,9 +80,17 @@ def radial_flops(shells):
 
 
 def _shell_dims(shell):
-    _, _, n_r, L = shell
+    _, _, n_r, L = shell[:4]
     nth, nph = L + 1, 2 * (L + 1)
     return n_r, nth, nph, nth * nph
+
+
+def _keep(shell, K):
+    """The kept degree of a shell: its L when K is None, floor(2L/3) for -2."""
+    L = shell[3]
+    if K is None:
+        return L
+    return (2 * L) // 3 if K == -2 else K
 
 
 def sep_angular_flops(shells, K=None, two=True):
@@ -93,8 +101,7 @@ def sep_angular_flops(shells, K=None, two=True):
     n_out = 2 if two else 1
     for sh in shells:
         n_r, nth, nph, na = _shell_dims(sh)
-        k = sh[3] if K is None else K
-        M = 2 * k + 1
+        M = 2 * _keep(sh, K) + 1
         f += 50 * n_r * (2 * nth * nph * M + n_out * 2 * nth * nth * M + n_out * 2 * na * M)
     return f
 
@@ -118,8 +125,7 @@ def fold_angular_flops(shells, K=None, two=True):
     n_out = 2 if two else 1
     for sh in shells:
         n_r, nth, nph, na = _shell_dims(sh)
-        k = sh[3] if K is None else K
-        M = 2 * k + 1
+        M = 2 * _keep(sh, K) + 1
         W = nph // 4 + 1 if nph % 4 == 0 else (nph + 2) // 4
         half, hs = nth // 2, (nth + 1) // 2
         per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W

@@ -52,3 +52,12 @@ def test_tensor_filter_components_and_flops():
     b = costmodel.tensor_filter_flops([(1.0, 2.0, 10, 7)], 4)
     assert b["total"] == 2 * a["total"] and a["spin"] > 0 and a["frame"] > 0
     assert costmodel.tensor_filter_flops([(1.0, 2.0, 5, 7)], -1)["total"] == 0
+
+
+def test_keep_minus_two_is_two_thirds_of_each_shells_L():
+    shells = [(1.0, 2.0, 9, 7), (2.0, 3.0, 9, 15)]
+    for alg in ("folded", "separable"):
+        a = costmodel.family_flops("angular_filter", shells, alg, -2)
+        b = (costmodel.family_flops("angular_filter", shells[:1], alg, 4)
+             + costmodel.family_flops("angular_filter", shells[1:], alg, 10))
+        assert a == b > 0
