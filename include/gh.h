@@ -285,11 +285,14 @@ gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
  * the characteristic speeds do not change (xdot is tangential).
  * gh_rhs, gh_constraints and gh_derivatives evaluate at the domain's time
  * (gh_set_time / gh_get_time); gh_rk4_step and accepted gh_dp5_step attempts
- * advance it and use their stage times.  With omega != 0: the adjoint entry
- * points and gh_rk4_graph_capture return GH_ENOTSUP, as do steps on domains
- * with a dt scale other than 1.  gh_set_rotating_frame synchronises the
- * stream and discards a captured graph; GH_EINVAL for a zero axis or a
- * non-finite rate. */
+ * advance it and use their stage times.  The clock also lives on the device
+ * and each step computes its stage frames from it there, so a captured RK4
+ * graph replays with the live time (each gh_rk4_graph_launch of n steps
+ * advances the clock by n dt).  With omega != 0: the adjoint entry points
+ * return GH_ENOTSUP, as do steps on domains with a dt scale other than 1.
+ * gh_set_rotating_frame and gh_set_time synchronise the stream;
+ * gh_set_rotating_frame discards a captured graph; GH_EINVAL for a zero axis
+ * or a non-finite rate. */
 gh_status gh_set_rotating_frame(gh_domain* dom, const double axis[3], double omega);
 gh_status gh_set_time(gh_domain* dom, double t);
 gh_status gh_get_time(const gh_domain* dom, double* t);

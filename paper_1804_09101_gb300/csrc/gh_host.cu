@@ -1147,8 +1147,6 @@ gh_status gh_set_dt_scale(gh_domain* d, int bh, double scale) {
 }
 
 gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
-  if (d && d->rot_omega != 0.0)
-    return fail(d, GH_ENOTSUP, "a captured step would freeze the rotating frame's time; step directly");
   if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   cudaStream_t saved = d->stream;
@@ -1158,6 +1156,7 @@ gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work,
   d->prof = false;
   d->stream = cap;
   const long long n0 = d->launches;
+  const double t0 = d->time;      // capturing executes nothing: the clock stays
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   gh_status st = GH_OK;
@@ -1166,6 +1165,7 @@ gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work,
     cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
     if (e2 != cudaSuccess && st == GH_OK) e = e2;
   }
+  d->time = t0;
   d->stream = saved;
   d->prof = prof;
   cudaStreamDestroy(cap);
@@ -1186,6 +1186,7 @@ gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work,
   if (e != cudaSuccess) return fail(d, GH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   d->graph_step_launches = d->launches - n0;
   d->launches = n0;
+  d->graph_dt = dt;
   return GH_OK;
 }
 
@@ -1195,6 +1196,7 @@ gh_status gh_rk4_graph_launch(gh_domain* d, int n_steps) {
   if (gh_status s = check_latched(d)) return s;
   for (int i = 0; i < n_steps; ++i) GH_CUDA(d, cudaGraphLaunch(d->graph_exec, d->stream));
   d->launches += (long long)n_steps * d->graph_step_launches;
+  d->time += n_steps * d->graph_dt;     // each replay advances the device clock by the captured dt
   return GH_OK;
 }
 
@@ -1257,11 +1259,20 @@ gh_status gh_add_perturbation(gh_domain* d, int kind, double A, double Rc, doubl
   return GH_OK;
 }
 
+// The rotating frame at the domain clock for one evaluation (no-op when static).
+gh_status frame_now(gh_domain* d) {
+  if (d->rot_omega == 0.0) return GH_OK;
+  const double off = 0.0;
+  GH_CUDA(d, gh::launch_frames(d, &off, 1, 0.0));
+  d->frd = d->frames_d;
+  return GH_OK;
+}
+
 gh_status gh_derivatives(gh_domain* d, const double* u, double* du) {
   if (!d || !u || !du) return fail(d, GH_EINVAL, "null argument");
   if (gh_status s = check_latched(d)) return s;
   if (gh_status s = derivatives(d, u)) return s;
-  d->fr = gh::frame_at(d, d->time);
+  if (gh_status s = frame_now(d)) return s;
   GH_CUDA(d, gh::launch_cartesian(d, u, du));
   return GH_OK;
 }
@@ -1270,7 +1281,7 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
   if (!d || !u || !dudt) return fail(d, GH_EINVAL, "null argument");
   if (u == dudt) return fail(d, GH_EINVAL, "u and dudt must not overlap");
   if (gh_status s = check_latched(d)) return s;
-  d->fr = gh::frame_at(d, d->time);
+  if (gh_status s = frame_now(d)) return s;
   if (gh_status s = derivatives(d, u)) return s;
   {
     ProfScope p(d, GH_K_POINTWISE);
@@ -1295,14 +1306,20 @@ gh_status rotation_guard(gh_domain* d) {
 
 gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages) {
   if (gh_status s = rotation_guard(d)) return s;
-  static const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  static const int fidx[4] = {0, 1, 1, 2};     // stage times t, t + dt/2, t + dt/2, t + dt
   double* us = work;
   double* k = work + d->state;
   double* acc = work + 2 * d->state;
   const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
+  if (d->rot_omega != 0.0) {
+    // the step's frames from the device clock, which then advances by dt
+    // (gh_rk4_step only: the adjoint's recomputation leaves the clock alone)
+    const double off[3] = {0.0, 0.5 * dt, dt};
+    GH_CUDA(d, gh::launch_frames(d, off, 3, stages ? 0.0 : dt));
+  }
   for (int stage = 1; stage <= 4; ++stage) {
     const double* in = (stage == 1) ? u : (stages ? stages + (stage - 2) * d->state : us);
-    d->fr = gh::frame_at(d, d->time + cst[stage - 1] * dt);
+    d->frd = d->frames_d ? d->frames_d + fidx[stage - 1] : nullptr;
     if (gh_status s = derivatives(d, in)) return s;
     double* target = (stage == 4) ? (filt ? us : u) : (stages ? stages + (stage - 1) * d->state : us);
     {
@@ -1365,9 +1382,14 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   for (int j = 0; j < 7; ++j) k[j] = work + j * N;
   double* ustage = work + 7 * N;
   double* unew = work + 8 * N;
+  if (d->rot_omega != 0.0) {
+    double off[7];
+    for (int s = 0; s < 7; ++s) off[s] = cdp[s] * dt;
+    GH_CUDA(d, gh::launch_frames(d, off, 7, 0.0));
+  }
   for (int s = 0; s < 7; ++s) {
     const double* in = (s == 0) ? u : (s == 6 ? unew : ustage);
-    d->fr = gh::frame_at(d, d->time + cdp[s] * dt);
+    d->frd = d->frames_d ? d->frames_d + s : nullptr;
     if (gh_status st = derivatives(d, in)) return st;
     {
       ProfScope p(d, GH_K_POINTWISE);
@@ -1410,6 +1432,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   *dt_next = dt * fac;
   if (ok) {
     d->time += dt;
+    GH_CUDA(d, gh::launch_frames(d, nullptr, 0, dt));     // the device clock follows
     const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
     if (filt) {
       if (gh_status st = filters(d, unew, u, ustage)) return st;
@@ -1428,7 +1451,7 @@ gh_status gh_apply_filters(gh_domain* d, double* u, double* work) {
 gh_status gh_constraints(gh_domain* d, const double* u, double* c_out, double* norm2) {
   if (!d || !u || !norm2) return fail(d, GH_EINVAL, "null argument");
   if (gh_status s = check_latched(d)) return s;
-  d->fr = gh::frame_at(d, d->time);
+  if (gh_status s = frame_now(d)) return s;
   if (gh_status s = derivatives(d, u)) return s;
   GH_CUDA(d, gh::launch_constraints(d, u, c_out));
   GH_CUDA(d, gh::launch_norm_reduce(d, norm2));
@@ -1533,6 +1556,17 @@ gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega
   for (int i = 0; i < 3; ++i) d->rot_axis[i] = axis[i];
   d->rot_omega = omega;
   d->fr = gh::frame_at(d, d->time);
+  d->frd = nullptr;
+  if (omega != 0.0 && !d->clock_d) {
+    void* p = nullptr;
+    GH_CUDA(d, cudaMalloc(&p, sizeof(double)));
+    d->owned.push_back(p);
+    d->clock_d = (double*)p;
+    GH_CUDA(d, cudaMalloc(&p, sizeof(gh::Frame) * 8));
+    d->owned.push_back(p);
+    d->frames_d = (gh::Frame*)p;
+  }
+  if (d->clock_d) GH_CUDA(d, cudaMemcpy(d->clock_d, &d->time, sizeof(double), cudaMemcpyHostToDevice));
   if (d->graph_exec) {
     cudaGraphExecDestroy(d->graph_exec);
     d->graph_exec = nullptr;
@@ -1542,7 +1576,9 @@ gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega
 
 gh_status gh_set_time(gh_domain* d, double t) {
   if (!d || !std::isfinite(t)) return GH_EINVAL;
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
   d->time = t;
+  if (d->clock_d) GH_CUDA(d, cudaMemcpy(d->clock_d, &d->time, sizeof(double), cudaMemcpyHostToDevice));
   return GH_OK;
 }
 

@@ -22,6 +22,11 @@ struct Frame {
   double R[9];
   double w[3];
 };
+// Stage times of one step relative to the domain clock (frame_kernel).
+struct FrameOffsets {
+  double off[8];
+  int n;
+};
 // Linear combination of up to seven stage derivatives (passed by value).
 struct LinComb {
   const double* k[7];
@@ -222,9 +227,13 @@ struct gh_domain {
   // small grids, partial field cotangents in adj_ubp (10 states, lazily)
   bool adj_pair_split = false;
   double* adj_ubp = nullptr;
+  double* clock_d = nullptr;    // rotating frame: the domain clock on the device
+  gh::Frame* frames_d = nullptr; // [8] frames of the current step's stage times
+  const gh::Frame* frd = nullptr; // frame of the launches being issued (device)
+  double graph_dt = 0.0;        // dt of the captured RK4 step
+  double* adj_cpbar = nullptr;  // reverse mode, constraint-preserving outer condition: [10][bc points][4]
   // SH filter mode (gh_set_sh_filter): 0 per Cartesian component, 1 tensor
   // harmonics; complex frame components [shell][r][TF_ROWS][na][2]
-  double* adj_cpbar = nullptr;  // reverse mode, constraint-preserving outer condition: [10][bc points][4]
   int sh_filter_mode = 0;
   double* tf_buf = nullptr;
   int* tf_pb_d = nullptr;       // tensor-filter launch maps: point blocks, then rows
@@ -269,6 +278,9 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
 cudaError_t launch_tensor_filter(gh_domain* d, const double* in, double* out);
 // Its transpose (reverse mode): out = S^T in (in and out distinct).
 cudaError_t launch_tensor_filter_transpose(gh_domain* d, const double* in, double* out);
+// The rotating frame at the device clock + off[i] into frames_d[i], i < n,
+// then the clock advances by `advance` (no-op without a rotating frame).
+cudaError_t launch_frames(gh_domain* d, const double* off, int n, double advance);
 // The rotating frame of the domain at time t (identity when not rotating).
 Frame frame_at(const gh_domain* d, double t);
 // Dormand-Prince step: out = base + sum_j c[j] k[j] (j < nk), and the scaled

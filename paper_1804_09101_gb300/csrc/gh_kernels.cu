@@ -326,6 +326,7 @@ struct PointwiseArgs {
   double gamma0, gamma1, gamma2, dt;
   int stage;
   Frame fr;              // rotating frame of this evaluation (fr.on = 0: static)
+  const Frame* frd;      // the same frame in device memory (used when set; from the domain clock)
 };
 
 __device__ __forceinline__ double stage_factor(int stage) {
@@ -424,7 +425,11 @@ pointwise_kernel(PointwiseArgs a) {
     PointGeom G;
     point_geom(sh, ir, q, G);
     double vel[3] = {0.0, 0.0, 0.0};
-    if (ROT) frame_geom(a.fr, G, vel);
+    Frame fr;
+    if (ROT) {
+      fr = a.frd ? *a.frd : a.fr;
+      frame_geom(fr, G, vel);
+    }
     double psi[10], Pi[10], Phi[30];
 #pragma unroll
     for (int p = 0; p < 10; ++p) {
@@ -437,7 +442,7 @@ pointwise_kernel(PointwiseArgs a) {
     double H[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
-    if (ROT) frame_rotate_h(a.fr, H);
+    if (ROT) frame_rotate_h(fr, H);
 
     Split S;
     spacetime_split(psi, S);
@@ -582,7 +587,7 @@ pointwise_kernel(PointwiseArgs a) {
         double dH[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
-        if (ROT) frame_rotate_dh(a.fr, dH);
+        if (ROT) frame_rotate_dh(fr, dH);
         double aH[4], PHa[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) aH[c] = al * H[c];
@@ -853,20 +858,21 @@ struct BcArgs {
   const double* dth;
   const double* dph;
   Frame fr;              // rotating frame (fr.on = 0: static)
+  const Frame* frd;      // the same frame in device memory (used when set)
 };
 
 // Bjorhus-form constraint-preserving corrections at an outer-boundary point for
 // pair p: nC3 = n^i C_ip (C_iab = d_i psi_ab - Phi_iab) and
 // Pm[i] = P_i^k n^j C_jkp (C_jkab = d_j Phi_kab - d_k Phi_jab).
-__device__ __forceinline__ void cp_corrections(const BcArgs& a, const BcSliceDev& sl, int q, int p,
+__device__ __forceinline__ void cp_corrections(const BcArgs& a, const Frame& fr, const BcSliceDev& sl, int q, int p,
                                                const double n_dn[3], const double n_up[3], double& nC3,
                                                double Pm[3]) {
   const ShellDev& sh = a.shells[sl.shell_a];
   PointGeom G;
   point_geom(sh, sh.n_r - 1, q, G);
-  if (a.fr.on) {
+  if (fr.on) {
     double vel[3];
-    frame_geom(a.fr, G, vel);
+    frame_geom(fr, G, vel);
   }
   const int na = sl.na;
   const long long base = sl.off_a + q;
@@ -921,13 +927,13 @@ __device__ __forceinline__ void char_project_pair(const double* k, long long bas
 // Grid-velocity term xdot^k d_k u of pair p's five fields at a boundary point
 // (shell `shell`, radial index ir, slice offset base), from the derivative
 // scratch of the state the RHS was evaluated at.
-__device__ __forceinline__ void frame_adv(const BcArgs& a, int shell, int ir, long long base, int na, int p, int q,
-                                          double adv[5]) {
+__device__ __forceinline__ void frame_adv(const BcArgs& a, const Frame& fr, int shell, int ir, long long base, int na,
+                                          int p, int q, double adv[5]) {
   const ShellDev& sh = a.shells[shell];
   PointGeom G;
   point_geom(sh, ir, q, G);
   double vel[3], vs[3];
-  frame_geom(a.fr, G, vel);
+  frame_geom(fr, G, vel);
 #pragma unroll
   for (int d = 0; d < 3; ++d) vs[d] = fma(vel[2], G.J[2][d], fma(vel[1], G.J[1][d], vel[0] * G.J[0][d]));
   const int f[5] = {p, 10 + p, 20 + p, 30 + p, 40 + p};
@@ -984,14 +990,15 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     beta[i] = sl.bg[(long long)(7 + i) * na + q];
   }
   const double alpha = sl.bg[(long long)6 * na + q];
-  if (a.fr.on) {
+  const Frame fr = (a.fr.on && a.frd) ? *a.frd : a.fr;
+  if (fr.on) {
     // the background's vectors at the moving point: rotated components
     double t1[3], t2[3], t3[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      t1[i] = fma(a.fr.R[3 * i + 2], n_dn[2], fma(a.fr.R[3 * i + 1], n_dn[1], a.fr.R[3 * i] * n_dn[0]));
-      t2[i] = fma(a.fr.R[3 * i + 2], n_up[2], fma(a.fr.R[3 * i + 1], n_up[1], a.fr.R[3 * i] * n_up[0]));
-      t3[i] = fma(a.fr.R[3 * i + 2], beta[2], fma(a.fr.R[3 * i + 1], beta[1], a.fr.R[3 * i] * beta[0]));
+      t1[i] = fma(fr.R[3 * i + 2], n_dn[2], fma(fr.R[3 * i + 1], n_dn[1], fr.R[3 * i] * n_dn[0]));
+      t2[i] = fma(fr.R[3 * i + 2], n_up[2], fma(fr.R[3 * i + 1], n_up[1], fr.R[3 * i] * n_up[0]));
+      t3[i] = fma(fr.R[3 * i + 2], beta[2], fma(fr.R[3 * i + 1], beta[1], fr.R[3 * i] * beta[0]));
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -1011,7 +1018,7 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
       // constraint preserving for u^psi and u^0, freezing for u^- (and u^+)
       if (v_psi < 0.0 || v_0 < 0.0) {
         double nC3, Pm[3];
-        cp_corrections(a, sl, q, p, n_dn, n_up, nC3, Pm);
+        cp_corrections(a, fr, sl, q, p, n_dn, n_up, nC3, Pm);
         if (v_psi < 0.0) c.psi = fma(v_psi, nC3, c.psi);
         if (v_0 < 0.0) {
 #pragma unroll
@@ -1025,9 +1032,9 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     if (v_p < 0.0) c.wp = 0.0;
     if (v_m < 0.0) c.wm = 0.0;
     double adv[5];
-    if (a.fr.on) frame_adv(a, sl.shell_a, a.shells[sl.shell_a].n_r - 1, base, na, p, q, adv);
+    if (fr.on) frame_adv(a, fr, sl.shell_a, a.shells[sl.shell_a].n_r - 1, base, na, p, q, adv);
     char_write_pair(a, base, na, p, c, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
-                    a.fr.on ? adv : nullptr);
+                    fr.on ? adv : nullptr);
   } else {
     const long long ba = sl.off_a + q, bb = sl.off_b + q;
     CharPair ci, co;
@@ -1039,14 +1046,14 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
     select_pair(ci.wp, co.wp, v_p);
     select_pair(ci.wm, co.wm, v_m);
     double adv_a[5], adv_b[5];
-    if (a.fr.on) {
-      frame_adv(a, sl.shell_a, a.shells[sl.shell_a].n_r - 1, ba, na, p, q, adv_a);
-      frame_adv(a, sl.shell_b, 0, bb, na, p, q, adv_b);
+    if (fr.on) {
+      frame_adv(a, fr, sl.shell_a, a.shells[sl.shell_a].n_r - 1, ba, na, p, q, adv_a);
+      frame_adv(a, fr, sl.shell_b, 0, bb, na, p, q, adv_b);
     }
     char_write_pair(a, ba, na, p, ci, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
-                    a.fr.on ? adv_a : nullptr);
+                    fr.on ? adv_a : nullptr);
     char_write_pair(a, bb, na, p, co, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
-                    a.fr.on ? adv_b : nullptr);
+                    fr.on ? adv_b : nullptr);
   }
 }
 
@@ -1096,7 +1103,8 @@ bc_background_kernel(const ShellDev* __restrict__ shells, BcSliceDev* slices, in
 __global__ void __launch_bounds__(PT_THREADS)
 cartesian_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                  const double* __restrict__ dr, const double* __restrict__ dth,
-                 const double* __restrict__ dph, double* __restrict__ du, long long state, Frame fr) {
+                 const double* __restrict__ dph, double* __restrict__ du, long long state, Frame fr,
+                 const Frame* __restrict__ frd) {
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int na = sh.na;
@@ -1108,6 +1116,7 @@ cartesian_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* _
   PointGeom G;
   point_geom(sh, ir, q, G);
   if (fr.on) {
+    if (frd) fr = *frd;
     double vel[3];
     frame_geom(fr, G, vel);
   }
@@ -1189,6 +1198,7 @@ cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const doubl
   a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
   a.dt = 0.0; a.stage = 0;
   a.fr = d->fr;
+  a.frd = d->fr.on ? d->frd : nullptr;
   if (a.fr.on)
     pointwise_kernel<true, false, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
   else
@@ -1219,6 +1229,7 @@ cudaError_t launch_pointwise(gh_domain* d, const double* u, double* k, int stage
   a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
   a.dt = dt; a.stage = stage;
   a.fr = d->fr;
+  a.frd = d->fr.on ? d->frd : nullptr;
   if (a.fr.on) {
     if (constraints)
       pointwise_kernel<true, true, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
@@ -1243,6 +1254,7 @@ cudaError_t launch_constraints(gh_domain* d, const double* u, double* c_out) {
   a.gamma0 = d->params.gamma0; a.gamma1 = d->params.gamma1; a.gamma2 = d->params.gamma2;
   a.dt = 0.0; a.stage = 0;
   a.fr = d->fr;
+  a.frd = d->fr.on ? d->frd : nullptr;
   if (a.fr.on)
     pointwise_kernel<false, true, true><<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(a);
   else
@@ -1272,6 +1284,7 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
   a.dth = deriv ? deriv[1] : d->d_th;
   a.dph = deriv ? deriv[2] : d->d_ph;
   a.fr = d->fr;
+  a.frd = d->fr.on ? d->frd : nullptr;
   if (a.cp_outer && !u_in) return cudaErrorInvalidValue;
   bc_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(a);
   d->launches++;
@@ -1286,10 +1299,52 @@ cudaError_t launch_bc_background(gh_domain* d, const double* u, int bh) {
   return cudaGetLastError();
 }
 
+// The rotating frame at n times clock + off[i] (Rodrigues, as on the host),
+// then clock += advance; one thread.  Kernels of the same step read the
+// frames, never the clock, so captured graphs replay with the live clock.
+__global__ void frame_kernel(double* clock, double e0, double e1, double e2, double omega, FrameOffsets fo,
+                             double advance, Frame* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double t0 = *clock;
+  const double K[9] = {0.0, -e2, e1, e2, 0.0, -e0, -e1, e0, 0.0};
+  for (int i = 0; i < fo.n; ++i) {
+    const double th = omega * (t0 + fo.off[i]);
+    double sn, c;
+    sincos(th, &sn, &c);
+    Frame f;
+    f.on = 1;
+    for (int r = 0; r < 3; ++r)
+      for (int col = 0; col < 3; ++col) {
+        double k2 = 0.0;
+        for (int m = 0; m < 3; ++m) k2 += K[3 * r + m] * K[3 * m + col];
+        f.R[3 * r + col] = (r == col ? 1.0 : 0.0) + sn * K[3 * r + col] + (1.0 - c) * k2;
+      }
+    f.w[0] = omega * e0;
+    f.w[1] = omega * e1;
+    f.w[2] = omega * e2;
+    out[i] = f;
+  }
+  if (advance != 0.0) *clock = t0 + advance;
+}
+
+cudaError_t launch_frames(gh_domain* d, const double* off, int n, double advance) {
+  if (d->rot_omega == 0.0 || !d->clock_d) return cudaSuccess;
+  if (n < 0 || n > 8) return cudaErrorInvalidValue;
+  FrameOffsets fo;
+  fo.n = n;
+  for (int i = 0; i < 8; ++i) fo.off[i] = i < n ? off[i] : 0.0;
+  const double nrm = std::sqrt(d->rot_axis[0] * d->rot_axis[0] + d->rot_axis[1] * d->rot_axis[1] +
+                               d->rot_axis[2] * d->rot_axis[2]);
+  frame_kernel<<<1, 32, 0, d->stream>>>(d->clock_d, d->rot_axis[0] / nrm, d->rot_axis[1] / nrm,
+                                        d->rot_axis[2] / nrm, d->rot_omega, fo, advance, d->frames_d);
+  d->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cartesian(gh_domain* d, const double* u, double* du) {
   (void)u;
   cartesian_kernel<<<d->pt_blocks, PT_THREADS, 0, d->stream>>>(
-      d->shells_d, d->n_shells, d->pt_block_begin_d, d->d_r, d->d_th, d->d_ph, du, d->state, d->fr);
+      d->shells_d, d->n_shells, d->pt_block_begin_d, d->d_r, d->d_th, d->d_ph, du, d->state, d->fr, d->frd);
   d->launches++;
   return cudaGetLastError();
 }

@@ -66,7 +66,11 @@ extern "C" gh_status gh_rhs_noalloc(gh_domain* d, const double* u, double* dudt)
     return GH_EINVAL;
   }
   double* w = nullptr;
-  d->fr = gh::frame_at(d, d->time);
+  if (e == cudaSuccess && d->rot_omega != 0.0) {
+    const double off = 0.0;            // the frame at the domain clock
+    e = gh::launch_frames(d, &off, 1, 0.0);
+    d->frd = d->frames_d;
+  }
   if (e == cudaSuccess) e = work_area(dev, &w);
   if (e == cudaSuccess) e = gh::launch_radial(d, u, w, false);
   if (e == cudaSuccess) e = gh::launch_angular_deriv_into(d, u, w + kMaxState, w + 2 * kMaxState);

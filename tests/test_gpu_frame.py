@@ -2,7 +2,8 @@
 SpatialCoordJac) with the oracle through the C ABI: right-hand sides at a
 given time and RK4 steps that advance the domain's clock, on a Schwarzschild
 shell rotating about a tilted axis and on two Kerr shells rotating about the
-spin axis; a static frame after a rotating one; the refusals."""
+spin axis; captured RK4 graphs that replay with the live clock; a static
+frame after a rotating one; the refusals."""
 import numpy as np
 import pytest
 import torch
@@ -119,8 +120,6 @@ def test_static_again_and_refusals():
     gh.gh_set_rotating_frame(dom, axis, omega)
     gh.gh_set_time(dom, 2.0)
     with pytest.raises(RuntimeError):
-        gh.gh_rk4_graph_capture(dom, w.dt, u.clone(), dom.new_work())
-    with pytest.raises(RuntimeError):
         gh.gh_rhs_vjp(dom, u, u.clone(), torch.zeros_like(u))
     with pytest.raises(RuntimeError):
         gh.gh_set_rotating_frame(dom, (0.0, 0.0, 0.0), 1.0)
@@ -128,3 +127,36 @@ def test_static_again_and_refusals():
     gh.gh_rhs(dom, u, k1)
     torch.cuda.synchronize()
     assert torch.equal(k0, k1)
+
+
+def test_captured_graph_replays_with_the_live_clock(case):
+    """The stage frames come from the device clock, so a captured RK4 step
+    replayed n times equals n direct steps bit for bit (each replay sees its
+    own time) and advances the domain's clock by n dt; and both equal the
+    oracle's moving-frame steps."""
+    gh = _gh()
+    w, axis, omega, odom, u0 = case
+    dom = _dom(w, odom, axis, omega)
+    gh.gh_set_time(dom, 0.1)
+    a = to_dev(flat(u0))
+    work = dom.new_work()
+    for _ in range(3):
+        gh.gh_rk4_step(dom, w.dt, a, work)
+    gh.gh_set_time(dom, 0.1)
+    b = to_dev(flat(u0))
+    work2 = dom.new_work()
+    gh.gh_rk4_graph_capture(dom, w.dt, b, work2)
+    assert abs(gh.gh_get_time(dom) - 0.1) < 1e-15
+    gh.gh_rk4_graph_launch(dom, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert abs(gh.gh_get_time(dom) - (0.1 + 3 * w.dt)) < 1e-15
+    ou, t = u0, 0.1
+    for _ in range(3):
+        ou = frame.rk4_step(odom, ou, t, w.dt, axis, omega)
+        t += w.dt
+    assert np.abs(to_host(b) - flat(ou)).max() <= REL_TOL * np.abs(flat(u0)).max()
+    # after the replays, a direct step continues from the advanced clock
+    gh.gh_rk4_step(dom, w.dt, b, work2)
+    ou = frame.rk4_step(odom, ou, t, w.dt, axis, omega)
+    assert np.abs(to_host(b) - flat(ou)).max() <= REL_TOL * np.abs(flat(u0)).max()
