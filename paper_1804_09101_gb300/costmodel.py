@@ -72,10 +72,15 @@ def angular_filter_flops(shells):
 
 
 def radial_flops(shells):
+    """FP64 flops of one folded radial launch (radial_kernel), per column of
+    n_r values: the fold 2 h, the ceil(n_r/2) folded rows of n_r FMAs each,
+    and the outputs 2 h + (n_r mod 2), with h = floor(n_r/2)."""
     f = 0
-    for (_, _, n_r, L) in shells:
+    for sh in shells:
+        n_r, L = sh[2], sh[3]
         na = (L + 1) * 2 * (L + 1)
-        f += 2 * 50 * na * n_r * n_r
+        h = n_r // 2
+        f += 50 * na * (2 * h + 2 * (n_r - h) * n_r + 2 * h + n_r % 2)
     return f
 
 

@@ -162,6 +162,24 @@ std::vector<double> cgl_filter_matrix(int n, double alpha, int order) {
   return F;
 }
 
+// Folded rows of a centro-symmetric (sigma = +1) or centro-antisymmetric
+// (sigma = -1) n x n matrix for radial_kernel: rows i < ceil(n/2), each
+// [A_i0 .. A_i,h-1, (M_im for odd n), B_i,h-1 .. B_i0] with
+// A_ij = (M_ij + M_i,n-1-j)/2, B_ij = (M_ij - M_i,n-1-j)/2, h = n/2.
+std::vector<double> fold_radial_matrix(const std::vector<double>& M, int n) {
+  const int h = n / 2, ne = n - h;
+  std::vector<double> F((size_t)ne * n, 0.0);
+  for (int i = 0; i < ne; ++i) {
+    for (int j = 0; j < h; ++j) {
+      const double a = M[(size_t)i * n + j], b = M[(size_t)i * n + (n - 1 - j)];
+      F[(size_t)i * n + j] = 0.5 * (a + b);
+      F[(size_t)i * n + (n - 1 - j)] = 0.5 * (a - b);
+    }
+    if (n % 2) F[(size_t)i * n + h] = M[(size_t)i * n + h];
+  }
+  return F;
+}
+
 struct AngularGrid {
   int L, nth, nph, na;
   std::vector<double> ct, st, wgl;
@@ -789,8 +807,11 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     pts += (long long)sh.n_r * sh.na;
     if (!radial_cache.count(sh.n_r)) {
       double *Dd = nullptr, *Fd = nullptr;
-      CREATE_CUDA(upload(d, cgl_derivative_matrix(sh.n_r), &Dd));
-      CREATE_CUDA(upload(d, cgl_filter_matrix(sh.n_r, params->filt_alpha, params->filt_order > 0 ? params->filt_order : 1), &Fd));
+      CREATE_CUDA(upload(d, fold_radial_matrix(cgl_derivative_matrix(sh.n_r), sh.n_r), &Dd));
+      CREATE_CUDA(upload(d, fold_radial_matrix(cgl_filter_matrix(sh.n_r, params->filt_alpha,
+                                                                  params->filt_order > 0 ? params->filt_order : 1),
+                                               sh.n_r),
+                         &Fd));
       radial_cache[sh.n_r] = {Dd, Fd};
     }
     sh.Dr = radial_cache[sh.n_r].first;

@@ -117,8 +117,8 @@ struct ShellDev {
   long long off;                // offset of the shell in a state vector (doubles)
   long long pt_off;             // offset of the shell's first point
   double r_in, r_out, rscale;   // rscale = 2 / (r_out - r_in) = dx/dr
-  const double* Dr;             // [n_r][n_r] d/dx on the CGL points
-  const double* Fr;             // [n_r][n_r] exponential Chebyshev filter
+  const double* Dr;             // d/dx on the CGL points, folded rows [ceil(n_r/2)][n_r] (radial_kernel)
+  const double* Fr;             // exponential Chebyshev filter, folded rows [ceil(n_r/2)][n_r]
   const double* Bth;            // [na][na] transposed d/dtheta map (out = U * Bth)
   const double* Bph;            // [na][na] transposed d/dphi map
   const double* Sf;             // [na][na] transposed SH truncation filter (or null)

@@ -21,12 +21,21 @@ namespace gh {
 // ---------------------------------------------------------------------------
 // Radial contraction (the R part of Eq. DifferentiatorI1S2, and the radial
 // ExpCheb filter): out[r][col] = sum_r' M[r][r'] in[r'][col] for every column
-// col = (field, theta, phi) of every shell.  One thread per column; the block's
-// columns are staged in shared memory (coalesced loads along col), the rows
-// of M it needs sit in shared memory too.  blockIdx.y splits the output rows
-// into gridDim.y groups (more, shorter warps per FP64 unit); within a group CH
-// rows are computed per pass as independent FMA chains and the remainder
-// rows one at a time, so no FMA works on padding.
+// col = (field, theta, phi) of every shell.  The CGL points are symmetric
+// (x_{n-1-j} = -x_j), so d/dx is centro-antisymmetric and the filter
+// centro-symmetric: with e_j = v_j + v_{n-1-j}, o_j = v_j - v_{n-1-j} (j < h =
+// n/2) and the middle value for odd n,
+//   out_i = E_i + O_i,  out_{n-1-i} = sigma (E_i - O_i)  (sigma = -1 for d/dx, +1),
+//   E_i = sum_j A_ij e_j (+ M_im v_m),  O_i = sum_j B_ij o_j,
+//   A_ij = (M_ij + M_i,n-1-j)/2,  B_ij = (M_ij - M_i,n-1-j)/2,
+// for the ceil(n/2) rows i <= n/2 only: half the FMAs of the plain product.
+// The host stores each folded row as [A_i0 .. A_i,h-1, (M_im), B_i,h-1 .. B_i0],
+// matching the column folded in place (e_j at j, o_j at n-1-j).  One thread per
+// column; the block's columns are staged in shared memory (coalesced loads
+// along col), the folded rows it needs sit in shared memory too.  blockIdx.y
+// splits the folded rows into gridDim.y groups (more, shorter warps per FP64
+// unit); within a group CH rows are computed per pass as independent FMA
+// chains and the remainder rows one at a time.
 constexpr int RAD_THREADS = RAD_THREADS_HOST;
 constexpr int MAXR = 64;
 
@@ -38,41 +47,64 @@ radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __re
   extern __shared__ double Vs[];           // [n_r][RAD_THREADS]
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
-  const int n = sh.n_r;
-  const double* M = FILTER ? sh.Fr : sh.Dr;
-  const int chunk = (n + gridDim.y - 1) / gridDim.y;
+  const int n = sh.n_r, h = n >> 1, ne = n - h;   // ne: even part incl. the middle value
+  const double* M = FILTER ? sh.Fr : sh.Dr;       // folded rows [ne][n]
+  const int chunk = (ne + gridDim.y - 1) / gridDim.y;
   const int r0 = blockIdx.y * chunk;
-  const int r1 = min(n, r0 + chunk);
+  const int r1 = min(ne, r0 + chunk);
   for (int i = threadIdx.x; i < (r1 - r0) * n; i += blockDim.x) Ms[i] = M[r0 * n + i];
   const long long cols = (long long)NF * sh.na;
   const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
   const bool valid = col < cols;
   const double* src = in + sh.off + col;
-  for (int r = 0; r < n; ++r) Vs[r * RAD_THREADS + threadIdx.x] = valid ? src[(long long)r * cols] : 0.0;
+  double* v = Vs + threadIdx.x;
+  for (int r = 0; r < n; ++r) v[r * RAD_THREADS] = valid ? src[(long long)r * cols] : 0.0;
+  for (int j = 0; j < h; ++j) {            // this thread's column, folded in place
+    const double a = v[j * RAD_THREADS], b = v[(n - 1 - j) * RAD_THREADS];
+    v[j * RAD_THREADS] = a + b;
+    v[(n - 1 - j) * RAD_THREADS] = a - b;
+  }
   __syncthreads();
-  if (!valid) return;
+  if (r0 >= r1 || !valid) return;
   double* dst = out + sh.off + col;
-  const double* v = Vs + threadIdx.x;
+  auto put = [&](int i, double E, double O) {
+    if (i < h) {
+      dst[(long long)i * cols] = E + O;
+      dst[(long long)(n - 1 - i) * cols] = FILTER ? E - O : O - E;
+    } else {
+      dst[(long long)i * cols] = E + O;    // middle row (odd n)
+    }
+  };
   int r = r0;
   for (; r + CH <= r1; r += CH) {
     const double* m0 = Ms + (r - r0) * n;
-    double acc[CH];
-    const double x0 = v[0];
+    double ae[CH], ao[CH];
+    const double x0 = v[0], y0 = v[ne * RAD_THREADS];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = m0[c * n] * x0;
-    for (int q = 1; q < n; ++q) {
+    for (int c = 0; c < CH; ++c) {
+      ae[c] = m0[c * n] * x0;
+      ao[c] = m0[c * n + ne] * y0;
+    }
+    for (int q = 1; q < ne; ++q) {
       const double x = v[q * RAD_THREADS];
 #pragma unroll
-      for (int c = 0; c < CH; ++c) acc[c] = fma(m0[c * n + q], x, acc[c]);
+      for (int c = 0; c < CH; ++c) ae[c] = fma(m0[c * n + q], x, ae[c]);
+    }
+    for (int q = ne + 1; q < n; ++q) {
+      const double x = v[q * RAD_THREADS];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) ao[c] = fma(m0[c * n + q], x, ao[c]);
     }
 #pragma unroll
-    for (int c = 0; c < CH; ++c) dst[(long long)(r + c) * cols] = acc[c];
+    for (int c = 0; c < CH; ++c) put(r + c, ae[c], ao[c]);
   }
   for (; r < r1; ++r) {
     const double* m0 = Ms + (r - r0) * n;
-    double acc = m0[0] * v[0];
-    for (int q = 1; q < n; ++q) acc = fma(m0[q], v[q * RAD_THREADS], acc);
-    dst[(long long)r * cols] = acc;
+    double E = m0[0] * v[0];
+    for (int q = 1; q < ne; ++q) E = fma(m0[q], v[q * RAD_THREADS], E);
+    double O = m0[ne] * v[ne * RAD_THREADS];
+    for (int q = ne + 1; q < n; ++q) O = fma(m0[q], v[q * RAD_THREADS], O);
+    put(r, E, O);
   }
 }
 
