@@ -42,12 +42,12 @@ constexpr int MAXR = 64;
 template <bool FILTER, int CH>
 __global__ void __launch_bounds__(RAD_THREADS)
 radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
-              const double* __restrict__ in, double* __restrict__ out) {
-  __shared__ double Ms[MAXR * MAXR];
-  extern __shared__ double Vs[];           // [n_r][RAD_THREADS]
+              const double* __restrict__ in, double* __restrict__ out, int max_n) {
+  extern __shared__ double Vs[];           // [max n_r][RAD_THREADS], then the block's folded rows
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int n = sh.n_r, h = n >> 1, ne = n - h;   // ne: even part incl. the middle value
+  double* Ms = Vs + (size_t)max_n * RAD_THREADS;
   const double* M = FILTER ? sh.Fr : sh.Dr;       // folded rows [ne][n]
   const int chunk = (ne + gridDim.y - 1) / gridDim.y;
   const int r0 = blockIdx.y * chunk;
@@ -117,8 +117,13 @@ cudaError_t raise_smem_limit(const void* f, size_t bytes, size_t* current) {
   return e;
 }
 
+// Dynamic shared memory of radial_kernel: the columns and the folded rows.
+size_t radial_smem_bytes(int max_n) {
+  return sizeof(double) * ((size_t)max_n * RAD_THREADS + (size_t)(max_n - max_n / 2) * max_n);
+}
+
 cudaError_t radial_set_smem_limits() {
-  const size_t bytes = sizeof(double) * MAXR * RAD_THREADS;
+  const size_t bytes = radial_smem_bytes(MAXR);
   static size_t cur[6] = {0, 0, 0, 0, 0, 0};
   const void* f[6] = {(const void*)radial_kernel<true, 2>, (const void*)radial_kernel<true, 3>,
                       (const void*)radial_kernel<true, 4>, (const void*)radial_kernel<false, 2>,
@@ -1188,12 +1193,12 @@ __global__ void norm_reduce_kernel(const int* __restrict__ begin, int n_shells,
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter) {
-  const size_t smem = sizeof(double) * (size_t)d->max_n_r * RAD_THREADS;
+  const size_t smem = radial_smem_bytes(d->max_n_r);
   const int ch = filter ? d->radf_chains : d->rad_chains;
   const dim3 grid(d->rad_blocks, filter ? d->radf_groups : d->rad_groups);
 #define GH_RAD(F, C)                                                                       \
   radial_kernel<F, C><<<grid, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,    \
-                                                               d->rad_block_begin_d, in, out)
+                                                               d->rad_block_begin_d, in, out, d->max_n_r)
   if (filter) {
     if (ch == 4) GH_RAD(true, 4); else if (ch == 3) GH_RAD(true, 3); else GH_RAD(true, 2);
   } else {
