@@ -22,30 +22,57 @@
 namespace gh {
 
 // ---------------------------------------------------------------------------
-// Transposed radial map: out[r][col] (+)= sum_q M^T[r][q] in[q][col].
+// Transposed radial map: out[r][col] (+)= sum_q M^T[r][q] in[q][col].  M^T
+// keeps the centro-(anti)symmetry of M, so the column is folded as in the
+// forward radial kernel and the folded rows of M^T (the exact transposes of
+// the folded forward operators) are applied: half the FMAs.
 constexpr int ADJ_RAD_THREADS = 128;
+
+size_t radial_adjoint_smem_bytes(int max_n) {
+  return sizeof(double) * ((size_t)max_n * ADJ_RAD_THREADS + (size_t)(max_n - max_n / 2) * max_n);
+}
 
 template <bool FILTER, bool ACCUM>
 __global__ void __launch_bounds__(ADJ_RAD_THREADS)
 radial_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
-                      const double* __restrict__ in, double* __restrict__ out) {
-  __shared__ double Ms[64 * 64];
+                      const double* __restrict__ in, double* __restrict__ out, int max_n) {
+  extern __shared__ double Vs[];           // [max n_r][ADJ_RAD_THREADS], then the folded rows
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
-  const int n = sh.n_r;
-  const double* M = FILTER ? sh.FrT : sh.DrT;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ms[i] = M[i];
-  __syncthreads();
+  const int n = sh.n_r, h = n >> 1, ne = n - h;
+  double* Ms = Vs + (size_t)max_n * ADJ_RAD_THREADS;
+  const double* M = FILTER ? sh.FrT : sh.DrT;     // folded rows of M^T [ne][n]
+  for (int i = threadIdx.x; i < ne * n; i += blockDim.x) Ms[i] = M[i];
   const long long cols = (long long)NF * sh.na;
   const long long col = (long long)(blockIdx.x - begin[s]) * blockDim.x + threadIdx.x;
-  if (col >= cols) return;
+  const bool valid = col < cols;
   const double* src = in + sh.off + col;
+  double* v = Vs + threadIdx.x;
+  for (int r = 0; r < n; ++r) v[r * ADJ_RAD_THREADS] = valid ? src[(long long)r * cols] : 0.0;
+  for (int j = 0; j < h; ++j) {
+    const double a = v[j * ADJ_RAD_THREADS], b = v[(n - 1 - j) * ADJ_RAD_THREADS];
+    v[j * ADJ_RAD_THREADS] = a + b;
+    v[(n - 1 - j) * ADJ_RAD_THREADS] = a - b;
+  }
+  __syncthreads();
+  if (!valid) return;
   double* dst = out + sh.off + col;
-  for (int r = 0; r < n; ++r) {
-    double acc = 0.0;
-    for (int q = 0; q < n; ++q) acc = fma(Ms[r * n + q], src[(long long)q * cols], acc);
+  auto put = [&](int r, double x) {
     const long long o = (long long)r * cols;
-    dst[o] = ACCUM ? dst[o] + acc : acc;
+    dst[o] = ACCUM ? dst[o] + x : x;
+  };
+  for (int i = 0; i < ne; ++i) {
+    const double* m0 = Ms + i * n;
+    double E = m0[0] * v[0];
+    for (int q = 1; q < ne; ++q) E = fma(m0[q], v[q * ADJ_RAD_THREADS], E);
+    double O = m0[ne] * v[ne * ADJ_RAD_THREADS];
+    for (int q = ne + 1; q < n; ++q) O = fma(m0[q], v[q * ADJ_RAD_THREADS], O);
+    if (i < h) {
+      put(i, E + O);
+      put(n - 1 - i, FILTER ? E - O : O - E);
+    } else {
+      put(i, E + O);
+    }
   }
 }
 
@@ -488,6 +515,14 @@ gh_status afail(gh_domain* d, gh_status s, const std::string& m) {
 
 unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+cudaError_t radial_adjoint_smem_limits() {
+  static size_t cur[2] = {0, 0};
+  const size_t bytes = gh::radial_adjoint_smem_bytes(64);
+  cudaError_t e = gh::raise_smem_limit((const void*)gh::radial_adjoint_kernel<false, true>, bytes, &cur[0]);
+  if (e == cudaSuccess) e = gh::raise_smem_limit((const void*)gh::radial_adjoint_kernel<true, false>, bytes, &cur[1]);
+  return e;
+}
+
 gh_status adj_ready(gh_domain* d) {
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
   if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
@@ -497,6 +532,7 @@ gh_status adj_ready(gh_domain* d) {
     d->adj_cpbar = (double*)p;
   }
   if (d->rot_omega != 0.0) return afail(d, GH_ENOTSUP, "the adjoint is built for a static grid only");
+  GH_ACUDA(d, radial_adjoint_smem_limits());
   if (!d->kbt) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * d->state));
@@ -523,8 +559,9 @@ cudaError_t fwd_derivs(gh_domain* d, const double* u) {
 
 // ubar += (transposed derivative maps) applied to the cotangents in d_r, d_th, d_ph.
 cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {
-  gh::radial_adjoint_kernel<false, true><<<d->rad_blocks, gh::ADJ_RAD_THREADS, 0, d->stream>>>(
-      d->shells_d, d->n_shells, d->rad_block_begin_d, d->d_r, ubar);
+  gh::radial_adjoint_kernel<false, true><<<d->rad_blocks, gh::ADJ_RAD_THREADS,
+                                           gh::radial_adjoint_smem_bytes(d->max_n_r), d->stream>>>(
+      d->shells_d, d->n_shells, d->rad_block_begin_d, d->d_r, ubar, d->max_n_r);
   d->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -747,8 +784,9 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
   }
   if (d->params.radial_filter_on) {
     double* dst = (gin == g) ? kb : g;
-    gh::radial_adjoint_kernel<true, false><<<d->rad_blocks, gh::ADJ_RAD_THREADS, 0, d->stream>>>(
-        d->shells_d, d->n_shells, d->rad_block_begin_d, gin, dst);
+    gh::radial_adjoint_kernel<true, false><<<d->rad_blocks, gh::ADJ_RAD_THREADS,
+                                             gh::radial_adjoint_smem_bytes(d->max_n_r), d->stream>>>(
+        d->shells_d, d->n_shells, d->rad_block_begin_d, gin, dst, d->max_n_r);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
     gin = dst;

@@ -824,8 +824,12 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
         return t;
       };
       double *DT = nullptr, *FT = nullptr;
-      CREATE_CUDA(upload(d, tr(cgl_derivative_matrix(sh.n_r), sh.n_r), &DT));
-      CREATE_CUDA(upload(d, tr(cgl_filter_matrix(sh.n_r, params->filt_alpha, params->filt_order > 0 ? params->filt_order : 1), sh.n_r), &FT));
+      CREATE_CUDA(upload(d, fold_radial_matrix(tr(cgl_derivative_matrix(sh.n_r), sh.n_r), sh.n_r), &DT));
+      CREATE_CUDA(upload(d, fold_radial_matrix(tr(cgl_filter_matrix(sh.n_r, params->filt_alpha,
+                                                                      params->filt_order > 0 ? params->filt_order : 1),
+                                                   sh.n_r),
+                                                sh.n_r),
+                         &FT));
       radial_t_cache[sh.n_r] = {DT, FT};
     }
     sh.DrT = radial_t_cache[sh.n_r].first;

@@ -142,8 +142,8 @@ struct ShellDev {
   FoldPlan fd;                  // folded d/dtheta, d/dphi (M = 0 if not applicable)
   FoldPlan ff;                  // folded SH filter
   TensorFilterPlan tf;          // tensor-harmonic SH filter (used when selected)
-  const double* DrT;            // [n_r][n_r] transpose of Dr
-  const double* FrT;            // [n_r][n_r] transpose of Fr
+  const double* DrT;            // transpose of d/dx, folded rows [ceil(n_r/2)][n_r] (reverse mode)
+  const double* FrT;            // transpose of the filter, folded rows
 };
 
 // A boundary slice: the outer boundary of the last shell (kind 0) or an
