@@ -321,8 +321,8 @@ gh_status gh_set_outer_bc(gh_domain* dom, int mode);
  *   harmonics sY_lm, |s| <= l <= keep, and the tensor is rebuilt with the dual
  *   frame.  keep is the domain's sh_keep_l (per shell for -2).  Uses a device
  *   buffer of 62 doubles per grid point (the 31 independent complex frame
- *   components), allocated by the first switch to this mode (GH_ECUDA if it
- *   does not fit).  The adjoint entry points use the filter's transpose (the
+ *   components), allocated by the first switch to this mode on a domain with
+ *   an angular filter (GH_ECUDA if it does not fit).  The adjoint entry points use the filter's transpose (the
  *   spin projection is self-adjoint under the quadrature weights).
  *   Synchronises the stream and discards a captured RK4 graph; GH_EINVAL for
  *   an unknown mode. */

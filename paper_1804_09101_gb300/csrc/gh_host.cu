@@ -1631,7 +1631,7 @@ gh_status gh_set_sh_filter(gh_domain* d, int mode) {
   if (mode != GH_SH_FILTER_COMPONENT && mode != GH_SH_FILTER_TENSOR)
     return fail(d, GH_EINVAL, "mode must be GH_SH_FILTER_COMPONENT or GH_SH_FILTER_TENSOR");
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
-  if (mode == GH_SH_FILTER_TENSOR && !d->tf_buf) {
+  if (mode == GH_SH_FILTER_TENSOR && !d->tf_buf && d->params.sh_keep_l != -1) {
     std::vector<std::vector<double>> xs, ws;
     for (const auto& sh : d->shells_h) {
       const AngularGrid ag = angular_grid(sh.L);

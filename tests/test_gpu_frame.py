@@ -160,3 +160,31 @@ def test_captured_graph_replays_with_the_live_clock(case):
     gh.gh_rk4_step(dom, w.dt, b, work2)
     ou = frame.rk4_step(odom, ou, t, w.dt, axis, omega)
     assert np.abs(to_host(b) - flat(ou)).max() <= REL_TOL * np.abs(flat(u0)).max()
+
+
+def test_noalloc_rhs_and_constraints_follow_the_clock():
+    """gh_rhs_noalloc takes its frame from the device clock like gh_rhs (bit for
+    bit), and the constraint norm of the rotating exact solution stays at its
+    truncation level at any time."""
+    gh = _gh()
+    w, axis, omega = _schw()
+    odom = oracle_domain(w)
+    u0 = oracle_initial_state(w, odom)
+    dom = _dom(w, odom, axis, omega)
+    u = to_dev(flat(u0))
+    for t in (0.0, 0.9, 2.3):
+        gh.gh_set_time(dom, t)
+        k1, k2 = dom.new_state(), dom.new_state()
+        gh.gh_rhs(dom, u, k1)
+        gh.gh_rhs_noalloc(dom, u, k2)
+        torch.cuda.synchronize()
+        assert torch.equal(k1, k2), t
+    gh.gh_set_time(dom, 0.0)
+    n0 = torch.zeros(len(w.shells), dtype=torch.float64, device="cuda")
+    gh.gh_constraints(dom, u, None, n0)
+    ue = to_dev(flat(frame.exact_state(odom, 1.7, axis, omega)))
+    gh.gh_set_time(dom, 1.7)
+    n1 = torch.zeros(len(w.shells), dtype=torch.float64, device="cuda")
+    gh.gh_constraints(dom, ue, None, n1)
+    torch.cuda.synchronize()
+    assert float(n1.sum()) <= 10 * float(n0.sum()) + 1e-20
