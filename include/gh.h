@@ -288,8 +288,12 @@ gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
  * advance it and use their stage times.  The clock also lives on the device
  * and each step computes its stage frames from it there, so a captured RK4
  * graph replays with the live time (each gh_rk4_graph_launch of n steps
- * advances the clock by n dt).  With omega != 0: the adjoint entry points
- * return GH_ENOTSUP, as do steps on domains with a dt scale other than 1.
+ * advances the clock by n dt).  The adjoint entry points evaluate at the
+ * clock too (gh_rk4_step_vjp: the clock is the time of u_n; the step's stage
+ * times follow from it), with the rotated DiffJac, gauge source and boundary
+ * background transposed and the grid-velocity term's transpose added.  With
+ * omega != 0, steps and adjoint calls on domains with a dt scale other than 1
+ * return GH_ENOTSUP (one clock per domain).
  * gh_set_rotating_frame and gh_set_time synchronise the stream;
  * gh_set_rotating_frame discards a captured graph; GH_EINVAL for a zero axis
  * or a non-finite rate. */

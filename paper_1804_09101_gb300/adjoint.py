@@ -84,7 +84,18 @@ def constraint_energy_gradient(dom, u0, dt, n_steps, ckpt=20):
     checkpoints u_0, u_ckpt, ... and, for the last segment, every state and its
     RK4 stage states; the reverse pass walks the segments (a, b] backwards,
     recomputing the other segments' states and stages from their checkpoints.
+
+    With a rotating frame every evaluation runs at the domain clock, so the
+    clock is set to t_0 + n dt before each step that is saved, recomputed or
+    reversed (gh_rk4_step_save leaves it alone); on return it reads t_0 + N dt.
     """
+    rot = getattr(dom, "rotating", False)
+    t0 = gh.gh_get_time(dom) if rot else 0.0
+
+    def clock(n):
+        if rot:
+            gh.gh_set_time(dom, t0 + n * dt)
+
     work = dom.new_work()
     vwork = gh.new_vjp_work(dom)
     N = dom.state_size
@@ -99,12 +110,14 @@ def constraint_energy_gradient(dom, u0, dt, n_steps, ckpt=20):
             saved_states = [u.clone()]
             saved_stages = torch.empty((n_steps - last, 3 * N), dtype=torch.float64, device=u0.device)
         if n - 1 >= last:
+            clock(n - 1)
             gh.gh_rk4_step_save(dom, dt, u, work, saved_stages[n - 1 - last], norms[n - 1])
             saved_states.append(u.clone())
         else:
             gh.gh_rk4_step(dom, dt, u, work, norms[n - 1])
         if n % ckpt == 0 and n < n_steps:
             checkpoints[n] = u.clone()
+    clock(n_steps)
     gh.gh_constraints(dom, u, None, norms[n_steps])
     E = float(dt * norms[1:].sum())
     lam = torch.zeros_like(u0)
@@ -118,13 +131,17 @@ def constraint_energy_gradient(dom, u0, dt, n_steps, ckpt=20):
             stages = torch.empty((b - a, 3 * N), dtype=torch.float64, device=u0.device)
             s = checkpoints[a].clone()
             for i in range(a, b):
+                clock(i)
                 gh.gh_rk4_step_save(dom, dt, s, work, stages[i - a])
                 states.append(s.clone())
         if b == n_steps:
+            clock(n_steps)
             gh.gh_constraint_energy_vjp(dom, states[b - a], dt, lam)      # lam_N = dt grad C(u_N)
         for n in range(b, a, -1):
             # lam_{n-1} = S'(u_{n-1})^T lam_n + dt grad C(u_{n-1}) (no C term for u_0)
             cw = dt if n - 1 >= 1 else 0.0
+            clock(n - 1)
             gh.gh_rk4_step_vjp_saved(dom, dt, states[n - 1 - a], stages[n - 1 - a], lam, nxt, vwork, cw)
             lam, nxt = nxt, lam
+    clock(n_steps)
     return E, lam

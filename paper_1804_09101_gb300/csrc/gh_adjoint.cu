@@ -213,7 +213,8 @@ __device__ __forceinline__ void select_transpose(double& wi, double& wo, double 
 // are stashed in cpbar[(p * npts + point) * 4 + {0, 1..3}] for cp_adjoint_kernel.
 __global__ void __launch_bounds__(128)
 bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int* __restrict__ pt_begin,
-                  double* __restrict__ kb, double gamma1, double gamma2, int cp, double* __restrict__ cpbar) {
+                  double* __restrict__ kb, double gamma1, double gamma2, int cp, double* __restrict__ cpbar,
+                  const Frame* __restrict__ frd) {
   const int npts = pt_begin[n_slices];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 10 * npts) return;
@@ -230,6 +231,7 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
     beta[i] = sl.bg[(long long)(7 + i) * na + q];
   }
   const double alpha = sl.bg[(long long)6 * na + q];
+  if (frd) frame_rotate_bg(*frd, n_dn, n_up, beta);   // the background at the moving point
   const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
   const double v_psi = -(1.0 + gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
   if (sl.kind == 0) {
@@ -282,7 +284,7 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
 __global__ void __launch_bounds__(128)
 cp_adjoint_kernel(const ShellDev* __restrict__ shells, const BcSliceDev* __restrict__ slices, int n_slices,
                   const int* __restrict__ pt_begin, const double* __restrict__ cpbar, double* dr, double* dth,
-                  double* dph, double* ubar) {
+                  double* dph, double* ubar, const Frame* __restrict__ frd) {
   const int npts = pt_begin[n_slices];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 10 * npts) return;
@@ -304,6 +306,11 @@ cp_adjoint_kernel(const ShellDev* __restrict__ shells, const BcSliceDev* __restr
   const ShellDev& sh = shells[sl.shell_a];
   PointGeom G;
   point_geom(sh, sh.n_r - 1, q, G);
+  if (frd) {
+    double beta[3] = {0.0, 0.0, 0.0}, vel[3];
+    frame_rotate_bg(*frd, n_dn, n_up, beta);
+    frame_geom(*frd, G, vel);
+  }
   const long long base = sl.off_a + q;
   auto add_d = [&](int f, const double v[3]) {   // D_d bar of field f += sum_i J_i^d v_i
     const long long o = base + (long long)f * na;
@@ -352,7 +359,8 @@ __global__ void __launch_bounds__(ADJ_PT_THREADS, GH_ADJ_MINB)
 pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                          const double* __restrict__ u, double* dr, double* dth, double* dph,
                          const double* __restrict__ kb, double* ubar, double g0, double g1, double g2,
-                         double weight, int assign) {
+                         double weight, int assign, const Frame* __restrict__ frd = nullptr,
+                         const double* __restrict__ kb0 = nullptr) {
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
   const int na = sh.na;
@@ -378,6 +386,13 @@ pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, cons
   for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
   PointGeom G;
   point_geom(sh, ir, q, G);
+  double vel[3] = {0.0, 0.0, 0.0};
+  if (frd) {                      // rotating frame: J <- R J, rotated gauge source
+    const Frame fr = *frd;
+    frame_geom(fr, G, vel);
+    frame_rotate_h(fr, H);
+    frame_rotate_dh(fr, dH);
+  }
   PointIn in;
   in.u = uu;
   in.ds = ds;
@@ -402,6 +417,16 @@ pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, cons
   if (MODE == 2) {
     const int j = q / sh.nph;
     constraint_part(in, weight * sh.wr[ir] * sh.wth[j], ub, dsb);
+  }
+  if (MODE != 1 && frd && kb0) {
+    // the grid-velocity term xdot . (J d u) of every point (added after the
+    // boundary conditions), transposed with the cotangent of the final rate
+    double vs[3];
+    for (int d = 0; d < 3; ++d) vs[d] = vel[0] * G.J[0][d] + vel[1] * G.J[1][d] + vel[2] * G.J[2][d];
+    for (int f = 0; f < NF; ++f) {
+      const double kv = kb0[base + (long long)f * na];
+      for (int d = 0; d < 3; ++d) dsb[3 * f + d] = fma(vs[d], kv, dsb[3 * f + d]);
+    }
   }
   for (int f = 0; f < NF; ++f) {
     const long long o = base + (long long)f * na;
@@ -523,6 +548,16 @@ cudaError_t radial_adjoint_smem_limits() {
   return e;
 }
 
+// Rotating frame: the frames of the domain clock + {0, dt/2, dt} (n of them)
+// into the device frame array; the clock does not move (no-op when static).
+gh_status frames_at(gh_domain* d, double half, double full, int n) {
+  if (d->rot_omega == 0.0) return GH_OK;
+  const double off[3] = {0.0, half, full};
+  GH_ACUDA(d, gh::launch_frames(d, off, n, 0.0));
+  d->frd = d->frames_d;
+  return GH_OK;
+}
+
 gh_status adj_ready(gh_domain* d) {
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
   if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
@@ -531,7 +566,9 @@ gh_status adj_ready(gh_domain* d) {
     d->owned.push_back(p);
     d->adj_cpbar = (double*)p;
   }
-  if (d->rot_omega != 0.0) return afail(d, GH_ENOTSUP, "the adjoint is built for a static grid only");
+  if (d->rot_omega != 0.0)
+    for (const auto& sh : d->shells_h)
+      if (sh.dt_scale != 1.0) return afail(d, GH_ENOTSUP, "the rotating frame needs dt_scale = 1 on every shell");
   GH_ACUDA(d, radial_adjoint_smem_limits());
   if (!d->kbt) {
     void* p = nullptr;
@@ -652,14 +689,15 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
   GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
   const int cp = d->outer_bc == GH_BC_CONSTRAINT_PRESERVING;
+  const gh::Frame* frd = d->rot_omega != 0.0 ? d->frd : nullptr;
   if (d->bc_points) {
     gh::bc_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
         d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->kbt, d->params.gamma1, d->params.gamma2, cp,
-        d->adj_cpbar);
+        d->adj_cpbar, frd);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
-  if (d->adj_pair_split) {
+  if (d->adj_pair_split && !frd) {
     // small grid: ten threads per point (one per symmetric pair)
     if (!d->adj_ubp) {
       void* p = nullptr;
@@ -686,17 +724,18 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
     if (cweight != 0.0)
       gh::pointwise_adjoint_kernel<2><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
           d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
-          d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight, assign ? 1 : 0);
+          d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight, assign ? 1 : 0, frd, kb);
     else
       gh::pointwise_adjoint_kernel<0><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
           d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
-          d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0);
+          d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0, frd, kb);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
   if (cp && d->bc_points) {
     gh::cp_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
-        d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpbar, d->d_r, d->d_th, d->d_ph, ubar);
+        d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpbar, d->d_r, d->d_th, d->d_ph, ubar,
+        frd);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
@@ -721,16 +760,19 @@ long long gh_rk4_vjp_work_size(const gh_domain* d) { return d ? 7 * d->state : -
 gh_status gh_rhs_vjp(gh_domain* d, const double* u, const double* kbar, double* ubar) {
   if (!d || !u || !kbar || !ubar) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
   if (gh_status s = adj_ready(d)) return s;
+  if (gh_status s = frames_at(d, 0.0, 0.0, 1)) return s;
   return rhs_vjp(d, u, kbar, ubar);
 }
 
 gh_status gh_constraint_energy_vjp(gh_domain* d, const double* u, double weight, double* ubar) {
   if (!d || !u || !ubar) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
   if (gh_status s = adj_ready(d)) return s;
+  if (gh_status s = frames_at(d, 0.0, 0.0, 1)) return s;
   GH_ACUDA(d, fwd_derivs(d, u));
   gh::pointwise_adjoint_kernel<1><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
       d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, nullptr, ubar,
-      d->params.gamma0, d->params.gamma1, d->params.gamma2, weight, 0);
+      d->params.gamma0, d->params.gamma1, d->params.gamma2, weight, 0,
+      d->rot_omega != 0.0 ? d->frd : nullptr, nullptr);
   d->launches++;
   GH_ACUDA(d, cudaGetLastError());
   GH_ACUDA(d, derivs_transpose_add(d, ubar));
@@ -744,6 +786,9 @@ namespace {
 gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double* stages, const double* ubar_np1,
                         double* ubar_n, double* work, double cweight) {
   if (gh_status s = adj_ready(d)) return s;
+  // stage times t, t + dt/2, t + dt/2, t + dt of the step from the domain clock
+  if (gh_status s = frames_at(d, 0.5 * dt, dt, 3)) return s;
+  auto at = [&](int i) { if (d->frames_d) d->frd = d->frames_d + i; };
   const long long N = d->state;
   const double *u2, *u3, *u4;
   double* k = work + 3 * N;
@@ -759,8 +804,10 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
     double* w2 = work;
     double* w3 = work + N;
     double* w4 = work + 2 * N;
+    at(0);
     if (gh_status s = rhs_fwd(d, u_n, k)) return s;
     GH_ACUDA(d, ew(d, 0, w2, u_n, k, 0.0, 0.5, dt));
+    at(1);
     if (gh_status s = rhs_fwd(d, w2, k)) return s;
     GH_ACUDA(d, ew(d, 0, w3, u_n, k, 0.0, 0.5, dt));
     if (gh_status s = rhs_fwd(d, w3, k)) return s;
@@ -796,12 +843,15 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
   if (gin != g) GH_ACUDA(d, cudaMemcpyAsync(g, gin, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
   GH_ACUDA(d, cudaMemcpyAsync(ubar_n, g, sizeof(double) * N, cudaMemcpyDeviceToDevice, d->stream));
   GH_ACUDA(d, ew(d, 1, kb, g, g, 1.0 / 6.0, 0.0, dt));                 // kb4 = dt/6 g
+  at(2);
   if (gh_status s = rhs_vjp(d, u4, kb, sb, 0.0, true)) return s;       // sb = J(u4)^T kb4
   GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 3.0, 1.0, dt, ubar_n));        // kb3 = dt (g/3 + sb); ubar_n += sb
+  at(1);
   if (gh_status s = rhs_vjp(d, u3, kb, sb, 0.0, true)) return s;
   GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 3.0, 0.5, dt, ubar_n));        // kb2 = dt (g/3 + sb/2)
   if (gh_status s = rhs_vjp(d, u2, kb, sb, 0.0, true)) return s;
   GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 6.0, 0.5, dt, ubar_n));        // kb1 = dt (g/6 + sb/2)
+  at(0);
   return rhs_vjp(d, u_n, kb, ubar_n, cweight);
 }
 

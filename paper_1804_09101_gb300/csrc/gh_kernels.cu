@@ -386,52 +386,6 @@ __device__ __forceinline__ void stage_combine(int stage, double cdt, double kv, 
   }
 }
 
-// Rotating frame: DiffJac followed by the map's Jacobian, J <- R J (the
-// SpatialCoordJac of Sec. 3.3 for a rotation), and the grid velocity
-// w x (R x_grid) at the point.
-__device__ __forceinline__ void frame_geom(const Frame& fr, PointGeom& G, double vel[3]) {
-  double J2[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      J2[k][d] = fma(fr.R[3 * k + 2], G.J[2][d], fma(fr.R[3 * k + 1], G.J[1][d], fr.R[3 * k] * G.J[0][d]));
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) G.J[k][d] = J2[k][d];
-  double xi[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    xi[k] = G.r * fma(fr.R[3 * k + 2], G.xhat[2], fma(fr.R[3 * k + 1], G.xhat[1], fr.R[3 * k] * G.xhat[0]));
-  vel[0] = fr.w[1] * xi[2] - fr.w[2] * xi[1];
-  vel[1] = fr.w[2] * xi[0] - fr.w[0] * xi[2];
-  vel[2] = fr.w[0] * xi[1] - fr.w[1] * xi[0];
-}
-
-// Gauge source of a background invariant under the rotation, at the moving
-// point: H_a -> Lambda_a^b H_b, d_i H_a -> R_ij Lambda_a^b d_j H_b.
-__device__ __forceinline__ void frame_rotate_h(const Frame& fr, double H[4]) {
-  const double h1 = H[1], h2 = H[2], h3 = H[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) H[1 + i] = fma(fr.R[3 * i + 2], h3, fma(fr.R[3 * i + 1], h2, fr.R[3 * i] * h1));
-}
-__device__ __forceinline__ void frame_rotate_dh(const Frame& fr, double dH[12]) {
-  double t[12];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-      t[4 * i + a] = fma(fr.R[3 * i + 2], dH[8 + a], fma(fr.R[3 * i + 1], dH[4 + a], fr.R[3 * i] * dH[a]));
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    dH[4 * i] = t[4 * i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      dH[4 * i + 1 + a] = fma(fr.R[3 * a + 2], t[4 * i + 3], fma(fr.R[3 * a + 1], t[4 * i + 2], fr.R[3 * a] * t[4 * i + 1]));
-  }
-}
-
 #ifndef GH_PT_MINB
 #define GH_PT_MINB 9
 #endif
@@ -1028,22 +982,7 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
   }
   const double alpha = sl.bg[(long long)6 * na + q];
   const Frame fr = (a.fr.on && a.frd) ? *a.frd : a.fr;
-  if (fr.on) {
-    // the background's vectors at the moving point: rotated components
-    double t1[3], t2[3], t3[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      t1[i] = fma(fr.R[3 * i + 2], n_dn[2], fma(fr.R[3 * i + 1], n_dn[1], fr.R[3 * i] * n_dn[0]));
-      t2[i] = fma(fr.R[3 * i + 2], n_up[2], fma(fr.R[3 * i + 1], n_up[1], fr.R[3 * i] * n_up[0]));
-      t3[i] = fma(fr.R[3 * i + 2], beta[2], fma(fr.R[3 * i + 1], beta[1], fr.R[3 * i] * beta[0]));
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      n_dn[i] = t1[i];
-      n_up[i] = t2[i];
-      beta[i] = t3[i];
-    }
-  }
+  if (fr.on) frame_rotate_bg(fr, n_dn, n_up, beta);   // the background at the moving point
   const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
   const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
   const double g2 = a.gamma2;

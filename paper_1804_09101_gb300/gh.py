@@ -133,6 +133,7 @@ class Domain:
         self.handle = h
         self.shells = [tuple(s) for s in shells]
         self.state_size = _lib.gh_state_size(h)
+        self.rotating = False
         self.num_points = _lib.gh_num_points(h)
         self.work_size = _lib.gh_rk4_work_size(h)
         self.vjp_work_size = _lib.gh_rk4_vjp_work_size(h)
@@ -291,6 +292,7 @@ def gh_set_rotating_frame(dom, axis, omega):
     v = (ctypes.c_double * 3)(*[float(c) for c in axis])
     dom._stream()
     dom._check(_lib.gh_set_rotating_frame(dom.handle, v, float(omega)))
+    dom.rotating = float(omega) != 0.0
 
 
 def gh_set_time(dom, t):

@@ -2,8 +2,9 @@
 SpatialCoordJac) with the oracle through the C ABI: right-hand sides at a
 given time and RK4 steps that advance the domain's clock, on a Schwarzschild
 shell rotating about a tilted axis and on two Kerr shells rotating about the
-spin axis; captured RK4 graphs that replay with the live clock; a static
-frame after a rotating one; the refusals."""
+spin axis; captured RK4 graphs that replay with the live clock; the reverse
+mode in the moving frame against finite differences; a static frame after a
+rotating one; the refusals."""
 import numpy as np
 import pytest
 import torch
@@ -120,9 +121,14 @@ def test_static_again_and_refusals():
     gh.gh_set_rotating_frame(dom, axis, omega)
     gh.gh_set_time(dom, 2.0)
     with pytest.raises(RuntimeError):
-        gh.gh_rhs_vjp(dom, u, u.clone(), torch.zeros_like(u))
-    with pytest.raises(RuntimeError):
         gh.gh_set_rotating_frame(dom, (0.0, 0.0, 0.0), 1.0)
+    # one clock per domain: a hole with its own dt scale cannot rotate
+    gh.gh_set_dt_scale(dom, 0, 0.5)
+    with pytest.raises(RuntimeError):
+        gh.gh_rk4_step(dom, w.dt, u.clone(), dom.new_work())
+    with pytest.raises(RuntimeError):
+        gh.gh_rhs_vjp(dom, u, u.clone(), torch.zeros_like(u))
+    gh.gh_set_dt_scale(dom, 0, 1.0)
     gh.gh_set_rotating_frame(dom, axis, 0.0)
     gh.gh_rhs(dom, u, k1)
     torch.cuda.synchronize()
@@ -188,3 +194,75 @@ def test_noalloc_rhs_and_constraints_follow_the_clock():
     gh.gh_constraints(dom, ue, None, n1)
     torch.cuda.synchronize()
     assert float(n1.sum()) <= 10 * float(n0.sum()) + 1e-20
+
+
+def _fd_dot(gh, dom, fwd, u0, v, dw, h=1e-6):
+    up, um = fwd(to_dev(u0 + h * dw)), fwd(to_dev(u0 - h * dw))
+    return float(v @ ((up - um) / (2 * h)))
+
+
+def test_reverse_mode_in_the_moving_frame(case):
+    """<v, J w> by central differences equals <J^T v, w> for the RHS and the
+    RK4 step at a nonzero time: the reverse passes use the rotated DiffJac,
+    gauge and boundary background of each stage time and transpose the
+    grid-velocity term."""
+    gh = _gh()
+    w, axis, omega, odom, u0 = case
+    dom = _dom(w, odom, axis, omega)
+    x = flat(u0)
+    rng = np.random.default_rng(51)
+    v = rng.standard_normal(x.shape)
+    dw = rng.standard_normal(x.shape)
+
+    def rhs(u):
+        gh.gh_set_time(dom, 0.7)
+        k = dom.new_state()
+        gh.gh_rhs(dom, u, k)
+        return to_host(k)
+
+    def step(u):
+        gh.gh_set_time(dom, 0.7)
+        gh.gh_rk4_step(dom, w.dt, u, dom.new_work())
+        return to_host(u)
+
+    lhs = _fd_dot(gh, dom, rhs, x, v, dw)
+    gh.gh_set_time(dom, 0.7)
+    ub = dom.new_state()
+    gh.gh_rhs_vjp(dom, to_dev(x), to_dev(v), ub)
+    assert abs(lhs - float(to_host(ub) @ dw)) <= 1e-6 * abs(lhs)
+    lhs = _fd_dot(gh, dom, step, x, v, dw)
+    gh.gh_set_time(dom, 0.7)
+    ub = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, w.dt, to_dev(x), to_dev(v), ub, gh.new_vjp_work(dom))
+    assert abs(lhs - float(to_host(ub) @ dw)) <= 1e-6 * abs(lhs)
+    # without the frame terms the identity fails
+    gh.gh_set_rotating_frame(dom, axis, 0.0)
+    ub0 = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, w.dt, to_dev(x), to_dev(v), ub0, gh.new_vjp_work(dom))
+    assert abs(lhs - float(to_host(ub0) @ dw)) > 1e-3 * abs(lhs)
+
+
+def test_checkpointed_energy_gradient_in_the_moving_frame():
+    """The checkpointed gradient of the time-integrated constraint energy
+    (the clock set for every saved, recomputed and reversed step) against a
+    central difference of the forward evolution."""
+    from paper_1804_09101_gb300.adjoint import constraint_energy_gradient, evolve_energy
+    gh = _gh()
+    w, axis, omega = _schw()
+    odom = oracle_domain(w)
+    u0 = to_dev(flat(oracle_initial_state(w, odom)))
+    dom = _dom(w, odom, axis, omega)
+    steps, dt = 7, 0.01
+    gh.gh_set_time(dom, 0.4)
+    E, lam = constraint_energy_gradient(dom, u0, dt, steps, ckpt=3)
+    assert abs(gh.gh_get_time(dom) - (0.4 + steps * dt)) < 1e-14
+    g = torch.Generator(device="cuda").manual_seed(52)
+    dw = 1e-3 * torch.randn(dom.state_size, dtype=torch.float64, device="cuda", generator=g)
+    h = 1e-4
+    gh.gh_set_time(dom, 0.4)
+    Ep = evolve_energy(dom, u0 + h * dw, dt, steps)
+    gh.gh_set_time(dom, 0.4)
+    Em = evolve_energy(dom, u0 - h * dw, dt, steps)
+    fd = (Ep - Em) / (2 * h)
+    an = float((lam * dw).sum())
+    assert abs(fd - an) <= 1e-5 * abs(fd), (fd, an)
