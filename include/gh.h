@@ -356,8 +356,10 @@ gh_status gh_dp5_step(gh_domain* dom, double dt, double rtol, double atol, doubl
  * products run as library GEMMs, Sec. 3.4); it never changes the arithmetic of
  * any output of the forward maps, so every schedule of sched[0..7] gives
  * bitwise identical results.
- *   sched[0], sched[1]: radial derivative -- FMA chains per pass (2..4) and
- *     row groups per column (1..4, one grid row each);
+ *   sched[0], sched[1]: radial derivative (folded: the centro-antisymmetric
+ *     CGL matrix applied through the ceil(n_r/2) rows that give a mirror pair
+ *     of outputs each) -- FMA chains per pass (2..4) and row groups per
+ *     column (1..4, one grid row each);
  *   sched[2], sched[3]: the same for the radial ExpCheb filter;
  *   sched[4], sched[5]: folded d/dtheta, d/dphi kernel -- threads per block
  *     (32..512, a multiple of 32) and the shared-memory budget per block in
@@ -381,7 +383,7 @@ gh_status gh_set_schedule(gh_domain* dom, const int* sched, int n);
 
 /* Kernel families for the profiler below. */
 typedef enum {
-  GH_K_RADIAL = 0,        /* radial derivative map (Chebyshev, n_r x n_r)          */
+  GH_K_RADIAL = 0,        /* radial derivative map (Chebyshev, folded n_r x n_r)   */
   GH_K_ANGULAR = 1,       /* angular derivative maps (d/dtheta, d/dphi)             */
   GH_K_POINTWISE = 2,     /* fused DiffJac + GH right-hand side + RK4 combine       */
   GH_K_BC = 3,            /* characteristic boundary conditions                     */
