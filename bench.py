@@ -71,6 +71,9 @@ def parse():
                         "compared with the plain per-hole launch loop")
     p.add_argument("--no-graph", action="store_true",
                    help="time direct gh_rk4_step calls instead of replays of the captured step graph")
+    p.add_argument("--no-overlap", action="store_true",
+                   help="run the radial and angular derivative maps one after the other on one stream "
+                        "(default: the radial map on the domain's second stream, beside the angular maps)")
     p.add_argument("--sh-filter", default="component", choices=["component", "tensor"],
                    help="angular filter: per Cartesian component (default) or tensor spherical harmonics "
                         "(spin-weighted harmonics in the complex frame)")
@@ -213,6 +216,7 @@ def run_ours(args, w):
     dev = torch.device("cuda", local)
 
     dom = gh.Domain.from_workload(w)
+    gh.gh_set_overlap(dom, not args.no_overlap)
     if args.algorithm == "auto":
         args.algorithm = "folded"          # the library's default
     else:
@@ -360,7 +364,9 @@ def run_ours(args, w):
                             timed_step=("one replay of the captured RK4 graph (gh_rk4_graph_launch)" if use_graph
                                         else "one gh_rk4_step call"),
                             kernel_times="per-family CUDA events on the domain's stream, from a second "
-                                         "timed region of the same steps called directly",
+                                         "timed region of the same steps called directly (the maps one "
+                                         "after the other)",
+                            overlap=not args.no_overlap,
                             parallelism="replicas" if world > 1 else "single GPU", algorithm=args.algorithm,
                             schedule=gh.gh_get_schedule(dom),
                             autotuned=not (args.no_autotune or args.schedule)),

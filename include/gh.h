@@ -98,6 +98,16 @@ gh_status gh_destroy_domain(gh_domain* dom);
 /* Change the stream later calls are enqueued on. */
 gh_status gh_set_stream(gh_domain* dom, void* stream);
 
+/* on = 1 (the default): each right-hand side runs its radial derivative map
+ * on a second stream the domain owns, beside the angular maps on the domain's
+ * stream, forked and joined by events.  Both read the state and write separate
+ * buffers, so the results are bitwise the same as with on = 0, where the maps
+ * run one after the other.  Calls still behave as if everything ran on the
+ * domain's stream, and graph captures include the fork and join.  With the
+ * profiler on (gh_profile_enable) the maps run one after the other so that
+ * each family is timed alone.  Errors: GH_EINVAL unless on is 0 or 1. */
+gh_status gh_set_overlap(gh_domain* dom, int on);
+
 /* Sizes in doubles: one state vector; one RK4 work area (gh_rk4_step). */
 long long gh_state_size(const gh_domain* dom);
 long long gh_num_points(const gh_domain* dom);

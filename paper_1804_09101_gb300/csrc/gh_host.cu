@@ -557,6 +557,17 @@ struct ProfScope {
 };
 
 gh_status derivatives(gh_domain* d, const double* u) {
+  if (d->overlap && !d->prof) {
+    // radial map on the side stream, angular maps on the domain's stream;
+    // the join makes everything after this call wait for both
+    GH_CUDA(d, cudaEventRecord(d->ev_fork, d->stream));
+    GH_CUDA(d, cudaStreamWaitEvent(d->side, d->ev_fork, 0));
+    GH_CUDA(d, gh::launch_radial_on(d, u, d->d_r, false, d->side));
+    GH_CUDA(d, gh::launch_angular_deriv(d, u));
+    GH_CUDA(d, cudaEventRecord(d->ev_join, d->side));
+    GH_CUDA(d, cudaStreamWaitEvent(d->stream, d->ev_join, 0));
+    return GH_OK;
+  }
   {
     ProfScope p(d, GH_K_RADIAL);
     GH_CUDA(d, gh::launch_radial(d, u, d->d_r, false));
@@ -1105,6 +1116,9 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
   CREATE_CUDA(alloc_zero(d, sizeof(int), &p)); d->err_flag = (int*)p;
   CREATE_CUDA(alloc_zero(d, sizeof(double) * gh::DP_MAX_BLOCKS, &p)); d->dp_partial = (double*)p;
   CREATE_CUDA(alloc_zero(d, sizeof(double), &p)); d->dp_err = (double*)p;
+  CREATE_CUDA(cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking));
+  CREATE_CUDA(cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming));
+  CREATE_CUDA(cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming));
   CREATE_CUDA(cudaDeviceSynchronize());
 #undef CREATE_CUDA
   *out = d;
@@ -1119,6 +1133,12 @@ gh_status gh_destroy_domain(gh_domain* d) {
     cudaEventDestroy(b.b);
   }
   for (cudaEvent_t e : d->event_pool) cudaEventDestroy(e);
+  if (d->side) {
+    cudaStreamSynchronize(d->side);
+    cudaStreamDestroy(d->side);
+  }
+  if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+  if (d->ev_join) cudaEventDestroy(d->ev_join);
   if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
   for (void* p : d->owned) cudaFree(p);
   delete d;
@@ -1128,6 +1148,12 @@ gh_status gh_destroy_domain(gh_domain* d) {
 gh_status gh_set_stream(gh_domain* d, void* stream) {
   if (!d) return GH_EINVAL;
   d->stream = (cudaStream_t)stream;
+  return GH_OK;
+}
+
+gh_status gh_set_overlap(gh_domain* d, int on) {
+  if (!d || (on != 0 && on != 1)) return fail(d, GH_EINVAL, "on must be 0 or 1");
+  d->overlap = on != 0;
   return GH_OK;
 }
 

@@ -251,6 +251,12 @@ struct gh_domain {
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_step_launches = 0;
+  // second stream for the radial map, which runs beside the angular maps of
+  // the same right-hand side (both read the state, neither reads the other's
+  // output); fork and join by events on the domain's stream (gh_set_overlap)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool overlap = true;
   // profiler (gh_profile_enable / gh_profile_read)
   bool prof = false;
   struct Bracket { int fam; cudaEvent_t a, b; };
@@ -264,6 +270,7 @@ namespace gh {
 
 // Kernel launchers (gh_kernels.cu).
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter);
+cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st);
 cudaError_t launch_angular_deriv(gh_domain* d, const double* in);
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph);

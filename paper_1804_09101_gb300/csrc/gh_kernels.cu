@@ -1132,11 +1132,15 @@ __global__ void norm_reduce_kernel(const int* __restrict__ begin, int n_shells,
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter) {
+  return launch_radial_on(d, in, out, filter, d->stream);
+}
+
+cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st) {
   const size_t smem = radial_smem_bytes(d->max_n_r);
   const int ch = filter ? d->radf_chains : d->rad_chains;
   const dim3 grid(d->rad_blocks, filter ? d->radf_groups : d->rad_groups);
 #define GH_RAD(F, C)                                                                       \
-  radial_kernel<F, C><<<grid, RAD_THREADS, smem, d->stream>>>(d->shells_d, d->n_shells,    \
+  radial_kernel<F, C><<<grid, RAD_THREADS, smem, st>>>(d->shells_d, d->n_shells,           \
                                                                d->rad_block_begin_d, in, out, d->max_n_r)
   if (filter) {
     if (ch == 4) GH_RAD(true, 4); else if (ch == 3) GH_RAD(true, 3); else GH_RAD(true, 2);

@@ -48,6 +48,7 @@ def _load():
         "gh_create_domain": ([ctypes.POINTER(gh_shell), I, ctypes.POINTER(gh_params), P, ctypes.POINTER(P)], I),
         "gh_destroy_domain": ([P], I),
         "gh_set_stream": ([P, P], I),
+        "gh_set_overlap": ([P, I], I),
         "gh_state_size": ([P], ctypes.c_longlong),
         "gh_num_points": ([P], ctypes.c_longlong),
         "gh_rk4_work_size": ([P], ctypes.c_longlong),
@@ -260,6 +261,10 @@ def gh_constraints(dom, u, c_out, norm2):
 
 
 KERNEL_FAMILIES = ["radial", "angular", "pointwise", "bc", "radial_filter", "angular_filter", "reduce", "combine"]
+
+
+def gh_set_overlap(dom, on=True):
+    dom._check(_lib.gh_set_overlap(dom.handle, int(bool(on))))
 
 
 def gh_profile_enable(dom, on=True):

@@ -82,3 +82,8 @@ def test_schedule_entry_points_reject_bad_arguments_on_the_host(lib):
     assert lib.gh_get_schedule(None, v, 9) == 1          # GH_EINVAL: no domain
     assert lib.gh_set_schedule(None, v, 9) == 1
     assert lib.gh_autotune(None, 3) == 1
+
+
+def test_overlap_switch_rejects_bad_arguments_on_the_host(lib):
+    lib.gh_set_overlap.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.gh_set_overlap(None, 1) == 1              # GH_EINVAL: no domain

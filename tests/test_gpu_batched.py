@@ -93,6 +93,36 @@ def test_graph_replay_equals_direct_steps():
     assert np.array_equal(to_host(u), to_host(u2))
 
 
+def test_radial_map_on_the_side_stream_changes_no_bit():
+    """gh_set_overlap: the radial map on the domain's second stream, beside the
+    angular maps, against both on one stream: direct steps, a graph replay and
+    a right-hand side issued on a user stream are bitwise the same."""
+    from paper_1804_09101_gb300 import gh
+    holes = _small_batch()
+    runs = []
+    for on in (0, 1):
+        dom, u, _ = _build(holes, gh)
+        gh.gh_set_overlap(dom, on)
+        work = dom.new_work()
+        for _ in range(2):
+            gh.gh_rk4_step(dom, 1.0, u, work)
+        u2 = u.clone()
+        work2 = dom.new_work()
+        gh.gh_rk4_graph_capture(dom, 1.0, u2, work2)
+        gh.gh_rk4_graph_launch(dom, 2)
+        user = torch.cuda.Stream()
+        user.wait_stream(torch.cuda.current_stream())   # after the replays
+        with torch.cuda.stream(user):
+            k = dom.new_state()
+            gh.gh_rhs(dom, u2, k)
+            kh = k.cpu()
+        torch.cuda.synchronize()
+        runs.append((to_host(u), to_host(u2), kh.numpy()))
+    for name, a, b in zip(("steps", "replays", "rhs on a user stream"), runs[0], runs[1]):
+        assert np.array_equal(a, b), (name, np.abs(a - b).max())
+    assert gh._lib.gh_set_overlap(dom.handle, 2) != 0      # GH_EINVAL
+
+
 def test_batched_workload_builds_and_steps():
     from paper_1804_09101_gb300 import gh
     w = workloads.batched_workload(n_bh=8)
