@@ -588,11 +588,7 @@ cudaError_t ew(gh_domain* d, int mode, double* out, const double* x, const doubl
 }
 
 // Forward derivatives of u into d_r, d_th, d_ph.
-cudaError_t fwd_derivs(gh_domain* d, const double* u) {
-  cudaError_t e = gh::launch_radial(d, u, d->d_r, false);
-  if (e != cudaSuccess) return e;
-  return gh::launch_angular_deriv(d, u);
-}
+cudaError_t fwd_derivs(gh_domain* d, const double* u) { return gh::launch_derivatives(d, u); }
 
 // ubar += (transposed derivative maps) applied to the cotangents in d_r, d_th, d_ph.
 cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {

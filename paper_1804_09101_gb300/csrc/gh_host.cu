@@ -558,14 +558,7 @@ struct ProfScope {
 
 gh_status derivatives(gh_domain* d, const double* u) {
   if (d->overlap && !d->prof) {
-    // radial map on the side stream, angular maps on the domain's stream;
-    // the join makes everything after this call wait for both
-    GH_CUDA(d, cudaEventRecord(d->ev_fork, d->stream));
-    GH_CUDA(d, cudaStreamWaitEvent(d->side, d->ev_fork, 0));
-    GH_CUDA(d, gh::launch_radial_on(d, u, d->d_r, false, d->side));
-    GH_CUDA(d, gh::launch_angular_deriv(d, u));
-    GH_CUDA(d, cudaEventRecord(d->ev_join, d->side));
-    GH_CUDA(d, cudaStreamWaitEvent(d->stream, d->ev_join, 0));
+    GH_CUDA(d, gh::launch_derivatives(d, u));
     return GH_OK;
   }
   {

@@ -271,6 +271,9 @@ namespace gh {
 // Kernel launchers (gh_kernels.cu).
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter);
 cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st);
+// radial and angular derivative maps of in into d_r, d_th, d_ph: side by side
+// on two streams when d->overlap, else one after the other
+cudaError_t launch_derivatives(gh_domain* d, const double* in);
 cudaError_t launch_angular_deriv(gh_domain* d, const double* in);
 cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out);
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph);

@@ -1156,6 +1156,22 @@ cudaError_t launch_angular_deriv(gh_domain* d, const double* in) {
   return launch_angular_deriv_into(d, in, d->d_th, d->d_ph);
 }
 
+cudaError_t launch_derivatives(gh_domain* d, const double* in) {
+  if (!d->overlap) {
+    cudaError_t e = launch_radial(d, in, d->d_r, false);
+    return e != cudaSuccess ? e : launch_angular_deriv(d, in);
+  }
+  // radial map on the side stream, angular maps on the domain's stream; the
+  // join makes everything enqueued after this call wait for both
+  cudaError_t e = cudaEventRecord(d->ev_fork, d->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d->side, d->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_radial_on(d, in, d->d_r, false, d->side);
+  if (e == cudaSuccess) e = launch_angular_deriv(d, in);
+  if (e == cudaSuccess) e = cudaEventRecord(d->ev_join, d->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, d->ev_join, 0);
+  return e;
+}
+
 cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dth, double* dph) {
   if (d->algorithm == 2) return launch_fold_deriv(d, in, dth, dph);
   if (d->algorithm == 1)
