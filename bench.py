@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel
 # from the ncu captures of the current kernels (None once a kernel changes).
 TRAFFIC_PER_LAUNCH = {
-    # pointwise_kernel<1,0>, 4-shell L=15: 121.8 MB read + 109.9 MB written
-    ("kerr_a0.9_4shells_nr21_L15", "folded", "pointwise"): 231.7e6,
+    # pointwise_kernel<1,0,0>, 4-shell L=15: 122.1 MB read + 110.1 MB written
+    ("kerr_a0.9_4shells_nr21_L15", "folded", "pointwise"): 232.2e6,
     # fold_angular_kernel<1>, 8-shell L=31: 269.1 MB read + 482.5 MB written
     ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): 751.6e6,
     # fold_angular_kernel<1>, 4-shell L=15: 17.3 MB read + 8.7 MB written
