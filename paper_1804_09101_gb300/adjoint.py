@@ -4,8 +4,12 @@ entry points (gh_rk4_step_vjp, gh_constraint_energy_vjp, gh_perturbation_vjp).
 Argument marshalling and control flow only: every forward and reverse step
 runs in libgh's CUDA kernels.
 
-* ``RK4Step`` / ``ConstraintEnergy``: torch.autograd.Function wrappers, so a
-  loss built from steps and constraint energies can call ``.backward()``.
+* ``RK4Step`` (alias ``GHStep``) / ``ConstraintEnergy``: torch.autograd.Function
+  wrappers, so a loss built from steps and constraint energies can call
+  ``.backward()``.
+* ``evolve``: N steps as one differentiable call with checkpoints every
+  ``ckpt`` steps (the backward pass recomputes each segment from its
+  checkpoint and runs the step VJPs backwards).
 * ``constraint_energy_gradient``: the time-integrated constraint energy
   E = sum_{n=1..N} dt * sum_shells norm2(u_n) of an N-step evolution and its
   gradient with respect to u_0, with checkpoints every ``ckpt`` steps: the
@@ -34,6 +38,74 @@ class RK4Step(torch.autograd.Function):
         ub = torch.zeros_like(u)
         gh.gh_rk4_step_vjp(ctx.dom, ctx.dt, u, g.contiguous(), ub, gh.new_vjp_work(ctx.dom))
         return ub, None, None
+
+
+GHStep = RK4Step
+
+
+class Evolve(torch.autograd.Function):
+    """u_N after n_steps gh_rk4_step calls from u_0 (with the domain's filters).
+
+    Forward keeps u_0, u_ckpt, u_2ckpt, ...; backward walks the segments
+    (a, b] from the last, recomputes the segment's states and RK4 stage states
+    from its checkpoint (gh_rk4_step_save) and applies the saved-stage step
+    VJPs from step b down to a + 1: ubar_{n-1} = S'(u_{n-1})^T ubar_n.  With a
+    rotating frame each recomputed or reversed step runs with the clock at
+    t_0 + n dt, and backward leaves the clock where it found it.
+    """
+
+    @staticmethod
+    def forward(ctx, u0, dom, dt, n_steps, ckpt):
+        rot = getattr(dom, "rotating", False)
+        ctx.t0 = gh.gh_get_time(dom) if rot else 0.0
+        u = u0.detach().clone()
+        work = dom.new_work()
+        ctx.checkpoints = {0: u.clone()}
+        for n in range(1, n_steps + 1):
+            gh.gh_rk4_step(dom, dt, u, work)
+            if n % ckpt == 0 and n < n_steps:
+                ctx.checkpoints[n] = u.clone()
+        ctx.dom, ctx.dt, ctx.n_steps, ctx.ckpt, ctx.rot = dom, dt, n_steps, ckpt, rot
+        return u
+
+    @staticmethod
+    def backward(ctx, g):
+        dom, dt, n_steps, ckpt, rot = ctx.dom, ctx.dt, ctx.n_steps, ctx.ckpt, ctx.rot
+        t_end = gh.gh_get_time(dom) if rot else 0.0
+
+        def clock(n):
+            if rot:
+                gh.gh_set_time(dom, ctx.t0 + n * dt)
+
+        work = dom.new_work()
+        vwork = gh.new_vjp_work(dom)
+        N = dom.state_size
+        lam = g.detach().contiguous().clone()
+        nxt = torch.zeros_like(lam)
+        for a in sorted(ctx.checkpoints, reverse=True):
+            b = min(a + ckpt, n_steps)
+            states = [ctx.checkpoints[a]]
+            stages = torch.empty((b - a, 3 * N), dtype=torch.float64, device=lam.device)
+            s = ctx.checkpoints[a].clone()
+            for i in range(a, b):
+                clock(i)
+                gh.gh_rk4_step_save(dom, dt, s, work, stages[i - a])
+                states.append(s.clone())
+            for n in range(b, a, -1):
+                clock(n - 1)
+                gh.gh_rk4_step_vjp_saved(dom, dt, states[n - 1 - a], stages[n - 1 - a], lam, nxt, vwork, 0.0)
+                lam, nxt = nxt, lam
+        if rot:
+            gh.gh_set_time(dom, t_end)
+        ctx.checkpoints = None
+        return lam, None, None, None, None
+
+
+def evolve(dom, u0, dt, n_steps, ckpt=20):
+    """u_N = S^N(u_0), differentiable with respect to u_0 (checkpointed; see Evolve)."""
+    if n_steps < 1 or ckpt < 1:
+        raise ValueError("need n_steps >= 1 and ckpt >= 1")
+    return Evolve.apply(u0, dom, dt, n_steps, ckpt)
 
 
 class ConstraintEnergy(torch.autograd.Function):

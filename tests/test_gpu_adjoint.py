@@ -182,6 +182,45 @@ def test_autograd_functions_chain():
     assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
 
 
+@pytest.mark.parametrize("ckpt", [3, 20])
+def test_checkpointed_evolve_backward_matches_step_chain_and_fd(ckpt):
+    """adjoint.evolve: its gradient equals the chain of RK4Step gradients
+    (the same VJPs, recomputed from checkpoints) and central differences of
+    <w, u_N> along a random direction; the forward result equals N plain steps."""
+    from paper_1804_09101_gb300 import gh
+    from paper_1804_09101_gb300.adjoint import GHStep, evolve
+    w = _kerr2()
+    odom, u0, dom = _setup(w)
+    n = 7
+    wt = to_dev(np.random.default_rng(21).standard_normal(u0.shape))
+    x = to_dev(u0).requires_grad_(True)
+    y = evolve(dom, x, w.dt, n, ckpt)
+    (y * wt).sum().backward()
+    plain = to_dev(u0)
+    work = dom.new_work()
+    for _ in range(n):
+        gh.gh_rk4_step(dom, w.dt, plain, work)
+    assert np.array_equal(to_host(y.detach()), to_host(plain))
+    x2 = to_dev(u0).requires_grad_(True)
+    y2 = x2
+    for _ in range(n):
+        y2 = GHStep.apply(y2, dom, w.dt)
+    (y2 * wt).sum().backward()
+    g1, g2 = to_host(x.grad), to_host(x2.grad)
+    assert np.abs(g1 - g2).max() <= 1e-12 * np.abs(g2).max()
+    dw = np.random.default_rng(22).standard_normal(u0.shape) * 1e-3
+    h = 1e-4
+
+    def f(u):
+        t = to_dev(u)
+        for _ in range(n):
+            gh.gh_rk4_step(dom, w.dt, t, work)
+        return float((t * wt).sum())
+    fd = (f(u0 + h * dw) - f(u0 - h * dw)) / (2 * h)
+    an = float(g1 @ dw)
+    assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
 def test_saved_stage_step_and_vjp_agree_with_the_plain_ones():
     from paper_1804_09101_gb300 import gh
     w = _kerr2()
