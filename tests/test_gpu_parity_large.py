@@ -1,6 +1,7 @@
 """Parity at the full size of the large workload (Kerr a = 0.95, 8 shells
-r in [1.2, 100], N_r = 41, L = 31; 671,744 points), in the launch configuration
-the benchmark times (folded angular maps, autotuned schedule).
+r in [1.2, 100], N_r = 41, L = 31; 671,744 points) and on the largest legal
+shell (N_r = 64, L = 47), in the launch configuration the benchmark times
+(folded angular maps, autotuned schedule).
 
 The input is the workload's initial data plus seeded noise (1e-4 on every
 value).  The oracle's whole-shell right-hand side is minutes of work at this size, so
@@ -59,9 +60,10 @@ def _bg_at(odom, s, ir, j, k):
     return {key: np.asarray(v)[j:j + 1, k:k + 1] for key, v in bg.items()}
 
 
-def test_rhs_at_sampled_points_full_size(large):
+def _check_sampled_rhs(w, odom, u0, n_interior=6, n_boundary=2, seed=2025):
+    """gh_rhs (autotuned schedule) against the oracle at sampled interior and
+    boundary points of every shell; returns the number of points compared."""
     from paper_1804_09101_gb300 import gh
-    w, odom, u0 = large
     dom = gpu_domain(w, odom)
     gh.gh_autotune(dom, 3)
     k = dom.new_state()
@@ -71,7 +73,7 @@ def test_rhs_at_sampled_points_full_size(large):
     scale = np.abs(flat(u0)).max()
     offs = np.cumsum([0] + [int(np.prod(sh)) for sh in odom.shapes()])
     jac = [spectral.spherical_jacobian(g) for g in odom.grids]
-    rng = np.random.default_rng(2025)
+    rng = np.random.default_rng(seed)
 
     def gpu_at(s, ir, j, kk):
         n_r, _, nth, nph = odom.shapes()[s]
@@ -83,14 +85,14 @@ def test_rhs_at_sampled_points_full_size(large):
     for s in range(ns):
         n_r, _, nth, nph = odom.shapes()[s]
         # interior points
-        for _ in range(6):
+        for _ in range(n_interior):
             ir, j, kk = int(rng.integers(1, n_r - 1)), int(rng.integers(0, nth)), int(rng.integers(0, nph))
             ref = _interior_rhs_at(odom, u0, s, ir, j, kk, jac)
             err = np.abs(gpu_at(s, ir, j, kk) - ref).max() / scale
             worst = max(worst, err)
             n_cmp += 1
         # the boundary slice at r_out: an interface with shell s + 1, or the outer boundary
-        for _ in range(2):
+        for _ in range(n_boundary):
             j, kk = int(rng.integers(0, nth)), int(rng.integers(0, nph))
             a = _interior_rhs_at(odom, u0, s, n_r - 1, j, kk, jac)
             bg = _bg_at(odom, s, n_r - 1, j, kk)
@@ -104,7 +106,24 @@ def test_rhs_at_sampled_points_full_size(large):
                 err = np.abs(gpu_at(s, n_r - 1, j, kk) - new[0, 0]).max() / scale
             worst = max(worst, err)
             n_cmp += 1
-    assert n_cmp == 8 * ns and worst < REL_TOL, worst
+    assert worst < REL_TOL, worst
+    return n_cmp
+
+
+def test_rhs_at_sampled_points_full_size(large):
+    w, odom, u0 = large
+    assert _check_sampled_rhs(w, odom, u0) == 8 * len(odom.grids)
+
+
+def test_rhs_at_sampled_points_largest_legal_shell():
+    """The largest shell gh_create_domain accepts (n_r = 64, L = 47: 294,912
+    points), r in [1.5, 20] around a Kerr hole a = 0.7 (inner boundary inside
+    the horizon r_+ = 1.71), with the radial filter and keep l <= 31."""
+    w = workloads.Workload(name="max_shell", shells=[(1.5, 20.0, 64, 47)], M=1.0, chi=0.7,
+                           radial_filter_on=True, sh_keep_l=31, dt=0.002, seed=31, noise_amp=1e-4)
+    odom = oracle_domain(w)
+    u0 = oracle_initial_state(w, odom)
+    assert _check_sampled_rhs(w, odom, u0, n_interior=10, n_boundary=4, seed=47) == 14
 
 
 def test_rk4_step_is_the_composition_of_its_parts_full_size(large):
