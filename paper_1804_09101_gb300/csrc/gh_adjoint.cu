@@ -471,6 +471,7 @@ ew_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restri
 // sum_p ubar(Pi_p) G(R) Y_lm over the block's points.
 constexpr int PV_THREADS = 64;
 constexpr int PV_MAX_MODES = 81;   // lmax <= 8
+static_assert(PV_MAX_MODES <= (PERT_LMAX + 1) * (PERT_LMAX + 1), "mode count exceeds the Legendre table");
 
 __global__ void __launch_bounds__(PV_THREADS)
 pi_modes_vjp_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
@@ -872,7 +873,8 @@ gh_status gh_perturbation_vjp(gh_domain* d, int kind, double Rc, double w, int l
                               double* grad) {
   if (!d || !ubar || !grad) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
   if (kind != 1) return afail(d, GH_ENOTSUP, "only the Pi-mode perturbation (kind 1) has a gradient entry");
-  if (lmax < 0 || lmax > 8 || !(w > 0.0)) return afail(d, GH_EINVAL, "need 0 <= lmax <= 8 and w > 0");
+  if (lmax < 0 || (lmax + 1) * (lmax + 1) > gh::PV_MAX_MODES || !(w > 0.0))
+    return afail(d, GH_EINVAL, "need 0 <= lmax <= 8 and w > 0");
   const int nm = (lmax + 1) * (lmax + 1);
   std::vector<int> begin(d->n_shells + 1);
   int blocks = 0;

@@ -1210,7 +1210,7 @@ cudaError_t launch_angular_filter(gh_domain* d, const double* in, double* out) {
         d->shells_d, d->n_shells, d->sf_block_begin_d, in, out, nullptr);
   else
     gemm_batched_kernel<<<d->ang_filt_tiles, GEMM_THREADS, 0, d->stream>>>(
-        d->ang_filt_d, d->ang_filt_np, in, out, out);
+        d->ang_filt_d, d->ang_filt_np, in, out, nullptr);   // filter problems write out0 only
   d->launches++;
   return cudaGetLastError();
 }
