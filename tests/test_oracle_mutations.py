@@ -1,0 +1,114 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a fresh copy of an oracle module (a dropped
+term, a flipped sign, a wrong index, a transposed operand, a wrong weight),
+puts the copy in place of the module for the duration of the test, and runs
+the pin that should notice it: the pin must fail.  The mistakes are planted
+on the CPU, in the oracle only; nothing here touches the library.
+"""
+import os
+import sys
+import types
+
+import pytest
+
+import test_oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _install_mutant(monkeypatch, modname, old, new):
+    """Replace oracle.<modname> everywhere it is referenced (the package, the
+    other oracle modules, the pin module) by a copy whose source has the one
+    occurrence of `old` replaced by `new`."""
+    path = os.path.join(ROOT, "oracle", modname + ".py")
+    with open(path) as f:
+        src = f.read()
+    assert src.count(old) == 1, "the planted mistake must match exactly one place: %r" % old
+    full = "oracle." + modname
+    orig = sys.modules[full]
+    mod = types.ModuleType(full)
+    mod.__file__ = path
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(old, new), path, "exec"), mod.__dict__)
+    monkeypatch.setitem(sys.modules, full, mod)
+    for name, m in list(sys.modules.items()):
+        if m is None or not (name == "oracle" or name.startswith("oracle.") or name.endswith("test_oracle_pins")):
+            continue
+        for k, v in list(vars(m).items()):
+            if v is orig:
+                monkeypatch.setattr(m, k, mod)
+    return mod
+
+
+# (module, original text, planted mistake, pin, pin arguments)
+CASES = {
+    # GH right-hand side (oracle/gh.py)
+    "T3 term sign": ("gh", '- np.einsum("...cd,...ef,...ace,...bdf->...ab", psi_inv, psi_inv, Gam, Gam))',
+                     '+ np.einsum("...cd,...ef,...ace,...bdf->...ab", psi_inv, psi_inv, Gam, Gam))',
+                     "test_rhs_of_exact_kerr_schild_converges_exponentially", (0.9, (3.0, 6.0))),
+    # (psi^cd Pi_ca Pi_db vanishes on stationary Kerr-Schild data: only the
+    # moving-coordinates flat-space pin sees this term)
+    "Pi-Pi term sign": ("gh", '- np.einsum("...cd,...ca,...db->...ab", psi_inv, Pi, Pi)',
+                        '+ np.einsum("...cd,...ca,...db->...ab", psi_inv, Pi, Pi)',
+                        "test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates", ()),
+    "t t Pi Pi term sign": ("gh", "- 0.5 * Nb * tPt[..., None, None] * Pi", "+ 0.5 * Nb * tPt[..., None, None] * Pi",
+                            "test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates", ()),
+    "dropped t.Pi g Phi term": ("gh", '- Nb * np.einsum("...i,...ij,...jab->...ab", tPi_i, ginv, Phi)\n', '\n',
+                                "test_rhs_of_exact_kerr_schild_converges_exponentially", (0.9, (3.0, 6.0))),
+    "Christoffel index": ("gh", 'Gam = 0.5 * (np.einsum("...bac->...abc", d)',
+                          'Gam = 0.5 * (np.einsum("...cba->...abc", d)',
+                          "test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates", ()),
+    "nabla H without the Gamma term": ("gh", 'nablaH = dH4 - np.einsum("...cab,...c->...ab", Gam_up, H)',
+                                       'nablaH = dH4 + 0.0 * np.einsum("...cab,...c->...ab", Gam_up, H)',
+                                       "test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates", ()),
+    "Phi equation t t Phi Pi term sign": ("gh", "+ 0.5 * Ni * np.einsum(\"...i,...ab->...iab\", tPhit, Pi)",
+                                          "- 0.5 * Ni * np.einsum(\"...i,...ab->...iab\", tPhit, Pi)",
+                                          "test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates", ()),
+    "dropped gamma2 damping of Phi": ("gh", "              - gamma2 * Ni * Phi)", "              )",
+                                      "test_three_index_constraint_decays_at_rate_gamma2_on_minkowski", ()),
+    "gamma0 damping sign": ("gh", "+ gamma0 * Nb * damp", "- gamma0 * Nb * damp",
+                            "test_gauge_constraint_damping_rates_on_minkowski", ()),
+    "gamma2 sign in u^pm": ("gh", "wp = Pi + nPhi - gamma2 * psi", "wp = Pi + nPhi + gamma2 * psi",
+                            "test_characteristic_round_trip", ()),
+    "interface upwind sides swapped": ("gh", "new_i = np.where(neg, wo[q], wi[q])", "new_i = np.where(pos, wo[q], wi[q])",
+                                       "test_interface_exchange_is_upwind_per_characteristic_family", (-1.0,)),
+    "outer BC freezes outgoing": ("gh", "        mask = (v < 0.0)\n", "        mask = (v > 0.0)\n",
+                                  "test_outer_bc_zeroes_only_incoming_fields", ()),
+    # spectral maps (oracle/spectral.py)
+    "Chebyshev derivative recurrence": ("spectral", "b[k] = (b[k + 2] + 2.0 * (k + 1) * a[k + 1]) / cb",
+                                        "b[k] = (b[k + 2] + 2.0 * k * a[k + 1]) / cb",
+                                        "test_radial_derivative_exact_below_degree_n_r", ()),
+    "Y_lm normalisation": ("spectral", "        return np.sqrt(2.0) * np.cos(m * phi)\n",
+                           "        return np.cos(m * phi)\n", "test_real_ylm_and_dtheta_match_scipy", (7,)),
+    "DiffJac entry sign": ("spectral", "J[2, 1] = -st / r * one", "J[2, 1] = st / r * one",
+                           "test_cartesian_gradient_exact_on_polynomials", (9, 5, 5)),
+    "DiffJac transposed": ("spectral", "J[1, 0] = st * sp * one\n    J[2, 0] = ct * one\n    J[0, 1] = ct * cp / r * one",
+                           "J[1, 0] = ct * cp / r * one\n    J[2, 0] = ct * one\n    J[0, 1] = st * sp * one",
+                           "test_cartesian_gradient_exact_on_polynomials", (9, 5, 5)),
+    "ExpCheb exponent": ("spectral", "return np.exp(-alpha * (k / (n - 1.0)) ** order)",
+                         "return np.exp(-alpha * (k / (n - 1.0)) ** (2 * order))",
+                         "test_expcheb_filter_scales_each_chebyshev_mode", ()),
+    # quadrature (oracle/grid.py)
+    "Clenshaw-Curtis end weights": ("grid", "c = 1.0 if j in (0, N) else 2.0", "c = 2.0 if j in (0, N) else 1.0",
+                                    "test_clenshaw_curtis_exact_on_polynomials", (11,)),
+    # time stepper (oracle/evolve.py)
+    "RK4 weights": ("evolve", "dt / 6.0 * (p + 2.0 * q + 2.0 * r + s)", "dt / 6.0 * (p + 2.0 * q + r + 2.0 * s)",
+                    "test_rk4_matches_stability_polynomial", "monkeypatch"),
+    # Kerr-Schild data (oracle/kerr_schild.py)
+    "Kerr-Schild H": ("kerr_schild", "H = M * r ** 3 / (r ** 4 + a * a * z * z)",
+                      "H = M * r ** 3 / (r ** 4 - a * a * z * z)",
+                      "test_rhs_of_exact_kerr_schild_converges_exponentially", (0.9, (3.0, 6.0))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_pin_catches_planted_mistake(name, monkeypatch):
+    modname, old, new, pin, args = CASES[name]
+    if args == "monkeypatch":
+        args = (monkeypatch,)
+    pin_fn = getattr(pins, pin)
+    pin_fn(*args)                                    # the pin passes on the real oracle
+    _install_mutant(monkeypatch, modname, old, new)
+    with pytest.raises(AssertionError):
+        pin_fn(*args)

@@ -83,6 +83,16 @@ def test_expcheb_filter_scales_each_chebyshev_mode():
         Tk = spectral.cheb_T(k, g["x"])[:, None, None] * np.ones((1, 2, 4))
         out = spectral.radial_filter(Tk, g, 36.0, 32)
         assert np.abs(out - s[k] * Tk).max() < 1e-13
+    # strength and order measured from the filter's action on T_k: the gain is
+    # exp(-36 (k/(N-1))^p) with p = 32 (the ExpCheb filter of order 32, Sec. 3.4)
+    gain = {}
+    for k in [7, 9]:
+        Tk = spectral.cheb_T(k, g["x"])
+        out = spectral.radial_filter(Tk[:, None, None], g, 36.0, 32)[:, 0, 0]
+        gain[k] = float(out @ Tk / (Tk @ Tk))
+    order = np.log(np.log(gain[7]) / np.log(gain[9])) / np.log(7.0 / 9.0)
+    strength = -np.log(gain[9]) / 0.9 ** order
+    assert abs(order - 32.0) < 1e-6 and abs(strength - 36.0) < 1e-6, (order, strength)
 
 
 # ---------------------------------------------------------- angular part
@@ -291,6 +301,90 @@ def test_rhs_of_exact_kerr_schild_converges_exponentially(chi, shell):
     assert errs[2] < 1e-6
 
 
+# Flat spacetime in time-dependent, non-linear coordinates: x^mu = F^mu(t, x, y, z)
+# with F close to the identity.  Every constraint vanishes (with H_a = -Gamma_a of
+# this metric), so the exact d_t u must equal the GH right-hand side; unlike the
+# stationary Kerr-Schild data it has psi^cd Pi_ca Pi_db != 0 and d_t H_a != 0.
+_PAIRS = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+
+
+def _moving_minkowski_metric():
+    import sympy as sp
+    t, x, y, z = c = sp.symbols("t x y z", real=True)
+    F = [t + sp.Rational(1, 5) * sp.sin(t) * (1 + sp.Rational(3, 10) * x) + sp.Rational(1, 10) * x * y,
+         x + sp.Rational(3, 20) * sp.sin(sp.Rational(7, 10) * t + y / 2),
+         y + z * t / 10,
+         z + t ** 2 / 20]
+    J = sp.Matrix(4, 4, lambda m, a: sp.diff(F[m], c[a]))
+    g = J.T * sp.diag(-1, 1, 1, 1) * J                  # g_ab = J^m_a eta_mn J^n_b
+    f_g = sp.lambdify(c, g, "numpy")
+    f_dg = sp.lambdify(c, [sp.diff(g, v) for v in c], "numpy")
+    return f_g, f_dg
+
+
+def _moving_minkowski_fields(f_g, f_dg, p):
+    """(u[50], H[4], alpha) at the event p = (t, x, y, z), computed from the exact
+    metric and its exact first derivatives: Phi_iab = d_i g_ab,
+    Pi_ab = -(d_t g_ab - beta^k Phi_kab) / alpha, H_a = -g^bc Gamma_abc."""
+    g = np.array(f_g(*p), dtype=float)
+    dg = np.array(f_dg(*p), dtype=float)                # dg[c, a, b] = d_c g_ab
+    gi3 = np.linalg.inv(g[1:, 1:])
+    b_up = gi3 @ g[0, 1:]
+    alpha = np.sqrt(b_up @ g[0, 1:] - g[0, 0])
+    Phi = dg[1:]
+    Pi = -(dg[0] - np.einsum("k,kab->ab", b_up, Phi)) / alpha
+    Gam = 0.5 * (np.einsum("bac->abc", dg) + np.einsum("cab->abc", dg) - dg)
+    H = -np.einsum("bc,abc->a", np.linalg.inv(g), Gam)
+    u = np.zeros(50)
+    for q, (a, b) in enumerate(_PAIRS):
+        u[q], u[10 + q] = g[a, b], Pi[a, b]
+        for i in range(3):
+            u[20 + 10 * i + q] = Phi[i, a, b]
+    return u, H, alpha
+
+
+def _central_diff(f, p, axis, h=2e-3):
+    """8th-order central difference of f along coordinate `axis` at p."""
+    w = [1 / 280, -4 / 105, 1 / 5, -4 / 5, 0.0, 4 / 5, -1 / 5, 4 / 105, -1 / 280]
+    acc = 0.0
+    for j, c in enumerate(w):
+        if c:
+            q = list(p)
+            q[axis] += (j - 4) * h
+            acc = acc + c * np.asarray(f(q))
+    return acc / h
+
+
+def test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates():
+    """The pointwise GH right-hand side at exact data of a solution equals its
+    exact time derivative, except for the d_t H_b part of -2 alpha nabla_(a H_b),
+    which the right-hand side leaves out (gauge source held fixed in time):
+    RHS(Pi_ab) = d_t Pi_ab + alpha (delta^0_a d_t H_b + delta^0_b d_t H_a).
+    Pins every term that does not multiply a constraint, including the
+    Pi-Pi, Gamma-Gamma and t t Pi Pi terms that vanish on stationary
+    Kerr-Schild data.  Any damping parameters: the constraints vanish."""
+    f_g, f_dg = _moving_minkowski_metric()
+    fields = lambda q: _moving_minkowski_fields(f_g, f_dg, q)[0]
+    gauge = lambda q: _moving_minkowski_fields(f_g, f_dg, q)[1]
+    rng = np.random.default_rng(15)
+    for _ in range(4):
+        p = [rng.uniform(0.0, 1.0)] + list(rng.uniform(-0.5, 0.5, 3))
+        u, H, alpha = _moving_minkowski_fields(f_g, f_dg, p)
+        du = np.stack([_central_diff(fields, p, 1 + k) for k in range(3)])      # [3, 50]
+        dH = np.stack([_central_diff(gauge, p, 1 + k) for k in range(3)])       # [3, 4]
+        dt_u = _central_diff(fields, p, 0)
+        dt_H = _central_diff(gauge, p, 0)
+        want = dt_u.copy()
+        for q, (a, b) in enumerate(_PAIRS):
+            want[10 + q] += alpha * ((dt_H[b] if a == 0 else 0.0) + (dt_H[a] if b == 0 else 0.0))
+        for g0, g1, g2 in [(1.0, -1.0, 1.0), (0.3, 0.7, 2.0)]:
+            got = gh.gh_rhs_pointwise(u[None], du[None], H[None], dH[None], g0, g1, g2)[0]
+            assert np.abs(got - want).max() < 1e-8, np.abs(got - want).max()
+    # the data are not trivial: the Pi-Pi contraction is of order one
+    psi, Pi, _ = gh.unpack_fields(u)
+    assert np.abs(np.einsum("cd,ca,db->ab", np.linalg.inv(psi), Pi, Pi)).max() > 1e-3
+
+
 def _minkowski_point_state(rng, n=6):
     psi = np.broadcast_to(np.diag([-1.0, 1, 1, 1]), (n, 4, 4)).copy()
     Pi = np.zeros((n, 4, 4))
@@ -400,6 +494,40 @@ def test_outer_bc_zeroes_only_incoming_fields():
     assert np.abs(w_out[0] - w_in[0]).max() < 1e-13      # zero speed: untouched
     assert np.abs(w_out[2] - w_in[2]).max() < 1e-13      # outgoing: untouched
     assert np.abs(w_out[1]).max() < 1e-13 and np.abs(w_out[3]).max() < 1e-13
+
+
+@pytest.mark.parametrize("gamma1", [-1.0, 0.5])
+def test_interface_exchange_is_upwind_per_characteristic_family(gamma1):
+    """At a shared radius outside the horizon (speeds of both signs), each
+    characteristic family of the new time derivatives is, on both sides, the
+    value of the side it comes from: the outer shell's where it moves inward
+    (v < 0), the inner shell's where it moves outward (v > 0); a zero-speed
+    family keeps each side's own value.  gamma1 = -1 gives v_psi = 0, gamma1 =
+    0.5 an inward v_psi."""
+    g = grid.shell_grid(3.0, 6.0, 5, 5)
+    X, Y, Z = grid.cartesian_coords(g)
+    gm, _, _ = kerr_schild.metric_and_derivatives(X[-1], Y[-1], Z[-1], 1.0, 0.7)
+    bg = gh.boundary_background(gm, X[-1], Y[-1], Z[-1])
+    rng = np.random.default_rng(14)
+    a = rng.standard_normal(X[-1].shape + (50,))
+    b = rng.standard_normal(X[-1].shape + (50,))
+    na, nb = gh.apply_interface_bc(a, b, bg, gamma1, 1.0)
+    wa, wb = gh.to_char(a, bg, 1.0), gh.to_char(b, bg, 1.0)
+    wna, wnb = gh.to_char(na, bg, 1.0), gh.to_char(nb, bg, 1.0)
+    speeds = gh.char_speeds(bg, gamma1)
+    assert np.all(speeds[1] < 0) and np.all(speeds[2] > 0) and np.all(speeds[3] < 0)
+    for q, v in enumerate(speeds):
+        ext = v.reshape(v.shape + (1,) * (wa[q].ndim - v.ndim))
+        want_a = np.where(ext < 0, wb[q], wa[q])        # inward: the outer side's value
+        want_b = np.where(ext > 0, wa[q], wb[q])        # outward: the inner side's value
+        assert np.abs(wna[q] - want_a).max() < 1e-12, q
+        assert np.abs(wnb[q] - want_b).max() < 1e-12, q
+    if gamma1 == -1.0:
+        assert np.all(speeds[0] == 0)
+        assert np.abs(wna[0] - wa[0]).max() < 1e-13 and np.abs(wnb[0] - wb[0]).max() < 1e-13
+    else:
+        assert np.all(speeds[0] < 0)
+        assert np.abs(wna[0] - wb[0]).max() < 1e-13
 
 
 # ------------------------------------------------------------------ RK4
