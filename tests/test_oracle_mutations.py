@@ -12,14 +12,21 @@ import types
 
 import pytest
 
-import test_oracle_pins as pins
+import test_oracle_cpbc
+import test_oracle_dp5
+import test_oracle_frame
+import test_oracle_pins
+import test_oracle_tensor_filter
+
+PIN_MODULES = {"pins": test_oracle_pins, "cpbc": test_oracle_cpbc, "dp5": test_oracle_dp5,
+               "frame": test_oracle_frame, "tensor_filter": test_oracle_tensor_filter}
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _install_mutant(monkeypatch, modname, old, new):
     """Replace oracle.<modname> everywhere it is referenced (the package, the
-    other oracle modules, the pin module) by a copy whose source has the one
+    other oracle modules, the pin modules) by a copy whose source has the one
     occurrence of `old` replaced by `new`."""
     path = os.path.join(ROOT, "oracle", modname + ".py")
     with open(path) as f:
@@ -33,7 +40,7 @@ def _install_mutant(monkeypatch, modname, old, new):
     exec(compile(src.replace(old, new), path, "exec"), mod.__dict__)
     monkeypatch.setitem(sys.modules, full, mod)
     for name, m in list(sys.modules.items()):
-        if m is None or not (name == "oracle" or name.startswith("oracle.") or name.endswith("test_oracle_pins")):
+        if m is None or not (name == "oracle" or name.startswith("oracle.") or "test_oracle_" in name):
             continue
         for k, v in list(vars(m).items()):
             if v is orig:
@@ -99,16 +106,50 @@ CASES = {
     "Kerr-Schild H": ("kerr_schild", "H = M * r ** 3 / (r ** 4 + a * a * z * z)",
                       "H = M * r ** 3 / (r ** 4 - a * a * z * z)",
                       "test_rhs_of_exact_kerr_schild_converges_exponentially", (0.9, (3.0, 6.0))),
+    # tensor spherical-harmonic filter (oracle/tensor_filter.py)
+    "tensor filter back-projection without conjugate": (
+        "tensor_filter", "w = w * np.conj(E[A[k]][I[k]])", "w = w * E[A[k]][I[k]]",
+        "tensor_filter::test_idempotent_and_real_on_random_fields", ()),
+    "spin weights of the frame vectors": (
+        "tensor_filter", "np.conj(m)]), [0, 1, -1]", "np.conj(m)]), [0, -1, 1]",
+        "tensor_filter::test_vector_harmonics_pass_below_and_vanish_above_the_cut", (2, 1)),
+    # Dormand-Prince pair (oracle/dp5.py)
+    "DP5 stage coefficient": ("dp5", "[_F(44, 45), _F(-56, 15), _F(32, 9)],", "[_F(44, 45), _F(-56, 15), _F(32, 7)],",
+                              "dp5::test_fifth_order_weights_satisfy_all_order_conditions_exactly", ()),
+    "DP5 embedded weight": ("dp5", "_F(187, 2100)", "_F(187, 2000)",
+                            "dp5::test_fourth_order_companion_is_order_four_not_five", ()),
+    # rotating frame (oracle/frame.py)
+    "grid velocity sign": ("frame", "xdot = omega * np.cross(", "xdot = -omega * np.cross(",
+                           "frame::test_rotating_exact_solution_matches_its_time_derivative",
+                           [(1.0, 0.0, (0.3, -0.5, 0.8)), (1.0, 0.7, (0.0, 0.0, 1.0))]),
+    # constraint-preserving outer condition (oracle/gh.py)
+    "constraint-preserving correction sign": (
+        "gh", "wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)",
+        "wpsi = np.where(inc_psi, wpsi - v_psi[..., None, None] * nC3, wpsi)",
+        "cpbc::test_constraint_preserving_upsi_removes_the_normal_derivative", ()),
 }
+
+
+def _fails(fn, args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return True
+    return False
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_pin_catches_planted_mistake(name, monkeypatch):
+    """The pin passes on the real oracle (for every argument set) and fails on
+    the planted mistake (for at least one)."""
     modname, old, new, pin, args = CASES[name]
+    where, _, fname = pin.rpartition("::")
+    pin_fn = getattr(PIN_MODULES[where or "pins"], fname)
     if args == "monkeypatch":
-        args = (monkeypatch,)
-    pin_fn = getattr(pins, pin)
-    pin_fn(*args)                                    # the pin passes on the real oracle
+        arg_sets = [(monkeypatch,)]
+    else:
+        arg_sets = args if isinstance(args, list) else [args]
+    for a in arg_sets:
+        pin_fn(*a)
     _install_mutant(monkeypatch, modname, old, new)
-    with pytest.raises(AssertionError):
-        pin_fn(*args)
+    assert any(_fails(pin_fn, a) for a in arg_sets), "no pin failed on: " + name
