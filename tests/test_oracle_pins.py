@@ -11,6 +11,7 @@ import pytest
 from scipy.special import sph_harm_y
 
 from oracle import grid, spectral, gh, kerr_schild, evolve
+import exact_solutions
 
 
 # ------------------------------------------------------------------ grids
@@ -301,88 +302,27 @@ def test_rhs_of_exact_kerr_schild_converges_exponentially(chi, shell):
     assert errs[2] < 1e-6
 
 
-# Flat spacetime in time-dependent, non-linear coordinates: x^mu = F^mu(t, x, y, z)
-# with F close to the identity.  Every constraint vanishes (with H_a = -Gamma_a of
-# this metric), so the exact d_t u must equal the GH right-hand side; unlike the
-# stationary Kerr-Schild data it has psi^cd Pi_ca Pi_db != 0 and d_t H_a != 0.
-_PAIRS = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
-
-
-def _moving_minkowski_metric():
-    import sympy as sp
-    t, x, y, z = c = sp.symbols("t x y z", real=True)
-    F = [t + sp.Rational(1, 5) * sp.sin(t) * (1 + sp.Rational(3, 10) * x) + sp.Rational(1, 10) * x * y,
-         x + sp.Rational(3, 20) * sp.sin(sp.Rational(7, 10) * t + y / 2),
-         y + z * t / 10,
-         z + t ** 2 / 20]
-    J = sp.Matrix(4, 4, lambda m, a: sp.diff(F[m], c[a]))
-    g = J.T * sp.diag(-1, 1, 1, 1) * J                  # g_ab = J^m_a eta_mn J^n_b
-    f_g = sp.lambdify(c, g, "numpy")
-    f_dg = sp.lambdify(c, [sp.diff(g, v) for v in c], "numpy")
-    return f_g, f_dg
-
-
-def _moving_minkowski_fields(f_g, f_dg, p):
-    """(u[50], H[4], alpha) at the event p = (t, x, y, z), computed from the exact
-    metric and its exact first derivatives: Phi_iab = d_i g_ab,
-    Pi_ab = -(d_t g_ab - beta^k Phi_kab) / alpha, H_a = -g^bc Gamma_abc."""
-    g = np.array(f_g(*p), dtype=float)
-    dg = np.array(f_dg(*p), dtype=float)                # dg[c, a, b] = d_c g_ab
-    gi3 = np.linalg.inv(g[1:, 1:])
-    b_up = gi3 @ g[0, 1:]
-    alpha = np.sqrt(b_up @ g[0, 1:] - g[0, 0])
-    Phi = dg[1:]
-    Pi = -(dg[0] - np.einsum("k,kab->ab", b_up, Phi)) / alpha
-    Gam = 0.5 * (np.einsum("bac->abc", dg) + np.einsum("cab->abc", dg) - dg)
-    H = -np.einsum("bc,abc->a", np.linalg.inv(g), Gam)
-    u = np.zeros(50)
-    for q, (a, b) in enumerate(_PAIRS):
-        u[q], u[10 + q] = g[a, b], Pi[a, b]
-        for i in range(3):
-            u[20 + 10 * i + q] = Phi[i, a, b]
-    return u, H, alpha
-
-
-def _central_diff(f, p, axis, h=2e-3):
-    """8th-order central difference of f along coordinate `axis` at p."""
-    w = [1 / 280, -4 / 105, 1 / 5, -4 / 5, 0.0, 4 / 5, -1 / 5, 4 / 105, -1 / 280]
-    acc = 0.0
-    for j, c in enumerate(w):
-        if c:
-            q = list(p)
-            q[axis] += (j - 4) * h
-            acc = acc + c * np.asarray(f(q))
-    return acc / h
-
-
 def test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates():
     """The pointwise GH right-hand side at exact data of a solution equals its
     exact time derivative, except for the d_t H_b part of -2 alpha nabla_(a H_b),
     which the right-hand side leaves out (gauge source held fixed in time):
     RHS(Pi_ab) = d_t Pi_ab + alpha (delta^0_a d_t H_b + delta^0_b d_t H_a).
-    Pins every term that does not multiply a constraint, including the
-    Pi-Pi, Gamma-Gamma and t t Pi Pi terms that vanish on stationary
-    Kerr-Schild data.  Any damping parameters: the constraints vanish."""
-    f_g, f_dg = _moving_minkowski_metric()
-    fields = lambda q: _moving_minkowski_fields(f_g, f_dg, q)[0]
-    gauge = lambda q: _moving_minkowski_fields(f_g, f_dg, q)[1]
+    The solution is flat space in time-dependent, non-linear coordinates
+    (tests/exact_solutions.py), where every constraint vanishes.  Pins every
+    term that does not multiply a constraint, including the Pi-Pi,
+    Gamma-Gamma and t t Pi Pi terms that vanish on stationary Kerr-Schild
+    data.  Any damping parameters: the constraints vanish."""
+    f_g, f_dg = exact_solutions.moving_minkowski_metric()
     rng = np.random.default_rng(15)
-    for _ in range(4):
-        p = [rng.uniform(0.0, 1.0)] + list(rng.uniform(-0.5, 0.5, 3))
-        u, H, alpha = _moving_minkowski_fields(f_g, f_dg, p)
-        du = np.stack([_central_diff(fields, p, 1 + k) for k in range(3)])      # [3, 50]
-        dH = np.stack([_central_diff(gauge, p, 1 + k) for k in range(3)])       # [3, 4]
-        dt_u = _central_diff(fields, p, 0)
-        dt_H = _central_diff(gauge, p, 0)
-        want = dt_u.copy()
-        for q, (a, b) in enumerate(_PAIRS):
-            want[10 + q] += alpha * ((dt_H[b] if a == 0 else 0.0) + (dt_H[a] if b == 0 else 0.0))
-        for g0, g1, g2 in [(1.0, -1.0, 1.0), (0.3, 0.7, 2.0)]:
-            got = gh.gh_rhs_pointwise(u[None], du[None], H[None], dH[None], g0, g1, g2)[0]
-            assert np.abs(got - want).max() < 1e-8, np.abs(got - want).max()
-    # the data are not trivial: the Pi-Pi contraction is of order one
+    t = rng.uniform(0.0, 1.0, 4)
+    x, y, z = rng.uniform(-0.5, 0.5, (3, 4))
+    u, du, H, dH, want = exact_solutions.expected_rhs(f_g, f_dg, t, x, y, z)
+    for g0, g1, g2 in [(1.0, -1.0, 1.0), (0.3, 0.7, 2.0)]:
+        got = gh.gh_rhs_pointwise(u, du, H, dH, g0, g1, g2)
+        assert np.abs(got - want).max() < 1e-8, np.abs(got - want).max()
+    # the data are not trivial: the Pi-Pi contraction is of order 1e-2
     psi, Pi, _ = gh.unpack_fields(u)
-    assert np.abs(np.einsum("cd,ca,db->ab", np.linalg.inv(psi), Pi, Pi)).max() > 1e-3
+    assert np.abs(np.einsum("...cd,...ca,...db->...ab", np.linalg.inv(psi), Pi, Pi)).max() > 1e-3
 
 
 def _minkowski_point_state(rng, n=6):
