@@ -192,15 +192,33 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.skip = 0
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
+    def _rows(self):
+        self.f.flush()
+        rows = []
+        for ln in open(self.f.name):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        return rows
+
     def start(self):
+        """Start sampling every 50 ms and wait for the first sample, so that the
+        samples taken from here on fall inside the region timed next."""
+        self.skip = 0
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and not self._rows():
+            time.sleep(0.02)
+        self.skip = len(self._rows())
 
     def stop(self):
         if self.proc is None:
@@ -210,13 +228,9 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.f.flush()
-        rows = []
-        for ln in open(self.f.name):
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        allrows = self._rows()
         os.unlink(self.f.name)
+        rows = allrows[self.skip:] or allrows[-1:]     # the samples inside the timed region
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -224,7 +238,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
         return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
-                    reasons=reasons, samples=len(rows))
+                    reasons=reasons, samples=len(allrows) - self.skip, interval_ms=50)
 
 
 # ------------------------------------------------------------- our arm
@@ -296,8 +310,8 @@ def run_ours(args, w):
     # ---- device-resident timed region (the headline value)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
-    barrier()
     clocks.start()
+    barrier()
     n0 = dom.launch_count()
     for i in range(args.steps):
         flush.zero_()
