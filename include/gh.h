@@ -29,6 +29,10 @@
  *    device (a non-finite constraint norm) are latched and reported by
  *    gh_sync.  No call throws or aborts; each returns a gh_status, and
  *    gh_last_error gives a one-line reason.
+ *  - Errors common to every call, unless its comment says more: GH_EINVAL for
+ *    a NULL domain or a NULL required pointer, GH_ECUDA when a CUDA call or a
+ *    launch fails (the reason in gh_last_error).  Device-side errors are only
+ *    read by gh_sync, so that no other call has to synchronise.
  */
 #ifndef GH_H
 #define GH_H
