@@ -87,3 +87,16 @@ def test_schedule_entry_points_reject_bad_arguments_on_the_host(lib):
 def test_overlap_switch_rejects_bad_arguments_on_the_host(lib):
     lib.gh_set_overlap.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.gh_set_overlap(None, 1) == 1              # GH_EINVAL: no domain
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """A copy of the package without libgh.so: importing the binding raises
+    instead of falling back to anything."""
+    import shutil
+    src = os.path.join(ROOT, "paper_1804_09101_gb300")
+    shutil.copytree(src, str(tmp_path / "paper_1804_09101_gb300"),
+                    ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1804_09101_gb300.gh"], cwd=str(tmp_path),
+                       capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert r.returncode != 0 and "libgh.so not built" in r.stderr, r.stderr[-500:]
