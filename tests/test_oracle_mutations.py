@@ -82,6 +82,12 @@ CASES = {
                                        "test_interface_exchange_is_upwind_per_characteristic_family", (-1.0,)),
     "outer BC freezes outgoing": ("gh", "        mask = (v < 0.0)\n", "        mask = (v > 0.0)\n",
                                   "test_outer_bc_zeroes_only_incoming_fields", ()),
+    "three-index constraint sign": ("gh", "    C3 = dpsi - Phi\n    C4 = np.einsum(", "    C3 = Phi - dpsi\n    C4 = np.einsum(",
+                                    "test_constraint_components_of_fields_with_a_known_violation", ()),
+    "four-index constraint antisymmetrised the wrong way": (
+        "gh", 'C4 = np.einsum("...ijab->...ijab", dPhi) - np.einsum("...jiab->...ijab", dPhi)',
+        'C4 = np.einsum("...jiab->...ijab", dPhi) - np.einsum("...ijab->...ijab", dPhi)',
+        "test_constraint_components_of_fields_with_a_known_violation", ()),
     # spectral maps (oracle/spectral.py)
     "Chebyshev derivative recurrence": ("spectral", "b[k] = (b[k + 2] + 2.0 * (k + 1) * a[k + 1]) / cb",
                                         "b[k] = (b[k + 2] + 2.0 * k * a[k + 1]) / cb",

@@ -325,6 +325,44 @@ def test_rhs_equals_the_time_derivative_of_flat_space_in_moving_coordinates():
     assert np.abs(np.einsum("...cd,...ca,...db->...ab", np.linalg.inv(psi), Pi, Pi)).max() > 1e-3
 
 
+def test_constraint_components_of_fields_with_a_known_violation():
+    """psi_ab a quadratic polynomial in (x, y, z) (differentiated exactly on the
+    grid), Phi_iab = d_i psi_ab + delta_iab with delta linear in (x, y, z):
+    then C_iab = -delta_iab and C_ijab = d_i delta_jab - d_j delta_iab (a
+    constant), stored at 4 + 10 i + p and 34 + 10 q + p with
+    q = 0, 1, 2 for (ij) = (xy), (xz), (yz).  The quadrature norm is checked
+    against the same values summed with the volume weights."""
+    g = grid.shell_grid(2.0, 3.5, 7, 5)
+    X, Y, Z = grid.cartesian_coords(g)                     # [n_r, th, ph]
+    rng = np.random.default_rng(16)
+    a0, A, B = rng.standard_normal(10), rng.standard_normal((10, 3)), rng.standard_normal((10, 3, 3))
+    D0, D1 = rng.standard_normal((3, 10)), rng.standard_normal((3, 10, 3))
+    P = np.stack([X, Y, Z])                                # [3, n_r, th, ph]
+    psi = 1e-2 * (a0[:, None, None, None] + np.einsum("pk,k...->p...", A, P)
+                  + np.einsum("pkl,k...,l...->p...", B, P, P))
+    for q, (a, b) in enumerate(gh.PAIRS):
+        psi[q] += {(0, 0): -1.0, (1, 1): 1.0, (2, 2): 1.0, (3, 3): 1.0}.get((a, b), 0.0)
+    dpsi = 1e-2 * (A.T[:, :, None, None, None] + np.einsum("pkl,l...->kp...", B + np.swapaxes(B, 1, 2), P))
+    delta = D0[:, :, None, None, None] + np.einsum("ipk,k...->ip...", D1, P)     # [3 (i), 10, ...]
+    Phi = dpsi + delta
+    u = np.zeros((g["n_r"], 50) + X.shape[1:])
+    u[:, 0:10] = np.moveaxis(psi, 0, 1)
+    u[:, 10:20] = 0.01 * rng.standard_normal((g["n_r"], 10) + X.shape[1:])
+    for i in range(3):
+        u[:, 20 + 10 * i:30 + 10 * i] = np.moveaxis(Phi[i], 0, 1)
+    dom = evolve.Domain([(2.0, 3.5, 7, 5)], 1.0, 0.0)
+    cs, norms = evolve.constraints(dom, [u])
+    c = cs[0]                                               # [n_r, 64, th, ph]
+    scale = np.abs(delta).max()
+    for i in range(3):
+        assert np.abs(c[:, 4 + 10 * i:14 + 10 * i] + np.moveaxis(delta[i], 0, 1)).max() < 1e-10 * scale
+    for q, (i, j) in enumerate([(0, 1), (0, 2), (1, 2)]):
+        want = D1[j, :, i] - D1[i, :, j]                   # d_i delta_j - d_j delta_i, per pair
+        assert np.abs(c[:, 34 + 10 * q:44 + 10 * q] - want[None, :, None, None]).max() < 1e-9 * scale
+    w = grid.volume_weights(g)
+    assert abs(norms[0] - float(np.sum(w * np.sum(c * c, axis=1)))) < 1e-12 * norms[0]
+
+
 def _minkowski_point_state(rng, n=6):
     psi = np.broadcast_to(np.diag([-1.0, 1, 1, 1]), (n, 4, 4)).copy()
     Pi = np.zeros((n, 4, 4))
