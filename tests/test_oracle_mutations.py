@@ -102,7 +102,21 @@ CASES = {
     "ExpCheb exponent": ("spectral", "return np.exp(-alpha * (k / (n - 1.0)) ** order)",
                          "return np.exp(-alpha * (k / (n - 1.0)) ** (2 * order))",
                          "test_expcheb_filter_scales_each_chebyshev_mode", ()),
+    "d/dphi harmonic sign": ("spectral", "        return -np.sqrt(2.0) * m * np.sin(m * phi)\n",
+                             "        return np.sqrt(2.0) * m * np.sin(m * phi)\n",
+                             "test_cartesian_gradient_exact_on_polynomials", (9, 5, 5)),
+    "SH truncation keeps one l too few": ("spectral", "mask = np.array([1.0 if l <= keep_l else 0.0",
+                                          "mask = np.array([1.0 if l < keep_l else 0.0",
+                                          "test_sh_truncation_filter_keeps_low_l_and_drops_high_l", ()),
+    # perturbations (oracle/perturb.py)
+    "pulse Phi without the radial factor": ("perturb", "    fr = A * dG * S[None]\n", "    fr = A * G * S[None]\n",
+                                            "test_psi_pulse_phi_is_the_gradient_of_psi", ()),
+    "pulse moving outward": ("perturb", "pi = -(fr - bdf) / s[\"alpha\"]", "pi = (fr - bdf) / s[\"alpha\"]",
+                             "test_psi_pulse_is_ingoing_on_flat_space", ()),
     # quadrature (oracle/grid.py)
+    "volume element without r^2": ("grid", "wr = g[\"wr\"] * 0.5 * (g[\"r_out\"] - g[\"r_in\"]) * g[\"r\"] ** 2",
+                                   "wr = g[\"wr\"] * 0.5 * (g[\"r_out\"] - g[\"r_in\"]) * g[\"r\"]",
+                                   "test_volume_weights_sum_to_shell_volume", ()),
     "Clenshaw-Curtis end weights": ("grid", "c = 1.0 if j in (0, N) else 2.0", "c = 2.0 if j in (0, N) else 1.0",
                                     "test_clenshaw_curtis_exact_on_polynomials", (11,)),
     # time stepper (oracle/evolve.py)
