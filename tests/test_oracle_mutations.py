@@ -142,6 +142,15 @@ CASES = {
     "grid velocity sign": ("frame", "xdot = omega * np.cross(", "xdot = -omega * np.cross(",
                            "frame::test_rotating_exact_solution_matches_its_time_derivative",
                            [(1.0, 0.0, (0.3, -0.5, 0.8)), (1.0, 0.7, (0.0, 0.0, 1.0))]),
+    "rotated Phi with the transposed rotation": (
+        "frame", 'Phi2 = np.einsum("ij,ac,bd,...jcd->...iab", R, L, L, Phi)',
+        'Phi2 = np.einsum("ji,ac,bd,...jcd->...iab", R, L, L, Phi)',
+        "frame::test_rotating_exact_solution_matches_its_time_derivative",
+        [(1.0, 0.0, (0.3, -0.5, 0.8)), (1.0, 0.7, (0.0, 0.0, 1.0))]),
+    "rotated gauge derivative with the transposed rotation": (
+        "frame", 'np.einsum("ij,ab,...jb->...ia", R, L, dH)', 'np.einsum("ji,ab,...jb->...ia", R, L, dH)',
+        "frame::test_rotating_exact_solution_matches_its_time_derivative",
+        [(1.0, 0.0, (0.3, -0.5, 0.8)), (1.0, 0.7, (0.0, 0.0, 1.0))]),
     # constraint-preserving outer condition (oracle/gh.py)
     "constraint-preserving correction sign": (
         "gh", "wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)",
