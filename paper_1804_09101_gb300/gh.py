@@ -103,6 +103,7 @@ _lib = _load()
 
 
 def library():
+    """The loaded libgh.so (ctypes.CDLL)."""
     return _lib
 
 
@@ -187,37 +188,45 @@ def gh_set_analytic_kerr_schild(dom, bh, M, chi, u):
 
 
 def gh_set_dt_scale(dom, bh, scale):
+    """gh_set_dt_scale: hole bh advances by dt * scale in every RK4 step."""
     dom._stream()
     dom._check(_lib.gh_set_dt_scale(dom.handle, int(bh), float(scale)))
 
 
 def gh_rk4_graph_capture(dom, dt, u, work, norm2_pre=None):
+    """gh_rk4_graph_capture: record one gh_rk4_step with these buffers as a CUDA graph (nothing runs)."""
     dom._stream()
     dom._check(_lib.gh_rk4_graph_capture(dom.handle, float(dt), _ptr(u, "u", dom.state_size),
                                          _ptr(work, "work", dom.work_size), _ptr(norm2_pre, "norm2_pre")))
 
 
 def gh_rk4_graph_launch(dom, n_steps):
+    """gh_rk4_graph_launch: replay the captured step n_steps times on the current stream."""
     dom._stream()
     dom._check(_lib.gh_rk4_graph_launch(dom.handle, int(n_steps)))
 
 
 def gh_set_gauge(dom, H, dH):
+    """gh_set_gauge: H [r][4][th][ph] and dH [r][12][th][ph] (entry 4i+a = d_i H_a) per shell."""
     dom._stream()
     dom._check(_lib.gh_set_gauge(dom.handle, _ptr(H, "H", 4 * dom.num_points), _ptr(dH, "dH", 12 * dom.num_points)))
 
 
 def gh_get_gauge(dom, H, dH):
+    """gh_get_gauge: copy the gauge source out, in the layout gh_set_gauge takes."""
     dom._stream()
     dom._check(_lib.gh_get_gauge(dom.handle, _ptr(H, "H", 4 * dom.num_points), _ptr(dH, "dH", 12 * dom.num_points)))
 
 
 def gh_set_background(dom, u_bg):
+    """gh_set_background: boundary background (lapse, shift, normal) from the metric part of u_bg."""
     dom._stream()
     dom._check(_lib.gh_set_background(dom.handle, _ptr(u_bg, "u_bg", dom.state_size)))
 
 
 def gh_add_perturbation(dom, kind, A, Rc, w, lmax, coeffs, u):
+    """gh_add_perturbation: add the psi pulse (kind 0) or the Pi modes (kind 1)
+    to u; coeffs holds (lmax+1)^2 values."""
     import numpy as np
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     if c.size != (lmax + 1) ** 2:
@@ -228,11 +237,13 @@ def gh_add_perturbation(dom, kind, A, Rc, w, lmax, coeffs, u):
 
 
 def gh_derivatives(dom, u, du):
+    """gh_derivatives: Cartesian derivatives of all 50 fields into du (3 states)."""
     dom._stream()
     dom._check(_lib.gh_derivatives(dom.handle, _ptr(u, "u", dom.state_size), _ptr(du, "du", 3 * dom.state_size)))
 
 
 def gh_rhs(dom, u, dudt):
+    """gh_rhs: dudt = F(u), the GH right-hand side with its boundary conditions."""
     dom._stream()
     dom._check(_lib.gh_rhs(dom.handle, _ptr(u, "u", dom.state_size), _ptr(dudt, "dudt", dom.state_size)))
 
@@ -244,17 +255,21 @@ def gh_rhs_noalloc(dom, u, dudt):
 
 
 def gh_rk4_step(dom, dt, u, work, norm2_pre=None):
+    """gh_rk4_step: one RK4 step of u in place, then the filters; norm2_pre
+    (optional) receives the constraint norms of the incoming u."""
     dom._stream()
     dom._check(_lib.gh_rk4_step(dom.handle, float(dt), _ptr(u, "u", dom.state_size),
                                 _ptr(work, "work", dom.work_size), _ptr(norm2_pre, "norm2_pre")))
 
 
 def gh_apply_filters(dom, u, work):
+    """gh_apply_filters: the domain's radial and angular filters on u in place."""
     dom._stream()
     dom._check(_lib.gh_apply_filters(dom.handle, _ptr(u, "u", dom.state_size), _ptr(work, "work", dom.work_size)))
 
 
 def gh_constraints(dom, u, c_out, norm2):
+    """gh_constraints: the 64 constraint components (c_out, optional) and the per-shell quadrature norms."""
     dom._stream()
     dom._check(_lib.gh_constraints(dom.handle, _ptr(u, "u", dom.state_size),
                                    _ptr(c_out, "c_out", 64 * dom.num_points), _ptr(norm2, "norm2", len(dom.shells))))
@@ -264,10 +279,12 @@ KERNEL_FAMILIES = ["radial", "angular", "pointwise", "bc", "radial_filter", "ang
 
 
 def gh_set_overlap(dom, on=True):
+    """gh_set_overlap: radial map on the domain's second stream beside the angular maps (default on)."""
     dom._check(_lib.gh_set_overlap(dom.handle, int(bool(on))))
 
 
 def gh_profile_enable(dom, on=True):
+    """gh_profile_enable: per-family CUDA-event timing of the library's launches (gh_profile_read)."""
     dom._stream()
     dom._check(_lib.gh_profile_enable(dom.handle, int(bool(on))))
 
@@ -284,6 +301,7 @@ GH_ALG_DENSE, GH_ALG_SEPARABLE, GH_ALG_SEPARABLE_FOLDED = 0, 1, 2
 
 
 def gh_set_algorithm(dom, algorithm):
+    """gh_set_algorithm: angular maps by GH_ALG_SEPARABLE_FOLDED (default), GH_ALG_SEPARABLE or GH_ALG_DENSE."""
     dom._stream()
     dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
 
@@ -301,16 +319,19 @@ def gh_set_rotating_frame(dom, axis, omega):
 
 
 def gh_set_time(dom, t):
+    """gh_set_time: set the domain clock (the rotating frame's angle follows it)."""
     dom._check(_lib.gh_set_time(dom.handle, float(t)))
 
 
 def gh_get_time(dom):
+    """gh_get_time: the domain clock."""
     t = ctypes.c_double()
     dom._check(_lib.gh_get_time(dom.handle, ctypes.byref(t)))
     return t.value
 
 
 def gh_set_outer_bc(dom, mode):
+    """gh_set_outer_bc: outer condition code, freezing (0) or constraint preserving (1)."""
     dom._stream()
     dom._check(_lib.gh_set_outer_bc(dom.handle, int(mode)))
 
@@ -336,6 +357,7 @@ def gh_dp5_step(dom, dt, rtol, atol, u, work):
 
 
 def new_dp5_work(dom):
+    """A zeroed device work area for gh_dp5_step."""
     return torch.zeros(dom.dp5_work_size, dtype=torch.float64, device="cuda")
 
 
@@ -353,6 +375,7 @@ def gh_autotune(dom, reps=5):
 
 
 def gh_get_schedule(dom):
+    """gh_get_schedule: the work schedule as a dict keyed by SCHEDULE_KEYS."""
     v = (ctypes.c_int * SCHEDULE_LEN)()
     dom._check(_lib.gh_get_schedule(dom.handle, v, SCHEDULE_LEN))
     return dict(zip(SCHEDULE_KEYS, list(v)))
@@ -418,8 +441,11 @@ def gh_perturbation_vjp(dom, kind, Rc, w, lmax, ubar):
 
 
 def new_vjp_work(dom):
+    """A zeroed device work area for the step VJPs."""
     return torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda")
 
 
 def gh_sync(dom):
+    """gh_sync: wait until the domain's stream is idle; raises on an error
+    latched on the device (and clears it)."""
     dom._check(_lib.gh_sync(dom.handle))
