@@ -182,6 +182,18 @@ gh_status gh_rhs(gh_domain* dom, const double* u, double* dudt);
  * s (computed inside the first stage, from the same derivatives). */
 gh_status gh_rk4_step(gh_domain* dom, double dt, double* u, double* work, double* norm2_pre);
 
+/* The same RK4 steps for data in HOST memory: copies u_in (host, one state)
+ * to a device state the domain owns (allocated on the first call, with an RK4
+ * work area), takes n_steps gh_rk4_step steps (filters included), copies the
+ * result to u_out (host, one state; may equal u_in) and, if norm2_out (host,
+ * n_shells doubles) is given, the constraint norms of the state the last step
+ * started from.  Synchronises the stream before returning.  Pinned host
+ * buffers (cudaHostAlloc, cudaHostRegister) copy asynchronously at full speed;
+ * pageable ones work too.  Errors: GH_EINVAL for n_steps < 1 or a NULL
+ * buffer, GH_ENOMEM on the first call, GH_ECUDA. */
+gh_status gh_rk4_step_host(gh_domain* dom, double dt, int n_steps, const double* u_in, double* u_out,
+                           double* norm2_out);
+
 /* CUDA graph of one RK4 step: gh_rk4_graph_capture records the launches of
  * gh_rk4_step(dom, dt, u, work, norm2_pre) (same pointers, profiler off) into a
  * graph owned by the domain, replacing any previous one; nothing runs.

@@ -1392,6 +1392,30 @@ gh_status gh_rk4_step(gh_domain* d, double dt, double* u, double* work, double* 
   return rk4_step_impl(d, dt, u, work, norm2_pre, nullptr);
 }
 
+gh_status gh_rk4_step_host(gh_domain* d, double dt, int n_steps, const double* u_in, double* u_out,
+                           double* norm2_out) {
+  if (!d || !u_in || !u_out) return fail(d, GH_EINVAL, "null argument");
+  if (n_steps < 1) return fail(d, GH_EINVAL, "need n_steps >= 1");
+  if (gh_status s = check_latched(d)) return s;
+  const size_t bytes = sizeof(double) * (size_t)d->state;
+  if (!d->host_u) {
+    void* p = nullptr;
+    GH_CUDA(d, alloc_zero(d, bytes, &p)); d->host_u = (double*)p;
+    GH_CUDA(d, alloc_zero(d, 3 * bytes, &p)); d->host_work = (double*)p;
+    GH_CUDA(d, alloc_zero(d, sizeof(double) * (size_t)d->n_shells, &p)); d->host_norm = (double*)p;
+  }
+  GH_CUDA(d, cudaMemcpyAsync(d->host_u, u_in, bytes, cudaMemcpyHostToDevice, d->stream));
+  for (int i = 0; i < n_steps; ++i)
+    if (gh_status s = rk4_step_impl(d, dt, d->host_u, d->host_work, norm2_out ? d->host_norm : nullptr, nullptr))
+      return s;
+  GH_CUDA(d, cudaMemcpyAsync(u_out, d->host_u, bytes, cudaMemcpyDeviceToHost, d->stream));
+  if (norm2_out)
+    GH_CUDA(d, cudaMemcpyAsync(norm2_out, d->host_norm, sizeof(double) * (size_t)d->n_shells,
+                               cudaMemcpyDeviceToHost, d->stream));
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  return GH_OK;
+}
+
 gh_status gh_rk4_step_save(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages) {
   if (!d || !u || !work || !stages) return fail(d, GH_EINVAL, "null argument");
   if (gh_status s = check_latched(d)) return s;

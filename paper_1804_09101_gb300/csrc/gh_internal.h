@@ -251,6 +251,10 @@ struct gh_domain {
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_step_launches = 0;
+  // device state, RK4 work area and norms of gh_rk4_step_host (allocated on first use)
+  double* host_u = nullptr;
+  double* host_work = nullptr;
+  double* host_norm = nullptr;
   // second stream for the radial map, which runs beside the angular maps of
   // the same right-hand side (both read the state, neither reads the other's
   // output); fork and join by events on the domain's stream (gh_set_overlap)

@@ -59,6 +59,7 @@ def _load():
         "gh_set_analytic_kerr_schild_spin": ([P, I, D, ctypes.POINTER(D), P], I),
         "gh_set_dt_scale": ([P, I, D], I),
         "gh_rk4_graph_capture": ([P, D, P, P, P], I),
+        "gh_rk4_step_host": ([P, D, I, P, P, P], I),
         "gh_rk4_graph_launch": ([P, I], I),
         "gh_set_gauge": ([P, P, P], I),
         "gh_set_background": ([P, P], I),
@@ -191,6 +192,26 @@ def gh_set_dt_scale(dom, bh, scale):
     """gh_set_dt_scale: hole bh advances by dt * scale in every RK4 step."""
     dom._stream()
     dom._check(_lib.gh_set_dt_scale(dom.handle, int(bh), float(scale)))
+
+
+def _host_ptr(t, name, numel):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 CPU tensor" % name)
+    if t.numel() < numel:
+        raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def gh_rk4_step_host(dom, dt, n_steps, u_in, u_out, norm2=None):
+    """gh_rk4_step_host: n_steps RK4 steps of a HOST state (CPU float64 tensors,
+    pinned for full-speed copies); copies in, steps on the device, copies out."""
+    dom._stream()
+    dom._check(_lib.gh_rk4_step_host(dom.handle, float(dt), int(n_steps),
+                                     _host_ptr(u_in, "u_in", dom.state_size),
+                                     _host_ptr(u_out, "u_out", dom.state_size),
+                                     _host_ptr(norm2, "norm2", len(dom.shells))))
 
 
 def gh_rk4_graph_capture(dom, dt, u, work, norm2_pre=None):

@@ -100,3 +100,10 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
                        capture_output=True, text=True, timeout=600,
                        env=dict(os.environ, PYTHONPATH=str(tmp_path)))
     assert r.returncode != 0 and "libgh.so not built" in r.stderr, r.stderr[-500:]
+
+
+def test_host_step_rejects_bad_arguments_on_the_host(lib):
+    lib.gh_rk4_step_host.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    buf = (ctypes.c_double * 4)()
+    assert lib.gh_rk4_step_host(None, 0.1, 1, buf, buf, None) == 1     # GH_EINVAL: no domain

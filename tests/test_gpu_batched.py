@@ -123,6 +123,32 @@ def test_radial_map_on_the_side_stream_changes_no_bit():
     assert gh._lib.gh_set_overlap(dom.handle, 2) != 0      # GH_EINVAL
 
 
+def test_host_buffer_steps_equal_device_steps_bitwise():
+    """gh_rk4_step_host (host state in and out, pinned or pageable) against the
+    same steps on a device state, with the constraint norms of the last step."""
+    from paper_1804_09101_gb300 import gh
+    holes = _small_batch()
+    dom, u, _ = _build(holes, gh)
+    u0 = to_host(u).copy()
+    work = dom.new_work()
+    n2 = torch.zeros(len(dom.shells), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        gh.gh_rk4_step(dom, 1.0, u, work, n2)
+    want, want_n2 = to_host(u), n2.cpu().numpy()
+    for pinned in (True, False):
+        src = torch.from_numpy(u0.copy())
+        out = torch.empty_like(src)
+        norms = torch.zeros(len(dom.shells), dtype=torch.float64)
+        if pinned:
+            src, out, norms = src.pin_memory(), out.pin_memory(), norms.pin_memory()
+        gh.gh_rk4_step_host(dom, 1.0, 3, src, out, norms)
+        assert np.array_equal(out.numpy(), want), pinned
+        assert np.array_equal(norms.numpy(), want_n2), pinned
+    inplace = torch.from_numpy(u0.copy()).pin_memory()
+    gh.gh_rk4_step_host(dom, 1.0, 3, inplace, inplace)
+    assert np.array_equal(inplace.numpy(), want)
+
+
 def test_batched_workload_builds_and_steps():
     from paper_1804_09101_gb300 import gh
     w = workloads.batched_workload(n_bh=8)
