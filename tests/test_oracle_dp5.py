@@ -85,3 +85,11 @@ def test_controller_rejects_large_steps_and_clamps_growth():
     assert ok and err == 0.0 and np.isclose(dt_next, 0.5 * dp5.FAC_MAX)
     _, err, ok, dt_next = dp5.attempt(f, u, 1e-3, 1e-6, 1e-6)
     assert ok and np.isclose(dt_next, 1e-3 * min(5.0, max(0.2, 0.9 * err ** -0.2)))
+    # the exponent 1/5 matches the embedded pair's dt^5 local error: from an
+    # unclamped error estimate, one controller step lands near err = 0.9^5
+    g = lambda v: [-1.0 * v[0]]
+    for dt in (0.2, 0.1):
+        _, err, _, dt_next = dp5.attempt(g, u, dt, 1e-8, 1e-8)
+        assert 0.2 < dt_next / dt < 5.0
+        _, err2, _, _ = dp5.attempt(g, u, dt_next, 1e-8, 1e-8)
+        assert abs(err2 - 0.9 ** 5) < 0.05, (dt, err, err2)

@@ -138,6 +138,12 @@ CASES = {
                               "dp5::test_fifth_order_weights_satisfy_all_order_conditions_exactly", ()),
     "DP5 embedded weight": ("dp5", "_F(187, 2100)", "_F(187, 2000)",
                             "dp5::test_fourth_order_companion_is_order_four_not_five", ()),
+    "DP5 controller exponent": ("dp5", "SAFETY * err ** (-0.2)", "SAFETY * err ** (-0.25)",
+                                "dp5::test_controller_rejects_large_steps_and_clamps_growth", ()),
+    "DP5 error estimate without dt": ("dp5", "e = [dt * sum((b[j] - bh[j]) * k[j][i]", "e = [sum((b[j] - bh[j]) * k[j][i]",
+                                      "dp5::test_observed_orders_of_solution_and_error_estimate", ()),
+    "spin-weighted harmonic phase": ("tensor_filter", "pref = (-1) ** m * sqrt(", "pref = sqrt(",
+                                     "tensor_filter::test_spin_zero_is_scipy_ylm_and_eth_raises_spin", ()),
     # rotating frame (oracle/frame.py)
     "grid velocity sign": ("frame", "xdot = omega * np.cross(", "xdot = -omega * np.cross(",
                            "frame::test_rotating_exact_solution_matches_its_time_derivative",
