@@ -113,6 +113,20 @@ CASES = {
                                             "test_psi_pulse_phi_is_the_gradient_of_psi", ()),
     "pulse moving outward": ("perturb", "pi = -(fr - bdf) / s[\"alpha\"]", "pi = (fr - bdf) / s[\"alpha\"]",
                              "test_psi_pulse_is_ingoing_on_flat_space", ()),
+    "Chebyshev analysis end weight": ("spectral", "cbar[0] = cbar[-1] = 2.0\n    a = np.zeros_like(u, dtype=float)",
+                                      "cbar[0] = 2.0\n    a = np.zeros_like(u, dtype=float)",
+                                      "test_radial_derivative_exact_below_degree_n_r", ()),
+    "harmonic analysis without the theta weights": ("spectral", 'w = g["wth"][:, None] * g["wphi"]',
+                                                    'w = 0.5 + 0.0 * g["wth"][:, None] * g["wphi"]',
+                                                    "test_sh_truncation_filter_keeps_low_l_and_drops_high_l", ()),
+    "Pi modes with the Gaussian's width squared twice": (
+        "perturb", "    G = np.exp(-((r - Rc) / w) ** 2)\n    du = np.zeros(",
+        "    G = np.exp(-((r - Rc) / w) ** 4)\n    du = np.zeros(",
+        "test_pi_modes_recover_their_coefficients", ()),
+    # Kerr-Schild data, spin-vector form (oracle/kerr_schild.py)
+    "spin-vector Kerr-Schild rotating the wrong way": (
+        "kerr_schild", "(r * X[i] - cross[i] + ad * A[i] / r)", "(r * X[i] + cross[i] + ad * A[i] / r)",
+        "test_spin_vector_along_z_matches_the_scalar_form", ()),
     # quadrature (oracle/grid.py)
     "volume element without r^2": ("grid", "wr = g[\"wr\"] * 0.5 * (g[\"r_out\"] - g[\"r_in\"]) * g[\"r\"] ** 2",
                                    "wr = g[\"wr\"] * 0.5 * (g[\"r_out\"] - g[\"r_in\"]) * g[\"r\"]",
