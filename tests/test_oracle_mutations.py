@@ -88,6 +88,10 @@ CASES = {
         "gh", 'C4 = np.einsum("...ijab->...ijab", dPhi) - np.einsum("...jiab->...ijab", dPhi)',
         'C4 = np.einsum("...jiab->...ijab", dPhi) - np.einsum("...ijab->...ijab", dPhi)',
         "test_constraint_components_of_fields_with_a_known_violation", ()),
+    "interface results written to the wrong sides": (
+        "evolve", "        out[s][nr - 1] = np.moveaxis(na, -1, 0)\n        out[s + 1][0] = np.moveaxis(nb, -1, 0)",
+        "        out[s][nr - 1] = np.moveaxis(nb, -1, 0)\n        out[s + 1][0] = np.moveaxis(na, -1, 0)",
+        "test_domain_boundaries_touch_only_boundary_slices_and_upwind_by_side", ()),
     # spectral maps (oracle/spectral.py)
     "Chebyshev derivative recurrence": ("spectral", "b[k] = (b[k + 2] + 2.0 * (k + 1) * a[k + 1]) / cb",
                                         "b[k] = (b[k + 2] + 2.0 * k * a[k + 1]) / cb",

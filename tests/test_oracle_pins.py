@@ -508,6 +508,33 @@ def test_interface_exchange_is_upwind_per_characteristic_family(gamma1):
         assert np.abs(wna[0] - wb[0]).max() < 1e-13
 
 
+def test_domain_boundaries_touch_only_boundary_slices_and_upwind_by_side():
+    """ApplyBCs on a two-shell domain with random time derivatives: interior
+    slices and the excision slice are untouched; at the shared radius the
+    inner shell's outer slice and the outer shell's inner slice carry, per
+    characteristic family, the outer shell's value where it moves inward and
+    the inner shell's where it moves outward; at the outer boundary every
+    incoming family is zero."""
+    dom = evolve.Domain([(1.8, 4.0, 5, 5), (4.0, 8.0, 5, 5)], 1.0, 0.6)
+    rng = np.random.default_rng(17)
+    d = [rng.standard_normal((5, 50) + g["theta"].shape + g["phi"].shape) for g in dom.grids]
+    out = evolve.apply_boundaries(dom, d)
+    assert np.array_equal(out[0][:4], d[0][:4]) and np.array_equal(out[1][1:4], d[1][1:4])
+    bg = dom.boundary_bg(0, 4)
+    last = lambda a: np.moveaxis(a, 0, -1)
+    wi, wo = gh.to_char(last(d[0][4]), bg, dom.gamma2), gh.to_char(last(d[1][0]), bg, dom.gamma2)
+    ni, no = gh.to_char(last(out[0][4]), bg, dom.gamma2), gh.to_char(last(out[1][0]), bg, dom.gamma2)
+    for q, v in enumerate(gh.char_speeds(bg, dom.gamma1)):
+        ext = v.reshape(v.shape + (1,) * (wi[q].ndim - v.ndim))
+        assert np.abs(ni[q] - np.where(ext < 0, wo[q], wi[q])).max() < 1e-12, q
+        assert np.abs(no[q] - np.where(ext > 0, wi[q], wo[q])).max() < 1e-12, q
+    bgo = dom.boundary_bg(1, 4)
+    wout = gh.to_char(last(out[1][4]), bgo, dom.gamma2)
+    for q, v in enumerate(gh.char_speeds(bgo, dom.gamma1)):
+        ext = v.reshape(v.shape + (1,) * (wout[q].ndim - v.ndim))
+        assert np.abs(np.where(ext < 0, wout[q], 0.0)).max() < 1e-12, q
+
+
 # ------------------------------------------------------------------ RK4
 def test_rk4_matches_stability_polynomial(monkeypatch):
     lam = -0.7 + 0.3j
