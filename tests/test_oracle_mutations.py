@@ -92,6 +92,16 @@ CASES = {
         "evolve", "        out[s][nr - 1] = np.moveaxis(na, -1, 0)\n        out[s + 1][0] = np.moveaxis(nb, -1, 0)",
         "        out[s][nr - 1] = np.moveaxis(nb, -1, 0)\n        out[s + 1][0] = np.moveaxis(na, -1, 0)",
         "test_domain_boundaries_touch_only_boundary_slices_and_upwind_by_side", ()),
+    "inverse spacetime metric sign": (
+        "gh", 'psi_inv[..., 1:, 1:] = ginv - np.einsum("...i,...j->...ij", beta_up, beta_up)',
+        'psi_inv[..., 1:, 1:] = ginv + np.einsum("...i,...j->...ij", beta_up, beta_up)',
+        "test_inverse_spacetime_metric", ()),
+    "boundary normal not raised": ("gh", 'n_up = np.einsum("...ij,...j->...i", s["ginv"], n_dn)', "n_up = n_dn",
+                                   "test_characteristic_round_trip", ()),
+    # grid coordinates (oracle/grid.py)
+    "x and y swapped in the coordinates": ("grid", "    X = r * st * cp\n    Y = r * st * sp\n",
+                                           "    X = r * st * sp\n    Y = r * st * cp\n",
+                                           "test_cartesian_gradient_exact_on_polynomials", (9, 5, 5)),
     # spectral maps (oracle/spectral.py)
     "Chebyshev derivative recurrence": ("spectral", "b[k] = (b[k + 2] + 2.0 * (k + 1) * a[k + 1]) / cb",
                                         "b[k] = (b[k + 2] + 2.0 * k * a[k + 1]) / cb",
