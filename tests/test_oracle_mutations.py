@@ -150,6 +150,9 @@ CASES = {
     # time stepper (oracle/evolve.py)
     "RK4 weights": ("evolve", "dt / 6.0 * (p + 2.0 * q + 2.0 * r + s)", "dt / 6.0 * (p + 2.0 * q + r + 2.0 * s)",
                     "test_rk4_matches_stability_polynomial", "monkeypatch"),
+    "RK4 second stage node": ("evolve", "k2 = rhs(dom, [a + 0.5 * dt * k for a, k in zip(u, k1)])",
+                              "k2 = rhs(dom, [a + dt * k for a, k in zip(u, k1)])",
+                              "test_rk4_matches_stability_polynomial", "monkeypatch"),
     # Kerr-Schild data (oracle/kerr_schild.py)
     "Kerr-Schild H": ("kerr_schild", "H = M * r ** 3 / (r ** 4 + a * a * z * z)",
                       "H = M * r ** 3 / (r ** 4 - a * a * z * z)",
