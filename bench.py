@@ -1,21 +1,32 @@
 """Benchmark: GH right-hand-side grid-point evaluations per second on one GB300.
 
-One step = one full pass of the hot path on the 4-shell Kerr workload
-(a = 0.9, M = 1, shells [1.3, 3, 6, 12, 30], N_r = 21, L = 15; 43,008 points):
-an RK4 step (4 right-hand sides with derivatives, the fused GH kernel,
-characteristic boundary conditions and stage combines), the exponential
-Chebyshev and SH 2/3 filters, and the quadrature constraint norms (computed
-inside the first stage).  Throughput = points x 4 RHS evaluations per step / time.
+One step = one full pass of the hot path on the 8-shell Kerr workload (the
+largest configuration: a = 0.95, M = 1, eight geometric shells spanning
+r in [1.2, 100], N_r = 41, L = 31 (32 x 64 angular points); 671,744 points,
+a 269 MB state): an RK4 step (4 right-hand sides with derivatives, the fused
+GH kernel, characteristic boundary conditions and stage combines), the
+exponential Chebyshev and SH 2/3 filters, and the quadrature constraint norms
+(computed inside the first stage).  Throughput = points x 4 RHS evaluations
+per step / time.
 
 Each timed step replays the step captured once as a CUDA graph
 (gh_rk4_graph_capture / gh_rk4_graph_launch; --no-graph times direct
 gh_rk4_step calls).  The per-kernel times behind the roofline come from a second
 timed region of the same steps called directly with the library's CUDA-event
-brackets, which would otherwise add gaps to the headline region.  The state
-(17 MB) fits in L2, so L2 is flushed (a 256 MB write) before every timed step,
-outside the step's events.
+brackets, which would otherwise add gaps to the headline region.  The large
+state is bigger than L2, so the K steps are timed back to back; a workload
+whose state fits in L2 (--workload kerr4) gets a 256 MB L2 flush before every
+timed step, outside the step's events.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+The same line carries the other two parts of the metric, measured after the
+headline region: batched_over_plain (64 independent holes of uneven
+resolution as one domain replayed as a CUDA graph, against the per-hole loop
+of step calls) and adjoint_over_forward (gradient of the 200-step constraint
+energy with checkpoints every 20 steps, against the forward evolution), plus
+the 4-shell workload's throughput as a secondary figure (--no-extras skips
+them).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload ...]
 
 For N > 1 (torchrun, one rank per GPU) every rank evolves its own replica:
 the workload is one coupled black hole and does not shard (replicas only).
@@ -63,12 +74,14 @@ def parse():
                    help="rk4 (fixed step, the headline) or dp5 (Dormand-Prince 5(4), adaptive)")
     p.add_argument("--schedule", default=None,
                    help="explicit work schedule as JSON (keys of gh.SCHEDULE_KEYS) instead of gh_autotune")
-    p.add_argument("--workload", default="kerr4",
+    p.add_argument("--workload", default="large",
                    choices=["kerr4", "large", "schwarzschild", "batched", "adjoint", "families", "paper"],
-                   help="kerr4: 4-shell Kerr a=0.9 (default, the headline); large: 8-shell Kerr a=0.95, "
-                        "N_r=41, L=31; schwarzschild: 1 shell N_r=11, L=7; batched: 64 independent "
-                        "single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
+                   help="large: 8-shell Kerr a=0.95, N_r=41, L=31 (default, the headline); kerr4: 4-shell "
+                        "Kerr a=0.9, N_r=21, L=15; schwarzschild: 1 shell N_r=11, L=7; batched: 64 "
+                        "independent single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
                         "compared with the plain per-hole launch loop")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched, adjoint and 4-shell figures added to the large workload's line")
     p.add_argument("--no-graph", action="store_true",
                    help="time direct gh_rk4_step calls instead of replays of the captured step graph")
     p.add_argument("--no-overlap", action="store_true",
@@ -101,34 +114,88 @@ def blas_threads():
 
 
 # ------------------------------------------------------------- oracle timing
-def oracle_setup(w):
+FULL_RHS_POINTS = 50_000       # above this, one full oracle right-hand side takes minutes
+L2_BYTES = 129e6               # GB300 L2
+
+
+def oracle_setup(w, shells=None):
+    """The oracle's domain for the workload (or for the listed shells of it:
+    each shell's exact data and gauge source depend on that shell alone) and
+    the workload's initial state on it."""
     import numpy as np
     from oracle import evolve, perturb
-    dom = evolve.Domain(w.shells, w.M, w.chi, w.gamma0, w.gamma1, w.gamma2, w.filt_alpha,
+    idx = list(range(len(w.shells))) if shells is None else list(shells)
+    dom = evolve.Domain([w.shells[i] for i in idx], w.M, w.chi, w.gamma0, w.gamma1, w.gamma2, w.filt_alpha,
                         w.filt_order, w.radial_filter_on, w.sh_keep_l)
+    sizes = [n_r * 50 * (L + 1) * 2 * (L + 1) for (_, _, n_r, L) in w.shells]
+    offs = np.cumsum([0] + sizes)
+    noise = w.noise() if w.noise_amp else None
     u = []
-    for s, g in enumerate(dom.grids):
+    for j, (i, g) in enumerate(zip(idx, dom.grids)):
+        a = dom.u_exact[j].copy()
         p = w.pulse
-        u.append(dom.u_exact[s] + perturb.psi_pulse(g, dom.u_exact[s], p.amplitude, p.center, p.width,
-                                                      p.lmax, p.coeffs))
+        if p is not None:
+            if p.kind == "psi_pulse":
+                a = a + perturb.psi_pulse(g, dom.u_exact[j], p.amplitude, p.center, p.width, p.lmax, p.coeffs)
+            else:
+                a = a + perturb.pi_modes(g, p.center, p.width, p.lmax, p.coeffs)
+        if noise is not None:
+            a = a + noise[offs[i]:offs[i + 1]].reshape(a.shape)
+        u.append(a)
     return dom, u
 
 
+def oracle_interior_rhs_slice(dom, u, s, ir):
+    """The oracle's GH right-hand side (before boundary conditions) on radial
+    slice ir of shell s: the radial derivative of the shell's lines, the
+    harmonic analysis and derivative synthesis of the slice, DiffJac and the
+    pointwise GH algebra -- the steps of the oracle's rhs_interior restricted
+    to one slice."""
+    import numpy as np
+    from oracle import gh as ogh
+    from oracle import spectral
+    g = dom.grids[s]
+    us = u[s]
+    dr = spectral.radial_derivative(us, g)[ir]                       # [50, th, ph]
+    dth, dph = spectral.angular_derivatives(us[ir], g)               # [50, th, ph]
+    J = spectral.spherical_jacobian(g)[:, :, ir]                     # [3, 3, th, ph]
+    du = J[:, 0, None] * dr[None] + J[:, 1, None] * dth[None] + J[:, 2, None] * dph[None]
+    U = np.moveaxis(us[ir], 0, -1)                                   # [th, ph, 50]
+    dU = np.moveaxis(du, (0, 1), (-2, -1))                           # [th, ph, 3, 50]
+    H = np.moveaxis(dom.H[s][ir], 0, -1)
+    dH = np.moveaxis(dom.dH[s][ir], 0, -1).reshape(U.shape[:-1] + (3, 4))
+    return ogh.gh_rhs_pointwise(U, dU, H, dH, dom.gamma0, dom.gamma1, dom.gamma2)
+
+
 def cpu_baseline(w, min_seconds=10.0):
-    """Time the oracle's full right-hand side (all shells) until >= min_seconds."""
+    """The oracle on the host cores: full right-hand sides (all shells) until
+    >= min_seconds when one fits in a few seconds, else one interior
+    right-hand side of the first shell (a bounded sample of the workload)."""
     from oracle import evolve
-    dom, u = oracle_setup(w)
-    evals = 0
-    t0 = time.perf_counter()
-    while True:
-        evolve.rhs(dom, u)
-        evals += 1
+    if w.points() <= FULL_RHS_POINTS:
+        dom, u = oracle_setup(w)
+        evals = 0
+        t0 = time.perf_counter()
+        while True:
+            evolve.rhs(dom, u)
+            evals += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds:
+                break
+        pts = w.points() * evals
+        sample = ("%d full right-hand-side evaluation(s) of %s (%d points), %.1f s, numpy FP64 on the host"
+                  % (evals, w.name, w.points(), el))
+    else:
+        dom, u = oracle_setup(w, shells=[0])
+        t0 = time.perf_counter()
+        evolve.rhs_interior(dom, u)
         el = time.perf_counter() - t0
-        if el >= min_seconds:
-            break
-    return dict(value=w.points() * evals / el, unit=UNIT, cores=blas_threads(), kind="oracle",
-                sample="%d full right-hand-side evaluation(s) of the 4-shell workload (%d points), "
-                       "%.1f s, numpy FP64 on the host" % (evals, w.points(), el))
+        g = dom.grids[0]
+        pts = g["n_r"] * g["n_th"] * g["n_ph"]
+        sample = ("one interior right-hand side of the first of %d shells of %s (%d of %d points, no "
+                  "boundary exchange: a bounded sample), %.1f s, numpy FP64 on the host"
+                  % (len(w.shells), w.name, pts, w.points(), el))
+    return dict(value=pts / el, unit=UNIT, cores=blas_threads(), kind="oracle", sample=sample)
 
 
 REFERENCE_BUDGET_S = 150.0     # the whole --impl reference run, warm-up included
@@ -138,31 +205,46 @@ def run_reference(args, w):
     """The oracle on the host cores, timed per step.  A step is one full oracle
     right-hand side of the workload when the run fits the time budget at that
     size; otherwise a bounded sample of it: the interior right-hand side of one
-    shell, taking the shells in turn (about a quarter of the work, no
-    boundary exchange).  The value counts the points each step evaluated."""
+    shell, taking the shells in turn, or, where one shell alone is too slow
+    for the budget (the large workload), of one radial slice, taking the
+    shells and slices in turn.  The value counts the points each step
+    evaluated."""
     import types
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from oracle import evolve
     dom, u = oracle_setup(w)
-    t0 = time.perf_counter()
-    evolve.rhs(dom, u)                       # first warm-up step, also sizes the sample
-    t_full = time.perf_counter() - t0
-    full = t_full * (args.steps + args.warmup) <= REFERENCE_BUDGET_S
     shells_pts = [g["n_r"] * g["n_th"] * g["n_ph"] for g in dom.grids]
+    n_steps = args.steps + args.warmup
+    ns = len(dom.grids)
+
+    def one_shell(s):
+        return types.SimpleNamespace(grids=[dom.grids[s]], H=[dom.H[s]], dH=[dom.dH[s]],
+                                     gamma0=dom.gamma0, gamma1=dom.gamma1, gamma2=dom.gamma2)
+
+    mode = "slice"
+    t_full = None
+    if w.points() <= FULL_RHS_POINTS:
+        t0 = time.perf_counter()
+        evolve.rhs(dom, u)                   # sizes the sample (and warms up)
+        t_full = time.perf_counter() - t0
+        mode = "full" if t_full * n_steps <= REFERENCE_BUDGET_S else "shell"
 
     def step(i):
-        if full:
+        if mode == "full":
             evolve.rhs(dom, u)
             return w.points()
-        s = i % len(dom.grids)
-        one = types.SimpleNamespace(grids=[dom.grids[s]], H=[dom.H[s]], dH=[dom.dH[s]],
-                                    gamma0=dom.gamma0, gamma1=dom.gamma1, gamma2=dom.gamma2)
-        evolve.rhs_interior(one, [u[s]])
-        return shells_pts[s]
+        if mode == "shell":
+            s = i % ns
+            evolve.rhs_interior(one_shell(s), [u[s]])
+            return shells_pts[s]
+        s = i % ns
+        ir = (i // ns) % dom.grids[s]["n_r"]
+        oracle_interior_rhs_slice(dom, u, s, ir)
+        return dom.grids[s]["n_th"] * dom.grids[s]["n_ph"]
 
-    for i in range(args.warmup - 1):
+    for i in range(args.warmup - (1 if t_full is not None else 0)):
         step(i)
     pts = 0
     t0 = time.perf_counter()
@@ -170,9 +252,13 @@ def run_reference(args, w):
         pts += step(i)
     el = time.perf_counter() - t0
     value = pts / el
-    what = ("one full oracle right-hand-side evaluation (all %d shells)" % len(dom.grids) if full else
-            "the oracle's interior right-hand side of one shell, the shells in turn (a bounded sample: "
-            "a full right-hand side takes %.2f s here)" % t_full)
+    what = {"full": "one full oracle right-hand-side evaluation (all %d shells)" % ns,
+            "shell": "the oracle's interior right-hand side of one shell, the shells in turn (a bounded "
+                     "sample: a full right-hand side takes %.2f s here)" % (t_full or 0.0),
+            "slice": "the oracle's interior right-hand side on one radial slice of one shell (the radial "
+                     "derivative of the shell's lines, the slice's harmonic analysis and derivative "
+                     "synthesis, DiffJac, the pointwise GH algebra), the shells and slices in turn (a "
+                     "bounded sample of the workload)"}[mode]
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000.0 * el / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
@@ -242,44 +328,78 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- our arm
-def run_ours(args, w):
+KERNEL_NAMES = {"pointwise": "pointwise_kernel (DiffJac + GH RHS + RK4 combine)",
+                "radial": "radial_kernel<false> (Chebyshev d/dx)"}
+ANGULAR_NAMES = {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: folded phi DFT, parity-split "
+                           "Legendre maps, folded inverse DFT)",
+                 "separable": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, Legendre maps, inverse DFT)",
+                 "dense": "gemm_batched_kernel (dense angular maps)"}
+PEAK_SOURCE = ("derived FP64 peak: 152 SMs x 4 SMSPs x one 32-lane DFMA every 64 cycles = 4 flop/clk/SM, at "
+               "2.07 GHz (the recipe's nominal 1.25 TFLOP/s; an FFMA loop measured 1.20)")
+
+
+def make_state(dom, w, dev):
     import torch
-    from paper_1804_09101_gb300 import build
-    build.build()
-    from paper_1804_09101_gb300 import costmodel, gh, replicas
+    from paper_1804_09101_gb300 import gh
+    u = dom.new_state()
+    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
+    p = w.pulse
+    if p is not None:
+        gh.gh_add_perturbation(dom, 0 if p.kind == "psi_pulse" else 1, p.amplitude, p.center, p.width, p.lmax,
+                               p.coeffs, u)
+    if w.noise_amp:
+        u += torch.from_numpy(w.noise()).to(dev)
+    return u
 
+
+def roofline_of(fam_ms, w, algorithm, sh_keep_l):
+    """Roofline object of the kernel family with the largest measured time:
+    its algorithmic flops per launch over its CUDA-event duration."""
+    from paper_1804_09101_gb300 import costmodel
+    dom_name = max(fam_ms, key=lambda n: fam_ms[n][0])
+    d_ms, d_n = fam_ms[dom_name]
+    d_flops = costmodel.family_flops(dom_name, w.shells, algorithm, sh_keep_l)
+    achieved = d_flops / (d_ms / d_n / 1000.0) / 1e12 if (d_n and d_flops) else None
+    peak = costmodel.GB300_FP64_PEAK_TFLOPS
+    names = dict(KERNEL_NAMES, angular=ANGULAR_NAMES[algorithm])
+    r = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=(achieved / peak) if achieved else None,
+             traffic=TRAFFIC_PER_LAUNCH.get((w.name, algorithm, dom_name)), kernel=names.get(dom_name, dom_name),
+             family=dom_name, flops_per_launch=d_flops, launch_ms=d_ms / d_n if d_n else None, peak_source=PEAK_SOURCE)
+    if dom_name == "pointwise":
+        r["flops_per_point"] = costmodel.POINTWISE_FLOPS_PER_POINT
+        r["flops_source"] = costmodel.POINTWISE_FLOPS_SOURCE
+        r["executed_flops_per_point"] = costmodel.POINTWISE_EXECUTED_FLOPS_PER_POINT
+    return r
+
+
+def measure_rk4(args, w, pg=None, host_e2e=True, clock_index=0):
+    """Time K RK4 steps of workload w (graph replays unless --no-graph): the
+    headline region, then the same steps called directly with the library's
+    per-family event brackets (kernel times), then end to end through
+    gh_rk4_step_host with pinned host buffers.  Returns the fields of the
+    bench line."""
+    import torch
+    from paper_1804_09101_gb300 import gh, replicas
     rank, world, local = dist_env()
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        pg = dist
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
     dom = gh.Domain.from_workload(w)
     gh.gh_set_overlap(dom, not args.no_overlap)
-    if args.algorithm == "auto":
-        args.algorithm = "folded"          # the library's default
-    else:
+    algorithm = "folded" if args.algorithm == "auto" else args.algorithm
+    if args.algorithm != "auto":
         gh.gh_set_algorithm(dom, {"dense": gh.GH_ALG_DENSE, "separable": gh.GH_ALG_SEPARABLE,
-                                  "folded": gh.GH_ALG_SEPARABLE_FOLDED}[args.algorithm])
+                                  "folded": gh.GH_ALG_SEPARABLE_FOLDED}[algorithm])
     if args.schedule:
         gh.gh_set_schedule(dom, json.loads(args.schedule))
     elif not args.no_autotune:
         gh.gh_autotune(dom, 5)
     if args.sh_filter == "tensor":
         gh.gh_set_sh_filter(dom, "tensor")
-    u = dom.new_state()
-    gh.gh_set_analytic_kerr_schild(dom, -1, w.M, w.chi, u)
-    p = w.pulse
-    if p is not None:
-        gh.gh_add_perturbation(dom, 0, p.amplitude, p.center, p.width, p.lmax, p.coeffs, u)
-    if w.noise_amp:
-        u += torch.from_numpy(w.noise()).to(dev)
+    u = make_state(dom, w, dev)
     work = dom.new_work()
     norm2 = torch.zeros(len(w.shells), dtype=torch.float64, device=dev)
-    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MB > L2
+    state_bytes = dom.state_size * 8
+    big = state_bytes > L2_BYTES
+    flush = None if big else torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -287,8 +407,12 @@ def run_ours(args, w):
         if pg is not None:
             pg.barrier()
 
+    def pre():
+        if flush is not None:
+            flush.zero_()
+
     for _ in range(args.warmup):
-        flush.zero_()
+        pre()
         gh.gh_rk4_step(dom, w.dt, u, work, norm2)
     gh.gh_sync(dom)
     use_graph = not args.no_graph
@@ -297,7 +421,7 @@ def run_ours(args, w):
         # steps); warm-up replays
         gh.gh_rk4_graph_capture(dom, w.dt, u, work, norm2)
         for _ in range(args.warmup):
-            flush.zero_()
+            pre()
             gh.gh_rk4_graph_launch(dom, 1)
         gh.gh_sync(dom)
 
@@ -307,22 +431,35 @@ def run_ours(args, w):
         else:
             gh.gh_rk4_step(dom, w.dt, u, work, norm2)
 
-    # ---- device-resident timed region (the headline value)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
+    # ---- device-resident timed region (the headline value): the state is
+    # larger than L2, so the K steps run back to back between one pair of
+    # events; otherwise L2 is flushed before each step, outside its events
+    clocks = ClockSampler(clock_index) if clock_index is not None else None
+    if clocks:
+        clocks.start()
     barrier()
     n0 = dom.launch_count()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        one_step()
-        ev[i][1].record(stream)
-    barrier()
+    if big:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(args.steps):
+            one_step()
+        b.record(stream)
+        barrier()
+        total_ms = a.elapsed_time(b)
+    else:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i in range(args.steps):
+            pre()
+            ev[i][0].record(stream)
+            one_step()
+            ev[i][1].record(stream)
+        barrier()
+        total_ms = sum(x.elapsed_time(y) for x, y in ev)
     launches = dom.launch_count() - n0
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    clk = clocks.stop() if clocks else None
     gh.gh_sync(dom)
     total_ms = replicas.max_over_ranks(total_ms, pg)
 
@@ -335,111 +472,133 @@ def run_ours(args, w):
         gh.gh_profile_read(dom, fam)
     barrier()
     for i in range(args.steps):
-        flush.zero_()
+        pre()
         gh.gh_rk4_step(dom, w.dt, u, work, norm2)
     barrier()
-    fam_ms = {}
-    for fam, name in enumerate(gh.KERNEL_FAMILIES):
-        fam_ms[name] = gh.gh_profile_read(dom, fam)
+    fam_ms = {name: gh.gh_profile_read(dom, fam) for fam, name in enumerate(gh.KERNEL_FAMILIES)}
     gh.gh_profile_enable(dom, False)
     gh.gh_sync(dom)
 
     pts = w.points()
-    value = replicas.job_throughput(pts * 4 * args.steps, world, total_ms)
-
-    # ---- end to end through the C ABI with host buffers: gh_rk4_step_host copies
-    # the state in from pinned host memory, steps, and copies the state and the
-    # constraint norms out, every step
-    u_host = u.detach().cpu().pin_memory()
-    out_host = torch.empty_like(u_host).pin_memory()
-    n_host = torch.empty(len(w.shells), dtype=torch.float64).pin_memory()
-    gh.gh_rk4_step_host(dom, w.dt, 1, u_host, out_host, n_host)     # allocates its device buffers
-    e2e_ms = 0.0
-    barrier()
-    for i in range(args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        gh.gh_rk4_step_host(dom, w.dt, 1, u_host, out_host, n_host)
-        b.record(stream)
-        b.synchronize()
-        e2e_ms += a.elapsed_time(b)
-    barrier()
-    e2e_ms = replicas.max_over_ranks(e2e_ms, pg)
-    e2e_value = replicas.job_throughput(pts * 4 * args.steps, world, e2e_ms)
-    state_bytes = dom.state_size * 8
-
-    # ---- roofline of the dominant kernel (the family with the largest time)
-    dom_name = max(fam_ms, key=lambda n: fam_ms[n][0])
-    d_ms, d_n = fam_ms[dom_name]
-    d_flops = costmodel.family_flops(dom_name, w.shells, args.algorithm, w.sh_keep_l)
-    achieved = d_flops / (d_ms / d_n / 1000.0) / 1e12 if (d_n and d_flops) else None
-    peak = costmodel.GB300_FP64_PEAK_TFLOPS
-    kernel_names = {"angular": {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: folded phi DFT, "
-                                          "parity-split Legendre maps, folded inverse DFT)",
-                                "separable": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, "
-                                             "Legendre maps, inverse DFT)",
-                                "dense": "gemm_batched_kernel (dense angular maps)"}[args.algorithm],
-                    "pointwise": "pointwise_kernel (DiffJac + GH RHS + RK4 combine)",
-                    "radial": "radial_kernel<false> (Chebyshev d/dx)"}
-    traffic = TRAFFIC_PER_LAUNCH.get((w.name, args.algorithm, dom_name))
-    roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                    frac=(achieved / peak) if achieved else None, traffic=traffic,
-                    kernel=kernel_names.get(dom_name, dom_name), family=dom_name,
-                    flops_per_launch=d_flops, launch_ms=d_ms / d_n if d_n else None,
-                    peak_source="derived FP64 FFMA peak: 152 SMs x 4 flop/clk x 2.07 GHz "
-                                "(recipe nominal 1.25 TFLOP/s; own FFMA loop measured 1.20)")
-    kernels = {name: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
-               for name, v in fam_ms.items() if v[1]}
-
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-                ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic",
-                config=dict(workload=w.name, points=pts, shells=[list(s) for s in w.shells], chi=w.chi,
-                            dt=w.dt, rhs_evals_per_step=4,
-                            step="RK4 step + ExpCheb(36,32) + SH keep l<=%d + constraint norms" % w.sh_keep_l,
-                            sh_filter={"component": "per Cartesian component (scalar Y_lm truncation)",
-                                       "tensor": "tensor spherical harmonics (spin-weighted sY_lm of the "
-                                                 "31 independent complex frame components)"}[args.sh_filter],
-                            l2="flushed before every timed step (256 MB write, outside the step events)",
-                            timed_step=("one replay of the captured RK4 graph (gh_rk4_graph_launch)" if use_graph
-                                        else "one gh_rk4_step call"),
-                            kernel_times="per-family CUDA events on the domain's stream, from a second "
-                                         "timed region of the same steps called directly (the maps one "
-                                         "after the other)",
-                            overlap=not args.no_overlap,
-                            parallelism="replicas" if world > 1 else "single GPU", algorithm=args.algorithm,
-                            schedule=gh.gh_get_schedule(dom),
-                            autotuned=not (args.no_autotune or args.schedule)),
-                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=state_bytes,
-                         d2h_bytes_per_step=state_bytes + 8 * len(w.shells),
-                         call="gh_rk4_step_host, pinned host buffers, one step per call"),
-                gpu_launches=launches, roofline=roofline, kernels=kernels)
+    out = dict(value=replicas.job_throughput(pts * 4 * args.steps, world, total_ms),
+               ms_per_step=total_ms / args.steps, launches=launches, clocks=clk, fam_ms=fam_ms,
+               roofline=roofline_of(fam_ms, w, algorithm, w.sh_keep_l), algorithm=algorithm,
+               schedule=gh.gh_get_schedule(dom), use_graph=use_graph, big=big, state_bytes=state_bytes,
+               kernels={name: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
+                        for name, v in fam_ms.items() if v[1]})
+    if host_e2e:
+        # ---- end to end through the C ABI with host buffers: gh_rk4_step_host
+        # copies the state in from pinned host memory, steps, and copies the
+        # state and the constraint norms out, every step
+        u_host = u.detach().cpu().pin_memory()
+        out_host = torch.empty_like(u_host).pin_memory()
+        n_host = torch.empty(len(w.shells), dtype=torch.float64).pin_memory()
+        gh.gh_rk4_step_host(dom, w.dt, 1, u_host, out_host, n_host)     # allocates its device buffers
+        e2e_ms = 0.0
+        barrier()
+        for i in range(args.steps):
+            pre()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gh.gh_rk4_step_host(dom, w.dt, 1, u_host, out_host, n_host)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms += a.elapsed_time(b)
+        barrier()
+        e2e_ms = replicas.max_over_ranks(e2e_ms, pg)
+        out["e2e"] = dict(value=replicas.job_throughput(pts * 4 * args.steps, world, e2e_ms), unit=UNIT,
+                          h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes + 8 * len(w.shells),
+                          call="gh_rk4_step_host, pinned host buffers, one step per call")
     if args.sh_filter == "tensor":
+        from paper_1804_09101_gb300 import costmodel
         tf = costmodel.tensor_filter_flops(w.shells, w.sh_keep_l)
         f_ms, f_n = fam_ms["angular_filter"]
         tf_ach = tf["total"] / (f_ms / f_n / 1000.0) / 1e12 if f_n else None
-        line["tensor_filter"] = dict(
+        peak = costmodel.GB300_FP64_PEAK_TFLOPS
+        out["tensor_filter"] = dict(
             kernels="tf_frame_kernel + tf_spin_kernel + tf_unframe_kernel", ms_per_step=f_ms / args.steps,
             flops_per_launch=tf["total"], flops_split={k: tf[k] for k in ("frame", "spin", "unframe")},
             achieved=tf_ach, peak=peak, unit="TFLOP/s", frac=(tf_ach / peak) if tf_ach else None, bound="alu")
-    if clk is not None:
-        line["clocks"] = clk
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "kerr4":
+    del dom
+    return out
+
+
+def run_ours(args, w):
+    import torch
+    from paper_1804_09101_gb300 import build
+    build.build()
+    rank, world, local = dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    torch.cuda.set_device(local)
+    m = measure_rk4(args, w, pg, clock_index=local)
+    big = m["big"]
+    line = dict(metric=METRIC, value=m["value"], unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=m["ms_per_step"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload=w.name, points=w.points(), shells=[list(s) for s in w.shells], chi=w.chi,
+                            dt=w.dt, rhs_evals_per_step=4,
+                            step="RK4 step + ExpCheb(36,32) + SH keep l<=%s + constraint norms"
+                                 % ("floor(2L/3)" if w.sh_keep_l == -2 else w.sh_keep_l),
+                            sh_filter={"component": "per Cartesian component (scalar Y_lm truncation)",
+                                       "tensor": "tensor spherical harmonics (spin-weighted sY_lm of the "
+                                                 "31 independent complex frame components)"}[args.sh_filter],
+                            l2=("inputs larger than L2: a %.0f MB state (7 states live: state, 3 derivative "
+                                "scratch, 3 RK4 work), K steps back to back between one pair of events"
+                                % (m["state_bytes"] / 1e6)) if big else
+                               "flushed before every timed step (256 MB write, outside the step events)",
+                            timed_step=("one replay of the captured RK4 graph (gh_rk4_graph_launch)"
+                                        if m["use_graph"] else "one gh_rk4_step call"),
+                            kernel_times="per-family CUDA events on the domain's stream, from a second "
+                                         "timed region of the same steps called directly",
+                            overlap=not args.no_overlap,
+                            parallelism="replicas" if world > 1 else "single GPU", algorithm=m["algorithm"],
+                            schedule=m["schedule"], autotuned=not (args.no_autotune or args.schedule)),
+                e2e=m["e2e"], gpu_launches=m["launches"], roofline=m["roofline"], kernels=m["kernels"])
+    if "tensor_filter" in m:
+        line["tensor_filter"] = m["tensor_filter"]
+    if m["clocks"] is not None:
+        line["clocks"] = m["clocks"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0 and world == 1 and args.workload == "large" and not args.no_extras:
+        from paper_1804_09101_gb300 import workloads
+        b = measure_batched(args)
+        line["batched_over_plain"] = b["batched_over_plain"]
+        line["adjoint_over_forward"] = None
+        a = measure_adjoint(args)
+        line["adjoint_over_forward"] = a["adjoint_over_forward"]
+        wk = workloads.kerr_four_shells()
+        k4 = measure_rk4(args, wk, None, host_e2e=False, clock_index=None)
+        line["secondary"] = dict(
+            batched=dict(workload=b["workload"], points=b["points"], holes=b["holes"], value=b["value"],
+                         plain_value=b["plain_value"], batched_over_plain=b["batched_over_plain"],
+                         steps=b["steps"], plain_steps=b["plain_steps"],
+                         nonfinite_holes_at_end=b["nonfinite_holes_at_end"],
+                         how="one domain over all holes, one CUDA-graph replay per RK4 step, against one "
+                             "domain per hole stepped by gh_rk4_step hole after hole"),
+            adjoint=dict(workload=a["workload"], points=a["points"], evolution_steps=a["evolution_steps"],
+                         checkpoint_every=a["checkpoint_every"], forward_s=a["forward_s"],
+                         gradient_s=a["gradient_s"], adjoint_over_forward=a["adjoint_over_forward"],
+                         backward_over_forward=a["backward_over_forward"], timing=a["timing"]),
+            kerr4=dict(workload=wk.name, points=wk.points(), value=k4["value"], ms_per_step=k4["ms_per_step"],
+                       roofline=k4["roofline"],
+                       l2="flushed before every timed step (256 MB write, outside the step events)"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
 
 
-def run_batched(args):
-    """64 independent holes: batched (one domain, CUDA graph per step) vs plain loop."""
+def measure_batched(args):
+    """64 independent holes: batched (one domain, CUDA graph per step) vs the
+    plain loop (one domain per hole, gh_rk4_step hole after hole)."""
     import torch
-    from paper_1804_09101_gb300 import build
-    build.build()
-    from paper_1804_09101_gb300 import costmodel, gh, workloads
+    from paper_1804_09101_gb300 import gh, workloads
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -484,13 +643,7 @@ def run_batched(args):
     clk = clocks.stop()
     launches = dom.launch_count() - n0
     batched_ms = a.elapsed_time(e)
-    # Holes with high spin at L = 7 are under-resolved near the ring singularity
-    # and can blow up within tens of steps; that is reported, not hidden.
-    try:
-        gh.gh_sync(dom)
-    except gh.GHError as err:
-        if err.status != gh.GH_ENONFINITE:
-            raise
+    gh.gh_sync(dom)
     nonfinite_holes = int((~torch.isfinite(norm2)).sum())
 
     # ---- plain: one domain per hole, launched hole after hole
@@ -519,10 +672,24 @@ def run_batched(args):
     e.record(stream)
     torch.cuda.synchronize()
     plain_ms = a.elapsed_time(e)
+    for d1, *_ in doms:
+        gh.gh_sync(d1)
 
     pts = w.points()
     value = pts * 4 * args.steps / (batched_ms / 1000.0)
     plain_value = pts * 4 * psteps / (plain_ms / 1000.0)
+    return dict(workload=w.name, points=pts, holes=len(w.holes), value=value, plain_value=plain_value,
+                batched_over_plain=value / plain_value, batched_ms=batched_ms, plain_ms=plain_ms,
+                steps=args.steps, plain_steps=psteps, nonfinite_holes_at_end=nonfinite_holes,
+                launches=launches, clocks=clk, fam_ms=fam_ms, state_bytes=dom.state_size * 8, w=w)
+
+
+def run_batched(args):
+    from paper_1804_09101_gb300 import build
+    build.build()
+    from paper_1804_09101_gb300 import costmodel
+    b = measure_batched(args)
+    w, fam_ms = b["w"], b["fam_ms"]
     dom_name = max(fam_ms, key=lambda n: fam_ms[n][0])
     d_ms, d_n = fam_ms[dom_name]
     d_flops = costmodel.family_flops(dom_name, [s[:4] for s in w.shells], "folded", None)
@@ -530,36 +697,34 @@ def run_batched(args):
         d_flops = sum(costmodel.fold_angular_flops([s[:4]], K=(2 * s[3]) // 3, two=False) for s in w.shells)
     achieved = d_flops / (d_ms / d_n / 1000.0) / 1e12 if (d_n and d_flops) else None
     peak = costmodel.GB300_FP64_PEAK_TFLOPS
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=args.steps, warmup=args.warmup,
-                ms_per_step=batched_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+    line = dict(metric=METRIC, value=b["value"], unit=UNIT, n_gpus=1, steps=args.steps, warmup=args.warmup,
+                ms_per_step=b["batched_ms"] / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
-                config=dict(workload=w.name, points=pts, holes=len(w.holes),
+                config=dict(workload=w.name, points=b["points"], holes=b["holes"],
                             step="batched: one CUDA-graph replay of an RK4 step over all holes "
                                  "(per-hole dt, ExpCheb + per-shell 2/3 SH truncation, constraint norms)",
-                            l2="state %.0f MB > L2" % (dom.state_size * 8 / 1e6),
-                            plain_value=plain_value, plain_ms_per_step=plain_ms / psteps,
-                            plain_steps=psteps, batched_over_plain=value / plain_value,
-                            plain="one domain per hole, gh_rk4_step hole after hole (18 launches each)",
-                            nonfinite_holes_at_end=nonfinite_holes),
-                gpu_launches=launches,
+                            l2="state %.0f MB > L2" % (b["state_bytes"] / 1e6),
+                            plain_value=b["plain_value"], plain_ms_per_step=b["plain_ms"] / b["plain_steps"],
+                            plain_steps=b["plain_steps"], batched_over_plain=b["batched_over_plain"],
+                            plain="one domain per hole, gh_rk4_step hole after hole",
+                            nonfinite_holes_at_end=b["nonfinite_holes_at_end"]),
+                batched_over_plain=b["batched_over_plain"], gpu_launches=b["launches"],
                 roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
                               frac=(achieved / peak) if achieved else None, traffic=None, family=dom_name,
                               flops_per_launch=d_flops, launch_ms=d_ms / d_n if d_n else None),
                 kernels={name: dict(ms_per_step=v[0] / 3, launches_per_step=v[1] / 3)
                          for name, v in fam_ms.items() if v[1]})
-    if clk is not None:
-        line["clocks"] = clk
+    if b["clocks"] is not None:
+        line["clocks"] = b["clocks"]
     print(json.dumps(line), flush=True)
 
 
-def run_adjoint(args):
+def measure_adjoint(args):
     """Adjoint workload: gradient of the 200-step time-integrated constraint
     energy with respect to 16 Pi-mode coefficients (checkpoints every 20 steps),
     timed against the forward evolution that defines it."""
     import numpy as np
     import torch
-    from paper_1804_09101_gb300 import build
-    build.build()
     from paper_1804_09101_gb300 import gh, workloads
     from paper_1804_09101_gb300.adjoint import constraint_energy_gradient, evolve_energy
     w = workloads.adjoint_single_shell()
@@ -592,20 +757,26 @@ def run_adjoint(args):
         E3, lam3 = constraint_energy_gradient(dom, u0, w.dt, steps, ckpt=steps)
     torch.cuda.synchronize()
     bwd_all = (time.perf_counter() - t0) / reps
-    pts = w.points()
-    line = dict(metric=METRIC, value=pts * 4 * steps / fwd, unit=UNIT, n_gpus=1, steps=reps, warmup=args.warmup,
-                ms_per_step=1000.0 * fwd / steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic",
-                config=dict(workload=w.name, points=pts, evolution_steps=steps, checkpoint_every=20,
-                            parameters=16, forward_s=fwd, gradient_s=bwd, adjoint_over_forward=bwd / fwd,
-                            backward_over_forward=(bwd - fwd) / fwd,
-                            keep_all_states_gradient_s=bwd_all,
-                            keep_all_states_backward_over_forward=(bwd_all - fwd) / fwd,
-                            energy=E, grad_norm=float(np.linalg.norm(g)),
-                            timing="wall clock around whole evolutions (host-driven launches), "
-                                   "mean of %d repetitions; gradient_s includes its own forward pass, "
-                                   "backward_over_forward excludes it (backward incl. checkpoint "
-                                   "recomputation)" % reps))
+    return dict(workload=w.name, points=w.points(), evolution_steps=steps, checkpoint_every=20, parameters=16,
+                forward_s=fwd, gradient_s=bwd, adjoint_over_forward=bwd / fwd,
+                backward_over_forward=(bwd - fwd) / fwd, keep_all_states_gradient_s=bwd_all,
+                keep_all_states_backward_over_forward=(bwd_all - fwd) / fwd, energy=E,
+                grad_norm=float(np.linalg.norm(g)), reps=reps, w=w,
+                timing="wall clock around whole evolutions (host-driven launches), mean of %d repetitions; "
+                       "gradient_s includes its own forward pass, backward_over_forward excludes it (backward "
+                       "incl. checkpoint recomputation)" % reps)
+
+
+def run_adjoint(args):
+    from paper_1804_09101_gb300 import build
+    build.build()
+    a = measure_adjoint(args)
+    steps = a["evolution_steps"]
+    line = dict(metric=METRIC, value=a["points"] * 4 * steps / a["forward_s"], unit=UNIT, n_gpus=1,
+                steps=a["reps"], warmup=args.warmup, ms_per_step=1000.0 * a["forward_s"] / steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                adjoint_over_forward=a["adjoint_over_forward"],
+                config={k: v for k, v in a.items() if k not in ("w", "reps")})
     print(json.dumps(line), flush=True)
 
 

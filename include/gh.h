@@ -225,6 +225,9 @@ gh_status gh_constraints(gh_domain* dom, const double* u, double* c_out, double*
  *     larger domains get GH_EINVAL with a message.  Use gh_rhs for them.
  *   - The first call on each device looks up the array's device address with
  *     that device current; make this first call before any stream capture.
+ *     The address is kept for the life of the process, so a device reset
+ *     (cudaDeviceReset, or the primary context torn down) while the library
+ *     is loaded is not supported for this entry point.
  *   - Every call uses the same array: calls that run at the same time on the
  *     GPU (other streams, other host threads) race and corrupt each other's
  *     results.  Serialise them.

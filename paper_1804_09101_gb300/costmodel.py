@@ -116,7 +116,9 @@ def sep_angular_flops(shells, K=None, two=True):
 # DFMA/DADD/DMUL counts of one launch on the 4-shell Kerr workload
 # (2 x 2,398,144 + 53,760 + 587,328 warp instructions x 32 lanes / 43,008
 # points).
-POINTWISE_FLOPS_PER_POINT = 4046
+POINTWISE_EXECUTED_FLOPS_PER_POINT = 4046
+POINTWISE_FLOPS_PER_POINT = POINTWISE_EXECUTED_FLOPS_PER_POINT
+POINTWISE_FLOPS_SOURCE = "executed FP64 instructions (ncu DFMA/DADD/DMUL), 4-shell Kerr workload"
 
 
 def fold_angular_flops(shells, K=None, two=True):

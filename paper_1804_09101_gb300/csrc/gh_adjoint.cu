@@ -150,10 +150,9 @@ sep_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
 }
 
 cudaError_t sep_adj_set_smem_limits(size_t bytes) {
-  static size_t cur[2] = {0, 0};
-  cudaError_t e = raise_smem_limit((const void*)sep_adjoint_kernel<true>, bytes, &cur[0]);
+  cudaError_t e = raise_smem_limit((const void*)sep_adjoint_kernel<true>, bytes);
   if (e != cudaSuccess) return e;
-  return raise_smem_limit((const void*)sep_adjoint_kernel<false>, bytes, &cur[1]);
+  return raise_smem_limit((const void*)sep_adjoint_kernel<false>, bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -542,10 +541,9 @@ gh_status afail(gh_domain* d, gh_status s, const std::string& m) {
 unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 cudaError_t radial_adjoint_smem_limits() {
-  static size_t cur[2] = {0, 0};
   const size_t bytes = gh::radial_adjoint_smem_bytes(64);
-  cudaError_t e = gh::raise_smem_limit((const void*)gh::radial_adjoint_kernel<false, true>, bytes, &cur[0]);
-  if (e == cudaSuccess) e = gh::raise_smem_limit((const void*)gh::radial_adjoint_kernel<true, false>, bytes, &cur[1]);
+  cudaError_t e = gh::raise_smem_limit((const void*)gh::radial_adjoint_kernel<false, true>, bytes);
+  if (e == cudaSuccess) e = gh::raise_smem_limit((const void*)gh::radial_adjoint_kernel<true, false>, bytes);
   return e;
 }
 
@@ -560,6 +558,7 @@ gh_status frames_at(gh_domain* d, double half, double full, int n) {
 }
 
 gh_status adj_ready(gh_domain* d) {
+  if (gh_status s = gh::check_latched(d)) return s;
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
   if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
     void* p = nullptr;

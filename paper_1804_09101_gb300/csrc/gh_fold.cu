@@ -219,10 +219,9 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
 }
 
 cudaError_t fold_set_smem_limits(size_t bytes) {
-  static size_t cur[2] = {0, 0};
-  cudaError_t e = raise_smem_limit((const void*)fold_angular_kernel<true>, bytes, &cur[0]);
+  cudaError_t e = raise_smem_limit((const void*)fold_angular_kernel<true>, bytes);
   if (e != cudaSuccess) return e;
-  return raise_smem_limit((const void*)fold_angular_kernel<false>, bytes, &cur[1]);
+  return raise_smem_limit((const void*)fold_angular_kernel<false>, bytes);
 }
 
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {

@@ -727,6 +727,7 @@ Frame frame_at(const gh_domain* d, double t) {
     for (int i = 0; i < 9; ++i) f.R[i] = (i % 4 == 0) ? 1.0 : 0.0;
   return f;
 }
+gh_status check_latched(gh_domain* d) { return ::check_latched(d); }
 }  // namespace gh
 
 extern "C" {
@@ -1398,11 +1399,20 @@ gh_status gh_rk4_step_host(gh_domain* d, double dt, int n_steps, const double* u
   if (n_steps < 1) return fail(d, GH_EINVAL, "need n_steps >= 1");
   if (gh_status s = check_latched(d)) return s;
   const size_t bytes = sizeof(double) * (size_t)d->state;
-  if (!d->host_u) {
-    void* p = nullptr;
-    GH_CUDA(d, alloc_zero(d, bytes, &p)); d->host_u = (double*)p;
-    GH_CUDA(d, alloc_zero(d, 3 * bytes, &p)); d->host_work = (double*)p;
-    GH_CUDA(d, alloc_zero(d, sizeof(double) * (size_t)d->n_shells, &p)); d->host_norm = (double*)p;
+  if (!d->host_u || !d->host_work || !d->host_norm) {
+    // All three buffers or none: a failed allocation leaves the domain without
+    // any, so the next call allocates again instead of launching on a null
+    // buffer (what did get allocated is freed with the domain).
+    void* pu = nullptr;
+    void* pw = nullptr;
+    void* pn = nullptr;
+    GH_CUDA(d, alloc_zero(d, bytes, &pu));
+    if (fault_injected("host_alloc")) return fail(d, GH_ENOMEM, "GH_FAULT=host_alloc: injected allocation failure");
+    GH_CUDA(d, alloc_zero(d, 3 * bytes, &pw));
+    GH_CUDA(d, alloc_zero(d, sizeof(double) * (size_t)d->n_shells, &pn));
+    d->host_u = (double*)pu;
+    d->host_work = (double*)pw;
+    d->host_norm = (double*)pn;
   }
   GH_CUDA(d, cudaMemcpyAsync(d->host_u, u_in, bytes, cudaMemcpyHostToDevice, d->stream));
   for (int i = 0; i < n_steps; ++i)
@@ -1513,6 +1523,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
 
 gh_status gh_apply_filters(gh_domain* d, double* u, double* work) {
   if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = check_latched(d)) return s;
   return filters(d, u, u, work);
 }
 

@@ -302,10 +302,13 @@ Frame frame_at(const gh_domain* d, double t);
 cudaError_t launch_dp5_lincomb(gh_domain* d, const double* base, const LinComb& lc, double* out);
 cudaError_t launch_dp5_error(gh_domain* d, const double* u, const double* unew, const LinComb& lc, double rtol,
                              double atol, double* err_dev);
-// Raise the dynamic shared-memory limit of kernel f to at least `bytes`.  The
-// limit is a process-wide attribute of the kernel that every domain shares, so
-// it only ever grows (*current tracks it; guarded by a mutex).
-cudaError_t raise_smem_limit(const void* f, size_t bytes, size_t* current);
+// Raise the dynamic shared-memory limit of kernel f on the current device to
+// at least `bytes`.  The limit is an attribute of the kernel on that device
+// which every domain there shares, so it only ever grows (tracked per kernel
+// and device, guarded by a mutex).
+cudaError_t raise_smem_limit(const void* f, size_t bytes);
+// Host-side fault injection (GH_FAULT=launch): GH_ECUDA before any launch.
+gh_status check_latched(gh_domain* d);
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph);
 cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out);
 cudaError_t sep_adj_set_smem_limits(size_t bytes);

@@ -10,7 +10,9 @@
 // is to keep the FP64 pipe busy, not to save HBM traffic.
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "gh_geom.cuh"
 #include "gh_internal.h"
@@ -108,12 +110,19 @@ radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __re
   }
 }
 
-cudaError_t raise_smem_limit(const void* f, size_t bytes, size_t* current) {
+cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+  // The attribute belongs to the kernel on the current device, so the largest
+  // limit set so far is tracked per (kernel, device).
   static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> current;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
-  if (bytes <= *current) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) *current = bytes;
+  size_t& cur = current[std::make_pair(f, dev)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
   return e;
 }
 
@@ -124,12 +133,11 @@ size_t radial_smem_bytes(int max_n) {
 
 cudaError_t radial_set_smem_limits() {
   const size_t bytes = radial_smem_bytes(MAXR);
-  static size_t cur[6] = {0, 0, 0, 0, 0, 0};
   const void* f[6] = {(const void*)radial_kernel<true, 2>, (const void*)radial_kernel<true, 3>,
                       (const void*)radial_kernel<true, 4>, (const void*)radial_kernel<false, 2>,
                       (const void*)radial_kernel<false, 3>, (const void*)radial_kernel<false, 4>};
   for (int i = 0; i < 6; ++i) {
-    cudaError_t e = raise_smem_limit(f[i], bytes, &cur[i]);
+    cudaError_t e = raise_smem_limit(f[i], bytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -328,10 +336,9 @@ sep_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
 }
 
 cudaError_t sep_set_smem_limits(size_t bytes) {
-  static size_t cur[2] = {0, 0};
-  cudaError_t e = raise_smem_limit((const void*)sep_angular_kernel<true>, bytes, &cur[0]);
+  cudaError_t e = raise_smem_limit((const void*)sep_angular_kernel<true>, bytes);
   if (e != cudaSuccess) return e;
-  return raise_smem_limit((const void*)sep_angular_kernel<false>, bytes, &cur[1]);
+  return raise_smem_limit((const void*)sep_angular_kernel<false>, bytes);
 }
 
 // ---------------------------------------------------------------------------

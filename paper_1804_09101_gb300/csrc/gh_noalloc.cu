@@ -59,6 +59,7 @@ extern "C" gh_status gh_rhs_noalloc(gh_domain* d, const double* u, double* dudt)
              std::to_string(kMaxState) + " doubles); use gh_rhs";
     return GH_EINVAL;
   }
+  if (gh_status s = gh::check_latched(d)) return s;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess && dev != d->device) {

@@ -809,8 +809,7 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
   d->tf_rows = nr;
   d->tf_smem = smem;
   d->tf_spin_threads = max_items >= 4 * TF_SPIN_MAX_THREADS ? TF_SPIN_MAX_THREADS : TF_SPIN_MAX_THREADS / 2;
-  static size_t spin_smem = 0;
-  if ((e = raise_smem_limit((const void*)tf_spin_kernel, smem, &spin_smem)) != cudaSuccess) return e;
+  if ((e = raise_smem_limit((const void*)tf_spin_kernel, smem)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(ShellDev) * d->shells_h.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
