@@ -29,6 +29,8 @@ Modules
   frame       rotating dual frame: SpatialCoordJac and the grid velocity (Sec. 3.1)
   tensor_filter  tensor (spin-weighted) spherical-harmonic truncation on S2 (Secs. 3.1, 3.4)
   perturb     seeded-coefficient perturbations added to the exact data
+  opcount     operation-counting build: gh's pointwise algebra run on
+              symbolic scalars, for the algorithmic flop count per point
 
 Nothing here is blocked, fused or reordered beyond what the definitions
 state: transforms are analysis sums followed by synthesis sums; tensor

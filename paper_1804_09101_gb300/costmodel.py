@@ -117,8 +117,20 @@ def sep_angular_flops(shells, K=None, two=True):
 # (2 x 2,398,144 + 53,760 + 587,328 warp instructions x 32 lanes / 43,008
 # points).
 POINTWISE_EXECUTED_FLOPS_PER_POINT = 4046
-POINTWISE_FLOPS_PER_POINT = POINTWISE_EXECUTED_FLOPS_PER_POINT
-POINTWISE_FLOPS_SOURCE = "executed FP64 instructions (ncu DFMA/DADD/DMUL), 4-shell Kerr workload"
+
+# Algorithmic FP64 flops per point of one launch of the fused pointwise stage,
+# independent of the kernel: the GH right-hand side as the equations define it
+# (Sec. 3.5, GHEqns), counted by running the oracle's pointwise algebra on
+# operation-counting scalars (common subexpressions and symmetric pairs
+# shared, each einsum contracted in numpy's optimal pairwise order, negation
+# free), plus DiffJac (Eq. DiffJac: 8 nonzero Jacobian entries, 13 flops per
+# field) and a quarter of the RK4 step's 13 combination flops per value.
+# Written by the counting build into the test suite's golden file, which a
+# CPU test compares with these constants.
+POINTWISE_GH_RHS_FLOPS_PER_POINT = 3694
+POINTWISE_FLOPS_PER_POINT = POINTWISE_GH_RHS_FLOPS_PER_POINT + 650 + 50 * 13 / 4.0     # 4506.5
+POINTWISE_FLOPS_SOURCE = ("algorithmic: the GH equations counted on the oracle's pointwise algebra (3,694 per "
+                          "point) + DiffJac (650) + RK4 stage combinations (162.5); the kernel executes 4,046")
 
 
 def fold_angular_flops(shells, K=None, two=True):

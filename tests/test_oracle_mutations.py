@@ -188,6 +188,14 @@ CASES = {
         "frame", 'np.einsum("ij,ab,...jb->...ia", R, L, dH)', 'np.einsum("ji,ab,...jb->...ia", R, L, dH)',
         "frame::test_rotating_exact_solution_matches_its_time_derivative",
         [(1.0, 0.0, (0.3, -0.5, 0.8)), (1.0, 0.7, (0.0, 0.0, 1.0))]),
+    # time-integrated constraint energy (oracle/evolve.py, R13)
+    "constraint energy summed from the initial state": (
+        "evolve", "u = rk4_step(dom, u, dt)\n        _, norms = constraints(dom, u)",
+        "_, norms = constraints(dom, u)\n        u = rk4_step(dom, u, dt)",
+        "test_constraint_energy_sums_the_rk4_decay_of_a_violation_on_flat_space", ()),
+    "constraint energy without the step size": (
+        "evolve", "E += dt * sum(norms)", "E += sum(norms)",
+        "test_constraint_energy_sums_the_rk4_decay_of_a_violation_on_flat_space", ()),
     # constraint-preserving outer condition (oracle/gh.py)
     "constraint-preserving correction sign": (
         "gh", "wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)",

@@ -535,6 +535,42 @@ def test_domain_boundaries_touch_only_boundary_slices_and_upwind_by_side():
         assert np.abs(np.where(ext < 0, wout[q], 0.0)).max() < 1e-12, q
 
 
+# ------------------------------------------------- constraint energy (R13)
+def test_constraint_energy_sums_the_rk4_decay_of_a_violation_on_flat_space():
+    """E = sum_{n=1..N} dt sum_shells int sum_c C_c^2 dV on a closed form.
+
+    Flat space (M = 0: alpha = 1, beta = 0, H = 0) with a small violation
+    Phi_x,yz = delta exp(-((R - 6)/w)^2) and nothing else.  The linear GH
+    system gives, already at the semi-discrete level, d_t C_iab = -gamma2
+    C_iab and d_t C_ijab = -gamma2 C_ijab: both are linear in the state and
+    the derivative maps cancel (C_iab exactly, C_ijab up to the commutator of
+    the discrete derivatives, small on a resolved bump).  The gauge
+    constraint starts at zero (the violation has no trace part and no time
+    component) and grows only like t^2 (d_t Pi_yz = -d_x Phi_x,yz feeds
+    Phi_y,yz and Phi_z,yz, whose trace enters Gamma_z), so its share of E is
+    of order t^4: about 1e-8 over this run of t = 0.02.  The bump is four
+    widths inside both boundaries, so no boundary condition acts.  Classic
+    RK4 multiplies each decaying mode by R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24
+    per step, z = -gamma2 dt, so with E_0 the integrated squared constraints
+    of the initial state, E = dt E_0 sum_{n=1..N} R(z)^(2n).  Summing from
+    n = 0 instead misses by 0.4 %, dropping dt by a factor 500."""
+    dom = evolve.Domain([(2.0, 10.0, 33, 3)], 0.0, 0.0, 1.0, -1.0, 1.0)
+    g = dom.grids[0]
+    X, Y, Z = grid.cartesian_coords(g)
+    R = np.sqrt(X * X + Y * Y + Z * Z)
+    u = dom.u_exact[0].copy()
+    assert np.abs(u[:, 10:]).max() == 0.0                     # flat: Pi = Phi = 0
+    u[:, 20 + gh.PAIRS.index((2, 3))] += 1e-8 * np.exp(-((R - 6.0) / 1.0) ** 2)
+    cs, n0 = evolve.constraints(dom, [u])
+    assert np.abs(cs[0][:, 0:4]).max() == 0.0 and n0[0] > 0.0
+    dt, N = 0.002, 10
+    z = -dom.gamma2 * dt
+    Rz = 1.0 + z + z * z / 2.0 + z ** 3 / 6.0 + z ** 4 / 24.0
+    want = dt * n0[0] * sum(Rz ** (2 * n) for n in range(1, N + 1))
+    E = evolve.constraint_energy(dom, [u], dt, N)
+    assert abs(E - want) <= 1e-7 * want, (E, want)
+
+
 # ------------------------------------------------------------------ RK4
 def test_rk4_matches_stability_polynomial(monkeypatch):
     lam = -0.7 + 0.3j
