@@ -7,7 +7,7 @@ import torch
 
 from oracle import evolve
 from paper_1804_09101_gb300 import workloads
-from parity_helpers import REL_TOL, flat, to_dev, to_host
+from parity_helpers import REL_TOL, assert_output_parity, flat, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -179,7 +179,10 @@ def test_full_size_batched_workload_sampled_holes_match_oracle():
     oracle run on each of those holes alone."""
     from paper_1804_09101_gb300 import gh
     w = workloads.batched_workload(64)
-    w.noise_amp = 1e-6
+    # noise of 1e-4 keeps every hole's right-hand side far above rounding
+    # (the best-resolved holes' exact-data right-hand side is below 1e-6), so
+    # the output-relative bar means something
+    w.noise_amp = 1e-4
     odoms = [evolve.Domain([(h["r_in"], h["r_out"], h["n_r"], h["L"])], h["M"], h["chi"], w.gamma0, w.gamma1,
                            w.gamma2, w.filt_alpha, w.filt_order, True, (2 * h["L"]) // 3) for h in w.holes]
     u_host = np.concatenate([flat(od.u_exact) for od in odoms]) + w.noise()
@@ -207,5 +210,5 @@ def test_full_size_batched_workload_sampled_holes_match_oracle():
         sl = slice(offs[b], offs[b + 1])
         ub = [u_host[sl].reshape(od.shapes()[0])]
         scale = np.abs(u_host[sl]).max()
-        assert np.abs(k_host[sl] - flat(evolve.rhs(od, ub))).max() <= REL_TOL * scale, (b, h)
+        assert_output_parity(k_host[sl], flat(evolve.rhs(od, ub)), scale, (b, h))
         assert np.abs(u1[sl] - flat(evolve.rk4_step(od, ub, h["dt"]))).max() <= REL_TOL * scale, (b, h)

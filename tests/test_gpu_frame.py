@@ -12,7 +12,7 @@ import torch
 from oracle import dp5 as odp5
 from oracle import frame
 from paper_1804_09101_gb300 import workloads
-from parity_helpers import REL_TOL, flat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
+from parity_helpers import REL_TOL, assert_output_parity, flat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,7 @@ def test_rhs_matches_oracle_at_a_given_time(case):
     gh.gh_rhs(dom, u, k)
     ref = flat(frame.rhs(odom, u0, 1.7, axis, omega))
     scale = np.abs(flat(u0)).max()
-    assert np.abs(to_host(k) - ref).max() <= REL_TOL * scale
+    assert_output_parity(to_host(k), ref, scale, "rhs")
     # and it is not the static right-hand side
     from oracle import evolve
     assert np.abs(flat(evolve.rhs(odom, u0)) - ref).max() > 1e3 * REL_TOL * scale

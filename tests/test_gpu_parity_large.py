@@ -21,7 +21,7 @@ import torch
 from oracle import gh as ogh
 from oracle import spectral
 from paper_1804_09101_gb300 import workloads
-from parity_helpers import REL_TOL, flat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
+from parity_helpers import REL_TOL, OUT_TOL, flat, to_dev, to_host, oracle_domain, oracle_initial_state, gpu_domain
 
 pytestmark = pytest.mark.gpu
 
@@ -80,7 +80,7 @@ def _check_sampled_rhs(w, odom, u0, n_interior=6, n_boundary=2, seed=2025):
         idx = offs[s] + ((ir * 50 + np.arange(50)) * nth + j) * nph + kk
         return got[idx]
 
-    n_cmp, worst = 0, 0.0
+    n_cmp, worst, d_max, ref_max = 0, 0.0, 0.0, 0.0
     ns = len(odom.grids)
     for s in range(ns):
         n_r, _, nth, nph = odom.shapes()[s]
@@ -90,6 +90,7 @@ def _check_sampled_rhs(w, odom, u0, n_interior=6, n_boundary=2, seed=2025):
             ref = _interior_rhs_at(odom, u0, s, ir, j, kk, jac)
             err = np.abs(gpu_at(s, ir, j, kk) - ref).max() / scale
             worst = max(worst, err)
+            ref_max = max(ref_max, float(np.abs(ref).max()))
             n_cmp += 1
         # the boundary slice at r_out: an interface with shell s + 1, or the outer boundary
         for _ in range(n_boundary):
@@ -101,12 +102,16 @@ def _check_sampled_rhs(w, odom, u0, n_interior=6, n_boundary=2, seed=2025):
                 na, nb = ogh.apply_interface_bc(a[None, None], b[None, None], bg, odom.gamma1, odom.gamma2)
                 err = max(np.abs(gpu_at(s, n_r - 1, j, kk) - na[0, 0]).max(),
                           np.abs(gpu_at(s + 1, 0, j, kk) - nb[0, 0]).max()) / scale
+                ref_max = max(ref_max, float(np.abs(na).max()), float(np.abs(nb).max()))
             else:
                 new = ogh.apply_outer_bc(a[None, None], bg, odom.gamma1, odom.gamma2)
                 err = np.abs(gpu_at(s, n_r - 1, j, kk) - new[0, 0]).max() / scale
+                ref_max = max(ref_max, float(np.abs(new).max()))
             worst = max(worst, err)
             n_cmp += 1
     assert worst < REL_TOL, worst
+    # and relative to the right-hand side's own size at the sampled points
+    assert worst * scale <= OUT_TOL * ref_max, (worst * scale, ref_max)
     return n_cmp
 
 
