@@ -11,9 +11,11 @@ analysis of the point's (r, field) slices and the synthesis of the
 derivative harmonics at the point, the DiffJac contraction, the pointwise GH
 algebra, and at boundary points the oracle's characteristic conditions
 (interface upwinding from both shells' interior values, outer freezing).
-The RK4 step at this size is checked by a property that holds at any size:
-it equals u + dt/6 (k1 + 2 k2 + 2 k3 + k4) built from gh_rhs calls, followed
-by the filters."""
+The RK4 step at this size is checked by a property that holds at any size
+(it equals u + dt/6 (k1 + 2 k2 + 2 k3 + k4) built from gh_rhs calls, followed
+by the filters) and against the oracle's own RK4 step at every point, with
+the oracle's per-shell work spread over worker processes (one shell per
+task)."""
 import numpy as np
 import pytest
 import torch
@@ -157,3 +159,31 @@ def test_rk4_step_is_the_composition_of_its_parts_full_size(large):
     torch.cuda.synchronize()
     err = float((step - ref).abs().max()) / float(u.abs().max())
     assert err < REL_TOL, err
+
+
+def test_rk4_step_full_size_matches_the_oracle_step(large, monkeypatch):
+    """One gh_rk4_step of the large workload (8 shells, N_r = 41, L = 31, with
+    its radial and SH filters), in the launch configuration the benchmark
+    times, against the oracle's rk4_step at every one of the 33.6 M values.
+    The oracle's interior right-hand sides and filters run one shell per
+    worker process; its rk4_step and apply_boundaries are the oracle's own."""
+    from oracle import evolve
+    from oracle_pool import ShellPool
+    from paper_1804_09101_gb300 import gh
+    w, odom, u0 = large
+    dom = gpu_domain(w, odom)
+    gh.gh_autotune(dom, 3)
+    u = to_dev(flat(u0))
+    gh.gh_rk4_step(dom, w.dt, u, dom.new_work())
+    got = to_host(u)
+    del u
+    pool = ShellPool(len(odom.grids))
+    try:
+        pool.install(monkeypatch)
+        ref = flat(evolve.rk4_step(odom, u0, w.dt))
+    finally:
+        pool.close()
+    err = float(np.abs(got - ref).max()) / float(np.abs(flat(u0)).max())
+    assert err < REL_TOL, err
+    # the step moved the state by far more than the tolerance
+    assert float(np.abs(ref - flat(u0)).max()) > 1e4 * REL_TOL * float(np.abs(flat(u0)).max())
