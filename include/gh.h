@@ -237,8 +237,11 @@ gh_status gh_rhs_noalloc(gh_domain* dom, const double* u, double* dudt);
 
 /* ---------------------------------------------------------------- adjoint
  * Vector-Jacobian products of the evolution (reverse-mode derivatives), for
- * gradients of functionals of the evolved state.  They need the separable
- * angular algorithm (GH_ENOTSUP otherwise).  The boundary projection is linear
+ * gradients of functionals of the evolved state.  The angular maps are
+ * transposed with the algorithm the domain uses: the folded separable maps
+ * (the default) with the forward's tables read with input and output
+ * swapped, the plain separable maps with their transposed plans; the dense
+ * traced matrices have no transpose here (GH_ENOTSUP).  The boundary projection is linear
  * in dudt (fixed background) and the filters and derivative maps are linear,
  * so the adjoint is exact up to rounding: transposed boundary conditions, the
  * reverse pass of the pointwise GH algebra, transposed DiffJac, radial and

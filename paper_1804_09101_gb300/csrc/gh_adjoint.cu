@@ -598,6 +598,7 @@ cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {
   d->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (d->algorithm == 2) return gh::launch_fold_adjoint(d, true, d->d_th, d->d_ph, ubar);
   gh::sep_adjoint_kernel<true><<<d->sda_blocks, gh::SEPA_THREADS, d->sda_smem, d->stream>>>(
       d->shells_d, d->n_shells, d->sda_block_begin_d, d->d_th, d->d_ph, ubar);
   d->launches++;
@@ -817,6 +818,8 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
   if (d->params.sh_keep_l != -1) {
     if (d->sh_filter_mode == GH_SH_FILTER_TENSOR) {
       GH_ACUDA(d, gh::launch_tensor_filter_transpose(d, gin, g));
+    } else if (d->algorithm == 2) {
+      GH_ACUDA(d, gh::launch_fold_adjoint(d, false, gin, nullptr, g));
     } else {
       gh::sep_adjoint_kernel<false><<<d->sfa_blocks, gh::SEPA_THREADS, d->sfa_smem, d->stream>>>(
           d->shells_d, d->n_shells, d->sfa_block_begin_d, gin, nullptr, g);

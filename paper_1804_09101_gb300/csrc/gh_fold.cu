@@ -218,10 +218,250 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Exact transpose of fold_angular_kernel (reverse mode).  TWO: out +=
+// Theta^T in0 + Phi^T in1 (the cotangents of d/dtheta and d/dphi); one:
+// out = S^T in0 (the filter).  The forward map of a row is C_o B_o A (analysis
+// A with its ring folding, half-size Legendre maps B_o, synthesis C_o of
+// output o), so the transpose is A^T sum_o B_o^T C_o^T, evaluated in three
+// phases with the same tables and foldings:
+//  * C_o^T is the forward's fold and phase A on each cotangent ring (the
+//    quarter-ring combinations are the transposed four-point outputs);
+//  * B_o^T reads the Legendre tables with input and output swapped, the
+//    output parity (and the d/dphi slot map) now combining the mirrored rings
+//    of the cotangent before the map, the symmetric/antisymmetric split after;
+//  * A^T is the forward's phase C on the per-ring coefficient cotangents.
+// Shared memory per row: region 1 (the cotangent ring and its folds, later the
+// parity-combined coefficients) and CB (the analysed coefficients of both
+// outputs, later the per-ring coefficient cotangents).
+__host__ __device__ inline size_t fold_adj_row_doubles(int na, int nth, int W, int M, int n_out) {
+  const size_t hs2 = 2 * (size_t)((nth + 1) / 2);
+  size_t r1 = (size_t)na + 4 * (size_t)nth * W;
+  if ((size_t)n_out * M * hs2 > r1) r1 = (size_t)n_out * M * hs2;
+  return r1 + (size_t)n_out * nth * M;
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_MAX_THREADS)
+fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                    const double* __restrict__ in0, const double* __restrict__ in1, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  const int nth = sh.nth, nph = sh.nph, na = sh.na;
+  const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = P.W, hs = P.hs, N2 = nph / 2;
+  const bool qself = P.qself != 0;
+  constexpr int NO = TWO ? 2 : 1;
+  const int T = blockDim.x;
+  const int rows = NF * sh.n_r;
+  const int RB = P.adj_rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  size_t r1 = (size_t)na + 4 * (size_t)nth * W;
+  if ((size_t)NO * M * 2 * hs > r1) r1 = (size_t)NO * M * 2 * hs;
+  double* Y = sm;                                   // [RB][na] one output's cotangent rings
+  double* F = Y + (size_t)RB * na;                  // [RB][nth][4][W] their folds
+  double* SV = sm;                                  // [NO][RB][M][2 hs] parity-combined (after Y, F)
+  double* CB = sm + (size_t)RB * r1;                // [NO][RB][nth][M] analysed coefficients
+  double* AB = CB;                                  // [RB][nth][M] coefficient cotangents (after CB)
+  const long long gbase = sh.off + (long long)row0 * na;
+  const unsigned long long sbit = 0x8000000000000000ULL;
+  // phase 1 (C_o^T): fold and analyse every cotangent ring of each output
+#pragma unroll
+  for (int o2 = 0; o2 < NO; ++o2) {
+    const double* in = o2 == 0 ? in0 : in1;
+    if (o2 > 0) __syncthreads();                    // Y and F are reused
+    for (int i = threadIdx.x; i < nr * na; i += T) Y[i] = in[gbase + i];
+    __syncthreads();
+    for (int o = threadIdx.x; o < nr * nth * W; o += T) {
+      const int k = o % W;
+      const int rj = o / W;
+      const double* ring = Y + (size_t)rj * nph;
+      double* f = F + (size_t)rj * 4 * W;
+      auto ev = [&](int kk) { return (kk == 0 || kk == N2) ? ring[kk] : ring[kk] + ring[nph - kk]; };
+      auto od = [&](int kk) { return (kk == 0 || kk == N2) ? 0.0 : ring[kk] - ring[nph - kk]; };
+      if (!(qself && k == N4)) {
+        const double e1 = ev(k), e2 = ev(N2 - k), o1 = od(k), o2v = od(N2 - k);
+        f[k] = e1 + e2;
+        f[W + k] = e1 - e2;
+        f[2 * W + k] = o1 + o2v;
+        f[3 * W + k] = o1 - o2v;
+      } else {
+        f[k] = ev(N4);
+        f[W + k] = 0.0;
+        f[2 * W + k] = od(N4);
+        f[3 * W + k] = 0.0;
+      }
+    }
+    __syncthreads();
+    // one item per (row, ring pair, mode): the coefficients of ring j and of
+    // its mirror share the table loads
+    for (int o = threadIdx.x; o < nr * hs * M; o += T) {
+      const int mode = o % M;
+      const int t = o / M;
+      const int jh = t % hs;
+      const int rr = t / hs;
+      const bool cosm = mode <= K;
+      const int m = cosm ? mode : mode - K;
+      const int q = cosm ? (m % 2 == 0 ? 0 : 1) : (m % 2 == 1 ? 2 : 3);
+      const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
+      const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
+      double* cb = CB + ((size_t)o2 * RB + rr) * nth * M + mode;
+      if (jh < half) {
+        const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
+        double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
+        for (int k = 1; k < W; ++k) {
+          const double tv = __ldg(tab + k);
+          c1 = fma(f1[k], tv, c1);
+          c2 = fma(f2[k], tv, c2);
+        }
+        cb[(size_t)jh * M] = c1;
+        cb[(size_t)(nth - 1 - jh) * M] = c2;
+      } else {
+        double c1 = f1[0] * __ldg(tab);
+        for (int k = 1; k < W; ++k) c1 = fma(f1[k], __ldg(tab + k), c1);
+        cb[(size_t)jh * M] = c1;
+      }
+    }
+  }
+  __syncthreads();
+  // phase 2a: per (output, row, mode, j < hs) the cotangents of the forward's
+  // symmetric and antisymmetric map outputs Sv, Tv (the forward wrote
+  // c[j] = f (Sv + Tv) and c[nth-1-j] = f p (Sv - Tv), f the d/dphi sign, p
+  // the output parity; the equator ring of an odd N_theta only Sv + Tv)
+  for (int o = threadIdx.x; o < NO * nr * M * hs; o += T) {
+    const int j = o % hs;
+    int t = o / hs;
+    const int mode = t % M;
+    t /= M;
+    const int rr = t % nr;
+    const int o2 = TWO ? t / nr : 0;
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    double* sv = SV + (((size_t)o2 * RB + rr) * M + mode) * 2 * hs;
+    int slot = mode;
+    unsigned long long flip = 0ULL;
+    if (TWO && o2 == 1) {
+      if (cosm) {
+        if (m == 0) {                  // the forward wrote a constant zero
+          sv[j] = 0.0;
+          sv[hs + j] = 0.0;
+          continue;
+        }
+        slot = K + m;
+        flip = sbit;
+      } else {
+        slot = m;
+      }
+    }
+    const unsigned long long par = ((o2 == 0 ? P.sigma0 : P.sigma1) < 0.0) ? sbit : 0ULL;
+    const double* cb = CB + ((size_t)o2 * RB + rr) * nth * M + slot;
+    const double y1 = flip_sign(cb[(size_t)j * M], flip);
+    if (j < half) {
+      const double y2 = flip_sign(cb[(size_t)(nth - 1 - j) * M], flip ^ par);
+      sv[j] = y1 + y2;
+      sv[hs + j] = y1 - y2;
+    } else {
+      sv[j] = y1;
+      sv[hs + j] = y1;
+    }
+  }
+  __syncthreads();
+  // phase 2b (B_o^T, summed over outputs, then the transposed split into the
+  // rings j and N_theta-1-j): one item per (row, mode, jp)
+  for (int o = threadIdx.x; o < nr * M * hs; o += T) {
+    const int jp = o % hs;
+    const int t = o / hs;
+    const int mode = t % M;
+    const int rr = t / M;
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    const size_t mo = (size_t)m * hs * hs + (size_t)jp * hs;
+    double sb = 0.0, tb = 0.0;
+#pragma unroll
+    for (int o2 = 0; o2 < NO; ++o2) {
+      const double* Qs = (o2 == 0 ? P.Q0s : P.Q1s) + mo;
+      const double* Qt = (o2 == 0 ? P.Q0t : P.Q1t) + mo;
+      const double* sv = SV + (((size_t)o2 * RB + rr) * M + mode) * 2 * hs;
+      for (int j = 0; j < hs; ++j) {
+        sb = fma(__ldg(Qs + j), sv[j], sb);
+        tb = fma(__ldg(Qt + j), sv[hs + j], tb);
+      }
+    }
+    double* ab = AB + (size_t)rr * nth * M + mode;
+    if (jp < half) {
+      ab[(size_t)jp * M] = sb + tb;
+      ab[(size_t)(nth - 1 - jp) * M] = sb - tb;
+    } else {
+      ab[(size_t)jp * M] = sb;           // the equator's t entry was a constant zero
+    }
+  }
+  __syncthreads();
+  // phase 3 (A^T): the forward's synthesis of four ring points per
+  // quarter-ring sum, from the coefficient cotangents
+  for (int o = threadIdx.x; o < nr * nth * W; o += T) {
+    const int k = o % W;
+    const int rj = o / W;
+    const int rr = rj / nth;
+    const int j = rj - rr * nth;
+    const double* c = AB + (size_t)rj * M;
+    double Ee = c[0] * __ldg(P.Tc + k), Eo = 0.0, Oe = 0.0, Oo = 0.0;
+    for (int m = 1; m <= K; m += 2) {
+      const double tc1 = __ldg(P.Tc + (size_t)m * W + k);
+      const double ts1 = __ldg(P.Ts + (size_t)m * W + k);
+      Eo = fma(c[m], tc1, Eo);
+      Oo = fma(c[K + m], ts1, Oo);
+      if (m + 1 <= K) {
+        const double tc2 = __ldg(P.Tc + (size_t)(m + 1) * W + k);
+        const double ts2 = __ldg(P.Ts + (size_t)(m + 1) * W + k);
+        Ee = fma(c[m + 1], tc2, Ee);
+        Oe = fma(c[K + m + 1], ts2, Oe);
+      }
+    }
+    const double Ek = Ee + Eo, Eh = Ee - Eo, Ok = Oe + Oo, Oh = Oo - Oe;
+    double* dst = out + gbase + (long long)rr * na + (long long)j * nph;
+    auto put = [&](int idx, double v) { dst[idx] = TWO ? dst[idx] + v : v; };
+    if (k == 0) {
+      put(0, Ek + Ok);
+      put(N2, Eh + Oh);
+    } else if (qself && k == N4) {
+      put(N4, Ek + Ok);
+      put(nph - N4, Ek - Ok);
+    } else {
+      put(k, Ek + Ok);
+      put(N2 - k, Eh + Oh);
+      put(N2 + k, Eh - Oh);
+      put(nph - k, Ek - Ok);
+    }
+  }
+}
+
+size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out) {
+  return fold_adj_row_doubles(na, nth, W, M, n_out);
+}
+
+cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const double* in1, double* out) {
+  if (two)
+    fold_adjoint_kernel<true><<<d->fda_blocks, FOLD_ADJ_THREADS, d->fda_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->fda_block_begin_d, in0, in1, out);
+  else
+    fold_adjoint_kernel<false><<<d->ffa_blocks, FOLD_ADJ_THREADS, d->ffa_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->ffa_block_begin_d, in0, nullptr, out);
+  d->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t fold_set_smem_limits(size_t bytes) {
   cudaError_t e = raise_smem_limit((const void*)fold_angular_kernel<true>, bytes);
   if (e != cudaSuccess) return e;
   return raise_smem_limit((const void*)fold_angular_kernel<false>, bytes);
+}
+
+cudaError_t fold_adjoint_set_smem_limits(size_t bytes) {
+  cudaError_t e = raise_smem_limit((const void*)fold_adjoint_kernel<true>, bytes);
+  if (e != cudaSuccess) return e;
+  return raise_smem_limit((const void*)fold_adjoint_kernel<false>, bytes);
 }
 
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {

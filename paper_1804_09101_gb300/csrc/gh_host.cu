@@ -501,10 +501,43 @@ cudaError_t fold_build_maps(gh_domain* d) {
   d->ff_blocks = nff;
   d->fd_smem = smfd;
   d->ff_smem = smff;
+  // transposed maps (reverse mode): a fixed thread count and budget
+  std::vector<int> fa2(n_shells + 1), ffa(n_shells + 1);
+  int nfa = 0, nffa = 0;
+  size_t smfa = 0, smffa = 0;
+  auto adj_rows = [](size_t row_doubles, int n_rows) {
+    int rb = (int)((size_t)gh::FOLD_ADJ_BUDGET / (sizeof(double) * row_doubles));
+    return std::max(1, std::min(std::min(rb, 64), n_rows));
+  };
+  for (int s = 0; s < n_shells; ++s) {
+    gh::ShellDev& sh = d->shells_h[s];
+    const int rows = gh::NF * sh.n_r;
+    const int W = sh.fd.W;
+    const size_t rd = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2);
+    sh.fd.adj_rows_per_cta = adj_rows(rd, rows);
+    fa2[s] = nfa;
+    nfa += (rows + sh.fd.adj_rows_per_cta - 1) / sh.fd.adj_rows_per_cta;
+    smfa = std::max(smfa, sizeof(double) * (size_t)sh.fd.adj_rows_per_cta * rd);
+    ffa[s] = nffa;
+    if (sh.ff.M > 0) {
+      const size_t rf = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1);
+      sh.ff.adj_rows_per_cta = adj_rows(rf, rows);
+      nffa += (rows + sh.ff.adj_rows_per_cta - 1) / sh.ff.adj_rows_per_cta;
+      smffa = std::max(smffa, sizeof(double) * (size_t)sh.ff.adj_rows_per_cta * rf);
+    }
+  }
+  fa2[n_shells] = nfa;
+  ffa[n_shells] = nffa;
+  d->fda_blocks = nfa;
+  d->ffa_blocks = nffa;
+  d->fda_smem = smfa;
+  d->ffa_smem = smffa;
   cudaError_t e;
   if (!d->fd_block_begin_d) {
     if ((e = upload(d, fb2, &d->fd_block_begin_d)) != cudaSuccess) return e;
     if ((e = upload(d, ffb, &d->ff_block_begin_d)) != cudaSuccess) return e;
+    if ((e = upload(d, fa2, &d->fda_block_begin_d)) != cudaSuccess) return e;
+    if ((e = upload(d, ffa, &d->ffa_block_begin_d)) != cudaSuccess) return e;
   } else {
     if ((e = cudaMemcpy(d->fd_block_begin_d, fb2.data(), sizeof(int) * fb2.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(d->ff_block_begin_d, ffb.data(), sizeof(int) * ffb.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
@@ -512,6 +545,7 @@ cudaError_t fold_build_maps(gh_domain* d) {
   if (d->shells_d &&
       (e = cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(gh::ShellDev) * d->shells_h.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
+  if ((e = gh::fold_adjoint_set_smem_limits(std::max(smfa, smffa))) != cudaSuccess) return e;
   return gh::fold_set_smem_limits(std::max(smfd, smff));
 }
 

@@ -80,6 +80,7 @@ struct FoldPlan {
   int W, hs;                    // quarter-ring points, symmetric half-ring size ceil(N_theta/2)
   int qself;                    // 1 if N_phi % 4 == 0 (the point N_phi/4 is its own mirror)
   int rows_per_cta, two;        // rows per block; 2 outputs (derivatives) or 1 (filter)
+  int adj_rows_per_cta, pad1;   // rows per block of the transposed map (fold_adjoint_kernel)
   const double* Tc;             // [K+1][W] cos(m phi_k)
   const double* Ts;             // [K+1][W] sin(m phi_k)
   // [K+1][hs][hs] (transposed: [m][j_in][j_out]) half-size Legendre maps,
@@ -198,6 +199,9 @@ struct gh_domain {
   int* sd_block_begin_d = nullptr; int sd_blocks = 0; size_t sd_smem = 0;
   int* fd_block_begin_d = nullptr; int fd_blocks = 0; size_t fd_smem = 0;
   int* ff_block_begin_d = nullptr; int ff_blocks = 0; size_t ff_smem = 0;
+  // transposed folded maps (reverse mode): launch maps and shared memory
+  int* fda_block_begin_d = nullptr; int fda_blocks = 0; size_t fda_smem = 0;
+  int* ffa_block_begin_d = nullptr; int ffa_blocks = 0; size_t ffa_smem = 0;
   // folded-map work schedule: threads per block and shared-memory budget per
   // block that sets the rows per block (chosen by gh_autotune, else defaults)
   int fd_threads = 256, ff_threads = 256;
@@ -310,6 +314,13 @@ cudaError_t raise_smem_limit(const void* f, size_t bytes);
 // Host-side fault injection (GH_FAULT=launch): GH_ECUDA before any launch.
 gh_status check_latched(gh_domain* d);
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph);
+// Transposed folded maps (reverse mode): two: out += Theta^T in0 + Phi^T in1;
+// else out = S^T in0 (the SH filter).  Launch maps from fold_build_maps.
+constexpr int FOLD_ADJ_THREADS = 256;
+constexpr int FOLD_ADJ_BUDGET = 72 * 1024;      // shared-memory budget per block (bytes)
+size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out);
+cudaError_t fold_adjoint_set_smem_limits(size_t bytes);
+cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const double* in1, double* out);
 cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out);
 cudaError_t sep_adj_set_smem_limits(size_t bytes);
 cudaError_t launch_pointwise_rhs_from(gh_domain* d, const double* u, const double* dr, const double* dth,

@@ -240,3 +240,62 @@ def test_saved_stage_step_and_vjp_agree_with_the_plain_ones():
     gh.gh_rk4_step_vjp_saved(dom, w.dt, to_dev(u0), stages, v, r3, gh.new_vjp_work(dom), 0.37)
     gh.gh_constraint_energy_vjp(dom, to_dev(u0), 0.37, r2)
     assert np.abs(to_host(r3) - to_host(r2)).max() <= 1e-12 * np.abs(to_host(r2)).max()
+
+
+def _fold_case(name):
+    if name == "schwarzschild":
+        return workloads.schwarzschild_single_shell()
+    if name == "kerr2":
+        return _kerr2()
+    if name == "even_L":
+        # even L: odd N_theta (an equator ring) and N_phi % 4 == 2 (no quarter point)
+        return workloads.Workload(name="even_L", shells=[(1.6, 3.0, 7, 6), (3.0, 5.0, 7, 6)], M=1.0, chi=0.4,
+                                  radial_filter_on=True, sh_keep_l=4, dt=0.005, seed=21, noise_amp=1e-7)
+    # three shells of 288 angular points and a filter keeping l <= 7
+    return workloads.Workload(name="ragged", shells=[(1.5, 2.5, 5, 11), (2.5, 4.0, 5, 11), (4.0, 7.0, 5, 11)],
+                              M=1.0, chi=0.5, radial_filter_on=True, sh_keep_l=7, dt=0.005, seed=9, noise_amp=1e-7)
+
+
+@pytest.mark.parametrize("wname", ["schwarzschild", "kerr2", "even_L", "ragged"])
+def test_folded_transposes_equal_the_separable_ones(wname):
+    """The reverse mode with the folded angular maps (the default) and with the
+    plain separable transposes applies the same linear maps, so gh_rhs_vjp and
+    the RK4 step's VJP (filters included) agree to rounding."""
+    from paper_1804_09101_gb300 import gh
+    w = _fold_case(wname)
+    odom = oracle_domain(w)
+    u0 = flat(oracle_initial_state(w, odom))
+    dom_f = gpu_domain(w, odom, "folded")
+    dom_s = gpu_domain(w, odom, "separable")
+    rng = np.random.default_rng(71)
+    v = to_dev(rng.standard_normal(u0.shape))
+    u = to_dev(u0)
+    out = []
+    for dom in (dom_f, dom_s):
+        ub = dom.new_state()
+        gh.gh_rhs_vjp(dom, u, v, ub)
+        ub2 = dom.new_state()
+        gh.gh_rk4_step_vjp(dom, w.dt, u, v, ub2, torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda"))
+        out.append((to_host(ub), to_host(ub2)))
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("wname", ["kerr2", "even_L", "ragged"])
+def test_folded_filter_transpose_is_exact(wname):
+    """A step with dt = 0 is the filters alone, so its VJP is F^T:
+    <ybar, F x> = <F^T ybar, x> to rounding, with the folded maps."""
+    from paper_1804_09101_gb300 import gh
+    w = _fold_case(wname)
+    odom = oracle_domain(w)
+    dom = gpu_domain(w, odom, "folded")
+    rng = np.random.default_rng(72)
+    x = rng.standard_normal(dom.state_size)
+    y = rng.standard_normal(dom.state_size)
+    fx = to_dev(x)
+    gh.gh_apply_filters(dom, fx, dom.new_work())
+    fty = dom.new_state()
+    gh.gh_rk4_step_vjp(dom, 0.0, to_dev(x), to_dev(y), fty,
+                       torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda"))
+    lhs, rhs = float(y @ to_host(fx)), float(to_host(fty) @ x)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(y), (lhs, rhs)
