@@ -596,14 +596,22 @@ def extras(args):
         out["secondary"]["batched"] = dict(error=traceback.format_exc(limit=3)[-600:])
     try:
         a = measure_adjoint(args)
-        out["adjoint_over_forward"] = a["adjoint_over_forward"]
+        # the backward pass with its checkpoint recomputation over the forward
+        # evolution; the whole gradient (its own forward included) is
+        # gradient_over_forward
+        out["adjoint_over_forward"] = a["backward_over_forward"]
         out["secondary"]["adjoint"] = dict(
             workload=a["workload"], points=a["points"], evolution_steps=a["evolution_steps"],
             checkpoint_every=a["checkpoint_every"], forward_s=a["forward_s"], gradient_s=a["gradient_s"],
-            adjoint_over_forward=a["adjoint_over_forward"], backward_over_forward=a["backward_over_forward"],
+            gradient_over_forward=a["adjoint_over_forward"], backward_over_forward=a["backward_over_forward"],
+            keep_all_states_backward_over_forward=a["keep_all_states_backward_over_forward"],
             timing=a["timing"])
     except Exception:
         out["secondary"]["adjoint"] = dict(error=traceback.format_exc(limit=3)[-600:])
+    try:
+        out["secondary"]["kerr4_step_vjp"] = measure_step_vjp(args, workloads.kerr_four_shells())
+    except Exception:
+        out["secondary"]["kerr4_step_vjp"] = dict(error=traceback.format_exc(limit=3)[-600:])
     try:
         wk = workloads.kerr_four_shells()
         k4 = measure_rk4(args, wk, None, host_e2e=False, clock_index=None)
@@ -807,6 +815,50 @@ def measure_adjoint(args):
                 timing="wall clock around whole evolutions (host-driven launches), mean of %d repetitions; "
                        "gradient_s includes its own forward pass, backward_over_forward excludes it (backward "
                        "incl. checkpoint recomputation)" % reps)
+
+
+def measure_step_vjp(args, w):
+    """One RK4 step's vector-Jacobian product (stage states recomputed, filters
+    transposed) against the step itself: direct calls, CUDA events, L2
+    flushed before each call."""
+    import torch
+    from paper_1804_09101_gb300 import gh
+    dom = gh.Domain.from_workload(w)
+    if not args.no_autotune:
+        gh.gh_autotune(dom, 5)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    u = make_state(dom, w, dev)
+    work = dom.new_work()
+    vwork = torch.zeros(dom.vjp_work_size, dtype=torch.float64, device=dev)
+    ybar = torch.ones_like(u)
+    ubar = dom.new_state()
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    steps = max(3, args.steps)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    us = u.clone()
+    step_ms = timed(lambda: gh.gh_rk4_step(dom, w.dt, us, work))
+    vjp_ms = timed(lambda: gh.gh_rk4_step_vjp(dom, w.dt, u, ybar, ubar, vwork))
+    gh.gh_sync(dom)
+    return dict(workload=w.name, points=w.points(), step_ms=step_ms, step_vjp_ms=vjp_ms,
+                step_vjp_over_step=vjp_ms / step_ms,
+                how="gh_rk4_step_vjp (recomputes the stage states) against gh_rk4_step, direct calls, "
+                    "CUDA events, L2 flushed before each call")
 
 
 def run_adjoint(args):

@@ -252,8 +252,9 @@ gh_status gh_rhs_vjp(gh_domain* dom, const double* u, const double* kbar, double
 
 /* ubar_n = (d step / d u_n)^T ubar_np1 for step = gh_rk4_step(dom, dt, .) with
  * its filters; u_n is the state the step started from.  Recomputes the stage
- * states.  work: gh_rk4_vjp_work_size doubles (device).  ubar_n must not
- * alias ubar_np1. */
+ * states and keeps their spherical derivatives for the reverse pass.  work:
+ * gh_rk4_vjp_work_size doubles (device; 16 states).  ubar_n must not alias
+ * ubar_np1. */
 long long gh_rk4_vjp_work_size(const gh_domain* dom);
 gh_status gh_rk4_step_vjp(gh_domain* dom, double dt, const double* u_n, const double* ubar_np1,
                           double* ubar_n, double* work);

@@ -350,8 +350,38 @@ __device__ __noinline__ void constraint_part(const PointIn& in, double w, double
   point_constraint_energy(in, w, ub, dsb);
 }
 
+// The reverse pass's per-pair access on global memory at one point (offset
+// base, field stride na): the derivative scratch dr/dth/dph is read and then
+// overwritten with the cotangents of those derivatives, pair by pair; kb is the
+// cotangent of dudt.  Each thread touches only its own point's entries.
+struct GlobalPairIO {
+  double* dr;
+  double* dth;
+  double* dph;
+  const double* kb;
+  long long base;
+  int na;
+  __device__ void load(int p, double ds15[15], double kb5[5]) const {
+    for (int e = 0; e < 5; ++e) {
+      const long long o = base + (long long)(e == 0 ? p : 10 * e + p) * na;
+      ds15[3 * e] = dr[o];
+      ds15[3 * e + 1] = dth[o];
+      ds15[3 * e + 2] = dph[o];
+      kb5[e] = kb[o];
+    }
+  }
+  __device__ void store(int p, const double dsb15[15]) const {
+    for (int e = 0; e < 5; ++e) {
+      const long long o = base + (long long)(e == 0 ? p : 10 * e + p) * na;
+      dr[o] = dsb15[3 * e];
+      dth[o] = dsb15[3 * e + 1];
+      dph[o] = dsb15[3 * e + 2];
+    }
+  }
+};
+
 #ifndef GH_ADJ_MINB
-#define GH_ADJ_MINB 16
+#define GH_ADJ_MINB 12
 #endif
 template <int MODE>
 __global__ void __launch_bounds__(ADJ_PT_THREADS, GH_ADJ_MINB)
@@ -369,6 +399,60 @@ pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, cons
   const int q = (lb - ir * bps) * ADJ_PT_THREADS + threadIdx.x;
   if (q >= na) return;
   const long long base = sh.off + (long long)ir * NF * na + q;
+  if (MODE == 0) {
+    // the plain RHS cotangent: each pair's derivatives, their cotangents and
+    // the output cotangents stream from and to global memory, so the thread
+    // holds only the point's fields and their cotangents
+    double uu[50], ub[50];
+    for (int f = 0; f < NF; ++f) {
+      uu[f] = u[base + (long long)f * na];
+      ub[f] = 0.0;
+    }
+    const double* gsrc = sh.gauge + (long long)ir * NGAUGE * na + q;
+    double H[4], dH[12];
+    for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
+    for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
+    PointGeom G;
+    point_geom(sh, ir, q, G);
+    double vel[3] = {0.0, 0.0, 0.0};
+    if (frd) {
+      const Frame fr = *frd;
+      frame_geom(fr, G, vel);
+      frame_rotate_h(fr, H);
+      frame_rotate_dh(fr, dH);
+    }
+    PointIn in;
+    in.u = uu;
+    in.ds = nullptr;
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 3; ++d) in.J[i][d] = G.J[i][d];
+    in.H = H;
+    in.dH = dH;
+    in.g0 = g0;
+    in.g1 = g1;
+    in.g2 = g2;
+    PointFwd fw;
+    point_intermediates(in, fw);
+    const GlobalPairIO io{dr, dth, dph, kb, base, na};
+    point_rhs_vjp_io(in, fw, io, ub);
+    if (frd && kb0) {
+      // transposed grid-velocity term, as below
+      double vs[3];
+      for (int d = 0; d < 3; ++d) vs[d] = vel[0] * G.J[0][d] + vel[1] * G.J[1][d] + vel[2] * G.J[2][d];
+      for (int f = 0; f < NF; ++f) {
+        const long long o = base + (long long)f * na;
+        const double kv = kb0[o];
+        dr[o] = fma(vs[0], kv, dr[o]);
+        dth[o] = fma(vs[1], kv, dth[o]);
+        dph[o] = fma(vs[2], kv, dph[o]);
+      }
+    }
+    for (int f = 0; f < NF; ++f) {
+      const long long o = base + (long long)f * na;
+      ubar[o] = assign ? ub[f] : ubar[o] + ub[f];
+    }
+    return;
+  }
   double uu[50], ds[150], ub[50], dsb[150];
   for (int f = 0; f < NF; ++f) {
     const long long o = base + (long long)f * na;
@@ -402,7 +486,7 @@ pointwise_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, cons
   in.g0 = g0;
   in.g1 = g1;
   in.g2 = g2;
-  if (MODE == 0 || MODE == 2) {
+  if (MODE == 2) {
     double kk[50];
     for (int f = 0; f < NF; ++f) kk[f] = kb[base + (long long)f * na];
     PointFwd fw;
@@ -590,19 +674,31 @@ cudaError_t ew(gh_domain* d, int mode, double* out, const double* x, const doubl
 // Forward derivatives of u into d_r, d_th, d_ph.
 cudaError_t fwd_derivs(gh_domain* d, const double* u) { return gh::launch_derivatives(d, u); }
 
-// ubar += (transposed derivative maps) applied to the cotangents in d_r, d_th, d_ph.
-cudaError_t derivs_transpose_add(gh_domain* d, double* ubar) {
+// ubar += (transposed derivative maps) applied to the derivative cotangents
+// in D[0] (d/dx), D[1] (d/dtheta), D[2] (d/dphi).
+cudaError_t derivs_transpose_add(gh_domain* d, double* ubar, double* const* D) {
   gh::radial_adjoint_kernel<false, true><<<d->rad_blocks, gh::ADJ_RAD_THREADS,
                                            gh::radial_adjoint_smem_bytes(d->max_n_r), d->stream>>>(
-      d->shells_d, d->n_shells, d->rad_block_begin_d, d->d_r, ubar, d->max_n_r);
+      d->shells_d, d->n_shells, d->rad_block_begin_d, D[0], ubar, d->max_n_r);
   d->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (d->algorithm == 2) return gh::launch_fold_adjoint(d, true, d->d_th, d->d_ph, ubar);
+  if (d->algorithm == 2) return gh::launch_fold_adjoint(d, true, D[1], D[2], ubar);
   gh::sep_adjoint_kernel<true><<<d->sda_blocks, gh::SEPA_THREADS, d->sda_smem, d->stream>>>(
-      d->shells_d, d->n_shells, d->sda_block_begin_d, d->d_th, d->d_ph, ubar);
+      d->shells_d, d->n_shells, d->sda_block_begin_d, D[1], D[2], ubar);
   d->launches++;
   return cudaGetLastError();
+}
+
+// Forward right-hand side k = F(u) with its derivatives written to D[0..2]
+// (which the reverse pass at u can then use instead of recomputing them).
+cudaError_t rhs_fwd_into(gh_domain* d, const double* u, double* k, double* const* D) {
+  cudaError_t e = gh::launch_radial(d, u, D[0], false);
+  if (e == cudaSuccess) e = gh::launch_angular_deriv_into(d, u, D[1], D[2]);
+  if (e == cudaSuccess) e = gh::launch_pointwise_rhs_from(d, u, D[0], D[1], D[2], k);
+  const double* cd[3] = {D[0], D[1], D[2]};
+  if (e == cudaSuccess) e = gh::launch_bc(d, k, 0, 0.0, nullptr, nullptr, nullptr, u, cd);
+  return e;
 }
 
 }  // namespace
@@ -681,9 +777,14 @@ namespace {
 
 // ubar (+)= J(u)^T kb (+ cweight * grad of the constraint energy at u when
 // cweight != 0); assign: overwrite ubar instead of adding; kb is not modified.
+// saved: the spherical derivatives of u already computed (three states,
+// consumed: overwritten with their cotangents); null: computed here into the
+// domain's scratch.
 gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar, double cweight = 0.0,
-                  bool assign = false) {
-  GH_ACUDA(d, fwd_derivs(d, u));
+                  bool assign = false, double* const* saved = nullptr) {
+  double* const scratch[3] = {D[0], D[1], D[2]};
+  double* const* D = saved ? saved : scratch;
+  if (!saved) GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
   const int cp = d->outer_bc == GH_BC_CONSTRAINT_PRESERVING;
   const gh::Frame* frd = d->rot_omega != 0.0 ? d->frd : nullptr;
@@ -705,11 +806,11 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
     const dim3 grid(d->pt_blocks, 10);
     if (cweight != 0.0)
       gh::pointwise_adjoint_pair_kernel<2><<<grid, gh::PAIR_PTS, 0, d->stream>>>(
-          d->shells_d, d->n_shells, d->pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, d->adj_ubp, d->state,
+          d->shells_d, d->n_shells, d->pt_block_begin_d, u, D[0], D[1], D[2], d->kbt, d->adj_ubp, d->state,
           d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight);
     else
       gh::pointwise_adjoint_pair_kernel<0><<<grid, gh::PAIR_PTS, 0, d->stream>>>(
-          d->shells_d, d->n_shells, d->pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, d->adj_ubp, d->state,
+          d->shells_d, d->n_shells, d->pt_block_begin_d, u, D[0], D[1], D[2], d->kbt, d->adj_ubp, d->state,
           d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
@@ -720,23 +821,23 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
   } else {
     if (cweight != 0.0)
       gh::pointwise_adjoint_kernel<2><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
-          d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
+          d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, D[0], D[1], D[2], d->kbt, ubar,
           d->params.gamma0, d->params.gamma1, d->params.gamma2, cweight, assign ? 1 : 0, frd, kb);
     else
       gh::pointwise_adjoint_kernel<0><<<d->adj_pt_blocks, gh::ADJ_PT_THREADS, 0, d->stream>>>(
-          d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, d->d_r, d->d_th, d->d_ph, d->kbt, ubar,
+          d->shells_d, d->n_shells, d->adj_pt_block_begin_d, u, D[0], D[1], D[2], d->kbt, ubar,
           d->params.gamma0, d->params.gamma1, d->params.gamma2, 0.0, assign ? 1 : 0, frd, kb);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
   if (cp && d->bc_points) {
     gh::cp_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
-        d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpbar, d->d_r, d->d_th, d->d_ph, ubar,
+        d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpbar, D[0], D[1], D[2], ubar,
         frd);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
-  GH_ACUDA(d, derivs_transpose_add(d, ubar));
+  GH_ACUDA(d, derivs_transpose_add(d, ubar, D));
   return GH_OK;
 }
 
@@ -752,7 +853,7 @@ gh_status rhs_fwd(gh_domain* d, const double* u, double* k) {
 
 extern "C" {
 
-long long gh_rk4_vjp_work_size(const gh_domain* d) { return d ? 7 * d->state : -1; }
+long long gh_rk4_vjp_work_size(const gh_domain* d) { return d ? 16 * d->state : -1; }
 
 gh_status gh_rhs_vjp(gh_domain* d, const double* u, const double* kbar, double* ubar) {
   if (!d || !u || !kbar || !ubar) return d ? afail(d, GH_EINVAL, "null argument") : GH_EINVAL;
@@ -772,7 +873,8 @@ gh_status gh_constraint_energy_vjp(gh_domain* d, const double* u, double weight,
       d->rot_omega != 0.0 ? d->frd : nullptr, nullptr);
   d->launches++;
   GH_ACUDA(d, cudaGetLastError());
-  GH_ACUDA(d, derivs_transpose_add(d, ubar));
+  double* const D[3] = {d->d_r, d->d_th, d->d_ph};
+  GH_ACUDA(d, derivs_transpose_add(d, ubar, D));
   return GH_OK;
 }
 
@@ -792,6 +894,11 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
   double* kb = work + 4 * N;
   double* g = work + 5 * N;
   double* sb = work + 6 * N;
+  // spherical derivatives of u_n, u2 and u3 kept from the recomputation
+  double* const D1[3] = {work + 7 * N, work + 8 * N, work + 9 * N};
+  double* const D2[3] = {work + 10 * N, work + 11 * N, work + 12 * N};
+  double* const D3[3] = {work + 13 * N, work + 14 * N, work + 15 * N};
+  const bool keep = stages == nullptr;
   if (stages) {
     u2 = stages;
     u3 = stages + N;
@@ -802,12 +909,12 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
     double* w3 = work + N;
     double* w4 = work + 2 * N;
     at(0);
-    if (gh_status s = rhs_fwd(d, u_n, k)) return s;
+    GH_ACUDA(d, rhs_fwd_into(d, u_n, k, D1));
     GH_ACUDA(d, ew(d, 0, w2, u_n, k, 0.0, 0.5, dt));
     at(1);
-    if (gh_status s = rhs_fwd(d, w2, k)) return s;
+    GH_ACUDA(d, rhs_fwd_into(d, w2, k, D2));
     GH_ACUDA(d, ew(d, 0, w3, u_n, k, 0.0, 0.5, dt));
-    if (gh_status s = rhs_fwd(d, w3, k)) return s;
+    GH_ACUDA(d, rhs_fwd_into(d, w3, k, D3));
     GH_ACUDA(d, ew(d, 0, w4, u_n, k, 0.0, 1.0, dt));
     u2 = w2;
     u3 = w3;
@@ -846,12 +953,12 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
   if (gh_status s = rhs_vjp(d, u4, kb, sb, 0.0, true)) return s;       // sb = J(u4)^T kb4
   GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 3.0, 1.0, dt, ubar_n));        // kb3 = dt (g/3 + sb); ubar_n += sb
   at(1);
-  if (gh_status s = rhs_vjp(d, u3, kb, sb, 0.0, true)) return s;
+  if (gh_status s = rhs_vjp(d, u3, kb, sb, 0.0, true, keep ? D3 : nullptr)) return s;
   GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 3.0, 0.5, dt, ubar_n));        // kb2 = dt (g/3 + sb/2)
-  if (gh_status s = rhs_vjp(d, u2, kb, sb, 0.0, true)) return s;
+  if (gh_status s = rhs_vjp(d, u2, kb, sb, 0.0, true, keep ? D2 : nullptr)) return s;
   GH_ACUDA(d, ew(d, 3, kb, g, sb, 1.0 / 6.0, 0.5, dt, ubar_n));        // kb1 = dt (g/6 + sb/2)
   at(0);
-  return rhs_vjp(d, u_n, kb, ubar_n, cweight);
+  return rhs_vjp(d, u_n, kb, ubar_n, cweight, false, keep ? D1 : nullptr);
 }
 
 }  // namespace

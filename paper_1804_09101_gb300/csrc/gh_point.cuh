@@ -300,11 +300,37 @@ GH_HD inline void gamma_split_reverse(const double psi[10], const double Pi[10],
     }
 }
 
-// Reverse pass: given kb[50] (cotangent of dudt), adds the cotangents of the
-// point's fields to ub[50] and of its spherical derivatives to dsb[150].
-// f must hold the intermediates of point_rhs for the same inputs.
-GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const double kb[50], double ub[50],
-                                double dsb[150]) {
+// Access of the reverse pass to one symmetric pair's entries: the spherical
+// derivatives ds15 and the output cotangents kb5 of its five fields (psi_p,
+// Pi_p, Phi_xp, Phi_yp, Phi_zp), and the cotangents dsb15 of those
+// derivatives.  The pass reads and writes pair p's entries only while it
+// handles pair p, so they need not be held for the whole point.
+// ArrayPairIO: whole-point arrays ds[150], kb[50], dsb[150] (dsb is added to).
+struct ArrayPairIO {
+  const double* ds;
+  const double* kb;
+  double* dsb;
+  GH_HD void load(int p, double ds15[15], double kb5[5]) const {
+    for (int e = 0; e < 5; ++e) {
+      const int fi = e == 0 ? p : 10 * e + p;
+      for (int d = 0; d < 3; ++d) ds15[3 * e + d] = ds[3 * fi + d];
+      kb5[e] = kb[fi];
+    }
+  }
+  GH_HD void store(int p, const double dsb15[15]) const {
+    for (int e = 0; e < 5; ++e) {
+      const int fi = e == 0 ? p : 10 * e + p;
+      for (int d = 0; d < 3; ++d) dsb[3 * fi + d] += dsb15[3 * e + d];
+    }
+  }
+};
+
+// Reverse pass: given the cotangent kb of dudt (through io), adds the
+// cotangents of the point's fields to ub[50] and hands those of its spherical
+// derivatives to io.store, pair by pair.  f must hold the intermediates of
+// point_rhs for the same inputs.
+template <class IO>
+GH_HD inline void point_rhs_vjp_io(const PointIn& in, const PointFwd& f, const IO& io, double ub[50]) {
   const double* psi = in.u;
   const double* Pi = in.u + 10;
   const double* Phi = in.u + 20;
@@ -338,11 +364,14 @@ GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const doub
 
   for (int p = 0; p < 10; ++p) {
     const int A = pair_a(p), B = pair_b(p);
-    const double kpsi = kb[p], kPi = kb[10 + p];
-    const double* dpsi = in.ds + 3 * p;
-    const double* dPi = in.ds + 3 * (10 + p);
-    double* dpsib = dsb + 3 * p;
-    double* dPib = dsb + 3 * (10 + p);
+    double ds15[15], kb5[5], dsb15[15];
+    io.load(p, ds15, kb5);
+    for (int e = 0; e < 15; ++e) dsb15[e] = 0.0;
+    const double kpsi = kb5[0], kPi = kb5[1];
+    const double* dpsi = ds15;
+    const double* dPi = ds15 + 3;
+    double* dpsib = dsb15;
+    double* dPib = dsb15 + 3;
     // ---- recompute the per-pair forward scalars needed below
     double T1 = 0.0, T2 = 0.0, T3 = 0.0;
     for (int j = 0; j < 3; ++j)
@@ -369,7 +398,7 @@ GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const doub
     }
     double gdPhi = 0.0;
     for (int i = 0; i < 3; ++i) {
-      const double* dPhi = in.ds + 3 * (20 + 10 * i + p);
+      const double* dPhi = ds15 + 3 * (2 + i);
       gdPhi += f.Gs[i][0] * dPhi[0] + f.Gs[i][1] * dPhi[1] + f.Gs[i][2] * dPhi[2];
     }
     // ---- out[p] = (1+g1) bdpsi - al Pi_p - g1 bPhi
@@ -386,9 +415,9 @@ GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const doub
     // ---- out[20+10i+p]
     double cpsib[3], cPib[3];
     for (int i = 0; i < 3; ++i) {
-      const double kPhi = kb[20 + 10 * i + p];
-      const double* dPhi = in.ds + 3 * (20 + 10 * i + p);
-      double* dPhib = dsb + 3 * (20 + 10 * i + p);
+      const double kPhi = kb5[2 + i];
+      const double* dPhi = ds15 + 3 * (2 + i);
+      double* dPhib = dsb15 + 3 * (2 + i);
       const double cpsi = in.J[i][0] * dpsi[0] + in.J[i][1] * dpsi[1] + in.J[i][2] * dpsi[2];
       const double cPi = in.J[i][0] * dPi[0] + in.J[i][1] * dPi[1] + in.J[i][2] * dPi[2];
       // bdPhi = bs . dPhi
@@ -424,8 +453,8 @@ GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const doub
     }
     // gdPhi = sum_i Gs[i] . dPhi_i
     for (int i = 0; i < 3; ++i) {
-      const double* dPhi = in.ds + 3 * (20 + 10 * i + p);
-      double* dPhib = dsb + 3 * (20 + 10 * i + p);
+      const double* dPhi = ds15 + 3 * (2 + i);
+      double* dPhib = dsb15 + 3 * (2 + i);
       for (int dd = 0; dd < 3; ++dd) {
         dPhib[dd] += f.Gs[i][dd] * gdPhib;
         Gsb[i][dd] += dPhi[dd] * gdPhib;
@@ -483,6 +512,7 @@ GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const doub
       Phib[j * 10 + p] += f.tPig[j] * tPiPhib + S.beta_up[j] * bPhib;
       betab[j] += Phi[j * 10 + p] * bPhib;
     }
+    io.store(p, dsb15);
   }
   // ---- bs[d] = sum_k beta^k J[k][d] ; Gs[i][d] = sum_k ginv(k,i) J[k][d]
   for (int dd = 0; dd < 3; ++dd) {
@@ -560,6 +590,13 @@ GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const doub
     Cb[c] += S.t_up[c] * tCb;
   }
   gamma_split_reverse(psi, Pi, Phi, S, f.Gam, Cb, Gamb, alb, betab, ginvb, tb, pinvb, psib, Pib, Phib);
+}
+
+// The reverse pass on whole-point arrays: kb[50], adds to ub[50] and dsb[150].
+GH_HD inline void point_rhs_vjp(const PointIn& in, const PointFwd& f, const double kb[50], double ub[50],
+                                double dsb[150]) {
+  ArrayPairIO io{in.ds, kb, dsb};
+  point_rhs_vjp_io(in, f, io, ub);
 }
 
 // Constraint energy density at a point, e = sum of the 64 squared stored

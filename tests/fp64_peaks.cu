@@ -135,6 +135,37 @@ __global__ void hmma_bf16_m16n8k16_kernel(double* out, int iters, float x) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// DMMA and DFMA in the same warps: 2 m16n8k8 mma.sync (4,096 flops per warp)
+// and 32 DFMAs per thread (2,048 flops per warp) per loop iteration.  If the
+// two share the FP64 units the combined rate stays near either alone; if
+// they are separate pipes it approaches their sum.
+__global__ void mixed_dmma_dfma_kernel(double* out, int iters, double x) {
+  double acc[2][4];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const double a0 = x + threadIdx.x, a1 = x * 0.5, a2 = x * 0.25, a3 = x * 0.125;
+  const double b0 = x - threadIdx.x, b1 = x * 2.0;
+  double f[CHAINS];
+  for (int i = 0; i < CHAINS; ++i) f[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      asm volatile(
+          "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};\n"
+          : "+d"(acc[i][0]), "+d"(acc[i][1]), "+d"(acc[i][2]), "+d"(acc[i][3])
+          : "d"(a0), "d"(a1), "d"(a2), "d"(a3), "d"(b0), "d"(b1));
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < CHAINS; ++i) f[i] = fma(f[i], 0.999999, 1e-7);
+  }
+  double s = 0.0;
+  for (int i = 0; i < 2; ++i) s += acc[i][0] + acc[i][1] + acc[i][2] + acc[i][3];
+  for (int i = 0; i < CHAINS; ++i) s += f[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <typename Launch>
 void run(const char* name, double flops_per_warp_iter, int iters, int blocks, double* out, Launch launch) {
   cudaEvent_t a, b;
@@ -181,6 +212,8 @@ int main() {
       [&](int it) { dmma_m16n8k8_kernel<<<blocks, THREADS>>>(out, it, 1e-3); });
   run("dmma_m16n8k16_f64", 4 * 2.0 * 16 * 8 * 16, 2500, blocks, out,
       [&](int it) { dmma_m16n8k16_kernel<<<blocks, THREADS>>>(out, it, 1e-3); });
+  run("mixed_dmma_m16n8k8_and_dfma", 2 * 2.0 * 16 * 8 * 8 + 4 * CHAINS * 2.0 * 32, 5000, blocks, out,
+      [&](int it) { mixed_dmma_dfma_kernel<<<blocks, THREADS>>>(out, it, 1e-3); });
   run("hmma_bf16_m16n8k16_f32acc", 4 * 2.0 * 16 * 8 * 16, 20000, blocks, out,
       [&](int it) { hmma_bf16_m16n8k16_kernel<<<blocks, THREADS>>>(out, it, 1e-3f); });
   CK(cudaFree(out));

@@ -284,10 +284,13 @@ def test_folded_transposes_equal_the_separable_ones(wname):
 @pytest.mark.parametrize("wname", ["kerr2", "even_L", "ragged"])
 def test_folded_filter_transpose_is_exact(wname):
     """A step with dt = 0 is the filters alone, so its VJP is F^T:
-    <ybar, F x> = <F^T ybar, x> to rounding, with the folded maps."""
+    <ybar, F x> = <F^T ybar, x> to rounding, with the folded maps.  The step
+    VJP is taken at a physical state (it re-evaluates the right-hand side
+    there, with weight dt = 0); x and ybar are random."""
     from paper_1804_09101_gb300 import gh
     w = _fold_case(wname)
     odom = oracle_domain(w)
+    u0 = flat(oracle_initial_state(w, odom))
     dom = gpu_domain(w, odom, "folded")
     rng = np.random.default_rng(72)
     x = rng.standard_normal(dom.state_size)
@@ -295,7 +298,7 @@ def test_folded_filter_transpose_is_exact(wname):
     fx = to_dev(x)
     gh.gh_apply_filters(dom, fx, dom.new_work())
     fty = dom.new_state()
-    gh.gh_rk4_step_vjp(dom, 0.0, to_dev(x), to_dev(y), fty,
+    gh.gh_rk4_step_vjp(dom, 0.0, to_dev(u0), to_dev(y), fty,
                        torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda"))
     lhs, rhs = float(y @ to_host(fx)), float(to_host(fty) @ x)
     assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(y), (lhs, rhs)
