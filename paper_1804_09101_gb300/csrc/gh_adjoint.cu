@@ -782,7 +782,7 @@ namespace {
 // domain's scratch.
 gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar, double cweight = 0.0,
                   bool assign = false, double* const* saved = nullptr) {
-  double* const scratch[3] = {D[0], D[1], D[2]};
+  double* const scratch[3] = {d->d_r, d->d_th, d->d_ph};
   double* const* D = saved ? saved : scratch;
   if (!saved) GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
