@@ -316,8 +316,14 @@ gh_status check_latched(gh_domain* d);
 cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph);
 // Transposed folded maps (reverse mode): two: out += Theta^T in0 + Phi^T in1;
 // else out = S^T in0 (the SH filter).  Launch maps from fold_build_maps.
-constexpr int FOLD_ADJ_THREADS = 256;
-constexpr int FOLD_ADJ_BUDGET = 72 * 1024;      // shared-memory budget per block (bytes)
+#ifndef GH_FOLD_ADJ_THREADS
+#define GH_FOLD_ADJ_THREADS 256
+#endif
+#ifndef GH_FOLD_ADJ_BUDGET
+#define GH_FOLD_ADJ_BUDGET (72 * 1024)
+#endif
+constexpr int FOLD_ADJ_THREADS = GH_FOLD_ADJ_THREADS;
+constexpr int FOLD_ADJ_BUDGET = GH_FOLD_ADJ_BUDGET;   // shared-memory budget per block (bytes)
 size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out);
 cudaError_t fold_adjoint_set_smem_limits(size_t bytes);
 cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const double* in1, double* out);
