@@ -139,36 +139,16 @@ def fold_angular_flops(shells, K=None, two=True):
     (hs - half) M 2 W for an odd N_theta's equator ring; phase B
     n_out M hs (4 hs + 5); phase C n_out N_theta W (2 M + 8), with
     W = N_phi/4 + 1 (N_phi % 4 == 0) or (N_phi + 2)/4, half = floor(N_theta/2),
-    hs = ceil(N_theta/2), M = 2K+1.
-
-    With N_phi % 8 == 0 the even modes are folded once more (k <-> N_phi/4 - k):
-    the fold adds 4 N_phi/8 per ring, an even mode's coefficient takes
-    N_phi/8 + 1 taps instead of W, and phase C takes, per (output, ring), the
-    K + 1 even-mode products once at each k <= N_phi/8 and the odd-mode ones
-    at k and N_phi/4 - k, with 8 flops of output combinations per point group
-    and 2 (4 when k < N_phi/8) to split the even sums."""
+    hs = ceil(N_theta/2), M = 2K+1."""
     f = 0
     n_out = 2 if two else 1
     for sh in shells:
         n_r, nth, nph, na = _shell_dims(sh)
-        Kk = _keep(sh, K)
-        M = 2 * Kk + 1
+        M = 2 * _keep(sh, K) + 1
         W = nph // 4 + 1 if nph % 4 == 0 else (nph + 2) // 4
         half, hs = nth // 2, (nth + 1) // 2
-        phase_b = n_out * M * hs * (4 * hs + 5)
-        if nph % 8 == 0 and nph >= 16:
-            N8 = nph // 8
-            n_even = Kk + 1                       # cos m even in 0..K, sin m even in 2..K
-            n_odd = M - n_even
-            fold = (8 * (W - 1) + 4 * N8) * nth
-            phase_a = (half * (n_even * (4 * (N8 + 1) + 2) + n_odd * (4 * W + 2))
-                       + (hs - half) * (n_even * 2 * (N8 + 1) + n_odd * 2 * W))
-            per_ring_c = sum(2 * n_even + (2 * n_odd + 8 + 2) * (2 if k < N8 else 1) for k in range(N8 + 1))
-            phase_c = n_out * nth * per_ring_c
-            per_row = fold + phase_a + phase_b + phase_c
-        else:
-            per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W
-                       + phase_b + n_out * nth * W * (2 * M + 8))
+        per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W
+                   + n_out * M * hs * (4 * hs + 5) + n_out * nth * W * (2 * M + 8))
         f += 50 * n_r * per_row
     return f
 

@@ -52,74 +52,33 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   const int RB = P.rows_per_cta;
   const int row0 = (blockIdx.x - begin[s]) * RB;
   const int nr = min(RB, rows - row0);
-  const int WF = W + 1;                             // stride of a fold class in F
-  const bool e8 = P.e8 != 0;
-  const int N8 = N4 / 2;
-  const int r1 = max(na + 4 * nth * WF, NO * nth * M);
+  const int r1 = max(na + 4 * nth * W, NO * nth * M);
   double* U = sm;                                   // [RB][na]
-  double* F = U + (size_t)RB * na;                  // [RB][nth][4][WF]
+  double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
   double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
   double* AB = sm + (size_t)RB * r1;                // [RB][M][2 hs]: s (hs) then t (hs)
   const long long gbase = sh.off + (long long)row0 * na;
   for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
   __syncthreads();
   // fold every ring: Cp, Cm (cos, even / odd m), Sp, Sm (sin, odd / even m)
-  // at the quarter-ring points k = 0..W-1.  With e8 (N_phi % 8 == 0) the even
-  // classes are folded once more under k <-> N/4 - k: cos(m phi) keeps its sign
-  // there for m = 0 mod 4 and flips it for m = 2 mod 4, sin(m phi) the other
-  // way round, so class 0 holds Cp[k] + Cp[N/4-k] then Cp[k] - Cp[N/4-k]
-  // (k = 0..N/8, the middle point once in both) and class 3 Sm[k] - Sm[N/4-k]
-  // then Sm[k] + Sm[N/4-k]: the even modes' coefficients become dot products of
-  // length N/8 + 1 instead of N/4 + 1.
-  auto fold4 = [&](const double* ring, int k, double& cp, double& cm, double& sp, double& smv) {
+  for (int o = threadIdx.x; o < nr * nth * W; o += T) {
+    const int k = o % W;
+    const int rj = o / W;
+    const double* ring = U + (size_t)rj * nph;
+    double* f = F + (size_t)rj * 4 * W;
     auto ev = [&](int kk) { return (kk == 0 || kk == N2) ? ring[kk] : ring[kk] + ring[nph - kk]; };
     auto od = [&](int kk) { return (kk == 0 || kk == N2) ? 0.0 : ring[kk] - ring[nph - kk]; };
     if (!(qself && k == N4)) {
       const double e1 = ev(k), e2 = ev(N2 - k), o1 = od(k), o2 = od(N2 - k);
-      cp = e1 + e2;
-      cm = e1 - e2;
-      sp = o1 + o2;
-      smv = o1 - o2;
+      f[k] = e1 + e2;
+      f[W + k] = e1 - e2;
+      f[2 * W + k] = o1 + o2;
+      f[3 * W + k] = o1 - o2;
     } else {
-      cp = ev(N4);
-      cm = 0.0;
-      sp = od(N4);
-      smv = 0.0;
-    }
-  };
-  if (!e8) {
-    for (int o = threadIdx.x; o < nr * nth * W; o += T) {
-      const int k = o % W;
-      const int rj = o / W;
-      double* f = F + (size_t)rj * 4 * WF;
-      fold4(U + (size_t)rj * nph, k, f[k], f[WF + k], f[2 * WF + k], f[3 * WF + k]);
-    }
-  } else {
-    for (int o = threadIdx.x; o < nr * nth * (N8 + 1); o += T) {
-      const int k = o % (N8 + 1);
-      const int rj = o / (N8 + 1);
-      const double* ring = U + (size_t)rj * nph;
-      double* f = F + (size_t)rj * 4 * WF;
-      double cp, cm, sp, smv;
-      fold4(ring, k, cp, cm, sp, smv);
-      f[WF + k] = cm;
-      f[2 * WF + k] = sp;
-      if (k < N8) {
-        const int kq = N4 - k;
-        double cp2, cm2, sp2, sm2;
-        fold4(ring, kq, cp2, cm2, sp2, sm2);
-        f[WF + kq] = cm2;
-        f[2 * WF + kq] = sp2;
-        f[k] = cp + cp2;
-        f[N8 + 1 + k] = cp - cp2;
-        f[3 * WF + k] = smv - sm2;
-        f[3 * WF + N8 + 1 + k] = smv + sm2;
-      } else {
-        f[k] = cp;
-        f[N8 + 1 + k] = cp;
-        f[3 * WF + k] = smv;
-        f[3 * WF + N8 + 1 + k] = smv;
-      }
+      f[k] = ev(N4);
+      f[W + k] = 0.0;
+      f[2 * W + k] = od(N4);
+      f[3 * W + k] = 0.0;
     }
   }
   __syncthreads();
@@ -135,16 +94,12 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     const int m = cosm ? mode : mode - K;
     const int q = cosm ? (m % 2 == 0 ? 0 : 1) : (m % 2 == 1 ? 2 : 3);
     const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
-    // even modes with e8: N/8 + 1 taps on the m mod 4 half of their class
-    const bool fold8 = e8 && (m % 2 == 0);
-    const int taps = fold8 ? N8 + 1 : W;
-    const int sub8 = (fold8 && (m % 4 == 2)) ? N8 + 1 : 0;
-    const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * WF + sub8;
+    const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
     double* ab = AB + ((size_t)rr * M + mode) * 2 * hs;
     if (jh < half) {
-      const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * WF + sub8;
+      const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
       double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
-      for (int k = 1; k < taps; ++k) {
+      for (int k = 1; k < W; ++k) {
         const double tv = __ldg(tab + k);
         c1 = fma(f1[k], tv, c1);
         c2 = fma(f2[k], tv, c2);
@@ -153,7 +108,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
       ab[hs + jh] = c1 - c2;
     } else {
       double c1 = f1[0] * __ldg(tab);
-      for (int k = 1; k < taps; ++k) c1 = fma(f1[k], __ldg(tab + k), c1);
+      for (int k = 1; k < W; ++k) c1 = fma(f1[k], __ldg(tab + k), c1);
       ab[jh] = c1;
       ab[hs + jh] = 0.0;
     }
@@ -223,12 +178,31 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     }
   }
   __syncthreads();
-  // phase C: quarter-ring sums give four output points each (k, N/2-k, N/2+k,
-  // N-k); one item per (output, ring, k).  With e8 one item per (output, ring,
-  // k <= N/8) serves k and N/4 - k: the even-mode sums are taken once (split by
-  // m mod 4) and give both points, the odd-mode sums are taken at both.
-  auto put4 = [&](double* dst, int k, double Ee, double Eo, double Oe, double Oo) {
+  // phase C: quarter-ring sums give four output points each; one item per
+  // (output, ring, k)
+  for (int o = threadIdx.x; o < NO * nr * nth * W; o += T) {
+    const int k = o % W;
+    const int t = o / W;
+    const int o2 = TWO ? t % NO : 0;
+    const int rj = TWO ? t / NO : t;
+    const int rr = rj / nth;
+    const int j = rj - rr * nth;
+    const double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M;
+    double Ee = c[0] * __ldg(P.Tc + k), Eo = 0.0, Oe = 0.0, Oo = 0.0;
+    for (int m = 1; m <= K; m += 2) {
+      const double tc1 = __ldg(P.Tc + (size_t)m * W + k);
+      const double ts1 = __ldg(P.Ts + (size_t)m * W + k);
+      Eo = fma(c[m], tc1, Eo);
+      Oo = fma(c[K + m], ts1, Oo);
+      if (m + 1 <= K) {
+        const double tc2 = __ldg(P.Tc + (size_t)(m + 1) * W + k);
+        const double ts2 = __ldg(P.Ts + (size_t)(m + 1) * W + k);
+        Ee = fma(c[m + 1], tc2, Ee);
+        Oe = fma(c[K + m + 1], ts2, Oe);
+      }
+    }
     const double Ek = Ee + Eo, Eh = Ee - Eo, Ok = Oe + Oo, Oh = Oo - Oe;
+    double* dst = (o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * nph;
     if (k == 0) {
       dst[0] = Ek + Ok;
       dst[N2] = Eh + Oh;
@@ -240,60 +214,6 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
       dst[N2 - k] = Eh + Oh;
       dst[N2 + k] = Eh - Oh;
       dst[nph - k] = Ek - Ok;
-    }
-  };
-  const int KW = e8 ? N8 + 1 : W;
-  for (int o = threadIdx.x; o < NO * nr * nth * KW; o += T) {
-    const int k = o % KW;
-    const int t = o / KW;
-    const int o2 = TWO ? t % NO : 0;
-    const int rj = TWO ? t / NO : t;
-    const int rr = rj / nth;
-    const int j = rj - rr * nth;
-    const double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M;
-    double* dst = (o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * nph;
-    if (!e8) {
-      double Ee = c[0] * __ldg(P.Tc + k), Eo = 0.0, Oe = 0.0, Oo = 0.0;
-      for (int m = 1; m <= K; m += 2) {
-        const double tc1 = __ldg(P.Tc + (size_t)m * W + k);
-        const double ts1 = __ldg(P.Ts + (size_t)m * W + k);
-        Eo = fma(c[m], tc1, Eo);
-        Oo = fma(c[K + m], ts1, Oo);
-        if (m + 1 <= K) {
-          const double tc2 = __ldg(P.Tc + (size_t)(m + 1) * W + k);
-          const double ts2 = __ldg(P.Ts + (size_t)(m + 1) * W + k);
-          Ee = fma(c[m + 1], tc2, Ee);
-          Oe = fma(c[K + m + 1], ts2, Oe);
-        }
-      }
-      put4(dst, k, Ee, Eo, Oe, Oo);
-    } else {
-      const int kq = N4 - k;
-      // even modes at k, split by m mod 4
-      double Ee0 = c[0] * __ldg(P.Tc + k), Ee2 = 0.0, Oe0 = 0.0, Oe2 = 0.0;
-      for (int m = 2; m <= K; m += 2) {
-        const double tc = __ldg(P.Tc + (size_t)m * W + k);
-        const double ts = __ldg(P.Ts + (size_t)m * W + k);
-        if (m % 4 == 0) {
-          Ee0 = fma(c[m], tc, Ee0);
-          Oe0 = fma(c[K + m], ts, Oe0);
-        } else {
-          Ee2 = fma(c[m], tc, Ee2);
-          Oe2 = fma(c[K + m], ts, Oe2);
-        }
-      }
-      // odd modes at k and at N/4 - k
-      double Eo = 0.0, Oo = 0.0, Eoq = 0.0, Ooq = 0.0;
-      for (int m = 1; m <= K; m += 2) {
-        Eo = fma(c[m], __ldg(P.Tc + (size_t)m * W + k), Eo);
-        Oo = fma(c[K + m], __ldg(P.Ts + (size_t)m * W + k), Oo);
-        if (k < N8) {
-          Eoq = fma(c[m], __ldg(P.Tc + (size_t)m * W + kq), Eoq);
-          Ooq = fma(c[K + m], __ldg(P.Ts + (size_t)m * W + kq), Ooq);
-        }
-      }
-      put4(dst, k, Ee0 + Ee2, Eo, Oe0 + Oe2, Oo);
-      if (k < N8) put4(dst, kq, Ee0 - Ee2, Eoq, Oe2 - Oe0, Ooq);
     }
   }
 }

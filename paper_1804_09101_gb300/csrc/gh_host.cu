@@ -426,7 +426,7 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
 // coefficients of the half-rings.
 size_t fold_row_doubles(int na, int nth, int W, int M, int n_out) {
   const size_t ab = (size_t)M * 2 * (size_t)((nth + 1) / 2);
-  return std::max((size_t)na + 4 * (size_t)nth * (W + 1), (size_t)n_out * nth * M) + ab;
+  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + ab;
 }
 
 int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int n_rows, int budget_bytes) {
@@ -924,10 +924,6 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
           P.W = f.W;
           P.hs = f.hs;
           P.qself = f.qself;
-#ifndef GH_FOLD_E8
-#define GH_FOLD_E8 1
-#endif
-          P.e8 = (GH_FOLD_E8 && ag.nph % 8 == 0 && ag.nph >= 16) ? 1 : 0;
           P.two = deriv ? 1 : 0;
           P.sigma0 = f.s0;
           P.sigma1 = f.s1;

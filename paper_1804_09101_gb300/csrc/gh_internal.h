@@ -80,8 +80,7 @@ struct FoldPlan {
   int W, hs;                    // quarter-ring points, symmetric half-ring size ceil(N_theta/2)
   int qself;                    // 1 if N_phi % 4 == 0 (the point N_phi/4 is its own mirror)
   int rows_per_cta, two;        // rows per block; 2 outputs (derivatives) or 1 (filter)
-  int adj_rows_per_cta;         // rows per block of the transposed map (fold_adjoint_kernel)
-  int e8;                       // 1 if N_phi % 8 == 0: even modes also folded under k <-> N/4 - k
+  int adj_rows_per_cta, pad1;   // rows per block of the transposed map (fold_adjoint_kernel)
   const double* Tc;             // [K+1][W] cos(m phi_k)
   const double* Ts;             // [K+1][W] sin(m phi_k)
   // [K+1][hs][hs] (transposed: [m][j_in][j_out]) half-size Legendre maps,
