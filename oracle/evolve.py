@@ -82,11 +82,13 @@ def rhs_interior(dom, u):
     return out
 
 
-def apply_boundaries(dom, dudt, u=None, bg_map=None):
+def apply_boundaries(dom, dudt, u=None, bg_map=None, bg_fn=None):
     """ApplyBCs: outer freezing (or constraint-preserving) condition, upwind
     interface exchange, no-op at excision.  u is needed for the
     constraint-preserving outer condition; bg_map transforms the boundary
-    background (the rotating frame rotates its vectors).
+    background (the rotating frame rotates its vectors); bg_fn(s, ir), when
+    given, supplies the background of radial slice ir of shell s instead (a
+    general time-dependent map evaluates it at the moving points).
 
     Shells are ordered by radius; shell s's outer slice and shell s+1's inner
     slice are the same physical points.
@@ -94,6 +96,8 @@ def apply_boundaries(dom, dudt, u=None, bg_map=None):
     out = [d.copy() for d in dudt]
     ns = len(out)
     bgf = (lambda b: b) if bg_map is None else bg_map
+    if bg_fn is not None:
+        dom = _BgOverride(dom, bg_fn)
     for s in range(ns - 1):
         nr = out[s].shape[0]
         bg = bgf(dom.boundary_bg(s, nr - 1))
@@ -114,6 +118,19 @@ def apply_boundaries(dom, dudt, u=None, bg_map=None):
         new = gh.apply_outer_bc(a, bg, dom.gamma1, dom.gamma2)
     out[s][nr - 1] = np.moveaxis(new, -1, 0)
     return out
+
+
+class _BgOverride:
+    """The domain with boundary_bg(s, ir) taken from a function."""
+
+    def __init__(self, dom, fn):
+        self._dom, self._fn = dom, fn
+
+    def __getattr__(self, k):
+        return getattr(self._dom, k)
+
+    def boundary_bg(self, s, ir):
+        return self._fn(s, ir)
 
 
 def rhs(dom, u):

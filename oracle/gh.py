@@ -213,9 +213,15 @@ def boundary_background(psi_bg, X, Y, Z):
 
 
 def char_speeds(bg, gamma1):
-    """Speeds (v_psi, v_0, v_plus, v_minus) along n = +R direction."""
+    """Speeds (v_psi, v_0, v_plus, v_minus) along n = +R direction.
+
+    A boundary that moves with the grid (a time-dependent map) carries
+    bg["n_xdot"] = n_i xdot^i, the normal grid velocity; the speeds relative
+    to the moving boundary are the inertial ones minus it (every family's
+    advection gains the grid velocity in the grid frame)."""
     nb = np.einsum("...i,...i->...", bg["n_dn"], bg["beta_up"])
-    return (-(1.0 + gamma1) * nb, -nb, -nb + bg["alpha"], -nb - bg["alpha"])
+    sh = bg.get("n_xdot", 0.0)
+    return (-(1.0 + gamma1) * nb - sh, -nb - sh, -nb + bg["alpha"] - sh, -nb - bg["alpha"] - sh)
 
 
 def to_char(v, bg, gamma2):
