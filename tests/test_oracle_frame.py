@@ -137,3 +137,19 @@ def test_a_boundary_outrunning_every_family_freezes_them_all():
     assert np.abs(out[0][6]).max() == 0.0 and np.abs(out[0][5] - F[0][5]).max() == 0.0
     still = evolve.apply_boundaries(dom, F, None, bg_fn=lambda s, ir: frame.map_bg(dom, s, ir, frame.AffineMap(), t))
     assert np.abs(still[0][6]).max() > 0.1
+
+
+def test_translated_boundary_normal_points_from_the_moving_centre():
+    """Under a pure translation the boundary sphere is |x - T| = r: its normal
+    at the grid point x_g is along x_g (normalised with the metric at x), and
+    n . xdot = n . V."""
+    dom = evolve.Domain([(2.0, 5.0, 5, 3)], M=1.0, chi=0.5)
+    mp = frame.AffineMap(V=(0.3, -0.2, 0.25))
+    t = 1.7
+    bg = frame.map_bg(dom, 0, 4, mp, t)
+    from oracle import grid
+    X, Y, Z = grid.cartesian_coords(dom.grids[0])
+    xg = np.stack([X[4], Y[4], Z[4]], axis=-1)
+    cross = np.cross(bg["n_dn"], xg)
+    assert np.abs(cross).max() < 1e-13 * np.abs(xg).max()
+    assert np.abs(bg["n_xdot"] - bg["n_dn"] @ mp.V).max() < 1e-14

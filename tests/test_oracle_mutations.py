@@ -196,6 +196,17 @@ CASES = {
     "constraint energy without the step size": (
         "evolve", "E += dt * sum(norms)", "E += sum(norms)",
         "test_constraint_energy_sums_the_rk4_decay_of_a_violation_on_flat_space", ()),
+    # general time-dependent map (oracle/frame.py, oracle/gh.py)
+    "moving frame without the expansion's Jacobian": (
+        "frame", 'dUi = np.einsum("kj,...jf->...kf", R, dUg) / a', 'dUi = np.einsum("kj,...jf->...kf", R, dUg)',
+        "frame::test_moving_exact_solution_matches_its_time_derivative_under_a_general_map",
+        [("contraction+translation",), ("expand+translate+tilted rotation",)]),
+    "moving boundary speed shift with the wrong sign": (
+        "gh", 'sh = bg.get("n_xdot", 0.0)', 'sh = -bg.get("n_xdot", 0.0)',
+        "frame::test_a_boundary_outrunning_every_family_freezes_them_all", ()),
+    "moving boundary normal from the fixed centre": (
+        "frame", "xc = x[ir] - T", "xc = x[ir]",
+        "frame::test_translated_boundary_normal_points_from_the_moving_centre", ()),
     # constraint-preserving outer condition (oracle/gh.py)
     "constraint-preserving correction sign": (
         "gh", "wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)",
