@@ -331,6 +331,24 @@ gh_status gh_set_algorithm(gh_domain* dom, int algorithm);
  * gh_set_rotating_frame discards a captured graph; GH_EINVAL for a zero axis
  * or a non-finite rate. */
 gh_status gh_set_rotating_frame(gh_domain* dom, const double axis[3], double omega);
+/* gh_set_frame_map: the general time-dependent map of the dual frame (Sec. 3.1:
+ * grid and inertial coordinates share the time and are related by a
+ * time-dependent map), x = a(t) R(t) x_grid + T(t) with a(t) = 1 + adot t
+ * (expansion, or contraction for adot < 0), R(t) the rotation about axis by
+ * omega t, T(t) = V t (translation); t is the domain clock (gh_set_time).  The
+ * derivative index takes the map's Jacobian, d_inertial = R d_grid / a (the
+ * SpatialCoordJac of Sec. 3.3), each RHS adds xdot . d u after the boundary
+ * conditions, and the hole's gauge source and the boundary background are
+ * evaluated at the moving inertial points every stage (so every hole must
+ * have been set with gh_set_analytic_kerr_schild*; GH_EINVAL otherwise), the
+ * boundary being the moving sphere |x - T| = a r with its characteristic speeds
+ * taken relative to it.  axis: 3 numbers (host), not all zero; rates finite.
+ * Replaces gh_set_rotating_frame's rotation (which rotates the stored gauge
+ * source and needs a background symmetric about the axis); the adjoint entry
+ * points return GH_ENOTSUP under a general map.  Captured RK4 graphs replay
+ * with the live clock. */
+gh_status gh_set_frame_map(gh_domain* dom, const double axis[3], double omega, double adot, const double V[3]);
+
 gh_status gh_set_time(gh_domain* dom, double t);
 gh_status gh_get_time(const gh_domain* dom, double* t);
 

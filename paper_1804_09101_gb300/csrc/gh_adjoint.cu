@@ -643,6 +643,8 @@ gh_status frames_at(gh_domain* d, double half, double full, int n) {
 
 gh_status adj_ready(gh_domain* d) {
   if (gh_status s = gh::check_latched(d)) return s;
+  if (d->map_gen)
+    return afail(d, GH_ENOTSUP, "the adjoint supports the static grid and the rotating frame, not a general map");
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
   if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
     void* p = nullptr;

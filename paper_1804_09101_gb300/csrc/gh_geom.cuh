@@ -64,9 +64,10 @@ __device__ inline void legendre_table(int lmax, double ct, double st, double* P,
     }
 }
 
-// Rotating frame: DiffJac followed by the map's Jacobian, J <- R J (the
-// SpatialCoordJac of Sec. 3.3 for a rotation), and the grid velocity
-// w x (R x_grid) at the point.
+// Moving frame: DiffJac followed by the map's Jacobian, J <- R J (the
+// SpatialCoordJac of Sec. 3.3 for a rotation; J <- R J / a with the
+// expansion of a general map), and the grid velocity w x (x - T) at the point
+// (plus (adot / a)(x - T) + V for a general map), x - T = a R x_grid.
 __device__ __forceinline__ void frame_geom(const Frame& fr, PointGeom& G, double vel[3]) {
   double J2[3][3];
 #pragma unroll
@@ -74,17 +75,24 @@ __device__ __forceinline__ void frame_geom(const Frame& fr, PointGeom& G, double
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       J2[k][d] = fma(fr.R[3 * k + 2], G.J[2][d], fma(fr.R[3 * k + 1], G.J[1][d], fr.R[3 * k] * G.J[0][d]));
+  const double ia = fr.gen ? 1.0 / fr.a : 1.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) G.J[k][d] = J2[k][d];
+    for (int d = 0; d < 3; ++d) G.J[k][d] = fr.gen ? J2[k][d] * ia : J2[k][d];
+  const double rr = fr.gen ? fr.a * G.r : G.r;
   double xi[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    xi[k] = G.r * fma(fr.R[3 * k + 2], G.xhat[2], fma(fr.R[3 * k + 1], G.xhat[1], fr.R[3 * k] * G.xhat[0]));
+    xi[k] = rr * fma(fr.R[3 * k + 2], G.xhat[2], fma(fr.R[3 * k + 1], G.xhat[1], fr.R[3 * k] * G.xhat[0]));
   vel[0] = fr.w[1] * xi[2] - fr.w[2] * xi[1];
   vel[1] = fr.w[2] * xi[0] - fr.w[0] * xi[2];
   vel[2] = fr.w[0] * xi[1] - fr.w[1] * xi[0];
+  if (fr.gen) {
+    const double h = fr.adot * ia;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vel[k] += fma(h, xi[k], fr.V[k]);
+  }
 }
 
 // Gauge source of a background invariant under the rotation, at the moving

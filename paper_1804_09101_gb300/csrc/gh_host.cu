@@ -743,7 +743,14 @@ void invalidate_graph(gh_domain* d) {
 namespace gh {
 Frame frame_at(const gh_domain* d, double t) {
   Frame f;
-  f.on = d->rot_omega != 0.0 ? 1 : 0;
+  f.on = frame_moving(d) ? 1 : 0;
+  f.gen = d->map_gen ? 1 : 0;
+  f.a = d->map_gen ? 1.0 + d->map_adot * t : 1.0;
+  f.adot = d->map_gen ? d->map_adot : 0.0;
+  for (int i = 0; i < 3; ++i) {
+    f.V[i] = d->map_gen ? d->map_V[i] : 0.0;
+    f.T[i] = f.V[i] * t;
+  }
   const double n = std::sqrt(d->rot_axis[0] * d->rot_axis[0] + d->rot_axis[1] * d->rot_axis[1] +
                              d->rot_axis[2] * d->rot_axis[2]);
   const double e[3] = {d->rot_axis[0] / n, d->rot_axis[1] / n, d->rot_axis[2] / n};
@@ -1201,6 +1208,18 @@ gh_status gh_set_analytic_kerr_schild_spin(gh_domain* d, int bh, double M, const
   if (gh_status s = check_latched(d)) return s;
   GH_CUDA(d, gh::launch_kerr_schild(d, bh, M, chi, u));
   GH_CUDA(d, gh::launch_bc_background(d, u, bh));
+  // the hole's parameters, for a general map's evaluations at moving points
+  int nbh = 0;
+  for (const auto& sh : d->shells_h) nbh = std::max(nbh, sh.bh + 1);
+  if ((int)d->holes.size() < 4 * nbh) d->holes.resize(4 * (size_t)nbh, 0.0);
+  for (int b = 0; b < nbh; ++b)
+    if (bh == -1 || bh == b) {
+      d->holes[4 * b] = M;
+      for (int i = 0; i < 3; ++i) d->holes[4 * b + 1 + i] = chi[i] * M;
+    }
+  if (d->holes_d && d->map_gen)
+    GH_CUDA(d, cudaMemcpyAsync(d->holes_d, d->holes.data(), sizeof(double) * d->holes.size(), cudaMemcpyHostToDevice,
+                               d->stream));
   return GH_OK;
 }
 
@@ -1338,12 +1357,14 @@ gh_status gh_add_perturbation(gh_domain* d, int kind, double A, double Rc, doubl
   return GH_OK;
 }
 
-// The rotating frame at the domain clock for one evaluation (no-op when static).
+// The moving frame at the domain clock for one evaluation (no-op when static);
+// a general map's gauge source and boundary background for it.
 gh_status frame_now(gh_domain* d) {
-  if (d->rot_omega == 0.0) return GH_OK;
+  if (!gh::frame_moving(d)) return GH_OK;
   const double off = 0.0;
   GH_CUDA(d, gh::launch_frames(d, &off, 1, 0.0));
   d->frd = d->frames_d;
+  GH_CUDA(d, gh::launch_map_stage(d));
   return GH_OK;
 }
 
@@ -1377,7 +1398,7 @@ gh_status gh_rhs(gh_domain* d, const double* u, double* dudt) {
 // u_n + dt/2 k1, u_n + dt/2 k2, u_n + dt k3 are written there (and used as the
 // stage buffers) instead of the work area.
 gh_status rotation_guard(gh_domain* d) {
-  if (d->rot_omega == 0.0) return GH_OK;
+  if (!gh::frame_moving(d)) return GH_OK;
   for (const auto& sh : d->shells_h)
     if (sh.dt_scale != 1.0) return fail(d, GH_ENOTSUP, "the rotating frame needs dt_scale = 1 on every shell");
   return GH_OK;
@@ -1390,7 +1411,7 @@ gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double
   double* k = work + d->state;
   double* acc = work + 2 * d->state;
   const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
-  if (d->rot_omega != 0.0) {
+  if (gh::frame_moving(d)) {
     // the step's frames from the device clock, which then advances by dt
     // (gh_rk4_step only: the adjoint's recomputation leaves the clock alone)
     const double off[3] = {0.0, 0.5 * dt, dt};
@@ -1399,6 +1420,7 @@ gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double
   for (int stage = 1; stage <= 4; ++stage) {
     const double* in = (stage == 1) ? u : (stages ? stages + (stage - 2) * d->state : us);
     d->frd = d->frames_d ? d->frames_d + fidx[stage - 1] : nullptr;
+    if (d->map_gen && (stage != 3)) GH_CUDA(d, gh::launch_map_stage(d));   // stage 3 shares stage 2's time
     if (gh_status s = derivatives(d, in)) return s;
     double* target = (stage == 4) ? (filt ? us : u) : (stages ? stages + (stage - 1) * d->state : us);
     {
@@ -1494,7 +1516,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   for (int j = 0; j < 7; ++j) k[j] = work + j * N;
   double* ustage = work + 7 * N;
   double* unew = work + 8 * N;
-  if (d->rot_omega != 0.0) {
+  if (gh::frame_moving(d)) {
     double off[7];
     for (int s = 0; s < 7; ++s) off[s] = cdp[s] * dt;
     GH_CUDA(d, gh::launch_frames(d, off, 7, 0.0));
@@ -1502,6 +1524,7 @@ gh_status gh_dp5_step(gh_domain* d, double dt, double rtol, double atol, double*
   for (int s = 0; s < 7; ++s) {
     const double* in = (s == 0) ? u : (s == 6 ? unew : ustage);
     d->frd = d->frames_d ? d->frames_d + s : nullptr;
+    GH_CUDA(d, gh::launch_map_stage(d));
     if (gh_status st = derivatives(d, in)) return st;
     {
       ProfScope p(d, GH_K_POINTWISE);
@@ -1668,6 +1691,9 @@ gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   for (int i = 0; i < 3; ++i) d->rot_axis[i] = axis[i];
   d->rot_omega = omega;
+  d->map_gen = false;                   // a rotation alone (stored background rotated)
+  d->map_adot = 0.0;
+  for (int i = 0; i < 3; ++i) d->map_V[i] = 0.0;
   d->fr = gh::frame_at(d, d->time);
   d->frd = nullptr;
   if (omega != 0.0 && !d->clock_d) {
@@ -1680,6 +1706,74 @@ gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega
     d->frames_d = (gh::Frame*)p;
   }
   if (d->clock_d) GH_CUDA(d, cudaMemcpy(d->clock_d, &d->time, sizeof(double), cudaMemcpyHostToDevice));
+  if (d->graph_exec) {
+    cudaGraphExecDestroy(d->graph_exec);
+    d->graph_exec = nullptr;
+  }
+  return GH_OK;
+}
+
+gh_status gh_set_frame_map(gh_domain* d, const double axis[3], double omega, double adot, const double V[3]) {
+  if (!d || !axis || !V) return GH_EINVAL;
+  const double n = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+  if (!(n > 0.0) || !std::isfinite(omega) || !std::isfinite(adot) || !std::isfinite(V[0]) || !std::isfinite(V[1]) ||
+      !std::isfinite(V[2]))
+    return fail(d, GH_EINVAL, "need a nonzero axis and finite rates");
+  for (const auto& sh : d->shells_h)
+    if (4 * (size_t)sh.bh + 3 >= d->holes.size() || !(d->holes[4 * sh.bh] > 0.0))
+      return fail(d, GH_EINVAL, "the map evaluates each hole at the moving points: set every hole with "
+                                "gh_set_analytic_kerr_schild first");
+  GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  if (!d->map_buf) {
+    long long nd = 0;
+    for (const auto& sh : d->shells_h) nd += (long long)sh.n_r * gh::NGAUGE * sh.na;
+    for (const auto& sl : d->bc_h) nd += 11LL * sl.na;
+    void* p = nullptr;
+    GH_CUDA(d, alloc_zero(d, sizeof(double) * (size_t)nd, &p));
+    d->map_buf = (double*)p;
+    double* q = d->map_buf;
+    for (auto& sh : d->shells_h) {
+      sh.gauge_t = q;
+      q += (long long)sh.n_r * gh::NGAUGE * sh.na;
+    }
+    for (auto& sl : d->bc_h) {
+      sl.bg_t = q;
+      q += 11LL * sl.na;
+    }
+    GH_CUDA(d, cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(gh::ShellDev) * d->shells_h.size(),
+                          cudaMemcpyHostToDevice));
+    if (!d->bc_h.empty())
+      GH_CUDA(d, cudaMemcpy(d->bc_d, d->bc_h.data(), sizeof(gh::BcSliceDev) * d->bc_h.size(), cudaMemcpyHostToDevice));
+    std::vector<int> begin(d->n_shells + 1);
+    int blocks = 0;
+    for (int s = 0; s < d->n_shells; ++s) {
+      begin[s] = blocks;
+      blocks += d->shells_h[s].n_r * ((d->shells_h[s].na + 63) / 64);
+    }
+    begin[d->n_shells] = blocks;
+    d->map_blocks = blocks;
+    GH_CUDA(d, upload(d, begin, &d->map_pt_begin_d));
+  }
+  GH_CUDA(d, upload(d, d->holes, &d->holes_d));
+  if (!d->clock_d) {
+    void* p = nullptr;
+    GH_CUDA(d, cudaMalloc(&p, sizeof(double)));
+    d->owned.push_back(p);
+    d->clock_d = (double*)p;
+    GH_CUDA(d, cudaMalloc(&p, sizeof(gh::Frame) * 8));
+    d->owned.push_back(p);
+    d->frames_d = (gh::Frame*)p;
+  }
+  for (int i = 0; i < 3; ++i) {
+    d->rot_axis[i] = axis[i];
+    d->map_V[i] = V[i];
+  }
+  d->rot_omega = omega;
+  d->map_adot = adot;
+  d->map_gen = true;
+  d->fr = gh::frame_at(d, d->time);
+  d->frd = nullptr;
+  GH_CUDA(d, cudaMemcpy(d->clock_d, &d->time, sizeof(double), cudaMemcpyHostToDevice));
   if (d->graph_exec) {
     cudaGraphExecDestroy(d->graph_exec);
     d->graph_exec = nullptr;

@@ -117,6 +117,35 @@ __device__ void kerr_schild_metric(double x, double y, double z, double M, const
   }
 }
 
+// The gauge source of a stationary metric from its jets: H_a = -Gamma_a and
+// d_i H_a = -d_i Gamma_a, with Gamma_abc from D[c][ab] = d_c g_ab (d_0 = 0).
+__device__ void ks_gauge(const Jet g[10], const Split& S, double H[4], double dH[12]) {
+  auto D = [&](int c, int A, int B) -> double { return c == 0 ? 0.0 : g[sym_index(A, B)].g[c - 1]; };
+  auto DD = [&](int i, int c, int A, int B) -> double {
+    return c == 0 ? 0.0 : g[sym_index(A, B)].h[h3(i, c - 1)];
+  };
+  for (int A = 0; A < 4; ++A) {
+    double acc = 0.0, dacc[3] = {0.0, 0.0, 0.0};
+    for (int B = 0; B < 4; ++B)
+      for (int C = 0; C < 4; ++C) {
+        const double gam = 0.5 * (D(B, A, C) + D(C, A, B) - D(A, B, C));
+        const double pinv = S.psi_inv[sym_index(B, C)];
+        acc += pinv * gam;
+        for (int i = 0; i < 3; ++i) {
+          // d_i psi^BC = -psi^BE d_i psi_EF psi^FC
+          double dpinv = 0.0;
+          for (int E = 0; E < 4; ++E)
+            for (int F = 0; F < 4; ++F)
+              dpinv -= S.psi_inv[sym_index(B, E)] * D(1 + i, E, F) * S.psi_inv[sym_index(F, C)];
+          const double dgam = 0.5 * (DD(i, B, A, C) + DD(i, C, A, B) - DD(i, A, B, C));
+          dacc[i] += dpinv * gam + pinv * dgam;
+        }
+      }
+    H[A] = -acc;
+    for (int i = 0; i < 3; ++i) dH[4 * i + A] = -dacc[i];
+  }
+}
+
 // One thread per point: u = (psi, Pi, Phi) of the stationary metric and the
 // gauge source H_a = -Gamma_a, d_i H_a = -d_i Gamma_a (d_t H_a = 0).
 __global__ void __launch_bounds__(64)
@@ -152,36 +181,114 @@ kerr_schild_kernel(const ShellDev* __restrict__ shells, int n_shells, const int*
     u[base + (long long)(10 + p) * na] = Pi[p];
     for (int i = 0; i < 3; ++i) u[base + (long long)(20 + 10 * i + p) * na] = Phi[i * 10 + p];
   }
-  // Gamma_abc from D[c][ab] = d_c g_ab (d_0 = 0)
-  auto D = [&](int c, int A, int B) -> double { return c == 0 ? 0.0 : g[sym_index(A, B)].g[c - 1]; };
-  auto DD = [&](int i, int c, int A, int B) -> double {
-    return c == 0 ? 0.0 : g[sym_index(A, B)].h[h3(i, c - 1)];
-  };
-  double Ga[4], dGa[3][4];
-  for (int A = 0; A < 4; ++A) {
-    double acc = 0.0, dacc[3] = {0.0, 0.0, 0.0};
-    for (int B = 0; B < 4; ++B)
-      for (int C = 0; C < 4; ++C) {
-        const double gam = 0.5 * (D(B, A, C) + D(C, A, B) - D(A, B, C));
-        const double pinv = S.psi_inv[sym_index(B, C)];
-        acc += pinv * gam;
-        for (int i = 0; i < 3; ++i) {
-          // d_i psi^BC = -psi^BE d_i psi_EF psi^FC
-          double dpinv = 0.0;
-          for (int E = 0; E < 4; ++E)
-            for (int F = 0; F < 4; ++F)
-              dpinv -= S.psi_inv[sym_index(B, E)] * D(1 + i, E, F) * S.psi_inv[sym_index(F, C)];
-          const double dgam = 0.5 * (DD(i, B, A, C) + DD(i, C, A, B) - DD(i, A, B, C));
-          dacc[i] += dpinv * gam + pinv * dgam;
-        }
-      }
-    Ga[A] = acc;
-    for (int i = 0; i < 3; ++i) dGa[i][A] = dacc[i];
-  }
+  double Hg[4], dHg[12];
+  ks_gauge(g, S, Hg, dHg);
   double* gd = sh.gauge + (long long)ir * NGAUGE * na + q;
-  for (int A = 0; A < 4; ++A) gd[(long long)A * na] = -Ga[A];
+  for (int c = 0; c < 16; ++c) gd[(long long)c * na] = c < 4 ? Hg[c] : dHg[c - 4];
+}
+
+// ------------------------------------------------------- general map
+// The inertial position x = a R x_grid + T of grid point (r, q) for frame f,
+// and x - T.
+__device__ __forceinline__ void map_point(const Frame& f, const ShellDev& sh, double r, int q, double x[3],
+                                          double xc[3]) {
+  const int j = q / sh.nph, k = q - j * sh.nph;
+  const double xg[3] = {r * sh.sth[j] * sh.cph[k], r * sh.sth[j] * sh.sph[k], r * sh.cth[j]};
+  for (int i = 0; i < 3; ++i) {
+    xc[i] = f.a * fma(f.R[3 * i + 2], xg[2], fma(f.R[3 * i + 1], xg[1], f.R[3 * i] * xg[0]));
+    x[i] = xc[i] + f.T[i];
+  }
+}
+
+// The hole's gauge source at every point's moving position, into gauge_t
+// (the reading of a general map: the hole is not assumed symmetric under it).
+__global__ void __launch_bounds__(64)
+map_gauge_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                 const Frame* __restrict__ frd, const double* __restrict__ holes) {
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const int na = sh.na;
+  const int bps = (na + 63) / 64;
+  const int lb = blockIdx.x - begin[s];
+  const int ir = lb / bps;
+  const int q = (lb - ir * bps) * 64 + threadIdx.x;
+  if (q >= na) return;
+  const Frame f = *frd;
+  double x[3], xc[3];
+  map_point(f, sh, sh.r[ir], q, x, xc);
+  const double* hp = holes + 4 * sh.bh;
+  const double av[3] = {hp[1], hp[2], hp[3]};
+  Jet g[10];
+  kerr_schild_metric(x[0], x[1], x[2], hp[0], av, g);
+  double psi[10];
+  for (int p = 0; p < 10; ++p) psi[p] = g[p].v;
+  Split S;
+  spacetime_split(psi, S);
+  double Hg[4], dHg[12];
+  ks_gauge(g, S, Hg, dHg);
+  double* gd = sh.gauge_t + (long long)ir * NGAUGE * na + q;
+  for (int c = 0; c < 16; ++c) gd[(long long)c * na] = c < 4 ? Hg[c] : dHg[c - 4];
+}
+
+// The boundary background at every boundary point's moving position, into
+// bg_t: the unit normal of the moving sphere (from x - T), n^i, the lapse, the
+// shift and n . xdot from the expansion and the translation (the rotation
+// moves the sphere within itself).
+__global__ void __launch_bounds__(128)
+map_bg_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int* __restrict__ pt_begin,
+              const ShellDev* __restrict__ shells, const Frame* __restrict__ frd, const double* __restrict__ holes) {
+  const int npts = pt_begin[n_slices];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npts) return;
+  const int s = find_segment(pt_begin, n_slices, t);
+  const BcSliceDev& sl = slices[s];
+  const int q = t - pt_begin[s];
+  const ShellDev& sh = shells[sl.shell_a];
+  const Frame f = *frd;
+  double x[3], xc[3];
+  map_point(f, sh, sh.r_out, q, x, xc);
+  const double* hp = holes + 4 * sh.bh;
+  const double av[3] = {hp[1], hp[2], hp[3]};
+  Jet g[10];
+  kerr_schild_metric(x[0], x[1], x[2], hp[0], av, g);
+  double psi[10];
+  for (int p = 0; p < 10; ++p) psi[p] = g[p].v;
+  Split S;
+  spacetime_split(psi, S);
+  const double R = sqrt(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
+  double n[3] = {xc[0] / R, xc[1] / R, xc[2] / R};
+  double nn = 0.0;
   for (int i = 0; i < 3; ++i)
-    for (int A = 0; A < 4; ++A) gd[(long long)(4 + 4 * i + A) * na] = -dGa[i][A];
+    for (int j = 0; j < 3; ++j) nn += S.ginv[s3(i, j)] * n[i] * n[j];
+  const double inv = 1.0 / sqrt(nn);
+  for (int i = 0; i < 3; ++i) n[i] *= inv;
+  double nu[3];
+  for (int i = 0; i < 3; ++i) nu[i] = S.ginv[s3(i, 0)] * n[0] + S.ginv[s3(i, 1)] * n[1] + S.ginv[s3(i, 2)] * n[2];
+  const double h = f.adot / f.a;
+  double nx = 0.0;
+  for (int i = 0; i < 3; ++i) nx += n[i] * fma(h, xc[i], f.V[i]);
+  const int na = sl.na;
+  double* b = sl.bg_t;
+  for (int i = 0; i < 3; ++i) {
+    b[(long long)i * na + q] = n[i];
+    b[(long long)(3 + i) * na + q] = nu[i];
+    b[(long long)(7 + i) * na + q] = S.beta_up[i];
+  }
+  b[(long long)6 * na + q] = S.alpha;
+  b[(long long)10 * na + q] = nx;
+}
+
+cudaError_t launch_map_stage(gh_domain* d) {
+  if (!d->map_gen) return cudaSuccess;
+  map_gauge_kernel<<<d->map_blocks, 64, 0, d->stream>>>(d->shells_d, d->n_shells, d->map_pt_begin_d, d->frd,
+                                                        d->holes_d);
+  d->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !d->bc_points) return e;
+  map_bg_kernel<<<(d->bc_points + 127) / 128, 128, 0, d->stream>>>(d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d,
+                                                                    d->shells_d, d->frd, d->holes_d);
+  d->launches++;
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------- perturbations

@@ -15,12 +15,20 @@ constexpr int NC = 64;      // stored constraint components per point
 constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
 constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
 constexpr int DP_MAX_BLOCKS = 1024;  // blocks of the Dormand-Prince elementwise kernels
-// Rotating dual frame at one instant (Sec. 3.1 dual frame): inertial position
-// x = R x_grid, grid velocity xdot = w x x.  on = 0: static grid.
+// Dual frame at one instant (Sec. 3.1 dual frame): inertial position
+// x = a R x_grid + T, grid velocity xdot = w x (x - T) + (adot / a)(x - T) + V.
+// on = 0: static grid.  gen = 0: the rotation alone (a = 1, T = V = 0), with
+// the gauge source and boundary background rotated from their stored values;
+// gen = 1: the general map, with both evaluated at the moving points for the
+// frame (map_stage kernels) and the speeds taken relative to the moving
+// boundary.
 struct Frame {
   int on;
+  int gen;
   double R[9];
   double w[3];
+  double a, adot;
+  double T[3], V[3];
 };
 // Stage times of one step relative to the domain clock (frame_kernel).
 struct FrameOffsets {
@@ -131,6 +139,7 @@ struct ShellDev {
   const double* cph;            // [nph]
   const double* sph;            // [nph]
   double* gauge;                // [n_r][16][na]
+  double* gauge_t;              // [n_r][16][na] at the moving points of the current frame (general map)
   int bc_inner;                 // boundary slice index at r_in, -1 if none (excision)
   int bc_outer;                 // boundary slice index at r_out
   int bh;                       // black hole this shell belongs to
@@ -155,6 +164,7 @@ struct BcSliceDev {
   int na;
   long long off_a, off_b;       // state offset of the boundary r-slice in a / b
   double* bg;                   // [10][na] n_dn(3) n_up(3) alpha beta_up(3)
+  double* bg_t;                 // [11][na] the same at the moving points, then n . xdot (general map)
   double dt_scale;              // the hole's step scale (see ShellDev)
   int bh, pad;
 };
@@ -247,8 +257,18 @@ struct gh_domain {
   // time, and the frame of the launches being issued
   double rot_axis[3] = {0.0, 0.0, 1.0};
   double rot_omega = 0.0;
+  // general map (gh_set_frame_map): expansion rate, translation velocity, and
+  // each hole's mass and spin vector a = chi M (recorded by
+  // gh_set_analytic_kerr_schild*), which the map evaluates at moving points
+  bool map_gen = false;
+  double map_adot = 0.0;
+  double map_V[3] = {0.0, 0.0, 0.0};
+  std::vector<double> holes;    // [bh][4]: M, a_x, a_y, a_z (M = 0: not set)
+  double* holes_d = nullptr;
+  double* map_buf = nullptr;    // gauge_t of every shell, then bg_t of every slice
+  int* map_pt_begin_d = nullptr; int map_blocks = 0;   // 64-point block map of map_gauge_kernel
   double time = 0.0;
-  gh::Frame fr = {0, {1, 0, 0, 0, 1, 0, 0, 0, 1}, {0, 0, 0}};
+  gh::Frame fr = {0, 0, {1, 0, 0, 0, 1, 0, 0, 0, 1}, {0, 0, 0}, 1.0, 0.0, {0, 0, 0}, {0, 0, 0}};
   // outer boundary condition: 0 freezing, 1 constraint preserving (gh_set_outer_bc)
   int outer_bc = 0;
   double* dp_err = nullptr;
@@ -296,9 +316,14 @@ cudaError_t tensor_filter_prepare(gh_domain* d, const std::vector<std::vector<do
 cudaError_t launch_tensor_filter(gh_domain* d, const double* in, double* out);
 // Its transpose (reverse mode): out = S^T in (in and out distinct).
 cudaError_t launch_tensor_filter_transpose(gh_domain* d, const double* in, double* out);
-// The rotating frame at the device clock + off[i] into frames_d[i], i < n,
-// then the clock advances by `advance` (no-op without a rotating frame).
+// The frame at the device clock + off[i] into frames_d[i], i < n, then the
+// clock advances by `advance` (no-op on a static grid).
 cudaError_t launch_frames(gh_domain* d, const double* off, int n, double advance);
+// True when the grid moves (a rotating frame or a general map).
+inline bool frame_moving(const gh_domain* d) { return d->rot_omega != 0.0 || d->map_gen; }
+// General map: the gauge source of every point and the boundary background of
+// every boundary point at the moving positions of the frame d->frd.
+cudaError_t launch_map_stage(gh_domain* d);
 // The rotating frame of the domain at time t (identity when not rotating).
 Frame frame_at(const gh_domain* d, double t);
 // Dormand-Prince step: out = base + sum_j c[j] k[j] (j < nk), and the scaled

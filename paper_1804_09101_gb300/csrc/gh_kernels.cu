@@ -436,11 +436,13 @@ pointwise_kernel(PointwiseArgs a) {
     }
 #pragma unroll
     for (int p = 0; p < 30; ++p) Phi[p] = a.u[base + (long long)(20 + p) * na];
-    const double* gsrc = sh.gauge + (long long)ir * NGAUGE * na + q;
+    // a general map's gauge source was evaluated at this frame's moving point;
+    // a rotation's is the stored one with rotated components
+    const double* gsrc = ((ROT && fr.gen) ? sh.gauge_t : sh.gauge) + (long long)ir * NGAUGE * na + q;
     double H[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) H[c] = gsrc[(long long)c * na];
-    if (ROT) frame_rotate_h(fr, H);
+    if (ROT && !fr.gen) frame_rotate_h(fr, H);
 
     Split S;
     spacetime_split(psi, S);
@@ -585,7 +587,7 @@ pointwise_kernel(PointwiseArgs a) {
         double dH[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) dH[c] = gsrc[(long long)(4 + c) * na];
-        if (ROT) frame_rotate_dh(fr, dH);
+        if (ROT && !fr.gen) frame_rotate_dh(fr, dH);
         double aH[4], PHa[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) aH[c] = al * H[c];
@@ -981,17 +983,22 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
   const int q = pt - a.pt_begin[s];
   const int na = sl.na;
   double n_dn[3], n_up[3], beta[3];
+  const Frame fr = (a.fr.on && a.frd) ? *a.frd : a.fr;
+  // the background at the moving point: a general map's evaluated there (with
+  // the normal velocity of the moving boundary), a rotation's rotated
+  const double* bgs = fr.gen ? sl.bg_t : sl.bg;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    n_dn[i] = sl.bg[(long long)i * na + q];
-    n_up[i] = sl.bg[(long long)(3 + i) * na + q];
-    beta[i] = sl.bg[(long long)(7 + i) * na + q];
+    n_dn[i] = bgs[(long long)i * na + q];
+    n_up[i] = bgs[(long long)(3 + i) * na + q];
+    beta[i] = bgs[(long long)(7 + i) * na + q];
   }
-  const double alpha = sl.bg[(long long)6 * na + q];
-  const Frame fr = (a.fr.on && a.frd) ? *a.frd : a.fr;
-  if (fr.on) frame_rotate_bg(fr, n_dn, n_up, beta);   // the background at the moving point
+  const double alpha = bgs[(long long)6 * na + q];
+  if (fr.on && !fr.gen) frame_rotate_bg(fr, n_dn, n_up, beta);
   const double nb = n_dn[0] * beta[0] + n_dn[1] * beta[1] + n_dn[2] * beta[2];
-  const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + alpha, v_m = -nb - alpha;
+  // speeds relative to the boundary: a moving one shifts them all by -n . xdot
+  const double vsh = fr.gen ? bgs[(long long)10 * na + q] : 0.0;
+  const double v_psi = -(1.0 + a.gamma1) * nb - vsh, v_0 = -nb - vsh, v_p = -nb + alpha - vsh, v_m = -nb - alpha - vsh;
   const double g2 = a.gamma2;
   if (sl.kind == 0) {
     const long long base = sl.off_a + q;
@@ -1305,8 +1312,8 @@ cudaError_t launch_bc_background(gh_domain* d, const double* u, int bh) {
 // The rotating frame at n times clock + off[i] (Rodrigues, as on the host),
 // then clock += advance; one thread.  Kernels of the same step read the
 // frames, never the clock, so captured graphs replay with the live clock.
-__global__ void frame_kernel(double* clock, double e0, double e1, double e2, double omega, FrameOffsets fo,
-                             double advance, Frame* out) {
+__global__ void frame_kernel(double* clock, double e0, double e1, double e2, double omega, int gen, double adot,
+                             double V0, double V1, double V2, FrameOffsets fo, double advance, Frame* out) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   const double t0 = *clock;
   const double K[9] = {0.0, -e2, e1, e2, 0.0, -e0, -e1, e0, 0.0};
@@ -1325,13 +1332,21 @@ __global__ void frame_kernel(double* clock, double e0, double e1, double e2, dou
     f.w[0] = omega * e0;
     f.w[1] = omega * e1;
     f.w[2] = omega * e2;
+    const double tt = t0 + fo.off[i];
+    f.gen = gen;
+    f.a = gen ? fma(adot, tt, 1.0) : 1.0;
+    f.adot = gen ? adot : 0.0;
+    f.V[0] = gen ? V0 : 0.0;
+    f.V[1] = gen ? V1 : 0.0;
+    f.V[2] = gen ? V2 : 0.0;
+    for (int c = 0; c < 3; ++c) f.T[c] = f.V[c] * tt;
     out[i] = f;
   }
   if (advance != 0.0) *clock = t0 + advance;
 }
 
 cudaError_t launch_frames(gh_domain* d, const double* off, int n, double advance) {
-  if (d->rot_omega == 0.0 || !d->clock_d) return cudaSuccess;
+  if (!frame_moving(d) || !d->clock_d) return cudaSuccess;
   if (n < 0 || n > 8) return cudaErrorInvalidValue;
   FrameOffsets fo;
   fo.n = n;
@@ -1339,7 +1354,8 @@ cudaError_t launch_frames(gh_domain* d, const double* off, int n, double advance
   const double nrm = std::sqrt(d->rot_axis[0] * d->rot_axis[0] + d->rot_axis[1] * d->rot_axis[1] +
                                d->rot_axis[2] * d->rot_axis[2]);
   frame_kernel<<<1, 32, 0, d->stream>>>(d->clock_d, d->rot_axis[0] / nrm, d->rot_axis[1] / nrm,
-                                        d->rot_axis[2] / nrm, d->rot_omega, fo, advance, d->frames_d);
+                                        d->rot_axis[2] / nrm, d->rot_omega, d->map_gen ? 1 : 0, d->map_adot,
+                                        d->map_V[0], d->map_V[1], d->map_V[2], fo, advance, d->frames_d);
   d->launches++;
   return cudaGetLastError();
 }

@@ -67,10 +67,11 @@ extern "C" gh_status gh_rhs_noalloc(gh_domain* d, const double* u, double* dudt)
     return GH_EINVAL;
   }
   double* w = nullptr;
-  if (e == cudaSuccess && d->rot_omega != 0.0) {
+  if (e == cudaSuccess && gh::frame_moving(d)) {
     const double off = 0.0;            // the frame at the domain clock
     e = gh::launch_frames(d, &off, 1, 0.0);
     d->frd = d->frames_d;
+    if (e == cudaSuccess) e = gh::launch_map_stage(d);
   }
   if (e == cudaSuccess) e = work_area(dev, &w);
   if (e == cudaSuccess) e = gh::launch_radial(d, u, w, false);

@@ -78,6 +78,7 @@ def _load():
         "gh_set_sh_filter": ([P, I], I),
         "gh_set_rotating_frame": ([P, ctypes.POINTER(D), D], I),
         "gh_set_time": ([P, D], I),
+        "gh_set_frame_map": ([P, ctypes.POINTER(D), D, D, ctypes.POINTER(D)], I),
         "gh_get_time": ([P, ctypes.POINTER(D)], I),
         "gh_dp5_work_size": ([P], ctypes.c_longlong),
         "gh_dp5_step": ([P, D, D, D, P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)], I),
@@ -337,6 +338,17 @@ def gh_set_rotating_frame(dom, axis, omega):
     dom._stream()
     dom._check(_lib.gh_set_rotating_frame(dom.handle, v, float(omega)))
     dom.rotating = float(omega) != 0.0
+
+
+def gh_set_frame_map(dom, axis, omega, adot, V):
+    """General map of the grid: x = (1 + adot t) R(axis, omega t) x_grid + V t;
+    the hole's gauge source and boundary data are evaluated at the moving
+    points every stage (set the holes with gh_set_analytic_kerr_schild first)."""
+    a = (ctypes.c_double * 3)(*[float(c) for c in axis])
+    v = (ctypes.c_double * 3)(*[float(c) for c in V])
+    dom._stream()
+    dom._check(_lib.gh_set_frame_map(dom.handle, a, float(omega), float(adot), v))
+    dom.rotating = True
 
 
 def gh_set_time(dom, t):
