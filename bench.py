@@ -80,6 +80,11 @@ def parse():
                         "Kerr a=0.9, N_r=21, L=15; schwarzschild: 1 shell N_r=11, L=7; batched: 64 "
                         "independent single-shell holes of uneven resolution, one CUDA graph per RK4 step, "
                         "compared with the plain per-hole launch loop")
+    p.add_argument("--frame", default="static", choices=["static", "rotating", "map"],
+                   help="grid motion: static (default); rotating about the hole's spin axis at 0.25; map: the "
+                        "general map (expansion 0.01, translation (0.01, 0, 0), rotation 0.25 about a tilted "
+                        "axis), with the hole's gauge source and boundary data evaluated at the moving points "
+                        "every stage")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched, adjoint and 4-shell figures added to the large workload's line")
     p.add_argument("--no-graph", action="store_true",
@@ -395,6 +400,11 @@ def measure_rk4(args, w, pg=None, host_e2e=True, clock_index=0):
     if args.sh_filter == "tensor":
         gh.gh_set_sh_filter(dom, "tensor")
     u = make_state(dom, w, dev)
+    frame = getattr(args, "frame", "static")
+    if frame == "rotating":
+        gh.gh_set_rotating_frame(dom, (0.0, 0.0, 1.0), 0.25)
+    elif frame == "map":
+        gh.gh_set_frame_map(dom, (0.6, 0.0, 0.8), 0.25, 0.01, (0.01, 0.0, 0.0))
     work = dom.new_work()
     norm2 = torch.zeros(len(w.shells), dtype=torch.float64, device=dev)
     state_bytes = dom.state_size * 8
@@ -555,7 +565,7 @@ def run_ours(args, w):
                                         if m["use_graph"] else "one gh_rk4_step call"),
                             kernel_times="per-family CUDA events on the domain's stream, from a second "
                                          "timed region of the same steps called directly",
-                            overlap=not args.no_overlap,
+                            overlap=not args.no_overlap, frame=args.frame,
                             parallelism="replicas" if world > 1 else "single GPU", algorithm=m["algorithm"],
                             schedule=m["schedule"], autotuned=not (args.no_autotune or args.schedule)),
                 e2e=m["e2e"], gpu_launches=m["launches"], roofline=m["roofline"], kernels=m["kernels"])
