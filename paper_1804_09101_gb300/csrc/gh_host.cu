@@ -1217,9 +1217,11 @@ gh_status gh_set_analytic_kerr_schild_spin(gh_domain* d, int bh, double M, const
       d->holes[4 * b] = M;
       for (int i = 0; i < 3; ++i) d->holes[4 * b + 1 + i] = chi[i] * M;
     }
-  if (d->holes_d && d->map_gen)
+  if (d->holes_d && d->map_gen) {
     GH_CUDA(d, cudaMemcpyAsync(d->holes_d, d->holes.data(), sizeof(double) * d->holes.size(), cudaMemcpyHostToDevice,
                                d->stream));
+    GH_CUDA(d, cudaMemsetAsync(d->map_gate_d, 0, sizeof(gh::MapGate), d->stream));   // new holes: re-evaluate
+  }
   return GH_OK;
 }
 
@@ -1753,8 +1755,13 @@ gh_status gh_set_frame_map(gh_domain* d, const double axis[3], double omega, dou
     begin[d->n_shells] = blocks;
     d->map_blocks = blocks;
     GH_CUDA(d, upload(d, begin, &d->map_pt_begin_d));
+    GH_CUDA(d, upload(d, d->holes, &d->holes_d));   // one slot per hole of the domain: its size never changes
+    GH_CUDA(d, alloc_zero(d, sizeof(gh::MapGate), &p));
+    d->map_gate_d = (gh::MapGate*)p;
+  } else {
+    GH_CUDA(d, cudaMemcpy(d->holes_d, d->holes.data(), sizeof(double) * d->holes.size(), cudaMemcpyHostToDevice));
   }
-  GH_CUDA(d, upload(d, d->holes, &d->holes_d));
+  GH_CUDA(d, cudaMemset(d->map_gate_d, 0, sizeof(gh::MapGate)));   // new map: nothing evaluated yet
   if (!d->clock_d) {
     void* p = nullptr;
     GH_CUDA(d, cudaMalloc(&p, sizeof(double)));

@@ -30,6 +30,15 @@ struct Frame {
   double a, adot;
   double T[3], V[3];
 };
+static_assert(sizeof(Frame) % 8 == 0, "frames are compared as 64-bit words");
+// The frame the general map's moving-point buffers (gauge_t, bg_t) were last
+// evaluated at (valid = 0: never, or the holes or the map changed since), and
+// whether the stage being issued may reuse them (skip).
+struct MapGate {
+  Frame last;
+  int valid;
+  int skip;
+};
 // Stage times of one step relative to the domain clock (frame_kernel).
 struct FrameOffsets {
   double off[8];
@@ -267,6 +276,7 @@ struct gh_domain {
   double* holes_d = nullptr;
   double* map_buf = nullptr;    // gauge_t of every shell, then bg_t of every slice
   int* map_pt_begin_d = nullptr; int map_blocks = 0;   // 64-point block map of map_gauge_kernel
+  gh::MapGate* map_gate_d = nullptr;   // reuse of the moving-point buffers between stages at one time
   double time = 0.0;
   gh::Frame fr = {0, 0, {1, 0, 0, 0, 1, 0, 0, 0, 1}, {0, 0, 0}, 1.0, 0.0, {0, 0, 0}, {0, 0, 0}};
   // outer boundary condition: 0 freezing, 1 constraint preserving (gh_set_outer_bc)
@@ -322,7 +332,9 @@ cudaError_t launch_frames(gh_domain* d, const double* off, int n, double advance
 // True when the grid moves (a rotating frame or a general map).
 inline bool frame_moving(const gh_domain* d) { return d->rot_omega != 0.0 || d->map_gen; }
 // General map: the gauge source of every point and the boundary background of
-// every boundary point at the moving positions of the frame d->frd.
+// every boundary point at the moving positions of the frame d->frd, unless
+// the buffers already hold that frame's (the last stage of one RK4 step and
+// the first of the next share a time).
 cudaError_t launch_map_stage(gh_domain* d);
 // The rotating frame of the domain at time t (identity when not rotating).
 Frame frame_at(const gh_domain* d, double t);
