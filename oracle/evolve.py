@@ -29,7 +29,9 @@ class Domain:
         self.gamma0, self.gamma1, self.gamma2 = gamma0, gamma1, gamma2
         self.filt_alpha, self.filt_order = filt_alpha, filt_order
         self.radial_filter_on, self.sh_keep_l = radial_filter_on, sh_keep_l
-        self.outer_bc = outer_bc                  # "freeze" or "cp" (constraint preserving, Bjorhus form)
+        # "freeze", "cp" (constraint preserving, Bjorhus form for u^psi and u^0, u^- frozen) or
+        # "cp_full" (also the constraint part of u^-)
+        self.outer_bc = outer_bc
         self.sh_filter = sh_filter                # "component" (each Cartesian component) or "tensor"
         self.grids = [grid.shell_grid(*s) for s in self.specs]
         self.u_exact, self.H, self.dH = [], [], []
@@ -110,10 +112,16 @@ def apply_boundaries(dom, dudt, u=None, bg_map=None, bg_fn=None):
     nr = out[s].shape[0]
     bg = bgf(dom.boundary_bg(s, nr - 1))
     a = np.moveaxis(out[s][nr - 1], 0, -1)
-    if dom.outer_bc == "cp":
+    if dom.outer_bc in ("cp", "cp_full"):
         ub = np.moveaxis(u[s][nr - 1], 0, -1)                                    # [th, ph, 50]
         dub = np.moveaxis(spectral.cartesian_gradient(u[s], dom.grids[s])[:, nr - 1], (0, 1), (-2, -1))
-        new = gh.apply_outer_bc_cp(a, ub, dub, bg, dom.gamma1, dom.gamma2)
+        Hb = dHb = None
+        if dom.outer_bc == "cp_full":
+            if bg_map is not None or bg_fn is not None:
+                raise NotImplementedError("the u^- constraint part is defined on a static grid")
+            Hb = np.moveaxis(dom.H[s][nr - 1], 0, -1)                            # [th, ph, 4]
+            dHb = np.moveaxis(dom.dH[s][nr - 1], 0, -1).reshape(Hb.shape[:-1] + (3, 4))
+        new = gh.apply_outer_bc_cp(a, ub, dub, bg, dom.gamma1, dom.gamma2, Hb, dHb)
     else:
         new = gh.apply_outer_bc(a, bg, dom.gamma1, dom.gamma2)
     out[s][nr - 1] = np.moveaxis(new, -1, 0)

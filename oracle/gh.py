@@ -196,12 +196,136 @@ def constraints_pointwise(u, du, H):
     return out
 
 
+def gauge_constraint_derivative(u, v, H, w):
+    """Directional derivative of C_a = H_a + psi^bc Gamma_abc along (v, w).
+
+    u[..., 50] is the state, v[..., 50] a direction in field space (a time
+    derivative or a Cartesian derivative d_i u), H[..., 4] the gauge source and
+    w[..., 4] its derivative along the same direction.  The product rule,
+    term by term (a prime is the derivative along v):
+      psi'^ab = -psi^ac psi'_cd psi^db,
+      N = (-psi^00)^(-1/2)          ->  N' = N^3 psi'^00 / 2,
+      t_c = (-N, 0, 0, 0)           ->  t'_c = (-N', 0, 0, 0),
+      t^i = -N psi^0i               ->  t'^i = -N' psi^0i - N psi'^0i,
+      g^i_c = delta^i_c + t^i t_c   ->  g'^i_c = t'^i t_c + t^i t'_c,
+      d_c psi_ab = t_c Pi_ab + g^i_c Phi_iab, and its prime from the above,
+      C'_a = w_a + psi'^bc Gamma_abc + psi^bc Gamma'_abc,
+    with Gamma'_abc built from the primed d_c psi_ab as Gamma_abc is from d_c psi_ab.
+    """
+    psi, Pi, Phi = unpack_fields(u)
+    dpsi, dPi, dPhi = unpack_fields(v)
+    s = spacetime_split(psi)
+    psi_inv = s["psi_inv"]
+    N = s["alpha"]
+    dpsi_inv = -np.einsum("...ac,...cd,...db->...ab", psi_inv, dpsi, psi_inv)
+    dN = 0.5 * N ** 3 * dpsi_inv[..., 0, 0]
+    dt_dn = np.zeros(N.shape + (4,))
+    dt_dn[..., 0] = -dN
+    t_up_i = s["t_up"][..., 1:]
+    dt_up_i = -dN[..., None] * psi_inv[..., 0, 1:] - N[..., None] * dpsi_inv[..., 0, 1:]
+    dproj = (np.einsum("...i,...c->...ic", dt_up_i, s["t_dn"])
+             + np.einsum("...i,...c->...ic", t_up_i, dt_dn))
+    _, Gam = christoffel_first_kind(s, Pi, Phi)
+    dd = (np.einsum("...c,...ab->...cab", dt_dn, Pi) + np.einsum("...c,...ab->...cab", s["t_dn"], dPi)
+          + np.einsum("...ic,...iab->...cab", dproj, Phi) + np.einsum("...ic,...iab->...cab", s["proj"], dPhi))
+    dGam = 0.5 * (np.einsum("...bac->...abc", dd) + np.einsum("...cab->...abc", dd)
+                  - np.einsum("...abc->...abc", dd))
+    return (w + np.einsum("...bc,...abc->...a", dpsi_inv, Gam)
+            + np.einsum("...bc,...abc->...a", psi_inv, dGam))
+
+
+def boundary_tetrad(bg):
+    """Null vectors and transverse projector of the background at boundary points.
+
+    From the background lapse N, shift beta^i, spatial metric g_ij and unit
+    normal n_i (n^i = g^ij n_j): the unit normal t^a = (1, -beta^i)/N,
+    t_a = (-N, 0, 0, 0); the spacetime normal n^a = (0, n^i),
+    n_a = (beta^i n_i, n_i); the outgoing null vector l = (t + n)/sqrt(2)
+    (both index positions), the incoming k = (t - n)/sqrt(2), and the
+    projector onto the 2-surface orthogonal to both,
+    P_ab = psi_ab + t_a t_b - n_a n_b, with the background 4-metric psi_ab.
+    """
+    N, beta, g, n_dn, n_up = bg["alpha"], bg["beta_up"], bg["g_dn"], bg["n_dn"], bg["n_up"]
+    shp = N.shape
+    beta_dn = np.einsum("...ij,...j->...i", g, beta)
+    psi4 = np.zeros(shp + (4, 4))
+    psi4[..., 0, 0] = -N * N + np.einsum("...i,...i->...", beta, beta_dn)
+    psi4[..., 0, 1:] = beta_dn
+    psi4[..., 1:, 0] = beta_dn
+    psi4[..., 1:, 1:] = g
+    t_dn = np.zeros(shp + (4,))
+    t_dn[..., 0] = -N
+    t_up = np.zeros(shp + (4,))
+    t_up[..., 0] = 1.0 / N
+    t_up[..., 1:] = -beta / N[..., None]
+    n4_dn = np.zeros(shp + (4,))
+    n4_dn[..., 0] = np.einsum("...i,...i->...", beta, n_dn)
+    n4_dn[..., 1:] = n_dn
+    n4_up = np.zeros(shp + (4,))
+    n4_up[..., 1:] = n_up
+    r2 = np.sqrt(0.5)
+    P = psi4 + np.einsum("...a,...b->...ab", t_dn, t_dn) - np.einsum("...a,...b->...ab", n4_dn, n4_dn)
+    return dict(l_dn=r2 * (t_dn + n4_dn), l_up=r2 * (t_up + n4_up), k_dn=r2 * (t_dn - n4_dn),
+                k_up=r2 * (t_up - n4_up), P=P)
+
+
+def uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2):
+    """The u^- time derivative of the constraint-preserving outer condition.
+
+    Reading of the condition on u^- (the paper's outer boundary is constraint
+    preserving, Sec. 5; the GH literature splits u^- into constraint, physical
+    and gauge parts): the gauge constraint C_a may not enter through the
+    boundary, i.e. its derivative along the incoming null direction vanishes,
+        K_a = (t^c - n^c) d_c C_a = (d_t C_a - beta^i d_i C_a) / N - n^i d_i C_a = 0,
+    with d_t C_a taken along the boundary-corrected time derivative of the
+    state.  The u^- time derivative is sought in the 4-dimensional subspace
+        S_ab = l_a lam_b + lam_a l_b + sig P_ab,   l^b lam_b = 0
+    (the l l, l m and transverse-trace parts in a null tetrad (l, k, m, conj m));
+    the remaining six (k k, k m, l k: gauge; the transverse traceless part:
+    physical) stay frozen at zero.  A u^- derivative S changes Pi by S/2 and
+    Phi_i by -n_i S/2 (from_char) and so d_t C_a linearly; the four
+    conditions K_a = 0 and l^b lam_b = 0 fix (lam, sig).
+
+    dudt0[..., 50] is the time derivative with the other families' conditions
+    applied and w^- = 0; u_b, du_b[..., 3, 50] the state and its Cartesian
+    derivatives; H_b[..., 4], dH_b[..., 3, 4] the gauge source and its
+    derivatives; bg the boundary background.  Returns S[..., 4, 4].
+    """
+    tet = boundary_tetrad(bg)
+    N, beta, n_up = bg["alpha"], bg["beta_up"], bg["n_up"]
+    shp = N.shape
+    zero4 = np.zeros(shp + (4,))
+    dtC0 = gauge_constraint_derivative(u_b, dudt0, H_b, zero4)
+    dC = np.stack([gauge_constraint_derivative(u_b, du_b[..., i, :], H_b, dH_b[..., i, :]) for i in range(3)],
+                  axis=-2)                                                     # [..., i, a]
+    K0 = ((dtC0 - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None]
+          - np.einsum("...i,...ia->...a", n_up, dC))
+    l = tet["l_dn"]
+    eye = np.eye(4)
+    basis = [np.einsum("...a,c->...ac", l, eye[b]) + np.einsum("a,...c->...ac", eye[b], l) for b in range(4)]
+    basis.append(tet["P"])
+    z44 = np.zeros(shp + (4, 4))
+    z344 = np.zeros(shp + (3, 4, 4))
+    M = np.zeros(shp + (5, 5))
+    rhs_v = np.zeros(shp + (5,))
+    for j, E in enumerate(basis):
+        v = from_char(z44, z344, z44, E, bg, gamma2)
+        M[..., 0:4, j] = gauge_constraint_derivative(u_b, v, H_b, zero4) / N[..., None]
+    M[..., 4, 0:4] = tet["l_up"]
+    rhs_v[..., 0:4] = -K0
+    x = np.linalg.solve(M, rhs_v[..., None])[..., 0]
+    lam, sig = x[..., 0:4], x[..., 4]
+    return (np.einsum("...a,...b->...ab", l, lam) + np.einsum("...a,...b->...ab", lam, l)
+            + sig[..., None, None] * tet["P"])
+
+
 # ---------------------------------------------------- characteristic fields
 def boundary_background(psi_bg, X, Y, Z):
     """Unit normal and speeds data from the background metric at boundary points.
 
     n_i = d_i R / |d R|_g with R the Euclidean radius, n^i = g^ij n_j.
-    Returns dict with n_dn[...,3], n_up[...,3], alpha, beta_up[...,3].
+    Returns dict with n_dn[...,3], n_up[...,3], alpha, beta_up[...,3] and the
+    spatial metric g_dn[...,3,3].
     """
     s = spacetime_split(psi_bg)
     R = np.sqrt(X * X + Y * Y + Z * Z)
@@ -209,7 +333,7 @@ def boundary_background(psi_bg, X, Y, Z):
     norm = np.sqrt(np.einsum("...ij,...i,...j->...", s["ginv"], dR, dR))
     n_dn = dR / norm[..., None]
     n_up = np.einsum("...ij,...j->...i", s["ginv"], n_dn)
-    return dict(n_dn=n_dn, n_up=n_up, alpha=s["alpha"], beta_up=s["beta_up"])
+    return dict(n_dn=n_dn, n_up=n_up, alpha=s["alpha"], beta_up=s["beta_up"], g_dn=psi_bg[..., 1:, 1:].copy())
 
 
 def char_speeds(bg, gamma1):
@@ -256,9 +380,11 @@ def apply_outer_bc(dudt_b, bg, gamma1, gamma2):
     return from_char(*w, bg, gamma2)
 
 
-def apply_outer_bc_cp(dudt_b, u_b, du_b, bg, gamma1, gamma2):
+def apply_outer_bc_cp(dudt_b, u_b, du_b, bg, gamma1, gamma2, H_b=None, dH_b=None):
     """Constraint-preserving outer condition of Bjorhus form for the u^psi and
-    u^0 families, freezing for u^- (and u^+ if it were incoming).
+    u^0 families; for u^- freezing, or (H_b and dH_b given) the constraint
+    part of uminus_constraint_part with its gauge and physical parts frozen;
+    u^+ frozen if it were incoming.
 
     The outer boundary condition of the paper is constraint preserving (Sec. 5);
     its equations are those of the standard first-order GH system (Lindblom
@@ -285,8 +411,13 @@ def apply_outer_bc_cp(dudt_b, u_b, du_b, bg, gamma1, gamma2):
     inc_0 = (v_0 < 0.0)[..., None, None, None]
     wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)
     w0 = np.where(inc_0, w0 + v_0[..., None, None, None] * Pm, w0)
-    wm = np.where((v_m < 0.0)[..., None, None], 0.0, wm)
     wp = np.where((v_p < 0.0)[..., None, None], 0.0, wp)
+    inc_m = (v_m < 0.0)[..., None, None]
+    if H_b is None:
+        wm = np.where(inc_m, 0.0, wm)
+    else:
+        dudt0 = from_char(wpsi, w0, wp, np.where(inc_m, 0.0, wm), bg, gamma2)
+        wm = np.where(inc_m, uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2), wm)
     return from_char(wpsi, w0, wp, wm, bg, gamma2)
 
 

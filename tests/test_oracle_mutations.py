@@ -13,12 +13,14 @@ import types
 import pytest
 
 import test_oracle_cpbc
+import test_oracle_cpbc_minus
 import test_oracle_dp5
 import test_oracle_frame
 import test_oracle_pins
 import test_oracle_tensor_filter
 
-PIN_MODULES = {"pins": test_oracle_pins, "cpbc": test_oracle_cpbc, "dp5": test_oracle_dp5,
+PIN_MODULES = {"pins": test_oracle_pins, "cpbc": test_oracle_cpbc, "cpbc_minus": test_oracle_cpbc_minus,
+               "dp5": test_oracle_dp5,
                "frame": test_oracle_frame, "tensor_filter": test_oracle_tensor_filter}
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -212,6 +214,24 @@ CASES = {
         "gh", "wpsi = np.where(inc_psi, wpsi + v_psi[..., None, None] * nC3, wpsi)",
         "wpsi = np.where(inc_psi, wpsi - v_psi[..., None, None] * nC3, wpsi)",
         "cpbc::test_constraint_preserving_upsi_removes_the_normal_derivative", ()),
+    # the u^- constraint part of the outer condition (oracle/gh.py)
+    "gauge constraint derivative without the inverse-metric variation": (
+        "gh", 'return (w + np.einsum("...bc,...abc->...a", dpsi_inv, Gam)',
+        'return (w + 0.0 * np.einsum("...bc,...abc->...a", dpsi_inv, Gam)',
+        "cpbc_minus::test_gauge_constraint_derivative_matches_central_differences", ()),
+    "gauge constraint derivative with the lapse variation doubled": (
+        "gh", "dN = 0.5 * N ** 3 * dpsi_inv[..., 0, 0]", "dN = N ** 3 * dpsi_inv[..., 0, 0]",
+        "cpbc_minus::test_gauge_constraint_derivative_matches_central_differences", ()),
+    "incoming null derivative with the shift term's sign flipped": (
+        "gh", "K0 = ((dtC0 - np.einsum(", "K0 = ((dtC0 + np.einsum(",
+        "cpbc_minus::test_incoming_gauge_constraint_derivative_vanishes", ()),
+    "u^- subspace condition on k instead of l": (
+        "gh", 'M[..., 4, 0:4] = tet["l_up"]', 'M[..., 4, 0:4] = tet["k_up"]',
+        "cpbc_minus::test_uminus_derivative_lies_in_the_constraint_subspace", ()),
+    "transverse projector without the t t term": (
+        "gh", 'P = psi4 + np.einsum("...a,...b->...ab", t_dn, t_dn) - np.einsum',
+        'P = psi4 - np.einsum',
+        "cpbc_minus::test_uminus_derivative_lies_in_the_constraint_subspace", ()),
 }
 
 
