@@ -275,10 +275,14 @@ def uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2):
     Reading of the condition on u^- (the paper's outer boundary is constraint
     preserving, Sec. 5; the GH literature splits u^- into constraint, physical
     and gauge parts): the gauge constraint C_a may not enter through the
-    boundary, i.e. its derivative along the incoming null direction vanishes,
-        K_a = (t^c - n^c) d_c C_a = (d_t C_a - beta^i d_i C_a) / N - n^i d_i C_a = 0,
+    boundary.  C_a propagates like a wave, whose incoming characteristic field
+    is its derivative along the outgoing null direction (as u^- = Pi - n.Phi is
+    -(t + n).d psi for psi), so that field is set to zero:
+        K_a = (t^c + n^c) d_c C_a = (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a = 0,
     with d_t C_a taken along the boundary-corrected time derivative of the
-    state.  The u^- time derivative is sought in the 4-dimensional subspace
+    state.  (Along the incoming direction, (t - n).d C_a, the condition would
+    restate the interior equation of u^- and give the incoming mode no
+    boundary data.)  The u^- time derivative is sought in the 4-dimensional subspace
         S_ab = l_a lam_b + lam_a l_b + sig P_ab,   l^b lam_b = 0
     (the l l, l m and transverse-trace parts in a null tetrad (l, k, m, conj m));
     the remaining six (k k, k m, l k: gauge; the transverse traceless part:
@@ -299,7 +303,7 @@ def uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2):
     dC = np.stack([gauge_constraint_derivative(u_b, du_b[..., i, :], H_b, dH_b[..., i, :]) for i in range(3)],
                   axis=-2)                                                     # [..., i, a]
     K0 = ((dtC0 - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None]
-          - np.einsum("...i,...ia->...a", n_up, dC))
+          + np.einsum("...i,...ia->...a", n_up, dC))
     l = tet["l_dn"]
     eye = np.eye(4)
     basis = [np.einsum("...a,c->...ac", l, eye[b]) + np.einsum("a,...c->...ac", eye[b], l) for b in range(4)]

@@ -646,6 +646,8 @@ gh_status adj_ready(gh_domain* d) {
   if (d->map_gen)
     return afail(d, GH_ENOTSUP, "the adjoint supports the static grid and the rotating frame, not a general map");
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
+  if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING_FULL)
+    return afail(d, GH_ENOTSUP, "the adjoint transposes the u^psi and u^0 outer conditions, not the u^- constraint part");
   if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * 40 * (size_t)d->bc_points));

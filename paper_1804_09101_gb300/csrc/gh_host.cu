@@ -1028,6 +1028,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
           bg[(size_t)(3 + i) * sa.na + q] = nh[i];
         }
         bg[(size_t)6 * sa.na + q] = 1.0;
+        for (int m : {10, 13, 15}) bg[(size_t)m * sa.na + q] = 1.0;   // g_ij = delta_ij
       }
     double* bgd = nullptr;
     CREATE_CUDA(upload(d, bg, &bgd));
@@ -1690,6 +1691,8 @@ gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega
   if (!d || !axis) return GH_EINVAL;
   const double n = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
   if (!(n > 0.0) || !std::isfinite(omega)) return fail(d, GH_EINVAL, "need a nonzero axis and a finite rate");
+  if (omega != 0.0 && d->outer_bc == GH_BC_CONSTRAINT_PRESERVING_FULL)
+    return fail(d, GH_ENOTSUP, "the u^- constraint part of the outer condition is defined on a static grid");
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   for (int i = 0; i < 3; ++i) d->rot_axis[i] = axis[i];
   d->rot_omega = omega;
@@ -1721,6 +1724,8 @@ gh_status gh_set_frame_map(gh_domain* d, const double axis[3], double omega, dou
   if (!(n > 0.0) || !std::isfinite(omega) || !std::isfinite(adot) || !std::isfinite(V[0]) || !std::isfinite(V[1]) ||
       !std::isfinite(V[2]))
     return fail(d, GH_EINVAL, "need a nonzero axis and finite rates");
+  if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING_FULL)
+    return fail(d, GH_ENOTSUP, "the u^- constraint part of the outer condition is defined on a static grid");
   for (const auto& sh : d->shells_h)
     if (4 * (size_t)sh.bh + 3 >= d->holes.size() || !(d->holes[4 * sh.bh] > 0.0))
       return fail(d, GH_EINVAL, "the map evaluates each hole at the moving points: set every hole with "
@@ -1804,9 +1809,17 @@ gh_status gh_get_time(const gh_domain* d, double* t) {
 
 gh_status gh_set_outer_bc(gh_domain* d, int mode) {
   if (!d) return GH_EINVAL;
-  if (mode != GH_BC_FREEZE && mode != GH_BC_CONSTRAINT_PRESERVING)
-    return fail(d, GH_EINVAL, "mode must be GH_BC_FREEZE or GH_BC_CONSTRAINT_PRESERVING");
+  if (mode != GH_BC_FREEZE && mode != GH_BC_CONSTRAINT_PRESERVING && mode != GH_BC_CONSTRAINT_PRESERVING_FULL)
+    return fail(d, GH_EINVAL,
+                "mode must be GH_BC_FREEZE, GH_BC_CONSTRAINT_PRESERVING or GH_BC_CONSTRAINT_PRESERVING_FULL");
+  if (mode == GH_BC_CONSTRAINT_PRESERVING_FULL && gh::frame_moving(d))
+    return fail(d, GH_ENOTSUP, "the u^- constraint part of the outer condition is defined on a static grid");
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
+  if (mode == GH_BC_CONSTRAINT_PRESERVING_FULL && !d->cpm_S && d->bc_points) {
+    void* p = nullptr;
+    GH_CUDA(d, alloc_zero(d, sizeof(double) * 10 * (size_t)d->bc_points, &p));
+    d->cpm_S = (double*)p;
+  }
   d->outer_bc = mode;
   if (d->graph_exec) {
     cudaGraphExecDestroy(d->graph_exec);

@@ -13,7 +13,7 @@ namespace gh {
 constexpr int NF = 50;      // evolved fields per point
 constexpr int NC = 64;      // stored constraint components per point
 constexpr int NGAUGE = 16;  // H_a (4) + d_i H_a (12) per point
-constexpr int NBG = 10;     // boundary background per point: n_i, n^i, alpha, beta^i
+constexpr int NBG = 16;     // boundary background per point: n_i, n^i, alpha, beta^i, g_ij (packed xx..zz)
 constexpr int DP_MAX_BLOCKS = 1024;  // blocks of the Dormand-Prince elementwise kernels
 // Dual frame at one instant (Sec. 3.1 dual frame): inertial position
 // x = a R x_grid + T, grid velocity xdot = w x (x - T) + (adot / a)(x - T) + V.
@@ -172,7 +172,7 @@ struct BcSliceDev {
   int shell_a, shell_b;         // shell_b = -1 for the outer boundary
   int na;
   long long off_a, off_b;       // state offset of the boundary r-slice in a / b
-  double* bg;                   // [10][na] n_dn(3) n_up(3) alpha beta_up(3)
+  double* bg;                   // [16][na] n_dn(3) n_up(3) alpha beta_up(3) g_ij(6: xx xy xz yy yz zz)
   double* bg_t;                 // [11][na] the same at the moving points, then n . xdot (general map)
   double dt_scale;              // the hole's step scale (see ShellDev)
   int bh, pad;
@@ -279,8 +279,10 @@ struct gh_domain {
   gh::MapGate* map_gate_d = nullptr;   // reuse of the moving-point buffers between stages at one time
   double time = 0.0;
   gh::Frame fr = {0, 0, {1, 0, 0, 0, 1, 0, 0, 0, 1}, {0, 0, 0}, 1.0, 0.0, {0, 0, 0}, {0, 0, 0}};
-  // outer boundary condition: 0 freezing, 1 constraint preserving (gh_set_outer_bc)
+  // outer boundary condition: 0 freezing, 1 constraint preserving for u^psi and u^0,
+  // 2 also the constraint part of u^- (gh_set_outer_bc)
   int outer_bc = 0;
+  double* cpm_S = nullptr;      // mode 2: d_t u^- per (pair, boundary point), [10][bc_points]
   double* dp_err = nullptr;
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;

@@ -859,6 +859,7 @@ struct BcArgs {
   const double* dph;
   Frame fr;              // rotating frame (fr.on = 0: static)
   const Frame* frd;      // the same frame in device memory (used when set)
+  const double* cpm_S;   // cp_outer = 2: d_t u^- per (pair, boundary point) from cp_minus_kernel
 };
 
 // Bjorhus-form constraint-preserving corrections at an outer-boundary point for
@@ -1020,7 +1021,7 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
       if (v_0 < 0.0) c.w0[0] = c.w0[1] = c.w0[2] = 0.0;
     }
     if (v_p < 0.0) c.wp = 0.0;
-    if (v_m < 0.0) c.wm = 0.0;
+    if (v_m < 0.0) c.wm = (a.cp_outer == 2) ? a.cpm_S[(long long)p * npts + pt] : 0.0;
     double adv[5];
     if (fr.on) frame_adv(a, fr, sl.shell_a, a.shells[sl.shell_a].n_r - 1, base, na, p, q, adv);
     char_write_pair(a, base, na, p, c, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
@@ -1044,6 +1045,311 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
                     fr.on ? adv_a : nullptr);
     char_write_pair(a, bb, na, p, co, n_dn, g2, stage_factor(a.stage) * a.dt * sl.dt_scale,
                     fr.on ? adv_b : nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The constraint part of u^- in the constraint-preserving outer condition
+// (cp_outer = 2).  Reading of Sec. 5's constraint-preserving outer boundary
+// for the u^- family: the gauge constraint C_a = H_a + psi^bc Gamma_abc may
+// not enter through the boundary.  It propagates like a wave, whose incoming
+// characteristic field is its derivative along the outgoing null direction
+// (as u^- is -(t + n).d psi for psi), so
+//   K_a = (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a = 0
+// (background lapse, shift and normal; d_t C_a along the boundary-corrected
+// time derivative of the state, d_i C_a along its Cartesian derivatives and
+// those of H_a).  d_t u^- is sought as S_ab = l_a lam_b + lam_a l_b + sig P_ab
+// with l^b lam_b = 0: the l l, l m and transverse-trace parts of a null tetrad
+// of the background (l = (t + n)/sqrt 2, P the projector orthogonal to t and
+// n); its gauge (k k, k m, l k) and physical (transverse traceless) parts stay
+// frozen.  Changing d_t u^- by S changes d_t Pi by S/2 and d_t Phi_i by
+// -n_i S/2, so K_a is affine in (lam, sig): one 5x5 solve per point.
+
+// The state's part of the directional derivative of C_a: its split and
+// D_cab = d_c psi_ab reconstructed as t_c Pi_ab + g^i_c Phi_iab, i.e.
+// D_0ab = -N Pi_ab + beta^i Phi_iab, D_jab = Phi_jab.
+struct CState {
+  double psi_inv[10];
+  double N;
+  double t_up[3];   // t^i = -beta^i / N
+  double beta[3];
+  double Pi[10];
+  double Phi[30];
+  double D[40];     // D[c * 10 + pair]
+};
+
+// E_a = X^bc (Y_bac - Y_abc / 2) for a symmetric X^bc and Y[c][pair(a, b)]:
+// psi^bc Gamma_abc for Y = D (psi^bc is symmetric, so the two Gamma terms
+// that swap b and c contribute equally).
+__device__ __forceinline__ void contract_gamma(const double X[10], const double* Y, double out[4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        acc = fma(X[sym_index(b, c)], Y[b * 10 + sym_index(a, c)] - 0.5 * Y[a * 10 + sym_index(b, c)], acc);
+    out[a] = acc;
+  }
+}
+
+// C'_a, the derivative of C_a along (dpsi, dPi, dPhi, dH), by the product rule:
+// psi'^ab = -psi^ac psi'_cd psi^db, N' = N^3 psi'^00 / 2,
+// t'^i = -N' psi^0i - N psi'^0i, D'_0ab = -N' Pi_ab - N Pi'_ab
+// + (-N t'^i - N' t^i) Phi_iab + beta^i Phi'_iab, D'_jab = Phi'_jab, and
+// C'_a = H'_a + psi'^bc (D_bac - D_abc / 2) + psi^bc (D'_bac - D'_abc / 2).
+__device__ __noinline__ void gauge_constraint_dir(const CState& s, const double dpsi[10], const double dPi[10],
+                                                  const double dPhi[30], const double dH[4], double out[4]) {
+  double dpi[10];
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    const int A = pair_a(p), B = pair_b(p);
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        acc = fma(s.psi_inv[sym_index(A, c)] * dpsi[sym_index(c, e)], s.psi_inv[sym_index(e, B)], acc);
+    dpi[p] = -acc;
+  }
+  const double N = s.N;
+  const double dN = 0.5 * N * N * N * dpi[0];
+  double g0[3];   // g'^i_0
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double dt = -dN * s.psi_inv[sym_index(0, 1 + i)] - N * dpi[sym_index(0, 1 + i)];
+    g0[i] = -N * dt - dN * s.t_up[i];
+  }
+  double Dp[40];
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    double v = -dN * s.Pi[p] - N * dPi[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v = fma(g0[i], s.Phi[10 * i + p], fma(s.beta[i], dPhi[10 * i + p], v));
+    Dp[p] = v;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Dp[(1 + j) * 10 + p] = dPhi[10 * j + p];
+  }
+  double e1[4], e2[4];
+  contract_gamma(dpi, s.D, e1);
+  contract_gamma(s.psi_inv, Dp, e2);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) out[a] = dH[a] + e1[a] + e2[a];
+}
+
+// One thread per outer-boundary point where u^- is incoming: writes
+// S[pair * npts + point] for bc_kernel (a singular system leaves u^- frozen).
+__global__ void __launch_bounds__(64) cp_minus_kernel(BcArgs a, double* __restrict__ Sout) {
+  const int npts = a.pt_begin[a.n_slices];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npts) return;
+  const int sidx = find_segment(a.pt_begin, a.n_slices, t);
+  const BcSliceDev& sl = a.slices[sidx];
+  if (sl.kind != 0) return;
+  const int q = t - a.pt_begin[sidx];
+  const int na = sl.na;
+  const double* bg = sl.bg;
+  double n_dn[3], n_up[3], bb[3], gb[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    n_dn[i] = bg[(long long)i * na + q];
+    n_up[i] = bg[(long long)(3 + i) * na + q];
+    bb[i] = bg[(long long)(7 + i) * na + q];
+  }
+  const double Nb = bg[(long long)6 * na + q];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) gb[m] = bg[(long long)(10 + m) * na + q];
+  const double nb = n_dn[0] * bb[0] + n_dn[1] * bb[1] + n_dn[2] * bb[2];
+  const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + Nb, v_m = -nb - Nb;
+  if (!(v_m < 0.0)) return;
+  const double g2 = a.gamma2;
+  const ShellDev& sh = a.shells[sl.shell_a];
+  PointGeom G;
+  point_geom(sh, sh.n_r - 1, q, G);
+  const long long base = sl.off_a + q;
+  auto cart = [&](int f, int i) {
+    const long long o = base + (long long)f * na;
+    return fma(G.J[i][2], a.dph[o], fma(G.J[i][1], a.dth[o], G.J[i][0] * a.dr[o]));
+  };
+  auto U = [&](int f) { return a.u_in[base + (long long)f * na]; };
+
+  CState cs;
+  {
+    double psi[10];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) psi[p] = U(p);
+    Split S;
+    spacetime_split(psi, S);
+#pragma unroll
+    for (int p = 0; p < 10; ++p) cs.psi_inv[p] = S.psi_inv[p];
+    cs.N = S.alpha;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cs.t_up[i] = S.t_up[1 + i];
+      cs.beta[i] = S.beta_up[i];
+    }
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      cs.Pi[p] = U(10 + p);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) cs.Phi[10 * i + p] = U(20 + 10 * i + p);
+    }
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      double v = -cs.N * cs.Pi[p];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v = fma(cs.beta[i], cs.Phi[10 * i + p], v);
+      cs.D[p] = v;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cs.D[(1 + j) * 10 + p] = cs.Phi[10 * j + p];
+    }
+  }
+  const double zero4[4] = {0.0, 0.0, 0.0, 0.0};
+  double K[4];
+  {
+    // the time derivative with the u^psi, u^0 and u^+ conditions applied and w^- = 0
+    double upsi[10], uPi[10], uPhi[30];
+#pragma unroll 1
+    for (int p = 0; p < 10; ++p) {
+      const double ps = a.k[base + (long long)p * na];
+      const double pi = a.k[base + (long long)(10 + p) * na];
+      double ph[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ph[i] = a.k[base + (long long)(20 + 10 * i + p) * na];
+      const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
+      double wpsi = ps, wp = pi + nphi - g2 * ps, w0[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w0[i] = ph[i] - n_dn[i] * nphi;
+      if (v_psi < 0.0) {
+        double nC3 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) nC3 = fma(n_up[i], cart(p, i) - U(20 + 10 * i + p), nC3);
+        wpsi = fma(v_psi, nC3, wpsi);
+      }
+      if (v_0 < 0.0) {
+        double m[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          double acc = 0.0;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc = fma(n_up[j], cart(20 + 10 * kk + p, j) - cart(20 + 10 * j + p, kk), acc);
+          m[kk] = acc;
+        }
+        const double nm = n_up[0] * m[0] + n_up[1] * m[1] + n_up[2] * m[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w0[i] = fma(v_0, m[i] - n_dn[i] * nm, w0[i]);
+      }
+      if (v_p < 0.0) wp = 0.0;
+      upsi[p] = wpsi;
+      uPi[p] = 0.5 * wp + g2 * wpsi;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) uPhi[10 * i + p] = n_dn[i] * (0.5 * wp) + w0[i];
+    }
+    double dtC[4];
+    gauge_constraint_dir(cs, upsi, uPi, uPhi, zero4, dtC);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) K[c] = dtC[c] / Nb;
+  }
+  const double* gauge = sh.gauge + (long long)(sh.n_r - 1) * NGAUGE * na + q;
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    double dpsi[10], dPi[10], dPhi[30], dH[4], dC[4];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      dpsi[p] = cart(p, i);
+      dPi[p] = cart(10 + p, i);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dPhi[10 * j + p] = cart(20 + 10 * j + p, i);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dH[c] = gauge[(long long)(4 + 4 * i + c) * na];
+    gauge_constraint_dir(cs, dpsi, dPi, dPhi, dH, dC);
+    const double w = n_up[i] - bb[i] / Nb;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) K[c] = fma(w, dC[c], K[c]);
+  }
+  // the background tetrad: l_a, l^a and P_ab
+  const double r2 = 0.70710678118654752440;
+  double bdn[3];   // beta_i
+  bdn[0] = gb[0] * bb[0] + gb[1] * bb[1] + gb[2] * bb[2];
+  bdn[1] = gb[1] * bb[0] + gb[3] * bb[1] + gb[4] * bb[2];
+  bdn[2] = gb[2] * bb[0] + gb[4] * bb[1] + gb[5] * bb[2];
+  const double n4[4] = {nb, n_dn[0], n_dn[1], n_dn[2]};
+  const double l_dn[4] = {r2 * (-Nb + nb), r2 * n_dn[0], r2 * n_dn[1], r2 * n_dn[2]};
+  const double l_up[4] = {r2 / Nb, r2 * (n_up[0] - bb[0] / Nb), r2 * (n_up[1] - bb[1] / Nb),
+                          r2 * (n_up[2] - bb[2] / Nb)};
+  double P[10];
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    const int A = pair_a(p), B = pair_b(p);
+    double psib;
+    if (A == 0 && B == 0) psib = -Nb * Nb + bb[0] * bdn[0] + bb[1] * bdn[1] + bb[2] * bdn[2];
+    else if (A == 0) psib = bdn[B - 1];
+    else psib = gb[s3(A - 1, B - 1)];
+    P[p] = psib + ((A == 0 && B == 0) ? Nb * Nb : 0.0) - n4[A] * n4[B];
+  }
+  // columns: d_t u^- = E_j changes Pi by E/2 and Phi_k by -n_k E/2, so
+  // D'_0ab = -(N + beta^k n_k) E_ab / 2, D'_kab = -n_k E_ab / 2 (psi' = 0)
+  double M[5][6];
+  const double c0 = -0.5 * (cs.N + cs.beta[0] * n_dn[0] + cs.beta[1] * n_dn[1] + cs.beta[2] * n_dn[2]);
+#pragma unroll 1
+  for (int j = 0; j < 5; ++j) {
+    double E[10];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      const int A = pair_a(p), B = pair_b(p);
+      E[p] = (j < 4) ? ((B == j ? l_dn[A] : 0.0) + (A == j ? l_dn[B] : 0.0)) : P[p];
+    }
+    double Dp[40], col[4];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      Dp[p] = c0 * E[p];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) Dp[(1 + kk) * 10 + p] = -0.5 * n_dn[kk] * E[p];
+    }
+    contract_gamma(cs.psi_inv, Dp, col);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) M[c][j] = col[c] / Nb;
+    M[4][j] = (j < 4) ? l_up[j] : 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) M[c][5] = -K[c];
+  M[4][5] = 0.0;
+  // Gaussian elimination with partial pivoting
+  bool ok = true;
+#pragma unroll 1
+  for (int c = 0; c < 5 && ok; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 5; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (!(fabs(M[piv][c]) > 0.0)) {
+      ok = false;
+      break;
+    }
+    if (piv != c)
+      for (int e = 0; e < 6; ++e) {
+        const double tmp = M[c][e];
+        M[c][e] = M[piv][e];
+        M[piv][e] = tmp;
+      }
+    for (int r = c + 1; r < 5; ++r) {
+      const double f = M[r][c] / M[c][c];
+      for (int e = c; e < 6; ++e) M[r][e] -= f * M[c][e];
+    }
+  }
+  double x[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (ok) {
+    for (int r = 4; r >= 0; --r) {
+      double v = M[r][5];
+      for (int e = r + 1; e < 5; ++e) v -= M[r][e] * x[e];
+      x[r] = v / M[r][r];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    const int A = pair_a(p), B = pair_b(p);
+    Sout[(long long)p * npts + t] = l_dn[A] * x[B] + x[A] * l_dn[B] + x[4] * P[p];
   }
 }
 
@@ -1085,6 +1391,8 @@ bc_background_kernel(const ShellDev* __restrict__ shells, BcSliceDev* slices, in
     sl.bg[(long long)(7 + i) * na + q] = S.beta_up[i];
   }
   sl.bg[(long long)6 * na + q] = S.alpha;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) sl.bg[(long long)(10 + m) * na + q] = psi[4 + m];   // g_ij, pairs 11 12 13 22 23 33
 }
 
 // ---------------------------------------------------------------------------
@@ -1295,7 +1603,13 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
   a.dph = deriv ? deriv[2] : d->d_ph;
   a.fr = d->fr;
   a.frd = d->fr.on ? d->frd : nullptr;
+  a.cpm_S = d->cpm_S;
   if (a.cp_outer && !u_in) return cudaErrorInvalidValue;
+  if (a.cp_outer == 2) {
+    if (!d->cpm_S || d->fr.on) return cudaErrorInvalidValue;
+    cp_minus_kernel<<<cdiv(d->bc_points, 64), 64, 0, d->stream>>>(a, d->cpm_S);
+    d->launches++;
+  }
   bc_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(a);
   d->launches++;
   return cudaGetLastError();

@@ -328,7 +328,7 @@ def gh_set_algorithm(dom, algorithm):
     dom._check(_lib.gh_set_algorithm(dom.handle, int(algorithm)))
 
 
-GH_BC_FREEZE, GH_BC_CONSTRAINT_PRESERVING = 0, 1
+GH_BC_FREEZE, GH_BC_CONSTRAINT_PRESERVING, GH_BC_CONSTRAINT_PRESERVING_FULL = 0, 1, 2
 GH_SH_FILTER_COMPONENT, GH_SH_FILTER_TENSOR = 0, 1
 
 
@@ -364,7 +364,8 @@ def gh_get_time(dom):
 
 
 def gh_set_outer_bc(dom, mode):
-    """gh_set_outer_bc: outer condition code, freezing (0) or constraint preserving (1)."""
+    """gh_set_outer_bc: outer condition code: freezing (0), constraint preserving for u^psi and u^0 (1),
+    and also the constraint part of u^- (2)."""
     dom._stream()
     dom._check(_lib.gh_set_outer_bc(dom.handle, int(mode)))
 

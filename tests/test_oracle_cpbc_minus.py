@@ -6,9 +6,10 @@ the reading is in ``oracle.gh.uminus_constraint_part``) against what fixes it:
    derivative of the oracle's own C_a: central differences of
    ``constraints_pointwise`` along random directions.
 2. The defining property: with the condition applied, the gauge constraint's
-   derivative along the incoming null direction, with d_t C_a taken by central
-   differences of C_a along the full boundary-corrected right-hand side,
-   vanishes at every outer point; with u^- frozen it does not.
+   incoming characteristic field, its derivative along the outgoing null
+   direction (t + n), with d_t C_a taken by central differences of C_a along
+   the full boundary-corrected right-hand side, vanishes at every outer point;
+   with u^- frozen it does not.
 3. The u^- time derivative lies in the constraint subspace: S_ab l^b = 0 and
    its transverse traceless part vanishes (the gauge and physical parts stay
    frozen), with the null tetrad built here from the background's lapse,
@@ -89,7 +90,7 @@ def test_gauge_constraint_derivative_matches_central_differences():
 
 
 def _incoming_derivative(dom, u, dudt):
-    """(t^c - n^c) d_c C_a at the outer points: d_t C_a by central differences
+    """(t^c + n^c) d_c C_a at the outer points: d_t C_a by central differences
     along the right-hand side, d_i C_a along the Cartesian derivatives."""
     bg, ub, dub, Hb, dHb = _outer_data(dom, u)
     k = _moveto(dudt[-1][-1])
@@ -97,7 +98,7 @@ def _incoming_derivative(dom, u, dudt):
     dtC = (_C(ub + h * k, Hb) - _C(ub - h * k, Hb)) / (2 * h)
     dC = np.stack([gh.gauge_constraint_derivative(ub, dub[..., i, :], Hb, dHb[..., i, :]) for i in range(3)], -2)
     N, beta, n_up = bg["alpha"], bg["beta_up"], bg["n_up"]
-    return (dtC - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None] - np.einsum("...i,...ia->...a", n_up, dC)
+    return (dtC - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None] + np.einsum("...i,...ia->...a", n_up, dC)
 
 
 def test_incoming_gauge_constraint_derivative_vanishes():

@@ -225,6 +225,10 @@ CASES = {
     "incoming null derivative with the shift term's sign flipped": (
         "gh", "K0 = ((dtC0 - np.einsum(", "K0 = ((dtC0 + np.einsum(",
         "cpbc_minus::test_incoming_gauge_constraint_derivative_vanishes", ()),
+    "incoming constraint field along the incoming null direction": (
+        "gh", """          + np.einsum("...i,...ia->...a", n_up, dC))""",
+        """          - np.einsum("...i,...ia->...a", n_up, dC))""",
+        "cpbc_minus::test_incoming_gauge_constraint_derivative_vanishes", ()),
     "u^- subspace condition on k instead of l": (
         "gh", 'M[..., 4, 0:4] = tet["l_up"]', 'M[..., 4, 0:4] = tet["k_up"]',
         "cpbc_minus::test_uminus_derivative_lies_in_the_constraint_subspace", ()),
