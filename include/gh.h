@@ -362,15 +362,18 @@ gh_status gh_get_time(const gh_domain* dom, double* t);
  *   u^- is frozen.  The adjoint entry points transpose these terms (they are
  *   linear in u and its derivatives for the fixed background).
  * GH_BC_CONSTRAINT_PRESERVING_FULL: as GH_BC_CONSTRAINT_PRESERVING, and u^-
- *   no longer frozen: the gauge constraint C_a = H_a + Gamma_a may not enter,
- *   its incoming characteristic field (its derivative along the outgoing null
- *   direction) vanishes, (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a = 0 at every outer point
- *   (background N, beta, n), with d_t u^- taken in the span of the l l, l m
- *   and transverse-trace parts of the background null tetrad
- *   (l = (t + n)/sqrt 2) and its gauge and transverse-traceless parts frozen;
- *   one 5x5 solve per outer point (a singular system leaves u^- frozen there).
- *   Static grid only: GH_ENOTSUP with a rotating frame or a general map (set
- *   either way round); the adjoint entry points return GH_ENOTSUP.
+ *   no longer frozen: the gauge constraint C_a = H_a + Gamma_a may not enter.
+ *   Its incoming characteristic field, K_a = (d_t C_a - beta^i d_i C_a) / N
+ *   + n^i d_i C_a (its derivative along the outgoing null direction;
+ *   background N, beta, n), holds the normal derivative of u^-; in Bjorhus
+ *   form that normal derivative is replaced in the u^- equation by the value
+ *   for which K_a, with the interior equations, vanishes.  d_t u^- is taken in
+ *   the span of the l l, l m and transverse-trace parts of the background null
+ *   tetrad (l = (t + n)/sqrt 2), with its gauge and transverse-traceless parts
+ *   frozen: one 5x5 solve per outer point (a singular system leaves u^-
+ *   frozen there).  Static grid only: GH_ENOTSUP with a rotating frame or a
+ *   general map (set either way round); the adjoint entry points return
+ *   GH_ENOTSUP.
  * Synchronises the stream and discards a captured RK4 graph. */
 enum { GH_BC_FREEZE = 0, GH_BC_CONSTRAINT_PRESERVING = 1, GH_BC_CONSTRAINT_PRESERVING_FULL = 2 };
 gh_status gh_set_outer_bc(gh_domain* dom, int mode);

@@ -269,7 +269,7 @@ def boundary_tetrad(bg):
                 k_up=r2 * (t_up - n4_up), P=P)
 
 
-def uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2):
+def uminus_constraint_part(dudt0, dudt_int, u_b, du_b, H_b, dH_b, bg, gamma2):
     """The u^- time derivative of the constraint-preserving outer condition.
 
     Reading of the condition on u^- (the paper's outer boundary is constraint
@@ -277,33 +277,50 @@ def uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2):
     and gauge parts): the gauge constraint C_a may not enter through the
     boundary.  C_a propagates like a wave, whose incoming characteristic field
     is its derivative along the outgoing null direction (as u^- = Pi - n.Phi is
-    -(t + n).d psi for psi), so that field is set to zero:
-        K_a = (t^c + n^c) d_c C_a = (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a = 0,
-    with d_t C_a taken along the boundary-corrected time derivative of the
-    state.  (Along the incoming direction, (t - n).d C_a, the condition would
-    restate the interior equation of u^- and give the incoming mode no
-    boundary data.)  The u^- time derivative is sought in the 4-dimensional subspace
-        S_ab = l_a lam_b + lam_a l_b + sig P_ab,   l^b lam_b = 0
-    (the l l, l m and transverse-trace parts in a null tetrad (l, k, m, conj m));
-    the remaining six (k k, k m, l k: gauge; the transverse traceless part:
-    physical) stay frozen at zero.  A u^- derivative S changes Pi by S/2 and
-    Phi_i by -n_i S/2 (from_char) and so d_t C_a linearly; the four
-    conditions K_a = 0 and l^b lam_b = 0 fix (lam, sig).
+    -(t + n).d psi for psi):
+        K_a = (t^c + n^c) d_c C_a = (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a.
+    Evaluated with the interior equations it holds the normal derivative of
+    u^- as 2 B(d_n u^-), B the linear map from a u^- derivative to d_t C_a / N
+    (a u^- derivative S changes Pi by S/2 and Phi_i by -n_i S/2, from_char).
+    In the Bjorhus form the condition replaces that normal derivative in the
+    u^- equation, d_t u^- = -v_- d_n u^- + ..., by the value for which K_a,
+    with the interior equations, vanishes:
+        d_t u^- = D_t u^- + (v_- / 2) B^-1 K_a[interior],   v_- = -n.beta - N,
+    so the boundary equation of u^- no longer holds its own normal derivative.
+    In terms of K_a[w] taken along a time derivative whose u^- part is w
+    (K_a is affine in w, with slope B): B(S) = -K_a[0] + (N - n.beta)/(2N) K_a[D_t u^-],
+    where the normal-derivative parts of the two terms cancel.  (Zeroing K_a
+    along the corrected time derivative instead leaves -N d_n u^- in the
+    boundary equation, upwinded against the incoming direction; along the
+    incoming null direction, (t - n).d C_a, it restates the interior equation.)
 
-    dudt0[..., 50] is the time derivative with the other families' conditions
-    applied and w^- = 0; u_b, du_b[..., 3, 50] the state and its Cartesian
-    derivatives; H_b[..., 4], dH_b[..., 3, 4] the gauge source and its
-    derivatives; bg the boundary background.  Returns S[..., 4, 4].
+    S is sought in the 4-dimensional subspace
+        S_ab = l_a lam_b + lam_a l_b + sig P_ab,   l^b lam_b = 0
+    (the l l, l m and transverse-trace parts in a null tetrad (l, k, m, conj m)),
+    on which B is invertible; the remaining six (k k, k m, l k: gauge; the
+    transverse traceless part: physical) lie in the kernel of B and stay frozen
+    at zero.  Four conditions and l^b lam_b = 0 fix (lam, sig).
+
+    dudt0[..., 50] and dudt_int[..., 50] are the time derivative with the other
+    families' conditions applied and w^- = 0, resp. w^- = D_t u^- (interior);
+    u_b, du_b[..., 3, 50] the state and its Cartesian derivatives; H_b[..., 4],
+    dH_b[..., 3, 4] the gauge source and its derivatives; bg the boundary
+    background (N, beta, n).  Returns S[..., 4, 4].
     """
     tet = boundary_tetrad(bg)
     N, beta, n_up = bg["alpha"], bg["beta_up"], bg["n_up"]
     shp = N.shape
     zero4 = np.zeros(shp + (4,))
-    dtC0 = gauge_constraint_derivative(u_b, dudt0, H_b, zero4)
     dC = np.stack([gauge_constraint_derivative(u_b, du_b[..., i, :], H_b, dH_b[..., i, :]) for i in range(3)],
                   axis=-2)                                                     # [..., i, a]
-    K0 = ((dtC0 - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None]
-          + np.einsum("...i,...ia->...a", n_up, dC))
+
+    def K(dudt):
+        dtC = gauge_constraint_derivative(u_b, dudt, H_b, zero4)
+        return ((dtC - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None]
+                + np.einsum("...i,...ia->...a", n_up, dC))
+
+    nb = np.einsum("...i,...i->...", bg["n_dn"], beta)
+    target = -K(dudt0) + ((N - nb) / (2.0 * N))[..., None] * K(dudt_int)
     l = tet["l_dn"]
     eye = np.eye(4)
     basis = [np.einsum("...a,c->...ac", l, eye[b]) + np.einsum("a,...c->...ac", eye[b], l) for b in range(4)]
@@ -316,7 +333,7 @@ def uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2):
         v = from_char(z44, z344, z44, E, bg, gamma2)
         M[..., 0:4, j] = gauge_constraint_derivative(u_b, v, H_b, zero4) / N[..., None]
     M[..., 4, 0:4] = tet["l_up"]
-    rhs_v[..., 0:4] = -K0
+    rhs_v[..., 0:4] = target
     x = np.linalg.solve(M, rhs_v[..., None])[..., 0]
     lam, sig = x[..., 0:4], x[..., 4]
     return (np.einsum("...a,...b->...ab", l, lam) + np.einsum("...a,...b->...ab", lam, l)
@@ -420,8 +437,9 @@ def apply_outer_bc_cp(dudt_b, u_b, du_b, bg, gamma1, gamma2, H_b=None, dH_b=None
     if H_b is None:
         wm = np.where(inc_m, 0.0, wm)
     else:
-        dudt0 = from_char(wpsi, w0, wp, np.where(inc_m, 0.0, wm), bg, gamma2)
-        wm = np.where(inc_m, uminus_constraint_part(dudt0, u_b, du_b, H_b, dH_b, bg, gamma2), wm)
+        dudt0 = from_char(wpsi, w0, wp, np.zeros_like(wm), bg, gamma2)
+        dudt_i = from_char(wpsi, w0, wp, wm, bg, gamma2)
+        wm = np.where(inc_m, uminus_constraint_part(dudt0, dudt_i, u_b, du_b, H_b, dH_b, bg, gamma2), wm)
     return from_char(wpsi, w0, wp, wm, bg, gamma2)
 
 

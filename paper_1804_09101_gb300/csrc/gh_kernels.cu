@@ -1054,63 +1054,93 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
 // for the u^- family: the gauge constraint C_a = H_a + psi^bc Gamma_abc may
 // not enter through the boundary.  It propagates like a wave, whose incoming
 // characteristic field is its derivative along the outgoing null direction
-// (as u^- is -(t + n).d psi for psi), so
-//   K_a = (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a = 0
-// (background lapse, shift and normal; d_t C_a along the boundary-corrected
-// time derivative of the state, d_i C_a along its Cartesian derivatives and
-// those of H_a).  d_t u^- is sought as S_ab = l_a lam_b + lam_a l_b + sig P_ab
-// with l^b lam_b = 0: the l l, l m and transverse-trace parts of a null tetrad
-// of the background (l = (t + n)/sqrt 2, P the projector orthogonal to t and
-// n); its gauge (k k, k m, l k) and physical (transverse traceless) parts stay
-// frozen.  Changing d_t u^- by S changes d_t Pi by S/2 and d_t Phi_i by
-// -n_i S/2, so K_a is affine in (lam, sig): one 5x5 solve per point.
+// (as u^- is -(t + n).d psi for psi),
+//   K_a = (d_t C_a - beta^i d_i C_a) / N + n^i d_i C_a
+// (background lapse, shift and normal; d_t C_a along a time derivative of the
+// state, d_i C_a along its Cartesian derivatives and those of H_a).  With the
+// interior equations K_a holds the normal derivative of u^- as 2 B(d_n u^-),
+// B the slope of K_a in d_t u^- (a u^- derivative S changes d_t Pi by S/2 and
+// d_t Phi_i by -n_i S/2).  In Bjorhus form the condition replaces d_n u^- in
+// the u^- equation by the value that makes K_a (interior) vanish, so the
+// boundary equation of u^- holds no normal derivative of u^-:
+//   B(S) = -K_a[w^- = 0] + (N - n.beta) / (2N) K_a[w^- = D_t u^-].
+// S is sought as l_a lam_b + lam_a l_b + sig P_ab with l^b lam_b = 0: the
+// l l, l m and transverse-trace parts of a null tetrad of the background
+// (l = (t + n)/sqrt 2, P the projector orthogonal to t and n), on which B is
+// invertible; its gauge (k k, k m, l k) and physical (transverse traceless)
+// parts lie in the kernel of B and stay frozen.  One 5x5 solve per point.
 
-// The state's part of the directional derivative of C_a: its split and
-// D_cab = d_c psi_ab reconstructed as t_c Pi_ab + g^i_c Phi_iab, i.e.
-// D_0ab = -N Pi_ab + beta^i Phi_iab, D_jab = Phi_jab.
-struct CState {
-  double psi_inv[10];
-  double N;
-  double t_up[3];   // t^i = -beta^i / N
-  double beta[3];
-  double Pi[10];
-  double Phi[30];
-  double D[40];     // D[c * 10 + pair]
+// Three outer-boundary points per warp where u^- is incoming (CPM_WARPS warps
+// per block); each point's data lives in shared memory:
+//   u, k       the state and its interior right-hand side (50 fields each),
+//   du[i]      the Cartesian derivatives d_i u,
+//   psi_inv, N, t^i, beta^i and D_cab = d_c psi_ab reconstructed from the
+//              state as t_c Pi_ab + g^i_c Phi_iab (D_0ab = -N Pi_ab +
+//              beta^i Phi_iab, D_jab = Phi_jab),
+//   ud         the time derivative with the u^psi, u^0, u^+ conditions and w^- = 0,
+//   wm_int     the interior d_t u^- per pair,
+//   l_dn, l_up, P  the background null vector and transverse projector,
+//   res[e]     the ten directional derivatives of C_a (see cp_minus_kernel).
+#ifndef GH_CPM_WARPS
+#define GH_CPM_WARPS 2
+#endif
+constexpr int CPM_WARPS = GH_CPM_WARPS;
+
+struct CpmWarp {
+  double u[50], k[50], du[3][50];
+  double psi_inv[10], t_up[3], beta[3], N;
+  double D[40];
+  double ud[50];
+  double wm_int[10];
+  double l_dn[4], l_up[4], P[10];
+  double vdir[6][50];   // the field-space directions of the slope evaluations (w^- = E)
+  double res[10][4];
+  double x[5];
 };
 
 // E_a = X^bc (Y_bac - Y_abc / 2) for a symmetric X^bc and Y[c][pair(a, b)]:
 // psi^bc Gamma_abc for Y = D (psi^bc is symmetric, so the two Gamma terms
-// that swap b and c contribute equally).
-__device__ __forceinline__ void contract_gamma(const double X[10], const double* Y, double out[4]) {
+// that swap b and c contribute equally).  The second sum runs over the ten
+// pairs (off-diagonal ones twice).
+__device__ __forceinline__ void contract_gamma(const double* X, const double* Y, double out[4]) {
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    double acc = 0.0;
+    double s1 = 0.0, s2 = 0.0;
 #pragma unroll
     for (int b = 0; b < 4; ++b)
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        acc = fma(X[sym_index(b, c)], Y[b * 10 + sym_index(a, c)] - 0.5 * Y[a * 10 + sym_index(b, c)], acc);
-    out[a] = acc;
+      for (int c = 0; c < 4; ++c) s1 = fma(X[sym_index(b, c)], Y[b * 10 + sym_index(a, c)], s1);
+#pragma unroll
+    for (int p = 0; p < 10; ++p) s2 = fma(pair_a(p) == pair_b(p) ? X[p] : 2.0 * X[p], Y[a * 10 + p], s2);
+    out[a] = fma(-0.5, s2, s1);
   }
 }
 
-// C'_a, the derivative of C_a along (dpsi, dPi, dPhi, dH), by the product rule:
+// C'_a, the derivative of C_a = H_a + psi^bc Gamma_abc along a field-space
+// direction v (50 fields: psi', Pi', Phi') and H', by the product rule:
 // psi'^ab = -psi^ac psi'_cd psi^db, N' = N^3 psi'^00 / 2,
 // t'^i = -N' psi^0i - N psi'^0i, D'_0ab = -N' Pi_ab - N Pi'_ab
 // + (-N t'^i - N' t^i) Phi_iab + beta^i Phi'_iab, D'_jab = Phi'_jab, and
 // C'_a = H'_a + psi'^bc (D_bac - D_abc / 2) + psi^bc (D'_bac - D'_abc / 2).
-__device__ __noinline__ void gauge_constraint_dir(const CState& s, const double dpsi[10], const double dPi[10],
-                                                  const double dPhi[30], const double dH[4], double out[4]) {
+__device__ __noinline__ void gauge_constraint_dir(const CpmWarp& s, const double* v, const double dH[4],
+                                                  double out[4]) {
+  double Mi[4][4];   // psi^ac psi'_cd
+#pragma unroll
+  for (int A = 0; A < 4; ++A)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(s.psi_inv[sym_index(A, c)], v[sym_index(c, e)], acc);
+      Mi[A][e] = acc;
+    }
   double dpi[10];
 #pragma unroll
   for (int p = 0; p < 10; ++p) {
     const int A = pair_a(p), B = pair_b(p);
     double acc = 0.0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        acc = fma(s.psi_inv[sym_index(A, c)] * dpsi[sym_index(c, e)], s.psi_inv[sym_index(e, B)], acc);
+    for (int e = 0; e < 4; ++e) acc = fma(Mi[A][e], s.psi_inv[sym_index(e, B)], acc);
     dpi[p] = -acc;
   }
   const double N = s.N;
@@ -1124,12 +1154,12 @@ __device__ __noinline__ void gauge_constraint_dir(const CState& s, const double 
   double Dp[40];
 #pragma unroll
   for (int p = 0; p < 10; ++p) {
-    double v = -dN * s.Pi[p] - N * dPi[p];
+    double w = -dN * s.u[10 + p] - N * v[10 + p];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v = fma(g0[i], s.Phi[10 * i + p], fma(s.beta[i], dPhi[10 * i + p], v));
-    Dp[p] = v;
+    for (int i = 0; i < 3; ++i) w = fma(g0[i], s.u[20 + 10 * i + p], fma(s.beta[i], v[20 + 10 * i + p], w));
+    Dp[p] = w;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Dp[(1 + j) * 10 + p] = dPhi[10 * j + p];
+    for (int j = 0; j < 3; ++j) Dp[(1 + j) * 10 + p] = v[20 + 10 * j + p];
   }
   double e1[4], e2[4];
   contract_gamma(dpi, s.D, e1);
@@ -1138,218 +1168,253 @@ __device__ __noinline__ void gauge_constraint_dir(const CState& s, const double 
   for (int a = 0; a < 4; ++a) out[a] = dH[a] + e1[a] + e2[a];
 }
 
-// One thread per outer-boundary point where u^- is incoming: writes
-// S[pair * npts + point] for bc_kernel (a singular system leaves u^- frozen).
-__global__ void __launch_bounds__(64) cp_minus_kernel(BcArgs a, double* __restrict__ Sout) {
+// Three outer-boundary points per warp, ten lanes each (lanes 30 and 31 idle),
+// where u^- is incoming: writes S[pair * npts + point] for bc_kernel (a
+// singular system leaves u^- frozen).  The ten lanes of a point evaluate, one
+// each, the directional derivatives of C_a that the solve needs: along the
+// corrected time derivative with w^- = 0 (e = 0), along d_i u with d_i H
+// (e = 1..3), and the slope B along the four l_(a e_b) basis tensors, P and
+// the interior w^- (e = 4..9); lane e = 0 solves.  Every lane reaches every
+// __syncwarp; a group without a point (or where u^- is not incoming) idles.
+__global__ void __launch_bounds__(32 * CPM_WARPS) cp_minus_kernel(BcArgs a, double* __restrict__ Sout) {
+  __shared__ CpmWarp smem[3 * CPM_WARPS];
+  const int warp = threadIdx.x >> 5, lane0 = threadIdx.x & 31;
+  const int sub = lane0 / 10, lane = lane0 - 10 * sub;
   const int npts = a.pt_begin[a.n_slices];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= npts) return;
-  const int sidx = find_segment(a.pt_begin, a.n_slices, t);
+  const int t = (blockIdx.x * CPM_WARPS + warp) * 3 + sub;
+  bool active = sub < 3 && t < npts;
+  const int sidx = active ? find_segment(a.pt_begin, a.n_slices, t) : 0;
   const BcSliceDev& sl = a.slices[sidx];
-  if (sl.kind != 0) return;
-  const int q = t - a.pt_begin[sidx];
+  active = active && sl.kind == 0;
+  const int q = active ? t - a.pt_begin[sidx] : 0;
   const int na = sl.na;
   const double* bg = sl.bg;
-  double n_dn[3], n_up[3], bb[3], gb[6];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    n_dn[i] = bg[(long long)i * na + q];
-    n_up[i] = bg[(long long)(3 + i) * na + q];
-    bb[i] = bg[(long long)(7 + i) * na + q];
-  }
-  const double Nb = bg[(long long)6 * na + q];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) gb[m] = bg[(long long)(10 + m) * na + q];
-  const double nb = n_dn[0] * bb[0] + n_dn[1] * bb[1] + n_dn[2] * bb[2];
-  const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + Nb, v_m = -nb - Nb;
-  if (!(v_m < 0.0)) return;
-  const double g2 = a.gamma2;
-  const ShellDev& sh = a.shells[sl.shell_a];
-  PointGeom G;
-  point_geom(sh, sh.n_r - 1, q, G);
-  const long long base = sl.off_a + q;
-  auto cart = [&](int f, int i) {
-    const long long o = base + (long long)f * na;
-    return fma(G.J[i][2], a.dph[o], fma(G.J[i][1], a.dth[o], G.J[i][0] * a.dr[o]));
-  };
-  auto U = [&](int f) { return a.u_in[base + (long long)f * na]; };
-
-  CState cs;
-  {
-    double psi[10];
-#pragma unroll
-    for (int p = 0; p < 10; ++p) psi[p] = U(p);
-    Split S;
-    spacetime_split(psi, S);
-#pragma unroll
-    for (int p = 0; p < 10; ++p) cs.psi_inv[p] = S.psi_inv[p];
-    cs.N = S.alpha;
+  double n_dn[3] = {1.0, 0.0, 0.0}, n_up[3] = {1.0, 0.0, 0.0}, bb[3] = {0.0, 0.0, 0.0}, Nb = 1.0;
+  if (active) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      cs.t_up[i] = S.t_up[1 + i];
-      cs.beta[i] = S.beta_up[i];
+      n_dn[i] = bg[(long long)i * na + q];
+      n_up[i] = bg[(long long)(3 + i) * na + q];
+      bb[i] = bg[(long long)(7 + i) * na + q];
     }
-#pragma unroll
-    for (int p = 0; p < 10; ++p) {
-      cs.Pi[p] = U(10 + p);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) cs.Phi[10 * i + p] = U(20 + 10 * i + p);
+    Nb = bg[(long long)6 * na + q];
+  }
+  const double nb = n_dn[0] * bb[0] + n_dn[1] * bb[1] + n_dn[2] * bb[2];
+  const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + Nb, v_m = -nb - Nb;
+  active = active && v_m < 0.0;
+  CpmWarp& S = smem[3 * warp + (sub < 3 ? sub : 0)];
+  const double g2 = a.gamma2;
+  const ShellDev& sh = a.shells[sl.shell_a];
+  const long long base = sl.off_a + q;
+
+  // 1. the state, its right-hand side and its Cartesian derivatives
+  if (active) {
+    PointGeom G;
+    point_geom(sh, sh.n_r - 1, q, G);
+    for (int f = lane; f < 50; f += 10) {
+      S.u[f] = a.u_in[base + (long long)f * na];
+      S.k[f] = a.k[base + (long long)f * na];
     }
-#pragma unroll
-    for (int p = 0; p < 10; ++p) {
-      double v = -cs.N * cs.Pi[p];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) v = fma(cs.beta[i], cs.Phi[10 * i + p], v);
-      cs.D[p] = v;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) cs.D[(1 + j) * 10 + p] = cs.Phi[10 * j + p];
+    for (int e = lane; e < 150; e += 10) {
+      const int i = e / 50, f = e - 50 * i;
+      const long long o = base + (long long)f * na;
+      S.du[i][f] = fma(G.J[i][2], a.dph[o], fma(G.J[i][1], a.dth[o], G.J[i][0] * a.dr[o]));
     }
   }
-  const double zero4[4] = {0.0, 0.0, 0.0, 0.0};
-  double K[4];
-  {
-    // the time derivative with the u^psi, u^0 and u^+ conditions applied and w^- = 0
-    double upsi[10], uPi[10], uPhi[30];
-#pragma unroll 1
-    for (int p = 0; p < 10; ++p) {
-      const double ps = a.k[base + (long long)p * na];
-      const double pi = a.k[base + (long long)(10 + p) * na];
-      double ph[3];
+  __syncwarp();
+
+  // 2. lane 0: the state's split and the background tetrad; then lane p: the
+  // characteristic time derivatives of pair p with the u^psi, u^0 and u^+
+  // conditions, w^- = 0, and the interior w^-
+  if (active && lane == 0) {
+    double psi[10];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) ph[i] = a.k[base + (long long)(20 + 10 * i + p) * na];
-      const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
-      double wpsi = ps, wp = pi + nphi - g2 * ps, w0[3];
+    for (int p = 0; p < 10; ++p) psi[p] = S.u[p];
+    Split sp;
+    spacetime_split(psi, sp);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) w0[i] = ph[i] - n_dn[i] * nphi;
-      if (v_psi < 0.0) {
-        double nC3 = 0.0;
+    for (int p = 0; p < 10; ++p) S.psi_inv[p] = sp.psi_inv[p];
+    S.N = sp.alpha;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) nC3 = fma(n_up[i], cart(p, i) - U(20 + 10 * i + p), nC3);
-        wpsi = fma(v_psi, nC3, wpsi);
-      }
-      if (v_0 < 0.0) {
-        double m[3];
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-          double acc = 0.0;
-#pragma unroll
-          for (int j = 0; j < 3; ++j) acc = fma(n_up[j], cart(20 + 10 * kk + p, j) - cart(20 + 10 * j + p, kk), acc);
-          m[kk] = acc;
-        }
-        const double nm = n_up[0] * m[0] + n_up[1] * m[1] + n_up[2] * m[2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w0[i] = fma(v_0, m[i] - n_dn[i] * nm, w0[i]);
-      }
-      if (v_p < 0.0) wp = 0.0;
-      upsi[p] = wpsi;
-      uPi[p] = 0.5 * wp + g2 * wpsi;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) uPhi[10 * i + p] = n_dn[i] * (0.5 * wp) + w0[i];
+    for (int i = 0; i < 3; ++i) {
+      S.t_up[i] = sp.t_up[1 + i];
+      S.beta[i] = sp.beta_up[i];
     }
-    double dtC[4];
-    gauge_constraint_dir(cs, upsi, uPi, uPhi, zero4, dtC);
+    double gb[6], bdn[3];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) K[c] = dtC[c] / Nb;
-  }
-  const double* gauge = sh.gauge + (long long)(sh.n_r - 1) * NGAUGE * na + q;
-#pragma unroll 1
-  for (int i = 0; i < 3; ++i) {
-    double dpsi[10], dPi[10], dPhi[30], dH[4], dC[4];
+    for (int m = 0; m < 6; ++m) gb[m] = bg[(long long)(10 + m) * na + q];
+    bdn[0] = gb[0] * bb[0] + gb[1] * bb[1] + gb[2] * bb[2];
+    bdn[1] = gb[1] * bb[0] + gb[3] * bb[1] + gb[4] * bb[2];
+    bdn[2] = gb[2] * bb[0] + gb[4] * bb[1] + gb[5] * bb[2];
+    const double r2 = 0.70710678118654752440;
+    const double n4[4] = {nb, n_dn[0], n_dn[1], n_dn[2]};
+    S.l_dn[0] = r2 * (-Nb + nb);
+    S.l_up[0] = r2 / Nb;
 #pragma unroll
-    for (int p = 0; p < 10; ++p) {
-      dpsi[p] = cart(p, i);
-      dPi[p] = cart(10 + p, i);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dPhi[10 * j + p] = cart(20 + 10 * j + p, i);
+    for (int i = 0; i < 3; ++i) {
+      S.l_dn[1 + i] = r2 * n_dn[i];
+      S.l_up[1 + i] = r2 * (n_up[i] - bb[i] / Nb);
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) dH[c] = gauge[(long long)(4 + 4 * i + c) * na];
-    gauge_constraint_dir(cs, dpsi, dPi, dPhi, dH, dC);
-    const double w = n_up[i] - bb[i] / Nb;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) K[c] = fma(w, dC[c], K[c]);
-  }
-  // the background tetrad: l_a, l^a and P_ab
-  const double r2 = 0.70710678118654752440;
-  double bdn[3];   // beta_i
-  bdn[0] = gb[0] * bb[0] + gb[1] * bb[1] + gb[2] * bb[2];
-  bdn[1] = gb[1] * bb[0] + gb[3] * bb[1] + gb[4] * bb[2];
-  bdn[2] = gb[2] * bb[0] + gb[4] * bb[1] + gb[5] * bb[2];
-  const double n4[4] = {nb, n_dn[0], n_dn[1], n_dn[2]};
-  const double l_dn[4] = {r2 * (-Nb + nb), r2 * n_dn[0], r2 * n_dn[1], r2 * n_dn[2]};
-  const double l_up[4] = {r2 / Nb, r2 * (n_up[0] - bb[0] / Nb), r2 * (n_up[1] - bb[1] / Nb),
-                          r2 * (n_up[2] - bb[2] / Nb)};
-  double P[10];
-#pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    const int A = pair_a(p), B = pair_b(p);
-    double psib;
-    if (A == 0 && B == 0) psib = -Nb * Nb + bb[0] * bdn[0] + bb[1] * bdn[1] + bb[2] * bdn[2];
-    else if (A == 0) psib = bdn[B - 1];
-    else psib = gb[s3(A - 1, B - 1)];
-    P[p] = psib + ((A == 0 && B == 0) ? Nb * Nb : 0.0) - n4[A] * n4[B];
-  }
-  // columns: d_t u^- = E_j changes Pi by E/2 and Phi_k by -n_k E/2, so
-  // D'_0ab = -(N + beta^k n_k) E_ab / 2, D'_kab = -n_k E_ab / 2 (psi' = 0)
-  double M[5][6];
-  const double c0 = -0.5 * (cs.N + cs.beta[0] * n_dn[0] + cs.beta[1] * n_dn[1] + cs.beta[2] * n_dn[2]);
-#pragma unroll 1
-  for (int j = 0; j < 5; ++j) {
-    double E[10];
 #pragma unroll
     for (int p = 0; p < 10; ++p) {
       const int A = pair_a(p), B = pair_b(p);
-      E[p] = (j < 4) ? ((B == j ? l_dn[A] : 0.0) + (A == j ? l_dn[B] : 0.0)) : P[p];
+      double psib;
+      if (A == 0 && B == 0) psib = -Nb * Nb + bb[0] * bdn[0] + bb[1] * bdn[1] + bb[2] * bdn[2];
+      else if (A == 0) psib = bdn[B - 1];
+      else psib = gb[s3(A - 1, B - 1)];
+      S.P[p] = psib + ((A == 0 && B == 0) ? Nb * Nb : 0.0) - n4[A] * n4[B];
     }
-    double Dp[40], col[4];
+  }
+  __syncwarp();
+  if (active) {
+    const int p = lane;
+    const double ps = S.k[p], pi = S.k[10 + p];
+    double ph[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ph[i] = S.k[20 + 10 * i + p];
+    const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
+    double wpsi = ps, wp = pi + nphi - g2 * ps, w0[3];
+    S.wm_int[p] = pi - nphi - g2 * ps;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w0[i] = ph[i] - n_dn[i] * nphi;
+    if (v_psi < 0.0) {
+      double nC3 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) nC3 = fma(n_up[i], S.du[i][p] - S.u[20 + 10 * i + p], nC3);
+      wpsi = fma(v_psi, nC3, wpsi);
+    }
+    if (v_0 < 0.0) {
+      double m[3];
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc = fma(n_up[j], S.du[j][20 + 10 * kk + p] - S.du[kk][20 + 10 * j + p], acc);
+        m[kk] = acc;
+      }
+      const double nm = n_up[0] * m[0] + n_up[1] * m[1] + n_up[2] * m[2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) w0[i] = fma(v_0, m[i] - n_dn[i] * nm, w0[i]);
+    }
+    if (v_p < 0.0) wp = 0.0;
+    S.ud[p] = wpsi;
+    S.ud[10 + p] = 0.5 * wp + g2 * wpsi;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S.ud[20 + 10 * i + p] = n_dn[i] * (0.5 * wp) + w0[i];
+  }
+  __syncwarp();
+
+  // 3. D_cab of the state, one pair per lane
+  if (active) {
+    const int p = lane;
+    double w = -S.N * S.u[10 + p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w = fma(S.beta[i], S.u[20 + 10 * i + p], w);
+    S.D[p] = w;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S.D[(1 + j) * 10 + p] = S.u[20 + 10 * j + p];
+  }
+  __syncwarp();
+
+  // 4. the ten directional derivatives, one per lane and all through one call:
+  // lanes 4..9 take the slope B(E) = C'(w^- = E) / N, with w^- = E changing
+  // Pi by E/2 and Phi_k by -n_k E/2 (psi' = 0), for E = l_(a e_b) (b = 0..3),
+  // P and the interior w^-
+  if (active && lane >= 4) {
+    double* v = S.vdir[lane - 4];
 #pragma unroll
     for (int p = 0; p < 10; ++p) {
-      Dp[p] = c0 * E[p];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) Dp[(1 + kk) * 10 + p] = -0.5 * n_dn[kk] * E[p];
-    }
-    contract_gamma(cs.psi_inv, Dp, col);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) M[c][j] = col[c] / Nb;
-    M[4][j] = (j < 4) ? l_up[j] : 0.0;
-  }
-#pragma unroll
-  for (int c = 0; c < 4; ++c) M[c][5] = -K[c];
-  M[4][5] = 0.0;
-  // Gaussian elimination with partial pivoting
-  bool ok = true;
-#pragma unroll 1
-  for (int c = 0; c < 5 && ok; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < 5; ++r)
-      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-    if (!(fabs(M[piv][c]) > 0.0)) {
-      ok = false;
-      break;
-    }
-    if (piv != c)
-      for (int e = 0; e < 6; ++e) {
-        const double tmp = M[c][e];
-        M[c][e] = M[piv][e];
-        M[piv][e] = tmp;
+      double E;
+      if (lane <= 7) {
+        const int A = pair_a(p), B = pair_b(p), j = lane - 4;
+        E = (B == j ? S.l_dn[A] : 0.0) + (A == j ? S.l_dn[B] : 0.0);
+      } else {
+        E = (lane == 8) ? S.P[p] : S.wm_int[p];
       }
-    for (int r = c + 1; r < 5; ++r) {
-      const double f = M[r][c] / M[c][c];
-      for (int e = c; e < 6; ++e) M[r][e] -= f * M[c][e];
-    }
-  }
-  double x[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (ok) {
-    for (int r = 4; r >= 0; --r) {
-      double v = M[r][5];
-      for (int e = r + 1; e < 5; ++e) v -= M[r][e] * x[e];
-      x[r] = v / M[r][r];
-    }
-  }
+      v[p] = 0.0;
+      v[10 + p] = 0.5 * E;
 #pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    const int A = pair_a(p), B = pair_b(p);
-    Sout[(long long)p * npts + t] = l_dn[A] * x[B] + x[A] * l_dn[B] + x[4] * P[p];
+      for (int i = 0; i < 3; ++i) v[20 + 10 * i + p] = -0.5 * n_dn[i] * E;
+    }
+  }
+  __syncwarp();
+  if (active) {
+    const double* v = (lane == 0) ? S.ud : (lane <= 3 ? S.du[lane - 1] : S.vdir[lane - 4]);
+    double dH[4] = {0.0, 0.0, 0.0, 0.0};
+    if (lane >= 1 && lane <= 3) {
+      const double* gauge = sh.gauge + (long long)(sh.n_r - 1) * NGAUGE * na + q;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dH[c] = gauge[(long long)(4 + 4 * (lane - 1) + c) * na];
+    }
+    double r[4];
+    gauge_constraint_dir(S, v, dH, r);
+    const double sc = (lane >= 4) ? 1.0 / Nb : 1.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) S.res[lane][c] = r[c] * sc;
+  }
+  __syncwarp();
+
+  // 5. lane 0: K_a[w^- = 0], the Bjorhus target and the 5x5 solve
+  if (active && lane == 0) {
+    double K[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double v = S.res[0][c] / Nb;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v = fma(n_up[i] - bb[i] / Nb, S.res[1 + i][c], v);
+      K[c] = v;
+    }
+    double M[5][6];
+    const double f = (Nb - nb) / (2.0 * Nb);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) M[c][j] = S.res[4 + j][c];
+      // -K[0] + (N - n.beta) / (2N) K[D_t u^-], K[D_t u^-] = K[0] + B(D_t u^-)
+      M[c][5] = fma(f, K[c] + S.res[9][c], -K[c]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) M[4][j] = S.l_up[j];
+    M[4][4] = 0.0;
+    M[4][5] = 0.0;
+    bool ok = true;
+#pragma unroll 1
+    for (int c = 0; c < 5 && ok; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 5; ++r)
+        if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+      if (!(fabs(M[piv][c]) > 0.0)) {
+        ok = false;
+        break;
+      }
+      if (piv != c)
+        for (int e = 0; e < 6; ++e) {
+          const double tmp = M[c][e];
+          M[c][e] = M[piv][e];
+          M[piv][e] = tmp;
+        }
+      for (int r = c + 1; r < 5; ++r) {
+        const double fr = M[r][c] / M[c][c];
+        for (int e = c; e < 6; ++e) M[r][e] -= fr * M[c][e];
+      }
+    }
+    double x[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (ok) {
+      for (int r = 4; r >= 0; --r) {
+        double v = M[r][5];
+        for (int e = r + 1; e < 5; ++e) v -= M[r][e] * x[e];
+        x[r] = v / M[r][r];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 5; ++e) S.x[e] = x[e];
+  }
+  __syncwarp();
+
+  // 6. S_ab = l_a lam_b + lam_a l_b + sig P_ab, one pair per lane
+  if (active) {
+    const int A = pair_a(lane), B = pair_b(lane);
+    Sout[(long long)lane * npts + t] = S.l_dn[A] * S.x[B] + S.x[A] * S.l_dn[B] + S.x[4] * S.P[lane];
   }
 }
 
@@ -1607,7 +1672,7 @@ cudaError_t launch_bc(gh_domain* d, double* k, int stage, double dt, const doubl
   if (a.cp_outer && !u_in) return cudaErrorInvalidValue;
   if (a.cp_outer == 2) {
     if (!d->cpm_S || d->fr.on) return cudaErrorInvalidValue;
-    cp_minus_kernel<<<cdiv(d->bc_points, 64), 64, 0, d->stream>>>(a, d->cpm_S);
+    cp_minus_kernel<<<cdiv(d->bc_points, 3 * CPM_WARPS), 32 * CPM_WARPS, 0, d->stream>>>(a, d->cpm_S);
     d->launches++;
   }
   bc_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(a);

@@ -5,11 +5,13 @@ the reading is in ``oracle.gh.uminus_constraint_part``) against what fixes it:
 1. The derivative of the gauge constraint C_a that the condition uses is the
    derivative of the oracle's own C_a: central differences of
    ``constraints_pointwise`` along random directions.
-2. The defining property: with the condition applied, the gauge constraint's
-   incoming characteristic field, its derivative along the outgoing null
-   direction (t + n), with d_t C_a taken by central differences of C_a along
-   the full boundary-corrected right-hand side, vanishes at every outer point;
-   with u^- frozen it does not.
+2. The defining property of the Bjorhus form: the boundary u^- derivative does
+   not hold u^-'s own normal derivative.  On exact Kerr-Schild data plus a
+   perturbation of u^- alone that vanishes on the outer sphere but not its
+   normal derivative, the interior D_t u^- at the boundary changes and the
+   condition's u^- derivative does not (and with the condition written along
+   the incoming null direction, or with its shift terms or its Bjorhus weight
+   wrong, it would).
 3. The u^- time derivative lies in the constraint subspace: S_ab l^b = 0 and
    its transverse traceless part vanishes (the gauge and physical parts stay
    frozen), with the null tetrad built here from the background's lapse,
@@ -89,26 +91,49 @@ def test_gauge_constraint_derivative_matches_central_differences():
         assert np.abs(d - fd).max() <= 1e-7 * np.abs(d).max(), (trial, np.abs(d - fd).max())
 
 
-def _incoming_derivative(dom, u, dudt):
-    """(t^c + n^c) d_c C_a at the outer points: d_t C_a by central differences
-    along the right-hand side, d_i C_a along the Cartesian derivatives."""
-    bg, ub, dub, Hb, dHb = _outer_data(dom, u)
-    k = _moveto(dudt[-1][-1])
-    h = 1e-6 / max(1.0, np.abs(k).max())
-    dtC = (_C(ub + h * k, Hb) - _C(ub - h * k, Hb)) / (2 * h)
-    dC = np.stack([gh.gauge_constraint_derivative(ub, dub[..., i, :], Hb, dHb[..., i, :]) for i in range(3)], -2)
-    N, beta, n_up = bg["alpha"], bg["beta_up"], bg["n_up"]
-    return (dtC - np.einsum("...i,...ia->...a", beta, dC)) / N[..., None] + np.einsum("...i,...ia->...a", n_up, dC)
+def _uminus_only_perturbation(dom, eps=1e-3, seed=8):
+    """d u with d Pi = d w / 2, d Phi_i = -n_i d w / 2 (d psi = 0) and
+    d w_ab = eps (r_out - r) g_ab(theta, phi), with n the outer sphere's
+    background normal carried along each radial line: on the outer sphere d u
+    vanishes and its normal derivative is a pure u^- one (d u^psi, d u^+ and
+    d u^0 have zero normal derivative there), and every factor is a low
+    polynomial in r or a function of angle alone, so the spectral radial
+    derivative is exact."""
+    g = dom.grids[0]
+    X, Y, Z = grid.cartesian_coords(g)
+    R = np.sqrt(X * X + Y * Y + Z * Z)
+    rng = np.random.default_rng(seed)
+    nr = dom.u_exact[0].shape[0]
+    du = np.zeros_like(dom.u_exact[0])
+    r_out = R[-1].max()
+    n = dom.boundary_bg(0, nr - 1)["n_dn"]                             # [th, ph, 3]
+    for ir in range(nr):
+        for p in range(10):
+            c = rng.normal(size=3)
+            dw = eps * (r_out - R[ir]) * (c[0] + c[1] * X[ir] / R[ir] + c[2] * Y[ir] * Z[ir] / R[ir] ** 2)
+            du[ir, 10 + p] = 0.5 * dw
+            for i in range(3):
+                du[ir, 20 + 10 * i + p] = -0.5 * n[..., i] * dw
+    return du
 
 
-def test_incoming_gauge_constraint_derivative_vanishes():
+def test_uminus_condition_ignores_the_normal_derivative_of_uminus():
+    dom = evolve.Domain([(2.5, 6.0, 9, 5)], M=1.0, chi=0.5, gamma1=0.5, outer_bc="cp_full")
+    u = dom.u_exact[0]
+    du = _uminus_only_perturbation(dom)
+    bg = _outer_data(dom, [u])[0]
     out = {}
-    for mode in ("cp", "cp_full"):
-        dom, u = _perturbed_domain(mode)
-        out[mode] = _incoming_derivative(dom, u, evolve.rhs(dom, u))
-    scale = np.abs(out["cp"]).max()
-    assert scale > 1e-3                                     # the frozen u^- lets the constraint in
-    assert np.abs(out["cp_full"]).max() <= 1e-7 * scale, np.abs(out["cp_full"]).max() / scale
+    for name, state in (("exact", u), ("perturbed", u + du)):
+        dom.outer_bc = "freeze"
+        interior = gh.to_char(_moveto(evolve.rhs_interior(dom, [state])[0][-1]), bg, dom.gamma2)
+        dom.outer_bc = "cp_full"
+        full = gh.to_char(_moveto(evolve.rhs(dom, [state])[0][-1]), bg, dom.gamma2)
+        out[name] = interior, full
+    d_int = [np.abs(a - b).max() for a, b in zip(out["exact"][0], out["perturbed"][0])]
+    d_full = [np.abs(a - b).max() for a, b in zip(out["exact"][1], out["perturbed"][1])]
+    assert d_int[3] > 1e-4                           # the interior D_t u^- sees the normal derivative
+    assert max(d_int[:3]) <= 1e-10 * d_int[3]        # the other families do not (it vanishes on the sphere)
+    assert max(d_full) <= 1e-10 * d_int[3], d_full   # the condition's u^- derivative does not either
 
 
 def test_uminus_derivative_lies_in_the_constraint_subspace():

@@ -222,13 +222,21 @@ CASES = {
     "gauge constraint derivative with the lapse variation doubled": (
         "gh", "dN = 0.5 * N ** 3 * dpsi_inv[..., 0, 0]", "dN = N ** 3 * dpsi_inv[..., 0, 0]",
         "cpbc_minus::test_gauge_constraint_derivative_matches_central_differences", ()),
-    "incoming null derivative with the shift term's sign flipped": (
-        "gh", "K0 = ((dtC0 - np.einsum(", "K0 = ((dtC0 + np.einsum(",
-        "cpbc_minus::test_incoming_gauge_constraint_derivative_vanishes", ()),
+    "incoming constraint field with the shift term's sign flipped": (
+        "gh", 'return ((dtC - np.einsum("...i,...ia->...a", beta, dC))',
+        'return ((dtC + np.einsum("...i,...ia->...a", beta, dC))',
+        "cpbc_minus::test_uminus_condition_ignores_the_normal_derivative_of_uminus", ()),
+    "Bjorhus weight with the shift term's sign flipped": (
+        "gh", "((N - nb) / (2.0 * N))", "((N + nb) / (2.0 * N))",
+        "cpbc_minus::test_uminus_condition_ignores_the_normal_derivative_of_uminus", ()),
+    "u^- condition along the corrected time derivative (no Bjorhus weight)": (
+        "gh", "target = -K(dudt0) + ((N - nb) / (2.0 * N))[..., None] * K(dudt_int)",
+        "target = -K(dudt0) + 0.0 * K(dudt_int)",
+        "cpbc_minus::test_uminus_condition_ignores_the_normal_derivative_of_uminus", ()),
     "incoming constraint field along the incoming null direction": (
-        "gh", """          + np.einsum("...i,...ia->...a", n_up, dC))""",
-        """          - np.einsum("...i,...ia->...a", n_up, dC))""",
-        "cpbc_minus::test_incoming_gauge_constraint_derivative_vanishes", ()),
+        "gh", """                + np.einsum("...i,...ia->...a", n_up, dC))""",
+        """                - np.einsum("...i,...ia->...a", n_up, dC))""",
+        "cpbc_minus::test_uminus_condition_ignores_the_normal_derivative_of_uminus", ()),
     "u^- subspace condition on k instead of l": (
         "gh", 'M[..., 4, 0:4] = tet["l_up"]', 'M[..., 4, 0:4] = tet["k_up"]',
         "cpbc_minus::test_uminus_derivative_lies_in_the_constraint_subspace", ()),
