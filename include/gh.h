@@ -372,8 +372,9 @@ gh_status gh_get_time(const gh_domain* dom, double* t);
  *   tetrad (l = (t + n)/sqrt 2), with its gauge and transverse-traceless parts
  *   frozen: one 5x5 solve per outer point (a singular system leaves u^-
  *   frozen there).  Static grid only: GH_ENOTSUP with a rotating frame or a
- *   general map (set either way round); the adjoint entry points return
- *   GH_ENOTSUP.
+ *   general map (set either way round).  The adjoint entry points transpose
+ *   it, nonlinear in u as it is (the inverse metric, the lapse and the solve),
+ *   with one extra interior right-hand side per reverse RHS.
  * Synchronises the stream and discards a captured RK4 graph. */
 enum { GH_BC_FREEZE = 0, GH_BC_CONSTRAINT_PRESERVING = 1, GH_BC_CONSTRAINT_PRESERVING_FULL = 2 };
 gh_status gh_set_outer_bc(gh_domain* dom, int mode);

@@ -16,6 +16,7 @@
 
 #include "gh_geom.cuh"
 #include "gh_internal.h"
+#include "gh_cpm.cuh"
 #include "gh_point.cuh"
 #include "gh_tensor.cuh"
 
@@ -210,10 +211,11 @@ __device__ __forceinline__ void select_transpose(double& wi, double& wo, double 
 // u^psi and u^0 cotangents pass through (the forward adds v_psi n^i C_ip and
 // v_0 P_i^k n^j C_jkp instead of freezing), and v_psi w_psi_bar, v_0 w0_bar
 // are stashed in cpbar[(p * npts + point) * 4 + {0, 1..3}] for cp_adjoint_kernel.
+// cp = 2 also stashes the u^- cotangent in cpm_Sb[p * npts + point].
 __global__ void __launch_bounds__(128)
 bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int* __restrict__ pt_begin,
                   double* __restrict__ kb, double gamma1, double gamma2, int cp, double* __restrict__ cpbar,
-                  const Frame* __restrict__ frd) {
+                  double* __restrict__ cpm_Sb, const Frame* __restrict__ frd) {
   const int npts = pt_begin[n_slices];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 10 * npts) return;
@@ -248,7 +250,11 @@ bc_adjoint_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int
       if (v_0 < 0.0) w.w0[0] = w.w0[1] = w.w0[2] = 0.0;
     }
     if (v_p < 0.0) w.wp = 0.0;
-    if (v_m < 0.0) w.wm = 0.0;
+    if (v_m < 0.0) {
+      // cp = 2: the forward wrote the u^- solve's S; its cotangent goes to cp_minus_adjoint_kernel
+      if (cp == 2) cpm_Sb[(long long)p * npts + pt] = w.wm;
+      w.wm = 0.0;
+    }
     t_transpose(w, n_dn, n_up, gamma2, v);
     store_pair(kb, base, na, p, v);
   } else {
@@ -333,6 +339,210 @@ cp_adjoint_kernel(const ShellDev* __restrict__ shells, const BcSliceDev* __restr
     for (int j = 0; j < 3; ++j) v[j] = n_up[j] * mb[k] - n_up[k] * mb[j];
     add_d(20 + 10 * k + p, v);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Reverse mode of the u^- constraint part of the outer condition (cp = 2).
+// Forward at an incoming outer point (cp_minus_kernel): S = l lam + lam l + sig P
+// with (lam, sig) = M^-1 T, where the rows of M and the target T are built from
+// ten directional derivatives res[e] of C_a (cpm_system), which depend on the
+// state u, its Cartesian derivatives du and the interior right-hand side kr
+// (through the corrected time derivative ud and the interior w^-).
+// Reverse, for the cotangent Sb of S (stashed by bc_adjoint_kernel):
+//   xb_b = sum_p Sb_p (l_A [B = b] + [A = b] l_B),  xb_4 = sum_p Sb_p P_p,
+//   y = M^-T xb,  Tb = y,  Mb = -y x^T (rows 0..3; row 4 is fixed),
+//   resb from cpm_system's linear form, then each res[e] reversed through
+//   gauge_constraint_dir_rev (state and direction), the state's split
+//   reversed down to the fields (state_rev), and cpm_pair reversed into
+//   krb, ub and dub.
+// krb is added to the interior right-hand side's cotangent kb at the point
+// (before the pointwise reverse pass consumes it); ub and the derivative
+// cotangents (dub through the DiffJac transpose) are stashed and added after
+// that pass (cp_minus_adjoint_add_kernel), which overwrites the derivative
+// scratch and may assign ubar.
+struct CpmPoint {
+  double u[50], k[50], du[3][50];
+  double psi_inv[10], t_up[3], beta[3], N;
+  double D[40];
+  double ud[50];
+  double wm_int[10];
+  double l_dn[4], l_up[4], P[10];
+  double vdir[6][50];
+  double res[10][4];
+};
+
+struct CpmAdjArgs {
+  const BcSliceDev* slices;
+  int n_slices;
+  const int* pt_begin;
+  const ShellDev* shells;
+  const double* u;        // the state
+  const double* kr;       // its interior right-hand side (before the boundary conditions)
+  const double* dr;       // its spherical derivatives
+  const double* dth;
+  const double* dph;
+  const double* Sb;       // [10][npts] cotangent of the condition's u^- derivative
+  double* kb;             // cotangent of the interior right-hand side (added to)
+  double* stash;          // [200][npts]: ub (50), then the d/dx, d/dtheta, d/dphi cotangents (3 x 50)
+  double gamma1, gamma2;
+};
+
+__global__ void __launch_bounds__(64) cp_minus_adjoint_kernel(CpmAdjArgs a) {
+  const int npts = a.pt_begin[a.n_slices];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npts) return;
+  const int sidx = find_segment(a.pt_begin, a.n_slices, t);
+  const BcSliceDev& sl = a.slices[sidx];
+  if (sl.kind != 0) return;
+  const int q = t - a.pt_begin[sidx];
+  const int na = sl.na;
+  CpmBg b;
+  cpm_load_bg(sl.bg, na, q, b);
+  if (!((-b.nb - b.Nb) < 0.0)) return;
+  double Sb[10];
+  bool any = false;
+  for (int p = 0; p < 10; ++p) {
+    Sb[p] = a.Sb[(long long)p * npts + t];
+    any = any || Sb[p] != 0.0;
+  }
+  // the stash of every incoming outer point is written (zeros where S does not depend on u)
+  auto write_zero = [&]() {
+    for (int e = 0; e < 200; ++e) a.stash[(long long)e * npts + t] = 0.0;
+  };
+  if (!any) {
+    write_zero();
+    return;
+  }
+  const ShellDev& sh = a.shells[sl.shell_a];
+  const long long base = sl.off_a + q;
+  PointGeom G;
+  point_geom(sh, sh.n_r - 1, q, G);
+  const double* gauge = sh.gauge + (long long)(sh.n_r - 1) * NGAUGE * na + q;
+
+  // the primal, as cp_minus_kernel computes it
+  CpmPoint S;
+  for (int f = 0; f < 50; ++f) {
+    const long long o = base + (long long)f * na;
+    S.u[f] = a.u[o];
+    S.k[f] = a.kr[o];
+    for (int i = 0; i < 3; ++i) S.du[i][f] = fma(G.J[i][2], a.dph[o], fma(G.J[i][1], a.dth[o], G.J[i][0] * a.dr[o]));
+  }
+  cpm_state(S);
+  cpm_tetrad(b, S.l_dn, S.l_up, S.P);
+  for (int p = 0; p < 10; ++p) cpm_pair(p, S.k, S.u, S.du, b, a.gamma1, a.gamma2, S.ud, &S.wm_int[p]);
+  for (int e = 0; e < 6; ++e) {
+    double E[10];
+    cpm_basis(e, S.l_dn, S.P, S.wm_int, E);
+    cpm_vdir(E, b.n_dn, S.vdir[e]);
+  }
+  double dH[3][4];
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 4; ++c) dH[i][c] = gauge[(long long)(4 + 4 * i + c) * na];
+  const double zero4[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = 0; e < 10; ++e) {
+    const double* v = (e == 0) ? S.ud : (e <= 3 ? S.du[e - 1] : S.vdir[e - 4]);
+    double r[4];
+    gauge_constraint_dir(S, v, (e >= 1 && e <= 3) ? dH[e - 1] : zero4, r);
+    const double sc = (e >= 4) ? 1.0 / b.Nb : 1.0;
+    for (int c = 0; c < 4; ++c) S.res[e][c] = r[c] * sc;
+  }
+  double M0[5][6], W[5][6], x[5];
+  cpm_system(S.res, b, S.l_up, M0);
+  for (int r = 0; r < 5; ++r)
+    for (int c = 0; c < 6; ++c) W[r][c] = M0[r][c];
+  if (!cpm_solve5(W, x)) {                    // S = 0 there: no dependence
+    write_zero();
+    return;
+  }
+
+  // reverse: S -> x -> (M, T) -> res
+  double xb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int p = 0; p < 10; ++p) {
+    const int A = pair_a(p), B = pair_b(p);
+    xb[B] = fma(Sb[p], S.l_dn[A], xb[B]);
+    xb[A] = fma(Sb[p], S.l_dn[B], xb[A]);
+    xb[4] = fma(Sb[p], S.P[p], xb[4]);
+  }
+  double y[5];
+  for (int r = 0; r < 5; ++r) {
+    for (int c = 0; c < 5; ++c) W[r][c] = M0[c][r];
+    W[r][5] = xb[r];
+  }
+  if (!cpm_solve5(W, y)) {
+    write_zero();
+    return;
+  }
+  double resb[10][4];
+  const double f = (b.Nb - b.nb) / (2.0 * b.Nb);
+  for (int c = 0; c < 4; ++c) {
+    for (int j = 0; j < 5; ++j) resb[4 + j][c] = -y[c] * x[j];
+    const double Kb = (f - 1.0) * y[c];
+    resb[9][c] = f * y[c];
+    resb[0][c] = Kb / b.Nb;
+    for (int i = 0; i < 3; ++i) resb[1 + i][c] = (b.n_up[i] - b.bb[i] / b.Nb) * Kb;
+  }
+  // res -> state, directions
+  CStateBar sb;
+  for (int f2 = 0; f2 < 50; ++f2) sb.u[f2] = 0.0;
+  for (int p = 0; p < 10; ++p) sb.psi_inv[p] = 0.0;
+  sb.N = 0.0;
+  for (int i = 0; i < 3; ++i) sb.t_up[i] = sb.beta[i] = 0.0;
+  for (int e = 0; e < 40; ++e) sb.D[e] = 0.0;
+  double udb[50], dub[3][50], v9b[50];
+  for (int f2 = 0; f2 < 50; ++f2) {
+    udb[f2] = v9b[f2] = 0.0;
+    for (int i = 0; i < 3; ++i) dub[i][f2] = 0.0;
+  }
+  for (int e = 0; e < 10; ++e) {
+    const double sc = (e >= 4) ? 1.0 / b.Nb : 1.0;
+    double ob[4];
+    for (int c = 0; c < 4; ++c) ob[c] = resb[e][c] * sc;
+    const double* v = (e == 0) ? S.ud : (e <= 3 ? S.du[e - 1] : S.vdir[e - 4]);
+    double* vb = (e == 0) ? udb : (e <= 3 ? dub[e - 1] : (e == 9 ? v9b : nullptr));
+    gauge_constraint_dir_rev(S, v, ob, sb, vb);
+  }
+  state_rev(S, sb);
+  double krb[50];
+  for (int f2 = 0; f2 < 50; ++f2) krb[f2] = 0.0;
+  for (int p = 0; p < 10; ++p) {
+    // the interior w^- enters through e = 9's direction: Pi' = w/2, Phi_i' = -n_i w/2
+    double wmb = 0.5 * v9b[10 + p];
+    for (int i = 0; i < 3; ++i) wmb = fma(-0.5 * b.n_dn[i], v9b[20 + 10 * i + p], wmb);
+    cpm_pair_rev(p, b, a.gamma1, a.gamma2, udb, wmb, krb, sb.u, dub);
+  }
+  for (int f2 = 0; f2 < 50; ++f2) {
+    const long long o = base + (long long)f2 * na;
+    a.kb[o] += krb[f2];
+    a.stash[(long long)f2 * npts + t] = sb.u[f2];
+    for (int dd = 0; dd < 3; ++dd)
+      a.stash[(long long)(50 + 50 * dd + f2) * npts + t] =
+          G.J[0][dd] * dub[0][f2] + G.J[1][dd] * dub[1][f2] + G.J[2][dd] * dub[2][f2];
+  }
+}
+
+// After the pointwise reverse pass: ubar and the derivative cotangents
+// (overwritten into dr/dth/dph by that pass) take the stashed contributions
+// of the u^- condition, one thread per (outer point, field).
+__global__ void __launch_bounds__(128)
+cp_minus_adjoint_add_kernel(const BcSliceDev* __restrict__ slices, int n_slices, const int* __restrict__ pt_begin,
+                            const double* __restrict__ stash, double* ubar, double* dr, double* dth, double* dph) {
+  const int npts = pt_begin[n_slices];
+  const long long tt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= 50LL * npts) return;
+  const int f = (int)(tt / npts);
+  const int t = (int)(tt - (long long)f * npts);
+  const int sidx = find_segment(pt_begin, n_slices, t);
+  const BcSliceDev& sl = slices[sidx];
+  if (sl.kind != 0) return;
+  const int q = t - pt_begin[sidx];
+  CpmBg b;
+  cpm_load_bg(sl.bg, sl.na, q, b);
+  if (!((-b.nb - b.Nb) < 0.0)) return;
+  const long long o = sl.off_a + q + (long long)f * sl.na;
+  ubar[o] += stash[(long long)f * npts + t];
+  dr[o] += stash[(long long)(50 + f) * npts + t];
+  dth[o] += stash[(long long)(100 + f) * npts + t];
+  dph[o] += stash[(long long)(150 + f) * npts + t];
 }
 
 // ---------------------------------------------------------------------------
@@ -646,9 +856,19 @@ gh_status adj_ready(gh_domain* d) {
   if (d->map_gen)
     return afail(d, GH_ENOTSUP, "the adjoint supports the static grid and the rotating frame, not a general map");
   if (d->algorithm == 0) return afail(d, GH_ENOTSUP, "the adjoint needs a separable angular algorithm");
-  if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING_FULL)
-    return afail(d, GH_ENOTSUP, "the adjoint transposes the u^psi and u^0 outer conditions, not the u^- constraint part");
-  if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING && !d->adj_cpbar && d->bc_points) {
+  if (d->outer_bc == GH_BC_CONSTRAINT_PRESERVING_FULL && d->bc_points && !d->adj_cpm_stash) {
+    void* p = nullptr;
+    GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * (size_t)d->state));
+    d->owned.push_back(p);
+    d->adj_kraw = (double*)p;
+    GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * 10 * (size_t)d->bc_points));
+    d->owned.push_back(p);
+    d->adj_cpm_Sb = (double*)p;
+    GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * 200 * (size_t)d->bc_points));
+    d->owned.push_back(p);
+    d->adj_cpm_stash = (double*)p;
+  }
+  if (d->outer_bc != GH_BC_FREEZE && !d->adj_cpbar && d->bc_points) {
     void* p = nullptr;
     GH_ACUDA(d, cudaMalloc(&p, sizeof(double) * 40 * (size_t)d->bc_points));
     d->owned.push_back(p);
@@ -790,12 +1010,24 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
   double* const* D = saved ? saved : scratch;
   if (!saved) GH_ACUDA(d, fwd_derivs(d, u));
   GH_ACUDA(d, cudaMemcpyAsync(d->kbt, kb, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
-  const int cp = d->outer_bc == GH_BC_CONSTRAINT_PRESERVING;
+  const int cp = d->outer_bc;   // 0 freezing, 1 u^psi and u^0, 2 also the u^- constraint part
   const gh::Frame* frd = d->rot_omega != 0.0 ? d->frd : nullptr;
   if (d->bc_points) {
     gh::bc_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
         d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->kbt, d->params.gamma1, d->params.gamma2, cp,
-        d->adj_cpbar, frd);
+        d->adj_cpbar, d->adj_cpm_Sb, frd);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+  }
+  if (cp == 2 && d->bc_points) {
+    // the interior right-hand side the forward condition read, then the u^- reverse
+    GH_ACUDA(d, gh::launch_pointwise_rhs_from(d, u, D[0], D[1], D[2], d->adj_kraw));
+    gh::CpmAdjArgs ca;
+    ca.slices = d->bc_d; ca.n_slices = (int)d->bc_h.size(); ca.pt_begin = d->bc_pt_begin_d;
+    ca.shells = d->shells_d; ca.u = u; ca.kr = d->adj_kraw; ca.dr = D[0]; ca.dth = D[1]; ca.dph = D[2];
+    ca.Sb = d->adj_cpm_Sb; ca.kb = d->kbt; ca.stash = d->adj_cpm_stash;
+    ca.gamma1 = d->params.gamma1; ca.gamma2 = d->params.gamma2;
+    gh::cp_minus_adjoint_kernel<<<cdiv(d->bc_points, 64), 64, 0, d->stream>>>(ca);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }
@@ -838,6 +1070,12 @@ gh_status rhs_vjp(gh_domain* d, const double* u, const double* kb, double* ubar,
     gh::cp_adjoint_kernel<<<cdiv(10LL * d->bc_points, 128), 128, 0, d->stream>>>(
         d->shells_d, d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpbar, D[0], D[1], D[2], ubar,
         frd);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+  }
+  if (cp == 2 && d->bc_points) {
+    gh::cp_minus_adjoint_add_kernel<<<cdiv(50LL * d->bc_points, 128), 128, 0, d->stream>>>(
+        d->bc_d, (int)d->bc_h.size(), d->bc_pt_begin_d, d->adj_cpm_stash, ubar, D[0], D[1], D[2]);
     d->launches++;
     GH_ACUDA(d, cudaGetLastError());
   }

@@ -255,6 +255,12 @@ struct gh_domain {
   const gh::Frame* frd = nullptr; // frame of the launches being issued (device)
   double graph_dt = 0.0;        // dt of the captured RK4 step
   double* adj_cpbar = nullptr;  // reverse mode, constraint-preserving outer condition: [10][bc points][4]
+  // reverse mode of the u^- constraint part (outer_bc 2): the interior right-hand
+  // side (one state), the cotangent of the condition's u^- derivative [10][bc points]
+  // and the stashed field and derivative cotangents [200][bc points]
+  double* adj_kraw = nullptr;
+  double* adj_cpm_Sb = nullptr;
+  double* adj_cpm_stash = nullptr;
   // SH filter mode (gh_set_sh_filter): 0 per Cartesian component, 1 tensor
   // harmonics; complex frame components [shell][r][TF_ROWS][na][2]
   int sh_filter_mode = 0;

@@ -16,6 +16,7 @@
 
 #include "gh_geom.cuh"
 #include "gh_internal.h"
+#include "gh_cpm.cuh"
 #include "gh_tensor.cuh"
 
 namespace gh {
@@ -1074,13 +1075,12 @@ __global__ void __launch_bounds__(128) bc_kernel(BcArgs a) {
 // per block); each point's data lives in shared memory:
 //   u, k       the state and its interior right-hand side (50 fields each),
 //   du[i]      the Cartesian derivatives d_i u,
-//   psi_inv, N, t^i, beta^i and D_cab = d_c psi_ab reconstructed from the
-//              state as t_c Pi_ab + g^i_c Phi_iab (D_0ab = -N Pi_ab +
-//              beta^i Phi_iab, D_jab = Phi_jab),
+//   psi_inv, N, t^i, beta^i and D_cab (the state's split, gh_cpm.cuh),
 //   ud         the time derivative with the u^psi, u^0, u^+ conditions and w^- = 0,
 //   wm_int     the interior d_t u^- per pair,
 //   l_dn, l_up, P  the background null vector and transverse projector,
-//   res[e]     the ten directional derivatives of C_a (see cp_minus_kernel).
+//   vdir       the field-space directions of the six slope evaluations,
+//   res[e]     the ten directional derivatives of C_a (cpm_system).
 #ifndef GH_CPM_WARPS
 #define GH_CPM_WARPS 2
 #endif
@@ -1093,80 +1093,10 @@ struct CpmWarp {
   double ud[50];
   double wm_int[10];
   double l_dn[4], l_up[4], P[10];
-  double vdir[6][50];   // the field-space directions of the slope evaluations (w^- = E)
+  double vdir[6][50];
   double res[10][4];
   double x[5];
 };
-
-// E_a = X^bc (Y_bac - Y_abc / 2) for a symmetric X^bc and Y[c][pair(a, b)]:
-// psi^bc Gamma_abc for Y = D (psi^bc is symmetric, so the two Gamma terms
-// that swap b and c contribute equally).  The second sum runs over the ten
-// pairs (off-diagonal ones twice).
-__device__ __forceinline__ void contract_gamma(const double* X, const double* Y, double out[4]) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    double s1 = 0.0, s2 = 0.0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s1 = fma(X[sym_index(b, c)], Y[b * 10 + sym_index(a, c)], s1);
-#pragma unroll
-    for (int p = 0; p < 10; ++p) s2 = fma(pair_a(p) == pair_b(p) ? X[p] : 2.0 * X[p], Y[a * 10 + p], s2);
-    out[a] = fma(-0.5, s2, s1);
-  }
-}
-
-// C'_a, the derivative of C_a = H_a + psi^bc Gamma_abc along a field-space
-// direction v (50 fields: psi', Pi', Phi') and H', by the product rule:
-// psi'^ab = -psi^ac psi'_cd psi^db, N' = N^3 psi'^00 / 2,
-// t'^i = -N' psi^0i - N psi'^0i, D'_0ab = -N' Pi_ab - N Pi'_ab
-// + (-N t'^i - N' t^i) Phi_iab + beta^i Phi'_iab, D'_jab = Phi'_jab, and
-// C'_a = H'_a + psi'^bc (D_bac - D_abc / 2) + psi^bc (D'_bac - D'_abc / 2).
-__device__ __noinline__ void gauge_constraint_dir(const CpmWarp& s, const double* v, const double dH[4],
-                                                  double out[4]) {
-  double Mi[4][4];   // psi^ac psi'_cd
-#pragma unroll
-  for (int A = 0; A < 4; ++A)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      double acc = 0.0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(s.psi_inv[sym_index(A, c)], v[sym_index(c, e)], acc);
-      Mi[A][e] = acc;
-    }
-  double dpi[10];
-#pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    const int A = pair_a(p), B = pair_b(p);
-    double acc = 0.0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc = fma(Mi[A][e], s.psi_inv[sym_index(e, B)], acc);
-    dpi[p] = -acc;
-  }
-  const double N = s.N;
-  const double dN = 0.5 * N * N * N * dpi[0];
-  double g0[3];   // g'^i_0
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const double dt = -dN * s.psi_inv[sym_index(0, 1 + i)] - N * dpi[sym_index(0, 1 + i)];
-    g0[i] = -N * dt - dN * s.t_up[i];
-  }
-  double Dp[40];
-#pragma unroll
-  for (int p = 0; p < 10; ++p) {
-    double w = -dN * s.u[10 + p] - N * v[10 + p];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) w = fma(g0[i], s.u[20 + 10 * i + p], fma(s.beta[i], v[20 + 10 * i + p], w));
-    Dp[p] = w;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Dp[(1 + j) * 10 + p] = v[20 + 10 * j + p];
-  }
-  double e1[4], e2[4];
-  contract_gamma(dpi, s.D, e1);
-  contract_gamma(s.psi_inv, Dp, e2);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) out[a] = dH[a] + e1[a] + e2[a];
-}
 
 // Three outer-boundary points per warp, ten lanes each (lanes 30 and 31 idle),
 // where u^- is incoming: writes S[pair * npts + point] for bc_kernel (a
@@ -1188,22 +1118,12 @@ __global__ void __launch_bounds__(32 * CPM_WARPS) cp_minus_kernel(BcArgs a, doub
   active = active && sl.kind == 0;
   const int q = active ? t - a.pt_begin[sidx] : 0;
   const int na = sl.na;
-  const double* bg = sl.bg;
-  double n_dn[3] = {1.0, 0.0, 0.0}, n_up[3] = {1.0, 0.0, 0.0}, bb[3] = {0.0, 0.0, 0.0}, Nb = 1.0;
+  CpmBg b;
   if (active) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      n_dn[i] = bg[(long long)i * na + q];
-      n_up[i] = bg[(long long)(3 + i) * na + q];
-      bb[i] = bg[(long long)(7 + i) * na + q];
-    }
-    Nb = bg[(long long)6 * na + q];
+    cpm_load_bg(sl.bg, na, q, b);
+    active = (-b.nb - b.Nb) < 0.0;          // u^- incoming
   }
-  const double nb = n_dn[0] * bb[0] + n_dn[1] * bb[1] + n_dn[2] * bb[2];
-  const double v_psi = -(1.0 + a.gamma1) * nb, v_0 = -nb, v_p = -nb + Nb, v_m = -nb - Nb;
-  active = active && v_m < 0.0;
   CpmWarp& S = smem[3 * warp + (sub < 3 ? sub : 0)];
-  const double g2 = a.gamma2;
   const ShellDev& sh = a.shells[sl.shell_a];
   const long long base = sl.off_a + q;
 
@@ -1222,122 +1142,23 @@ __global__ void __launch_bounds__(32 * CPM_WARPS) cp_minus_kernel(BcArgs a, doub
     }
   }
   __syncwarp();
-
-  // 2. lane 0: the state's split and the background tetrad; then lane p: the
-  // characteristic time derivatives of pair p with the u^psi, u^0 and u^+
-  // conditions, w^- = 0, and the interior w^-
+  // 2. lane 0: the state's split, D and the background tetrad; lane p: pair p
+  // of the corrected time derivative (w^- = 0) and of the interior w^-
   if (active && lane == 0) {
-    double psi[10];
-#pragma unroll
-    for (int p = 0; p < 10; ++p) psi[p] = S.u[p];
-    Split sp;
-    spacetime_split(psi, sp);
-#pragma unroll
-    for (int p = 0; p < 10; ++p) S.psi_inv[p] = sp.psi_inv[p];
-    S.N = sp.alpha;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      S.t_up[i] = sp.t_up[1 + i];
-      S.beta[i] = sp.beta_up[i];
-    }
-    double gb[6], bdn[3];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) gb[m] = bg[(long long)(10 + m) * na + q];
-    bdn[0] = gb[0] * bb[0] + gb[1] * bb[1] + gb[2] * bb[2];
-    bdn[1] = gb[1] * bb[0] + gb[3] * bb[1] + gb[4] * bb[2];
-    bdn[2] = gb[2] * bb[0] + gb[4] * bb[1] + gb[5] * bb[2];
-    const double r2 = 0.70710678118654752440;
-    const double n4[4] = {nb, n_dn[0], n_dn[1], n_dn[2]};
-    S.l_dn[0] = r2 * (-Nb + nb);
-    S.l_up[0] = r2 / Nb;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      S.l_dn[1 + i] = r2 * n_dn[i];
-      S.l_up[1 + i] = r2 * (n_up[i] - bb[i] / Nb);
-    }
-#pragma unroll
-    for (int p = 0; p < 10; ++p) {
-      const int A = pair_a(p), B = pair_b(p);
-      double psib;
-      if (A == 0 && B == 0) psib = -Nb * Nb + bb[0] * bdn[0] + bb[1] * bdn[1] + bb[2] * bdn[2];
-      else if (A == 0) psib = bdn[B - 1];
-      else psib = gb[s3(A - 1, B - 1)];
-      S.P[p] = psib + ((A == 0 && B == 0) ? Nb * Nb : 0.0) - n4[A] * n4[B];
-    }
+    cpm_state(S);
+    cpm_tetrad(b, S.l_dn, S.l_up, S.P);
   }
+  if (active) cpm_pair(lane, S.k, S.u, S.du, b, a.gamma1, a.gamma2, S.ud, &S.wm_int[lane]);
   __syncwarp();
-  if (active) {
-    const int p = lane;
-    const double ps = S.k[p], pi = S.k[10 + p];
-    double ph[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ph[i] = S.k[20 + 10 * i + p];
-    const double nphi = n_up[0] * ph[0] + n_up[1] * ph[1] + n_up[2] * ph[2];
-    double wpsi = ps, wp = pi + nphi - g2 * ps, w0[3];
-    S.wm_int[p] = pi - nphi - g2 * ps;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) w0[i] = ph[i] - n_dn[i] * nphi;
-    if (v_psi < 0.0) {
-      double nC3 = 0.0;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) nC3 = fma(n_up[i], S.du[i][p] - S.u[20 + 10 * i + p], nC3);
-      wpsi = fma(v_psi, nC3, wpsi);
-    }
-    if (v_0 < 0.0) {
-      double m[3];
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        double acc = 0.0;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) acc = fma(n_up[j], S.du[j][20 + 10 * kk + p] - S.du[kk][20 + 10 * j + p], acc);
-        m[kk] = acc;
-      }
-      const double nm = n_up[0] * m[0] + n_up[1] * m[1] + n_up[2] * m[2];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) w0[i] = fma(v_0, m[i] - n_dn[i] * nm, w0[i]);
-    }
-    if (v_p < 0.0) wp = 0.0;
-    S.ud[p] = wpsi;
-    S.ud[10 + p] = 0.5 * wp + g2 * wpsi;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) S.ud[20 + 10 * i + p] = n_dn[i] * (0.5 * wp) + w0[i];
-  }
-  __syncwarp();
-
-  // 3. D_cab of the state, one pair per lane
-  if (active) {
-    const int p = lane;
-    double w = -S.N * S.u[10 + p];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) w = fma(S.beta[i], S.u[20 + 10 * i + p], w);
-    S.D[p] = w;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) S.D[(1 + j) * 10 + p] = S.u[20 + 10 * j + p];
-  }
-  __syncwarp();
-
-  // 4. the ten directional derivatives, one per lane and all through one call:
-  // lanes 4..9 take the slope B(E) = C'(w^- = E) / N, with w^- = E changing
-  // Pi by E/2 and Phi_k by -n_k E/2 (psi' = 0), for E = l_(a e_b) (b = 0..3),
-  // P and the interior w^-
+  // 3. lanes 4..9: the directions of the slopes B(E) = C'(w^- = E) / N for
+  // E = l_(a e_b) (b = 0..3), P and the interior w^-
   if (active && lane >= 4) {
-    double* v = S.vdir[lane - 4];
-#pragma unroll
-    for (int p = 0; p < 10; ++p) {
-      double E;
-      if (lane <= 7) {
-        const int A = pair_a(p), B = pair_b(p), j = lane - 4;
-        E = (B == j ? S.l_dn[A] : 0.0) + (A == j ? S.l_dn[B] : 0.0);
-      } else {
-        E = (lane == 8) ? S.P[p] : S.wm_int[p];
-      }
-      v[p] = 0.0;
-      v[10 + p] = 0.5 * E;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) v[20 + 10 * i + p] = -0.5 * n_dn[i] * E;
-    }
+    double E[10];
+    cpm_basis(lane - 4, S.l_dn, S.P, S.wm_int, E);
+    cpm_vdir(E, b.n_dn, S.vdir[lane - 4]);
   }
   __syncwarp();
+  // 4. the ten directional derivatives, one per lane and all through one call
   if (active) {
     const double* v = (lane == 0) ? S.ud : (lane <= 3 ? S.du[lane - 1] : S.vdir[lane - 4]);
     double dH[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1348,69 +1169,20 @@ __global__ void __launch_bounds__(32 * CPM_WARPS) cp_minus_kernel(BcArgs a, doub
     }
     double r[4];
     gauge_constraint_dir(S, v, dH, r);
-    const double sc = (lane >= 4) ? 1.0 / Nb : 1.0;
+    const double sc = (lane >= 4) ? 1.0 / b.Nb : 1.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) S.res[lane][c] = r[c] * sc;
   }
   __syncwarp();
-
-  // 5. lane 0: K_a[w^- = 0], the Bjorhus target and the 5x5 solve
+  // 5. lane 0: the Bjorhus target and the 5x5 solve
   if (active && lane == 0) {
-    double K[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      double v = S.res[0][c] / Nb;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) v = fma(n_up[i] - bb[i] / Nb, S.res[1 + i][c], v);
-      K[c] = v;
-    }
-    double M[5][6];
-    const double f = (Nb - nb) / (2.0 * Nb);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-#pragma unroll
-      for (int j = 0; j < 5; ++j) M[c][j] = S.res[4 + j][c];
-      // -K[0] + (N - n.beta) / (2N) K[D_t u^-], K[D_t u^-] = K[0] + B(D_t u^-)
-      M[c][5] = fma(f, K[c] + S.res[9][c], -K[c]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) M[4][j] = S.l_up[j];
-    M[4][4] = 0.0;
-    M[4][5] = 0.0;
-    bool ok = true;
-#pragma unroll 1
-    for (int c = 0; c < 5 && ok; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < 5; ++r)
-        if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-      if (!(fabs(M[piv][c]) > 0.0)) {
-        ok = false;
-        break;
-      }
-      if (piv != c)
-        for (int e = 0; e < 6; ++e) {
-          const double tmp = M[c][e];
-          M[c][e] = M[piv][e];
-          M[piv][e] = tmp;
-        }
-      for (int r = c + 1; r < 5; ++r) {
-        const double fr = M[r][c] / M[c][c];
-        for (int e = c; e < 6; ++e) M[r][e] -= fr * M[c][e];
-      }
-    }
-    double x[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (ok) {
-      for (int r = 4; r >= 0; --r) {
-        double v = M[r][5];
-        for (int e = r + 1; e < 5; ++e) v -= M[r][e] * x[e];
-        x[r] = v / M[r][r];
-      }
-    }
+    double M[5][6], x[5];
+    cpm_system(S.res, b, S.l_up, M);
+    cpm_solve5(M, x);
 #pragma unroll
     for (int e = 0; e < 5; ++e) S.x[e] = x[e];
   }
   __syncwarp();
-
   // 6. S_ab = l_a lam_b + lam_a l_b + sig P_ab, one pair per lane
   if (active) {
     const int A = pair_a(lane), B = pair_b(lane);
