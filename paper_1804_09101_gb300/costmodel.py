@@ -133,22 +133,47 @@ POINTWISE_FLOPS_SOURCE = ("algorithmic: the GH equations counted on the oracle's
                           "point) + DiffJac (650) + RK4 stage combinations (162.5); the kernel executes 4,046")
 
 
+# A mode's half-size Legendre map is applied as analysis then synthesis when
+# (1 + n_out)(K + 1 - m) is below this percentage of 2 n_out hs (the fused
+# map's FMAs per output ring); the library's fold plans use the same rule.
+FOLD_RANK_PERCENT = 75
+
+
+def fold_rank_m0(K, hs, n_out):
+    """First mode m whose Legendre map the folded kernel factorises (K + 1: none)."""
+    for m in range(K + 1):
+        if (1 + n_out) * (K + 1 - m) * 100 < FOLD_RANK_PERCENT * 2 * n_out * hs:
+            return m
+    return K + 1
+
+
 def fold_angular_flops(shells, K=None, two=True):
     """FP64 flops of one folded separable launch (fold_angular_kernel), per
     (r, field) row: fold 8 (W - 1) N_theta; phase A half M (4 W + 2) plus
-    (hs - half) M 2 W for an odd N_theta's equator ring; phase B
-    n_out M hs (4 hs + 5); phase C n_out N_theta W (2 M + 8), with
-    W = N_phi/4 + 1 (N_phi % 4 == 0) or (N_phi + 2)/4, half = floor(N_theta/2),
-    hs = ceil(N_theta/2), M = 2K+1."""
+    (hs - half) M 2 W for an odd N_theta's equator ring; phase B per mode
+    (cos m, and sin m for m >= 1): fused, n_out hs (4 hs + 5); factorised
+    (m >= m0, rank r = K + 1 - m), the analysis 2 r hs plus n_out hs (2 r + 5);
+    phase C n_out N_theta W (2 M + 8), with W = N_phi/4 + 1 (N_phi % 4 == 0)
+    or (N_phi + 2)/4, half = floor(N_theta/2), hs = ceil(N_theta/2), M = 2K+1."""
     f = 0
     n_out = 2 if two else 1
     for sh in shells:
         n_r, nth, nph, na = _shell_dims(sh)
-        M = 2 * _keep(sh, K) + 1
+        Kk = _keep(sh, K)
+        M = 2 * Kk + 1
         W = nph // 4 + 1 if nph % 4 == 0 else (nph + 2) // 4
         half, hs = nth // 2, (nth + 1) // 2
+        m0 = fold_rank_m0(Kk, hs, n_out)
+        phase_b = 0
+        for m in range(Kk + 1):
+            modes = 1 if m == 0 else 2
+            r = Kk + 1 - m
+            if m < m0:
+                phase_b += modes * n_out * hs * (4 * hs + 5)
+            else:
+                phase_b += modes * (2 * r * hs + n_out * hs * (2 * r + 5))
         per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W
-                   + n_out * M * hs * (4 * hs + 5) + n_out * nth * W * (2 * M + 8))
+                   + phase_b + n_out * nth * W * (2 * M + 8))
         f += 50 * n_r * per_row
     return f
 

@@ -57,6 +57,8 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
   double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
   double* AB = sm + (size_t)RB * r1;                // [RB][M][2 hs]: s (hs) then t (hs)
+  const int ncoef = P.ncoef;
+  double* COEF = AB + (size_t)RB * M * 2 * hs;      // [RB][2][ncoef]: a_l of the cos, then the sin modes m >= m0
   const long long gbase = sh.off + (long long)row0 * na;
   for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
   __syncthreads();
@@ -114,7 +116,28 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     }
   }
   __syncthreads();
-  // phase B: half-size Legendre maps (tables carry the synthesis factors)
+  // phase B1: for modes m >= m0, the Legendre analysis a_l = sum_j A_l(j) (s or
+  // t)_j for l = m .. K (s part for l + m even, t part for l + m odd)
+  if (ncoef > 0) {
+    for (int o = threadIdx.x; o < nr * 2 * ncoef; o += T) {
+      const int slot = o % ncoef;
+      const int t = o / ncoef;
+      const int sinp = t & 1;
+      const int rr = t >> 1;
+      const int m = __ldg(P.slot_m + slot);
+      if (sinp && m == 0) continue;               // no sin mode 0
+      const int idx = slot - __ldg(P.coef_off + m);
+      const int mode = sinp ? K + m : m;
+      const double* v = AB + ((size_t)rr * M + mode) * 2 * hs + ((idx & 1) ? hs : 0);
+      const double* a = P.A + (size_t)slot * hs;
+      double acc = v[0] * __ldg(a);
+      for (int jj = 1; jj < hs; ++jj) acc = fma(v[jj], __ldg(a + jj), acc);
+      COEF[((size_t)rr * 2 + sinp) * ncoef + slot] = acc;
+    }
+    __syncthreads();
+  }
+  // phase B: half-size Legendre maps (tables carry the synthesis factors);
+  // modes m >= m0 synthesise from their coefficients instead
   const unsigned long long sbit = 0x8000000000000000ULL;
   for (int o = threadIdx.x; o < nr * M * hs; o += T) {
     const int j = o % hs;
@@ -125,7 +148,24 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     const int m = cosm ? mode : mode - K;
     const double* ab = AB + ((size_t)rr * M + mode) * 2 * hs;
     double Sv[2], Tv[2];
-    {
+    if (m >= P.m0) {
+      const int off = __ldg(P.coef_off + m), nl = K + 1 - m;
+      const double* a = COEF + ((size_t)rr * 2 + (cosm ? 0 : 1)) * ncoef + off;
+      const double* y0 = P.Y0 + (size_t)off * hs + j;
+      const double* y1 = TWO ? P.Y1 + (size_t)off * hs + j : nullptr;
+      Sv[0] = Tv[0] = 0.0;
+      if (TWO) Sv[1] = Tv[1] = 0.0;
+      for (int idx = 0; idx < nl; idx += 2) {         // l + m even: the s part
+        const double av = a[idx];
+        Sv[0] = fma(__ldg(y0 + (size_t)idx * hs), av, Sv[0]);
+        if (TWO) Sv[1] = fma(__ldg(y1 + (size_t)idx * hs), av, Sv[1]);
+      }
+      for (int idx = 1; idx < nl; idx += 2) {         // l + m odd: the t part
+        const double av = a[idx];
+        Tv[0] = fma(__ldg(y0 + (size_t)idx * hs), av, Tv[0]);
+        if (TWO) Tv[1] = fma(__ldg(y1 + (size_t)idx * hs), av, Tv[1]);
+      }
+    } else {
       const size_t mo = (size_t)m * hs * hs + j;
       const double* Q0s = P.Q0s + mo;
       const double* Q0t = P.Q0t + mo;

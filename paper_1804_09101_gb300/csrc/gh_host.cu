@@ -346,11 +346,20 @@ int sep_rows_per_block(int na, int nth, int M, bool two, int n_rows) {
   return rb;
 }
 
-// Folded plan (see fold_angular_kernel).
+// Folded plan (see fold_angular_kernel).  A mode's Legendre map is factorised
+// when (1 + n_out)(K + 1 - m) is below GH_FOLD_RANK_PERCENT % of the fused
+// 2 n_out hs^2 / hs (the FMA count per output ring; the factorised form adds a
+// shared-memory pass and a barrier, so the break-even is below 100 %).
+#ifndef GH_FOLD_RANK_PERCENT
+#define GH_FOLD_RANK_PERCENT 75
+#endif
 struct FoldHost {
   int K, M, N4, half, W, hs, qself;
   std::vector<double> Tc, Ts, Q0s, Q0t, Q1s, Q1t;
   double s0, s1;
+  int m0;                               // first mode taken as analysis then synthesis
+  std::vector<int> coef_off, slot_m;    // [K + 2], [coef_off[K + 1]]
+  std::vector<double> A, Y0, Y1;        // [slots][hs]
 };
 
 // The phi grid has N_phi = 2(L+1) points (always even) and the Gauss-Legendre
@@ -418,19 +427,49 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
   if (deriv) build(false, true, h.Q1s, h.Q1t);
   h.s0 = deriv ? -1.0 : 1.0;
   h.s1 = 1.0;
+  // Factorised Legendre maps.  The half-size map of mode m has rank K + 1 - m
+  // (the degrees l = m .. K, split by the parity of l + m between the s and t
+  // parts): projecting onto a_l = sum_j Pbar_lm(theta_j) w_j (s or t)_j and
+  // synthesising sum_l Y_o(l, j) a_l costs (1 + n_out)(K + 1 - m) hs FMAs per
+  // mode instead of the fused 2 n_out hs^2, so it is taken where cheaper.
+  const int n_out = deriv ? 2 : 1;
+  h.m0 = K + 1;
+  for (int m = 0; m <= K; ++m)
+    if ((1 + n_out) * (K + 1 - m) * 100 < GH_FOLD_RANK_PERCENT * 2 * n_out * hs) {
+      h.m0 = m;
+      break;
+    }
+  h.coef_off.assign((size_t)K + 2, 0);
+  for (int m = 0; m <= K; ++m) h.coef_off[m + 1] = h.coef_off[m] + (m >= h.m0 ? K + 1 - m : 0);
+  const int ns = h.coef_off[K + 1];
+  h.slot_m.assign((size_t)std::max(ns, 1), 0);
+  h.A.assign((size_t)std::max(ns, 1) * hs, 0.0);
+  h.Y0.assign((size_t)std::max(ns, 1) * hs, 0.0);
+  h.Y1.assign((size_t)std::max(ns, 1) * hs, 0.0);
+  for (int m = h.m0; m <= K; ++m)
+    for (int l = m; l <= K; ++l) {
+      const int slot = h.coef_off[m] + (l - m);
+      h.slot_m[slot] = m;
+      const size_t pl = ((size_t)l * Wl + m) * nth;
+      for (int j = 0; j < hs; ++j) {
+        h.A[(size_t)slot * hs + j] = P[pl + j] * g.wgl[j];
+        h.Y0[(size_t)slot * hs + j] = cfac(m) * (deriv ? dP[pl + j] : P[pl + j]);
+        h.Y1[(size_t)slot * hs + j] = deriv ? (double)m * cfac(m) * P[pl + j] : 0.0;
+      }
+    }
   return h;
 }
 
 // Shared memory (doubles) per row of the folded kernel: ring values and their
 // quarter folds (reused for the synthesis coefficients) plus the Fourier
 // coefficients of the half-rings.
-size_t fold_row_doubles(int na, int nth, int W, int M, int n_out) {
+size_t fold_row_doubles(int na, int nth, int W, int M, int n_out, int ncoef) {
   const size_t ab = (size_t)M * 2 * (size_t)((nth + 1) / 2);
-  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + ab;
+  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + ab + 2 * (size_t)ncoef;
 }
 
-int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int n_rows, int budget_bytes) {
-  int rb = (int)((size_t)budget_bytes / (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out)));
+int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int ncoef, int n_rows, int budget_bytes) {
+  int rb = (int)((size_t)budget_bytes / (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out, ncoef)));
   if (rb < 1) rb = 1;
   if (rb > 64) rb = 64;
   if (rb > n_rows) rb = n_rows;
@@ -484,15 +523,17 @@ cudaError_t fold_build_maps(gh_domain* d) {
     gh::ShellDev& sh = d->shells_h[s];
     const int rows = gh::NF * sh.n_r;
     const int W = sh.fd.W;
-    sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, rows, d->fd_budget);
+    sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef, rows, d->fd_budget);
     fb2[s] = nfd;
     nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
-    smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta * fold_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2));
+    smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta *
+                              fold_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef));
     ffb[s] = nff;
     if (sh.ff.M > 0) {
-      sh.ff.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.ff.M, 1, rows, d->ff_budget);
+      sh.ff.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef, rows, d->ff_budget);
       nff += (rows + sh.ff.rows_per_cta - 1) / sh.ff.rows_per_cta;
-      smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta * fold_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1));
+      smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta *
+                                fold_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef));
     }
   }
   fb2[n_shells] = nfd;
@@ -944,6 +985,14 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
             if ((e = upload(d, f.Q1s, &q)) != cudaSuccess) return e; P.Q1s = q;
             if ((e = upload(d, f.Q1t, &q)) != cudaSuccess) return e; P.Q1t = q;
           }
+          P.m0 = f.m0;
+          P.ncoef = f.coef_off[f.K + 1];
+          if ((e = upload(d, f.A, &q)) != cudaSuccess) return e; P.A = q;
+          if ((e = upload(d, f.Y0, &q)) != cudaSuccess) return e; P.Y0 = q;
+          if ((e = upload(d, f.Y1, &q)) != cudaSuccess) return e; P.Y1 = q;
+          int* qi = nullptr;
+          if ((e = upload(d, f.coef_off, &qi)) != cudaSuccess) return e; P.coef_off = qi;
+          if ((e = upload(d, f.slot_m, &qi)) != cudaSuccess) return e; P.slot_m = qi;
           fold_cache[key] = P;
         }
         out = fold_cache[key];

@@ -108,6 +108,17 @@ struct FoldPlan {
   const double* Q1s;            // output 1 (value map feeding d/dphi; derivative plan only)
   const double* Q1t;
   double sigma0, sigma1;        // parity of output 0 / 1 (-1 for d/dtheta, +1 for values)
+  // Modes m >= m0 take the Legendre map as analysis then synthesis (its rank
+  // K + 1 - m is below the half-ring size there): per m, slots off[m] ..
+  // off[m + 1] - 1 hold l = m .. K (parity of l + m alternating, s part first);
+  // A [slots][hs] = Pbar_lm(theta_j) w_j, Y0 / Y1 [slots][hs] the synthesis of
+  // output 0 / 1 with the factors of Q0 / Q1; slot_m[slot] = m.
+  int m0, ncoef;                // ncoef = off[K + 1] (cos modes; sin modes use a second bank)
+  const int* coef_off;          // [K + 2]
+  const int* slot_m;            // [ncoef]
+  const double* A;
+  const double* Y0;
+  const double* Y1;
 };
 
 // Tensor spherical-harmonic filter of one shell (tensor_filter kernels).  The
