@@ -49,9 +49,11 @@ sys.path.insert(0, ROOT)
 TRAFFIC_PER_LAUNCH = {
     # pointwise_kernel<1,0,0>, 4-shell L=15: 122.1 MB read + 110.1 MB written
     ("kerr_a0.9_4shells_nr21_L15", "folded", "pointwise"): 232.2e6,
-    # fold_angular_kernel<1> changed (factorised Legendre maps): recaptured below when measured
-    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): None,
-    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): None,
+    # fold_angular_kernel<1> (factorised Legendre maps), 8-shell L=31: 270.3 MB read + 477.1 MB written
+    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): 747.4e6,
+    # fold_angular_kernel<1>, 4-shell L=15: 17.3 MB read, 0 written (L2-resident output)
+    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): 17.3e6,
+    # the paper's 2-shell L=18 grid: not captured since the kernel changed
     ("paper_singlebh_chi0.2_0.3_0.4_2shells_nr10_L18", "folded", "angular"): None,
 }
 
