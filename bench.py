@@ -336,7 +336,7 @@ class ClockSampler:
 KERNEL_NAMES = {"pointwise": "pointwise_kernel (DiffJac + GH RHS + RK4 combine)",
                 "radial": "radial_kernel<false> (Chebyshev d/dx)"}
 ANGULAR_NAMES = {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: folded phi DFT, parity-split "
-                           "Legendre maps, folded inverse DFT)",
+                           "Legendre maps, factorised for high m, folded inverse DFT)",
                  "separable": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, Legendre maps, inverse DFT)",
                  "dense": "gemm_batched_kernel (dense angular maps)"}
 PEAK_SOURCE = ("derived FP64 peak: 152 SMs x 4 SMSPs x one 32-lane DFMA every 64 cycles = 4 flop/clk/SM, at "
