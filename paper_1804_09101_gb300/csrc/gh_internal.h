@@ -375,8 +375,10 @@ cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, doubl
 #ifndef GH_FOLD_ADJ_THREADS
 #define GH_FOLD_ADJ_THREADS 256
 #endif
+// 256 threads and 48 KiB: the fastest of 128-512 threads and 16-112 KiB on the
+// 4-shell (N_r = 21, L = 15) step VJP.
 #ifndef GH_FOLD_ADJ_BUDGET
-#define GH_FOLD_ADJ_BUDGET (72 * 1024)
+#define GH_FOLD_ADJ_BUDGET (48 * 1024)
 #endif
 constexpr int FOLD_ADJ_THREADS = GH_FOLD_ADJ_THREADS;
 constexpr int FOLD_ADJ_BUDGET = GH_FOLD_ADJ_BUDGET;   // shared-memory budget per block (bytes)
