@@ -773,11 +773,21 @@ bool schedule_ok(const int* v) {
          in(v[6], 32, 512) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024) && in(v[8], 0, 1);
 }
 
+// The host path's captured step is rebuilt after any change to the step's
+// launches (algorithm, schedule, overlap, frame, outer condition, S2 filter).
+void invalidate_host_graph(gh_domain* d) {
+  if (d->host_graph) {
+    cudaGraphExecDestroy(d->host_graph);
+    d->host_graph = nullptr;
+  }
+}
+
 void invalidate_graph(gh_domain* d) {
   if (d->graph_exec) {
     cudaGraphExecDestroy(d->graph_exec);
     d->graph_exec = nullptr;
   }
+  invalidate_host_graph(d);
 }
 }  // namespace
 
@@ -1225,6 +1235,7 @@ gh_status gh_destroy_domain(gh_domain* d) {
   if (d->ev_fork) cudaEventDestroy(d->ev_fork);
   if (d->ev_join) cudaEventDestroy(d->ev_join);
   if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
+  if (d->host_graph) cudaGraphExecDestroy(d->host_graph);
   for (void* p : d->owned) cudaFree(p);
   delete d;
   return GH_OK;
@@ -1239,6 +1250,7 @@ gh_status gh_set_stream(gh_domain* d, void* stream) {
 gh_status gh_set_overlap(gh_domain* d, int on) {
   if (!d || (on != 0 && on != 1)) return fail(d, GH_EINVAL, "on must be 0 or 1");
   d->overlap = on != 0;
+  invalidate_host_graph(d);
   return GH_OK;
 }
 
@@ -1296,8 +1308,13 @@ gh_status gh_set_dt_scale(gh_domain* d, int bh, double scale) {
   return GH_OK;
 }
 
-gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
-  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+}  // extern "C"
+
+namespace {
+// One gh_rk4_step captured on a private stream and instantiated into *exec
+// (replacing what it held); nothing executes and the clock stays.
+gh_status capture_step(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, cudaGraphExec_t* exec,
+                       long long* n_launches) {
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   cudaStream_t saved = d->stream;
   cudaStream_t cap = nullptr;
@@ -1319,6 +1336,8 @@ gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work,
   d->stream = saved;
   d->prof = prof;
   cudaStreamDestroy(cap);
+  const long long n = d->launches - n0;
+  d->launches = n0;
   if (st != GH_OK) {
     if (graph) cudaGraphDestroy(graph);
     return st;
@@ -1327,15 +1346,23 @@ gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work,
     if (graph) cudaGraphDestroy(graph);
     return fail(d, GH_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
-  if (d->graph_exec) {
-    cudaGraphExecDestroy(d->graph_exec);
-    d->graph_exec = nullptr;
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
   }
-  e = cudaGraphInstantiate(&d->graph_exec, graph, 0);
+  e = cudaGraphInstantiate(exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(d, GH_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  d->graph_step_launches = d->launches - n0;
-  d->launches = n0;
+  *n_launches = n;
+  return GH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gh_status gh_rk4_graph_capture(gh_domain* d, double dt, double* u, double* work, double* norm2_pre) {
+  if (!d || !u || !work) return fail(d, GH_EINVAL, "null argument");
+  if (gh_status s = capture_step(d, dt, u, work, norm2_pre, &d->graph_exec, &d->graph_step_launches)) return s;
   d->graph_dt = dt;
   return GH_OK;
 }
@@ -1522,10 +1549,22 @@ gh_status gh_rk4_step_host(gh_domain* d, double dt, int n_steps, const double* u
     d->host_work = (double*)pw;
     d->host_norm = (double*)pn;
   }
-  GH_CUDA(d, cudaMemcpyAsync(d->host_u, u_in, bytes, cudaMemcpyHostToDevice, d->stream));
-  for (int i = 0; i < n_steps; ++i)
-    if (gh_status s = rk4_step_impl(d, dt, d->host_u, d->host_work, norm2_out ? d->host_norm : nullptr, nullptr))
+  // the step as a captured graph on the domain's own buffers (captured once per
+  // dt and norm choice, and again after a setter changes the step's launches)
+  const int want_norm = norm2_out ? 1 : 0;
+  if (!d->host_graph || d->host_graph_dt != dt || d->host_graph_norm != want_norm) {
+    if (gh_status s = capture_step(d, dt, d->host_u, d->host_work, want_norm ? d->host_norm : nullptr,
+                                   &d->host_graph, &d->host_graph_launches))
       return s;
+    d->host_graph_dt = dt;
+    d->host_graph_norm = want_norm;
+  }
+  GH_CUDA(d, cudaMemcpyAsync(d->host_u, u_in, bytes, cudaMemcpyHostToDevice, d->stream));
+  for (int i = 0; i < n_steps; ++i) {
+    GH_CUDA(d, cudaGraphLaunch(d->host_graph, d->stream));
+    d->launches += d->host_graph_launches;
+    d->time += dt;                       // each replay advances the device clock by dt
+  }
   GH_CUDA(d, cudaMemcpyAsync(u_out, d->host_u, bytes, cudaMemcpyDeviceToHost, d->stream));
   if (norm2_out)
     GH_CUDA(d, cudaMemcpyAsync(norm2_out, d->host_norm, sizeof(double) * (size_t)d->n_shells,
@@ -1656,6 +1695,7 @@ gh_status gh_set_algorithm(gh_domain* d, int algorithm) {
     if (gh_status st = build_dense(d)) return st;
   }
   d->algorithm = algorithm;
+  invalidate_host_graph(d);
   return GH_OK;
 }
 
@@ -1760,10 +1800,7 @@ gh_status gh_set_rotating_frame(gh_domain* d, const double axis[3], double omega
     d->frames_d = (gh::Frame*)p;
   }
   if (d->clock_d) GH_CUDA(d, cudaMemcpy(d->clock_d, &d->time, sizeof(double), cudaMemcpyHostToDevice));
-  if (d->graph_exec) {
-    cudaGraphExecDestroy(d->graph_exec);
-    d->graph_exec = nullptr;
-  }
+  invalidate_graph(d);
   return GH_OK;
 }
 
@@ -1835,10 +1872,7 @@ gh_status gh_set_frame_map(gh_domain* d, const double axis[3], double omega, dou
   d->fr = gh::frame_at(d, d->time);
   d->frd = nullptr;
   GH_CUDA(d, cudaMemcpy(d->clock_d, &d->time, sizeof(double), cudaMemcpyHostToDevice));
-  if (d->graph_exec) {
-    cudaGraphExecDestroy(d->graph_exec);
-    d->graph_exec = nullptr;
-  }
+  invalidate_graph(d);
   return GH_OK;
 }
 
@@ -1870,10 +1904,7 @@ gh_status gh_set_outer_bc(gh_domain* d, int mode) {
     d->cpm_S = (double*)p;
   }
   d->outer_bc = mode;
-  if (d->graph_exec) {
-    cudaGraphExecDestroy(d->graph_exec);
-    d->graph_exec = nullptr;
-  }
+  invalidate_graph(d);
   return GH_OK;
 }
 
@@ -1892,10 +1923,7 @@ gh_status gh_set_sh_filter(gh_domain* d, int mode) {
     GH_CUDA(d, gh::tensor_filter_prepare(d, xs, ws));
   }
   d->sh_filter_mode = mode;
-  if (d->graph_exec) {
-    cudaGraphExecDestroy(d->graph_exec);
-    d->graph_exec = nullptr;
-  }
+  invalidate_graph(d);
   return GH_OK;
 }
 

@@ -304,6 +304,12 @@ struct gh_domain {
   // CUDA graph of one RK4 step (gh_rk4_graph_capture / _launch)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_step_launches = 0;
+  // gh_rk4_step_host's own captured step on host_u / host_work (dt and whether
+  // it writes the norms), rebuilt when a setter changes the step's launches
+  cudaGraphExec_t host_graph = nullptr;
+  double host_graph_dt = 0.0;
+  int host_graph_norm = 0;
+  long long host_graph_launches = 0;
   // device state, RK4 work area and norms of gh_rk4_step_host (allocated on first use)
   double* host_u = nullptr;
   double* host_work = nullptr;
