@@ -187,10 +187,14 @@ gh_status gh_rk4_step(gh_domain* dom, double dt, double* u, double* work, double
  * work area), takes n_steps gh_rk4_step steps (filters included), copies the
  * result to u_out (host, one state; may equal u_in) and, if norm2_out (host,
  * n_shells doubles) is given, the constraint norms of the state the last step
- * started from.  Synchronises the stream before returning.  Pinned host
- * buffers (cudaHostAlloc, cudaHostRegister) copy asynchronously at full speed;
- * pageable ones work too.  Errors: GH_EINVAL for n_steps < 1 or a NULL
- * buffer, GH_ENOMEM on the first call, GH_ECUDA. */
+ * started from.  The steps replay a CUDA graph of one step on those buffers,
+ * captured on the first call with a given dt (and norm2_out null or not) and
+ * again after any setter that changes the step's launches (algorithm,
+ * schedule, overlap, frame, outer condition, S2 filter); it is separate from
+ * gh_rk4_graph_capture's graph.  Synchronises the stream before returning.
+ * Pinned host buffers (cudaHostAlloc, cudaHostRegister) copy asynchronously at
+ * full speed; pageable ones work too.  Errors: GH_EINVAL for n_steps < 1 or a
+ * NULL buffer, GH_ENOMEM on the first call, GH_ECUDA. */
 gh_status gh_rk4_step_host(gh_domain* dom, double dt, int n_steps, const double* u_in, double* u_out,
                            double* norm2_out);
 
