@@ -85,6 +85,9 @@ def parse():
                         "general map (expansion 0.01, translation (0.01, 0, 0), rotation 0.25 about a tilted "
                         "axis), with the hole's gauge source and boundary data evaluated at the moving points "
                         "every stage")
+    p.add_argument("--outer-bc", default="freeze", choices=["freeze", "cp", "cp_full"],
+                   help="outer boundary condition: freeze (default); cp: constraint preserving for u^psi and "
+                        "u^0; cp_full: also the constraint part of u^- (static grid only)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched, adjoint and 4-shell figures added to the large workload's line")
     p.add_argument("--no-graph", action="store_true",
@@ -405,6 +408,9 @@ def measure_rk4(args, w, pg=None, host_e2e=True, clock_index=0):
         gh.gh_set_rotating_frame(dom, (0.0, 0.0, 1.0), 0.25)
     elif frame == "map":
         gh.gh_set_frame_map(dom, (0.6, 0.0, 0.8), 0.25, 0.01, (0.01, 0.0, 0.0))
+    outer_bc = getattr(args, "outer_bc", "freeze")
+    gh.gh_set_outer_bc(dom, {"freeze": gh.GH_BC_FREEZE, "cp": gh.GH_BC_CONSTRAINT_PRESERVING,
+                             "cp_full": gh.GH_BC_CONSTRAINT_PRESERVING_FULL}[outer_bc])
     work = dom.new_work()
     norm2 = torch.zeros(len(w.shells), dtype=torch.float64, device=dev)
     state_bytes = dom.state_size * 8
@@ -565,7 +571,7 @@ def run_ours(args, w):
                                         if m["use_graph"] else "one gh_rk4_step call"),
                             kernel_times="per-family CUDA events on the domain's stream, from a second "
                                          "timed region of the same steps called directly",
-                            overlap=not args.no_overlap, frame=args.frame,
+                            overlap=not args.no_overlap, frame=args.frame, outer_bc=args.outer_bc,
                             parallelism="replicas" if world > 1 else "single GPU", algorithm=m["algorithm"],
                             schedule=m["schedule"], autotuned=not (args.no_autotune or args.schedule)),
                 e2e=m["e2e"], gpu_launches=m["launches"], roofline=m["roofline"], kernels=m["kernels"])
