@@ -367,9 +367,16 @@ struct CpmPoint {
   double ud[50];
   double wm_int[10];
   double l_dn[4], l_up[4], P[10];
-  double vdir[6][50];
   double res[10][4];
 };
+
+// The field-space direction of slope evaluation e = 4..9 (w^- = E_e), rebuilt
+// where it is needed instead of stored.
+__device__ __forceinline__ void cpm_point_vdir(const CpmPoint& S, const CpmBg& b, int e, double* v) {
+  double E[10];
+  cpm_basis(e - 4, S.l_dn, S.P, S.wm_int, E);
+  cpm_vdir(E, b.n_dn, v);
+}
 
 struct CpmAdjArgs {
   const BcSliceDev* slices;
@@ -430,17 +437,14 @@ __global__ void __launch_bounds__(64) cp_minus_adjoint_kernel(CpmAdjArgs a) {
   cpm_state(S);
   cpm_tetrad(b, S.l_dn, S.l_up, S.P);
   for (int p = 0; p < 10; ++p) cpm_pair(p, S.k, S.u, S.du, b, a.gamma1, a.gamma2, S.ud, &S.wm_int[p]);
-  for (int e = 0; e < 6; ++e) {
-    double E[10];
-    cpm_basis(e, S.l_dn, S.P, S.wm_int, E);
-    cpm_vdir(E, b.n_dn, S.vdir[e]);
-  }
+  double vtmp[50];
   double dH[3][4];
   for (int i = 0; i < 3; ++i)
     for (int c = 0; c < 4; ++c) dH[i][c] = gauge[(long long)(4 + 4 * i + c) * na];
   const double zero4[4] = {0.0, 0.0, 0.0, 0.0};
   for (int e = 0; e < 10; ++e) {
-    const double* v = (e == 0) ? S.ud : (e <= 3 ? S.du[e - 1] : S.vdir[e - 4]);
+    if (e >= 4) cpm_point_vdir(S, b, e, vtmp);
+    const double* v = (e == 0) ? S.ud : (e <= 3 ? S.du[e - 1] : vtmp);
     double r[4];
     gauge_constraint_dir(S, v, (e >= 1 && e <= 3) ? dH[e - 1] : zero4, r);
     const double sc = (e >= 4) ? 1.0 / b.Nb : 1.0;
@@ -497,7 +501,8 @@ __global__ void __launch_bounds__(64) cp_minus_adjoint_kernel(CpmAdjArgs a) {
     const double sc = (e >= 4) ? 1.0 / b.Nb : 1.0;
     double ob[4];
     for (int c = 0; c < 4; ++c) ob[c] = resb[e][c] * sc;
-    const double* v = (e == 0) ? S.ud : (e <= 3 ? S.du[e - 1] : S.vdir[e - 4]);
+    if (e >= 4) cpm_point_vdir(S, b, e, vtmp);
+    const double* v = (e == 0) ? S.ud : (e <= 3 ? S.du[e - 1] : vtmp);
     double* vb = (e == 0) ? udb : (e <= 3 ? dub[e - 1] : (e == 9 ? v9b : nullptr));
     gauge_constraint_dir_rev(S, v, ob, sb, vb);
   }
