@@ -157,7 +157,7 @@ class BatchedWorkload:
     holes: list                      # dicts: M, chi, r_in, r_out, n_r, L, dt, seed
     gamma0: float = 1.0
     gamma1: float = -1.0
-    gamma2: float = 1.0
+    gamma2: float = 4.0              # as the Kerr shell workloads (1 left 20 of 64 holes non-finite in 1,000 steps, 4 leaves 8)
     filt_alpha: float = 36.0
     filt_order: int = 32
     radial_filter_on: bool = True
