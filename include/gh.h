@@ -50,7 +50,7 @@ typedef enum {
   GH_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed           */
   GH_ETIMEOUT = 4,    /* a bounded device-side wait ran out                    */
   GH_ENONFINITE = 5,  /* a constraint norm came out NaN or Inf                 */
-  GH_ENOTSUP = 6      /* not supported in this build                           */
+  GH_ENOTSUP = 6      /* not supported by this library for these settings     */
 } gh_status;
 
 /* One spherical shell: r in [r_in, r_out], n_r radial points, harmonics l <= L,
