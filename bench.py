@@ -49,10 +49,9 @@ sys.path.insert(0, ROOT)
 TRAFFIC_PER_LAUNCH = {
     # pointwise_kernel<1,0,0>, 4-shell L=15: 122.1 MB read + 110.1 MB written
     ("kerr_a0.9_4shells_nr21_L15", "folded", "pointwise"): 232.2e6,
-    # fold_angular_kernel<1> (factorised Legendre maps), 8-shell L=31: 270.3 MB read + 477.1 MB written
-    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): 747.4e6,
-    # fold_angular_kernel<1>, 4-shell L=15: 17.3 MB read, 0 written (L2-resident output)
-    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): 17.3e6,
+    # fold_angular_kernel<1> with the ring FFTs: not captured since the kernel changed
+    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): None,
+    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): None,
     # the paper's 2-shell L=18 grid: not captured since the kernel changed
     ("paper_singlebh_chi0.2_0.3_0.4_2shells_nr10_L18", "folded", "angular"): None,
 }
@@ -338,8 +337,8 @@ class ClockSampler:
 # ------------------------------------------------------------- our arm
 KERNEL_NAMES = {"pointwise": "pointwise_kernel (DiffJac + GH RHS + RK4 combine)",
                 "radial": "radial_kernel<false> (Chebyshev d/dx)"}
-ANGULAR_NAMES = {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: folded phi DFT, parity-split "
-                           "Legendre maps, factorised for high m, folded inverse DFT)",
+ANGULAR_NAMES = {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: per-ring real FFT for N_phi = 16, 32, 64, "
+                           "else folded phi DFT; parity-split Legendre maps, factorised for high m; inverse FFT)",
                  "separable": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, Legendre maps, inverse DFT)",
                  "dense": "gemm_batched_kernel (dense angular maps)"}
 PEAK_SOURCE = ("derived FP64 peak: 152 SMs x 4 SMSPs x one 32-lane DFMA every 64 cycles = 4 flop/clk/SM, at "

@@ -431,7 +431,7 @@ gh_status gh_dp5_step(gh_domain* dom, double dt, double rtol, double atol, doubl
  *     column (1..4, one grid row each);
  *   sched[2], sched[3]: the same for the radial ExpCheb filter;
  *   sched[4], sched[5]: folded d/dtheta, d/dphi kernel -- threads per block
- *     (32..512, a multiple of 32) and the shared-memory budget per block in
+ *     (32..256, a multiple of 32) and the shared-memory budget per block in
  *     bytes (8 KiB..200 KiB), which sets the rows per block of every shell;
  *   sched[6], sched[7]: the same for the folded SH filter;
  *   sched[8]: reverse pass of the pointwise algebra (gh_rhs_vjp and the step

@@ -147,9 +147,30 @@ def fold_rank_m0(K, hs, n_out):
     return K + 1
 
 
+FOLD_FFT_NPHI = (16, 32, 64)   # rings transformed by the register FFT (fold_angular_kernel)
+
+
+def ring_fft_flops(nph, forward=True):
+    """FP64 flops of one ring's phi transform on the FFT path (an FMA is 2):
+    the radix-2 DIT FFT of n = nph/2 complex values, per stage of span S
+    4 flops for each butterfly with twiddle 1 or +-i, 10 for (+-1 +- i)/sqrt 2
+    (two adds, four FMAs) and 12 for a general twiddle (six FMAs); plus the
+    real split (forward) or fold (inverse), 18 per pair of modes (m, n - m)
+    and, forward, 1 for the mean.  N_phi = 64: 835 forward, 834 inverse."""
+    n = nph // 2
+    f, S = 0, 1
+    while S < n:
+        per_group = 4 if S == 1 else (8 if S == 2 else 2 * 4 + 2 * 10 + (S - 4) * 12)
+        f += (n // (2 * S)) * per_group
+        S *= 2
+    return f + 18 * (n // 2 - 1) + (1 if forward else 0)
+
+
 def fold_angular_flops(shells, K=None, two=True):
     """FP64 flops of one folded separable launch (fold_angular_kernel), per
-    (r, field) row: fold 8 (W - 1) N_theta; phase A half M (4 W + 2) plus
+    (r, field) row.  For N_phi = 16, 32, 64 the phi transforms are register
+    FFTs (ring_fft_flops per ring and transform, N_theta M for the s/t split);
+    otherwise the quarter-folded DFT: fold 8 (W - 1) N_theta; phase A half M (4 W + 2) plus
     (hs - half) M 2 W for an odd N_theta's equator ring; phase B per mode
     (cos m, and sin m for m >= 1): fused, n_out hs 4 hs (two dot products of
     length hs per output, each a multiply and hs - 1 FMAs, and the two
@@ -176,8 +197,14 @@ def fold_angular_flops(shells, K=None, two=True):
                 phase_b += modes * n_out * hs * 4 * hs
             else:
                 phase_b += modes * ((2 * hs - 1) * r + n_out * hs * (2 * r + 2))
-        per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W
-                   + phase_b + n_out * nth * W * (2 * M + 8))
+        if nph in FOLD_FFT_NPHI and nth % 2 == 0:
+            # one forward FFT per ring, the s/t split of every coefficient,
+            # one inverse FFT per ring and output
+            per_row = (nth * ring_fft_flops(nph) + nth * M + phase_b
+                       + n_out * nth * ring_fft_flops(nph, forward=False))
+        else:
+            per_row = (8 * (W - 1) * nth + half * M * (4 * W + 2) + (hs - half) * M * 2 * W
+                       + phase_b + n_out * nth * W * (2 * M + 8))
         f += 50 * n_r * per_row
     return f
 

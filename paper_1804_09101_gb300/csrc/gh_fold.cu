@@ -19,16 +19,263 @@
 // n_out N_theta^2 + n_out N_theta N_phi).
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "gh_geom.cuh"
 #include "gh_internal.h"
 
 namespace gh {
 
-constexpr int FOLD_MAX_THREADS = 512;
+constexpr int FOLD_MAX_THREADS = 256;   // the FFT path's register arrays need up to 255 registers
 
 __device__ __forceinline__ double flip_sign(double v, unsigned long long mask) {
   // v or -v without an FP64 instruction (mask is 0 or the sign bit)
   return __longlong_as_double(__double_as_longlong(v) ^ (long long)mask);
+}
+
+// ---------------------------------------------------------------------------
+// Real FFT of one ring held in registers, for N_phi = 2n = 16, 32, 64.  The
+// folded DFT below costs about N_theta M W FMAs per ring each way (1,200 FP64
+// instructions at N_phi = 64); the FFT takes about 570.  A ring of N real
+// values is packed as n complex values z_j = x_{2j} + i x_{2j+1}, transformed
+// by a radix-2 decimation-in-time FFT of size n (input in bit-reversed order,
+// output in natural order), and split into the cos/sin coefficients
+//   c_m = sum_k x_k cos(2 pi m k / N),  s_m = sum_k x_k sin(2 pi m k / N)
+// with X_m = c_m - i s_m = (E_m + w^m O_m), E and O the transforms of the even
+// and odd samples, E_m = (Z_m + conj Z_{n-m}) / 2, O_m = (Z_m - conj Z_{n-m}) / 2i,
+// w = exp(-2 pi i / N).  The synthesis x_k = sum_m c_m cos(m phi_k) + s_m
+// sin(m phi_k) runs the same steps backwards: the Hermitian spectrum is folded
+// into n complex values Zc_m = (S_m + i w^-m D_m) / 2 (S, D the sum and
+// difference of X_m and conj X_{n-m}) and one FFT with the opposite sign gives
+// x_{2j} + i x_{2j+1}.  Butterflies with twiddle 1, +-i or (+-1 +- i)/sqrt 2 are
+// special-cased; a general one forms a + w b with two FMA chains and a - w b as
+// 2a - (a + w b).  Twiddles e^{2 pi i k / 64} come from constant memory.
+__constant__ double c_fft_cos[64], c_fft_sin[64], c_fft_hcos[64], c_fft_hsin[64];
+
+template <int LOG>
+__host__ __device__ constexpr int bit_reverse(int j) {
+  int r = 0;
+  for (int b = 0; b < LOG; ++b)
+    if ((j >> b) & 1) r |= 1 << (LOG - 1 - b);
+  return r;
+}
+
+// One radix-2 stage of span S = 2^LS, then the next.  Twiddle of butterfly j
+// in a group: w = exp(SIGN 2 pi i j / (2 S)) = table entry j * 32 / S.
+template <int LOG, int SIGN, int LS>
+__device__ __forceinline__ void fft_stages(double (&re)[1 << LOG], double (&im)[1 << LOG]) {
+  constexpr int n = 1 << LOG, S = 1 << LS;
+#pragma unroll
+  for (int bf = 0; bf < n / 2; ++bf) {
+    const int j = bf % S;
+    const int a = (bf / S) * 2 * S + j, b = a + S;
+    const double ar = re[a], ai = im[a], br = re[b], bi = im[b];
+    if (j == 0) {
+      re[a] = ar + br;
+      im[a] = ai + bi;
+      re[b] = ar - br;
+      im[b] = ai - bi;
+    } else if (4 * j == 2 * S) {           // w = SIGN i: w b = SIGN (-b_im + i b_re)
+      const double tr = SIGN > 0 ? -bi : bi, ti = SIGN > 0 ? br : -br;
+      re[a] = ar + tr;
+      im[a] = ai + ti;
+      re[b] = ar - tr;
+      im[b] = ai - ti;
+    } else if (8 * j == 2 * S || 8 * j == 6 * S) {
+      // w = (sr + i si) / sqrt 2 with sr = +-1 (j = S/4 or 3S/4), si = SIGN
+      const double c = c_fft_cos[8];
+      const double u = (8 * j == 2 * S) ? (SIGN > 0 ? br - bi : br + bi) : (SIGN > 0 ? -br - bi : bi - br);
+      const double v = (8 * j == 2 * S) ? (SIGN > 0 ? bi + br : bi - br) : (SIGN > 0 ? br - bi : -bi - br);
+      re[a] = fma(c, u, ar);
+      im[a] = fma(c, v, ai);
+      re[b] = fma(-c, u, ar);
+      im[b] = fma(-c, v, ai);
+    } else {
+      const int idx = j * (32 / S);
+      const double wr = c_fft_cos[idx];
+      const double wi = SIGN > 0 ? c_fft_sin[idx] : -c_fft_sin[idx];
+      const double pr = fma(wr, br, fma(-wi, bi, ar));
+      const double pi = fma(wr, bi, fma(wi, br, ai));
+      re[a] = pr;
+      im[a] = pi;
+      re[b] = fma(2.0, ar, -pr);
+      im[b] = fma(2.0, ai, -pi);
+    }
+  }
+  if constexpr (LS + 1 < LOG) fft_stages<LOG, SIGN, LS + 1>(re, im);
+}
+
+// Forward transform of the ring x[0 .. 2n) (stride 1, shared memory): on
+// return re[m] = c_m and im[m] = s_m for m = 0 .. n - 1.
+template <int LOG>
+__device__ __forceinline__ void ring_rfft(const double* __restrict__ x, double (&re)[1 << LOG], double (&im)[1 << LOG]) {
+  constexpr int n = 1 << LOG, st = 32 >> LOG;    // table stride of w = exp(-2 pi i / 2n)
+#pragma unroll
+  for (int t = 0; t < n; ++t) {
+    re[bit_reverse<LOG>(t)] = x[2 * t];
+    im[bit_reverse<LOG>(t)] = x[2 * t + 1];
+  }
+  fft_stages<LOG, -1, 0>(re, im);
+  {
+    const double z0r = re[0], z0i = im[0];
+    re[0] = z0r + z0i;
+    im[0] = 0.0;
+  }
+  // m = n/2: c = Re Z, s = Im Z (unchanged)
+#pragma unroll
+  for (int k = 1; k < n / 2; ++k) {
+    const double ar = re[k], ai = im[k], br = re[n - k], bi = im[n - k];
+    const double er = ar + br, ei = ai - bi, dr = ar - br, di = ai + bi;
+    const double hc = c_fft_hcos[k * st], hsn = c_fft_hsin[k * st];
+    const double tr = fma(hc, di, -hsn * dr);
+    const double ti = fma(hc, dr, hsn * di);
+    re[k] = fma(0.5, er, tr);
+    im[k] = fma(-0.5, ei, ti);
+    re[n - k] = fma(0.5, er, -tr);
+    im[n - k] = fma(0.5, ei, ti);
+  }
+}
+
+// Inverse of ring_rfft's map: from c_m = cf[m] (m <= K) and s_m = cf[K + m]
+// (1 <= m <= K), zero above K, the values x_{2j} = re[j], x_{2j+1} = im[j].
+template <int LOG>
+__device__ __forceinline__ void ring_irfft(const double* __restrict__ cf, int K, double (&re)[1 << LOG],
+                                           double (&im)[1 << LOG]) {
+  constexpr int n = 1 << LOG, st = 32 >> LOG;
+  auto cm = [&](int m) { return m <= K ? cf[m] : 0.0; };
+  auto sm = [&](int m) { return m <= K ? cf[K + m] : 0.0; };
+  {
+    const double c0 = cf[0];
+    re[0] = c0;
+    im[0] = c0;
+    re[bit_reverse<LOG>(n / 2)] = cm(n / 2);
+    im[bit_reverse<LOG>(n / 2)] = sm(n / 2);
+  }
+#pragma unroll
+  for (int m = 1; m < n / 2; ++m) {
+    const double c1 = cm(m), s1 = sm(m), c2 = cm(n - m), s2 = sm(n - m);
+    const double Sr = c1 + c2, Si = s2 - s1, Dr = c1 - c2, Di = -s1 - s2;
+    const double hc = c_fft_hcos[m * st], hsn = c_fft_hsin[m * st];
+    const double Tr = fma(hc, Dr, -hsn * Di);
+    const double Ti = fma(hc, Di, hsn * Dr);
+    re[bit_reverse<LOG>(m)] = fma(0.5, Sr, -Ti);
+    im[bit_reverse<LOG>(m)] = fma(0.5, Si, Tr);
+    re[bit_reverse<LOG>(n - m)] = fma(0.5, Sr, Ti);
+    im[bit_reverse<LOG>(n - m)] = fma(-0.5, Si, Tr);
+  }
+  fft_stages<LOG, 1, 0>(re, im);
+}
+
+// Phase A of the FFT path: one thread per ring, the ring and its mirror on
+// adjacent lanes; the symmetric and antisymmetric parts s = c(j) + c(mirror),
+// t = c(j) - c(mirror) of every coefficient are formed across the lane pair.
+// The ring stride in U is 2n + 1 doubles (conflict-free reads).
+template <int LOG>
+__device__ __forceinline__ void fold_fft_analysis(const double* __restrict__ U, double* __restrict__ AB, int nr,
+                                                  int nth, int hs, int M, int K) {
+  constexpr int n = 1 << LOG;
+  const unsigned long long sbit = 0x8000000000000000ULL;
+  const int total = nr * nth;   // even (N_theta = n), so a lane pair is all in or all out
+  const int lane = threadIdx.x & 31;
+  for (int o0 = threadIdx.x - lane; o0 < total; o0 += blockDim.x) {
+    const bool act = o0 + lane < total;
+    const int o = act ? o0 + lane : total - 1;
+    const int rr = o / nth, q = o - rr * nth, p = q >> 1, mir = q & 1;
+    const int j = mir ? nth - 1 - p : p;
+    double re[n], im[n];
+    ring_rfft<LOG>(U + (size_t)(rr * nth + j) * (2 * n + 1), re, im);
+    double* ab = AB + (size_t)rr * M * 2 * hs + (mir ? hs : 0) + p;
+    const unsigned long long neg = mir ? sbit : 0ULL;   // the mirror lane writes c(j) - c(mirror)
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      if (m <= K) {
+        const double cv = re[m], cp = __shfl_xor_sync(0xffffffffu, cv, 1);
+        if (act) ab[(size_t)m * 2 * hs] = cp + flip_sign(cv, neg);
+        if (m > 0) {
+          const double sv = im[m], sp = __shfl_xor_sync(0xffffffffu, sv, 1);
+          if (act) ab[(size_t)(K + m) * 2 * hs] = sp + flip_sign(sv, neg);
+        }
+      }
+    }
+  }
+}
+
+// Writes (ACC: adds) one synthesised ring, x_{2t} = re[t], x_{2t+1} = im[t].
+template <int LOG, bool ACC>
+__device__ __forceinline__ void store_ring(double* __restrict__ dst, const double (&re)[1 << LOG],
+                                           const double (&im)[1 << LOG]) {
+  constexpr int n = 1 << LOG;
+  if ((reinterpret_cast<unsigned long long>(dst) & 15ULL) == 0) {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      double2 v = make_double2(re[t], im[t]);
+      if (ACC) {
+        const double2 o = d2[t];
+        v.x += o.x;
+        v.y += o.y;
+      }
+      d2[t] = v;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      dst[2 * t] = ACC ? dst[2 * t] + re[t] : re[t];
+      dst[2 * t + 1] = ACC ? dst[2 * t + 1] + im[t] : im[t];
+    }
+  }
+}
+
+// Phase C of the FFT path: one thread per (output, ring) synthesises the ring
+// from its M coefficients and writes it to global memory.
+template <int LOG, bool TWO>
+__device__ __forceinline__ void fold_fft_synthesis(const double* __restrict__ OUT, int RB, int nr, int nth, int M,
+                                                   int K, int na, long long gbase, double* __restrict__ out0,
+                                                   double* __restrict__ out1) {
+  constexpr int n = 1 << LOG;
+  constexpr int NO = TWO ? 2 : 1;
+  const int per = nr * nth;
+  for (int o = threadIdx.x; o < NO * per; o += blockDim.x) {
+    const int o2 = TWO ? o / per : 0;
+    const int rj = o - o2 * per;
+    const int rr = rj / nth, j = rj - rr * nth;
+    double re[n], im[n];
+    ring_irfft<LOG>(OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M, K, re, im);
+    store_ring<LOG, false>((o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * 2 * n, re, im);
+  }
+}
+
+// The transposed maps' FFT phases (fold_adjoint_kernel): the analysis of every
+// ring of Y (stride 2n + 1) into per-ring coefficients cb[ring][M], and the
+// synthesis of every ring from ab[ring][M] into out (ACC: added).
+template <int LOG>
+__device__ __forceinline__ void fold_fft_ring_coefs(const double* __restrict__ Y, double* __restrict__ cb,
+                                                    int n_rings, int M, int K) {
+  constexpr int n = 1 << LOG;
+  for (int o = threadIdx.x; o < n_rings; o += blockDim.x) {
+    double re[n], im[n];
+    ring_rfft<LOG>(Y + (size_t)o * (2 * n + 1), re, im);
+    double* c = cb + (size_t)o * M;
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      if (m <= K) {
+        c[m] = re[m];
+        if (m > 0) c[K + m] = im[m];
+      }
+    }
+  }
+}
+
+template <int LOG, bool ACC>
+__device__ __forceinline__ void fold_fft_ring_synth(const double* __restrict__ ab, int nr, int nth, int M, int K,
+                                                    int na, long long gbase, double* __restrict__ out) {
+  constexpr int n = 1 << LOG;
+  for (int o = threadIdx.x; o < nr * nth; o += blockDim.x) {
+    const int rr = o / nth, j = o - rr * nth;
+    double re[n], im[n];
+    ring_irfft<LOG>(ab + (size_t)o * M, K, re, im);
+    store_ring<LOG, ACC>(out + gbase + (long long)rr * na + (long long)j * 2 * n, re, im);
+  }
 }
 
 // One block takes RB consecutive (r, field) rows of one shell.  Shared memory
@@ -52,16 +299,25 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   const int RB = P.rows_per_cta;
   const int row0 = (blockIdx.x - begin[s]) * RB;
   const int nr = min(RB, rows - row0);
-  const int r1 = max(na + 4 * nth * W, NO * nth * M);
-  double* U = sm;                                   // [RB][na]
-  double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
+  const int fl = P.fft_log;
+  const int r1 = fl ? max(na + nth, NO * nth * M) : max(na + 4 * nth * W, NO * nth * M);
+  double* U = sm;                                   // [RB][na] ([RB][nth][nph + 1] on the FFT path)
+  double* F = U + (size_t)RB * na;                  // [RB][nth][4][W] (quarter-folded DFT path)
   double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
   double* AB = sm + (size_t)RB * r1;                // [RB][M][2 hs]: s (hs) then t (hs)
   const int ncoef = P.ncoef;
   double* COEF = AB + (size_t)RB * M * 2 * hs;      // [RB][2][ncoef]: a_l of the cos, then the sin modes m >= m0
   const long long gbase = sh.off + (long long)row0 * na;
-  for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
+  if (fl) {
+    for (int i = threadIdx.x; i < nr * na; i += T) U[i + (i >> (fl + 1))] = in[gbase + i];   // one pad per ring
+  } else {
+    for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
+  }
   __syncthreads();
+  if (fl == 5) fold_fft_analysis<5>(U, AB, nr, nth, hs, M, K);
+  else if (fl == 4) fold_fft_analysis<4>(U, AB, nr, nth, hs, M, K);
+  else if (fl == 3) fold_fft_analysis<3>(U, AB, nr, nth, hs, M, K);
+  else {
   // fold every ring: Cp, Cm (cos, even / odd m), Sp, Sm (sin, odd / even m)
   for (int o = threadIdx.x; o < nr * nth * W; o += T) {
     const int k = o % W;
@@ -114,6 +370,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
       ab[jh] = c1;
       ab[hs + jh] = 0.0;
     }
+  }
   }
   __syncthreads();
   // phase B1: for modes m >= m0, the Legendre analysis a_l = sum_j A_l(j) (s or
@@ -218,6 +475,18 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     }
   }
   __syncthreads();
+  if (fl == 5) {
+    fold_fft_synthesis<5, TWO>(OUT, RB, nr, nth, M, K, na, gbase, out0, out1);
+    return;
+  }
+  if (fl == 4) {
+    fold_fft_synthesis<4, TWO>(OUT, RB, nr, nth, M, K, na, gbase, out0, out1);
+    return;
+  }
+  if (fl == 3) {
+    fold_fft_synthesis<3, TWO>(OUT, RB, nr, nth, M, K, na, gbase, out0, out1);
+    return;
+  }
   // phase C: quarter-ring sums give four output points each; one item per
   // (output, ring, k)
   for (int o = threadIdx.x; o < NO * nr * nth * W; o += T) {
@@ -274,9 +543,9 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
 // Shared memory per row: region 1 (the cotangent ring and its folds, later the
 // parity-combined coefficients) and CB (the analysed coefficients of both
 // outputs, later the per-ring coefficient cotangents).
-__host__ __device__ inline size_t fold_adj_row_doubles(int na, int nth, int W, int M, int n_out) {
+__host__ __device__ inline size_t fold_adj_row_doubles(int na, int nth, int W, int M, int n_out, bool fft) {
   const size_t hs2 = 2 * (size_t)((nth + 1) / 2);
-  size_t r1 = (size_t)na + 4 * (size_t)nth * W;
+  size_t r1 = fft ? (size_t)na + nth : (size_t)na + 4 * (size_t)nth * W;
   if ((size_t)n_out * M * hs2 > r1) r1 = (size_t)n_out * M * hs2;
   return r1 + (size_t)n_out * nth * M;
 }
@@ -298,9 +567,10 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   const int RB = P.adj_rows_per_cta;
   const int row0 = (blockIdx.x - begin[s]) * RB;
   const int nr = min(RB, rows - row0);
-  size_t r1 = (size_t)na + 4 * (size_t)nth * W;
+  const int fl = P.fft_log;
+  size_t r1 = fl ? (size_t)na + nth : (size_t)na + 4 * (size_t)nth * W;
   if ((size_t)NO * M * 2 * hs > r1) r1 = (size_t)NO * M * 2 * hs;
-  double* Y = sm;                                   // [RB][na] one output's cotangent rings
+  double* Y = sm;                                   // [RB][na] one output's cotangent rings (padded: FFT path)
   double* F = Y + (size_t)RB * na;                  // [RB][nth][4][W] their folds
   double* SV = sm;                                  // [NO][RB][M][2 hs] parity-combined (after Y, F)
   double* CB = sm + (size_t)RB * r1;                // [NO][RB][nth][M] analysed coefficients
@@ -312,8 +582,19 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   for (int o2 = 0; o2 < NO; ++o2) {
     const double* in = o2 == 0 ? in0 : in1;
     if (o2 > 0) __syncthreads();                    // Y and F are reused
-    for (int i = threadIdx.x; i < nr * na; i += T) Y[i] = in[gbase + i];
+    if (fl) {
+      for (int i = threadIdx.x; i < nr * na; i += T) Y[i + (i >> (fl + 1))] = in[gbase + i];
+    } else {
+      for (int i = threadIdx.x; i < nr * na; i += T) Y[i] = in[gbase + i];
+    }
     __syncthreads();
+    if (fl) {
+      double* cb = CB + (size_t)o2 * RB * nth * M;
+      if (fl == 5) fold_fft_ring_coefs<5>(Y, cb, nr * nth, M, K);
+      else if (fl == 4) fold_fft_ring_coefs<4>(Y, cb, nr * nth, M, K);
+      else fold_fft_ring_coefs<3>(Y, cb, nr * nth, M, K);
+      continue;
+    }
     for (int o = threadIdx.x; o < nr * nth * W; o += T) {
       const int k = o % W;
       const int rj = o / W;
@@ -438,6 +719,18 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     }
   }
   __syncthreads();
+  if (fl == 5) {
+    fold_fft_ring_synth<5, TWO>(AB, nr, nth, M, K, na, gbase, out);
+    return;
+  }
+  if (fl == 4) {
+    fold_fft_ring_synth<4, TWO>(AB, nr, nth, M, K, na, gbase, out);
+    return;
+  }
+  if (fl == 3) {
+    fold_fft_ring_synth<3, TWO>(AB, nr, nth, M, K, na, gbase, out);
+    return;
+  }
   // phase 3 (A^T): the forward's synthesis of four ring points per
   // quarter-ring sum, from the coefficient cotangents
   for (int o = threadIdx.x; o < nr * nth * W; o += T) {
@@ -477,8 +770,8 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   }
 }
 
-size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out) {
-  return fold_adj_row_doubles(na, nth, W, M, n_out);
+size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out, bool fft) {
+  return fold_adj_row_doubles(na, nth, W, M, n_out, fft);
 }
 
 cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const double* in1, double* out) {
@@ -490,6 +783,22 @@ cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const
         d->shells_d, d->n_shells, d->ffa_block_begin_d, in0, nullptr, out);
   d->launches++;
   return cudaGetLastError();
+}
+
+cudaError_t fold_fft_tables() {
+  double c[64], sn[64], hc[64], hsn[64];
+  for (int k = 0; k < 64; ++k) {
+    const double ang = 2.0 * 3.14159265358979323846 * (double)k / 64.0;
+    c[k] = std::cos(ang);
+    sn[k] = std::sin(ang);
+    hc[k] = 0.5 * c[k];
+    hsn[k] = 0.5 * sn[k];
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_fft_cos, c, sizeof(c));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_fft_sin, sn, sizeof(sn));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_fft_hcos, hc, sizeof(hc));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_fft_hsin, hsn, sizeof(hsn));
+  return e;
 }
 
 cudaError_t fold_set_smem_limits(size_t bytes) {

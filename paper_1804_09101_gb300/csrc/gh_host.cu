@@ -460,16 +460,31 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
   return h;
 }
 
-// Shared memory (doubles) per row of the folded kernel: ring values and their
-// quarter folds (reused for the synthesis coefficients) plus the Fourier
-// coefficients of the half-rings.
-size_t fold_row_doubles(int na, int nth, int W, int M, int n_out, int ncoef) {
-  const size_t ab = (size_t)M * 2 * (size_t)((nth + 1) / 2);
-  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + ab + 2 * (size_t)ncoef;
+// Rings whose phi transforms run as a register FFT in fold_angular_kernel:
+// N_phi = 16, 32 or 64 (log2 of the complex size N_phi / 2), else 0.
+#ifndef GH_FOLD_FFT_MAX_NPHI
+#define GH_FOLD_FFT_MAX_NPHI 64
+#endif
+int fold_fft_log(const AngularGrid& g) {
+  if (g.nph > GH_FOLD_FFT_MAX_NPHI || g.nth % 2 != 0) return 0;
+  if (g.nph == 16) return 3;
+  if (g.nph == 32) return 4;
+  if (g.nph == 64) return 5;
+  return 0;
 }
 
-int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int ncoef, int n_rows, int budget_bytes) {
-  int rb = (int)((size_t)budget_bytes / (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out, ncoef)));
+// Shared memory (doubles) per row of the folded kernel: ring values and their
+// quarter folds, or the padded rings of the FFT path (reused for the synthesis
+// coefficients), plus the Fourier coefficients of the half-rings.
+size_t fold_row_doubles(int na, int nth, int W, int M, int n_out, int ncoef, bool fft) {
+  const size_t ab = (size_t)M * 2 * (size_t)((nth + 1) / 2);
+  const size_t rings = fft ? (size_t)na + nth : (size_t)na + 4 * (size_t)nth * W;
+  return std::max(rings, (size_t)n_out * nth * M) + ab + 2 * (size_t)ncoef;
+}
+
+int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int ncoef, bool fft, int n_rows,
+                        int budget_bytes) {
+  int rb = (int)((size_t)budget_bytes / (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out, ncoef, fft)));
   if (rb < 1) rb = 1;
   if (rb > 64) rb = 64;
   if (rb > n_rows) rb = n_rows;
@@ -523,17 +538,19 @@ cudaError_t fold_build_maps(gh_domain* d) {
     gh::ShellDev& sh = d->shells_h[s];
     const int rows = gh::NF * sh.n_r;
     const int W = sh.fd.W;
-    sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef, rows, d->fd_budget);
+    const bool fft = sh.fd.fft_log != 0;
+    sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef, fft, rows, d->fd_budget);
     fb2[s] = nfd;
     nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
     smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta *
-                              fold_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef));
+                              fold_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef, fft));
     ffb[s] = nff;
     if (sh.ff.M > 0) {
-      sh.ff.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef, rows, d->ff_budget);
+      sh.ff.rows_per_cta =
+          fold_rows_per_block(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef, fft, rows, d->ff_budget);
       nff += (rows + sh.ff.rows_per_cta - 1) / sh.ff.rows_per_cta;
       smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta *
-                                fold_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef));
+                                fold_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef, fft));
     }
   }
   fb2[n_shells] = nfd;
@@ -542,27 +559,35 @@ cudaError_t fold_build_maps(gh_domain* d) {
   d->ff_blocks = nff;
   d->fd_smem = smfd;
   d->ff_smem = smff;
-  // transposed maps (reverse mode): a fixed thread count and budget
+  // transposed maps (reverse mode): a fixed thread count and budget; on the
+  // FFT path (one thread per ring) at least 128 rings per block where 200 KiB
+  // of shared memory allow it, so that four warps share the ring transforms
   std::vector<int> fa2(n_shells + 1), ffa(n_shells + 1);
   int nfa = 0, nffa = 0;
   size_t smfa = 0, smffa = 0;
-  auto adj_rows = [](size_t row_doubles, int n_rows) {
+  auto adj_rows = [](size_t row_doubles, int n_rows, int fft_rings) {
     int rb = (int)((size_t)gh::FOLD_ADJ_BUDGET / (sizeof(double) * row_doubles));
+    if (fft_rings > 0) {
+      const int cap = (int)((size_t)200 * 1024 / (sizeof(double) * row_doubles));
+      rb = std::max(rb, std::min((128 + fft_rings - 1) / fft_rings, cap));
+    }
     return std::max(1, std::min(std::min(rb, 64), n_rows));
   };
   for (int s = 0; s < n_shells; ++s) {
     gh::ShellDev& sh = d->shells_h[s];
     const int rows = gh::NF * sh.n_r;
     const int W = sh.fd.W;
-    const size_t rd = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2);
-    sh.fd.adj_rows_per_cta = adj_rows(rd, rows);
+    const bool fft = sh.fd.fft_log != 0;
+    const int fft_rings = fft ? sh.nth : 0;
+    const size_t rd = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2, fft);
+    sh.fd.adj_rows_per_cta = adj_rows(rd, rows, fft_rings);
     fa2[s] = nfa;
     nfa += (rows + sh.fd.adj_rows_per_cta - 1) / sh.fd.adj_rows_per_cta;
     smfa = std::max(smfa, sizeof(double) * (size_t)sh.fd.adj_rows_per_cta * rd);
     ffa[s] = nffa;
     if (sh.ff.M > 0) {
-      const size_t rf = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1);
-      sh.ff.adj_rows_per_cta = adj_rows(rf, rows);
+      const size_t rf = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1, fft);
+      sh.ff.adj_rows_per_cta = adj_rows(rf, rows, fft_rings);
       nffa += (rows + sh.ff.adj_rows_per_cta - 1) / sh.ff.adj_rows_per_cta;
       smffa = std::max(smffa, sizeof(double) * (size_t)sh.ff.adj_rows_per_cta * rf);
     }
@@ -769,8 +794,8 @@ cudaError_t time_calls(gh_domain* d, int reps, F f, float* ms) {
 bool schedule_ok(const int* v) {
   auto in = [](int x, int lo, int hi) { return x >= lo && x <= hi; };
   return in(v[0], 2, 4) && in(v[1], 1, 4) && in(v[2], 2, 4) && in(v[3], 1, 4) &&
-         in(v[4], 32, 512) && v[4] % 32 == 0 && in(v[5], 8 * 1024, 200 * 1024) &&
-         in(v[6], 32, 512) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024) && in(v[8], 0, 1);
+         in(v[4], 32, 256) && v[4] % 32 == 0 && in(v[5], 8 * 1024, 200 * 1024) &&
+         in(v[6], 32, 256) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024) && in(v[8], 0, 1);
 }
 
 // The host path's captured step is rebuilt after any change to the step's
@@ -997,6 +1022,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
           }
           P.m0 = f.m0;
           P.ncoef = f.coef_off[f.K + 1];
+          P.fft_log = fold_fft_log(ag);
           if ((e = upload(d, f.A, &q)) != cudaSuccess) return e; P.A = q;
           if ((e = upload(d, f.Y0, &q)) != cudaSuccess) return e; P.Y0 = q;
           if ((e = upload(d, f.Y1, &q)) != cudaSuccess) return e; P.Y1 = q;
@@ -1198,6 +1224,7 @@ gh_status gh_create_domain(const gh_shell* shells, int n_shells, const gh_params
     CREATE_CUDA(gh::sep_adj_set_smem_limits(std::max(sma, smfa)));
     // folded maps
     d->fold_ok = all_fold;
+    if (all_fold) CREATE_CUDA(gh::fold_fft_tables());
     if (all_fold) CREATE_CUDA(fold_build_maps(d));
     d->algorithm = all_fold ? 2 : 1;
   }
@@ -1746,8 +1773,9 @@ gh_status gh_autotune(gh_domain* d, int reps) {
   }
   // folded angular maps: threads per block x shared-memory budget per block
   if (d->fold_ok) {
-    const int threads[] = {128, 256, 384, 512};
-    const int budgets[] = {16 * 1024, 24 * 1024, 32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024, 112 * 1024};
+    const int threads[] = {128, 192, 256};
+    const int budgets[] = {16 * 1024,  24 * 1024,  32 * 1024,  48 * 1024, 64 * 1024,
+                           96 * 1024, 112 * 1024, 160 * 1024, 200 * 1024};
     bool any_filter = false;
     for (const auto& sh : d->shells_h) any_filter = any_filter || sh.ff.M > 0;
     for (int filter = 0; filter < (any_filter ? 2 : 1); ++filter) {

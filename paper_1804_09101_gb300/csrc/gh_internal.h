@@ -97,7 +97,9 @@ struct FoldPlan {
   int W, hs;                    // quarter-ring points, symmetric half-ring size ceil(N_theta/2)
   int qself;                    // 1 if N_phi % 4 == 0 (the point N_phi/4 is its own mirror)
   int rows_per_cta, two;        // rows per block; 2 outputs (derivatives) or 1 (filter)
-  int adj_rows_per_cta, pad1;   // rows per block of the transposed map (fold_adjoint_kernel)
+  int adj_rows_per_cta;         // rows per block of the transposed map (fold_adjoint_kernel)
+  int fft_log;                  // log2(N_phi / 2) where each ring's phi transforms run as a real FFT
+                                // in registers (N_phi = 16, 32, 64), else 0 (quarter-folded DFT)
   const double* Tc;             // [K+1][W] cos(m phi_k)
   const double* Ts;             // [K+1][W] sin(m phi_k)
   // [K+1][hs][hs] (transposed: [m][j_in][j_out]) half-size Legendre maps,
@@ -343,6 +345,9 @@ cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dt
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
 cudaError_t fold_set_smem_limits(size_t bytes);
+// Uploads the twiddle table of the folded kernel's ring FFTs (constant memory
+// of the current device; the same values on every call).
+cudaError_t fold_fft_tables();
 // Tensor-harmonic SH filter: tables, launch maps and the component buffer
 // (once; gl_x / gl_w are each shell's Gauss-Legendre nodes cos(theta) and
 // weights), then in -> out (may alias) using d->tf_buf.
@@ -388,7 +393,7 @@ cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, doubl
 #endif
 constexpr int FOLD_ADJ_THREADS = GH_FOLD_ADJ_THREADS;
 constexpr int FOLD_ADJ_BUDGET = GH_FOLD_ADJ_BUDGET;   // shared-memory budget per block (bytes)
-size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out);
+size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out, bool fft);
 cudaError_t fold_adjoint_set_smem_limits(size_t bytes);
 cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const double* in1, double* out);
 cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out);

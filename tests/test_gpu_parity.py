@@ -76,6 +76,19 @@ def w_bbh_k1():
     return w
 
 
+def w_fft_rings_32():
+    # N_phi = 32: the folded maps' register FFT of 16 complex values, with the
+    # SH filter (keep l <= 10)
+    return workloads.Workload(name="fft_rings_32", shells=[(1.5, 2.5, 3, 15), (2.5, 4.0, 5, 15)], M=1.0,
+                              chi=0.6, radial_filter_on=True, sh_keep_l=10, dt=0.002, seed=13, noise_amp=1e-6)
+
+
+def w_fft_rings_64():
+    # N_phi = 64: the register FFT of 32 complex values (keep l <= 20)
+    return workloads.Workload(name="fft_rings_64", shells=[(1.5, 2.5, 3, 31), (2.5, 4.0, 3, 31)], M=1.0,
+                              chi=0.6, radial_filter_on=True, sh_keep_l=20, dt=0.002, seed=14, noise_amp=1e-6)
+
+
 def w_paper_singlebh():
     # the paper's own test problem: tilted spin (0.2, 0.3, 0.4), two 10 x 19 x 38 shells
     return workloads.paper_single_bh()
@@ -83,7 +96,8 @@ def w_paper_singlebh():
 
 CASES = {"schwarzschild": w_schwarzschild, "kerr2": w_kerr_two_shells, "ragged": w_ragged,
          "minimal": w_minimal, "even_L": w_even_L, "singlebh_k1": w_singlebh_k1, "bbh_k1": w_bbh_k1,
-         "paper_singlebh": w_paper_singlebh}
+         "paper_singlebh": w_paper_singlebh, "fft_rings_32": w_fft_rings_32,
+         "fft_rings_64": w_fft_rings_64}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
