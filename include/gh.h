@@ -431,8 +431,10 @@ gh_status gh_dp5_step(gh_domain* dom, double dt, double rtol, double atol, doubl
  *     column (1..4, one grid row each);
  *   sched[2], sched[3]: the same for the radial ExpCheb filter;
  *   sched[4], sched[5]: folded d/dtheta, d/dphi kernel -- threads per block
- *     (32..256, a multiple of 32) and the shared-memory budget per block in
- *     bytes (8 KiB..200 KiB), which sets the rows per block of every shell;
+ *     (32..512, a multiple of 32) and the shared-memory budget per block in
+ *     bytes (8 KiB..200 KiB), which sets the rows per block of every shell
+ *     (for shells with N_phi = 16, 32, 64 these set the Legendre stage; their
+ *     ring FFTs run in fixed blocks of 128 threads);
  *   sched[6], sched[7]: the same for the folded SH filter;
  *   sched[8]: reverse pass of the pointwise algebra (gh_rhs_vjp and the step
  *     VJPs) with one thread per point (0) or ten, one per symmetric pair (1):

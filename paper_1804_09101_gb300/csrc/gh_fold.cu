@@ -26,7 +26,12 @@
 
 namespace gh {
 
-constexpr int FOLD_MAX_THREADS = 256;   // the FFT path's register arrays need up to 255 registers
+constexpr int FOLD_MAX_THREADS = 512;
+// The ring-FFT kernels run FOLD_FFT_WARPS warps of 32 rings per block, three
+// blocks per SM (the transforms hold a ring of N_phi <= 64 values in registers,
+// up to 168 registers a thread under that bound).
+// The transposed maps carry the ring FFTs inline: at most 256 threads a block.
+constexpr int FOLD_ADJ_MAX_THREADS = 256;
 
 __device__ __forceinline__ double flip_sign(double v, unsigned long long mask) {
   // v or -v without an FP64 instruction (mask is 0 or the sign bit)
@@ -166,40 +171,6 @@ __device__ __forceinline__ void ring_irfft(const double* __restrict__ cf, int K,
   fft_stages<LOG, 1, 0>(re, im);
 }
 
-// Phase A of the FFT path: one thread per ring, the ring and its mirror on
-// adjacent lanes; the symmetric and antisymmetric parts s = c(j) + c(mirror),
-// t = c(j) - c(mirror) of every coefficient are formed across the lane pair.
-// The ring stride in U is 2n + 1 doubles (conflict-free reads).
-template <int LOG>
-__device__ __forceinline__ void fold_fft_analysis(const double* __restrict__ U, double* __restrict__ AB, int nr,
-                                                  int nth, int hs, int M, int K) {
-  constexpr int n = 1 << LOG;
-  const unsigned long long sbit = 0x8000000000000000ULL;
-  const int total = nr * nth;   // even (N_theta = n), so a lane pair is all in or all out
-  const int lane = threadIdx.x & 31;
-  for (int o0 = threadIdx.x - lane; o0 < total; o0 += blockDim.x) {
-    const bool act = o0 + lane < total;
-    const int o = act ? o0 + lane : total - 1;
-    const int rr = o / nth, q = o - rr * nth, p = q >> 1, mir = q & 1;
-    const int j = mir ? nth - 1 - p : p;
-    double re[n], im[n];
-    ring_rfft<LOG>(U + (size_t)(rr * nth + j) * (2 * n + 1), re, im);
-    double* ab = AB + (size_t)rr * M * 2 * hs + (mir ? hs : 0) + p;
-    const unsigned long long neg = mir ? sbit : 0ULL;   // the mirror lane writes c(j) - c(mirror)
-#pragma unroll
-    for (int m = 0; m < n; ++m) {
-      if (m <= K) {
-        const double cv = re[m], cp = __shfl_xor_sync(0xffffffffu, cv, 1);
-        if (act) ab[(size_t)m * 2 * hs] = cp + flip_sign(cv, neg);
-        if (m > 0) {
-          const double sv = im[m], sp = __shfl_xor_sync(0xffffffffu, sv, 1);
-          if (act) ab[(size_t)(K + m) * 2 * hs] = sp + flip_sign(sv, neg);
-        }
-      }
-    }
-  }
-}
-
 // Writes (ACC: adds) one synthesised ring, x_{2t} = re[t], x_{2t+1} = im[t].
 template <int LOG, bool ACC>
 __device__ __forceinline__ void store_ring(double* __restrict__ dst, const double (&re)[1 << LOG],
@@ -223,25 +194,6 @@ __device__ __forceinline__ void store_ring(double* __restrict__ dst, const doubl
       dst[2 * t] = ACC ? dst[2 * t] + re[t] : re[t];
       dst[2 * t + 1] = ACC ? dst[2 * t + 1] + im[t] : im[t];
     }
-  }
-}
-
-// Phase C of the FFT path: one thread per (output, ring) synthesises the ring
-// from its M coefficients and writes it to global memory.
-template <int LOG, bool TWO>
-__device__ __forceinline__ void fold_fft_synthesis(const double* __restrict__ OUT, int RB, int nr, int nth, int M,
-                                                   int K, int na, long long gbase, double* __restrict__ out0,
-                                                   double* __restrict__ out1) {
-  constexpr int n = 1 << LOG;
-  constexpr int NO = TWO ? 2 : 1;
-  const int per = nr * nth;
-  for (int o = threadIdx.x; o < NO * per; o += blockDim.x) {
-    const int o2 = TWO ? o / per : 0;
-    const int rj = o - o2 * per;
-    const int rr = rj / nth, j = rj - rr * nth;
-    double re[n], im[n];
-    ring_irfft<LOG>(OUT + (size_t)o2 * RB * nth * M + (size_t)rj * M, K, re, im);
-    store_ring<LOG, false>((o2 == 0 ? out0 : out1) + gbase + (long long)rr * na + (long long)j * 2 * n, re, im);
   }
 }
 
@@ -278,101 +230,16 @@ __device__ __forceinline__ void fold_fft_ring_synth(const double* __restrict__ a
   }
 }
 
-// One block takes RB consecutive (r, field) rows of one shell.  Shared memory
-// per row: the input ring values and their quarter folds, later reused for the
-// synthesis coefficients, plus the Fourier coefficients of both half-rings.
-// The thread count is a launch parameter (a multiple of 32, at most 512).
+// Phases B1 and B of the folded maps (fold_angular_kernel, fold_legendre_kernel):
+// from the symmetric/antisymmetric Fourier coefficients AB [RB][M][2 hs] of nr
+// rows, the synthesis coefficients OUT [NO][RB][nth][M] of every output ring
+// (COEF [RB][2][ncoef] holds the analysed a_l of the factorised modes).  The
+// caller synchronises before reading OUT.
 template <bool TWO>
-__global__ void __launch_bounds__(FOLD_MAX_THREADS)
-fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
-                    const double* __restrict__ in, double* __restrict__ out0, double* __restrict__ out1) {
-  extern __shared__ double sm[];
-  const int s = find_segment(begin, n_shells, blockIdx.x);
-  const ShellDev& sh = shells[s];
-  const FoldPlan& P = TWO ? sh.fd : sh.ff;
-  const int nth = sh.nth, nph = sh.nph, na = sh.na;
-  const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = P.W, hs = P.hs, N2 = nph / 2;
-  const bool qself = P.qself != 0;
-  constexpr int NO = TWO ? 2 : 1;
-  const int T = blockDim.x;
-  const int rows = NF * sh.n_r;
-  const int RB = P.rows_per_cta;
-  const int row0 = (blockIdx.x - begin[s]) * RB;
-  const int nr = min(RB, rows - row0);
-  const int fl = P.fft_log;
-  const int r1 = fl ? max(na + nth, NO * nth * M) : max(na + 4 * nth * W, NO * nth * M);
-  double* U = sm;                                   // [RB][na] ([RB][nth][nph + 1] on the FFT path)
-  double* F = U + (size_t)RB * na;                  // [RB][nth][4][W] (quarter-folded DFT path)
-  double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
-  double* AB = sm + (size_t)RB * r1;                // [RB][M][2 hs]: s (hs) then t (hs)
-  const int ncoef = P.ncoef;
-  double* COEF = AB + (size_t)RB * M * 2 * hs;      // [RB][2][ncoef]: a_l of the cos, then the sin modes m >= m0
-  const long long gbase = sh.off + (long long)row0 * na;
-  if (fl) {
-    for (int i = threadIdx.x; i < nr * na; i += T) U[i + (i >> (fl + 1))] = in[gbase + i];   // one pad per ring
-  } else {
-    for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
-  }
-  __syncthreads();
-  if (fl == 5) fold_fft_analysis<5>(U, AB, nr, nth, hs, M, K);
-  else if (fl == 4) fold_fft_analysis<4>(U, AB, nr, nth, hs, M, K);
-  else if (fl == 3) fold_fft_analysis<3>(U, AB, nr, nth, hs, M, K);
-  else {
-  // fold every ring: Cp, Cm (cos, even / odd m), Sp, Sm (sin, odd / even m)
-  for (int o = threadIdx.x; o < nr * nth * W; o += T) {
-    const int k = o % W;
-    const int rj = o / W;
-    const double* ring = U + (size_t)rj * nph;
-    double* f = F + (size_t)rj * 4 * W;
-    auto ev = [&](int kk) { return (kk == 0 || kk == N2) ? ring[kk] : ring[kk] + ring[nph - kk]; };
-    auto od = [&](int kk) { return (kk == 0 || kk == N2) ? 0.0 : ring[kk] - ring[nph - kk]; };
-    if (!(qself && k == N4)) {
-      const double e1 = ev(k), e2 = ev(N2 - k), o1 = od(k), o2 = od(N2 - k);
-      f[k] = e1 + e2;
-      f[W + k] = e1 - e2;
-      f[2 * W + k] = o1 + o2;
-      f[3 * W + k] = o1 - o2;
-    } else {
-      f[k] = ev(N4);
-      f[W + k] = 0.0;
-      f[2 * W + k] = od(N4);
-      f[3 * W + k] = 0.0;
-    }
-  }
-  __syncthreads();
-  // phase A: Fourier coefficient of mode for rings j and N_theta-1-j, stored as
-  // their sum (symmetric part s) and difference (antisymmetric part t); the
-  // equator ring of an odd N_theta is symmetric (s = its coefficient, t = 0)
-  for (int o = threadIdx.x; o < nr * hs * M; o += T) {
-    const int mode = o % M;
-    const int t = o / M;
-    const int jh = t % hs;
-    const int rr = t / hs;
-    const bool cosm = mode <= K;
-    const int m = cosm ? mode : mode - K;
-    const int q = cosm ? (m % 2 == 0 ? 0 : 1) : (m % 2 == 1 ? 2 : 3);
-    const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
-    const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
-    double* ab = AB + ((size_t)rr * M + mode) * 2 * hs;
-    if (jh < half) {
-      const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
-      double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
-      for (int k = 1; k < W; ++k) {
-        const double tv = __ldg(tab + k);
-        c1 = fma(f1[k], tv, c1);
-        c2 = fma(f2[k], tv, c2);
-      }
-      ab[jh] = c1 + c2;
-      ab[hs + jh] = c1 - c2;
-    } else {
-      double c1 = f1[0] * __ldg(tab);
-      for (int k = 1; k < W; ++k) c1 = fma(f1[k], __ldg(tab + k), c1);
-      ab[jh] = c1;
-      ab[hs + jh] = 0.0;
-    }
-  }
-  }
-  __syncthreads();
+__device__ __forceinline__ void fold_legendre_phase(const FoldPlan& P, const double* __restrict__ AB,
+                                                    double* __restrict__ COEF, double* __restrict__ OUT, int RB,
+                                                    int nr, int nth) {
+  const int K = P.K, M = P.M, half = P.half, hs = P.hs, ncoef = P.ncoef, T = blockDim.x;
   // phase B1: for modes m >= m0, the Legendre analysis a_l = sum_j A_l(j) (s or
   // t)_j for l = m .. K (s part for l + m even, t part for l + m odd)
   if (ncoef > 0) {
@@ -446,8 +313,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
       }
     }
     const bool eq = (j >= half);            // the equator ring of an odd N_theta
-#pragma unroll
-    for (int o2 = 0; o2 < NO; ++o2) {
+    auto emit = [&](int o2, double sv, double tv) {
       // parity of the output about the equator
       const unsigned long long par = ((o2 == 0 ? P.sigma0 : P.sigma1) < 0.0) ? sbit : 0ULL;
       unsigned long long flip = 0ULL;
@@ -460,7 +326,7 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
             double* c = OUT + (size_t)RB * nth * M + (size_t)rr * nth * M;
             c[(size_t)j * M] = 0.0;
             if (!eq) c[(size_t)(nth - 1 - j) * M] = 0.0;
-            continue;
+            return;
           }
           slot = K + m;
           flip = sbit;
@@ -468,25 +334,101 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
           slot = m;
         }
       }
-      const double y1 = Sv[o2] + Tv[o2];
       double* c = OUT + (size_t)o2 * RB * nth * M + (size_t)rr * nth * M;
-      c[(size_t)j * M + slot] = flip_sign(y1, flip);
-      if (!eq) c[(size_t)(nth - 1 - j) * M + slot] = flip_sign(Sv[o2] - Tv[o2], flip ^ par);
+      c[(size_t)j * M + slot] = flip_sign(sv + tv, flip);
+      if (!eq) c[(size_t)(nth - 1 - j) * M + slot] = flip_sign(sv - tv, flip ^ par);
+    };
+    emit(0, Sv[0], Tv[0]);
+    if (TWO) emit(1, Sv[1], Tv[1]);
+  }
+}
+
+// One block takes RB consecutive (r, field) rows of one shell.  Shared memory
+// per row: the input ring values and their quarter folds, later reused for the
+// synthesis coefficients, plus the Fourier coefficients of both half-rings.
+// The thread count is a launch parameter (a multiple of 32, at most 512).
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_MAX_THREADS)
+fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                    const double* __restrict__ in, double* __restrict__ out0, double* __restrict__ out1) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  const int nth = sh.nth, nph = sh.nph, na = sh.na;
+  const int K = P.K, M = P.M, N4 = P.N4, half = P.half, W = P.W, hs = P.hs, N2 = nph / 2;
+  const bool qself = P.qself != 0;
+  constexpr int NO = TWO ? 2 : 1;
+  const int T = blockDim.x;
+  const int rows = NF * sh.n_r;
+  const int RB = P.rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  const int r1 = max(na + 4 * nth * W, NO * nth * M);
+  double* U = sm;                                   // [RB][na]
+  double* F = U + (size_t)RB * na;                  // [RB][nth][4][W]
+  double* OUT = sm;                                 // [NO][RB][nth][M] (after U, F are dead)
+  double* AB = sm + (size_t)RB * r1;                // [RB][M][2 hs]: s (hs) then t (hs)
+  double* COEF = AB + (size_t)RB * M * 2 * hs;      // [RB][2][ncoef]: a_l of the cos, then the sin modes m >= m0
+  const long long gbase = sh.off + (long long)row0 * na;
+  for (int i = threadIdx.x; i < nr * na; i += T) U[i] = in[gbase + i];
+  __syncthreads();
+  // fold every ring: Cp, Cm (cos, even / odd m), Sp, Sm (sin, odd / even m)
+  for (int o = threadIdx.x; o < nr * nth * W; o += T) {
+    const int k = o % W;
+    const int rj = o / W;
+    const double* ring = U + (size_t)rj * nph;
+    double* f = F + (size_t)rj * 4 * W;
+    auto ev = [&](int kk) { return (kk == 0 || kk == N2) ? ring[kk] : ring[kk] + ring[nph - kk]; };
+    auto od = [&](int kk) { return (kk == 0 || kk == N2) ? 0.0 : ring[kk] - ring[nph - kk]; };
+    if (!(qself && k == N4)) {
+      const double e1 = ev(k), e2 = ev(N2 - k), o1 = od(k), o2 = od(N2 - k);
+      f[k] = e1 + e2;
+      f[W + k] = e1 - e2;
+      f[2 * W + k] = o1 + o2;
+      f[3 * W + k] = o1 - o2;
+    } else {
+      f[k] = ev(N4);
+      f[W + k] = 0.0;
+      f[2 * W + k] = od(N4);
+      f[3 * W + k] = 0.0;
     }
   }
   __syncthreads();
-  if (fl == 5) {
-    fold_fft_synthesis<5, TWO>(OUT, RB, nr, nth, M, K, na, gbase, out0, out1);
-    return;
+  // phase A: Fourier coefficient of mode for rings j and N_theta-1-j, stored as
+  // their sum (symmetric part s) and difference (antisymmetric part t); the
+  // equator ring of an odd N_theta is symmetric (s = its coefficient, t = 0)
+  for (int o = threadIdx.x; o < nr * hs * M; o += T) {
+    const int mode = o % M;
+    const int t = o / M;
+    const int jh = t % hs;
+    const int rr = t / hs;
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    const int q = cosm ? (m % 2 == 0 ? 0 : 1) : (m % 2 == 1 ? 2 : 3);
+    const double* tab = (cosm ? P.Tc : P.Ts) + (size_t)m * W;
+    const double* f1 = F + ((size_t)(rr * nth + jh) * 4 + q) * W;
+    double* ab = AB + ((size_t)rr * M + mode) * 2 * hs;
+    if (jh < half) {
+      const double* f2 = F + ((size_t)(rr * nth + nth - 1 - jh) * 4 + q) * W;
+      double c1 = f1[0] * __ldg(tab), c2 = f2[0] * __ldg(tab);
+      for (int k = 1; k < W; ++k) {
+        const double tv = __ldg(tab + k);
+        c1 = fma(f1[k], tv, c1);
+        c2 = fma(f2[k], tv, c2);
+      }
+      ab[jh] = c1 + c2;
+      ab[hs + jh] = c1 - c2;
+    } else {
+      double c1 = f1[0] * __ldg(tab);
+      for (int k = 1; k < W; ++k) c1 = fma(f1[k], __ldg(tab + k), c1);
+      ab[jh] = c1;
+      ab[hs + jh] = 0.0;
+    }
   }
-  if (fl == 4) {
-    fold_fft_synthesis<4, TWO>(OUT, RB, nr, nth, M, K, na, gbase, out0, out1);
-    return;
-  }
-  if (fl == 3) {
-    fold_fft_synthesis<3, TWO>(OUT, RB, nr, nth, M, K, na, gbase, out0, out1);
-    return;
-  }
+  __syncthreads();
+  fold_legendre_phase<TWO>(P, AB, COEF, OUT, RB, nr, nth);
+  __syncthreads();
   // phase C: quarter-ring sums give four output points each; one item per
   // (output, ring, k)
   for (int o = threadIdx.x; o < NO * nr * nth * W; o += T) {
@@ -528,6 +470,160 @@ fold_angular_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
 }
 
 // ---------------------------------------------------------------------------
+// The folded maps of shells with N_phi = 16, 32, 64 run as three launches:
+// fold_fft_analysis_kernel (the phi analysis of every ring by register FFT),
+// fold_legendre_kernel (phases B1 and B above) and fold_fft_synthesis_kernel
+// (the inverse FFT of every output ring).  Split this way each part runs at
+// the occupancy it needs: the FFTs hold a ring in registers (168 a thread), the
+// Legendre maps want many warps to hide their shared and L2 loads.  Between the
+// launches the coefficients go through state-sized scratch buffers with the
+// state's own row stride na: AB [row][M][2 hs] and, per output, OUT
+// [row][N_theta][M] (both smaller than a row of values).
+
+// One warp per 32 consecutive rings of a shell (whole rows: N_theta divides
+// 32).  The rings are staged in shared memory with stride 2n + 1; ring j and its
+// mirror N_theta-1-j sit on adjacent lanes and form s = c(j) + c(mirror),
+// t = c(j) - c(mirror) by shuffle.
+template <int LOG>
+__device__ __forceinline__ void warp_ring_analysis(const double* __restrict__ st, double* __restrict__ abg,
+                                                   long long row0, int nw, int nth, int na, int hs, int K) {
+  constexpr int n = 1 << LOG;
+  const unsigned long long sbit = 0x8000000000000000ULL;
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < nw;              // nw is a multiple of N_theta: lane pairs are all in or all out
+  const int q = act ? lane : nw - 1;
+  const int rw = q / nth, qq = q - rw * nth, p = qq >> 1, mir = qq & 1;
+  const int j = mir ? nth - 1 - p : p;
+  double re[n], im[n];
+  ring_rfft<LOG>(st + (size_t)(rw * nth + j) * (2 * n + 1), re, im);
+  double* ab = abg + (row0 + rw) * na + (mir ? hs : 0) + p;
+  const unsigned long long neg = mir ? sbit : 0ULL;
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    if (m <= K) {
+      const double cv = re[m], cp = __shfl_xor_sync(0xffffffffu, cv, 1);
+      if (act) ab[(size_t)m * 2 * hs] = cp + flip_sign(cv, neg);
+      if (m > 0) {
+        const double sv = im[m], sp = __shfl_xor_sync(0xffffffffu, sv, 1);
+        if (act) ab[(size_t)(K + m) * 2 * hs] = sp + flip_sign(sv, neg);
+      }
+    }
+  }
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_FFT_WARPS * 32, 3)
+fold_fft_analysis_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                         const double* __restrict__ in, double* __restrict__ ab_g) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  const int fl = P.fft_log, nth = sh.nth, nph = sh.nph, na = sh.na;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n_rings = (long long)NF * sh.n_r * nth;
+  const long long ring0 = ((long long)(blockIdx.x - begin[s]) * FOLD_FFT_WARPS + warp) * 32;
+  if (ring0 >= n_rings) return;
+  const int nw = (int)min(32LL, n_rings - ring0);
+  double* st = sm + (size_t)warp * 32 * (nph + 1);
+  const double* src = in + sh.off + ring0 * nph;
+  for (int i = lane; i < nw * nph; i += 32) st[i + (i >> (fl + 1))] = src[i];
+  __syncwarp();
+  double* abg = ab_g + sh.off;
+  const long long row0 = ring0 / nth;
+  if (fl == 5) warp_ring_analysis<5>(st, abg, row0, nw, nth, na, P.hs, P.K);
+  else if (fl == 4) warp_ring_analysis<4>(st, abg, row0, nw, nth, na, P.hs, P.K);
+  else warp_ring_analysis<3>(st, abg, row0, nw, nth, na, P.hs, P.K);
+}
+
+// RB rows of one shell per block: AB in, phases B1 and B, OUT out.
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_MAX_THREADS)
+fold_legendre_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                     const double* __restrict__ ab_g, double* __restrict__ c0_g, double* __restrict__ c1_g) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  constexpr int NO = TWO ? 2 : 1;
+  const int nth = sh.nth, na = sh.na, M = P.M, hs = P.hs, T = blockDim.x;
+  const int rows = NF * sh.n_r;
+  const int RB = P.rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  const int abn = M * 2 * hs, outn = nth * M;
+  double* AB = sm;                                  // [RB][M][2 hs]
+  double* COEF = AB + (size_t)RB * abn;             // [RB][2][ncoef]
+  double* OUT = COEF + (size_t)RB * 2 * P.ncoef;    // [NO][RB][nth][M]
+  const long long gbase = sh.off + (long long)row0 * na;
+  for (int i = threadIdx.x; i < nr * abn; i += T) {
+    const int rr = i / abn;
+    AB[i] = ab_g[gbase + (long long)rr * na + (i - rr * abn)];
+  }
+  __syncthreads();
+  fold_legendre_phase<TWO>(P, AB, COEF, OUT, RB, nr, nth);
+  __syncthreads();
+#pragma unroll
+  for (int o2 = 0; o2 < NO; ++o2) {
+    double* cg = o2 == 0 ? c0_g : c1_g;
+    const double* src = OUT + (size_t)o2 * RB * outn;
+    for (int i = threadIdx.x; i < nr * outn; i += T) {
+      const int rr = i / outn;
+      cg[gbase + (long long)rr * na + (i - rr * outn)] = src[i];
+    }
+  }
+}
+
+// One warp per 32 consecutive rings of one output: the rings' coefficients
+// (M each) are staged in shared memory, one lane synthesises a ring.
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_FFT_WARPS * 32, 3)
+fold_fft_synthesis_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                          const double* __restrict__ c0_g, const double* __restrict__ c1_g,
+                          double* __restrict__ out0, double* __restrict__ out1) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  constexpr int NO = TWO ? 2 : 1;
+  const int fl = P.fft_log, nth = sh.nth, nph = sh.nph, na = sh.na, M = P.M, K = P.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n_rings = (long long)NF * sh.n_r * nth;
+  const long long wpo = (n_rings + 31) / 32;       // warps per output
+  const long long w = (long long)(blockIdx.x - begin[s]) * FOLD_FFT_WARPS + warp;
+  const int o2 = (int)(w / wpo);
+  if (o2 >= NO) return;
+  const long long ring0 = (w - o2 * wpo) * 32;
+  const int nw = (int)min(32LL, n_rings - ring0);
+  const long long row0 = ring0 / nth;
+  const double* cg = (o2 == 0 ? c0_g : c1_g) + sh.off + row0 * na;
+  double* st = sm + (size_t)warp * 32 * M;
+  const int rown = nth * M;
+  for (int i = lane; i < nw * M; i += 32) {
+    const int rw = i / rown;
+    st[i] = cg[(long long)rw * na + (i - rw * rown)];
+  }
+  __syncwarp();
+  if (lane >= nw) return;
+  const int rw = lane / nth, j = lane - rw * nth;
+  double* dst = (o2 == 0 ? out0 : out1) + sh.off + (row0 + rw) * na + (long long)j * nph;
+  const double* cf = st + (size_t)lane * M;
+  if (fl == 5) {
+    double re[32], im[32];
+    ring_irfft<5>(cf, K, re, im);
+    store_ring<5, false>(dst, re, im);
+  } else if (fl == 4) {
+    double re[16], im[16];
+    ring_irfft<4>(cf, K, re, im);
+    store_ring<4, false>(dst, re, im);
+  } else {
+    double re[8], im[8];
+    ring_irfft<3>(cf, K, re, im);
+    store_ring<3, false>(dst, re, im);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Exact transpose of fold_angular_kernel (reverse mode).  TWO: out +=
 // Theta^T in0 + Phi^T in1 (the cotangents of d/dtheta and d/dphi); one:
 // out = S^T in0 (the filter).  The forward map of a row is C_o B_o A (analysis
@@ -551,7 +647,7 @@ __host__ __device__ inline size_t fold_adj_row_doubles(int na, int nth, int W, i
 }
 
 template <bool TWO>
-__global__ void __launch_bounds__(FOLD_MAX_THREADS)
+__global__ void __launch_bounds__(FOLD_ADJ_MAX_THREADS)
 fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                     const double* __restrict__ in0, const double* __restrict__ in1, double* __restrict__ out) {
   extern __shared__ double sm[];
@@ -813,18 +909,51 @@ cudaError_t fold_adjoint_set_smem_limits(size_t bytes) {
   return raise_smem_limit((const void*)fold_adjoint_kernel<false>, bytes);
 }
 
-cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {
-  fold_angular_kernel<true><<<d->fd_blocks, d->fd_threads, d->fd_smem, d->stream>>>(
-      d->shells_d, d->n_shells, d->fd_block_begin_d, in, dth, dph);
-  d->launches++;
+cudaError_t fold_fft_set_smem_limits(size_t an_bytes, size_t leg_bytes, size_t sy_bytes) {
+  cudaError_t e = raise_smem_limit((const void*)fold_fft_analysis_kernel<true>, an_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_fft_analysis_kernel<false>, an_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_legendre_kernel<true>, leg_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_legendre_kernel<false>, leg_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_fft_synthesis_kernel<true>, sy_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_fft_synthesis_kernel<false>, sy_bytes);
+  return e;
+}
+
+// The FFT-path launches of one map (TWO: derivatives, else the filter).
+template <bool TWO>
+cudaError_t launch_fold_fft(gh_domain* d, const double* in, double* out0, double* out1) {
+  const gh_domain::FoldFftMap& m = d->fxm[TWO ? 0 : 1];
+  if (m.an_blocks == 0) return cudaSuccess;
+  fold_fft_analysis_kernel<TWO><<<m.an_blocks, FOLD_FFT_WARPS * 32, m.an_smem, d->stream>>>(
+      d->shells_d, d->n_shells, m.an_begin_d, in, d->fft_ab);
+  fold_legendre_kernel<TWO><<<m.leg_blocks, TWO ? d->fd_threads : d->ff_threads, m.leg_smem, d->stream>>>(
+      d->shells_d, d->n_shells, m.leg_begin_d, d->fft_ab, d->fft_c0, d->fft_c1);
+  fold_fft_synthesis_kernel<TWO><<<m.sy_blocks, FOLD_FFT_WARPS * 32, m.sy_smem, d->stream>>>(
+      d->shells_d, d->n_shells, m.sy_begin_d, d->fft_c0, d->fft_c1, out0, out1);
+  d->launches += 3;
   return cudaGetLastError();
 }
 
+cudaError_t launch_fold_deriv(gh_domain* d, const double* in, double* dth, double* dph) {
+  if (d->fd_blocks > 0) {
+    fold_angular_kernel<true><<<d->fd_blocks, d->fd_threads, d->fd_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->fd_block_begin_d, in, dth, dph);
+    d->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_fold_fft<true>(d, in, dth, dph);
+}
+
 cudaError_t launch_fold_filter(gh_domain* d, const double* in, double* out) {
-  fold_angular_kernel<false><<<d->ff_blocks, d->ff_threads, d->ff_smem, d->stream>>>(
-      d->shells_d, d->n_shells, d->ff_block_begin_d, in, out, nullptr);
-  d->launches++;
-  return cudaGetLastError();
+  if (d->ff_blocks > 0) {
+    fold_angular_kernel<false><<<d->ff_blocks, d->ff_threads, d->ff_smem, d->stream>>>(
+        d->shells_d, d->n_shells, d->ff_block_begin_d, in, out, nullptr);
+    d->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_fold_fft<false>(d, in, out, nullptr);
 }
 
 }  // namespace gh

@@ -473,18 +473,21 @@ int fold_fft_log(const AngularGrid& g) {
   return 0;
 }
 
-// Shared memory (doubles) per row of the folded kernel: ring values and their
-// quarter folds, or the padded rings of the FFT path (reused for the synthesis
-// coefficients), plus the Fourier coefficients of the half-rings.
-size_t fold_row_doubles(int na, int nth, int W, int M, int n_out, int ncoef, bool fft) {
+// Shared memory (doubles) per row of the fused folded kernel: ring values and
+// their quarter folds (reused for the synthesis coefficients) plus the Fourier
+// coefficients of the half-rings; of fold_legendre_kernel (legendre_only): the
+// half-ring coefficients, the factorised modes' a_l and the synthesis
+// coefficients.
+size_t fold_row_doubles(int na, int nth, int W, int M, int n_out, int ncoef, bool legendre_only) {
   const size_t ab = (size_t)M * 2 * (size_t)((nth + 1) / 2);
-  const size_t rings = fft ? (size_t)na + nth : (size_t)na + 4 * (size_t)nth * W;
-  return std::max(rings, (size_t)n_out * nth * M) + ab + 2 * (size_t)ncoef;
+  if (legendre_only) return ab + 2 * (size_t)ncoef + (size_t)n_out * nth * M;
+  return std::max((size_t)na + 4 * (size_t)nth * W, (size_t)n_out * nth * M) + ab + 2 * (size_t)ncoef;
 }
 
-int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int ncoef, bool fft, int n_rows,
+int fold_rows_per_block(int na, int nth, int W, int M, int n_out, int ncoef, bool legendre_only, int n_rows,
                         int budget_bytes) {
-  int rb = (int)((size_t)budget_bytes / (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out, ncoef, fft)));
+  int rb = (int)((size_t)budget_bytes /
+                 (sizeof(double) * fold_row_doubles(na, nth, W, M, n_out, ncoef, legendre_only)));
   if (rb < 1) rb = 1;
   if (rb > 64) rb = 64;
   if (rb > n_rows) rb = n_rows;
@@ -531,26 +534,51 @@ cudaError_t alloc_zero(gh_domain* d, size_t bytes, void** out) {
 // domain's current schedule (fd/ff threads and budgets); re-run by gh_autotune.
 cudaError_t fold_build_maps(gh_domain* d) {
   const int n_shells = d->n_shells;
+  // fused kernel: the shells without ring FFTs; the FFT path: the others
   std::vector<int> fb2(n_shells + 1), ffb(n_shells + 1);
-  int nfd = 0, nff = 0;
-  size_t smfd = 0, smff = 0;
+  std::vector<int> an[2], leg[2], sy[2];
+  for (int k = 0; k < 2; ++k) {
+    an[k].assign(n_shells + 1, 0);
+    leg[k].assign(n_shells + 1, 0);
+    sy[k].assign(n_shells + 1, 0);
+  }
+  int nfd = 0, nff = 0, nan[2] = {0, 0}, nleg[2] = {0, 0}, nsy[2] = {0, 0};
+  size_t smfd = 0, smff = 0, sman[2] = {0, 0}, smleg[2] = {0, 0}, smsy[2] = {0, 0};
+  bool any_fft = false;
   for (int s = 0; s < n_shells; ++s) {
     gh::ShellDev& sh = d->shells_h[s];
     const int rows = gh::NF * sh.n_r;
     const int W = sh.fd.W;
     const bool fft = sh.fd.fft_log != 0;
-    sh.fd.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef, fft, rows, d->fd_budget);
-    fb2[s] = nfd;
-    nfd += (rows + sh.fd.rows_per_cta - 1) / sh.fd.rows_per_cta;
-    smfd = std::max(smfd, sizeof(double) * (size_t)sh.fd.rows_per_cta *
-                              fold_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2, sh.fd.ncoef, fft));
-    ffb[s] = nff;
-    if (sh.ff.M > 0) {
-      sh.ff.rows_per_cta =
-          fold_rows_per_block(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef, fft, rows, d->ff_budget);
-      nff += (rows + sh.ff.rows_per_cta - 1) / sh.ff.rows_per_cta;
-      smff = std::max(smff, sizeof(double) * (size_t)sh.ff.rows_per_cta *
-                                fold_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1, sh.ff.ncoef, fft));
+    any_fft = any_fft || fft;
+    const long long rings = (long long)rows * sh.nth;
+    const int ring_warps = (int)((rings + 31) / 32);
+    for (int k = 0; k < 2; ++k) {
+      gh::FoldPlan& P = k == 0 ? sh.fd : sh.ff;
+      const int n_out = k == 0 ? 2 : 1;
+      const bool on = k == 0 || sh.ff.M > 0;
+      int& nb = k == 0 ? nfd : nff;
+      size_t& sm = k == 0 ? smfd : smff;
+      (k == 0 ? fb2 : ffb)[s] = nb;
+      an[k][s] = nan[k];
+      leg[k][s] = nleg[k];
+      sy[k][s] = nsy[k];
+      if (!on) continue;
+      P.rows_per_cta = fold_rows_per_block(sh.na, sh.nth, W, P.M, n_out, P.ncoef, fft, rows,
+                                           k == 0 ? d->fd_budget : d->ff_budget);
+      const size_t row_bytes = sizeof(double) * (size_t)P.rows_per_cta *
+                               fold_row_doubles(sh.na, sh.nth, W, P.M, n_out, P.ncoef, fft);
+      if (!fft) {
+        nb += (rows + P.rows_per_cta - 1) / P.rows_per_cta;
+        sm = std::max(sm, row_bytes);
+        continue;
+      }
+      nan[k] += (ring_warps + gh::FOLD_FFT_WARPS - 1) / gh::FOLD_FFT_WARPS;
+      nleg[k] += (rows + P.rows_per_cta - 1) / P.rows_per_cta;
+      nsy[k] += (n_out * ring_warps + gh::FOLD_FFT_WARPS - 1) / gh::FOLD_FFT_WARPS;
+      sman[k] = std::max(sman[k], sizeof(double) * gh::FOLD_FFT_WARPS * 32 * (size_t)(sh.nph + 1));
+      smleg[k] = std::max(smleg[k], row_bytes);
+      smsy[k] = std::max(smsy[k], sizeof(double) * gh::FOLD_FFT_WARPS * 32 * (size_t)P.M);
     }
   }
   fb2[n_shells] = nfd;
@@ -559,6 +587,18 @@ cudaError_t fold_build_maps(gh_domain* d) {
   d->ff_blocks = nff;
   d->fd_smem = smfd;
   d->ff_smem = smff;
+  for (int k = 0; k < 2; ++k) {
+    an[k][n_shells] = nan[k];
+    leg[k][n_shells] = nleg[k];
+    sy[k][n_shells] = nsy[k];
+    gh_domain::FoldFftMap& m = d->fxm[k];
+    m.an_blocks = nan[k];
+    m.leg_blocks = nleg[k];
+    m.sy_blocks = nsy[k];
+    m.an_smem = sman[k];
+    m.leg_smem = smleg[k];
+    m.sy_smem = smsy[k];
+  }
   // transposed maps (reverse mode): a fixed thread count and budget; on the
   // FFT path (one thread per ring) at least 128 rings per block where 200 KiB
   // of shared memory allow it, so that four warps share the ring transforms
@@ -608,6 +648,27 @@ cudaError_t fold_build_maps(gh_domain* d) {
     if ((e = cudaMemcpy(d->fd_block_begin_d, fb2.data(), sizeof(int) * fb2.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(d->ff_block_begin_d, ffb.data(), sizeof(int) * ffb.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   }
+  auto put = [&](const std::vector<int>& h, int*& dev) -> cudaError_t {
+    if (!dev) return upload(d, h, &dev);
+    return cudaMemcpy(dev, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+  };
+  for (int k = 0; k < 2; ++k) {
+    if ((e = put(an[k], d->fxm[k].an_begin_d)) != cudaSuccess) return e;
+    if ((e = put(leg[k], d->fxm[k].leg_begin_d)) != cudaSuccess) return e;
+    if ((e = put(sy[k], d->fxm[k].sy_begin_d)) != cudaSuccess) return e;
+  }
+  if (any_fft && !d->fft_ab) {
+    void* p = nullptr;
+    if ((e = alloc_zero(d, sizeof(double) * d->state, &p)) != cudaSuccess) return e;
+    d->fft_ab = (double*)p;
+    if ((e = alloc_zero(d, sizeof(double) * d->state, &p)) != cudaSuccess) return e;
+    d->fft_c0 = (double*)p;
+    if ((e = alloc_zero(d, sizeof(double) * d->state, &p)) != cudaSuccess) return e;
+    d->fft_c1 = (double*)p;
+  }
+  if ((e = gh::fold_fft_set_smem_limits(std::max(sman[0], sman[1]), std::max(smleg[0], smleg[1]),
+                                        std::max(smsy[0], smsy[1]))) != cudaSuccess)
+    return e;
   if (d->shells_d &&
       (e = cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(gh::ShellDev) * d->shells_h.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
@@ -794,8 +855,8 @@ cudaError_t time_calls(gh_domain* d, int reps, F f, float* ms) {
 bool schedule_ok(const int* v) {
   auto in = [](int x, int lo, int hi) { return x >= lo && x <= hi; };
   return in(v[0], 2, 4) && in(v[1], 1, 4) && in(v[2], 2, 4) && in(v[3], 1, 4) &&
-         in(v[4], 32, 256) && v[4] % 32 == 0 && in(v[5], 8 * 1024, 200 * 1024) &&
-         in(v[6], 32, 256) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024) && in(v[8], 0, 1);
+         in(v[4], 32, 512) && v[4] % 32 == 0 && in(v[5], 8 * 1024, 200 * 1024) &&
+         in(v[6], 32, 512) && v[6] % 32 == 0 && in(v[7], 8 * 1024, 200 * 1024) && in(v[8], 0, 1);
 }
 
 // The host path's captured step is rebuilt after any change to the step's
@@ -1773,7 +1834,7 @@ gh_status gh_autotune(gh_domain* d, int reps) {
   }
   // folded angular maps: threads per block x shared-memory budget per block
   if (d->fold_ok) {
-    const int threads[] = {128, 192, 256};
+    const int threads[] = {128, 256, 384, 512};
     const int budgets[] = {16 * 1024,  24 * 1024,  32 * 1024,  48 * 1024, 64 * 1024,
                            96 * 1024, 112 * 1024, 160 * 1024, 200 * 1024};
     bool any_filter = false;

@@ -231,6 +231,18 @@ struct gh_domain {
   int* sd_block_begin_d = nullptr; int sd_blocks = 0; size_t sd_smem = 0;
   int* fd_block_begin_d = nullptr; int fd_blocks = 0; size_t fd_smem = 0;
   int* ff_block_begin_d = nullptr; int ff_blocks = 0; size_t ff_smem = 0;
+  // folded maps of the shells with ring FFTs (fft_log != 0), [0] derivatives,
+  // [1] filter: block maps and shared memory of the analysis, Legendre and
+  // synthesis launches, and the state-sized scratch between them
+  struct FoldFftMap {
+    int* an_begin_d = nullptr;  int an_blocks = 0;  size_t an_smem = 0;
+    int* leg_begin_d = nullptr; int leg_blocks = 0; size_t leg_smem = 0;
+    int* sy_begin_d = nullptr;  int sy_blocks = 0;  size_t sy_smem = 0;
+  };
+  FoldFftMap fxm[2];
+  double* fft_ab = nullptr;
+  double* fft_c0 = nullptr;
+  double* fft_c1 = nullptr;
   // transposed folded maps (reverse mode): launch maps and shared memory
   int* fda_block_begin_d = nullptr; int fda_blocks = 0; size_t fda_smem = 0;
   int* ffa_block_begin_d = nullptr; int ffa_blocks = 0; size_t ffa_smem = 0;
@@ -345,9 +357,12 @@ cudaError_t launch_angular_deriv_into(gh_domain* d, const double* in, double* dt
 cudaError_t sep_set_smem_limits(size_t bytes);
 cudaError_t radial_set_smem_limits();
 cudaError_t fold_set_smem_limits(size_t bytes);
-// Uploads the twiddle table of the folded kernel's ring FFTs (constant memory
-// of the current device; the same values on every call).
+// Uploads the twiddle table of the folded maps' ring FFTs (constant memory of
+// the current device; the same values on every call).
 cudaError_t fold_fft_tables();
+// Warps (of 32 rings each) per block of the ring-FFT kernels.
+constexpr int FOLD_FFT_WARPS = 4;
+cudaError_t fold_fft_set_smem_limits(size_t an_bytes, size_t leg_bytes, size_t sy_bytes);
 // Tensor-harmonic SH filter: tables, launch maps and the component buffer
 // (once; gl_x / gl_w are each shell's Gauss-Legendre nodes cos(theta) and
 // weights), then in -> out (may alias) using d->tf_buf.

@@ -49,8 +49,8 @@ def test_autotune_keeps_results_bitwise():
 @pytest.mark.parametrize("sched", [
     (2, 1, 2, 1, 128, 49152, 128, 49152, 1),
     (3, 2, 4, 3, 32, 8192, 64, 8192, 0),
-    (4, 4, 3, 2, 256, 200 * 1024, 256, 112 * 1024, 1),
-    (2, 3, 2, 4, 96, 24576, 224, 65536, 0),
+    (4, 4, 3, 2, 512, 200 * 1024, 256, 112 * 1024, 1),
+    (2, 3, 2, 4, 96, 24576, 480, 65536, 0),
 ])
 def test_every_schedule_gives_identical_results(sched):
     w, dom, u = _domain()
@@ -65,7 +65,7 @@ def test_every_schedule_gives_identical_results(sched):
     (2, 5, 2, 1, 128, 49152, 128, 49152, 0),     # groups > 4
     (2, 1, 2, 1, 100, 49152, 128, 49152, 0),     # threads not a multiple of 32
     (2, 1, 2, 1, 128, 1024, 128, 49152, 0),      # budget below 8 KiB
-    (2, 1, 2, 1, 128, 49152, 288, 49152, 0),     # threads above 256
+    (2, 1, 2, 1, 128, 49152, 1024, 49152, 0),    # threads above 512
     (2, 1, 2, 1, 128, 49152, 128, 49152, 2),     # pair split not 0 or 1
 ])
 def test_invalid_schedules_are_rejected(bad):
