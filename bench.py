@@ -49,9 +49,11 @@ sys.path.insert(0, ROOT)
 TRAFFIC_PER_LAUNCH = {
     # pointwise_kernel<1,0,0>, 4-shell L=15: 122.1 MB read + 110.1 MB written
     ("kerr_a0.9_4shells_nr21_L15", "folded", "pointwise"): 232.2e6,
-    # fold_angular_kernel<1> with the ring FFTs: not captured since the kernel changed
-    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): None,
-    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): None,
+    # the three launches of the ring-FFT angular map, 8-shell L=31: analysis 268.8 + 210.3 MB,
+    # Legendre 264.7 + 469.5 MB, synthesis 529.1 + 482.6 MB (read + written)
+    ("kerr_a0.95_8shells_nr41_L31", "folded", "angular"): 2225.0e6,
+    # the same, 4-shell L=15: 17.3 + 0, 16.7 + 16.9, 33.4 + 17.9 MB (the scratch mostly L2-resident)
+    ("kerr_a0.9_4shells_nr21_L15", "folded", "angular"): 102.2e6,
     # the paper's 2-shell L=18 grid: not captured since the kernel changed
     ("paper_singlebh_chi0.2_0.3_0.4_2shells_nr10_L18", "folded", "angular"): None,
 }
@@ -337,8 +339,9 @@ class ClockSampler:
 # ------------------------------------------------------------- our arm
 KERNEL_NAMES = {"pointwise": "pointwise_kernel (DiffJac + GH RHS + RK4 combine)",
                 "radial": "radial_kernel<false> (Chebyshev d/dx)"}
-ANGULAR_NAMES = {"folded": "fold_angular_kernel<true> (d/dtheta, d/dphi: per-ring real FFT for N_phi = 16, 32, 64, "
-                           "else folded phi DFT; parity-split Legendre maps, factorised for high m; inverse FFT)",
+ANGULAR_NAMES = {"folded": "fold_fft_analysis_kernel + fold_legendre_kernel + fold_fft_synthesis_kernel (d/dtheta, "
+                           "d/dphi: per-ring real FFTs, parity-split Legendre maps factorised for high m, inverse "
+                           "ring FFTs; three launches per map)",
                  "separable": "sep_angular_kernel<true> (d/dtheta, d/dphi: phi DFT, Legendre maps, inverse DFT)",
                  "dense": "gemm_batched_kernel (dense angular maps)"}
 PEAK_SOURCE = ("derived FP64 peak: 152 SMs x 4 SMSPs x one 32-lane DFMA every 64 cycles = 4 flop/clk/SM, at "

@@ -30,8 +30,6 @@ constexpr int FOLD_MAX_THREADS = 512;
 // The ring-FFT kernels run FOLD_FFT_WARPS warps of 32 rings per block, three
 // blocks per SM (the transforms hold a ring of N_phi <= 64 values in registers,
 // up to 168 registers a thread under that bound).
-// The transposed maps carry the ring FFTs inline: at most 256 threads a block.
-constexpr int FOLD_ADJ_MAX_THREADS = 256;
 
 __device__ __forceinline__ double flip_sign(double v, unsigned long long mask) {
   // v or -v without an FP64 instruction (mask is 0 or the sign bit)
@@ -194,39 +192,6 @@ __device__ __forceinline__ void store_ring(double* __restrict__ dst, const doubl
       dst[2 * t] = ACC ? dst[2 * t] + re[t] : re[t];
       dst[2 * t + 1] = ACC ? dst[2 * t + 1] + im[t] : im[t];
     }
-  }
-}
-
-// The transposed maps' FFT phases (fold_adjoint_kernel): the analysis of every
-// ring of Y (stride 2n + 1) into per-ring coefficients cb[ring][M], and the
-// synthesis of every ring from ab[ring][M] into out (ACC: added).
-template <int LOG>
-__device__ __forceinline__ void fold_fft_ring_coefs(const double* __restrict__ Y, double* __restrict__ cb,
-                                                    int n_rings, int M, int K) {
-  constexpr int n = 1 << LOG;
-  for (int o = threadIdx.x; o < n_rings; o += blockDim.x) {
-    double re[n], im[n];
-    ring_rfft<LOG>(Y + (size_t)o * (2 * n + 1), re, im);
-    double* c = cb + (size_t)o * M;
-#pragma unroll
-    for (int m = 0; m < n; ++m) {
-      if (m <= K) {
-        c[m] = re[m];
-        if (m > 0) c[K + m] = im[m];
-      }
-    }
-  }
-}
-
-template <int LOG, bool ACC>
-__device__ __forceinline__ void fold_fft_ring_synth(const double* __restrict__ ab, int nr, int nth, int M, int K,
-                                                    int na, long long gbase, double* __restrict__ out) {
-  constexpr int n = 1 << LOG;
-  for (int o = threadIdx.x; o < nr * nth; o += blockDim.x) {
-    const int rr = o / nth, j = o - rr * nth;
-    double re[n], im[n];
-    ring_irfft<LOG>(ab + (size_t)o * M, K, re, im);
-    store_ring<LOG, ACC>(out + gbase + (long long)rr * na + (long long)j * 2 * n, re, im);
   }
 }
 
@@ -639,15 +604,55 @@ fold_fft_synthesis_kernel(const ShellDev* __restrict__ shells, int n_shells, con
 // Shared memory per row: region 1 (the cotangent ring and its folds, later the
 // parity-combined coefficients) and CB (the analysed coefficients of both
 // outputs, later the per-ring coefficient cotangents).
-__host__ __device__ inline size_t fold_adj_row_doubles(int na, int nth, int W, int M, int n_out, bool fft) {
+__host__ __device__ inline size_t fold_adj_row_doubles(int na, int nth, int W, int M, int n_out) {
   const size_t hs2 = 2 * (size_t)((nth + 1) / 2);
-  size_t r1 = fft ? (size_t)na + nth : (size_t)na + 4 * (size_t)nth * W;
+  size_t r1 = (size_t)na + 4 * (size_t)nth * W;
   if ((size_t)n_out * M * hs2 > r1) r1 = (size_t)n_out * M * hs2;
   return r1 + (size_t)n_out * nth * M;
 }
 
+// Phase 2b of the transposed maps (fold_adjoint_kernel, fold_adj_legendre_kernel):
+// B_o^T summed over the outputs, then the transposed split into the rings j and
+// N_theta-1-j.  SV [NO][RB][M][2 hs] in (the parity-combined cotangents of the
+// forward's symmetric and antisymmetric map outputs), AB [RB][N_theta][M] out
+// (the cotangents of every ring's Fourier coefficients).  One item per
+// (row, mode, jp); the caller synchronises before reading AB.
 template <bool TWO>
-__global__ void __launch_bounds__(FOLD_ADJ_MAX_THREADS)
+__device__ __forceinline__ void fold_adj_legendre_phase(const FoldPlan& P, const double* __restrict__ SV,
+                                                        double* __restrict__ AB, int RB, int nr, int nth) {
+  constexpr int NO = TWO ? 2 : 1;
+  const int K = P.K, M = P.M, half = P.half, hs = P.hs, T = blockDim.x;
+  for (int o = threadIdx.x; o < nr * M * hs; o += T) {
+    const int jp = o % hs;
+    const int t = o / hs;
+    const int mode = t % M;
+    const int rr = t / M;
+    const bool cosm = mode <= K;
+    const int m = cosm ? mode : mode - K;
+    const size_t mo = (size_t)m * hs * hs + (size_t)jp * hs;
+    double sb = 0.0, tb = 0.0;
+#pragma unroll
+    for (int o2 = 0; o2 < NO; ++o2) {
+      const double* Qs = (o2 == 0 ? P.Q0s : P.Q1s) + mo;
+      const double* Qt = (o2 == 0 ? P.Q0t : P.Q1t) + mo;
+      const double* sv = SV + (((size_t)o2 * RB + rr) * M + mode) * 2 * hs;
+      for (int j = 0; j < hs; ++j) {
+        sb = fma(__ldg(Qs + j), sv[j], sb);
+        tb = fma(__ldg(Qt + j), sv[hs + j], tb);
+      }
+    }
+    double* ab = AB + (size_t)rr * nth * M + mode;
+    if (jp < half) {
+      ab[(size_t)jp * M] = sb + tb;
+      ab[(size_t)(nth - 1 - jp) * M] = sb - tb;
+    } else {
+      ab[(size_t)jp * M] = sb;           // the equator's t entry was a constant zero
+    }
+  }
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_MAX_THREADS)
 fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
                     const double* __restrict__ in0, const double* __restrict__ in1, double* __restrict__ out) {
   extern __shared__ double sm[];
@@ -663,10 +668,9 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   const int RB = P.adj_rows_per_cta;
   const int row0 = (blockIdx.x - begin[s]) * RB;
   const int nr = min(RB, rows - row0);
-  const int fl = P.fft_log;
-  size_t r1 = fl ? (size_t)na + nth : (size_t)na + 4 * (size_t)nth * W;
+  size_t r1 = (size_t)na + 4 * (size_t)nth * W;
   if ((size_t)NO * M * 2 * hs > r1) r1 = (size_t)NO * M * 2 * hs;
-  double* Y = sm;                                   // [RB][na] one output's cotangent rings (padded: FFT path)
+  double* Y = sm;                                   // [RB][na] one output's cotangent rings
   double* F = Y + (size_t)RB * na;                  // [RB][nth][4][W] their folds
   double* SV = sm;                                  // [NO][RB][M][2 hs] parity-combined (after Y, F)
   double* CB = sm + (size_t)RB * r1;                // [NO][RB][nth][M] analysed coefficients
@@ -678,19 +682,8 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   for (int o2 = 0; o2 < NO; ++o2) {
     const double* in = o2 == 0 ? in0 : in1;
     if (o2 > 0) __syncthreads();                    // Y and F are reused
-    if (fl) {
-      for (int i = threadIdx.x; i < nr * na; i += T) Y[i + (i >> (fl + 1))] = in[gbase + i];
-    } else {
-      for (int i = threadIdx.x; i < nr * na; i += T) Y[i] = in[gbase + i];
-    }
+    for (int i = threadIdx.x; i < nr * na; i += T) Y[i] = in[gbase + i];
     __syncthreads();
-    if (fl) {
-      double* cb = CB + (size_t)o2 * RB * nth * M;
-      if (fl == 5) fold_fft_ring_coefs<5>(Y, cb, nr * nth, M, K);
-      else if (fl == 4) fold_fft_ring_coefs<4>(Y, cb, nr * nth, M, K);
-      else fold_fft_ring_coefs<3>(Y, cb, nr * nth, M, K);
-      continue;
-    }
     for (int o = threadIdx.x; o < nr * nth * W; o += T) {
       const int k = o % W;
       const int rj = o / W;
@@ -785,48 +778,8 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
     }
   }
   __syncthreads();
-  // phase 2b (B_o^T, summed over outputs, then the transposed split into the
-  // rings j and N_theta-1-j): one item per (row, mode, jp)
-  for (int o = threadIdx.x; o < nr * M * hs; o += T) {
-    const int jp = o % hs;
-    const int t = o / hs;
-    const int mode = t % M;
-    const int rr = t / M;
-    const bool cosm = mode <= K;
-    const int m = cosm ? mode : mode - K;
-    const size_t mo = (size_t)m * hs * hs + (size_t)jp * hs;
-    double sb = 0.0, tb = 0.0;
-#pragma unroll
-    for (int o2 = 0; o2 < NO; ++o2) {
-      const double* Qs = (o2 == 0 ? P.Q0s : P.Q1s) + mo;
-      const double* Qt = (o2 == 0 ? P.Q0t : P.Q1t) + mo;
-      const double* sv = SV + (((size_t)o2 * RB + rr) * M + mode) * 2 * hs;
-      for (int j = 0; j < hs; ++j) {
-        sb = fma(__ldg(Qs + j), sv[j], sb);
-        tb = fma(__ldg(Qt + j), sv[hs + j], tb);
-      }
-    }
-    double* ab = AB + (size_t)rr * nth * M + mode;
-    if (jp < half) {
-      ab[(size_t)jp * M] = sb + tb;
-      ab[(size_t)(nth - 1 - jp) * M] = sb - tb;
-    } else {
-      ab[(size_t)jp * M] = sb;           // the equator's t entry was a constant zero
-    }
-  }
+  fold_adj_legendre_phase<TWO>(P, SV, AB, RB, nr, nth);
   __syncthreads();
-  if (fl == 5) {
-    fold_fft_ring_synth<5, TWO>(AB, nr, nth, M, K, na, gbase, out);
-    return;
-  }
-  if (fl == 4) {
-    fold_fft_ring_synth<4, TWO>(AB, nr, nth, M, K, na, gbase, out);
-    return;
-  }
-  if (fl == 3) {
-    fold_fft_ring_synth<3, TWO>(AB, nr, nth, M, K, na, gbase, out);
-    return;
-  }
   // phase 3 (A^T): the forward's synthesis of four ring points per
   // quarter-ring sum, from the coefficient cotangents
   for (int o = threadIdx.x; o < nr * nth * W; o += T) {
@@ -866,19 +819,206 @@ fold_adjoint_kernel(const ShellDev* __restrict__ shells, int n_shells, const int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Transposed maps of the shells with ring FFTs, as three launches like the
+// forward: fold_fft_adj_analysis_kernel (C_o^T: the analysis of every
+// cotangent ring and the parity combination of phase 2a), fold_adj_legendre_kernel
+// (phase 2b) and fold_fft_adj_synthesis_kernel (A^T: the synthesis of every
+// ring from its coefficient cotangents, added to the output for the
+// derivative maps).  Scratch as in the forward (row stride na): SV of output o
+// [row][M][2 hs], AB [row][N_theta][M].
+
+// The cotangent rings of output o2 analysed as in warp_ring_analysis; the
+// parity-combined cotangents are SV[mode][j] = f (c_j[slot] + p c_mirror[slot])
+// and SV[mode][hs + j] = f (c_j[slot] - p c_mirror[slot]), p the output's
+// parity about the equator, slot and f the d/dphi slot map and sign (cos mode m
+// from sin slot m with -1, sin mode m from cos slot m; cos mode 0 of d/dphi is
+// a constant zero in the forward, so its cotangent entries are zero).
+template <int LOG>
+__device__ __forceinline__ void warp_ring_adj_analysis(const double* __restrict__ st, double* __restrict__ svg,
+                                                       long long row0, int nw, int nth, int na, int hs, int K,
+                                                       bool dphi, bool odd_parity) {
+  constexpr int n = 1 << LOG;
+  const unsigned long long sbit = 0x8000000000000000ULL;
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < nw;
+  const int q = act ? lane : nw - 1;
+  const int rw = q / nth, qq = q - rw * nth, p = qq >> 1, mir = qq & 1;
+  const int j = mir ? nth - 1 - p : p;
+  double re[n], im[n];
+  ring_rfft<LOG>(st + (size_t)(rw * nth + j) * (2 * n + 1), re, im);
+  double* sv = svg + (row0 + rw) * na + (mir ? hs : 0) + p;
+  const unsigned long long par = odd_parity ? sbit : 0ULL, sgn = mir ? sbit : 0ULL;
+  // lane j: f own + f p other; its mirror lane: f other - f p own
+  auto put = [&](int mode, double own, unsigned long long f) {
+    const double other = __shfl_xor_sync(0xffffffffu, own, 1);
+    const double a = mir ? other : own, b = mir ? own : other;
+    if (act) sv[(size_t)mode * 2 * hs] = flip_sign(a, f) + flip_sign(b, f ^ par ^ sgn);
+  };
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    if (m <= K) {
+      if (!dphi) {
+        put(m, re[m], 0ULL);
+        if (m > 0) put(K + m, im[m], 0ULL);
+      } else if (m == 0) {
+        if (act) sv[0] = 0.0;
+      } else {
+        put(m, im[m], sbit);
+        put(K + m, re[m], 0ULL);
+      }
+    }
+  }
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_FFT_WARPS * 32, 3)
+fold_fft_adj_analysis_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                             const double* __restrict__ in0, const double* __restrict__ in1,
+                             double* __restrict__ sv0_g, double* __restrict__ sv1_g) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  constexpr int NO = TWO ? 2 : 1;
+  const int fl = P.fft_log, nth = sh.nth, nph = sh.nph, na = sh.na;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n_rings = (long long)NF * sh.n_r * nth;
+  const long long wpo = (n_rings + 31) / 32;
+  const long long w = (long long)(blockIdx.x - begin[s]) * FOLD_FFT_WARPS + warp;
+  const int o2 = (int)(w / wpo);
+  if (o2 >= NO) return;
+  const long long ring0 = (w - o2 * wpo) * 32;
+  const int nw = (int)min(32LL, n_rings - ring0);
+  double* st = sm + (size_t)warp * 32 * (nph + 1);
+  const double* src = (o2 == 0 ? in0 : in1) + sh.off + ring0 * nph;
+  for (int i = lane; i < nw * nph; i += 32) st[i + (i >> (fl + 1))] = src[i];
+  __syncwarp();
+  double* svg = (o2 == 0 ? sv0_g : sv1_g) + sh.off;
+  const long long row0 = ring0 / nth;
+  const bool dphi = TWO && o2 == 1;
+  const bool odd = (o2 == 0 ? P.sigma0 : P.sigma1) < 0.0;
+  if (fl == 5) warp_ring_adj_analysis<5>(st, svg, row0, nw, nth, na, P.hs, P.K, dphi, odd);
+  else if (fl == 4) warp_ring_adj_analysis<4>(st, svg, row0, nw, nth, na, P.hs, P.K, dphi, odd);
+  else warp_ring_adj_analysis<3>(st, svg, row0, nw, nth, na, P.hs, P.K, dphi, odd);
+}
+
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_ADJ_THREADS)
+fold_adj_legendre_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                         const double* __restrict__ sv0_g, const double* __restrict__ sv1_g,
+                         double* __restrict__ ab_g) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  constexpr int NO = TWO ? 2 : 1;
+  const int nth = sh.nth, na = sh.na, M = P.M, hs = P.hs, T = blockDim.x;
+  const int rows = NF * sh.n_r;
+  const int RB = P.adj_rows_per_cta;
+  const int row0 = (blockIdx.x - begin[s]) * RB;
+  const int nr = min(RB, rows - row0);
+  const int svn = M * 2 * hs, abn = nth * M;
+  double* SV = sm;                                  // [NO][RB][M][2 hs]
+  double* AB = SV + (size_t)NO * RB * svn;          // [RB][N_theta][M]
+  const long long gbase = sh.off + (long long)row0 * na;
+#pragma unroll
+  for (int o2 = 0; o2 < NO; ++o2) {
+    const double* src = o2 == 0 ? sv0_g : sv1_g;
+    double* dst = SV + (size_t)o2 * RB * svn;
+    for (int i = threadIdx.x; i < nr * svn; i += T) {
+      const int rr = i / svn;
+      dst[i] = src[gbase + (long long)rr * na + (i - rr * svn)];
+    }
+  }
+  __syncthreads();
+  fold_adj_legendre_phase<TWO>(P, SV, AB, RB, nr, nth);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr * abn; i += T) {
+    const int rr = i / abn;
+    ab_g[gbase + (long long)rr * na + (i - rr * abn)] = AB[i];
+  }
+}
+
+// One warp per 32 consecutive rings: A^T of each ring (its synthesis from the
+// coefficient cotangents), added to out for the derivative maps, written for
+// the filter.
+template <bool TWO>
+__global__ void __launch_bounds__(FOLD_FFT_WARPS * 32, 3)
+fold_fft_adj_synthesis_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
+                              const double* __restrict__ ab_g, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  const int s = find_segment(begin, n_shells, blockIdx.x);
+  const ShellDev& sh = shells[s];
+  const FoldPlan& P = TWO ? sh.fd : sh.ff;
+  const int fl = P.fft_log, nth = sh.nth, nph = sh.nph, na = sh.na, M = P.M, K = P.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long n_rings = (long long)NF * sh.n_r * nth;
+  const long long ring0 = ((long long)(blockIdx.x - begin[s]) * FOLD_FFT_WARPS + warp) * 32;
+  if (ring0 >= n_rings) return;
+  const int nw = (int)min(32LL, n_rings - ring0);
+  const long long row0 = ring0 / nth;
+  const double* ag = ab_g + sh.off + row0 * na;
+  double* st = sm + (size_t)warp * 32 * M;
+  const int rown = nth * M;
+  for (int i = lane; i < nw * M; i += 32) {
+    const int rw = i / rown;
+    st[i] = ag[(long long)rw * na + (i - rw * rown)];
+  }
+  __syncwarp();
+  if (lane >= nw) return;
+  const int rw = lane / nth, j = lane - rw * nth;
+  double* dst = out + sh.off + (row0 + rw) * na + (long long)j * nph;
+  const double* cf = st + (size_t)lane * M;
+  if (fl == 5) {
+    double re[32], im[32];
+    ring_irfft<5>(cf, K, re, im);
+    store_ring<5, TWO>(dst, re, im);
+  } else if (fl == 4) {
+    double re[16], im[16];
+    ring_irfft<4>(cf, K, re, im);
+    store_ring<4, TWO>(dst, re, im);
+  } else {
+    double re[8], im[8];
+    ring_irfft<3>(cf, K, re, im);
+    store_ring<3, TWO>(dst, re, im);
+  }
+}
+
 size_t fold_adjoint_row_doubles(int na, int nth, int W, int M, int n_out, bool fft) {
-  return fold_adj_row_doubles(na, nth, W, M, n_out, fft);
+  // FFT path: fold_adj_legendre_kernel's SV [NO][M][2 hs] and AB [N_theta][M]
+  if (fft) return (size_t)n_out * M * 2 * (size_t)((nth + 1) / 2) + (size_t)nth * M;
+  return fold_adj_row_doubles(na, nth, W, M, n_out);
+}
+
+template <bool TWO>
+cudaError_t launch_fold_adjoint_fft(gh_domain* d, const double* in0, const double* in1, double* out) {
+  const gh_domain::FoldFftMap& m = d->fxa[TWO ? 0 : 1];
+  if (m.an_blocks == 0) return cudaSuccess;
+  fold_fft_adj_analysis_kernel<TWO><<<m.an_blocks, FOLD_FFT_WARPS * 32, m.an_smem, d->stream>>>(
+      d->shells_d, d->n_shells, m.an_begin_d, in0, in1, d->fft_c0, d->fft_c1);
+  fold_adj_legendre_kernel<TWO><<<m.leg_blocks, FOLD_ADJ_THREADS, m.leg_smem, d->stream>>>(
+      d->shells_d, d->n_shells, m.leg_begin_d, d->fft_c0, d->fft_c1, d->fft_ab);
+  fold_fft_adj_synthesis_kernel<TWO><<<m.sy_blocks, FOLD_FFT_WARPS * 32, m.sy_smem, d->stream>>>(
+      d->shells_d, d->n_shells, m.sy_begin_d, d->fft_ab, out);
+  d->launches += 3;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fold_adjoint(gh_domain* d, bool two, const double* in0, const double* in1, double* out) {
-  if (two)
-    fold_adjoint_kernel<true><<<d->fda_blocks, FOLD_ADJ_THREADS, d->fda_smem, d->stream>>>(
-        d->shells_d, d->n_shells, d->fda_block_begin_d, in0, in1, out);
-  else
-    fold_adjoint_kernel<false><<<d->ffa_blocks, FOLD_ADJ_THREADS, d->ffa_smem, d->stream>>>(
-        d->shells_d, d->n_shells, d->ffa_block_begin_d, in0, nullptr, out);
-  d->launches++;
-  return cudaGetLastError();
+  const int blocks = two ? d->fda_blocks : d->ffa_blocks;
+  if (blocks > 0) {
+    if (two)
+      fold_adjoint_kernel<true><<<d->fda_blocks, FOLD_ADJ_THREADS, d->fda_smem, d->stream>>>(
+          d->shells_d, d->n_shells, d->fda_block_begin_d, in0, in1, out);
+    else
+      fold_adjoint_kernel<false><<<d->ffa_blocks, FOLD_ADJ_THREADS, d->ffa_smem, d->stream>>>(
+          d->shells_d, d->n_shells, d->ffa_block_begin_d, in0, nullptr, out);
+    d->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return two ? launch_fold_adjoint_fft<true>(d, in0, in1, out) : launch_fold_adjoint_fft<false>(d, in0, nullptr, out);
 }
 
 cudaError_t fold_fft_tables() {
@@ -907,6 +1047,16 @@ cudaError_t fold_adjoint_set_smem_limits(size_t bytes) {
   cudaError_t e = raise_smem_limit((const void*)fold_adjoint_kernel<true>, bytes);
   if (e != cudaSuccess) return e;
   return raise_smem_limit((const void*)fold_adjoint_kernel<false>, bytes);
+}
+
+cudaError_t fold_fft_adj_set_smem_limits(size_t an_bytes, size_t leg_bytes, size_t sy_bytes) {
+  cudaError_t e = raise_smem_limit((const void*)fold_fft_adj_analysis_kernel<true>, an_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_fft_adj_analysis_kernel<false>, an_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_adj_legendre_kernel<true>, leg_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_adj_legendre_kernel<false>, leg_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_fft_adj_synthesis_kernel<true>, sy_bytes);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)fold_fft_adj_synthesis_kernel<false>, sy_bytes);
+  return e;
 }
 
 cudaError_t fold_fft_set_smem_limits(size_t an_bytes, size_t leg_bytes, size_t sy_bytes) {

@@ -599,18 +599,19 @@ cudaError_t fold_build_maps(gh_domain* d) {
     m.leg_smem = smleg[k];
     m.sy_smem = smsy[k];
   }
-  // transposed maps (reverse mode): a fixed thread count and budget; on the
-  // FFT path (one thread per ring) at least 128 rings per block where 200 KiB
-  // of shared memory allow it, so that four warps share the ring transforms
+  // transposed maps (reverse mode): a fixed thread count and budget; the
+  // shells with ring FFTs take the three-launch form as in the forward
   std::vector<int> fa2(n_shells + 1), ffa(n_shells + 1);
-  int nfa = 0, nffa = 0;
-  size_t smfa = 0, smffa = 0;
-  auto adj_rows = [](size_t row_doubles, int n_rows, int fft_rings) {
+  std::vector<int> aan[2], aleg[2], asy[2];
+  for (int k = 0; k < 2; ++k) {
+    aan[k].assign(n_shells + 1, 0);
+    aleg[k].assign(n_shells + 1, 0);
+    asy[k].assign(n_shells + 1, 0);
+  }
+  int nfa = 0, nffa = 0, naan[2] = {0, 0}, naleg[2] = {0, 0}, nasy[2] = {0, 0};
+  size_t smfa = 0, smffa = 0, smaan[2] = {0, 0}, smaleg[2] = {0, 0}, smasy[2] = {0, 0};
+  auto adj_rows = [](size_t row_doubles, int n_rows) {
     int rb = (int)((size_t)gh::FOLD_ADJ_BUDGET / (sizeof(double) * row_doubles));
-    if (fft_rings > 0) {
-      const int cap = (int)((size_t)200 * 1024 / (sizeof(double) * row_doubles));
-      rb = std::max(rb, std::min((128 + fft_rings - 1) / fft_rings, cap));
-    }
     return std::max(1, std::min(std::min(rb, 64), n_rows));
   };
   for (int s = 0; s < n_shells; ++s) {
@@ -618,19 +619,44 @@ cudaError_t fold_build_maps(gh_domain* d) {
     const int rows = gh::NF * sh.n_r;
     const int W = sh.fd.W;
     const bool fft = sh.fd.fft_log != 0;
-    const int fft_rings = fft ? sh.nth : 0;
-    const size_t rd = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.fd.M, 2, fft);
-    sh.fd.adj_rows_per_cta = adj_rows(rd, rows, fft_rings);
-    fa2[s] = nfa;
-    nfa += (rows + sh.fd.adj_rows_per_cta - 1) / sh.fd.adj_rows_per_cta;
-    smfa = std::max(smfa, sizeof(double) * (size_t)sh.fd.adj_rows_per_cta * rd);
-    ffa[s] = nffa;
-    if (sh.ff.M > 0) {
-      const size_t rf = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, sh.ff.M, 1, fft);
-      sh.ff.adj_rows_per_cta = adj_rows(rf, rows, fft_rings);
-      nffa += (rows + sh.ff.adj_rows_per_cta - 1) / sh.ff.adj_rows_per_cta;
-      smffa = std::max(smffa, sizeof(double) * (size_t)sh.ff.adj_rows_per_cta * rf);
+    const int ring_warps = (int)(((long long)rows * sh.nth + 31) / 32);
+    for (int k = 0; k < 2; ++k) {
+      gh::FoldPlan& P = k == 0 ? sh.fd : sh.ff;
+      const int n_out = k == 0 ? 2 : 1;
+      int& nb = k == 0 ? nfa : nffa;
+      size_t& sm = k == 0 ? smfa : smffa;
+      (k == 0 ? fa2 : ffa)[s] = nb;
+      aan[k][s] = naan[k];
+      aleg[k][s] = naleg[k];
+      asy[k][s] = nasy[k];
+      if (k == 1 && sh.ff.M <= 0) continue;
+      const size_t rd = gh::fold_adjoint_row_doubles(sh.na, sh.nth, W, P.M, n_out, fft);
+      P.adj_rows_per_cta = adj_rows(rd, rows);
+      const size_t bytes = sizeof(double) * (size_t)P.adj_rows_per_cta * rd;
+      if (!fft) {
+        nb += (rows + P.adj_rows_per_cta - 1) / P.adj_rows_per_cta;
+        sm = std::max(sm, bytes);
+        continue;
+      }
+      naan[k] += (n_out * ring_warps + gh::FOLD_FFT_WARPS - 1) / gh::FOLD_FFT_WARPS;
+      naleg[k] += (rows + P.adj_rows_per_cta - 1) / P.adj_rows_per_cta;
+      nasy[k] += (ring_warps + gh::FOLD_FFT_WARPS - 1) / gh::FOLD_FFT_WARPS;
+      smaan[k] = std::max(smaan[k], sizeof(double) * gh::FOLD_FFT_WARPS * 32 * (size_t)(sh.nph + 1));
+      smaleg[k] = std::max(smaleg[k], bytes);
+      smasy[k] = std::max(smasy[k], sizeof(double) * gh::FOLD_FFT_WARPS * 32 * (size_t)P.M);
     }
+  }
+  for (int k = 0; k < 2; ++k) {
+    aan[k][n_shells] = naan[k];
+    aleg[k][n_shells] = naleg[k];
+    asy[k][n_shells] = nasy[k];
+    gh_domain::FoldFftMap& m = d->fxa[k];
+    m.an_blocks = naan[k];
+    m.leg_blocks = naleg[k];
+    m.sy_blocks = nasy[k];
+    m.an_smem = smaan[k];
+    m.leg_smem = smaleg[k];
+    m.sy_smem = smasy[k];
   }
   fa2[n_shells] = nfa;
   ffa[n_shells] = nffa;
@@ -656,6 +682,9 @@ cudaError_t fold_build_maps(gh_domain* d) {
     if ((e = put(an[k], d->fxm[k].an_begin_d)) != cudaSuccess) return e;
     if ((e = put(leg[k], d->fxm[k].leg_begin_d)) != cudaSuccess) return e;
     if ((e = put(sy[k], d->fxm[k].sy_begin_d)) != cudaSuccess) return e;
+    if ((e = put(aan[k], d->fxa[k].an_begin_d)) != cudaSuccess) return e;
+    if ((e = put(aleg[k], d->fxa[k].leg_begin_d)) != cudaSuccess) return e;
+    if ((e = put(asy[k], d->fxa[k].sy_begin_d)) != cudaSuccess) return e;
   }
   if (any_fft && !d->fft_ab) {
     void* p = nullptr;
@@ -668,6 +697,9 @@ cudaError_t fold_build_maps(gh_domain* d) {
   }
   if ((e = gh::fold_fft_set_smem_limits(std::max(sman[0], sman[1]), std::max(smleg[0], smleg[1]),
                                         std::max(smsy[0], smsy[1]))) != cudaSuccess)
+    return e;
+  if ((e = gh::fold_fft_adj_set_smem_limits(std::max(smaan[0], smaan[1]), std::max(smaleg[0], smaleg[1]),
+                                            std::max(smasy[0], smasy[1]))) != cudaSuccess)
     return e;
   if (d->shells_d &&
       (e = cudaMemcpy(d->shells_d, d->shells_h.data(), sizeof(gh::ShellDev) * d->shells_h.size(), cudaMemcpyHostToDevice)) != cudaSuccess)

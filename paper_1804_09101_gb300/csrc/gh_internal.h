@@ -240,6 +240,7 @@ struct gh_domain {
     int* sy_begin_d = nullptr;  int sy_blocks = 0;  size_t sy_smem = 0;
   };
   FoldFftMap fxm[2];
+  FoldFftMap fxa[2];            // the same for the transposed maps (reverse mode)
   double* fft_ab = nullptr;
   double* fft_c0 = nullptr;
   double* fft_c1 = nullptr;
@@ -363,6 +364,7 @@ cudaError_t fold_fft_tables();
 // Warps (of 32 rings each) per block of the ring-FFT kernels.
 constexpr int FOLD_FFT_WARPS = 4;
 cudaError_t fold_fft_set_smem_limits(size_t an_bytes, size_t leg_bytes, size_t sy_bytes);
+cudaError_t fold_fft_adj_set_smem_limits(size_t an_bytes, size_t leg_bytes, size_t sy_bytes);
 // Tensor-harmonic SH filter: tables, launch maps and the component buffer
 // (once; gl_x / gl_w are each shell's Gauss-Legendre nodes cos(theta) and
 // weights), then in -> out (may alias) using d->tf_buf.

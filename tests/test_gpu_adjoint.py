@@ -251,12 +251,20 @@ def _fold_case(name):
         # even L: odd N_theta (an equator ring) and N_phi % 4 == 2 (no quarter point)
         return workloads.Workload(name="even_L", shells=[(1.6, 3.0, 7, 6), (3.0, 5.0, 7, 6)], M=1.0, chi=0.4,
                                   radial_filter_on=True, sh_keep_l=4, dt=0.005, seed=21, noise_amp=1e-7)
+    if name == "fft_rings_32":
+        # N_phi = 32: the transposed maps' ring FFTs of 16 complex values
+        return workloads.Workload(name="fft_rings_32", shells=[(1.5, 2.5, 3, 15), (2.5, 4.0, 5, 15)], M=1.0,
+                                  chi=0.6, radial_filter_on=True, sh_keep_l=10, dt=0.002, seed=13, noise_amp=1e-6)
+    if name == "fft_rings_64":
+        # N_phi = 64: ring FFTs of 32 complex values
+        return workloads.Workload(name="fft_rings_64", shells=[(1.5, 2.5, 3, 31), (2.5, 4.0, 3, 31)], M=1.0,
+                                  chi=0.6, radial_filter_on=True, sh_keep_l=20, dt=0.002, seed=14, noise_amp=1e-6)
     # three shells of 288 angular points and a filter keeping l <= 7
     return workloads.Workload(name="ragged", shells=[(1.5, 2.5, 5, 11), (2.5, 4.0, 5, 11), (4.0, 7.0, 5, 11)],
                               M=1.0, chi=0.5, radial_filter_on=True, sh_keep_l=7, dt=0.005, seed=9, noise_amp=1e-7)
 
 
-@pytest.mark.parametrize("wname", ["schwarzschild", "kerr2", "even_L", "ragged"])
+@pytest.mark.parametrize("wname", ["schwarzschild", "kerr2", "even_L", "ragged", "fft_rings_32", "fft_rings_64"])
 def test_folded_transposes_equal_the_separable_ones(wname):
     """The reverse mode with the folded angular maps (the default) and with the
     plain separable transposes applies the same linear maps, so gh_rhs_vjp and
@@ -281,7 +289,7 @@ def test_folded_transposes_equal_the_separable_ones(wname):
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("wname", ["kerr2", "even_L", "ragged"])
+@pytest.mark.parametrize("wname", ["kerr2", "even_L", "ragged", "fft_rings_32", "fft_rings_64"])
 def test_folded_filter_transpose_is_exact(wname):
     """A step with dt = 0 is the filters alone, so its VJP is F^T:
     <ybar, F x> = <F^T ybar, x> to rounding, with the folded maps.  The step
@@ -302,3 +310,38 @@ def test_folded_filter_transpose_is_exact(wname):
                        torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda"))
     lhs, rhs = float(y @ to_host(fx)), float(to_host(fty) @ x)
     assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(y), (lhs, rhs)
+
+
+def test_folded_transposes_with_both_paths_in_one_domain():
+    """Independent holes of L = 7 (ring FFTs: three launches per map) and
+    L = 11, 5 (the quarter-folded DFT: one fused launch) in one domain: the
+    folded reverse mode equals the separable one on every hole."""
+    from paper_1804_09101_gb300 import gh
+    holes = [dict(M=1.0, chi=0.3, shells=[(1.6, 8.0, 9, 7)], dt=0.004, seed=11),
+             dict(M=0.7, chi=0.8, shells=[(0.9, 3.0, 7, 11), (3.0, 9.0, 7, 11)], dt=0.003, seed=12),
+             dict(M=1.5, chi=0.0, shells=[(2.5, 20.0, 11, 5)], dt=0.006, seed=13)]
+    shells = [sh + (b,) for b, h in enumerate(holes) for sh in h["shells"]]
+    doms = []
+    for alg in (gh.GH_ALG_SEPARABLE_FOLDED, gh.GH_ALG_SEPARABLE):
+        dom = gh.Domain(shells, radial_filter_on=True, sh_keep_l=-2)
+        gh.gh_set_algorithm(dom, alg)
+        doms.append(dom)
+    u = doms[0].new_state()
+    for dom in doms:                     # each domain's holes (background, gauge) and time-step scales
+        ud = dom.new_state()
+        for b, h in enumerate(holes):
+            gh.gh_set_analytic_kerr_schild(dom, b, h["M"], h["chi"], ud)
+            gh.gh_set_dt_scale(dom, b, h["dt"])
+        u.copy_(ud)
+    rng = np.random.default_rng(73)
+    u += to_dev(rng.standard_normal(u.numel()) * 1e-7)
+    v = to_dev(rng.standard_normal(u.numel()))
+    out = []
+    for dom in doms:
+        ub = dom.new_state()
+        gh.gh_rhs_vjp(dom, u, v, ub)
+        ub2 = dom.new_state()
+        gh.gh_rk4_step_vjp(dom, 1.0, u, v, ub2, torch.zeros(dom.vjp_work_size, dtype=torch.float64, device="cuda"))
+        out.append((to_host(ub), to_host(ub2)))
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), np.abs(a - b).max() / np.abs(b).max()
