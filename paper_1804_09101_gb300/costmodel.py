@@ -147,7 +147,7 @@ def fold_rank_m0(K, hs, n_out):
     return K + 1
 
 
-FOLD_FFT_NPHI = (16, 32, 64)   # rings transformed by the register FFT (fold_angular_kernel)
+FOLD_FFT_NPHI = (16, 32, 64)   # rings transformed by register FFTs (fold_fft_analysis/synthesis_kernel)
 
 
 def ring_fft_flops(nph, forward=True):
@@ -167,10 +167,12 @@ def ring_fft_flops(nph, forward=True):
 
 
 def fold_angular_flops(shells, K=None, two=True):
-    """FP64 flops of one folded separable launch (fold_angular_kernel), per
-    (r, field) row.  For N_phi = 16, 32, 64 the phi transforms are register
-    FFTs (ring_fft_flops per ring and transform, N_theta M for the s/t split);
-    otherwise the quarter-folded DFT: fold 8 (W - 1) N_theta; phase A half M (4 W + 2) plus
+    """FP64 flops of one folded separable map, per (r, field) row.  For
+    N_phi = 16, 32, 64 (three launches: fold_fft_analysis_kernel,
+    fold_legendre_kernel, fold_fft_synthesis_kernel) the phi transforms are
+    register FFTs (ring_fft_flops per ring and transform, N_theta M for the
+    s/t split); otherwise (fold_angular_kernel) the quarter-folded DFT: fold
+    8 (W - 1) N_theta; phase A half M (4 W + 2) plus
     (hs - half) M 2 W for an odd N_theta's equator ring; phase B per mode
     (cos m, and sin m for m >= 1): fused, n_out hs 4 hs (two dot products of
     length hs per output, each a multiply and hs - 1 FMAs, and the two
