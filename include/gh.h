@@ -193,8 +193,15 @@ gh_status gh_rk4_step(gh_domain* dom, double dt, double* u, double* work, double
  * schedule, overlap, frame, outer condition, S2 filter); it is separate from
  * gh_rk4_graph_capture's graph.  Synchronises the stream before returning.
  * Pinned host buffers (cudaHostAlloc, cudaHostRegister) copy asynchronously at
- * full speed; pageable ones work too.  Errors: GH_EINVAL for n_steps < 1 or a
- * NULL buffer, GH_ENOMEM on the first call, GH_ECUDA. */
+ * full speed; pageable ones work too.  With n_steps == 1, both buffers pinned
+ * and at least one filter on, no separate copies run: the step's first radial
+ * derivative reads u_in over the host link (writing the device state as it
+ * goes) and its last filter writes u_out, so the transfers overlap those
+ * kernels' arithmetic; that form is captured once per (dt, norm2_out null or
+ * not, u_in, u_out) and gives the same bits as the copy form.  The domain's
+ * filters run SH truncation first, then the radial filter (they commute).
+ * Errors: GH_EINVAL for n_steps < 1 or a NULL buffer, GH_ENOMEM on the first
+ * call, GH_ECUDA. */
 gh_status gh_rk4_step_host(gh_domain* dom, double dt, int n_steps, const double* u_in, double* u_out,
                            double* norm2_out);
 

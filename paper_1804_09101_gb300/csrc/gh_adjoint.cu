@@ -1167,9 +1167,19 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
     u3 = w3;
     u4 = w4;
   }
-  // transposed filters: u_new = Fa(Fr(v))  =>  g = Fr^T Fa^T ubar_np1
+  // transposed filters: u_new = Fr(Fa(v))  =>  g = Fa^T Fr^T ubar_np1
   const double* gin = ubar_np1;
-  if (d->params.sh_keep_l != -1) {
+  const bool ang_f = d->params.sh_keep_l != -1;
+  if (d->params.radial_filter_on) {
+    double* dst = ang_f ? kb : g;
+    gh::radial_adjoint_kernel<true, false><<<d->rad_blocks, gh::ADJ_RAD_THREADS,
+                                             gh::radial_adjoint_smem_bytes(d->max_n_r), d->stream>>>(
+        d->shells_d, d->n_shells, d->rad_block_begin_d, gin, dst, d->max_n_r);
+    d->launches++;
+    GH_ACUDA(d, cudaGetLastError());
+    gin = dst;
+  }
+  if (ang_f) {                           // gin is ubar_np1 or kb here, never g
     if (d->sh_filter_mode == GH_SH_FILTER_TENSOR) {
       GH_ACUDA(d, gh::launch_tensor_filter_transpose(d, gin, g));
     } else if (d->algorithm == 2) {
@@ -1181,15 +1191,6 @@ gh_status step_vjp_impl(gh_domain* d, double dt, const double* u_n, const double
       GH_ACUDA(d, cudaGetLastError());
     }
     gin = g;
-  }
-  if (d->params.radial_filter_on) {
-    double* dst = (gin == g) ? kb : g;
-    gh::radial_adjoint_kernel<true, false><<<d->rad_blocks, gh::ADJ_RAD_THREADS,
-                                             gh::radial_adjoint_smem_bytes(d->max_n_r), d->stream>>>(
-        d->shells_d, d->n_shells, d->rad_block_begin_d, gin, dst, d->max_n_r);
-    d->launches++;
-    GH_ACUDA(d, cudaGetLastError());
-    gin = dst;
   }
   // ubar_n starts as g (the direct u_n term of u_n + dt/6 (...)); g itself is
   // kept for the stage cotangents

@@ -765,27 +765,33 @@ gh_status derivatives(gh_domain* d, const double* u) {
   return GH_OK;
 }
 
-gh_status filters(gh_domain* d, double* src, double* u, double* tmp) {
-  // src -> (radial) -> (angular) -> u ; tmp must not alias src or u
+gh_status filters(gh_domain* d, double* src, double* u, double* tmp, double* dest_host = nullptr) {
+  // src -> (angular) -> (radial) -> u, or -> dest_host (pinned host memory, as
+  // seen from the device) when given; tmp must not alias src or u.  The two
+  // filters act on different axes (the angular maps on the rows, the radial on
+  // the columns of the [row][angle] layout), so they commute; the radial one
+  // runs last because its column-wise stores are coalesced, also into host memory.
   const bool rad = d->params.radial_filter_on != 0;
   const bool ang = d->params.sh_keep_l != -1;
+  double* dest = dest_host ? dest_host : u;
   double* cur = src;
-  if (rad) {
-    ProfScope p(d, GH_K_RADIAL_FILTER);
-    GH_CUDA(d, gh::launch_radial(d, cur, d->d_r, true));
-    cur = d->d_r;
-  }
   if (ang) {
     ProfScope p(d, GH_K_ANGULAR_FILTER);
-    double* dst = (cur == u) ? tmp : u;
+    double* dst = rad ? d->d_r : ((cur == dest) ? tmp : dest);
     if (d->sh_filter_mode == GH_SH_FILTER_TENSOR)
       GH_CUDA(d, gh::launch_tensor_filter(d, cur, dst));
     else
       GH_CUDA(d, gh::launch_angular_filter(d, cur, dst));
     cur = dst;
   }
-  if (cur != u)
-    GH_CUDA(d, cudaMemcpyAsync(u, cur, sizeof(double) * d->state, cudaMemcpyDeviceToDevice, d->stream));
+  if (rad) {
+    ProfScope p(d, GH_K_RADIAL_FILTER);
+    double* dst = (cur == dest) ? tmp : dest;
+    GH_CUDA(d, gh::launch_radial(d, cur, dst, true));
+    cur = dst;
+  }
+  if (cur != dest)
+    GH_CUDA(d, cudaMemcpyAsync(dest, cur, sizeof(double) * d->state, cudaMemcpyDefault, d->stream));
   return GH_OK;
 }
 
@@ -898,7 +904,24 @@ void invalidate_host_graph(gh_domain* d) {
     cudaGraphExecDestroy(d->host_graph);
     d->host_graph = nullptr;
   }
+  if (d->host_graph_io) {
+    cudaGraphExecDestroy(d->host_graph_io);
+    d->host_graph_io = nullptr;
+  }
 }
+
+// The device address of a pinned (page-locked, mapped) host buffer, or NULL
+// for any other pointer (pageable host memory, device memory).
+const double* device_view(const double* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();                  // clear the sticky-free error of an unknown pointer
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return (const double*)a.devicePointer;
+}
+double* device_view(double* p) { return const_cast<double*>(device_view((const double*)p)); }
 
 void invalidate_graph(gh_domain* d) {
   if (d->graph_exec) {
@@ -1356,6 +1379,7 @@ gh_status gh_destroy_domain(gh_domain* d) {
   if (d->ev_join) cudaEventDestroy(d->ev_join);
   if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
   if (d->host_graph) cudaGraphExecDestroy(d->host_graph);
+  if (d->host_graph_io) cudaGraphExecDestroy(d->host_graph_io);
   for (void* p : d->owned) cudaFree(p);
   delete d;
   return GH_OK;
@@ -1430,11 +1454,14 @@ gh_status gh_set_dt_scale(gh_domain* d, int bh, double scale) {
 
 }  // extern "C"
 
+extern "C" gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double* norm2_pre,
+                                   double* stages, const double* host_in = nullptr, double* host_out = nullptr);
+
 namespace {
 // One gh_rk4_step captured on a private stream and instantiated into *exec
 // (replacing what it held); nothing executes and the clock stays.
 gh_status capture_step(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, cudaGraphExec_t* exec,
-                       long long* n_launches) {
+                       long long* n_launches, const double* host_in = nullptr, double* host_out = nullptr) {
   GH_CUDA(d, cudaStreamSynchronize(d->stream));
   cudaStream_t saved = d->stream;
   cudaStream_t cap = nullptr;
@@ -1448,7 +1475,8 @@ gh_status capture_step(gh_domain* d, double dt, double* u, double* work, double*
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   gh_status st = GH_OK;
   if (e == cudaSuccess) {
-    st = gh_rk4_step(d, dt, u, work, norm2_pre);
+    st = check_latched(d);
+    if (st == GH_OK) st = rk4_step_impl(d, dt, u, work, norm2_pre, nullptr, host_in, host_out);
     cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
     if (e2 != cudaSuccess && st == GH_OK) e = e2;
   }
@@ -1603,7 +1631,12 @@ gh_status rotation_guard(gh_domain* d) {
   return GH_OK;
 }
 
-gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages) {
+// host_in / host_out (host-memory step, device-visible pinned buffers): the
+// stage-1 radial map reads u_n from host_in and writes its device image to u,
+// the angular maps then read u; the last filter writes u_{n+1} to host_out
+// (u keeps u_n).  Both NULL: the device step.
+gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double* norm2_pre, double* stages,
+                        const double* host_in, double* host_out) {
   if (gh_status s = rotation_guard(d)) return s;
   static const int fidx[4] = {0, 1, 1, 2};     // stage times t, t + dt/2, t + dt/2, t + dt
   double* us = work;
@@ -1620,7 +1653,16 @@ gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double
     const double* in = (stage == 1) ? u : (stages ? stages + (stage - 2) * d->state : us);
     d->frd = d->frames_d ? d->frames_d + fidx[stage - 1] : nullptr;
     if (d->map_gen && (stage != 3)) GH_CUDA(d, gh::launch_map_stage(d));   // stage 3 shares stage 2's time
-    if (gh_status s = derivatives(d, in)) return s;
+    if (stage == 1 && host_in) {
+      {
+        ProfScope p(d, GH_K_RADIAL);
+        GH_CUDA(d, gh::launch_radial_on(d, host_in, d->d_r, false, d->stream, u));
+      }
+      ProfScope p(d, GH_K_ANGULAR);
+      GH_CUDA(d, gh::launch_angular_deriv(d, u));
+    } else if (gh_status s = derivatives(d, in)) {
+      return s;
+    }
     double* target = (stage == 4) ? (filt ? us : u) : (stages ? stages + (stage - 1) * d->state : us);
     {
       ProfScope p(d, GH_K_POINTWISE);
@@ -1636,7 +1678,9 @@ gh_status rk4_step_impl(gh_domain* d, double dt, double* u, double* work, double
     }
   }
   if (filt) {
-    if (gh_status s = filters(d, us, u, k)) return s;
+    if (gh_status s = filters(d, us, u, k, host_out)) return s;
+  } else if (host_out) {
+    GH_CUDA(d, cudaMemcpyAsync(host_out, u, sizeof(double) * d->state, cudaMemcpyDefault, d->stream));
   }
   if (!stages) d->time += dt;   // gh_rk4_step advances the clock; the adjoint's recomputation does not
   return GH_OK;
@@ -1669,9 +1713,47 @@ gh_status gh_rk4_step_host(gh_domain* d, double dt, int n_steps, const double* u
     d->host_work = (double*)pw;
     d->host_norm = (double*)pn;
   }
-  // the step as a captured graph on the domain's own buffers (captured once per
-  // dt and norm choice, and again after a setter changes the step's launches)
   const int want_norm = norm2_out ? 1 : 0;
+  // One step with both buffers in pinned (device-visible) host memory and a
+  // filter at the end of the step: the step's own kernels move the state, the
+  // stage-1 radial map reading u_n from u_in and the last filter writing
+  // u_{n+1} to u_out, so the link transfers overlap the FP64 work of those
+  // kernels instead of preceding and following the step.
+  const bool filt = d->params.radial_filter_on || d->params.sh_keep_l != -1;
+  const double* hin = nullptr;
+  double* hout = nullptr;
+  if (n_steps == 1 && filt) {
+    hin = device_view(u_in);
+    hout = device_view(u_out);
+    if (!hin || !hout) hin = hout = nullptr;
+  }
+  if (hin) {
+    if (!d->host_graph_io || d->host_graph_io_dt != dt || d->host_graph_io_norm != want_norm ||
+        d->host_graph_io_in != hin || d->host_graph_io_out != hout) {
+      if (d->host_graph_io) {
+        cudaGraphExecDestroy(d->host_graph_io);
+        d->host_graph_io = nullptr;
+      }
+      if (gh_status s = capture_step(d, dt, d->host_u, d->host_work, want_norm ? d->host_norm : nullptr,
+                                     &d->host_graph_io, &d->host_graph_io_launches, hin, hout))
+        return s;
+      d->host_graph_io_dt = dt;
+      d->host_graph_io_norm = want_norm;
+      d->host_graph_io_in = hin;
+      d->host_graph_io_out = hout;
+    }
+    GH_CUDA(d, cudaGraphLaunch(d->host_graph_io, d->stream));
+    d->launches += d->host_graph_io_launches;
+    d->time += dt;
+    if (norm2_out)
+      GH_CUDA(d, cudaMemcpyAsync(norm2_out, d->host_norm, sizeof(double) * (size_t)d->n_shells,
+                                 cudaMemcpyDeviceToHost, d->stream));
+    GH_CUDA(d, cudaStreamSynchronize(d->stream));
+    return GH_OK;
+  }
+  // otherwise copies around the step as a captured graph on the domain's own
+  // buffers (captured once per dt and norm choice, and again after a setter
+  // changes the step's launches)
   if (!d->host_graph || d->host_graph_dt != dt || d->host_graph_norm != want_norm) {
     if (gh_status s = capture_step(d, dt, d->host_u, d->host_work, want_norm ? d->host_norm : nullptr,
                                    &d->host_graph, &d->host_graph_launches))

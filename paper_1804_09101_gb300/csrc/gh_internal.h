@@ -325,6 +325,14 @@ struct gh_domain {
   double host_graph_dt = 0.0;
   int host_graph_norm = 0;
   long long host_graph_launches = 0;
+  // its one-step form that reads and writes the caller's pinned buffers from
+  // the step's kernels (also keyed by those buffers' device addresses)
+  cudaGraphExec_t host_graph_io = nullptr;
+  double host_graph_io_dt = 0.0;
+  int host_graph_io_norm = 0;
+  const double* host_graph_io_in = nullptr;
+  double* host_graph_io_out = nullptr;
+  long long host_graph_io_launches = 0;
   // device state, RK4 work area and norms of gh_rk4_step_host (allocated on first use)
   double* host_u = nullptr;
   double* host_work = nullptr;
@@ -348,7 +356,10 @@ namespace gh {
 
 // Kernel launchers (gh_kernels.cu).
 cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filter);
-cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st);
+// copy != NULL: the input is also written to copy (one row group reads it: the
+// input may be pinned host memory, the copy its device image).
+cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st,
+                             double* copy = nullptr);
 // radial and angular derivative maps of in into d_r, d_th, d_ph: side by side
 // on two streams when d->overlap, else one after the other
 cudaError_t launch_derivatives(gh_domain* d, const double* in);

@@ -45,7 +45,8 @@ constexpr int MAXR = 64;
 template <bool FILTER, int CH>
 __global__ void __launch_bounds__(RAD_THREADS)
 radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __restrict__ begin,
-              const double* __restrict__ in, double* __restrict__ out, int max_n) {
+              const double* __restrict__ in, double* __restrict__ out, int max_n,
+              double* __restrict__ copy) {
   extern __shared__ double Vs[];           // [max n_r][RAD_THREADS], then the block's folded rows
   const int s = find_segment(begin, n_shells, blockIdx.x);
   const ShellDev& sh = shells[s];
@@ -61,7 +62,14 @@ radial_kernel(const ShellDev* __restrict__ shells, int n_shells, const int* __re
   const bool valid = col < cols;
   const double* src = in + sh.off + col;
   double* v = Vs + threadIdx.x;
-  for (int r = 0; r < n; ++r) v[r * RAD_THREADS] = valid ? src[(long long)r * cols] : 0.0;
+  // copy != NULL: the input (the state in pinned host memory, read once) is
+  // also written to copy at the same offsets (row group 0 only)
+  double* cp = (copy && blockIdx.y == 0 && valid) ? copy + sh.off + col : nullptr;
+  for (int r = 0; r < n; ++r) {
+    const double x = valid ? src[(long long)r * cols] : 0.0;
+    v[r * RAD_THREADS] = x;
+    if (cp) cp[(long long)r * cols] = x;
+  }
   for (int j = 0; j < h; ++j) {            // this thread's column, folded in place
     const double a = v[j * RAD_THREADS], b = v[(n - 1 - j) * RAD_THREADS];
     v[j * RAD_THREADS] = a + b;
@@ -1294,13 +1302,15 @@ cudaError_t launch_radial(gh_domain* d, const double* in, double* out, bool filt
   return launch_radial_on(d, in, out, filter, d->stream);
 }
 
-cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st) {
+cudaError_t launch_radial_on(gh_domain* d, const double* in, double* out, bool filter, cudaStream_t st,
+                             double* copy) {
   const size_t smem = radial_smem_bytes(d->max_n_r);
   const int ch = filter ? d->radf_chains : d->rad_chains;
-  const dim3 grid(d->rad_blocks, filter ? d->radf_groups : d->rad_groups);
+  // with a copy-out the input is read by one row group only (it may be host memory)
+  const dim3 grid(d->rad_blocks, copy ? 1 : (filter ? d->radf_groups : d->rad_groups));
 #define GH_RAD(F, C)                                                                       \
   radial_kernel<F, C><<<grid, RAD_THREADS, smem, st>>>(d->shells_d, d->n_shells,           \
-                                                               d->rad_block_begin_d, in, out, d->max_n_r)
+                                                               d->rad_block_begin_d, in, out, d->max_n_r, copy)
   if (filter) {
     if (ch == 4) GH_RAD(true, 4); else if (ch == 3) GH_RAD(true, 3); else GH_RAD(true, 2);
   } else {

@@ -207,7 +207,9 @@ def _host_ptr(t, name, numel):
 
 def gh_rk4_step_host(dom, dt, n_steps, u_in, u_out, norm2=None):
     """gh_rk4_step_host: n_steps RK4 steps of a HOST state (CPU float64 tensors,
-    pinned for full-speed copies); copies in, steps on the device, copies out."""
+    pinned for full-speed copies); copies in, steps on the device, copies out.
+    One step with pinned buffers: the step's own kernels read u_in and write
+    u_out, overlapping the link transfers with the step's work."""
     dom._stream()
     dom._check(_lib.gh_rk4_step_host(dom.handle, float(dt), int(n_steps),
                                      _host_ptr(u_in, "u_in", dom.state_size),

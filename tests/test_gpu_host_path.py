@@ -74,3 +74,51 @@ def test_host_path_rotating_frame_advances_the_clock():
     assert np.array_equal(host, dev)
     assert abs(t_host - gh.gh_get_time(dom)) == 0.0
     assert abs(t_host - (0.2 + 3 * w.dt)) < 1e-14
+
+
+def _one_step_calls(gh, dom, dt, u0, n, pinned=True, in_place=False):
+    src = u0.cpu()
+    if pinned:
+        src = src.pin_memory()
+    out = src if in_place else (torch.empty_like(src).pin_memory() if pinned else torch.empty_like(src))
+    for _ in range(n):
+        gh.gh_rk4_step_host(dom, dt, 1, src, out)
+        if not in_place:
+            src.copy_(out)
+    return out.numpy().copy()
+
+
+def test_one_step_calls_move_the_state_from_the_step_kernels():
+    """With one step per call and pinned buffers the step's first radial map
+    reads u_in and its last filter writes u_out; the results equal device
+    steps bit for bit, also in place (u_in == u_out), after a setter change,
+    with a rotating frame, and from pageable buffers (plain copies)."""
+    gh, w, dom, u0 = _setup()
+    dev = _device_steps(gh, dom, w.dt, u0, 3)
+    assert np.array_equal(_one_step_calls(gh, dom, w.dt, u0, 3), dev)
+    assert np.array_equal(_one_step_calls(gh, dom, w.dt, u0, 3, in_place=True), dev)
+    assert np.array_equal(_one_step_calls(gh, dom, w.dt, u0, 3, pinned=False), dev)
+    gh.gh_set_outer_bc(dom, gh.GH_BC_CONSTRAINT_PRESERVING)
+    cp = _one_step_calls(gh, dom, w.dt, u0, 2)
+    assert np.array_equal(cp, _device_steps(gh, dom, w.dt, u0, 2))
+    gh.gh_set_rotating_frame(dom, (0.0, 0.0, 1.0), 0.3)
+    gh.gh_set_time(dom, 0.1)
+    host = _one_step_calls(gh, dom, w.dt, u0, 2)
+    t_host = gh.gh_get_time(dom)
+    gh.gh_set_time(dom, 0.1)
+    assert np.array_equal(host, _device_steps(gh, dom, w.dt, u0, 2))
+    assert t_host == gh.gh_get_time(dom)
+
+
+def test_one_step_call_norms_match_the_device_step():
+    gh, w, dom, u0 = _setup()
+    src = u0.cpu().pin_memory()
+    out = torch.empty_like(src).pin_memory()
+    n_host = torch.zeros(len(w.shells), dtype=torch.float64)
+    gh.gh_rk4_step_host(dom, w.dt, 1, src, out, n_host)
+    u = u0.clone()
+    n_dev = torch.zeros(len(w.shells), dtype=torch.float64, device="cuda")
+    gh.gh_rk4_step(dom, w.dt, u, dom.new_work(), n_dev)
+    gh.gh_sync(dom)
+    assert np.array_equal(out.numpy(), u.cpu().numpy())
+    assert np.array_equal(n_host.numpy(), n_dev.cpu().numpy())
