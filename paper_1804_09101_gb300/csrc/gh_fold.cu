@@ -17,6 +17,11 @@
 // Per (r, field) row: about 2 (N_theta M (N/4+1) + n_out M N_theta N_theta/2 +
 // n_out N_theta (N/4+1) M) flops, M = 2K+1, instead of 2 M (N_theta N_phi +
 // n_out N_theta^2 + n_out N_theta N_phi).
+// For N_phi = 16, 32, 64 the phi transforms are real FFTs of each ring in
+// registers instead (about 570 FP64 instructions per 64-point ring and
+// transform, against about 1,200 for the folded DFT), and a map runs as three
+// launches (ring FFTs, Legendre stage, inverse ring FFTs) through state-sized
+// scratch; fold_angular_kernel serves the other N_phi in one launch.
 #include <cuda_runtime.h>
 
 #include <cmath>
