@@ -466,7 +466,9 @@ FoldHost fold_plan(const AngularGrid& g, int K, bool deriv) {
 #define GH_FOLD_FFT_MAX_NPHI 64
 #endif
 int fold_fft_log(const AngularGrid& g) {
-  if (g.nph > GH_FOLD_FFT_MAX_NPHI || g.nth % 2 != 0) return 0;
+  // the ring-FFT kernels take whole rows per warp of 32 rings and pair ring j
+  // with its mirror on adjacent lanes: N_theta must divide 32 (and be even)
+  if (g.nph > GH_FOLD_FFT_MAX_NPHI || g.nth % 2 != 0 || 32 % g.nth != 0) return 0;
   if (g.nph == 16) return 3;
   if (g.nph == 32) return 4;
   if (g.nph == 64) return 5;
