@@ -872,11 +872,20 @@ def measure_step_vjp(args, w):
     us = u.clone()
     step_ms = timed(lambda: gh.gh_rk4_step(dom, w.dt, us, work))
     vjp_ms = timed(lambda: gh.gh_rk4_step_vjp(dom, w.dt, u, ybar, ubar, vwork))
+    # the same VJP from stage states kept by the forward step (gh_rk4_step_save),
+    # as a checkpointed adjoint that stores stages would run it
+    stages = torch.zeros(3 * dom.state_size, dtype=torch.float64, device=dev)
+    uf = u.clone()
+    save_ms = timed(lambda: gh.gh_rk4_step_save(dom, w.dt, uf, work, stages))
+    gh.gh_rk4_step_save(dom, w.dt, u.clone(), work, stages)        # the stage states of u itself
+    saved_ms = timed(lambda: gh.gh_rk4_step_vjp_saved(dom, w.dt, u, stages, ybar, ubar, vwork))
     gh.gh_sync(dom)
     return dict(workload=w.name, points=w.points(), step_ms=step_ms, step_vjp_ms=vjp_ms,
-                step_vjp_over_step=vjp_ms / step_ms,
-                how="gh_rk4_step_vjp (recomputes the stage states) against gh_rk4_step, direct calls, "
-                    "CUDA events, L2 flushed before each call")
+                step_vjp_over_step=vjp_ms / step_ms, save_step_ms=save_ms, step_vjp_saved_ms=saved_ms,
+                step_vjp_saved_over_step=saved_ms / step_ms,
+                how="gh_rk4_step_vjp (recomputes the stage states) and gh_rk4_step_vjp_saved (stage states "
+                    "kept by gh_rk4_step_save) against gh_rk4_step, direct calls, CUDA events, L2 flushed "
+                    "before each call")
 
 
 def run_adjoint(args):
